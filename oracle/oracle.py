@@ -1,0 +1,194 @@
+"""ctypes front end of the FP64 CPU oracle (mm_oracle.c).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the benchmark's
+CPU-baseline leg are the only callers. Nothing here is shared with the CUDA
+path; the oracle library is compiled from its own C source with gcc
+(-O2, no fast-math, no floating-point contraction, so x86 and Arm hosts give
+the same results).
+
+All arrays are float64 numpy arrays in the layouts of mm_oracle.c:
+psi [ny][nx][nth], mb [ny][nx][nth][ns], u [2][ny][nx], mf/c/mtot [ny][nx].
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "mm_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle library in-tree (oracle/_build/liboracle.so)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-ffp-contract=off",
+                               "-fno-fast-math", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nth", C.c_int), ("ns", C.c_int),
+                ("L", C.c_double)]
+
+
+class _Rates(C.Structure):
+    _fields_ = [("v_walk", C.c_double), ("k_on", C.c_double), ("k_off", C.c_double),
+                ("glide", C.c_double), ("v_sp", C.c_double), ("force_scale", C.c_double),
+                ("ell", C.c_double), ("cfl", C.c_double)]
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.POINTER(C.c_double)
+            G, R = C.POINTER(_Grid), C.POINTER(_Rates)
+            lib.or_dt.argtypes = [G, R, P, P, P, P]
+            lib.or_init_free.argtypes = [G, P, P, P, P, P]
+            lib.or_substep.argtypes = [G, R, C.c_double, P, P, P, P, P, P]
+            lib.or_run.argtypes = [G, R, C.c_double, P, P, P, P, P, P, C.c_int]
+            lib.or_moments.argtypes = [G, R, P, P, P, P, P, P]
+            lib.or_tangent_substep.argtypes = [G, R, C.c_double, P, P, P, P, P, P, P, P, P, P]
+            lib.or_adjoint_substep.argtypes = [G, R, C.c_double, P, P, P, P, P, P, P, P, P, P]
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _grid(g) -> _Grid:
+    return _Grid(g.nx, g.ny, g.ntheta, g.ns, g.L)
+
+
+def _rates(r) -> _Rates:
+    return _Rates(r.v_walk, r.k_on, r.k_off, r.glide, r.v_sp, r.force_scale, r.ell, r.cfl)
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+FIELD_NAMES = ("rho", "Px", "Py", "Qxx", "Qxy", "C", "Mf", "Fx", "Fy", "Sxx", "Sxy", "Syy")
+SCALAR_NAMES = ("N_psi", "bound", "free", "motors", "polar_order", "mean_stress",
+                "sum_psi_cos", "sum_psi_sin")
+
+
+@dataclass
+class State:
+    """Oracle state: psi, mb, mf, c and the fixed total motor density mtot."""
+
+    grid: object
+    psi: np.ndarray
+    mb: np.ndarray
+    mf: np.ndarray
+    c: np.ndarray
+    mtot: np.ndarray
+
+    def copy(self) -> "State":
+        return State(self.grid, self.psi.copy(), self.mb.copy(), self.mf.copy(), self.c.copy(),
+                     self.mtot.copy())
+
+
+def make_state(grid, psi, mb=None, mtot=None) -> State:
+    """Set up a state: Mb (default 0), M (default 1), then C, the Alg. 2 clip
+    and Mf = M - C."""
+    g = grid
+    psi = np.ascontiguousarray(psi, dtype=np.float64).reshape(g.ny, g.nx, g.ntheta).copy()
+    mb = (np.zeros((g.ny, g.nx, g.ntheta, g.ns)) if mb is None
+          else np.ascontiguousarray(mb, dtype=np.float64).reshape(g.ny, g.nx, g.ntheta, g.ns).copy())
+    mtot = (np.ones((g.ny, g.nx)) if mtot is None
+            else np.ascontiguousarray(mtot, dtype=np.float64).reshape(g.ny, g.nx).copy())
+    mf = np.empty((g.ny, g.nx))
+    c = np.empty((g.ny, g.nx))
+    _check(_load().or_init_free(C.byref(_grid(g)), _p(psi), _p(mb), _p(mtot), _p(mf), _p(c)),
+           "init_free")
+    return State(g, psi, mb, mf, c, mtot)
+
+
+def dt(grid, rates, state: State, u: np.ndarray) -> float:
+    out = C.c_double(0.0)
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    _check(_load().or_dt(C.byref(_grid(grid)), C.byref(_rates(rates)), _p(state.psi),
+                         _p(state.mb), _p(u), C.byref(out)), "dt")
+    return out.value
+
+
+def run(grid, rates, state: State, u: np.ndarray, dt_: float, nsub: int) -> State:
+    """Advance nsub substeps in place; returns the same state object."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    _check(_load().or_run(C.byref(_grid(grid)), C.byref(_rates(rates)), float(dt_), _p(u),
+                          _p(state.psi), _p(state.mb), _p(state.mf), _p(state.c),
+                          _p(state.mtot), int(nsub)), "run")
+    return state
+
+
+def moments(grid, rates, state: State):
+    """Returns (fields dict name -> [ny][nx], scalars dict)."""
+    g = grid
+    f = np.empty((12, g.ny, g.nx))
+    s = np.empty(8)
+    _check(_load().or_moments(C.byref(_grid(g)), C.byref(_rates(rates)), _p(state.psi),
+                              _p(state.mb), _p(state.mf), _p(state.c), _p(f), _p(s)), "moments")
+    return dict(zip(FIELD_NAMES, f)), dict(zip(SCALAR_NAMES, s))
+
+
+def tangent_substep(grid, rates, dt_, u, du, dparams, state: State, dpsi, dmb, dmf):
+    """Tangent of one substep at `state` (not modified); dpsi/dmb/dmf updated in place.
+    dparams = (d k_off, d v_walk, d k_on)."""
+    dp = np.ascontiguousarray(dparams, dtype=np.float64)
+    _check(_load().or_tangent_substep(
+        C.byref(_grid(grid)), C.byref(_rates(rates)), float(dt_),
+        _p(np.ascontiguousarray(u, dtype=np.float64)), _p(np.ascontiguousarray(du, dtype=np.float64)),
+        _p(dp), _p(state.psi), _p(state.mb), _p(state.mf), _p(state.mtot), _p(dpsi), _p(dmb),
+        _p(dmf)), "tangent")
+
+
+def adjoint_substep(grid, rates, dt_, u, state: State, lpsi, lmb, lmf, lu, lp):
+    """Adjoint of one substep at `state` (state at step n, not modified).
+    lpsi/lmb/lmf: adjoint at n+1 in, at n out. lu [2][ny][nx] and
+    lp (k_off, v_walk, k_on) accumulate."""
+    _check(_load().or_adjoint_substep(
+        C.byref(_grid(grid)), C.byref(_rates(rates)), float(dt_),
+        _p(np.ascontiguousarray(u, dtype=np.float64)), _p(state.psi), _p(state.mb), _p(state.mf),
+        _p(state.mtot), _p(lpsi), _p(lmb), _p(lmf), _p(lu), _p(lp)), "adjoint")
+
+
+def substep_states(grid, rates, state: State, u, dt_, nsub: int) -> list[State]:
+    """States 0..nsub of a trajectory (for the adjoint sweep)."""
+    out = [state.copy()]
+    cur = state.copy()
+    for _ in range(nsub):
+        run(grid, rates, cur, u, dt_, 1)
+        out.append(cur.copy())
+    return out
+
+
+def adjoint(grid, rates, state0: State, u, dt_, nsub: int, lpsi, lmb, lmf):
+    """Reverse sweep over nsub substeps from state0 (all states stored).
+    Returns (lpsi0, lmb0, lmf0, lu, lp)."""
+    states = substep_states(grid, rates, state0, u, dt_, nsub)
+    lpsi = np.array(lpsi, dtype=np.float64, copy=True)
+    lmb = np.array(lmb, dtype=np.float64, copy=True)
+    lmf = np.array(lmf, dtype=np.float64, copy=True)
+    lu = np.zeros((2, grid.ny, grid.nx))
+    lp = np.zeros(3)
+    for n in range(nsub - 1, -1, -1):
+        adjoint_substep(grid, rates, dt_, u, states[n], lpsi, lmb, lmf, lu, lp)
+    return lpsi, lmb, lmf, lu, lp

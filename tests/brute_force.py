@@ -1,0 +1,109 @@
+"""Deliberately naive pure-Python expansion of one substep, for tiny grids.
+
+It is written independently of the oracle and in a different form, so that a
+slip in either shows up as a disagreement:
+  * psi transport is done in scatter form: every face flux is subtracted from
+    the donor side and added to the receiving side;
+  * the Superbee slope uses the ratio form phi(r) = max(0, min(2r,1), min(r,2))
+    times the forward difference (equal to the division-free form wherever the
+    forward difference is non-zero, and zero otherwise);
+  * the RK2 midpoint stages are applied to the whole motor array at once;
+  * every trigonometric value is recomputed where it is used.
+Model: Eq. 1-6 of the paper with the readings listed in the oracle's header.
+"""
+from __future__ import annotations
+
+import math
+
+
+def _phi_superbee(r: float) -> float:
+    return max(0.0, min(2.0 * r, 1.0), min(r, 2.0))
+
+
+def _slope(back: float, fwd: float) -> float:
+    if fwd == 0.0:
+        return 0.0
+    return _phi_superbee(back / fwd) * fwd
+
+
+def substep(grid, rates, dt, u, psi, mb, mf, mtot):
+    """One substep on nested Python lists; returns (psi, mb, mf, c) new lists.
+    psi[iy][ix][k], mb[iy][ix][k][j], u[c][iy][ix], mf/mtot[iy][ix]."""
+    nx, ny, nth, ns, L = grid.nx, grid.ny, grid.ntheta, grid.ns, grid.L
+    dx, dy, dth, ds = 1.0 / nx, 1.0 / ny, 2.0 * math.pi / nth, L / ns
+
+    nb = [[[sum(mb[iy][ix][k][j] for j in range(ns)) * ds for k in range(nth)]
+           for ix in range(nx)] for iy in range(ny)]
+
+    def vel(ix, iy, k):
+        V = rates.v_sp + rates.glide * nb[iy][ix][k]
+        th = k * dth
+        return (u[0][iy][ix] - V * math.cos(th), u[1][iy][ix] - V * math.sin(th))
+
+    dpsi = [[[0.0] * nth for _ in range(nx)] for _ in range(ny)]
+
+    def face(amount_vel, left, right, h):
+        (lx, ly, lk), (rx, ry, rk) = left, right
+        donor = psi[ly][lx][lk] if amount_vel > 0 else psi[ry][rx][rk]
+        flux = amount_vel * donor
+        dpsi[ly][lx][lk] -= dt * flux / h
+        dpsi[ry][rx][rk] += dt * flux / h
+
+    for iy in range(ny):
+        for ix in range(nx):
+            e = (ix + 1) % nx
+            n = (iy + 1) % ny
+            gxx = (u[0][iy][e] - u[0][iy][(ix - 1) % nx]) / (2 * dx)
+            gxy = (u[0][n][ix] - u[0][(iy - 1) % ny][ix]) / (2 * dy)
+            gyx = (u[1][iy][e] - u[1][iy][(ix - 1) % nx]) / (2 * dx)
+            gyy = (u[1][n][ix] - u[1][(iy - 1) % ny][ix]) / (2 * dy)
+            for k in range(nth):
+                ax = 0.5 * (vel(ix, iy, k)[0] + vel(e, iy, k)[0])
+                face(ax, (ix, iy, k), (e, iy, k), dx)
+                ay = 0.5 * (vel(ix, iy, k)[1] + vel(ix, n, k)[1])
+                face(ay, (ix, iy, k), (ix, n, k), dy)
+                ph = (k + 0.5) * dth
+                px, py = math.cos(ph), math.sin(ph)
+                # p_perp . (G p), p_perp = (-py, px), (G p)_a = sum_b G_ab p_b
+                om = -py * (gxx * px + gxy * py) + px * (gyx * px + gyy * py)
+                face(om, (ix, iy, k), (ix, iy, (k + 1) % nth), dth)
+
+    psi_new = [[[psi[iy][ix][k] + dpsi[iy][ix][k] for k in range(nth)] for ix in range(nx)]
+               for iy in range(ny)]
+
+    def rhs(M, mfree):
+        out = []
+        for j in range(ns):
+            def flux_right(jj):
+                if jj == ns - 1:
+                    return rates.v_walk * M[jj]
+                back = M[jj] - (M[jj - 1] if jj > 0 else 0.0)
+                fwd = M[jj + 1] - M[jj]
+                return rates.v_walk * (M[jj] + 0.5 * _slope(back, fwd))
+            fin = flux_right(j - 1) if j > 0 else 0.0
+            out.append(-(flux_right(j) - fin) / ds - rates.k_off * M[j] + rates.k_on * mfree)
+        return out
+
+    mb_new, c_new, mf_new = [], [], []
+    for iy in range(ny):
+        rowy_mb, rowy_c, rowy_mf = [], [], []
+        for ix in range(nx):
+            cell = []
+            for k in range(nth):
+                M = mb[iy][ix][k]
+                k1 = rhs(M, mf[iy][ix])
+                half = [M[j] + 0.5 * dt * k1[j] for j in range(ns)]
+                k2 = rhs(half, mf[iy][ix])
+                cell.append([M[j] + dt * k2[j] for j in range(ns)])
+            coarse = sum(psi_new[iy][ix][k] * sum(cell[k]) * ds * dth for k in range(nth))
+            if coarse > mtot[iy][ix]:
+                scale = mtot[iy][ix] / coarse
+                cell = [[v * scale for v in row] for row in cell]
+                coarse = mtot[iy][ix]
+            rowy_mb.append(cell)
+            rowy_c.append(coarse)
+            rowy_mf.append(mtot[iy][ix] - coarse)
+        mb_new.append(rowy_mb)
+        c_new.append(rowy_c)
+        mf_new.append(rowy_mf)
+    return psi_new, mb_new, mf_new, c_new

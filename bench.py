@@ -1,0 +1,358 @@
+"""Benchmark of the microscale kinetic step on GB300.
+
+A step is one macro step of the workload: prescribe that macro step's
+velocity (mm_set_velocity, which also recomputes the adaptive substep), run its
+substeps (mm_micro_step) and reduce the macroscale moments (mm_moments).
+Metric: micro-state cell-updates per second = nx*ny*ntheta*ns*substeps / time.
+
+Default workload "precision128": 128x128 periodic grid, 32 orientations, 32
+arclength nodes, 50 substeps per macro step, velocity from a seeded random
+divergence-free field (8 Fourier modes, amplitude 0.1) refreshed every macro
+step, mixed precision (float32 Mb/psi, float64 sums). The float64 path is timed
+on the same workload and reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload precision128|large512|adjoint64|cellular32]
+
+Under torchrun (N > 1) every rank advances its own instance of the workload
+(weak scaling, no collective in the data path); the time is the maximum over
+ranks. --impl reference times the float64 CPU oracle on the host cores (rank 0
+only) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1908_04279_gb300.inputs import (WORKLOADS, Rates, psi_isotropic_perturbed,  # noqa: E402
+                                           workload_velocity)
+
+METRIC = "micro-state cell-updates/s"
+UNIT = "cell-updates/s"
+STEP_KERNEL_SRC = os.path.join(ROOT, "paper_1908_04279_gb300", "csrc", "mm_step.cu")
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def algorithmic_bytes_per_launch(g, tsize: int) -> int:
+    """Bytes one substep launch must move at minimum: Mb read and written once
+    (2 * tsize per motor cell); per (cell, theta) psi read and written
+    (2 * tsize) and n_b read and written (2 * 8); per cell Mf read and written,
+    C written, M read and u read (4 * 8 + 2 * tsize)."""
+    cells = g.nx * g.ny
+    return (cells * g.ntheta * g.ns * 2 * tsize + cells * g.ntheta * (2 * tsize + 16)
+            + cells * (32 + 2 * tsize))
+
+
+def read_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def read_profile_traffic(workload: str, precision: str):
+    """DRAM bytes per launch of the substep kernel from the committed ncu
+    summary, if it was taken on the current kernel source (sha256 match)."""
+    path = os.path.join(ROOT, "profiles", f"k_substep_{workload}_{precision}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
+    if not m or not h:
+        return None
+    cur = hashlib.sha256(open(STEP_KERNEL_SRC, "rb").read()).hexdigest()
+    return float(m.group(1)) if h.group(1) == cur else None
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = list(csv.reader(open(self.path)))
+        os.unlink(self.path)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def time_oracle_sample(name: str, budget_s: float = 12.0, max_sub: int = 40):
+    """Float64 CPU oracle on a bounded sample of the workload: the workload's
+    initial state and first velocity, as many substeps as fit in budget_s."""
+    from oracle import oracle as O
+    w = WORKLOADS[name]
+    g, r = w["grid"], Rates()
+    st = O.make_state(g, psi_isotropic_perturbed(g, w["seed"]))
+    u = workload_velocity(name, 0)
+    dt = O.dt(g, r, st, u)
+    t0 = time.perf_counter()
+    O.run(g, r, st, u, dt, 1)
+    t1 = time.perf_counter() - t0
+    n = max(1, min(max_sub, int(budget_s / max(t1, 1e-9)) - 1))
+    t0 = time.perf_counter()
+    O.run(g, r, st, u, dt, n)
+    el = time.perf_counter() - t0
+    return {"value": g.micro_cells * n / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{name}: {n} substeps of the float64 oracle on 1 host core "
+                      f"({g.nx}x{g.ny}x{g.ntheta}x{g.ns})"}
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    from oracle import oracle as O
+    name = args.workload
+    w = WORKLOADS[name]
+    g, r = w["grid"], Rates()
+    st = O.make_state(g, psi_isotropic_perturbed(g, w["seed"]))
+    u = workload_velocity(name, 0)
+    dt = O.dt(g, r, st, u)
+    # a step of the reference arm: one substep of the workload (a bounded
+    # sample of its macro step), timed on one host core
+    per_step = 1
+    for _ in range(args.warmup):
+        O.run(g, r, st, u, dt, per_step)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.run(g, r, st, u, dt, per_step)
+    el = time.perf_counter() - t0
+    units = g.micro_cells * per_step * args.steps
+    value = units / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": name, "grid": f"{g.nx}x{g.ny}", "ntheta": g.ntheta, "ns": g.ns,
+                       "substeps_per_step": per_step},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps of {per_step} oracle substep(s) of "
+                                       f"{name} on 1 host core"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise RuntimeError("no CUDA device: the benchmark needs the GPU path")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1908_04279_gb300 import build as B
+    if rank == 0:
+        B.build()
+    if world > 1:
+        torch.distributed.barrier()
+    from paper_1908_04279_gb300 import mm
+
+    name = args.workload
+    w = WORKLOADS[name]
+    g, r = w["grid"], Rates()
+    nsub = w["substeps"]
+    n_vel = max(w["macro"], 1)
+    stream = torch.cuda.current_stream(dev)
+    vels_host = [np.ascontiguousarray(workload_velocity(name, m)) for m in range(n_vel)]
+    vels_dev = [torch.tensor(v, device=dev) for v in vels_host]
+    psi0 = psi_isotropic_perturbed(g, w["seed"])
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    fields_dev = torch.empty(12 * g.nx * g.ny, dtype=torch.float64, device=dev)
+
+    def device_run(precision, steps, warmup, timed_kernel=True):
+        sim = mm.Simulation(g, r, precision, stream=stream.cuda_stream)
+        sim.set_state(psi0)
+        m = 0
+        for _ in range(warmup):
+            sim.set_velocity(vels_dev[m % n_vel]); m += 1
+            sim.step(nsub)
+            sim.moments(fields=fields_dev)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+        step_ms, kern_ms = [], []
+        for _ in range(steps):
+            flush.zero_()  # L2 flush between timed steps, outside the timed events
+            e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+            e0.record(stream)
+            sim.set_velocity(vels_dev[m % n_vel]); m += 1
+            e1.record(stream)
+            sim.step(nsub)
+            e2.record(stream)
+            sim.moments(fields=fields_dev)
+            e3.record(stream)
+            e3.synchronize()
+            step_ms.append(e0.elapsed_time(e3))
+            kern_ms.append(e1.elapsed_time(e2))
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        sim.close()
+        return sum(step_ms), sum(kern_ms)
+
+    def e2e_run(precision, steps, warmup):
+        """Through the public API with host buffers: every step copies its
+        velocity from pinned host memory and reads the moments back."""
+        sim = mm.Simulation(g, r, precision, stream=stream.cuda_stream)
+        sim.set_state(psi0)
+        pinned = [torch.from_numpy(v).pin_memory() for v in vels_host]
+        out = torch.empty(12 * g.nx * g.ny, dtype=torch.float64).pin_memory()
+        m = 0
+        for _ in range(warmup):
+            sim.set_velocity(pinned[m % n_vel]); m += 1
+            sim.step(nsub)
+            sim.moments(fields=out)
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            torch.distributed.barrier()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            sim.set_velocity(pinned[m % n_vel]); m += 1
+            sim.step(nsub)
+            sim.moments(fields=out)
+        torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        sim.close()
+        return el, pinned[0].numel() * 8, out.numel() * 8 + 64
+
+    units_per_step = g.micro_cells * nsub
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms, kern_ms = device_run("fp32", args.steps, args.warmup)
+    clk = clocks.stop()
+    fp64_steps = max(2, min(args.steps, 3))
+    fp64_ms, fp64_kern = device_run("fp64", fp64_steps, 1)
+    e2e_s, h2d, d2h = e2e_run("fp32", args.steps, args.warmup)
+
+    t = torch.tensor([total_ms, kern_ms, fp64_ms, e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    total_ms, kern_ms, fp64_ms, e2e_s = t.tolist()
+
+    value = world * units_per_step * args.steps / (total_ms * 1e-3)
+    launch_ms = kern_ms / (args.steps * nsub)
+    peak, peak_src = read_peaks()
+    algo = algorithmic_bytes_per_launch(g, 4)
+    achieved = algo / (launch_ms * 1e-3) / 1e9
+    traffic = read_profile_traffic(name, "fp32")
+    fp64_value = world * units_per_step * fp64_steps / (fp64_ms * 1e-3)
+    if rank == 0:
+        cpu = time_oracle_sample(name) if world == 1 or rank == 0 else None
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": name, "grid": f"{g.nx}x{g.ny}", "ntheta": g.ntheta, "ns": g.ns,
+                       "substeps_per_step": nsub, "precision": "float32 Mb/psi, float64 sums",
+                       "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                       "parallelism": f"{world} independent instance(s), one per GPU"},
+            "fp64": {"value": fp64_value, "unit": UNIT, "steps": fp64_steps,
+                     "ms_per_step": fp64_ms / fp64_steps,
+                     "kernel_ms_per_launch": fp64_kern / (fp64_steps * nsub),
+                     "fp32_over_fp64": value / fp64_value},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_substep (float32)", "peak_source": peak_src,
+                         "kernel_ms_per_launch": launch_ms,
+                         "algorithmic_bytes_per_launch": algo},
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * units_per_step * args.steps / e2e_s, "unit": UNIT,
+                    "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": args.steps * (nsub + 3),
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="precision128", choices=sorted(WORKLOADS))
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,160 @@
+/*
+ * mm.h -- C ABI of the GB300 microscale kinetic step of the micro-macro
+ * gliding-motility-assay model (Cook & Shinar, arXiv:1908.04279).
+ *
+ * One handle holds one simulation instance resident on one GPU: the bound-
+ * motor density Mb(x, theta, s) (Sec. 2, the high-dimensional density of
+ * Eq. 4), the filament density Psi(x, theta) (Eq. 1), the free, coarse and
+ * total motor densities (Eq. 5-6), the prescribed in-plane fluid velocity and
+ * the substep dt. Every step of the path runs in the library's CUDA kernels;
+ * there is no CPU fallback: without a usable CUDA device every call that
+ * needs one returns MM_ERR_CUDA.
+ *
+ * Grid and layouts (all row-major, float64 at this boundary in both
+ * precisions):
+ *   the unit periodic square with nx * ny cells, dx = 1/nx, dy = 1/ny, cell
+ *   centres at ((i + 1/2) dx, (j + 1/2) dy);
+ *   orientations theta_k = k * 2 pi / ntheta (Sec. 2: theta and s uniform);
+ *   arclength nodes s_j = -L/2 + (j + 1/2) L / ns on the filament.
+ *   psi  [ny][nx][ntheta]         mb [ny][nx][ntheta][ns]
+ *   u    [2][ny][nx]   (u_x then u_y)
+ *   mtot, mf, c [ny][nx]
+ *
+ * Memory: the caller owns every buffer it passes; the handle owns its device
+ * state (allocated in mm_create, released in mm_destroy). A flag on_device
+ * says whether a pointer is a device pointer (read or written in stream
+ * order on the handle's stream) or a host pointer (the call synchronises the
+ * stream before it returns). A handle is not thread-safe; distinct handles
+ * may be used from distinct threads.
+ *
+ * Errors: every call returns an mm_status; no exception crosses the ABI.
+ * mm_last_error(h) gives a human-readable message for the last failing call
+ * on h (for a NULL handle: the last mm_create failure of this thread).
+ */
+#ifndef MM_H
+#define MM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mm_handle mm_handle;
+
+/* Resolution (Sec. 2: x, y on a regular square grid; theta and s uniform).
+ * Limits: nx, ny >= 1; 1 <= ntheta <= 1024; L > 0; one s-row is spread over
+ * at most one warp, so ns <= 128 (multiple of 4) or <= 32 (otherwise) in
+ * MM_FP32_MIXED, and ns <= 64 (even) or <= 32 (odd) in MM_FP64. Other sizes
+ * return MM_ERR_UNSUPPORTED. */
+typedef struct {
+  int nx, ny, ntheta, ns;
+  double L;
+} mm_grid;
+
+/* Nondimensional parameters.
+ *   v_walk  walking speed of bound motor heads (Eq. 4, the d_s term); >= 0
+ *   k_on    binding rate (Eq. 4)          k_off  unbinding rate (Eq. 4)
+ *   glide, v_sp  gliding speed V = v_sp + glide * n_b of a filament carrying
+ *           n_b = sum_j Mb ds bound motors (Eq. 2's -V_sp p term, with the
+ *           motor dependence read into it)
+ *   force_scale, ell  F and l/L of the motor force, Eq. 10
+ *   cfl     Courant number of the adaptive substep */
+typedef struct {
+  double v_walk, k_on, k_off;
+  double glide, v_sp;
+  double force_scale, ell;
+  double cfl;
+} mm_rates;
+
+typedef enum {
+  MM_FP64 = 0,       /* every array and every operation in float64 */
+  MM_FP32_MIXED = 1  /* Mb, psi and u stored and stepped in float32; s-row
+                        sums, coarse, free and total motor densities, the
+                        global sums and the mass correction in float64 */
+} mm_precision;
+
+typedef enum {
+  MM_OK = 0,
+  MM_ERR_INVALID = 1,     /* bad argument: NULL, non-positive size, NaN rate */
+  MM_ERR_OOM = 2,         /* the device has not enough free memory */
+  MM_ERR_CUDA = 3,        /* a CUDA runtime call failed (see mm_last_error) */
+  MM_ERR_UNSUPPORTED = 4, /* valid but not supported (v_walk < 0, ns too large) */
+  MM_ERR_TIMEOUT = 5,     /* a bounded device-side wait gave up */
+  MM_ERR_NONFINITE = 6,   /* a global sum came out NaN or infinite */
+  MM_ERR_STATE = 7        /* call out of order (no state or velocity yet,
+                             adjoint without a matching recording) */
+} mm_status;
+
+/* Create an instance (Sec. 3.1: all microscale data resident on the GPU).
+ * stream: a cudaStream_t (NULL = the legacy default stream) on which every
+ * kernel of this handle runs. The state starts as psi = 1/(2 pi), Mb = 0,
+ * M = 1 (Mf = 1) with zero velocity and no dt; call mm_set_state and
+ * mm_set_velocity before stepping. */
+mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision prec,
+                    void* stream, mm_handle** out);
+mm_status mm_destroy(mm_handle* h);
+mm_status mm_set_stream(mm_handle* h, void* stream);
+mm_status mm_set_rates(mm_handle* h, const mm_rates* rates);
+
+/* Load a state. psi (required), mb (NULL: all zero), mtot (NULL: all one).
+ * Computes n_b and the coarse density C = sum_k psi n_b dtheta (Eq. 5),
+ * applies the scale-down of Alg. 2 where C > M, and sets Mf = M - C (Eq. 6). */
+mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const double* mtot,
+                       int on_device);
+/* Export the state; any output pointer may be NULL. In MM_FP32_MIXED the
+ * pending mass-correction factor is applied to psi on export. */
+mm_status mm_get_state(mm_handle* h, double* psi, double* mb, double* mf, double* c,
+                       int on_device);
+
+/* Prescribe the in-plane velocity u (held fixed over the following substeps)
+ * and recompute the adaptive substep from the current state (Sec. 2: the
+ * outer step is limited by the advective fluxes of Eq. 1, the inner one by the
+ * motor speed and the binding and unbinding rates of Eq. 4):
+ *   dt = cfl / max(v_walk/ds, max(|ax|/dx + |ay|/dy), max|omega|/dtheta,
+ *                  k_off + k_on L max_cell sum_k psi dtheta),
+ * with a = u - V p and omega the Jeffery rotation rate at theta faces. */
+mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device);
+mm_status mm_get_dt(mm_handle* h, double* dt);
+/* Override the substep (e.g. to compare runs at the same dt). dt > 0. */
+mm_status mm_set_dt(mm_handle* h, double dt);
+
+/* Advance n_substeps substeps (Alg. 1 inner loop, with psi advanced inside
+ * each substep). Each substep:
+ *   1. psi by Eq. 1 in donor-cell flux form in x, y and theta;
+ *   2. every s-row of Mb by Eq. 4, Superbee-limited walking flux plus binding
+ *      and unbinding, midpoint RK2 with Mf frozen (Alg. 2 half and full
+ *      stage);
+ *   3. n_b, the coarse density (Eq. 5) with psi at the new time, the
+ *      scale-down of Alg. 2, and Mf = M - C (Eq. 6).
+ * Asynchronous on the handle's stream; launched as a captured CUDA graph. */
+mm_status mm_micro_step(mm_handle* h, int n_substeps);
+
+/* Macroscale moments (Alg. 1 after the inner loop), all float64.
+ * fields (may be NULL) receives [12][ny][nx]:
+ *   0 rho = sum psi dtheta    1,2 P = sum psi p dtheta
+ *   3,4 Q = sum psi (p p - I/2) dtheta (xx, xy)    5 C (Eq. 5)   6 Mf (Eq. 6)
+ *   7,8 F = F sum_k p psi n_b dtheta (Eq. 10 with anchors in the cell)
+ *   9,10,11 sigma_a = F ell sum_k p p psi m1 dtheta (xx, xy, yy),
+ *           m1 = sum_j s_j Mb ds (force dipole of an s-row)
+ * scalars (always written, host memory):
+ *   0 total filament number sum psi dx dy dtheta   1 bound sum C dx dy
+ *   2 free sum Mf dx dy   3 bound + free   4 polar order |sum psi e^{i theta}|
+ *   / sum psi   5 mean over cells of tr sigma_a   6 sum psi cos  7 sum psi sin.
+ * Returns MM_ERR_NONFINITE if a global sum is not finite. */
+typedef struct {
+  double* fields;
+  int fields_on_device;
+  double scalars[8];
+} mm_moments_out;
+mm_status mm_moments(mm_handle* h, mm_moments_out* out);
+
+const char* mm_last_error(const mm_handle* h);
+
+/* A short description of the build (library name and target architecture). */
+const char* mm_build_info(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MM_H */

@@ -24,8 +24,8 @@
  *   psi  [ny][nx][nth]        mb [ny][nx][nth][ns]     u [2][ny][nx]
  *   mf, c, mtot [ny][nx]
  * theta_k = k dth (dth = 2 pi / nth); s_j = -L/2 + (j + 1/2) ds (ds = L/ns);
- * the square is the unit periodic square, dx = 1/nx, dy = 1/ny, cell centres
- * at (i + 1/2) dx.
+ * the domain is the periodic square of sides lx, ly (the unit square unless a
+ * patch is being evaluated), dx = lx/nx, dy = ly/ny.
  *
  * Readings of the paper taken where it is silent (each is listed in the
  * design notes): motor anchors collapse to the filament-centre cell and the
@@ -37,9 +37,13 @@
 #include <stdlib.h>
 #include <string.h>
 
+/* lx, ly: side lengths of the periodic domain (1 for the unit square). A
+ * 3x3 periodic patch with lx = 3/N reproduces exactly the substep of its
+ * centre cell on an N-cell grid, since one substep reads only the 4
+ * neighbour cells. */
 typedef struct {
   int nx, ny, nth, ns;
-  double L;
+  double L, lx, ly;
 } or_grid;
 
 typedef struct {
@@ -56,8 +60,11 @@ enum { OR_OK = 0, OR_ERR_INVALID = 1, OR_ERR_NOMEM = 2 };
 static const double OR_PI = 3.14159265358979323846264338327950288;
 
 static int grid_ok(const or_grid* g) {
-  return g && g->nx > 0 && g->ny > 0 && g->nth > 0 && g->ns > 0 && g->L > 0.0;
+  return g && g->nx > 0 && g->ny > 0 && g->nth > 0 && g->ns > 0 && g->L > 0.0 && g->lx > 0.0 &&
+         g->ly > 0.0;
 }
+static double dx_of(const or_grid* g) { return g->lx / g->nx; }
+static double dy_of(const or_grid* g) { return g->ly / g->ny; }
 
 static size_t ncell(const or_grid* g) { return (size_t)g->nx * (size_t)g->ny; }
 static size_t cidx(const or_grid* g, int ix, int iy) { return (size_t)iy * g->nx + ix; }
@@ -110,7 +117,7 @@ static double superbee(double a, double b, double* ca, double* cb) {
 static void vel_grad(const or_grid* g, const double* u, int ix, int iy, double G[4]) {
   const double* ux = u;
   const double* uy = u + ncell(g);
-  double dx = 1.0 / g->nx, dy = 1.0 / g->ny;
+  double dx = dx_of(g), dy = dy_of(g);
   int xp = wrap(ix + 1, g->nx), xm = wrap(ix - 1, g->nx);
   int yp = wrap(iy + 1, g->ny), ym = wrap(iy - 1, g->ny);
   G[0] = (ux[cidx(g, xp, iy)] - ux[cidx(g, xm, iy)]) / (2.0 * dx);
@@ -160,7 +167,7 @@ static double donor(double A, double pl, double pr) { return dmax(A, 0.0) * pl +
  * psi' = psi - dt [dFx/dx + dFy/dy + dFth/dth]. */
 static void psi_transport(const or_grid* g, const or_rates* r, double dt, const double* u,
                           const double* psi, const double* nb, double* out) {
-  double dx = 1.0 / g->nx, dy = 1.0 / g->ny, dth = dth_of(g);
+  double dx = dx_of(g), dy = dy_of(g), dth = dth_of(g);
   for (int iy = 0; iy < g->ny; ++iy)
     for (int ix = 0; ix < g->nx; ++ix) {
       double G[4];
@@ -227,7 +234,7 @@ static void motor_rhs(const or_grid* g, const or_rates* r, const double* M, doub
 int or_dt(const or_grid* g, const or_rates* r, const double* psi, const double* mb,
           const double* u, double* dt_out) {
   if (!grid_ok(g) || !r || !psi || !mb || !u || !dt_out) return OR_ERR_INVALID;
-  double dx = 1.0 / g->nx, dy = 1.0 / g->ny, dth = dth_of(g);
+  double dx = dx_of(g), dy = dy_of(g), dth = dth_of(g);
   double* nb = (double*)malloc(sizeof(double) * ncell(g) * g->nth);
   if (!nb) return OR_ERR_NOMEM;
   rows_nb(g, mb, nb);
@@ -352,7 +359,7 @@ int or_moments(const or_grid* g, const or_rates* r, const double* psi, const dou
                const double* mf, const double* c, double* fields, double* scalars) {
   if (!grid_ok(g) || !r || !psi || !mb || !mf || !c || !fields || !scalars) return OR_ERR_INVALID;
   size_t nc = ncell(g);
-  double dth = dth_of(g), ds = ds_of(g), dA = (1.0 / g->nx) * (1.0 / g->ny);
+  double dth = dth_of(g), ds = ds_of(g), dA = dx_of(g) * dy_of(g);
   double Ntot = 0.0, bound = 0.0, freem = 0.0, sc = 0.0, ss = 0.0, spsi = 0.0, tr = 0.0;
   for (size_t i = 0; i < nc; ++i) {
     double f[12] = {0};
@@ -445,7 +452,7 @@ int or_tangent_substep(const or_grid* g, const or_rates* r, double dt, const dou
     return OR_ERR_INVALID;
   size_t rows = ncell(g) * g->nth, nc = ncell(g);
   int ns = g->ns;
-  double dx = 1.0 / g->nx, dy = 1.0 / g->ny, dth = dth_of(g), ds = ds_of(g);
+  double dx = dx_of(g), dy = dy_of(g), dth = dth_of(g), ds = ds_of(g);
   double* nb = (double*)malloc(sizeof(double) * rows);
   double* dnb = (double*)malloc(sizeof(double) * rows);
   double* pn = (double*)malloc(sizeof(double) * rows);
@@ -598,7 +605,7 @@ int or_adjoint_substep(const or_grid* g, const or_rates* r, double dt, const dou
     return OR_ERR_INVALID;
   size_t rows = ncell(g) * g->nth, nc = ncell(g);
   int ns = g->ns;
-  double dx = 1.0 / g->nx, dy = 1.0 / g->ny, dth = dth_of(g), ds = ds_of(g);
+  double dx = dx_of(g), dy = dy_of(g), dth = dth_of(g), ds = ds_of(g);
   double* nb = (double*)malloc(sizeof(double) * rows);
   double* pn = (double*)malloc(sizeof(double) * rows);
   double* lpn = (double*)malloc(sizeof(double) * rows);  /* adjoint of psi^{n+1} */

@@ -40,7 +40,7 @@ def build(force: bool = False) -> str:
 
 class _Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nth", C.c_int), ("ns", C.c_int),
-                ("L", C.c_double)]
+                ("L", C.c_double), ("lx", C.c_double), ("ly", C.c_double)]
 
 
 class _Rates(C.Structure):
@@ -73,7 +73,20 @@ def _p(a: np.ndarray):
 
 
 def _grid(g) -> _Grid:
-    return _Grid(g.nx, g.ny, g.ntheta, g.ns, g.L)
+    return _Grid(g.nx, g.ny, g.ntheta, g.ns, g.L, getattr(g, "lx", 1.0), getattr(g, "ly", 1.0))
+
+
+@dataclass(frozen=True)
+class PatchGrid:
+    """Grid of a periodic patch cut out of a larger grid (same dx, dy)."""
+
+    nx: int
+    ny: int
+    ntheta: int
+    ns: int
+    L: float
+    lx: float
+    ly: float
 
 
 def _rates(r) -> _Rates:
@@ -192,3 +205,25 @@ def adjoint(grid, rates, state0: State, u, dt_, nsub: int, lpsi, lmb, lmf):
     for n in range(nsub - 1, -1, -1):
         adjoint_substep(grid, rates, dt_, u, states[n], lpsi, lmb, lmf, lu, lp)
     return lpsi, lmb, lmf, lu, lp
+
+
+def patch_substep(grid, rates, dt_, u, psi, mb, mf, mtot, cells):
+    """One substep for selected cells only, each evaluated on the 3x3 periodic
+    patch around it (one substep reads only a cell's 4 neighbours, so the
+    patch centre equals the full-grid result). psi/mb/mf/mtot/u are the full
+    float64 arrays (numpy, any layout-compatible view); cells is a list of
+    (iy, ix). Returns a list of dicts psi [nth], mb [nth][ns], mf, c."""
+    g = grid
+    pg = PatchGrid(3, 3, g.ntheta, g.ns, g.L, 3.0 / g.nx, 3.0 / g.ny)
+    out = []
+    for iy, ix in cells:
+        ys = [(iy + d) % g.ny for d in (-1, 0, 1)]
+        xs = [(ix + d) % g.nx for d in (-1, 0, 1)]
+        sel = np.ix_(ys, xs)
+        st = State(pg, np.ascontiguousarray(psi[sel]), np.ascontiguousarray(mb[sel]),
+                   np.ascontiguousarray(mf[sel]), np.zeros((3, 3)), np.ascontiguousarray(mtot[sel]))
+        uu = np.ascontiguousarray(np.stack([u[0][sel], u[1][sel]]))
+        run(pg, rates, st, uu, dt_, 1)
+        out.append(dict(psi=st.psi[1, 1].copy(), mb=st.mb[1, 1].copy(), mf=float(st.mf[1, 1]),
+                        c=float(st.c[1, 1])))
+    return out

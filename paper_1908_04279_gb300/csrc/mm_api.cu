@@ -1,0 +1,639 @@
+// Host side of the C ABI (include/mm.h): handle life cycle, state transfer,
+// velocity and adaptive substep, the substep launch plan (captured CUDA
+// graphs), and the moments.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "mm_internal.cuh"
+
+using mm::DevParams;
+using mm::StepArgs;
+
+namespace {
+thread_local std::string g_create_error;
+const double kPi = 3.14159265358979323846264338327950288;
+constexpr size_t kStagingDoubles = size_t(1) << 22;  // 32 MiB of float64 staging
+}  // namespace
+
+struct mm_handle {
+  mm_grid g{};
+  mm_rates r{};
+  mm_precision prec = MM_FP64;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream used only for graph capture
+  int device = 0, sms = 0;
+  long long ncells = 0;
+  size_t rows = 0, mbn = 0, tsz = 8;
+  void* mb = nullptr;
+  void* psi[2] = {nullptr, nullptr};
+  double* nb[2] = {nullptr, nullptr};
+  double* m1 = nullptr;
+  double* mf = nullptr;
+  double* c = nullptr;
+  double* mtot = nullptr;
+  void* u = nullptr;
+  double* u64 = nullptr;
+  void* trig = nullptr;
+  double* trig64 = nullptr;
+  double* partial = nullptr;
+  double* fields = nullptr;
+  double* staging = nullptr;
+  DevParams* prm = nullptr;
+  int npartial = 0;
+  int parity = 0;
+  double dt = 0.0;
+  bool have_state = false, have_vel = false, have_dt = false;
+  // substep launch configuration
+  int V = 1, seg = 1, block = 32, rpt = 1, grid_step = 1, grid_mom = 1;
+  size_t smem = 0;
+  std::map<long long, cudaGraphExec_t> graphs;
+  bool use_graphs = true;
+  std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+mm_status fail(mm_handle* h, mm_status st, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_create_error = msg;
+  return st;
+}
+
+mm_status cuda_fail(mm_handle* h, const char* what, cudaError_t e) {
+  return fail(h, MM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                                  cudaGetErrorString(e) + ")");
+}
+
+#define CK(...)                                               \
+  do {                                                        \
+    cudaError_t e_ = (__VA_ARGS__);                           \
+    if (e_ != cudaSuccess) return cuda_fail(h, #__VA_ARGS__, e_); \
+  } while (0)
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+mm_status check_rates(const mm_rates* r, mm_handle* h) {
+  if (!r) return fail(h, MM_ERR_INVALID, "rates is NULL");
+  const double v[8] = {r->v_walk, r->k_on, r->k_off, r->glide,
+                       r->v_sp, r->force_scale, r->ell, r->cfl};
+  for (double x : v)
+    if (!std::isfinite(x)) return fail(h, MM_ERR_INVALID, "a rate is not finite");
+  if (r->k_on < 0.0 || r->k_off < 0.0) return fail(h, MM_ERR_INVALID, "k_on and k_off must be >= 0");
+  if (!(r->cfl > 0.0)) return fail(h, MM_ERR_INVALID, "cfl must be > 0");
+  if (r->v_walk < 0.0)
+    return fail(h, MM_ERR_UNSUPPORTED, "v_walk < 0 (walking toward the minus end) is not supported");
+  return MM_OK;
+}
+
+mm_status free_all(mm_handle* h) {
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  void* ptrs[] = {h->mb,  h->psi[0], h->psi[1], h->nb[0],   h->nb[1],  h->m1,
+                  h->mf,  h->c,      h->mtot,   h->u,       h->u64,    h->trig,
+                  h->trig64, h->partial, h->fields, h->staging, h->prm};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (h->cap) cudaStreamDestroy(h->cap);
+  return MM_OK;
+}
+
+mm_status upload_params(mm_handle* h) {
+  DevParams p{};
+  p.dt = h->dt;
+  p.psi_scale = 1.0;
+  p.v_walk = h->r.v_walk;
+  p.k_on = h->r.k_on;
+  p.k_off = h->r.k_off;
+  p.glide = h->r.glide;
+  p.v_sp = h->r.v_sp;
+  p.force_scale = h->r.force_scale;
+  p.ell = h->r.ell;
+  CK(cudaMemcpy(h->prm, &p, sizeof(p), cudaMemcpyHostToDevice));
+  return MM_OK;
+}
+
+template <typename T>
+StepArgs<T> step_args(mm_handle* h, int parity, int write_m1) {
+  StepArgs<T> a{};
+  a.nx = h->g.nx;
+  a.ny = h->g.ny;
+  a.nth = h->g.ntheta;
+  a.ns = h->g.ns;
+  a.seg = h->seg;
+  a.rpt = h->rpt;
+  a.ncells = h->ncells;
+  a.inv_dx = (double)h->g.nx;
+  a.inv_dy = (double)h->g.ny;
+  a.dth = 2.0 * kPi / h->g.ntheta;
+  a.inv_dth = 1.0 / a.dth;
+  a.ds = h->g.L / h->g.ns;
+  a.L = h->g.L;
+  a.mb = (T*)h->mb;
+  a.psi_in = (const T*)h->psi[parity];
+  a.psi_out = (T*)h->psi[parity ^ 1];
+  a.nb_in = h->nb[parity];
+  a.nb_out = h->nb[parity ^ 1];
+  a.m1 = h->m1;
+  a.mf = h->mf;
+  a.c = h->c;
+  a.mtot = h->mtot;
+  a.u = (const T*)h->u;
+  a.trig = (const T*)h->trig;
+  a.partial = h->partial;
+  a.prm = h->prm;
+  a.write_m1 = write_m1;
+  a.mass_correct = h->prec == MM_FP32_MIXED ? 1 : 0;
+  return a;
+}
+
+cudaError_t launch_one(mm_handle* h, int parity, int write_m1, cudaStream_t s) {
+  if (h->prec == MM_FP64) {
+    StepArgs<double> a = step_args<double>(h, parity, write_m1);
+    return h->V == 2 ? mm::launch_substep<double, 2>(a, h->grid_step, h->block, h->smem, s)
+                     : mm::launch_substep<double, 1>(a, h->grid_step, h->block, h->smem, s);
+  }
+  StepArgs<float> a = step_args<float>(h, parity, write_m1);
+  return h->V == 4 ? mm::launch_substep<float, 4>(a, h->grid_step, h->block, h->smem, s)
+                   : mm::launch_substep<float, 1>(a, h->grid_step, h->block, h->smem, s);
+}
+
+mm_status configure(mm_handle* h) {
+  const int ns = h->g.ns, nth = h->g.ntheta;
+  const int vmax = h->prec == MM_FP64 ? 2 : 4;
+  h->V = ns % vmax == 0 ? vmax : 1;
+  const int nl = ns / h->V;
+  if (nl > 32)
+    return fail(h, MM_ERR_UNSUPPORTED, "ns too large: one s-row must fit in one warp");
+  int seg = 1;
+  while (seg < nl) seg <<= 1;
+  h->seg = seg;
+  long long want = (long long)nth * seg;
+  int block = 256;
+  if (want < 256) block = (int)((want + 31) / 32 * 32);
+  h->block = block;
+  const int slots = block / seg;
+  h->rpt = (nth + slots - 1) / slots;
+  h->smem = h->prec == MM_FP64 ? mm::substep_smem<double>(nth) : mm::substep_smem<float>(nth);
+  int bps = 0;
+  cudaError_t e;
+  if (h->prec == MM_FP64)
+    e = h->V == 2 ? mm::substep_occupancy<double, 2>(block, h->smem, &bps)
+                  : mm::substep_occupancy<double, 1>(block, h->smem, &bps);
+  else
+    e = h->V == 4 ? mm::substep_occupancy<float, 4>(block, h->smem, &bps)
+                  : mm::substep_occupancy<float, 1>(block, h->smem, &bps);
+  CK(e);
+  if (bps < 1) return fail(h, MM_ERR_UNSUPPORTED, "substep kernel cannot be resident");
+  long long g = (long long)bps * h->sms;
+  if (g > h->ncells) g = h->ncells;
+  h->grid_step = (int)g;
+  long long gm = 4LL * h->sms;
+  if (gm > h->ncells) gm = h->ncells;
+  h->grid_mom = (int)gm;
+  h->npartial = std::max(h->grid_step, 8 * h->grid_mom);
+  return MM_OK;
+}
+
+// Copy a float64 array of n elements from (host or device) src into the
+// device array dst of the handle's precision, in staging chunks for host src.
+mm_status put_array(mm_handle* h, void* dst, const double* src, size_t n, int on_device) {
+  if (h->prec == MM_FP64) {
+    CK(cudaMemcpyAsync(dst, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                       h->stream));
+    return MM_OK;
+  }
+  float* d = (float*)dst;
+  if (on_device) {
+    CK(mm::launch_convert<float, double>(d, src, n, nullptr, h->stream));
+    return MM_OK;
+  }
+  for (size_t off = 0; off < n; off += kStagingDoubles) {
+    size_t m = std::min(kStagingDoubles, n - off);
+    CK(cudaMemcpyAsync(h->staging, src + off, m * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(mm::launch_convert<float, double>(d + off, h->staging, m, nullptr, h->stream));
+  }
+  return MM_OK;
+}
+
+// Inverse of put_array; scale (device pointer or NULL) multiplies on export.
+mm_status get_array(mm_handle* h, double* dst, const void* src, size_t n, int on_device,
+                    const double* scale) {
+  if (h->prec == MM_FP64 && !scale) {
+    CK(cudaMemcpyAsync(dst, src, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream));
+    return MM_OK;
+  }
+  if (on_device) {
+    if (h->prec == MM_FP64)
+      CK(mm::launch_convert<double, double>(dst, (const double*)src, n, scale, h->stream));
+    else
+      CK(mm::launch_convert<double, float>(dst, (const float*)src, n, scale, h->stream));
+    return MM_OK;
+  }
+  for (size_t off = 0; off < n; off += kStagingDoubles) {
+    size_t m = std::min(kStagingDoubles, n - off);
+    if (h->prec == MM_FP64)
+      CK(mm::launch_convert<double, double>(h->staging, (const double*)src + off, m, scale, h->stream));
+    else
+      CK(mm::launch_convert<double, float>(h->staging, (const float*)src + off, m, scale, h->stream));
+    CK(cudaMemcpyAsync(dst + off, h->staging, m * 8, cudaMemcpyDeviceToHost, h->stream));
+  }
+  return MM_OK;
+}
+
+mm_status run_init(mm_handle* h) {
+  const double ds = h->g.L / h->g.ns, dth = 2.0 * kPi / h->g.ntheta;
+  cudaError_t e;
+  if (h->prec == MM_FP64)
+    e = mm::launch_init_cells<double>((double*)h->mb, (const double*)h->psi[h->parity],
+                                      h->nb[h->parity], h->m1, h->mf, h->c, h->mtot, h->ncells,
+                                      h->g.ntheta, h->g.ns, ds, dth, h->g.L, h->stream);
+  else
+    e = mm::launch_init_cells<float>((float*)h->mb, (const float*)h->psi[h->parity],
+                                     h->nb[h->parity], h->m1, h->mf, h->c, h->mtot, h->ncells,
+                                     h->g.ntheta, h->g.ns, ds, dth, h->g.L, h->stream);
+  CK(e);
+  return MM_OK;
+}
+
+mm_status run_moments(mm_handle* h) {
+  const double dth = 2.0 * kPi / h->g.ntheta;
+  const double dA = (1.0 / h->g.nx) * (1.0 / h->g.ny);
+  cudaError_t e;
+  if (h->prec == MM_FP64)
+    e = mm::launch_moments<double>((const double*)h->psi[h->parity], h->nb[h->parity], h->m1,
+                                   h->mf, h->c, h->trig64, h->ncells, h->g.ntheta, dth, dA,
+                                   h->fields, h->partial, h->grid_mom, h->prm, h->stream);
+  else
+    e = mm::launch_moments<float>((const float*)h->psi[h->parity], h->nb[h->parity], h->m1,
+                                  h->mf, h->c, h->trig64, h->ncells, h->g.ntheta, dth, dA,
+                                  h->fields, h->partial, h->grid_mom, h->prm, h->stream);
+  CK(e);
+  return MM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision prec, void* stream,
+                    mm_handle** out) {
+  g_create_error.clear();
+  if (!grid || !out) return fail(nullptr, MM_ERR_INVALID, "grid or out is NULL");
+  *out = nullptr;
+  if (grid->nx < 1 || grid->ny < 1 || grid->ntheta < 1 || grid->ns < 1 || !finite_pos(grid->L))
+    return fail(nullptr, MM_ERR_INVALID, "grid sizes must be >= 1 and L > 0");
+  if (prec != MM_FP64 && prec != MM_FP32_MIXED)
+    return fail(nullptr, MM_ERR_INVALID, "unknown precision");
+  if (grid->ntheta > 1024) return fail(nullptr, MM_ERR_UNSUPPORTED, "ntheta > 1024");
+  {
+    mm_status st = check_rates(rates, nullptr);
+    if (st != MM_OK) return st;
+  }
+  const int vmax = prec == MM_FP64 ? 2 : 4;
+  if (grid->ns > 32 * vmax)
+    return fail(nullptr, MM_ERR_UNSUPPORTED, prec == MM_FP64 ? "ns > 64 in MM_FP64" : "ns > 128 in MM_FP32_MIXED");
+  if ((long long)grid->nx * grid->ny > (1LL << 40))
+    return fail(nullptr, MM_ERR_INVALID, "grid too large");
+
+  mm_handle* h = new mm_handle();
+  h->g = *grid;
+  h->r = *rates;
+  h->prec = prec;
+  h->stream = (cudaStream_t)stream;
+  h->tsz = prec == MM_FP64 ? 8 : 4;
+  h->ncells = (long long)grid->nx * grid->ny;
+  h->rows = (size_t)h->ncells * grid->ntheta;
+  h->mbn = h->rows * grid->ns;
+  auto bail = [&](mm_status st) {
+    g_create_error = h->err;
+    free_all(h);
+    delete h;
+    return st;
+  };
+  cudaError_t e = cudaGetDevice(&h->device);
+  if (e != cudaSuccess) {
+    cuda_fail(h, "cudaGetDevice", e);
+    return bail(MM_ERR_CUDA);
+  }
+  e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+  if (e != cudaSuccess) {
+    cuda_fail(h, "cudaDeviceGetAttribute", e);
+    return bail(MM_ERR_CUDA);
+  }
+  {
+    mm_status st = configure(h);
+    if (st != MM_OK) return bail(st);
+  }
+  const size_t nc = (size_t)h->ncells;
+  const size_t need = h->mbn * h->tsz + 2 * h->rows * h->tsz + 3 * h->rows * 8 + 3 * nc * 8 +
+                      2 * nc * (h->tsz + 8) + 12 * nc * 8 + kStagingDoubles * 8 +
+                      (size_t)h->npartial * 8 * 8 + 4 * grid->ntheta * (h->tsz + 8) + 4096;
+  size_t freeb = 0, totalb = 0;
+  e = cudaMemGetInfo(&freeb, &totalb);
+  if (e != cudaSuccess) {
+    cuda_fail(h, "cudaMemGetInfo", e);
+    return bail(MM_ERR_CUDA);
+  }
+  if (need > freeb) {
+    char buf[160];
+    snprintf(buf, sizeof buf, "needs %zu bytes of device memory, %zu free", need, freeb);
+    fail(h, MM_ERR_OOM, buf);
+    return bail(MM_ERR_OOM);
+  }
+#define ALLOC(ptr, bytes)                                        \
+  do {                                                           \
+    e = cudaMalloc((void**)&(ptr), (bytes));                     \
+    if (e != cudaSuccess) {                                      \
+      cuda_fail(h, "cudaMalloc " #ptr, e);                       \
+      return bail(e == cudaErrorMemoryAllocation ? MM_ERR_OOM : MM_ERR_CUDA); \
+    }                                                            \
+  } while (0)
+  ALLOC(h->mb, h->mbn * h->tsz);
+  ALLOC(h->psi[0], h->rows * h->tsz);
+  ALLOC(h->psi[1], h->rows * h->tsz);
+  ALLOC(h->nb[0], h->rows * 8);
+  ALLOC(h->nb[1], h->rows * 8);
+  ALLOC(h->m1, h->rows * 8);
+  ALLOC(h->mf, nc * 8);
+  ALLOC(h->c, nc * 8);
+  ALLOC(h->mtot, nc * 8);
+  ALLOC(h->u, 2 * nc * h->tsz);
+  ALLOC(h->u64, 2 * nc * 8);
+  ALLOC(h->trig, 4 * (size_t)grid->ntheta * h->tsz);
+  ALLOC(h->trig64, 4 * (size_t)grid->ntheta * 8);
+  ALLOC(h->partial, (size_t)h->npartial * 8 * 8);
+  ALLOC(h->fields, 12 * nc * 8);
+  ALLOC(h->staging, kStagingDoubles * 8);
+  ALLOC(h->prm, sizeof(DevParams));
+#undef ALLOC
+  e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cuda_fail(h, "cudaStreamCreate", e);
+    return bail(MM_ERR_CUDA);
+  }
+  // trigonometric tables: cos, sin at theta_k and at the faces theta_{k+1/2}
+  const int nth = grid->ntheta;
+  std::vector<double> tr(4 * (size_t)nth);
+  const double dth = 2.0 * kPi / nth;
+  for (int k = 0; k < nth; ++k) {
+    tr[k] = std::cos(k * dth);
+    tr[nth + k] = std::sin(k * dth);
+    tr[2 * nth + k] = std::cos((k + 0.5) * dth);
+    tr[3 * nth + k] = std::sin((k + 0.5) * dth);
+  }
+  e = cudaMemcpy(h->trig64, tr.data(), tr.size() * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    if (prec == MM_FP64) {
+      e = cudaMemcpy(h->trig, tr.data(), tr.size() * 8, cudaMemcpyHostToDevice);
+    } else {
+      std::vector<float> tf(tr.begin(), tr.end());
+      e = cudaMemcpy(h->trig, tf.data(), tf.size() * 4, cudaMemcpyHostToDevice);
+    }
+  }
+  if (e != cudaSuccess) {
+    cuda_fail(h, "upload trig tables", e);
+    return bail(MM_ERR_CUDA);
+  }
+  if (upload_params(h) != MM_OK) return bail(MM_ERR_CUDA);
+  // default state: psi = 1/(2 pi), Mb = 0, M = 1, u = 0
+  {
+    std::vector<double> ones(nc, 1.0), zeros(2 * nc, 0.0);
+    e = cudaMemcpy(h->mtot, ones.data(), nc * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(h->u64, zeros.data(), 2 * nc * 8, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(h->u, 0, 2 * nc * h->tsz);
+    if (e == cudaSuccess) e = cudaMemset(h->mb, 0, h->mbn * h->tsz);
+    if (e == cudaSuccess) e = cudaMemset(h->partial, 0, (size_t)h->npartial * 64);
+    if (e != cudaSuccess) {
+      cuda_fail(h, "initial state", e);
+      return bail(MM_ERR_CUDA);
+    }
+    std::vector<double> p0(h->rows, 1.0 / (2.0 * kPi));
+    if (mm_set_state(h, p0.data(), nullptr, nullptr, 0) != MM_OK) return bail(MM_ERR_CUDA);
+    h->have_state = false;
+  }
+  *out = h;
+  return MM_OK;
+}
+
+mm_status mm_destroy(mm_handle* h) {
+  if (!h) return MM_ERR_INVALID;
+  DeviceGuard dg(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_all(h);
+  delete h;
+  return MM_OK;
+}
+
+mm_status mm_set_stream(mm_handle* h, void* stream) {
+  if (!h) return MM_ERR_INVALID;
+  h->stream = (cudaStream_t)stream;
+  return MM_OK;
+}
+
+mm_status mm_set_rates(mm_handle* h, const mm_rates* rates) {
+  if (!h) return MM_ERR_INVALID;
+  mm_status st = check_rates(rates, h);
+  if (st != MM_OK) return st;
+  DeviceGuard dg(h->device);
+  h->r = *rates;
+  CK(cudaStreamSynchronize(h->stream));
+  double v[7] = {rates->v_walk, rates->k_on, rates->k_off, rates->glide,
+                 rates->v_sp, rates->force_scale, rates->ell};
+  CK(cudaMemcpy(&h->prm->v_walk, v, sizeof v, cudaMemcpyHostToDevice));
+  return MM_OK;
+}
+
+mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const double* mtot,
+                       int on_device) {
+  if (!h) return MM_ERR_INVALID;
+  if (!psi) return fail(h, MM_ERR_INVALID, "psi is NULL");
+  DeviceGuard dg(h->device);
+  mm_status st;
+  h->parity = 0;
+  if ((st = put_array(h, h->psi[0], psi, h->rows, on_device)) != MM_OK) return st;
+  if (mb) {
+    if ((st = put_array(h, h->mb, mb, h->mbn, on_device)) != MM_OK) return st;
+  } else {
+    CK(cudaMemsetAsync(h->mb, 0, h->mbn * h->tsz, h->stream));
+  }
+  if (mtot) {
+    CK(cudaMemcpyAsync(h->mtot, mtot, (size_t)h->ncells * 8,
+                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+  } else {
+    std::vector<double> ones((size_t)h->ncells, 1.0);
+    CK(cudaMemcpyAsync(h->mtot, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+  }
+  const double one = 1.0;
+  CK(cudaMemcpyAsync(&h->prm->psi_scale, &one, 8, cudaMemcpyHostToDevice, h->stream));
+  if ((st = run_init(h)) != MM_OK) return st;
+  // reference filament number for the float32 mass correction
+  if ((st = run_moments(h)) != MM_OK) return st;
+  double sum_psi = 0.0;
+  CK(cudaMemcpyAsync(&sum_psi, &h->prm->sum_psi, 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (!std::isfinite(sum_psi)) return fail(h, MM_ERR_NONFINITE, "psi sums to a non-finite value");
+  CK(cudaMemcpy(&h->prm->mass0, &sum_psi, 8, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(&h->prm->mass, &sum_psi, 8, cudaMemcpyHostToDevice));
+  h->have_state = true;
+  return MM_OK;
+}
+
+mm_status mm_get_state(mm_handle* h, double* psi, double* mb, double* mf, double* c,
+                       int on_device) {
+  if (!h) return MM_ERR_INVALID;
+  DeviceGuard dg(h->device);
+  mm_status st;
+  const double* scale = h->prec == MM_FP32_MIXED ? &h->prm->psi_scale : nullptr;
+  if (psi && (st = get_array(h, psi, h->psi[h->parity], h->rows, on_device, scale)) != MM_OK)
+    return st;
+  if (mb && (st = get_array(h, mb, h->mb, h->mbn, on_device, nullptr)) != MM_OK) return st;
+  const cudaMemcpyKind kd = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  if (mf) CK(cudaMemcpyAsync(mf, h->mf, (size_t)h->ncells * 8, kd, h->stream));
+  if (c) CK(cudaMemcpyAsync(c, h->c, (size_t)h->ncells * 8, kd, h->stream));
+  if (!on_device) CK(cudaStreamSynchronize(h->stream));
+  return MM_OK;
+}
+
+mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
+  if (!h) return MM_ERR_INVALID;
+  if (!u) return fail(h, MM_ERR_INVALID, "u is NULL");
+  DeviceGuard dg(h->device);
+  const size_t n = 2 * (size_t)h->ncells;
+  CK(cudaMemcpyAsync(h->u64, u, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                     h->stream));
+  if (h->prec == MM_FP64)
+    CK(cudaMemcpyAsync(h->u, h->u64, n * 8, cudaMemcpyDeviceToDevice, h->stream));
+  else
+    CK(mm::launch_convert<float, double>((float*)h->u, h->u64, n, nullptr, h->stream));
+  // maxima of the substep rule on the device, the rule itself in float64 here
+  CK(cudaMemsetAsync(h->prm->dtmax, 0, sizeof(h->prm->dtmax), h->stream));
+  const double dth = 2.0 * kPi / h->g.ntheta;
+  cudaError_t e;
+  if (h->prec == MM_FP64)
+    e = mm::launch_dt_max<double>((const double*)h->psi[h->parity], h->nb[h->parity], h->u64,
+                                  h->trig64, h->ncells, h->g.nx, h->g.ny, h->g.ntheta,
+                                  (double)h->g.nx, (double)h->g.ny, 1.0 / dth, dth, h->r.glide,
+                                  h->r.v_sp, h->prm, h->stream);
+  else
+    e = mm::launch_dt_max<float>((const float*)h->psi[h->parity], h->nb[h->parity], h->u64,
+                                 h->trig64, h->ncells, h->g.nx, h->g.ny, h->g.ntheta,
+                                 (double)h->g.nx, (double)h->g.ny, 1.0 / dth, dth, h->r.glide,
+                                 h->r.v_sp, h->prm, h->stream);
+  CK(e);
+  double mx[3];
+  CK(cudaMemcpyAsync(mx, h->prm->dtmax, sizeof mx, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const double ds = h->g.L / h->g.ns;
+  double rate = std::max(std::max(h->r.v_walk / ds, mx[0]),
+                         std::max(mx[1], h->r.k_off + h->r.k_on * h->g.L * mx[2]));
+  if (!(rate > 0.0) || !std::isfinite(rate))
+    return fail(h, MM_ERR_NONFINITE, "substep rule has no positive finite rate");
+  h->dt = h->r.cfl / rate;
+  CK(cudaMemcpy(&h->prm->dt, &h->dt, 8, cudaMemcpyHostToDevice));
+  h->have_vel = true;
+  h->have_dt = true;
+  return MM_OK;
+}
+
+mm_status mm_get_dt(mm_handle* h, double* dt) {
+  if (!h || !dt) return MM_ERR_INVALID;
+  if (!h->have_dt) return fail(h, MM_ERR_STATE, "no dt yet: call mm_set_velocity or mm_set_dt");
+  *dt = h->dt;
+  return MM_OK;
+}
+
+mm_status mm_set_dt(mm_handle* h, double dt) {
+  if (!h) return MM_ERR_INVALID;
+  if (!finite_pos(dt)) return fail(h, MM_ERR_INVALID, "dt must be finite and > 0");
+  DeviceGuard dg(h->device);
+  h->dt = dt;
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(&h->prm->dt, &h->dt, 8, cudaMemcpyHostToDevice));
+  h->have_dt = true;
+  return MM_OK;
+}
+
+mm_status mm_micro_step(mm_handle* h, int n) {
+  if (!h) return MM_ERR_INVALID;
+  if (n < 0) return fail(h, MM_ERR_INVALID, "n_substeps < 0");
+  if (n == 0) return MM_OK;
+  if (!h->have_state) return fail(h, MM_ERR_STATE, "no state: call mm_set_state first");
+  if (!h->have_vel) return fail(h, MM_ERR_STATE, "no velocity: call mm_set_velocity first");
+  if (!h->have_dt) return fail(h, MM_ERR_STATE, "no dt");
+  DeviceGuard dg(h->device);
+  if (!h->use_graphs) {
+    for (int i = 0; i < n; ++i) {
+      CK(launch_one(h, h->parity, i == n - 1, h->stream));
+      h->parity ^= 1;
+    }
+    return MM_OK;
+  }
+  const long long key = (long long)n * 2 + h->parity;
+  auto it = h->graphs.find(key);
+  if (it == h->graphs.end()) {
+    cudaGraph_t graph;
+    CK(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal));
+    int par = h->parity;
+    cudaError_t le = cudaSuccess;
+    for (int i = 0; i < n && le == cudaSuccess; ++i) {
+      le = launch_one(h, par, i == n - 1, h->cap);
+      par ^= 1;
+    }
+    cudaError_t ce = cudaStreamEndCapture(h->cap, &graph);
+    if (le != cudaSuccess) return cuda_fail(h, "substep launch during capture", le);
+    CK(ce);
+    cudaGraphExec_t exec;
+    cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    CK(ie);
+    it = h->graphs.emplace(key, exec).first;
+  }
+  CK(cudaGraphLaunch(it->second, h->stream));
+  h->parity ^= (n & 1);
+  return MM_OK;
+}
+
+mm_status mm_moments(mm_handle* h, mm_moments_out* out) {
+  if (!h || !out) return MM_ERR_INVALID;
+  DeviceGuard dg(h->device);
+  mm_status st;
+  if ((st = run_moments(h)) != MM_OK) return st;
+  if (out->fields)
+    CK(cudaMemcpyAsync(out->fields, h->fields, 12 * (size_t)h->ncells * 8,
+                       out->fields_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                       h->stream));
+  CK(cudaMemcpyAsync(out->scalars, h->prm->scalars, sizeof out->scalars, cudaMemcpyDeviceToHost,
+                     h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (double x : out->scalars)
+    if (!std::isfinite(x)) return fail(h, MM_ERR_NONFINITE, "a global moment is not finite");
+  return MM_OK;
+}
+
+const char* mm_last_error(const mm_handle* h) {
+  return h ? h->err.c_str() : g_create_error.c_str();
+}
+
+const char* mm_build_info(void) { return "libmm sm_103a (tcgen05-free streaming stencil path)"; }
+
+}  // extern "C"

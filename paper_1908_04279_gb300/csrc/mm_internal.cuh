@@ -1,0 +1,82 @@
+// Internal declarations shared by the CUDA translation units of libmm.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "mm.h"
+
+namespace mm {
+
+// Device-resident per-handle scalars. Kernels read dt and the rates from here
+// (not from launch arguments) so that captured graphs stay valid when dt or
+// the rates change.
+struct DevParams {
+  double dt;
+  double psi_scale;   // mass-correction factor applied to psi on load (FP32)
+  double mass0;       // target sum(psi) for the mass correction
+  double mass;        // sum(psi) after the last substep (float64)
+  double v_walk, k_on, k_off, glide, v_sp;
+  double force_scale, ell;
+  double dtmax[4];    // [adv, rot, rho_max, spare] for the dt rule (bits as u64)
+  double scalars[8];  // global moments
+  double sum_psi;     // sum of psi over all cells and angles (moments kernel)
+  unsigned int counter;   // last-block-done counter of the substep kernel
+  unsigned int counter2;  // last-block-done counter of the moments kernel
+  int status;
+  int pad;
+};
+
+// Everything a substep kernel touches, by value as a launch argument.
+template <typename T>
+struct StepArgs {
+  int nx, ny, nth, ns;
+  int seg;            // lanes per s-row segment (power of two <= 32)
+  int rpt;            // s-rows per thread per cell
+  long long ncells;
+  double inv_dx, inv_dy, inv_dth, dth, ds, L;
+  T* mb;              // [cells][nth][ns]
+  const T* psi_in;    // [cells][nth]
+  T* psi_out;
+  const double* nb_in;  // [cells][nth]
+  double* nb_out;
+  double* m1;         // [cells][nth]
+  double* mf;         // [cells]
+  double* c;          // [cells]
+  const double* mtot; // [cells]
+  const T* u;         // [2][cells]
+  const T* trig;      // [4][nth]: cos th_k, sin th_k, cos th_{k+1/2}, sin th_{k+1/2}
+  double* partial;    // [gridDim.x] per-CTA sum(psi)
+  DevParams* prm;
+  int write_m1;
+  int mass_correct;   // 1: compute psi_scale = mass0 / mass after the substep
+};
+
+// Kernel launchers (defined in mm_step.cu); V = values per lane.
+template <typename T, int V>
+cudaError_t launch_substep(const StepArgs<T>& a, int grid, int block, size_t smem,
+                           cudaStream_t s);
+template <typename T>
+size_t substep_smem(int nth);
+template <typename T, int V>
+cudaError_t substep_occupancy(int block, size_t smem, int* blocks_per_sm);
+
+// Auxiliary kernels (mm_aux.cu).
+template <typename TO, typename TI>
+cudaError_t launch_convert(TO* out, const TI* in, size_t n, const double* scale, cudaStream_t s);
+template <typename T>
+cudaError_t launch_init_cells(T* mb, const T* psi, double* nb, double* m1, double* mf,
+                              double* c, const double* mtot, long long ncells, int nth, int ns,
+                              double ds, double dth, double L, cudaStream_t s);
+template <typename T>
+cudaError_t launch_dt_max(const T* psi, const double* nb, const double* u64, const double* trig,
+                          long long ncells, int nx, int ny, int nth, double inv_dx,
+                          double inv_dy, double inv_dth, double dth, double glide, double vsp,
+                          DevParams* prm, cudaStream_t s);
+template <typename T>
+cudaError_t launch_moments(const T* psi, const double* nb, const double* m1, const double* mf,
+                           const double* c, const double* trig, long long ncells, int nth,
+                           double dth, double dA, double* fields, double* partial,
+                           int nblocks, DevParams* prm, cudaStream_t s);
+
+}  // namespace mm

@@ -1,0 +1,237 @@
+"""Thin ctypes binding of the C ABI in include/mm.h (argument marshalling only).
+
+Every computation runs in libmm.so's CUDA kernels; if the library is missing
+or no CUDA device is usable, the calls raise -- there is no fallback.
+
+Arrays: numpy float64 arrays are passed as host pointers; torch float64 CUDA
+tensors are passed as device pointers (read or written in stream order on the
+handle's stream, by default torch's current stream).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from .inputs import Grid, Rates
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libmm.so")
+
+MM_FP64 = 0
+MM_FP32_MIXED = 1
+STATUS = {0: "MM_OK", 1: "MM_ERR_INVALID", 2: "MM_ERR_OOM", 3: "MM_ERR_CUDA",
+          4: "MM_ERR_UNSUPPORTED", 5: "MM_ERR_TIMEOUT", 6: "MM_ERR_NONFINITE", 7: "MM_ERR_STATE"}
+FIELD_NAMES = ("rho", "Px", "Py", "Qxx", "Qxy", "C", "Mf", "Fx", "Fy", "Sxx", "Sxy", "Syy")
+SCALAR_NAMES = ("N_psi", "bound", "free", "motors", "polar_order", "mean_stress",
+                "sum_psi_cos", "sum_psi_sin")
+
+
+class MMError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class mm_grid(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("ntheta", C.c_int), ("ns", C.c_int),
+                ("L", C.c_double)]
+
+
+class mm_rates(C.Structure):
+    _fields_ = [("v_walk", C.c_double), ("k_on", C.c_double), ("k_off", C.c_double),
+                ("glide", C.c_double), ("v_sp", C.c_double), ("force_scale", C.c_double),
+                ("ell", C.c_double), ("cfl", C.c_double)]
+
+
+class mm_moments_out(C.Structure):
+    _fields_ = [("fields", C.c_void_p), ("fields_on_device", C.c_int),
+                ("scalars", C.c_double * 8)]
+
+
+# Every symbol include/mm.h declares, with its argument types.
+_P = C.c_void_p
+_H = C.c_void_p
+PROTOTYPES = {
+    "mm_create": ([C.POINTER(mm_grid), C.POINTER(mm_rates), C.c_int, _P, C.POINTER(C.c_void_p)], C.c_int),
+    "mm_destroy": ([_H], C.c_int),
+    "mm_set_stream": ([_H, _P], C.c_int),
+    "mm_set_rates": ([_H, C.POINTER(mm_rates)], C.c_int),
+    "mm_set_state": ([_H, _P, _P, _P, C.c_int], C.c_int),
+    "mm_get_state": ([_H, _P, _P, _P, _P, C.c_int], C.c_int),
+    "mm_set_velocity": ([_H, _P, C.c_int], C.c_int),
+    "mm_get_dt": ([_H, C.POINTER(C.c_double)], C.c_int),
+    "mm_set_dt": ([_H, C.c_double], C.c_int),
+    "mm_micro_step": ([_H, C.c_int], C.c_int),
+    "mm_moments": ([_H, C.POINTER(mm_moments_out)], C.c_int),
+    "mm_last_error": ([_H], C.c_char_p),
+    "mm_build_info": ([], C.c_char_p),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load_library(path: str | None = None):
+    """Load libmm.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            p = path or LIB_PATH
+            if not os.path.exists(p):
+                raise RuntimeError(f"CUDA library not built: {p} is missing "
+                                   "(run paper_1908_04279_gb300.build.build())")
+            lib = C.CDLL(p)
+            for name, (args, res) in PROTOTYPES.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = lib
+    return _lib
+
+
+def _ptr(a, what: str):
+    """(pointer, on_device) for a numpy host array or a torch CUDA tensor."""
+    if a is None:
+        return None, None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags.c_contiguous:
+            raise TypeError(f"{what}: need a C-contiguous float64 array")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise TypeError(f"{what}: need a contiguous float64 tensor")
+        if not a.is_cuda:
+            return a.data_ptr(), 0
+        return a.data_ptr(), 1
+    raise TypeError(f"{what}: unsupported array type {type(a)}")
+
+
+def current_stream_handle() -> int:
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except Exception:  # torch missing is fine: the legacy default stream is used
+        pass
+    return 0
+
+
+class Simulation:
+    """One simulation instance resident on the current CUDA device."""
+
+    def __init__(self, grid: Grid, rates: Rates = Rates(), precision: str = "fp64",
+                 stream: int | None = None):
+        self.lib = load_library()
+        self.grid, self.rates = grid, rates
+        self.precision = precision
+        prec = {"fp64": MM_FP64, "fp32": MM_FP32_MIXED}[precision]
+        h = C.c_void_p()
+        st = self.lib.mm_create(C.byref(self._g()), C.byref(self._r(rates)), prec,
+                                C.c_void_p(stream if stream is not None else current_stream_handle()),
+                                C.byref(h))
+        if st != 0:
+            raise MMError(st, self.lib.mm_last_error(None).decode())
+        self.h = h
+
+    def _g(self):
+        g = self.grid
+        return mm_grid(g.nx, g.ny, g.ntheta, g.ns, g.L)
+
+    @staticmethod
+    def _r(r: Rates):
+        return mm_rates(r.v_walk, r.k_on, r.k_off, r.glide, r.v_sp, r.force_scale, r.ell, r.cfl)
+
+    def _check(self, st: int):
+        if st != 0:
+            raise MMError(st, self.lib.mm_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.mm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- state -------------------------------------------------------------
+    def set_stream(self, stream: int):
+        self._check(self.lib.mm_set_stream(self.h, C.c_void_p(stream)))
+
+    def set_rates(self, rates: Rates):
+        self.rates = rates
+        self._check(self.lib.mm_set_rates(self.h, C.byref(self._r(rates))))
+
+    def set_state(self, psi, mb=None, mtot=None):
+        pp, d0 = _ptr(psi, "psi")
+        pm, d1 = _ptr(mb, "mb")
+        pt, d2 = _ptr(mtot, "mtot")
+        flags = {d for d in (d0, d1, d2) if d is not None}
+        if len(flags) > 1:
+            raise TypeError("psi, mb and mtot must all be host arrays or all device tensors")
+        self._check(self.lib.mm_set_state(self.h, pp, pm, pt, d0))
+
+    def get_state(self):
+        """Host copies: dict psi, mb, mf, c (float64)."""
+        g = self.grid
+        out = dict(psi=np.empty((g.ny, g.nx, g.ntheta)), mb=np.empty((g.ny, g.nx, g.ntheta, g.ns)),
+                   mf=np.empty((g.ny, g.nx)), c=np.empty((g.ny, g.nx)))
+        self._check(self.lib.mm_get_state(self.h, out["psi"].ctypes.data, out["mb"].ctypes.data,
+                                          out["mf"].ctypes.data, out["c"].ctypes.data, 0))
+        return out
+
+    def get_state_into(self, psi=None, mb=None, mf=None, c=None):
+        ptrs = [_ptr(a, n) for a, n in ((psi, "psi"), (mb, "mb"), (mf, "mf"), (c, "c"))]
+        flags = {d for _, d in ptrs if d is not None}
+        if len(flags) > 1:
+            raise TypeError("outputs must all be host arrays or all device tensors")
+        dev = flags.pop() if flags else 0
+        self._check(self.lib.mm_get_state(self.h, *[p for p, _ in ptrs], dev))
+
+    def set_velocity(self, u):
+        p, d = _ptr(u, "u")
+        self._check(self.lib.mm_set_velocity(self.h, p, d))
+
+    @property
+    def dt(self) -> float:
+        v = C.c_double()
+        self._check(self.lib.mm_get_dt(self.h, C.byref(v)))
+        return v.value
+
+    def set_dt(self, dt: float):
+        self._check(self.lib.mm_set_dt(self.h, float(dt)))
+
+    def step(self, n: int):
+        self._check(self.lib.mm_micro_step(self.h, int(n)))
+
+    def moments(self, fields=True):
+        """(fields dict name -> [ny][nx] or None, scalars dict). `fields` may be
+        True (host numpy), False, or a float64 CUDA tensor of 12*ny*nx."""
+        g = self.grid
+        out = mm_moments_out()
+        host = None
+        if fields is True:
+            host = np.empty((12, g.ny, g.nx))
+            out.fields, out.fields_on_device = host.ctypes.data, 0
+        elif fields is not False and fields is not None:
+            p, d = _ptr(fields, "fields")
+            out.fields, out.fields_on_device = p, d
+        self._check(self.lib.mm_moments(self.h, C.byref(out)))
+        sc = dict(zip(SCALAR_NAMES, list(out.scalars)))
+        return (dict(zip(FIELD_NAMES, host)) if host is not None else None), sc
+
+
+def build_info() -> str:
+    return load_library().mm_build_info().decode()

@@ -515,3 +515,19 @@ def test_adjoint_dot_product(oracle_mod, clip):
     rhs = ((lpsi * dpsi).sum() + (lmb * dmb).sum() + (lmf * dmf).sum() + (lu * du).sum()
            + (lp * dp).sum())
     assert abs(lhs - rhs) <= 1e-12 * max(abs(lhs), 1e-300)
+
+
+def test_patch_substep_equals_full_grid(oracle_mod):
+    """The 3x3 periodic patch (same dx, dy) reproduces the full-grid substep of
+    its centre cell exactly: the basis of the sampled full-size GPU checks."""
+    O = oracle_mod
+    g, r = Grid(9, 7, 8, 6), Rates(v_sp=0.1, glide=0.5)
+    st = _rand_state(O, g, 81)
+    u = random_divfree_flow(g, 23, 6, 0.4)
+    full = _step(O, g, r, st, u, 0.01)
+    cells = [(0, 0), (3, 4), (6, 8), (2, 0)]
+    res = O.patch_substep(g, r, 0.01, u, st.psi, st.mb, st.mf, st.mtot, cells)
+    for (iy, ix), c in zip(cells, res):
+        assert np.array_equal(c["psi"], full.psi[iy, ix])
+        assert np.array_equal(c["mb"], full.mb[iy, ix])
+        assert c["mf"] == full.mf[iy, ix] and c["c"] == full.c[iy, ix]

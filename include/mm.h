@@ -149,6 +149,22 @@ typedef struct {
 } mm_moments_out;
 mm_status mm_moments(mm_handle* h, mm_moments_out* out);
 
+/* Wait for the handle's stream and report a failure recorded by a kernel
+ * since the last check (MM_ERR_TIMEOUT: a bounded device-side wait gave up and
+ * the state is no longer valid). mm_get_state and mm_moments check too. */
+mm_status mm_sync(mm_handle* h);
+
+/* Test and tuning knobs of the substep kernel (no counterpart in the paper).
+ * wait_limit: polls of an mbarrier before a device wait gives up (default
+ * 4194304); flags bit 0: wait on a barrier nothing completes, so that
+ * every wait runs out -- used by tests of the timeout path, never in production. */
+mm_status mm_debug_set(mm_handle* h, unsigned int wait_limit, unsigned int flags);
+
+/* Launch plan of the substep kernel, for tests and profiling: info[0..9] =
+ * grid, block, dynamic shared bytes, uses bulk copies (0/1), ring stages,
+ * s-rows per stage, stages per cell, values per lane, lanes per s-row, SMs. */
+mm_status mm_get_launch_info(mm_handle* h, int* info, int n);
+
 const char* mm_last_error(const mm_handle* h);
 
 /* A short description of the build (library name and target architecture). */

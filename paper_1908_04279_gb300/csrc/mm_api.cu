@@ -37,6 +37,7 @@ struct mm_handle {
   double* c = nullptr;
   double* mtot = nullptr;
   void* u = nullptr;
+  void* ucell = nullptr;
   double* u64 = nullptr;
   void* trig = nullptr;
   double* trig64 = nullptr;
@@ -49,7 +50,9 @@ struct mm_handle {
   double dt = 0.0;
   bool have_state = false, have_vel = false, have_dt = false;
   // substep launch configuration
-  int V = 1, seg = 1, block = 32, rpt = 1, grid_step = 1, grid_mom = 1;
+  int V = 1, seg = 1, block = 128, grid_step = 1, grid_mom = 1;
+  int stages = 1, chunk_rows = 1, chunks_per_cell = 1;
+  bool tma = false;
   size_t smem = 0;
   std::map<long long, cudaGraphExec_t> graphs;
   bool use_graphs = true;
@@ -108,7 +111,7 @@ mm_status free_all(mm_handle* h) {
   h->graphs.clear();
   void* ptrs[] = {h->mb,  h->psi[0], h->psi[1], h->nb[0],   h->nb[1],  h->m1,
                   h->mf,  h->c,      h->mtot,   h->u,       h->u64,    h->trig,
-                  h->trig64, h->partial, h->fields, h->staging, h->prm};
+                  h->trig64, h->partial, h->fields, h->staging, h->prm, h->ucell};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   if (h->cap) cudaStreamDestroy(h->cap);
@@ -126,6 +129,8 @@ mm_status upload_params(mm_handle* h) {
   p.v_sp = h->r.v_sp;
   p.force_scale = h->r.force_scale;
   p.ell = h->r.ell;
+  p.wait_limit = 1u << 22;
+  p.debug_flags = 0;
   CK(cudaMemcpy(h->prm, &p, sizeof(p), cudaMemcpyHostToDevice));
   return MM_OK;
 }
@@ -138,7 +143,10 @@ StepArgs<T> step_args(mm_handle* h, int parity, int write_m1) {
   a.nth = h->g.ntheta;
   a.ns = h->g.ns;
   a.seg = h->seg;
-  a.rpt = h->rpt;
+  a.stages = h->stages;
+  a.chunk_rows = h->chunk_rows;
+  a.chunks_per_cell = h->chunks_per_cell;
+  a.nb_tma = h->tma && ((size_t)h->g.ntheta * h->tsz) % 16 == 0 && h->g.ntheta % 2 == 0;
   a.ncells = h->ncells;
   a.inv_dx = (double)h->g.nx;
   a.inv_dy = (double)h->g.ny;
@@ -155,7 +163,7 @@ StepArgs<T> step_args(mm_handle* h, int parity, int write_m1) {
   a.mf = h->mf;
   a.c = h->c;
   a.mtot = h->mtot;
-  a.u = (const T*)h->u;
+  a.ucell = (const T*)h->ucell;
   a.trig = (const T*)h->trig;
   a.partial = h->partial;
   a.prm = h->prm;
@@ -167,13 +175,23 @@ StepArgs<T> step_args(mm_handle* h, int parity, int write_m1) {
 cudaError_t launch_one(mm_handle* h, int parity, int write_m1, cudaStream_t s) {
   if (h->prec == MM_FP64) {
     StepArgs<double> a = step_args<double>(h, parity, write_m1);
-    return h->V == 2 ? mm::launch_substep<double, 2>(a, h->grid_step, h->block, h->smem, s)
-                     : mm::launch_substep<double, 1>(a, h->grid_step, h->block, h->smem, s);
+    return h->V == 2 ? mm::launch_substep<double, 2>(a, h->grid_step, h->block, h->smem, h->tma, s)
+                     : mm::launch_substep<double, 1>(a, h->grid_step, h->block, h->smem, h->tma, s);
   }
   StepArgs<float> a = step_args<float>(h, parity, write_m1);
-  return h->V == 4 ? mm::launch_substep<float, 4>(a, h->grid_step, h->block, h->smem, s)
-                   : mm::launch_substep<float, 1>(a, h->grid_step, h->block, h->smem, s);
+  return h->V == 4 ? mm::launch_substep<float, 4>(a, h->grid_step, h->block, h->smem, h->tma, s)
+                   : mm::launch_substep<float, 1>(a, h->grid_step, h->block, h->smem, h->tma, s);
 }
+
+// Launch plan of the substep kernel: one warp per cell, the cell's rows
+// streamed in chunks of chunk_rows rows (at most kChunkBytes) through a ring of
+// `stages` shared-memory stages per warp filled by bulk copies (TMA) when an
+// s-row is a whole number of 16-byte vectors; otherwise rows are read from
+// global memory directly.
+constexpr int kChunkBytes = 4096;
+constexpr int kWarpInflightBytes = 8192;
+constexpr int kMaxWarpsPerBlock = 4;
+constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory per block at most
 
 mm_status configure(mm_handle* h) {
   const int ns = h->g.ns, nth = h->g.ntheta;
@@ -185,30 +203,54 @@ mm_status configure(mm_handle* h) {
   int seg = 1;
   while (seg < nl) seg <<= 1;
   h->seg = seg;
-  long long want = (long long)nth * seg;
-  int block = 256;
-  if (want < 256) block = (int)((want + 31) / 32 * 32);
-  h->block = block;
-  const int slots = block / seg;
-  h->rpt = (nth + slots - 1) / slots;
-  h->smem = h->prec == MM_FP64 ? mm::substep_smem<double>(nth) : mm::substep_smem<float>(nth);
+  h->tma = h->V == vmax;
+  const size_t row_bytes = (size_t)ns * h->tsz;
+  int ch = 1;
+  while (ch < nth && (nth % ch != 0 || (size_t)(nth / ch) * row_bytes > kChunkBytes)) ++ch;
+  h->chunks_per_cell = ch;
+  h->chunk_rows = nth / ch;
+  const size_t chunk_bytes = (size_t)h->chunk_rows * row_bytes;
+  int S = (int)(kWarpInflightBytes / std::max<size_t>(chunk_bytes, 1));
+  S = std::max(2, std::min(8, S));
+  h->stages = h->tma ? S : 1;
+  const size_t per_warp =
+      mm::step_smem_per_warp(h->stages, h->tma ? h->chunk_rows * ns : 0, nth, (int)h->tsz);
+  const int wpb = (int)std::min<size_t>(kMaxWarpsPerBlock, kSmemBudget / per_warp);
+  if (wpb < 1) return fail(h, MM_ERR_UNSUPPORTED, "ntheta too large for the shared-memory plan");
+  h->block = 32 * wpb;
+  h->smem = (size_t)wpb * per_warp;
   int bps = 0;
   cudaError_t e;
   if (h->prec == MM_FP64)
-    e = h->V == 2 ? mm::substep_occupancy<double, 2>(block, h->smem, &bps)
-                  : mm::substep_occupancy<double, 1>(block, h->smem, &bps);
+    e = h->V == 2 ? mm::substep_prepare<double, 2>(h->block, h->smem, h->tma, &bps)
+                  : mm::substep_prepare<double, 1>(h->block, h->smem, h->tma, &bps);
   else
-    e = h->V == 4 ? mm::substep_occupancy<float, 4>(block, h->smem, &bps)
-                  : mm::substep_occupancy<float, 1>(block, h->smem, &bps);
+    e = h->V == 4 ? mm::substep_prepare<float, 4>(h->block, h->smem, h->tma, &bps)
+                  : mm::substep_prepare<float, 1>(h->block, h->smem, h->tma, &bps);
   CK(e);
   if (bps < 1) return fail(h, MM_ERR_UNSUPPORTED, "substep kernel cannot be resident");
   long long g = (long long)bps * h->sms;
-  if (g > h->ncells) g = h->ncells;
+  const long long need = (h->ncells + wpb - 1) / wpb;
+  if (g > need) g = need;
   h->grid_step = (int)g;
   long long gm = 4LL * h->sms;
   if (gm > h->ncells) gm = h->ncells;
   h->grid_mom = (int)gm;
-  h->npartial = std::max(h->grid_step, 8 * h->grid_mom);
+  h->npartial = std::max(h->grid_step * wpb, 8 * h->grid_mom);
+  return MM_OK;
+}
+
+// Read and clear the device status word; a set bit means a bounded device
+// wait gave up during an earlier kernel.
+mm_status check_status(mm_handle* h) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, &h->prm->status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (st) {
+    const int zero = 0;
+    CK(cudaMemcpy(&h->prm->status, &zero, sizeof zero, cudaMemcpyHostToDevice));
+    return fail(h, MM_ERR_TIMEOUT, "a bounded wait in the substep kernel gave up; the state is invalid");
+  }
   return MM_OK;
 }
 
@@ -345,7 +387,7 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
   }
   const size_t nc = (size_t)h->ncells;
   const size_t need = h->mbn * h->tsz + 2 * h->rows * h->tsz + 3 * h->rows * 8 + 3 * nc * 8 +
-                      2 * nc * (h->tsz + 8) + 12 * nc * 8 + kStagingDoubles * 8 +
+                      2 * nc * (h->tsz + 8) + 12 * nc * (8 + h->tsz) + kStagingDoubles * 8 +
                       (size_t)h->npartial * 8 * 8 + 4 * grid->ntheta * (h->tsz + 8) + 4096;
   size_t freeb = 0, totalb = 0;
   e = cudaMemGetInfo(&freeb, &totalb);
@@ -377,6 +419,7 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
   ALLOC(h->c, nc * 8);
   ALLOC(h->mtot, nc * 8);
   ALLOC(h->u, 2 * nc * h->tsz);
+  ALLOC(h->ucell, 12 * nc * h->tsz);
   ALLOC(h->u64, 2 * nc * 8);
   ALLOC(h->trig, 4 * (size_t)grid->ntheta * h->tsz);
   ALLOC(h->trig64, 4 * (size_t)grid->ntheta * 8);
@@ -420,6 +463,7 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
     e = cudaMemcpy(h->mtot, ones.data(), nc * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(h->u64, zeros.data(), 2 * nc * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->u, 0, 2 * nc * h->tsz);
+    if (e == cudaSuccess) e = cudaMemset(h->ucell, 0, 12 * nc * h->tsz);
     if (e == cudaSuccess) e = cudaMemset(h->mb, 0, h->mbn * h->tsz);
     if (e == cudaSuccess) e = cudaMemset(h->partial, 0, (size_t)h->npartial * 64);
     if (e != cudaSuccess) {
@@ -510,8 +554,7 @@ mm_status mm_get_state(mm_handle* h, double* psi, double* mb, double* mf, double
   const cudaMemcpyKind kd = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
   if (mf) CK(cudaMemcpyAsync(mf, h->mf, (size_t)h->ncells * 8, kd, h->stream));
   if (c) CK(cudaMemcpyAsync(c, h->c, (size_t)h->ncells * 8, kd, h->stream));
-  if (!on_device) CK(cudaStreamSynchronize(h->stream));
-  return MM_OK;
+  return check_status(h);
 }
 
 mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
@@ -525,6 +568,12 @@ mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
     CK(cudaMemcpyAsync(h->u, h->u64, n * 8, cudaMemcpyDeviceToDevice, h->stream));
   else
     CK(mm::launch_convert<float, double>((float*)h->u, h->u64, n, nullptr, h->stream));
+  if (h->prec == MM_FP64)
+    CK(mm::launch_prep_ucell<double>((double*)h->ucell, h->u64, h->ncells, h->g.nx, h->g.ny,
+                                     (double)h->g.nx, (double)h->g.ny, h->stream));
+  else
+    CK(mm::launch_prep_ucell<float>((float*)h->ucell, h->u64, h->ncells, h->g.nx, h->g.ny,
+                                    (double)h->g.nx, (double)h->g.ny, h->stream));
   // maxima of the substep rule on the device, the rule itself in float64 here
   CK(cudaMemsetAsync(h->prm->dtmax, 0, sizeof(h->prm->dtmax), h->stream));
   const double dth = 2.0 * kPi / h->g.ntheta;
@@ -624,9 +673,32 @@ mm_status mm_moments(mm_handle* h, mm_moments_out* out) {
                        h->stream));
   CK(cudaMemcpyAsync(out->scalars, h->prm->scalars, sizeof out->scalars, cudaMemcpyDeviceToHost,
                      h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+  if ((st = check_status(h)) != MM_OK) return st;
   for (double x : out->scalars)
     if (!std::isfinite(x)) return fail(h, MM_ERR_NONFINITE, "a global moment is not finite");
+  return MM_OK;
+}
+
+mm_status mm_sync(mm_handle* h) {
+  if (!h) return MM_ERR_INVALID;
+  DeviceGuard dg(h->device);
+  return check_status(h);
+}
+
+mm_status mm_debug_set(mm_handle* h, unsigned int wait_limit, unsigned int flags) {
+  if (!h) return MM_ERR_INVALID;
+  DeviceGuard dg(h->device);
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(&h->prm->wait_limit, &wait_limit, sizeof wait_limit, cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(&h->prm->debug_flags, &flags, sizeof flags, cudaMemcpyHostToDevice));
+  return MM_OK;
+}
+
+mm_status mm_get_launch_info(mm_handle* h, int* info, int n) {
+  if (!h || !info || n < 1) return MM_ERR_INVALID;
+  const int v[10] = {h->grid_step, h->block, (int)h->smem, h->tma ? 1 : 0, h->stages,
+                     h->chunk_rows, h->chunks_per_cell, h->V, h->seg, h->sms};
+  for (int i = 0; i < n && i < 10; ++i) info[i] = v[i];
   return MM_OK;
 }
 

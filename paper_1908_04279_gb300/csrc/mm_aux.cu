@@ -224,6 +224,39 @@ __global__ void k_moments(const T* psi, const double* nb, const double* m1, cons
   }
 }
 
+// Per-cell velocity data of the psi transport: the cell's own u, the x
+// component at the east/west neighbours, the y component at the north/south
+// neighbours, and the central-difference velocity gradient G_ab = du_a/dx_b.
+template <typename T>
+__global__ void k_prep_ucell(T* ucell, const double* u64, long long ncells, int nx, int ny,
+                             double inv_dx, double inv_dy) {
+  const double* ux = u64;
+  const double* uy = u64 + ncells;
+  for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < ncells;
+       cell += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(cell % nx), iy = (int)(cell / nx);
+    const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
+    const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
+    const long long ce = (long long)iy * nx + xp, cw = (long long)iy * nx + xm;
+    const long long cn = (long long)yp * nx + ix, cs = (long long)ym * nx + ix;
+    T* o = ucell + cell * 12;
+    o[0] = (T)ux[cell];
+    o[1] = (T)uy[cell];
+    o[2] = (T)ux[ce];
+    o[3] = (T)ux[cw];
+    o[4] = (T)uy[cn];
+    o[5] = (T)uy[cs];
+    // differences of the stored (precision T) velocities, as the oracle
+    // differences its own velocity array
+    o[6] = ((T)ux[ce] - (T)ux[cw]) * (T)(0.5 * inv_dx);
+    o[7] = ((T)ux[cn] - (T)ux[cs]) * (T)(0.5 * inv_dy);
+    o[8] = ((T)uy[ce] - (T)uy[cw]) * (T)(0.5 * inv_dx);
+    o[9] = ((T)uy[cn] - (T)uy[cs]) * (T)(0.5 * inv_dy);
+    o[10] = T(0);
+    o[11] = T(0);
+  }
+}
+
 int grid_for(long long n, int block) {
   long long g = (n + block - 1) / block;
   if (g > 152 * 16) g = 152 * 16;
@@ -237,6 +270,13 @@ template <typename TO, typename TI>
 cudaError_t launch_convert(TO* out, const TI* in, size_t n, const double* scale, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   k_convert<TO, TI><<<grid_for((long long)n, 256), 256, 0, s>>>(out, in, n, scale);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_prep_ucell(T* ucell, const double* u64, long long ncells, int nx, int ny,
+                              double inv_dx, double inv_dy, cudaStream_t s) {
+  k_prep_ucell<T><<<grid_for(ncells, 256), 256, 0, s>>>(ucell, u64, ncells, nx, ny, inv_dx, inv_dy);
   return cudaGetLastError();
 }
 
@@ -280,6 +320,10 @@ template cudaError_t launch_convert<double, float>(double*, const float*, size_t
                                                    cudaStream_t);
 template cudaError_t launch_convert<double, double>(double*, const double*, size_t,
                                                     const double*, cudaStream_t);
+template cudaError_t launch_prep_ucell<float>(float*, const double*, long long, int, int, double,
+                                              double, cudaStream_t);
+template cudaError_t launch_prep_ucell<double>(double*, const double*, long long, int, int,
+                                               double, double, cudaStream_t);
 template cudaError_t launch_init_cells<float>(float*, const float*, double*, double*, double*,
                                               double*, const double*, long long, int, int, double,
                                               double, double, cudaStream_t);

@@ -21,9 +21,11 @@ struct DevParams {
   double dtmax[4];    // [adv, rot, rho_max, spare] for the dt rule (bits as u64)
   double scalars[8];  // global moments
   double sum_psi;     // sum of psi over all cells and angles (moments kernel)
-  unsigned int counter;   // last-block-done counter of the substep kernel
+  unsigned int counter;   // last-warp-done counter of the substep kernel
   unsigned int counter2;  // last-block-done counter of the moments kernel
-  int status;
+  int status;             // bit 0: a bounded device wait gave up
+  unsigned int wait_limit;   // polls of an mbarrier before a wait gives up
+  unsigned int debug_flags;  // bit 0: wait on a phase nothing completes (tests)
   int pad;
 };
 
@@ -32,7 +34,10 @@ template <typename T>
 struct StepArgs {
   int nx, ny, nth, ns;
   int seg;            // lanes per s-row segment (power of two <= 32)
-  int rpt;            // s-rows per thread per cell
+  int stages;         // shared-memory ring depth per warp
+  int chunk_rows;     // s-rows per ring stage (divides nth)
+  int chunks_per_cell;
+  int nb_tma;         // 1: stage the psi / n_b neighbourhood by bulk copies
   long long ncells;
   double inv_dx, inv_dy, inv_dth, dth, ds, L;
   T* mb;              // [cells][nth][ns]
@@ -44,9 +49,10 @@ struct StepArgs {
   double* mf;         // [cells]
   double* c;          // [cells]
   const double* mtot; // [cells]
-  const T* u;         // [2][cells]
+  const T* ucell;     // [cells][12]: ux, uy, ux east, ux west, uy north, uy south,
+                      //   Gxx, Gxy, Gyx, Gyy (central differences), 2 spare
   const T* trig;      // [4][nth]: cos th_k, sin th_k, cos th_{k+1/2}, sin th_{k+1/2}
-  double* partial;    // [gridDim.x] per-CTA sum(psi)
+  double* partial;    // [warps in the grid] per-warp sum(psi)
   DevParams* prm;
   int write_m1;
   int mass_correct;   // 1: compute psi_scale = mass0 / mass after the substep
@@ -54,16 +60,18 @@ struct StepArgs {
 
 // Kernel launchers (defined in mm_step.cu); V = values per lane.
 template <typename T, int V>
-cudaError_t launch_substep(const StepArgs<T>& a, int grid, int block, size_t smem,
+cudaError_t launch_substep(const StepArgs<T>& a, int grid, int block, size_t smem, bool tma,
                            cudaStream_t s);
-template <typename T>
-size_t substep_smem(int nth);
+size_t step_smem_per_warp(int S, int chunk_elems, int nth, int tsz);
 template <typename T, int V>
-cudaError_t substep_occupancy(int block, size_t smem, int* blocks_per_sm);
+cudaError_t substep_prepare(int block, size_t smem, bool tma, int* blocks_per_sm);
 
 // Auxiliary kernels (mm_aux.cu).
 template <typename TO, typename TI>
 cudaError_t launch_convert(TO* out, const TI* in, size_t n, const double* scale, cudaStream_t s);
+template <typename T>
+cudaError_t launch_prep_ucell(T* ucell, const double* u64, long long ncells, int nx, int ny,
+                              double inv_dx, double inv_dy, cudaStream_t s);
 template <typename T>
 cudaError_t launch_init_cells(T* mb, const T* psi, double* nb, double* m1, double* mf,
                               double* c, const double* mtot, long long ncells, int nth, int ns,

@@ -66,6 +66,9 @@ PROTOTYPES = {
     "mm_set_dt": ([_H, C.c_double], C.c_int),
     "mm_micro_step": ([_H, C.c_int], C.c_int),
     "mm_moments": ([_H, C.POINTER(mm_moments_out)], C.c_int),
+    "mm_sync": ([_H], C.c_int),
+    "mm_debug_set": ([_H, C.c_uint, C.c_uint], C.c_int),
+    "mm_get_launch_info": ([_H, C.POINTER(C.c_int), C.c_int], C.c_int),
     "mm_last_error": ([_H], C.c_char_p),
     "mm_build_info": ([], C.c_char_p),
 }
@@ -215,6 +218,19 @@ class Simulation:
 
     def step(self, n: int):
         self._check(self.lib.mm_micro_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(self.lib.mm_sync(self.h))
+
+    def debug_set(self, wait_limit: int, flags: int = 0):
+        self._check(self.lib.mm_debug_set(self.h, int(wait_limit), int(flags)))
+
+    def launch_info(self) -> dict:
+        arr = (C.c_int * 10)()
+        self._check(self.lib.mm_get_launch_info(self.h, arr, 10))
+        keys = ("grid", "block", "smem", "tma", "stages", "chunk_rows", "chunks_per_cell", "V",
+                "seg", "sms")
+        return dict(zip(keys, list(arr)))
 
     def moments(self, fields=True):
         """(fields dict name -> [ny][nx] or None, scalars dict). `fields` may be

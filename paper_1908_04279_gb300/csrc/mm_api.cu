@@ -31,8 +31,7 @@ struct mm_handle {
   size_t rows = 0, mbn = 0, tsz = 8;
   void* mb = nullptr;
   void* psi[2] = {nullptr, nullptr};
-  double* nb[2] = {nullptr, nullptr};
-  double* m1 = nullptr;
+  void* nb[2] = {nullptr, nullptr};
   double* mf = nullptr;
   double* c = nullptr;
   double* mtot = nullptr;
@@ -109,7 +108,7 @@ mm_status check_rates(const mm_rates* r, mm_handle* h) {
 mm_status free_all(mm_handle* h) {
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
-  void* ptrs[] = {h->mb,  h->psi[0], h->psi[1], h->nb[0],   h->nb[1],  h->m1,
+  void* ptrs[] = {h->mb,  h->psi[0], h->psi[1], h->nb[0],   h->nb[1],
                   h->mf,  h->c,      h->mtot,   h->u,       h->u64,    h->trig,
                   h->trig64, h->partial, h->fields, h->staging, h->prm, h->ucell};
   for (void* p : ptrs)
@@ -136,7 +135,7 @@ mm_status upload_params(mm_handle* h) {
 }
 
 template <typename T>
-StepArgs<T> step_args(mm_handle* h, int parity, int write_m1) {
+StepArgs<T> step_args(mm_handle* h, int parity) {
   StepArgs<T> a{};
   a.nx = h->g.nx;
   a.ny = h->g.ny;
@@ -146,7 +145,7 @@ StepArgs<T> step_args(mm_handle* h, int parity, int write_m1) {
   a.stages = h->stages;
   a.chunk_rows = h->chunk_rows;
   a.chunks_per_cell = h->chunks_per_cell;
-  a.nb_tma = h->tma && ((size_t)h->g.ntheta * h->tsz) % 16 == 0 && h->g.ntheta % 2 == 0;
+  a.nb_tma = h->tma && ((size_t)h->g.ntheta * h->tsz) % 16 == 0;
   a.ncells = h->ncells;
   a.inv_dx = (double)h->g.nx;
   a.inv_dy = (double)h->g.ny;
@@ -157,9 +156,8 @@ StepArgs<T> step_args(mm_handle* h, int parity, int write_m1) {
   a.mb = (T*)h->mb;
   a.psi_in = (const T*)h->psi[parity];
   a.psi_out = (T*)h->psi[parity ^ 1];
-  a.nb_in = h->nb[parity];
-  a.nb_out = h->nb[parity ^ 1];
-  a.m1 = h->m1;
+  a.nb_in = (const T*)h->nb[parity];
+  a.nb_out = (T*)h->nb[parity ^ 1];
   a.mf = h->mf;
   a.c = h->c;
   a.mtot = h->mtot;
@@ -167,18 +165,17 @@ StepArgs<T> step_args(mm_handle* h, int parity, int write_m1) {
   a.trig = (const T*)h->trig;
   a.partial = h->partial;
   a.prm = h->prm;
-  a.write_m1 = write_m1;
   a.mass_correct = h->prec == MM_FP32_MIXED ? 1 : 0;
   return a;
 }
 
-cudaError_t launch_one(mm_handle* h, int parity, int write_m1, cudaStream_t s) {
+cudaError_t launch_one(mm_handle* h, int parity, cudaStream_t s) {
   if (h->prec == MM_FP64) {
-    StepArgs<double> a = step_args<double>(h, parity, write_m1);
+    StepArgs<double> a = step_args<double>(h, parity);
     return h->V == 2 ? mm::launch_substep<double, 2>(a, h->grid_step, h->block, h->smem, h->tma, s)
                      : mm::launch_substep<double, 1>(a, h->grid_step, h->block, h->smem, h->tma, s);
   }
-  StepArgs<float> a = step_args<float>(h, parity, write_m1);
+  StepArgs<float> a = step_args<float>(h, parity);
   return h->V == 4 ? mm::launch_substep<float, 4>(a, h->grid_step, h->block, h->smem, h->tma, s)
                    : mm::launch_substep<float, 1>(a, h->grid_step, h->block, h->smem, h->tma, s);
 }
@@ -306,28 +303,30 @@ mm_status run_init(mm_handle* h) {
   cudaError_t e;
   if (h->prec == MM_FP64)
     e = mm::launch_init_cells<double>((double*)h->mb, (const double*)h->psi[h->parity],
-                                      h->nb[h->parity], h->m1, h->mf, h->c, h->mtot, h->ncells,
-                                      h->g.ntheta, h->g.ns, ds, dth, h->g.L, h->stream);
+                                      (double*)h->nb[h->parity], h->mf, h->c, h->mtot, h->ncells,
+                                      h->g.ntheta, h->g.ns, ds, dth, h->stream);
   else
     e = mm::launch_init_cells<float>((float*)h->mb, (const float*)h->psi[h->parity],
-                                     h->nb[h->parity], h->m1, h->mf, h->c, h->mtot, h->ncells,
-                                     h->g.ntheta, h->g.ns, ds, dth, h->g.L, h->stream);
+                                     (float*)h->nb[h->parity], h->mf, h->c, h->mtot, h->ncells,
+                                     h->g.ntheta, h->g.ns, ds, dth, h->stream);
   CK(e);
   return MM_OK;
 }
 
 mm_status run_moments(mm_handle* h) {
-  const double dth = 2.0 * kPi / h->g.ntheta;
+  const double dth = 2.0 * kPi / h->g.ntheta, ds = h->g.L / h->g.ns;
   const double dA = (1.0 / h->g.nx) * (1.0 / h->g.ny);
   cudaError_t e;
   if (h->prec == MM_FP64)
-    e = mm::launch_moments<double>((const double*)h->psi[h->parity], h->nb[h->parity], h->m1,
-                                   h->mf, h->c, h->trig64, h->ncells, h->g.ntheta, dth, dA,
-                                   h->fields, h->partial, h->grid_mom, h->prm, h->stream);
+    e = mm::launch_moments<double>((const double*)h->psi[h->parity], (const double*)h->mb, h->mf,
+                                   h->c, h->trig64, h->ncells, h->g.ntheta, h->g.ns, dth, ds,
+                                   h->g.L, dA, h->fields, h->partial, h->grid_mom, h->prm,
+                                   h->stream);
   else
-    e = mm::launch_moments<float>((const float*)h->psi[h->parity], h->nb[h->parity], h->m1,
-                                  h->mf, h->c, h->trig64, h->ncells, h->g.ntheta, dth, dA,
-                                  h->fields, h->partial, h->grid_mom, h->prm, h->stream);
+    e = mm::launch_moments<float>((const float*)h->psi[h->parity], (const float*)h->mb, h->mf,
+                                  h->c, h->trig64, h->ncells, h->g.ntheta, h->g.ns, dth, ds,
+                                  h->g.L, dA, h->fields, h->partial, h->grid_mom, h->prm,
+                                  h->stream);
   CK(e);
   return MM_OK;
 }
@@ -353,8 +352,8 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
   const int vmax = prec == MM_FP64 ? 2 : 4;
   if (grid->ns > 32 * vmax)
     return fail(nullptr, MM_ERR_UNSUPPORTED, prec == MM_FP64 ? "ns > 64 in MM_FP64" : "ns > 128 in MM_FP32_MIXED");
-  if ((long long)grid->nx * grid->ny > (1LL << 40))
-    return fail(nullptr, MM_ERR_INVALID, "grid too large");
+  if ((long long)grid->nx * grid->ny > 0x7fffffffLL)
+    return fail(nullptr, MM_ERR_UNSUPPORTED, "more than 2^31 - 1 cells");
 
   mm_handle* h = new mm_handle();
   h->g = *grid;
@@ -412,9 +411,8 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
   ALLOC(h->mb, h->mbn * h->tsz);
   ALLOC(h->psi[0], h->rows * h->tsz);
   ALLOC(h->psi[1], h->rows * h->tsz);
-  ALLOC(h->nb[0], h->rows * 8);
-  ALLOC(h->nb[1], h->rows * 8);
-  ALLOC(h->m1, h->rows * 8);
+  ALLOC(h->nb[0], h->rows * h->tsz);
+  ALLOC(h->nb[1], h->rows * h->tsz);
   ALLOC(h->mf, nc * 8);
   ALLOC(h->c, nc * 8);
   ALLOC(h->mtot, nc * 8);
@@ -579,12 +577,12 @@ mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
   const double dth = 2.0 * kPi / h->g.ntheta;
   cudaError_t e;
   if (h->prec == MM_FP64)
-    e = mm::launch_dt_max<double>((const double*)h->psi[h->parity], h->nb[h->parity], h->u64,
+    e = mm::launch_dt_max<double>((const double*)h->psi[h->parity], (const double*)h->nb[h->parity], h->u64,
                                   h->trig64, h->ncells, h->g.nx, h->g.ny, h->g.ntheta,
                                   (double)h->g.nx, (double)h->g.ny, 1.0 / dth, dth, h->r.glide,
                                   h->r.v_sp, h->prm, h->stream);
   else
-    e = mm::launch_dt_max<float>((const float*)h->psi[h->parity], h->nb[h->parity], h->u64,
+    e = mm::launch_dt_max<float>((const float*)h->psi[h->parity], (const float*)h->nb[h->parity], h->u64,
                                  h->trig64, h->ncells, h->g.nx, h->g.ny, h->g.ntheta,
                                  (double)h->g.nx, (double)h->g.ny, 1.0 / dth, dth, h->r.glide,
                                  h->r.v_sp, h->prm, h->stream);
@@ -632,7 +630,7 @@ mm_status mm_micro_step(mm_handle* h, int n) {
   DeviceGuard dg(h->device);
   if (!h->use_graphs) {
     for (int i = 0; i < n; ++i) {
-      CK(launch_one(h, h->parity, i == n - 1, h->stream));
+      CK(launch_one(h, h->parity, h->stream));
       h->parity ^= 1;
     }
     return MM_OK;
@@ -645,7 +643,7 @@ mm_status mm_micro_step(mm_handle* h, int n) {
     int par = h->parity;
     cudaError_t le = cudaSuccess;
     for (int i = 0; i < n && le == cudaSuccess; ++i) {
-      le = launch_one(h, par, i == n - 1, h->cap);
+      le = launch_one(h, par, h->cap);
       par ^= 1;
     }
     cudaError_t ce = cudaStreamEndCapture(h->cap, &graph);

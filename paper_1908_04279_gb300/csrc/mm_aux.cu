@@ -45,29 +45,25 @@ __global__ void k_convert(TO* out, const TI* in, size_t n, const double* scale) 
   }
 }
 
-// Per cell: n_b and m1 of every row (sequential sums over s in float64),
-// C = sum_k psi n_b dtheta, the Alg. 2 scale-down where C > M, Mf = M - C.
+// Per cell: n_b of every row (sequential sum over s in float64, stored in the
+// state precision), C = sum_k psi n_b dtheta, the Alg. 2 scale-down where
+// C > M, Mf = M - C.
 template <typename T>
-__global__ void k_init_cells(T* mb, const T* psi, double* nb, double* m1, double* mf, double* c,
+__global__ void k_init_cells(T* mb, const T* psi, T* nb, double* mf, double* c,
                              const double* mtot, long long ncells, int nth, int ns, double ds,
-                             double dth, double L) {
+                             double dth) {
   __shared__ double red[32];
+  __shared__ double s_f;
   for (long long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
     double acc = 0.0;
     for (int k = threadIdx.x; k < nth; k += blockDim.x) {
       const T* row = mb + ((size_t)cell * nth + k) * ns;
-      double s0 = 0.0, s1 = 0.0;
-      for (int j = 0; j < ns; ++j) {
-        const double sj = -0.5 * L + (j + 0.5) * ds;
-        s0 += (double)row[j] * ds;
-        s1 += sj * (double)row[j] * ds;
-      }
-      nb[cell * nth + k] = s0;
-      m1[cell * nth + k] = s1;
+      double s0 = 0.0;
+      for (int j = 0; j < ns; ++j) s0 += (double)row[j] * ds;
+      nb[cell * nth + k] = (T)s0;
       acc += (double)psi[cell * nth + k] * s0 * dth;
     }
     const double C = block_sum(acc, red);
-    __shared__ double s_f;
     if (threadIdx.x == 0) {
       const double M = mtot[cell];
       double f = 1.0, Cc = C;
@@ -85,8 +81,7 @@ __global__ void k_init_cells(T* mb, const T* psi, double* nb, double* m1, double
       for (int k = threadIdx.x; k < nth; k += blockDim.x) {
         T* row = mb + ((size_t)cell * nth + k) * ns;
         for (int j = 0; j < ns; ++j) row[j] = (T)((double)row[j] * f);
-        nb[cell * nth + k] *= f;
-        m1[cell * nth + k] *= f;
+        nb[cell * nth + k] = (T)((double)nb[cell * nth + k] * f);
       }
     }
     __syncthreads();
@@ -101,7 +96,7 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
 // Maxima of the adaptive-substep rule: max(|ax|/dx + |ay|/dy),
 // max |omega(theta_{k+1/2})| / dtheta, and max_cell sum_k psi dtheta.
 template <typename T>
-__global__ void k_dt_max(const T* psi, const double* nb, const double* u64, const double* trig,
+__global__ void k_dt_max(const T* psi, const T* nb, const double* u64, const double* trig,
                          long long ncells, int nx, int ny, int nth, double inv_dx, double inv_dy,
                          double inv_dth, double dth, double glide, double vsp, DevParams* prm) {
   __shared__ double red[32];
@@ -119,7 +114,7 @@ __global__ void k_dt_max(const T* psi, const double* nb, const double* u64, cons
     const double Gyy = (uy[(long long)yp * nx + ix] - uy[(long long)ym * nx + ix]) * 0.5 * inv_dy;
     double rho = 0.0;
     for (int k = threadIdx.x; k < nth; k += blockDim.x) {
-      const double V = vsp + glide * nb[cell * nth + k];
+      const double V = vsp + glide * (double)nb[cell * nth + k];
       const double ax = ux[cell] - V * trig[k], ay = uy[cell] - V * trig[nth + k];
       adv = fmax(adv, fabs(ax) * inv_dx + fabs(ay) * inv_dy);
       const double cp = trig[2 * nth + k], sp = trig[3 * nth + k];
@@ -140,11 +135,14 @@ __global__ void k_dt_max(const T* psi, const double* nb, const double* u64, cons
 }
 
 // Moments per cell (one CTA per cell, threads over theta) and per-CTA
-// partial global sums; the last CTA adds the partials in a fixed order.
+// partial global sums; the last CTA adds the partials in a fixed order. The
+// s-reductions feeding the force and the force dipole -- n_b = sum_j Mb ds and
+// m1 = sum_j s_j Mb ds -- are recomputed here from Mb in float64 sequential
+// sums, in both precisions.
 template <typename T>
-__global__ void k_moments(const T* psi, const double* nb, const double* m1, const double* mf,
-                          const double* c, const double* trig, long long ncells, int nth,
-                          double dth, double dA, double* fields, double* partial,
+__global__ void k_moments(const T* psi, const T* mb, const double* mf, const double* c,
+                          const double* trig, long long ncells, int nth, int ns, double dth,
+                          double ds, double L, double dA, double* fields, double* partial,
                           DevParams* prm) {
   __shared__ double red[32];
   __shared__ unsigned int s_last;
@@ -157,7 +155,13 @@ __global__ void k_moments(const T* psi, const double* nb, const double* m1, cons
     for (int k = threadIdx.x; k < nth; k += blockDim.x) {
       const double ct = trig[k], st = trig[nth + k];
       const double p = (double)psi[cell * nth + k] * g;
-      const double nbk = nb[cell * nth + k], m1k = m1[cell * nth + k];
+      const T* row = mb + ((size_t)cell * nth + k) * ns;
+      double nbk = 0.0, m1k = 0.0;
+      for (int j = 0; j < ns; ++j) {
+        const double mj = (double)row[j];
+        nbk += mj * ds;
+        m1k += (-0.5 * L + (j + 0.5) * ds) * mj * ds;
+      }
       f[0] += p * dth;
       f[1] += p * ct * dth;
       f[2] += p * st * dth;
@@ -281,18 +285,17 @@ cudaError_t launch_prep_ucell(T* ucell, const double* u64, long long ncells, int
 }
 
 template <typename T>
-cudaError_t launch_init_cells(T* mb, const T* psi, double* nb, double* m1, double* mf, double* c,
+cudaError_t launch_init_cells(T* mb, const T* psi, T* nb, double* mf, double* c,
                               const double* mtot, long long ncells, int nth, int ns, double ds,
-                              double dth, double L, cudaStream_t s) {
+                              double dth, cudaStream_t s) {
   int block = nth >= 128 ? 128 : (nth >= 64 ? 64 : 32);
   long long g = ncells < 152 * 16 ? ncells : 152 * 16;
-  k_init_cells<T><<<(int)g, block, 0, s>>>(mb, psi, nb, m1, mf, c, mtot, ncells, nth, ns, ds, dth,
-                                           L);
+  k_init_cells<T><<<(int)g, block, 0, s>>>(mb, psi, nb, mf, c, mtot, ncells, nth, ns, ds, dth);
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_dt_max(const T* psi, const double* nb, const double* u64, const double* trig,
+cudaError_t launch_dt_max(const T* psi, const T* nb, const double* u64, const double* trig,
                           long long ncells, int nx, int ny, int nth, double inv_dx,
                           double inv_dy, double inv_dth, double dth, double glide, double vsp,
                           DevParams* prm, cudaStream_t s) {
@@ -304,13 +307,13 @@ cudaError_t launch_dt_max(const T* psi, const double* nb, const double* u64, con
 }
 
 template <typename T>
-cudaError_t launch_moments(const T* psi, const double* nb, const double* m1, const double* mf,
-                           const double* c, const double* trig, long long ncells, int nth,
-                           double dth, double dA, double* fields, double* partial, int nblocks,
-                           DevParams* prm, cudaStream_t s) {
+cudaError_t launch_moments(const T* psi, const T* mb, const double* mf, const double* c,
+                           const double* trig, long long ncells, int nth, int ns, double dth,
+                           double ds, double L, double dA, double* fields, double* partial,
+                           int nblocks, DevParams* prm, cudaStream_t s) {
   int block = nth >= 128 ? 128 : (nth >= 64 ? 64 : 32);
-  k_moments<T><<<nblocks, block, 0, s>>>(psi, nb, m1, mf, c, trig, ncells, nth, dth, dA, fields,
-                                         partial, prm);
+  k_moments<T><<<nblocks, block, 0, s>>>(psi, mb, mf, c, trig, ncells, nth, ns, dth, ds, L, dA,
+                                         fields, partial, prm);
   return cudaGetLastError();
 }
 
@@ -324,13 +327,13 @@ template cudaError_t launch_prep_ucell<float>(float*, const double*, long long, 
                                               double, cudaStream_t);
 template cudaError_t launch_prep_ucell<double>(double*, const double*, long long, int, int,
                                                double, double, cudaStream_t);
-template cudaError_t launch_init_cells<float>(float*, const float*, double*, double*, double*,
-                                              double*, const double*, long long, int, int, double,
-                                              double, double, cudaStream_t);
+template cudaError_t launch_init_cells<float>(float*, const float*, float*, double*, double*,
+                                              const double*, long long, int, int, double, double,
+                                              cudaStream_t);
 template cudaError_t launch_init_cells<double>(double*, const double*, double*, double*, double*,
-                                               double*, const double*, long long, int, int,
-                                               double, double, double, cudaStream_t);
-template cudaError_t launch_dt_max<float>(const float*, const double*, const double*,
+                                               const double*, long long, int, int, double, double,
+                                               cudaStream_t);
+template cudaError_t launch_dt_max<float>(const float*, const float*, const double*,
                                           const double*, long long, int, int, int, double, double,
                                           double, double, double, double, DevParams*,
                                           cudaStream_t);
@@ -338,13 +341,13 @@ template cudaError_t launch_dt_max<double>(const double*, const double*, const d
                                            const double*, long long, int, int, int, double,
                                            double, double, double, double, double,
                                            DevParams*, cudaStream_t);
-template cudaError_t launch_moments<float>(const float*, const double*, const double*,
-                                           const double*, const double*, const double*, long long,
-                                           int, double, double, double*, double*, int, DevParams*,
-                                           cudaStream_t);
+template cudaError_t launch_moments<float>(const float*, const float*, const double*,
+                                           const double*, const double*, long long, int, int,
+                                           double, double, double, double, double*, double*, int,
+                                           DevParams*, cudaStream_t);
 template cudaError_t launch_moments<double>(const double*, const double*, const double*,
-                                            const double*, const double*, const double*,
-                                            long long, int, double, double, double*, double*, int,
+                                            const double*, const double*, long long, int, int,
+                                            double, double, double, double, double*, double*, int,
                                             DevParams*, cudaStream_t);
 
 }  // namespace mm

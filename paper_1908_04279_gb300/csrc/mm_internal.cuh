@@ -43,9 +43,8 @@ struct StepArgs {
   T* mb;              // [cells][nth][ns]
   const T* psi_in;    // [cells][nth]
   T* psi_out;
-  const double* nb_in;  // [cells][nth]
-  double* nb_out;
-  double* m1;         // [cells][nth]
+  const T* nb_in;     // [cells][nth] n_b = sum_j Mb ds (precision T)
+  T* nb_out;
   double* mf;         // [cells]
   double* c;          // [cells]
   const double* mtot; // [cells]
@@ -54,7 +53,6 @@ struct StepArgs {
   const T* trig;      // [4][nth]: cos th_k, sin th_k, cos th_{k+1/2}, sin th_{k+1/2}
   double* partial;    // [warps in the grid] per-warp sum(psi)
   DevParams* prm;
-  int write_m1;
   int mass_correct;   // 1: compute psi_scale = mass0 / mass after the substep
 };
 
@@ -73,18 +71,18 @@ template <typename T>
 cudaError_t launch_prep_ucell(T* ucell, const double* u64, long long ncells, int nx, int ny,
                               double inv_dx, double inv_dy, cudaStream_t s);
 template <typename T>
-cudaError_t launch_init_cells(T* mb, const T* psi, double* nb, double* m1, double* mf,
-                              double* c, const double* mtot, long long ncells, int nth, int ns,
-                              double ds, double dth, double L, cudaStream_t s);
+cudaError_t launch_init_cells(T* mb, const T* psi, T* nb, double* mf, double* c,
+                              const double* mtot, long long ncells, int nth, int ns, double ds,
+                              double dth, cudaStream_t s);
 template <typename T>
-cudaError_t launch_dt_max(const T* psi, const double* nb, const double* u64, const double* trig,
+cudaError_t launch_dt_max(const T* psi, const T* nb, const double* u64, const double* trig,
                           long long ncells, int nx, int ny, int nth, double inv_dx,
                           double inv_dy, double inv_dth, double dth, double glide, double vsp,
                           DevParams* prm, cudaStream_t s);
 template <typename T>
-cudaError_t launch_moments(const T* psi, const double* nb, const double* m1, const double* mf,
-                           const double* c, const double* trig, long long ncells, int nth,
-                           double dth, double dA, double* fields, double* partial,
+cudaError_t launch_moments(const T* psi, const T* mb, const double* mf, const double* c,
+                           const double* trig, long long ncells, int nth, int ns, double dth,
+                           double ds, double L, double dA, double* fields, double* partial,
                            int nblocks, DevParams* prm, cudaStream_t s);
 
 }  // namespace mm

@@ -11,7 +11,8 @@
 //      with V consecutive s-nodes per lane; the Superbee stencil reaches across
 //      lanes with warp shuffles; the new row goes straight back to global
 //      memory in place (16-byte vector stores);
-//   2. n_b and the force dipole m1 of every row by a shuffle reduction over s;
+//   2. n_b of every row by a shuffle reduction over s (the force and force
+//      dipole are reduced in float64 by the moments kernel instead);
 //   3. psi^{n+1}(cell, :) by Eq. 1 in donor-cell flux form (lane = theta), from
 //      psi^n and n_b^n of the cell and its 4 neighbours (loaded when the cell
 //      starts, so their latency overlaps the motor rows);
@@ -50,51 +51,63 @@ __device__ __forceinline__ T donor(T A, T pl, T pr) {
   return fma_t(tmax(A, T(0)), pl, tmin(A, T(0)) * pr);
 }
 
-// Half of the Superbee slope, sigma/2 with sigma = maxmod(minmod(2a,b),
-// minmod(a,2b)), on magnitudes: with s = sign(b), A = s a, B = |b|,
-// sigma/2 = s max(0, max(min(A, B/2), min(A/2, B))). Zero when a and b differ
-// in sign or either vanishes.
-template <typename T>
-__device__ __forceinline__ T half_superbee(T a, T b) {
-  const T s = copysign(T(1), b);
-  const T A = a * s;
-  const T B = fabs(b);
-  T r = tmax(tmin(A, T(0.5) * B), tmin(T(0.5) * A, B));
-  r = tmax(r, T(0));
-  return s * r;
+__device__ __forceinline__ float max3_t(float a, float b, float c) {
+  float r;
+  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
+  return r;
+}
+__device__ __forceinline__ double max3_t(double a, double b, double c) {
+  return fmax(fmax(a, b), c);
 }
 
-// Right-hand side of Eq. 4 for the V nodes a lane holds:
-// R_j = (v/ds) (F_{j-1} - F_j) - k_off M_j + k_on Mf, F_j = M_j + sigma_j/2
-// (walking flux / v through the right face of node j), F_{-1} = 0 (no inflow
-// at the minus end), F_{ns-1} = M_{ns-1} (donor-cell outflow at the plus end),
-// ghost M_{-1} = 0 in the first slope.
+// Walking-flux differences of the V nodes a lane holds (the d_s term of
+// Eq. 4 divided by v/ds): D_v = F_{j-1} - F_j with F_j = M_j + sigma_j/2 the
+// flux / v through the right face of node j = lane*V + v, F_{-1} = 0 (nothing
+// walks on at the minus end) and F_{ns-1} = M_{ns-1} (donor-cell outflow at
+// the plus end). sigma_j is the Superbee slope
+// maxmod(minmod(2a, b), minmod(a, 2b)) of the backward and forward
+// differences a, b (ghost M_{-1} = 0), evaluated on magnitudes: with
+// s = sign(b), sigma/2 = s max(min(s a, |b|/2), min(s a/2, |b|), 0).
+// Neighbouring nodes of other lanes come by warp shuffles within the row's
+// `seg`-lane segment.
 template <typename T, int V>
-__device__ __forceinline__ void motor_rhs(const T (&M)[V], T (&R)[V], bool first, bool last,
-                                          int seg, T cw, T koff, T src) {
+__device__ __forceinline__ void walk_dflux(const T (&M)[V], T (&D)[V], bool first, bool last,
+                                           int seg) {
   T ml = __shfl_up_sync(0xffffffffu, M[V - 1], 1, seg);
   const T mr = __shfl_down_sync(0xffffffffu, M[0], 1, seg);
   if (first) ml = T(0);
+  T d[V + 1], hd[V + 1];  // d[i] = M_i - M_{i-1}, i = 0..V, with M_{-1} = ml, M_V = mr
+  d[0] = M[0] - ml;
+#pragma unroll
+  for (int v = 1; v < V; ++v) d[v] = M[v] - M[v - 1];
+  d[V] = mr - M[V - 1];
+#pragma unroll
+  for (int i = 0; i <= V; ++i) hd[i] = T(0.5) * d[i];
   T F[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const T mm = v == 0 ? ml : M[v - 1];
-    const T mp = v == V - 1 ? mr : M[v + 1];
-    F[v] = M[v] + half_superbee(M[v] - mm, mp - M[v]);
+    T sgn = copysign(T(1), d[v + 1]);
+    if (v == V - 1 && last) sgn = T(0);  // plus end: F = M, no slope
+    const T A = d[v] * sgn, hA = hd[v] * sgn;
+    const T r = max3_t(tmin(A, fabs(hd[v + 1])), tmin(hA, fabs(d[v + 1])), T(0));
+    F[v] = fma_t(r, sgn, M[v]);
   }
-  if (last) F[V - 1] = M[V - 1];
   T fl = __shfl_up_sync(0xffffffffu, F[V - 1], 1, seg);
   if (first) fl = T(0);
+  D[0] = fl - F[0];
 #pragma unroll
-  for (int v = 0; v < V; ++v) {
-    const T fin = v == 0 ? fl : F[v - 1];
-    R[v] = cw * (fin - F[v]) - koff * M[v] + src;
-  }
+  for (int v = 1; v < V; ++v) D[v] = F[v - 1] - F[v];
 }
 
 template <typename T>
 __device__ __forceinline__ T seg_sum(T x, int seg) {
   for (int o = seg >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o, seg);
+  return x;
+}
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
   return x;
 }
 __device__ __forceinline__ double warp_sum(double x) {
@@ -148,13 +161,23 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 
 constexpr uint32_t kDrainLimit = 1u << 24;  // polls while draining after a timeout
 
+// Occupancy target (resident 4-warp blocks per SM, caps registers per thread)
+// and unroll depth of the s-row pass loop.
+#ifndef MM_STEP_MIN_BLOCKS
+#define MM_STEP_MIN_BLOCKS 4
+#endif
+#ifndef MM_STEP_UNROLL
+#define MM_STEP_UNROLL 2
+#endif
+constexpr int kStepUnroll = MM_STEP_UNROLL;
+
 // ------------------------------------------------------------------- layout
 
 // Per-warp shared memory: S + 2 mbarriers (S ring stages, 1 neighbourhood, 1
-// that never completes, waited on by the timeout test knob),
-// S stages of chunk_elems values, the psi columns of the cell and its east,
-// west, north and south neighbours (5 nth values of T), their n_b columns
-// (5 nth doubles), and n_b, m1 of the cell's new rows (2 nth doubles).
+// that never completes, waited on by the timeout test knob), S stages of
+// chunk_elems values, the psi and n_b columns of the cell and its east, west,
+// north and south neighbours (2 x 5 nth values), and n_b of the cell's new
+// rows (nth values), all in the state precision.
 struct WarpSmem {
   size_t bars, stages, psi5, nb5, nbm, total;
 };
@@ -170,9 +193,10 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int S, int chunk_elems, int
   off += 5 * (size_t)nth * tsz;
   off = (off + 15) & ~(size_t)15;
   w.nb5 = off;
-  off += 5 * (size_t)nth * 8;
+  off += 5 * (size_t)nth * tsz;
+  off = (off + 15) & ~(size_t)15;
   w.nbm = off;
-  off += 2 * (size_t)nth * 8;
+  off += (size_t)nth * tsz;
   off = (off + 127) & ~(size_t)127;
   w.total = off;
   return w;
@@ -183,34 +207,37 @@ size_t step_smem_per_warp(int S, int chunk_elems, int nth, int tsz) {
 }
 
 template <typename T, int V, bool TMA, bool MASSCORR>
-__global__ void __launch_bounds__(128, 4) k_substep(const StepArgs<T> a) {
+__global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepArgs<T> a) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int nth = a.nth, ns = a.ns, seg = a.seg;
   const int S = a.stages, RC = a.chunk_rows, CH = a.chunks_per_cell;
   const int chunk_elems = RC * ns;
+  const uint32_t chunk_bytes = (uint32_t)(chunk_elems * sizeof(T));
   // the ring exists only with bulk copies (the host sizes shared memory alike)
   const WarpSmem L = warp_smem_layout(S, TMA ? chunk_elems : 0, nth, (int)sizeof(T));
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   unsigned char* wbase = smem_raw + (size_t)wib * L.total;
   uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + L.bars);
   T* stages = reinterpret_cast<T*>(wbase + L.stages);
-  T* psi5 = reinterpret_cast<T*>(wbase + L.psi5);          // [5][nth]: c, e, w, n, s
-  double* nb5 = reinterpret_cast<double*>(wbase + L.nb5);  // [5][nth]
-  double* s_nb = reinterpret_cast<double*>(wbase + L.nbm);
-  double* s_m1 = s_nb + nth;
-  uint64_t* nbar = bars + S;      // neighbourhood barrier
+  T* psi5 = reinterpret_cast<T*>(wbase + L.psi5);  // [5][nth]: c, e, w, n, s
+  T* nb5 = reinterpret_cast<T*>(wbase + L.nb5);    // [5][nth]
+  T* s_nb = reinterpret_cast<T*>(wbase + L.nbm);   // n_b of the new rows
+  uint64_t* nbar = bars + S;       // neighbourhood barrier
   uint64_t* never = bars + S + 1;  // no copy or arrival ever completes it
   const bool nb_tma = TMA && a.nb_tma;
 
+  // Cells fit in 32 bits (checked on the host); all loop bookkeeping below is
+  // incremental, with no 64-bit integer division.
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
   const int W = gridDim.x * (blockDim.x >> 5);
-  const long long nc = a.ncells;
-  const long long my_cells = gw < nc ? (nc - 1 - gw) / W + 1 : 0;
-  const long long nchunks = my_cells * CH;
+  const int nc = (int)a.ncells;
+  const int nx = a.nx, ny = a.ny;
+  const int my_cells = gw < nc ? (nc - 1 - gw) / W + 1 : 0;
+  const int nchunks = my_cells * CH;
 
-  const int sl = lane & (seg - 1);      // lane within its row
-  const int rslot = lane / seg;         // row within a pass
-  const int rpp = 32 / seg;             // rows per pass
+  const int sl = lane & (seg - 1);  // lane within its row
+  const int rslot = lane / seg;     // row within a pass
+  const int rpp = 32 / seg;         // rows per pass
   const int passes = (RC + rpp - 1) / rpp;
   const int nl = ns / V;
   const bool first = sl == 0, last = sl == nl - 1, lane_ok = sl < nl;
@@ -230,111 +257,118 @@ __global__ void __launch_bounds__(128, 4) k_substep(const StepArgs<T> a) {
   const T* sink = a.trig + nth;
   const T* cosf = a.trig + 2 * nth;
   const T* sinf = a.trig + 3 * nth;
+  const T ds = (T)a.ds, dth_t = (T)a.dth;
+  const T c1 = hdt * cw, c2 = T(1) - hdt * koff;
+  const T e1 = dt * cw, e2 = -dt * koff;
 
-  T sj[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) sj[v] = (T)(-0.5 * a.L + ((double)(sl * V + v) + 0.5) * a.ds);
-
-  auto chunk_src = [&](long long t) -> const T* {
-    const long long cell = gw + (t / CH) * (long long)W;
-    const int part = (int)(t % CH);
-    return a.mb + ((size_t)cell * nth + (size_t)part * RC) * ns;
+  // producer cursor: next chunk to issue (cell, part, stage)
+  int icell = gw, ipart = 0, istage = 0, issued = 0;
+  auto issue_next = [&]() {
+    mbar_expect_tx(&bars[istage], chunk_bytes);
+    bulk_g2s(stages + (size_t)istage * chunk_elems,
+             a.mb + ((size_t)icell * nth + (size_t)ipart * RC) * ns, chunk_bytes, &bars[istage]);
+    ++issued;
+    if (++ipart == CH) { ipart = 0; icell += W; }
+    if (++istage == S) istage = 0;
   };
 
   if (TMA) {
     if (lane == 0) {
-      for (int s = 0; s <= S + 1; ++s) mbar_init(&bars[s], 1);
+      for (int q = 0; q <= S + 1; ++q) mbar_init(&bars[q], 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-      for (int s = 0; s < S && s < nchunks; ++s) {
-        mbar_expect_tx(&bars[s], (uint32_t)(chunk_elems * sizeof(T)));
-        bulk_g2s(stages + (size_t)s * chunk_elems, chunk_src(s), (uint32_t)(chunk_elems * sizeof(T)),
-                 &bars[s]);
-      }
+      while (issued < S && issued < nchunks) issue_next();
     }
     __syncwarp();
   }
 
   double mass_acc = 0.0;
   bool timed_out = false, nb_pending = false;
-  long long t_fail = 0;
+  int fail_stage = 0, fail_left = 0;
+  uint32_t fail_par = 0;
   T uxc = 0, uyc = 0, uxe = 0, uxw = 0, uyn = 0, uys = 0, Gxx = 0, Gxy = 0, Gyx = 0, Gyy = 0;
-  long long ce = 0, cwc = 0, cn = 0, cs = 0, cell = 0, jc = -1;
+  int cell = gw - W, ce = 0, cwc = 0, cn = 0, cs = 0;
+  uint32_t nb_par = 1;  // parity of the neighbourhood phase of the current cell
   double mf_n = 0.0, mtot = 0.0;
-  T src = 0;
+  T c3 = 0, e3 = 0;
+  int part = 0, s = 0;
+  uint32_t par = 0;  // parity of the phase chunk t waits for on stage s
 
-  for (long long t = 0; t < nchunks && !timed_out; ++t) {
-    const int part = (int)(t % CH);
-    const int s = (int)(t % S);
+  for (int t = 0; t < nchunks; ++t) {
     if (part == 0) {
       // a new cell: per-cell scalars and the psi-transport inputs
-      cell = gw + (t / CH) * (long long)W;
-      const int ix = (int)(cell % a.nx), iy = (int)(cell / a.nx);
-      const int xp = ix + 1 == a.nx ? 0 : ix + 1, xm = ix == 0 ? a.nx - 1 : ix - 1;
-      const int yp = iy + 1 == a.ny ? 0 : iy + 1, ym = iy == 0 ? a.ny - 1 : iy - 1;
-      ce = (long long)iy * a.nx + xp;
-      cwc = (long long)iy * a.nx + xm;
-      cn = (long long)yp * a.nx + ix;
-      cs = (long long)ym * a.nx + ix;
+      cell += W;
+      nb_par ^= 1u;
+      const int iy = cell / nx, ix = cell - iy * nx;
+      const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
+      const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
+      ce = iy * nx + xp;
+      cwc = iy * nx + xm;
+      cn = yp * nx + ix;
+      cs = ym * nx + ix;
       mf_n = a.mf[cell];
       mtot = a.mtot[cell];
-      src = (T)(kon64 * mf_n);
-      const T* uc = a.ucell + cell * 12;
+      // stage constants: c for the half step, e for the full step
+      c3 = (T)(0.5 * dt64 * kon64 * mf_n);
+      e3 = (T)(dt64 * kon64 * mf_n);
+      const T* uc = a.ucell + (size_t)cell * 12;
       uxc = uc[0]; uyc = uc[1]; uxe = uc[2]; uxw = uc[3]; uyn = uc[4]; uys = uc[5];
       Gxx = uc[6]; Gxy = uc[7]; Gyx = uc[8]; Gyy = uc[9];
-      ++jc;
       if (nb_tma && lane == 0) {
         // stage the psi^n and n_b^n columns of the cell and its 4 neighbours
-        const uint32_t pb = (uint32_t)(nth * sizeof(T)), nbb = (uint32_t)(nth * 8);
-        mbar_expect_tx(nbar, 5 * (pb + nbb));
-        const long long src_cells[5] = {cell, ce, cwc, cn, cs};
+        const uint32_t pb = (uint32_t)(nth * sizeof(T));
+        mbar_expect_tx(nbar, 10 * pb);
+        const int src_cells[5] = {cell, ce, cwc, cn, cs};
 #pragma unroll
         for (int q = 0; q < 5; ++q) {
-          bulk_g2s(psi5 + q * nth, a.psi_in + src_cells[q] * nth, pb, nbar);
-          bulk_g2s(nb5 + q * nth, a.nb_in + src_cells[q] * nth, nbb, nbar);
+          bulk_g2s(psi5 + q * nth, a.psi_in + (size_t)src_cells[q] * nth, pb, nbar);
+          bulk_g2s(nb5 + q * nth, a.nb_in + (size_t)src_cells[q] * nth, pb, nbar);
         }
       }
     }
 
     // ---- motor rows of this chunk
-    const T* stg = stages + (size_t)s * chunk_elems;
-    const T* gsrc = TMA ? nullptr : chunk_src(t);
+    const size_t chunk_off = ((size_t)cell * nth + (size_t)part * RC) * ns;
+    const T* src_rows = TMA ? stages + (size_t)s * chunk_elems : a.mb + chunk_off;
     if (TMA) {
-      const uint32_t par = (uint32_t)((t / S) & 1);
       const bool ok = __all_sync(0xffffffffu, wait_never ? mbar_wait(never, 0u, wait_limit)
                                                          : mbar_wait(&bars[s], par, wait_limit));
       if (!ok) {
+        // chunks t .. t + S - 1 (as many as were issued) are in flight
         timed_out = true;
-        t_fail = t;
-        nb_pending = nb_tma && jc >= 0;
+        fail_stage = s;
+        fail_par = par;
+        fail_left = issued - t;
+        nb_pending = nb_tma;
         break;
       }
     }
-    T* dst = a.mb + ((size_t)cell * nth + (size_t)part * RC) * ns;
+    T* dst = a.mb + chunk_off;
+#pragma unroll kStepUnroll
     for (int p = 0; p < passes; ++p) {
       const int r = p * rpp + rslot;  // row within the chunk
       const bool row_ok = r < RC;
       const bool act = row_ok && lane_ok;
-      const size_t off = (size_t)(row_ok ? r : 0) * ns + (size_t)sl * V;
-      T M[V], R[V], Ms[V];
+      const int off = (row_ok ? r : 0) * ns + sl * V;
+      T M[V], D[V], Ms[V];
       if (act) {
-        const Pack<T, V> q = TMA ? *reinterpret_cast<const Pack<T, V>*>(stg + off)
-                                 : *reinterpret_cast<const Pack<T, V>*>(gsrc + off);
+        const Pack<T, V> q = *reinterpret_cast<const Pack<T, V>*>(src_rows + off);
 #pragma unroll
         for (int v = 0; v < V; ++v) M[v] = q.v[v];
       } else {
 #pragma unroll
         for (int v = 0; v < V; ++v) M[v] = T(0);
       }
-      motor_rhs<T, V>(M, R, first, last, seg, cw, koff, src);
+      // Eq. 4 right-hand side R = (v/ds) D - k_off M + k_on Mf; midpoint RK2
+      // Ms = M + (dt/2) R(M), M' = M + dt R(Ms), with the constants folded
+      walk_dflux<T, V>(M, D, first, last, seg);
 #pragma unroll
-      for (int v = 0; v < V; ++v) Ms[v] = M[v] + hdt * R[v];
-      motor_rhs<T, V>(Ms, R, first, last, seg, cw, koff, src);
-      T snb = T(0), sm1 = T(0);
+      for (int v = 0; v < V; ++v) Ms[v] = fma_t(c1, D[v], fma_t(c2, M[v], c3));
+      walk_dflux<T, V>(Ms, D, first, last, seg);
+      T snb = T(0);
 #pragma unroll
       for (int v = 0; v < V; ++v) {
-        M[v] = M[v] + dt * R[v];
+        M[v] = fma_t(e1, D[v], fma_t(e2, Ms[v], M[v] + e3));
         snb += act ? M[v] : T(0);
-        sm1 = fma_t(sj[v], act ? M[v] : T(0), sm1);
       }
       if (act) {
         Pack<T, V> q;
@@ -343,50 +377,45 @@ __global__ void __launch_bounds__(128, 4) k_substep(const StepArgs<T> a) {
         *reinterpret_cast<Pack<T, V>*>(dst + off) = q;
       }
       snb = seg_sum(snb, seg);
-      sm1 = seg_sum(sm1, seg);
-      if (first && row_ok) {
-        const int k = part * RC + r;
-        s_nb[k] = (double)snb * a.ds;
-        s_m1[k] = (double)sm1 * a.ds;
-      }
+      if (first && row_ok) s_nb[part * RC + r] = snb * ds;
     }
     __syncwarp();
     // the stage is consumed: refill it with the chunk S ahead
-    if (TMA && lane == 0 && t + S < nchunks) {
-      mbar_expect_tx(&bars[s], (uint32_t)(chunk_elems * sizeof(T)));
-      bulk_g2s(stages + (size_t)s * chunk_elems, chunk_src(t + S),
-               (uint32_t)(chunk_elems * sizeof(T)), &bars[s]);
-    }
-    if (part != CH - 1) continue;
+    if (TMA && lane == 0 && issued < nchunks) issue_next();
+    if (++s == S) { s = 0; par ^= 1u; }
+    if (++part != CH) continue;
+    part = 0;
 
     // ---- end of the cell: Eq. 1 for psi, then Eq. 5, Alg. 2 and Eq. 6
     if (nb_tma) {
       const bool ok = __all_sync(0xffffffffu, wait_never ? mbar_wait(never, 0u, wait_limit)
-                                                         : mbar_wait(nbar, (uint32_t)(jc & 1),
-                                                                     wait_limit));
+                                                         : mbar_wait(nbar, nb_par, wait_limit));
       if (!ok) {
         timed_out = true;
-        t_fail = t + 1;  // ring chunks t+1 .. t+S and this neighbourhood are in flight
+        fail_stage = s;
+        fail_par = par;
+        fail_left = issued - (t + 1);
         nb_pending = true;
         break;
       }
     } else {
-      const long long src_cells[5] = {cell, ce, cwc, cn, cs};
+      const int src_cells[5] = {cell, ce, cwc, cn, cs};
       for (int q = 0; q < 5; ++q)
         for (int k = lane; k < nth; k += 32) {
-          psi5[q * nth + k] = a.psi_in[src_cells[q] * nth + k];
-          nb5[q * nth + k] = a.nb_in[src_cells[q] * nth + k];
+          psi5[q * nth + k] = a.psi_in[(size_t)src_cells[q] * nth + k];
+          nb5[q * nth + k] = a.nb_in[(size_t)src_cells[q] * nth + k];
         }
       __syncwarp();
     }
-    double acc = 0.0;
+    T acc = T(0), cell_mass = T(0);
+    const size_t cbase = (size_t)cell * nth;
     for (int k = lane; k < nth; k += 32) {
       const T Pc = g * psi5[k], Pe = g * psi5[nth + k], Pw = g * psi5[2 * nth + k];
       const T Pn = g * psi5[3 * nth + k], Ps = g * psi5[4 * nth + k];
       const T ck = cosk[k], sk = sink[k];
-      const T Vc = vsp + glide * (T)nb5[k], Ve = vsp + glide * (T)nb5[nth + k];
-      const T Vw = vsp + glide * (T)nb5[2 * nth + k], Vn = vsp + glide * (T)nb5[3 * nth + k];
-      const T Vs = vsp + glide * (T)nb5[4 * nth + k];
+      const T Vc = vsp + glide * nb5[k], Ve = vsp + glide * nb5[nth + k];
+      const T Vw = vsp + glide * nb5[2 * nth + k], Vn = vsp + glide * nb5[3 * nth + k];
+      const T Vs = vsp + glide * nb5[4 * nth + k];
       const T axc = fma_t(-Vc, ck, uxc), axe = fma_t(-Ve, ck, uxe), axw = fma_t(-Vw, ck, uxw);
       const T ayc = fma_t(-Vc, sk, uyc), ayn = fma_t(-Vn, sk, uyn), ays = fma_t(-Vs, sk, uys);
       const T Ae = T(0.5) * (axc + axe), Aw = T(0.5) * (axw + axc);
@@ -400,11 +429,12 @@ __global__ void __launch_bounds__(128, 4) k_substep(const StepArgs<T> a) {
       const T Fn = donor(An, Pc, Pn), Fs = donor(As, Ps, Pc);
       const T Fp = donor(wp, Pc, g * psi5[kp]), Fm = donor(wm, g * psi5[km], Pc);
       const T pnew = Pc - dt * ((Fe - Fw) * inv_dx + (Fn - Fs) * inv_dy + (Fp - Fm) * inv_dth);
-      a.psi_out[cell * nth + k] = pnew;
-      mass_acc += (double)pnew;
-      acc += (double)pnew * s_nb[k] * a.dth;
+      a.psi_out[cbase + k] = pnew;
+      cell_mass += pnew;
+      acc = fma_t(pnew * s_nb[k], dth_t, acc);
     }
-    const double Cpre = warp_sum(acc);
+    mass_acc += (double)cell_mass;
+    const double Cpre = (double)warp_sum_t(acc);
     double f = 1.0, C = Cpre;
     if (mtot < Cpre) {
       f = mtot / Cpre;
@@ -414,29 +444,31 @@ __global__ void __launch_bounds__(128, 4) k_substep(const StepArgs<T> a) {
       // rare: rescale the rows of this cell just written (own writes, ordered
       // by the __syncwarp above)
       const T ft = (T)f;
-      T* base = a.mb + (size_t)cell * nth * ns;
-      for (size_t e = lane; e < (size_t)nth * ns; e += 32) base[e] = __ldcg(base + e) * ft;
+      T* base = a.mb + cbase * ns;
+      for (int e = lane; e < nth * ns; e += 32) base[e] = __ldcg(base + e) * ft;
+      for (int k = lane; k < nth; k += 32) a.nb_out[cbase + k] = s_nb[k] * ft;
+    } else {
+      for (int k = lane; k < nth; k += 32) a.nb_out[cbase + k] = s_nb[k];
     }
     if (lane == 0) {
       a.c[cell] = C;
       a.mf[cell] = mtot - C;
-    }
-    for (int k = lane; k < nth; k += 32) {
-      a.nb_out[cell * nth + k] = s_nb[k] * f;
-      if (a.write_m1) a.m1[cell * nth + k] = s_m1[k] * f;
     }
     __syncwarp();
   }
 
   if (TMA && timed_out) {
     // record the failure, then wait (bounded) for the copies this warp still
-    // has in flight -- chunks t_fail .. t_fail + S - 1 -- before leaving
+    // has in flight before leaving
     if (lane == 0) {
       atomicOr(&a.prm->status, 1);
-      const long long hi = t_fail + S < nchunks ? t_fail + S : nchunks;
-      for (long long t2 = t_fail; t2 < hi; ++t2)
-        (void)mbar_wait(&bars[t2 % S], (uint32_t)((t2 / S) & 1), kDrainLimit);
-      if (nb_pending) (void)mbar_wait(nbar, (uint32_t)(jc & 1), kDrainLimit);
+      int st = fail_stage;
+      uint32_t pp = fail_par;
+      for (int i = 0; i < fail_left; ++i) {
+        (void)mbar_wait(&bars[st], pp, kDrainLimit);
+        if (++st == S) { st = 0; pp ^= 1u; }
+      }
+      if (nb_pending) (void)mbar_wait(nbar, nb_par, kDrainLimit);
     }
     __syncwarp();
   }

@@ -78,11 +78,12 @@ _lib = None
 
 
 def load_library(path: str | None = None):
-    """Load libmm.so (raises if it has not been built)."""
+    """Load libmm.so (raises if it has not been built). The environment
+    variable MM_LIBRARY may name another build of the same library."""
     global _lib
     with _lock:
         if _lib is None:
-            p = path or LIB_PATH
+            p = path or os.environ.get("MM_LIBRARY") or LIB_PATH
             if not os.path.exists(p):
                 raise RuntimeError(f"CUDA library not built: {p} is missing "
                                    "(run paper_1908_04279_gb300.build.build())")

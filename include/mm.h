@@ -29,7 +29,8 @@
  *
  * Errors: every call returns an mm_status; no exception crosses the ABI.
  * mm_last_error(h) gives a human-readable message for the last failing call
- * on h (for a NULL handle: the last mm_create failure of this thread).
+ * on h (for a NULL handle: the last failure of mm_create or
+ * mm_moments_static on this thread).
  */
 #ifndef MM_H
 #define MM_H
@@ -166,6 +167,26 @@ mm_status mm_debug_set(mm_handle* h, unsigned int wait_limit, unsigned int flags
 mm_status mm_get_launch_info(mm_handle* h, int* info, int n);
 
 const char* mm_last_error(const mm_handle* h);
+
+/* Moments of a state held by the caller, with no device allocation (this
+ * entry point has no counterpart in the paper). For callers that cannot call
+ * cudaMalloc -- an application that reserved the GPU's memory for its own
+ * pool and forbids allocations it does not manage, or a time-critical loop
+ * that must not pay the synchronisation an allocation may imply.
+ *   psi, mb, mf, c: float64 device arrays in the layouts above (inputs);
+ *   fields: float64 device array [12][ny][nx] as in mm_moments, or NULL;
+ *   scalars: float64 device array [8] as in mm_moments (output);
+ *   stream: cudaStream_t for the two kernels (asynchronous; the caller
+ *   synchronises before reading the outputs).
+ * Scratch is one file-scope device array of 65536 cell records (4 MiB) that
+ * every GPU loading the library holds until exit: grids above 65536 cells are
+ * rejected with MM_ERR_UNSUPPORTED. The first call on a device looks up that
+ * array's device address (once per device, with that device current), so it
+ * should come before any stream capture. All calls share the array: calls
+ * that overlap on the GPU race. Errors: mm_last_error(NULL). */
+mm_status mm_moments_static(const mm_grid* grid, const mm_rates* rates, const double* psi,
+                            const double* mb, const double* mf, const double* c, double* fields,
+                            double* scalars, void* stream);
 
 /* A short description of the build (library name and target architecture). */
 const char* mm_build_info(void);

@@ -20,6 +20,8 @@ const double kPi = 3.14159265358979323846264338327950288;
 constexpr size_t kStagingDoubles = size_t(1) << 22;  // 32 MiB of float64 staging
 }  // namespace
 
+void mm::set_thread_error(const char* msg) { g_create_error = msg; }
+
 struct mm_handle {
   mm_grid g{};
   mm_rates r{};

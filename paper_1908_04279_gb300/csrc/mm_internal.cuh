@@ -85,4 +85,7 @@ cudaError_t launch_moments(const T* psi, const T* mb, const double* mf, const do
                            double ds, double L, double dA, double* fields, double* partial,
                            int nblocks, DevParams* prm, cudaStream_t s);
 
+// Message returned by mm_last_error(NULL) on this thread.
+void set_thread_error(const char* msg);
+
 }  // namespace mm

@@ -69,6 +69,8 @@ PROTOTYPES = {
     "mm_sync": ([_H], C.c_int),
     "mm_debug_set": ([_H, C.c_uint, C.c_uint], C.c_int),
     "mm_get_launch_info": ([_H, C.POINTER(C.c_int), C.c_int], C.c_int),
+    "mm_moments_static": ([C.POINTER(mm_grid), C.POINTER(mm_rates), _P, _P, _P, _P, _P, _P, _P],
+                          C.c_int),
     "mm_last_error": ([_H], C.c_char_p),
     "mm_build_info": ([], C.c_char_p),
 }
@@ -248,6 +250,25 @@ class Simulation:
         self._check(self.lib.mm_moments(self.h, C.byref(out)))
         sc = dict(zip(SCALAR_NAMES, list(out.scalars)))
         return (dict(zip(FIELD_NAMES, host)) if host is not None else None), sc
+
+
+def moments_static(grid: Grid, rates: Rates, psi, mb, mf, c, fields, scalars, stream: int = 0):
+    """Allocation-free moments of a caller-held float64 device state (see
+    mm_moments_static in include/mm.h); all arrays are CUDA tensors."""
+    lib = load_library()
+    ptrs = [_ptr(a, n) for a, n in ((psi, "psi"), (mb, "mb"), (mf, "mf"), (c, "c"),
+                                    (scalars, "scalars"))]
+    if any(d != 1 for _, d in ptrs):
+        raise TypeError("mm_moments_static takes device arrays only")
+    fp, fd = _ptr(fields, "fields")
+    if fields is not None and fd != 1:
+        raise TypeError("fields must be a device array")
+    g = mm_grid(grid.nx, grid.ny, grid.ntheta, grid.ns, grid.L)
+    r = Simulation._r(rates)
+    st = lib.mm_moments_static(C.byref(g), C.byref(r), ptrs[0][0], ptrs[1][0], ptrs[2][0],
+                               ptrs[3][0], fp, ptrs[4][0], C.c_void_p(stream))
+    if st != 0:
+        raise MMError(st, lib.mm_last_error(None).decode())
 
 
 def build_info() -> str:

@@ -70,9 +70,11 @@ typedef struct {
 
 typedef enum {
   MM_FP64 = 0,       /* every array and every operation in float64 */
-  MM_FP32_MIXED = 1  /* Mb, psi and u stored and stepped in float32; s-row
-                        sums, coarse, free and total motor densities, the
-                        global sums and the mass correction in float64 */
+  MM_FP32_MIXED = 1  /* Mb, psi, u and the per-cell motor densities stored
+                        and stepped in float32 (the paper's mixed precision,
+                        Sec. 3.1); the s-reductions feeding the force and
+                        force dipole (compensated), the moments, the global
+                        sums and the mass correction in float64 */
 } mm_precision;
 
 typedef enum {

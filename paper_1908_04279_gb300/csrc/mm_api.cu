@@ -14,6 +14,11 @@
 using mm::DevParams;
 using mm::StepArgs;
 
+// Widest vector (values per lane) of the float32 substep kernel.
+#ifndef MM_FP32_VMAX
+#define MM_FP32_VMAX 8
+#endif
+
 namespace {
 thread_local std::string g_create_error;
 const double kPi = 3.14159265358979323846264338327950288;
@@ -34,9 +39,9 @@ struct mm_handle {
   void* mb = nullptr;
   void* psi[2] = {nullptr, nullptr};
   void* nb[2] = {nullptr, nullptr};
-  double* mf = nullptr;
-  double* c = nullptr;
-  double* mtot = nullptr;
+  void* mf = nullptr;    // free, coarse and total motors per cell, state precision
+  void* c = nullptr;
+  void* mtot = nullptr;
   void* u = nullptr;
   void* ucell = nullptr;
   double* u64 = nullptr;
@@ -160,9 +165,9 @@ StepArgs<T> step_args(mm_handle* h, int parity) {
   a.psi_out = (T*)h->psi[parity ^ 1];
   a.nb_in = (const T*)h->nb[parity];
   a.nb_out = (T*)h->nb[parity ^ 1];
-  a.mf = h->mf;
-  a.c = h->c;
-  a.mtot = h->mtot;
+  a.mf = (T*)h->mf;
+  a.c = (T*)h->c;
+  a.mtot = (const T*)h->mtot;
   a.ucell = (const T*)h->ucell;
   a.trig = (const T*)h->trig;
   a.partial = h->partial;
@@ -178,6 +183,7 @@ cudaError_t launch_one(mm_handle* h, int parity, cudaStream_t s) {
                      : mm::launch_substep<double, 1>(a, h->grid_step, h->block, h->smem, h->tma, s);
   }
   StepArgs<float> a = step_args<float>(h, parity);
+  if (h->V == 8) return mm::launch_substep<float, 8>(a, h->grid_step, h->block, h->smem, h->tma, s);
   return h->V == 4 ? mm::launch_substep<float, 4>(a, h->grid_step, h->block, h->smem, h->tma, s)
                    : mm::launch_substep<float, 1>(a, h->grid_step, h->block, h->smem, h->tma, s);
 }
@@ -194,15 +200,23 @@ constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory per block a
 
 mm_status configure(mm_handle* h) {
   const int ns = h->g.ns, nth = h->g.ntheta;
-  const int vmax = h->prec == MM_FP64 ? 2 : 4;
-  h->V = ns % vmax == 0 ? vmax : 1;
+  // values per lane: the widest instantiated vector that divides ns -- float64
+  // {2, 1}, float32 {8, 4, 1} (two 16-byte vectors, one, or scalar lanes)
+  h->V = 1;
+  if (h->prec == MM_FP64) {
+    if (ns % 2 == 0) h->V = 2;
+  } else if (MM_FP32_VMAX >= 8 && ns % 8 == 0) {
+    h->V = 8;
+  } else if (ns % 4 == 0) {
+    h->V = 4;
+  }
   const int nl = ns / h->V;
   if (nl > 32)
     return fail(h, MM_ERR_UNSUPPORTED, "ns too large: one s-row must fit in one warp");
   int seg = 1;
   while (seg < nl) seg <<= 1;
   h->seg = seg;
-  h->tma = h->V == vmax;
+  h->tma = ((size_t)h->V * h->tsz) % 16 == 0;
   const size_t row_bytes = (size_t)ns * h->tsz;
   int ch = 1;
   while (ch < nth && (nth % ch != 0 || (size_t)(nth / ch) * row_bytes > kChunkBytes)) ++ch;
@@ -224,18 +238,19 @@ mm_status configure(mm_handle* h) {
     e = h->V == 2 ? mm::substep_prepare<double, 2>(h->block, h->smem, h->tma, &bps)
                   : mm::substep_prepare<double, 1>(h->block, h->smem, h->tma, &bps);
   else
-    e = h->V == 4 ? mm::substep_prepare<float, 4>(h->block, h->smem, h->tma, &bps)
-                  : mm::substep_prepare<float, 1>(h->block, h->smem, h->tma, &bps);
+    e = h->V == 8 ? mm::substep_prepare<float, 8>(h->block, h->smem, h->tma, &bps)
+        : h->V == 4 ? mm::substep_prepare<float, 4>(h->block, h->smem, h->tma, &bps)
+                    : mm::substep_prepare<float, 1>(h->block, h->smem, h->tma, &bps);
   CK(e);
   if (bps < 1) return fail(h, MM_ERR_UNSUPPORTED, "substep kernel cannot be resident");
   long long g = (long long)bps * h->sms;
   const long long need = (h->ncells + wpb - 1) / wpb;
   if (g > need) g = need;
   h->grid_step = (int)g;
-  long long gm = 4LL * h->sms;
-  if (gm > h->ncells) gm = h->ncells;
+  long long gm = 8LL * h->sms;  // blocks of 4 warps, one warp per cell
+  if (gm > (h->ncells + 3) / 4) gm = (h->ncells + 3) / 4;
   h->grid_mom = (int)gm;
-  h->npartial = std::max(h->grid_step * wpb, 8 * h->grid_mom);
+  h->npartial = std::max(h->grid_step * wpb, 4 * h->grid_mom);
   return MM_OK;
 }
 
@@ -248,7 +263,9 @@ mm_status check_status(mm_handle* h) {
   if (st) {
     const int zero = 0;
     CK(cudaMemcpy(&h->prm->status, &zero, sizeof zero, cudaMemcpyHostToDevice));
-    return fail(h, MM_ERR_TIMEOUT, "a bounded wait in the substep kernel gave up; the state is invalid");
+    if (st & 1)
+      return fail(h, MM_ERR_TIMEOUT, "a bounded wait in the substep kernel gave up; the state is invalid");
+    return fail(h, MM_ERR_NONFINITE, "the substep rule found no positive finite rate");
   }
   return MM_OK;
 }
@@ -305,11 +322,13 @@ mm_status run_init(mm_handle* h) {
   cudaError_t e;
   if (h->prec == MM_FP64)
     e = mm::launch_init_cells<double>((double*)h->mb, (const double*)h->psi[h->parity],
-                                      (double*)h->nb[h->parity], h->mf, h->c, h->mtot, h->ncells,
+                                      (double*)h->nb[h->parity], (double*)h->mf, (double*)h->c,
+                                      (const double*)h->mtot, h->ncells,
                                       h->g.ntheta, h->g.ns, ds, dth, h->stream);
   else
     e = mm::launch_init_cells<float>((float*)h->mb, (const float*)h->psi[h->parity],
-                                     (float*)h->nb[h->parity], h->mf, h->c, h->mtot, h->ncells,
+                                     (float*)h->nb[h->parity], (float*)h->mf, (float*)h->c,
+                                     (const float*)h->mtot, h->ncells,
                                      h->g.ntheta, h->g.ns, ds, dth, h->stream);
   CK(e);
   return MM_OK;
@@ -318,15 +337,21 @@ mm_status run_init(mm_handle* h) {
 mm_status run_moments(mm_handle* h) {
   const double dth = 2.0 * kPi / h->g.ntheta, ds = h->g.L / h->g.ns;
   const double dA = (1.0 / h->g.nx) * (1.0 / h->g.ny);
+  // the moments kernel reads rows with at most 4 values per lane
+  const int mV = std::min(h->V, 4);
+  int mseg = 1;
+  while (mseg < h->g.ns / mV) mseg <<= 1;
   cudaError_t e;
   if (h->prec == MM_FP64)
-    e = mm::launch_moments<double>((const double*)h->psi[h->parity], (const double*)h->mb, h->mf,
-                                   h->c, h->trig64, h->ncells, h->g.ntheta, h->g.ns, dth, ds,
+    e = mm::launch_moments<double>((const double*)h->psi[h->parity], (const double*)h->mb,
+                                   (const double*)h->mf, (const double*)h->c, h->trig64, h->ncells, h->g.ntheta, h->g.ns, mV,
+                                   mseg, dth, ds,
                                    h->g.L, dA, h->fields, h->partial, h->grid_mom, h->prm,
                                    h->stream);
   else
-    e = mm::launch_moments<float>((const float*)h->psi[h->parity], (const float*)h->mb, h->mf,
-                                  h->c, h->trig64, h->ncells, h->g.ntheta, h->g.ns, dth, ds,
+    e = mm::launch_moments<float>((const float*)h->psi[h->parity], (const float*)h->mb,
+                                  (const float*)h->mf, (const float*)h->c, h->trig64, h->ncells, h->g.ntheta, h->g.ns, mV,
+                                  mseg, dth, ds,
                                   h->g.L, dA, h->fields, h->partial, h->grid_mom, h->prm,
                                   h->stream);
   CK(e);
@@ -415,14 +440,14 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
   ALLOC(h->psi[1], h->rows * h->tsz);
   ALLOC(h->nb[0], h->rows * h->tsz);
   ALLOC(h->nb[1], h->rows * h->tsz);
-  ALLOC(h->mf, nc * 8);
-  ALLOC(h->c, nc * 8);
-  ALLOC(h->mtot, nc * 8);
+  ALLOC(h->mf, nc * h->tsz);
+  ALLOC(h->c, nc * h->tsz);
+  ALLOC(h->mtot, nc * h->tsz);
   ALLOC(h->u, 2 * nc * h->tsz);
   ALLOC(h->ucell, 12 * nc * h->tsz);
   ALLOC(h->u64, 2 * nc * 8);
   ALLOC(h->trig, 4 * (size_t)grid->ntheta * h->tsz);
-  ALLOC(h->trig64, 4 * (size_t)grid->ntheta * 8);
+  ALLOC(h->trig64, 14 * (size_t)grid->ntheta * 8);
   ALLOC(h->partial, (size_t)h->npartial * 8 * 8);
   ALLOC(h->fields, 12 * nc * 8);
   ALLOC(h->staging, kStagingDoubles * 8);
@@ -443,7 +468,24 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
     tr[2 * nth + k] = std::cos((k + 0.5) * dth);
     tr[3 * nth + k] = std::sin((k + 0.5) * dth);
   }
-  e = cudaMemcpy(h->trig64, tr.data(), tr.size() * 8, cudaMemcpyHostToDevice);
+  // moment weights after the four trigonometric rows (see k_moments)
+  std::vector<double> tw(14 * (size_t)nth);
+  std::copy(tr.begin(), tr.end(), tw.begin());
+  for (int k = 0; k < nth; ++k) {
+    const double c = tr[k], s = tr[nth + k];
+    double* w = tw.data() + 4 * (size_t)nth;
+    w[k] = dth;
+    w[nth + k] = c * dth;
+    w[2 * nth + k] = s * dth;
+    w[3 * nth + k] = (c * c - 0.5) * dth;
+    w[4 * nth + k] = c * s * dth;
+    w[5 * nth + k] = c;
+    w[6 * nth + k] = s;
+    w[7 * nth + k] = c * c * dth;
+    w[8 * nth + k] = c * s * dth;
+    w[9 * nth + k] = s * s * dth;
+  }
+  e = cudaMemcpy(h->trig64, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
     if (prec == MM_FP64) {
       e = cudaMemcpy(h->trig, tr.data(), tr.size() * 8, cudaMemcpyHostToDevice);
@@ -459,9 +501,8 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
   if (upload_params(h) != MM_OK) return bail(MM_ERR_CUDA);
   // default state: psi = 1/(2 pi), Mb = 0, M = 1, u = 0
   {
-    std::vector<double> ones(nc, 1.0), zeros(2 * nc, 0.0);
-    e = cudaMemcpy(h->mtot, ones.data(), nc * 8, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(h->u64, zeros.data(), 2 * nc * 8, cudaMemcpyHostToDevice);
+    std::vector<double> zeros(2 * nc, 0.0);
+    e = cudaMemcpy(h->u64, zeros.data(), 2 * nc * 8, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(h->u, 0, 2 * nc * h->tsz);
     if (e == cudaSuccess) e = cudaMemset(h->ucell, 0, 12 * nc * h->tsz);
     if (e == cudaSuccess) e = cudaMemset(h->mb, 0, h->mbn * h->tsz);
@@ -520,11 +561,10 @@ mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const 
     CK(cudaMemsetAsync(h->mb, 0, h->mbn * h->tsz, h->stream));
   }
   if (mtot) {
-    CK(cudaMemcpyAsync(h->mtot, mtot, (size_t)h->ncells * 8,
-                       on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->stream));
+    if ((st = put_array(h, h->mtot, mtot, (size_t)h->ncells, on_device)) != MM_OK) return st;
   } else {
     std::vector<double> ones((size_t)h->ncells, 1.0);
-    CK(cudaMemcpyAsync(h->mtot, ones.data(), ones.size() * 8, cudaMemcpyHostToDevice, h->stream));
+    if ((st = put_array(h, h->mtot, ones.data(), ones.size(), 0)) != MM_OK) return st;
     CK(cudaStreamSynchronize(h->stream));
   }
   const double one = 1.0;
@@ -551,9 +591,8 @@ mm_status mm_get_state(mm_handle* h, double* psi, double* mb, double* mf, double
   if (psi && (st = get_array(h, psi, h->psi[h->parity], h->rows, on_device, scale)) != MM_OK)
     return st;
   if (mb && (st = get_array(h, mb, h->mb, h->mbn, on_device, nullptr)) != MM_OK) return st;
-  const cudaMemcpyKind kd = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-  if (mf) CK(cudaMemcpyAsync(mf, h->mf, (size_t)h->ncells * 8, kd, h->stream));
-  if (c) CK(cudaMemcpyAsync(c, h->c, (size_t)h->ncells * 8, kd, h->stream));
+  if (mf && (st = get_array(h, mf, h->mf, (size_t)h->ncells, on_device, nullptr)) != MM_OK) return st;
+  if (c && (st = get_array(h, c, h->c, (size_t)h->ncells, on_device, nullptr)) != MM_OK) return st;
   return check_status(h);
 }
 
@@ -589,16 +628,7 @@ mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
                                  (double)h->g.nx, (double)h->g.ny, 1.0 / dth, dth, h->r.glide,
                                  h->r.v_sp, h->prm, h->stream);
   CK(e);
-  double mx[3];
-  CK(cudaMemcpyAsync(mx, h->prm->dtmax, sizeof mx, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
-  const double ds = h->g.L / h->g.ns;
-  double rate = std::max(std::max(h->r.v_walk / ds, mx[0]),
-                         std::max(mx[1], h->r.k_off + h->r.k_on * h->g.L * mx[2]));
-  if (!(rate > 0.0) || !std::isfinite(rate))
-    return fail(h, MM_ERR_NONFINITE, "substep rule has no positive finite rate");
-  h->dt = h->r.cfl / rate;
-  CK(cudaMemcpy(&h->prm->dt, &h->dt, 8, cudaMemcpyHostToDevice));
+  CK(mm::launch_dt_finalize(h->prm, h->g.L / h->g.ns, h->g.L, h->r.cfl, h->stream));
   h->have_vel = true;
   h->have_dt = true;
   return MM_OK;
@@ -607,6 +637,10 @@ mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
 mm_status mm_get_dt(mm_handle* h, double* dt) {
   if (!h || !dt) return MM_ERR_INVALID;
   if (!h->have_dt) return fail(h, MM_ERR_STATE, "no dt yet: call mm_set_velocity or mm_set_dt");
+  DeviceGuard dg(h->device);
+  CK(cudaMemcpyAsync(&h->dt, &h->prm->dt, 8, cudaMemcpyDeviceToHost, h->stream));
+  mm_status st = check_status(h);
+  if (st != MM_OK) return st;
   *dt = h->dt;
   return MM_OK;
 }

@@ -49,9 +49,8 @@ __global__ void k_convert(TO* out, const TI* in, size_t n, const double* scale) 
 // state precision), C = sum_k psi n_b dtheta, the Alg. 2 scale-down where
 // C > M, Mf = M - C.
 template <typename T>
-__global__ void k_init_cells(T* mb, const T* psi, T* nb, double* mf, double* c,
-                             const double* mtot, long long ncells, int nth, int ns, double ds,
-                             double dth) {
+__global__ void k_init_cells(T* mb, const T* psi, T* nb, T* mf, T* c, const T* mtot,
+                             long long ncells, int nth, int ns, double ds, double dth) {
   __shared__ double red[32];
   __shared__ double s_f;
   for (long long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
@@ -65,15 +64,15 @@ __global__ void k_init_cells(T* mb, const T* psi, T* nb, double* mf, double* c,
     }
     const double C = block_sum(acc, red);
     if (threadIdx.x == 0) {
-      const double M = mtot[cell];
+      const double M = (double)mtot[cell];
       double f = 1.0, Cc = C;
       if (M < C) {
         f = M / C;
         Cc = M;
       }
       s_f = f;
-      c[cell] = Cc;
-      mf[cell] = M - Cc;
+      c[cell] = (T)Cc;
+      mf[cell] = (T)(M - Cc);
     }
     __syncthreads();
     const double f = s_f;
@@ -134,87 +133,188 @@ __global__ void k_dt_max(const T* psi, const T* nb, const double* u64, const dou
   if (threadIdx.x == 0) atomic_max_nonneg(&prm->dtmax[2], rhomax);
 }
 
-// Moments per cell (one CTA per cell, threads over theta) and per-CTA
-// partial global sums; the last CTA adds the partials in a fixed order. The
-// s-reductions feeding the force and the force dipole -- n_b = sum_j Mb ds and
-// m1 = sum_j s_j Mb ds -- are recomputed here from Mb in float64 sequential
-// sums, in both precisions.
-template <typename T>
-__global__ void k_moments(const T* psi, const T* mb, const double* mf, const double* c,
-                          const double* trig, long long ncells, int nth, int ns, double dth,
-                          double ds, double L, double dA, double* fields, double* partial,
-                          DevParams* prm) {
-  __shared__ double red[32];
-  __shared__ unsigned int s_last;
+// ---- s-row sums for the moments: n_b = sum_j Mb_j ds and m1 = sum_j s_j Mb_j ds
+
+// Compensated float32 accumulator (hi + lo), error-free transformations of
+// Knuth (TwoSum) and of the fused multiply-add (TwoProduct).
+struct FF {
+  float hi, lo;
+};
+__device__ __forceinline__ void ff_add(FF& a, float x) {
+  const float s = a.hi + x;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (x - bb);
+  a.hi = s;
+  a.lo += e;
+}
+__device__ __forceinline__ void ff_add_prod(FF& a, float u, float v) {
+  const float p = __fmul_rn(u, v);  // not contracted into the sum below
+  const float pe = __fmaf_rn(u, v, -p);
+  ff_add(a, p);
+  a.lo += pe;
+}
+__device__ __forceinline__ void ff_merge(FF& a, const FF& b) {
+  const float lo = a.lo + b.lo;
+  a.lo = 0.0f;
+  ff_add(a, b.hi);
+  a.lo += lo;
+}
+
+// Row sums of the V values a lane holds, reduced over the row's `seg` lanes;
+// every lane of the segment gets (n_b / ds, m1 / ds) in float64.
+template <int V>
+__device__ __forceinline__ void row_sums(const float (&m)[V], const float (&sj)[V], int seg,
+                                         double& nb, double& m1) {
+  FF a{0.f, 0.f}, b{0.f, 0.f};
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    ff_add(a, m[v]);
+    ff_add_prod(b, sj[v], m[v]);
+  }
+  for (int o = seg >> 1; o > 0; o >>= 1) {
+    FF ao{__shfl_xor_sync(0xffffffffu, a.hi, o, seg), __shfl_xor_sync(0xffffffffu, a.lo, o, seg)};
+    FF bo{__shfl_xor_sync(0xffffffffu, b.hi, o, seg), __shfl_xor_sync(0xffffffffu, b.lo, o, seg)};
+    ff_merge(a, ao);
+    ff_merge(b, bo);
+  }
+  nb = (double)a.hi + (double)a.lo;
+  m1 = (double)b.hi + (double)b.lo;
+}
+template <int V>
+__device__ __forceinline__ void row_sums(const double (&m)[V], const double (&sj)[V], int seg,
+                                         double& nb, double& m1) {
+  double a = 0.0, b = 0.0;
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    a += m[v];
+    b += sj[v] * m[v];
+  }
+  for (int o = seg >> 1; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o, seg);
+    b += __shfl_xor_sync(0xffffffffu, b, o, seg);
+  }
+  nb = a;
+  m1 = b;
+}
+
+template <typename T, int V>
+struct alignas(sizeof(T) * V) VPack {
+  T v[V];
+};
+
+// Moments, one warp per cell, no block barriers. The s-rows of the cell are
+// read with the substep kernel's lane mapping (a row over `seg` lanes, V
+// consecutive nodes per lane, vector loads) and reduced to n_b and m1: in
+// float64 in the float64 form, compensated float32 (float-float) converted to
+// float64 per row in the float32 form -- these are the s-reductions feeding
+// the force and the force dipole. Then lanes over theta form the 12 fields.
+// Each warp keeps partial global sums; the last warp to finish adds the
+// per-warp partials in a fixed order.
+template <typename T, int V>
+__global__ void k_moments(const T* psi, const T* mb, const T* mf, const T* c,
+                          const double* trig, long long ncells, int nth, int ns, int seg,
+                          double dth, double ds, double L, double dA, double* fields,
+                          double* partial, DevParams* prm) {
+  extern __shared__ double msm[];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  double* s_nb = msm + (size_t)wib * 2 * nth;
+  double* s_m1 = s_nb + nth;
+  const long long gw = blockIdx.x * (long long)(blockDim.x >> 5) + wib;
+  const long long W = (long long)gridDim.x * (blockDim.x >> 5);
   const double g = prm->psi_scale;
   const double Fm = prm->force_scale, ell = prm->ell;
+  const int sl = lane & (seg - 1), rslot = lane / seg, rpp = 32 / seg;
+  const int nl = ns / V;
+  const bool lane_ok = sl < nl;
+  T sj[V];
+#pragma unroll
+  for (int v = 0; v < V; ++v) sj[v] = (T)(-0.5 * L + ((double)(sl * V + v) + 0.5) * ds);
   // global accumulators: N_psi, bound, free, sum psi cos, sum psi sin, sum psi, sum tr
   double gs[7] = {0, 0, 0, 0, 0, 0, 0};
-  for (long long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
-    double f[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int k = threadIdx.x; k < nth; k += blockDim.x) {
-      const double ct = trig[k], st = trig[nth + k];
-      const double p = (double)psi[cell * nth + k] * g;
-      const T* row = mb + ((size_t)cell * nth + k) * ns;
-      double nbk = 0.0, m1k = 0.0;
-      for (int j = 0; j < ns; ++j) {
-        const double mj = (double)row[j];
-        nbk += mj * ds;
-        m1k += (-0.5 * L + (j + 0.5) * ds) * mj * ds;
+  for (long long cell = gw; cell < ncells; cell += W) {
+    for (int r0 = 0; r0 < nth; r0 += rpp) {
+      const int k = r0 + rslot;
+      const bool act = k < nth && lane_ok;
+      T m[V];
+      if (act) {
+        const VPack<T, V> q =
+            *reinterpret_cast<const VPack<T, V>*>(mb + ((size_t)cell * nth + k) * ns + sl * V);
+#pragma unroll
+        for (int v = 0; v < V; ++v) m[v] = q.v[v];
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) m[v] = T(0);
       }
-      f[0] += p * dth;
-      f[1] += p * ct * dth;
-      f[2] += p * st * dth;
-      f[3] += p * (ct * ct - 0.5) * dth;
-      f[4] += p * ct * st * dth;
-      f[5] += Fm * ct * p * nbk * dth;
-      f[6] += Fm * st * p * nbk * dth;
-      f[7] += Fm * ell * ct * ct * p * m1k * dth;
-      f[8] += Fm * ell * ct * st * p * m1k * dth;
-      f[9] += Fm * ell * st * st * p * m1k * dth;
-      gs[3] += p * ct;
-      gs[4] += p * st;
+      double nbk, m1k;
+      row_sums<V>(m, sj, seg, nbk, m1k);
+      if (sl == 0 && k < nth) {
+        s_nb[k] = nbk * ds;
+        s_m1[k] = m1k * ds;
+      }
+    }
+    __syncwarp();
+    double f[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+    // weights w[q][k] (built on the host): dth, cos dth, sin dth,
+    // (cos^2 - 1/2) dth, cos sin dth, cos, sin, cos^2 dth, cos sin dth, sin^2 dth
+    const double* w = trig + 4 * (size_t)nth;
+    for (int k = lane; k < nth; k += 32) {
+      const double p = (double)psi[cell * nth + k] * g;
+      const double pn = p * s_nb[k] * Fm, pm = p * s_m1[k] * (Fm * ell);
+      f[0] = fma(p, w[k], f[0]);
+      f[1] = fma(p, w[nth + k], f[1]);
+      f[2] = fma(p, w[2 * nth + k], f[2]);
+      f[3] = fma(p, w[3 * nth + k], f[3]);
+      f[4] = fma(p, w[4 * nth + k], f[4]);
+      f[5] = fma(pn, w[nth + k], f[5]);
+      f[6] = fma(pn, w[2 * nth + k], f[6]);
+      f[7] = fma(pm, w[7 * nth + k], f[7]);
+      f[8] = fma(pm, w[8 * nth + k], f[8]);
+      f[9] = fma(pm, w[9 * nth + k], f[9]);
+      gs[3] = fma(p, w[5 * nth + k], gs[3]);
+      gs[4] = fma(p, w[6 * nth + k], gs[4]);
       gs[5] += p;
     }
-    double tot[10];
+    __syncwarp();
 #pragma unroll
-    for (int q = 0; q < 10; ++q) tot[q] = block_sum(f[q], red);
-    if (threadIdx.x == 0) {
-      const double cc = c[cell], ff = mf[cell];
-      fields[0 * ncells + cell] = tot[0];
-      fields[1 * ncells + cell] = tot[1];
-      fields[2 * ncells + cell] = tot[2];
-      fields[3 * ncells + cell] = tot[3];
-      fields[4 * ncells + cell] = tot[4];
+    for (int q = 0; q < 10; ++q) f[q] = warp_sum(f[q]);
+    if (lane == 0) {
+      const double cc = (double)c[cell], ff = (double)mf[cell];
+      fields[0 * ncells + cell] = f[0];
+      fields[1 * ncells + cell] = f[1];
+      fields[2 * ncells + cell] = f[2];
+      fields[3 * ncells + cell] = f[3];
+      fields[4 * ncells + cell] = f[4];
       fields[5 * ncells + cell] = cc;
       fields[6 * ncells + cell] = ff;
-      fields[7 * ncells + cell] = tot[5];
-      fields[8 * ncells + cell] = tot[6];
-      fields[9 * ncells + cell] = tot[7];
-      fields[10 * ncells + cell] = tot[8];
-      fields[11 * ncells + cell] = tot[9];
-      gs[0] += tot[0] * dA;
+      fields[7 * ncells + cell] = f[5];
+      fields[8 * ncells + cell] = f[6];
+      fields[9 * ncells + cell] = f[7];
+      fields[10 * ncells + cell] = f[8];
+      fields[11 * ncells + cell] = f[9];
+      gs[0] += f[0] * dA;
       gs[1] += cc * dA;
       gs[2] += ff * dA;
-      gs[6] += tot[7] + tot[9];
+      gs[6] += f[7] + f[9];
     }
   }
-  double tot[7];
 #pragma unroll
-  for (int q = 0; q < 7; ++q) tot[q] = block_sum(gs[q], red);
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < 7; ++q) partial[(size_t)blockIdx.x * 8 + q] = tot[q];
+  for (int q = 0; q < 7; ++q) gs[q] = warp_sum(gs[q]);
+  unsigned int is_last = 0;
+  if (lane == 0) {
+    for (int q = 0; q < 7; ++q) partial[gw * 8 + q] = gs[q];
     __threadfence();
-    const unsigned int prev = atomicInc(&prm->counter2, gridDim.x - 1);
-    s_last = prev == gridDim.x - 1;
+    const unsigned int prev = atomicInc(&prm->counter2, (unsigned int)W - 1);
+    is_last = prev == (unsigned int)W - 1;
   }
-  __syncthreads();
-  if (s_last) {
+  is_last = __shfl_sync(0xffffffffu, is_last, 0);
+  if (is_last) {
     __threadfence();
-    if (threadIdx.x == 0) {
-      double t[7] = {0, 0, 0, 0, 0, 0, 0};
-      for (unsigned int b = 0; b < gridDim.x; ++b)
-        for (int q = 0; q < 7; ++q) t[q] += __ldcg(partial + (size_t)b * 8 + q);
+    double t[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (long long b = lane; b < W; b += 32)
+      for (int q = 0; q < 7; ++q) t[q] += __ldcg(partial + b * 8 + q);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) t[q] = warp_sum(t[q]);
+    if (lane == 0) {
       prm->scalars[0] = t[0];
       prm->scalars[1] = t[1];
       prm->scalars[2] = t[2];
@@ -226,6 +326,18 @@ __global__ void k_moments(const T* psi, const T* mb, const double* mf, const dou
       prm->sum_psi = t[5];
     }
   }
+}
+
+// The adaptive-substep rule, evaluated on the device in float64 from the
+// maxima of k_dt_max: dt = cfl / max(v/ds, adv, rot, k_off + k_on L rho_max).
+// A non-finite or non-positive rate leaves dt unchanged and sets status bit 1.
+__global__ void k_dt_finalize(DevParams* prm, double ds, double L, double cfl) {
+  const double rate = fmax(fmax(prm->v_walk / ds, prm->dtmax[0]),
+                           fmax(prm->dtmax[1], prm->k_off + prm->k_on * L * prm->dtmax[2]));
+  if (rate > 0.0 && isfinite(rate))
+    prm->dt = cfl / rate;
+  else
+    atomicOr(&prm->status, 2);
 }
 
 // Per-cell velocity data of the psi transport: the cell's own u, the x
@@ -285,9 +397,9 @@ cudaError_t launch_prep_ucell(T* ucell, const double* u64, long long ncells, int
 }
 
 template <typename T>
-cudaError_t launch_init_cells(T* mb, const T* psi, T* nb, double* mf, double* c,
-                              const double* mtot, long long ncells, int nth, int ns, double ds,
-                              double dth, cudaStream_t s) {
+cudaError_t launch_init_cells(T* mb, const T* psi, T* nb, T* mf, T* c, const T* mtot,
+                              long long ncells, int nth, int ns, double ds, double dth,
+                              cudaStream_t s) {
   int block = nth >= 128 ? 128 : (nth >= 64 ? 64 : 32);
   long long g = ncells < 152 * 16 ? ncells : 152 * 16;
   k_init_cells<T><<<(int)g, block, 0, s>>>(mb, psi, nb, mf, c, mtot, ncells, nth, ns, ds, dth);
@@ -306,14 +418,34 @@ cudaError_t launch_dt_max(const T* psi, const T* nb, const double* u64, const do
   return cudaGetLastError();
 }
 
+cudaError_t launch_dt_finalize(DevParams* prm, double ds, double L, double cfl, cudaStream_t s) {
+  k_dt_finalize<<<1, 1, 0, s>>>(prm, ds, L, cfl);
+  return cudaGetLastError();
+}
+
 template <typename T>
-cudaError_t launch_moments(const T* psi, const T* mb, const double* mf, const double* c,
-                           const double* trig, long long ncells, int nth, int ns, double dth,
-                           double ds, double L, double dA, double* fields, double* partial,
-                           int nblocks, DevParams* prm, cudaStream_t s) {
-  int block = nth >= 128 ? 128 : (nth >= 64 ? 64 : 32);
-  k_moments<T><<<nblocks, block, 0, s>>>(psi, mb, mf, c, trig, ncells, nth, ns, dth, ds, L, dA,
-                                         fields, partial, prm);
+cudaError_t launch_moments(const T* psi, const T* mb, const T* mf, const T* c,
+                           const double* trig, long long ncells, int nth, int ns, int V, int seg,
+                           double dth, double ds, double L, double dA, double* fields,
+                           double* partial, int nblocks, DevParams* prm, cudaStream_t s) {
+  // nblocks blocks of 4 warps; the partial buffer holds 8 doubles per warp
+  const int block = 128;
+  const size_t smem = (size_t)4 * 2 * nth * sizeof(double);
+  if (smem > 48 * 1024) {
+    const void* fn = V == 4 ? (const void*)k_moments<T, 4>
+                            : (V == 2 ? (const void*)k_moments<T, 2> : (const void*)k_moments<T, 1>);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  if (V == 4)
+    k_moments<T, 4><<<nblocks, block, smem, s>>>(psi, mb, mf, c, trig, ncells, nth, ns, seg, dth,
+                                                 ds, L, dA, fields, partial, prm);
+  else if (V == 2)
+    k_moments<T, 2><<<nblocks, block, smem, s>>>(psi, mb, mf, c, trig, ncells, nth, ns, seg, dth,
+                                                 ds, L, dA, fields, partial, prm);
+  else
+    k_moments<T, 1><<<nblocks, block, smem, s>>>(psi, mb, mf, c, trig, ncells, nth, ns, seg, dth,
+                                                 ds, L, dA, fields, partial, prm);
   return cudaGetLastError();
 }
 
@@ -327,8 +459,8 @@ template cudaError_t launch_prep_ucell<float>(float*, const double*, long long, 
                                               double, cudaStream_t);
 template cudaError_t launch_prep_ucell<double>(double*, const double*, long long, int, int,
                                                double, double, cudaStream_t);
-template cudaError_t launch_init_cells<float>(float*, const float*, float*, double*, double*,
-                                              const double*, long long, int, int, double, double,
+template cudaError_t launch_init_cells<float>(float*, const float*, float*, float*, float*,
+                                              const float*, long long, int, int, double, double,
                                               cudaStream_t);
 template cudaError_t launch_init_cells<double>(double*, const double*, double*, double*, double*,
                                                const double*, long long, int, int, double, double,
@@ -341,13 +473,13 @@ template cudaError_t launch_dt_max<double>(const double*, const double*, const d
                                            const double*, long long, int, int, int, double,
                                            double, double, double, double, double,
                                            DevParams*, cudaStream_t);
-template cudaError_t launch_moments<float>(const float*, const float*, const double*,
-                                           const double*, const double*, long long, int, int,
-                                           double, double, double, double, double*, double*, int,
-                                           DevParams*, cudaStream_t);
+template cudaError_t launch_moments<float>(const float*, const float*, const float*,
+                                           const float*, const double*, long long, int, int, int,
+                                           int, double, double, double, double, double*, double*,
+                                           int, DevParams*, cudaStream_t);
 template cudaError_t launch_moments<double>(const double*, const double*, const double*,
                                             const double*, const double*, long long, int, int,
-                                            double, double, double, double, double*, double*, int,
-                                            DevParams*, cudaStream_t);
+                                            int, int, double, double, double, double, double*,
+                                            double*, int, DevParams*, cudaStream_t);
 
 }  // namespace mm

@@ -23,7 +23,7 @@ struct DevParams {
   double sum_psi;     // sum of psi over all cells and angles (moments kernel)
   unsigned int counter;   // last-warp-done counter of the substep kernel
   unsigned int counter2;  // last-block-done counter of the moments kernel
-  int status;             // bit 0: a bounded device wait gave up
+  int status;             // bit 0: a bounded device wait gave up; bit 1: no valid dt
   unsigned int wait_limit;   // polls of an mbarrier before a wait gives up
   unsigned int debug_flags;  // bit 0: wait on a phase nothing completes (tests)
   int pad;
@@ -45,9 +45,9 @@ struct StepArgs {
   T* psi_out;
   const T* nb_in;     // [cells][nth] n_b = sum_j Mb ds (precision T)
   T* nb_out;
-  double* mf;         // [cells]
-  double* c;          // [cells]
-  const double* mtot; // [cells]
+  T* mf;              // [cells] free motors (Eq. 6), state precision
+  T* c;               // [cells] coarse bound motors (Eq. 5)
+  const T* mtot;      // [cells] total motors
   const T* ucell;     // [cells][12]: ux, uy, ux east, ux west, uy north, uy south,
                       //   Gxx, Gxy, Gyx, Gyy (central differences), 2 spare
   const T* trig;      // [4][nth]: cos th_k, sin th_k, cos th_{k+1/2}, sin th_{k+1/2}
@@ -71,19 +71,20 @@ template <typename T>
 cudaError_t launch_prep_ucell(T* ucell, const double* u64, long long ncells, int nx, int ny,
                               double inv_dx, double inv_dy, cudaStream_t s);
 template <typename T>
-cudaError_t launch_init_cells(T* mb, const T* psi, T* nb, double* mf, double* c,
-                              const double* mtot, long long ncells, int nth, int ns, double ds,
-                              double dth, cudaStream_t s);
+cudaError_t launch_init_cells(T* mb, const T* psi, T* nb, T* mf, T* c, const T* mtot,
+                              long long ncells, int nth, int ns, double ds, double dth,
+                              cudaStream_t s);
 template <typename T>
 cudaError_t launch_dt_max(const T* psi, const T* nb, const double* u64, const double* trig,
                           long long ncells, int nx, int ny, int nth, double inv_dx,
                           double inv_dy, double inv_dth, double dth, double glide, double vsp,
                           DevParams* prm, cudaStream_t s);
+cudaError_t launch_dt_finalize(DevParams* prm, double ds, double L, double cfl, cudaStream_t s);
 template <typename T>
-cudaError_t launch_moments(const T* psi, const T* mb, const double* mf, const double* c,
-                           const double* trig, long long ncells, int nth, int ns, double dth,
-                           double ds, double L, double dA, double* fields, double* partial,
-                           int nblocks, DevParams* prm, cudaStream_t s);
+cudaError_t launch_moments(const T* psi, const T* mb, const T* mf, const T* c,
+                           const double* trig, long long ncells, int nth, int ns, int V, int seg,
+                           double dth, double ds, double L, double dA, double* fields,
+                           double* partial, int nblocks, DevParams* prm, cudaStream_t s);
 
 // Message returned by mm_last_error(NULL) on this thread.
 void set_thread_error(const char* msg);

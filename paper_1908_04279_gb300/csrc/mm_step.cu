@@ -36,10 +36,11 @@ struct alignas(sizeof(T) * V) Pack {
   T v[V];
 };
 
-template <typename T>
-__device__ __forceinline__ T tmax(T a, T b) { return a > b ? a : b; }
-template <typename T>
-__device__ __forceinline__ T tmin(T a, T b) { return a < b ? a : b; }
+// Single min/max instructions (the operands are never NaN here).
+__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
 
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
   const T dt = (T)dt64, hdt = (T)(0.5 * dt64);
   const T cw = (T)(P->v_walk / a.ds);
   const T koff = (T)P->k_off;
-  const double kon64 = P->k_on;
+  const T kon = (T)P->k_on;
   const T glide = (T)P->glide, vsp = (T)P->v_sp;
   const T g = MASSCORR ? (T)P->psi_scale : T(1);
   const uint32_t wait_limit = P->wait_limit;
@@ -288,8 +289,9 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
   T uxc = 0, uyc = 0, uxe = 0, uxw = 0, uyn = 0, uys = 0, Gxx = 0, Gxy = 0, Gyx = 0, Gyy = 0;
   int cell = gw - W, ce = 0, cwc = 0, cn = 0, cs = 0;
   uint32_t nb_par = 1;  // parity of the neighbourhood phase of the current cell
-  double mf_n = 0.0, mtot = 0.0;
+  T mtot = 0;
   T c3 = 0, e3 = 0;
+  T mass_hi = T(0), mass_lo = T(0);  // compensated sum of psi^{n+1} over this warp's cells
   int part = 0, s = 0;
   uint32_t par = 0;  // parity of the phase chunk t waits for on stage s
 
@@ -305,11 +307,11 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
       cwc = iy * nx + xm;
       cn = yp * nx + ix;
       cs = ym * nx + ix;
-      mf_n = a.mf[cell];
+      const T mf_n = a.mf[cell];
       mtot = a.mtot[cell];
       // stage constants: c for the half step, e for the full step
-      c3 = (T)(0.5 * dt64 * kon64 * mf_n);
-      e3 = (T)(dt64 * kon64 * mf_n);
+      c3 = hdt * kon * mf_n;
+      e3 = dt * kon * mf_n;
       const T* uc = a.ucell + (size_t)cell * 12;
       uxc = uc[0]; uyc = uc[1]; uxe = uc[2]; uxw = uc[3]; uyn = uc[4]; uys = uc[5];
       Gxx = uc[6]; Gxy = uc[7]; Gyx = uc[8]; Gyy = uc[9];
@@ -368,8 +370,9 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         M[v] = fma_t(e1, D[v], fma_t(e2, Ms[v], M[v] + e3));
-        snb += act ? M[v] : T(0);
+        snb += M[v];
       }
+      if (!act) snb = T(0);
       if (act) {
         Pack<T, V> q;
 #pragma unroll
@@ -433,17 +436,22 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
       cell_mass += pnew;
       acc = fma_t(pnew * s_nb[k], dth_t, acc);
     }
-    mass_acc += (double)cell_mass;
-    const double Cpre = (double)warp_sum_t(acc);
-    double f = 1.0, C = Cpre;
+    {
+      // TwoSum: mass_hi + mass_lo += cell_mass without rounding loss
+      const T s2 = mass_hi + cell_mass, bb = s2 - mass_hi;
+      mass_lo += (mass_hi - (s2 - bb)) + (cell_mass - bb);
+      mass_hi = s2;
+    }
+    const T Cpre = warp_sum_t(acc);
+    T f = T(1), C = Cpre;
     if (mtot < Cpre) {
       f = mtot / Cpre;
       C = mtot;
     }
-    if (f != 1.0) {
+    if (f != T(1)) {
       // rare: rescale the rows of this cell just written (own writes, ordered
       // by the __syncwarp above)
-      const T ft = (T)f;
+      const T ft = f;
       T* base = a.mb + cbase * ns;
       for (int e = lane; e < nth * ns; e += 32) base[e] = __ldcg(base + e) * ft;
       for (int k = lane; k < nth; k += 32) a.nb_out[cbase + k] = s_nb[k] * ft;
@@ -473,8 +481,9 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
     __syncwarp();
   }
 
-  // sum psi^{n+1}: per-warp partial, the last warp finalises in a fixed order
-  mass_acc = warp_sum(mass_acc);
+  // sum psi^{n+1}: per-warp partial in float64, the last warp finalises in a
+  // fixed order
+  mass_acc = warp_sum((double)mass_hi + (double)mass_lo);
   unsigned int is_last = 0;
   if (lane == 0) {
     a.partial[gw] = mass_acc;
@@ -526,6 +535,8 @@ cudaError_t substep_prepare(int block, size_t smem, bool tma, int* blocks_per_sm
       blocks_per_sm, tma ? k_substep<T, V, true, true> : k_substep<T, V, false, true>, block, smem);
 }
 
+template cudaError_t launch_substep<float, 8>(const StepArgs<float>&, int, int, size_t, bool,
+                                              cudaStream_t);
 template cudaError_t launch_substep<float, 4>(const StepArgs<float>&, int, int, size_t, bool,
                                               cudaStream_t);
 template cudaError_t launch_substep<float, 1>(const StepArgs<float>&, int, int, size_t, bool,
@@ -534,6 +545,7 @@ template cudaError_t launch_substep<double, 2>(const StepArgs<double>&, int, int
                                                cudaStream_t);
 template cudaError_t launch_substep<double, 1>(const StepArgs<double>&, int, int, size_t, bool,
                                                cudaStream_t);
+template cudaError_t substep_prepare<float, 8>(int, size_t, bool, int*);
 template cudaError_t substep_prepare<float, 4>(int, size_t, bool, int*);
 template cudaError_t substep_prepare<float, 1>(int, size_t, bool, int*);
 template cudaError_t substep_prepare<double, 2>(int, size_t, bool, int*);

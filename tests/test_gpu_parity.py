@@ -154,7 +154,9 @@ def test_conservation_on_gpu(mmod, precision, tol):
         f, s1 = sim.moments()
         st = sim.get_state()
     assert abs(s1["N_psi"] - s0["N_psi"]) <= tol * s0["N_psi"]
-    assert abs(s1["motors"] - 1.0) <= 1e-14
+    # Mf = M - C per cell in the state precision: exact in float64, to float32
+    # rounding in the float32 form
+    assert abs(s1["motors"] - 1.0) <= (1e-14 if precision == "fp64" else 1e-7)
     dth, ds = 2 * math.pi / g.ntheta, g.L / g.ns
     C = np.einsum("yxk,yxkj->yx", st["psi"], st["mb"]) * dth * ds
     assert np.abs(st["mf"] + C - 1.0).max() <= (1e-13 if precision == "fp64" else 1e-6)
@@ -171,7 +173,8 @@ def test_fp32_cellular_flow_within_tolerance(mmod, oracle_mod):
     assert_moments_close(om, gm, TOL["fp32"], st)
 
 
-@pytest.mark.parametrize("dims", [(37, 29, 6, 8), (20, 24, 12, 6), (9, 7, 5, 31), (5, 6, 3, 128)])
+@pytest.mark.parametrize("dims", [(37, 29, 6, 8), (20, 24, 12, 6), (9, 7, 5, 31), (5, 6, 3, 128),
+                                  (11, 13, 7, 12)])
 def test_fp32_ragged_shapes_within_tolerance(mmod, oracle_mod, dims):
     g = Grid(*dims)
     r = Rates(glide=0.3, v_sp=0.1)

@@ -297,6 +297,39 @@ def run_ours(args):
         sim.close()
         return el, pinned[0].numel() * 8, out.numel() * 8 + 64
 
+    def adjoint_ratio(precision):
+        """Adjoint workload (64x64 x 32 x 32, 100 substeps, checkpoint every
+        10): time of the recorded forward plus the reverse sweep over the time
+        of the plain forward (graph replay), CUDA events on the handle's stream."""
+        wa = WORKLOADS["adjoint64"]
+        ga, na = wa["grid"], wa["substeps"]
+        pa = psi_isotropic_perturbed(ga, wa["seed"])
+        ua = workload_velocity("adjoint64", 0)
+        sim = mm.Simulation(ga, r, precision, stream=stream.cuda_stream)
+        best_f, best_a = 1e30, 1e30
+        for rep in range(4):
+            sim.set_state(pa)
+            sim.set_velocity(ua)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(na)
+            e1.record(stream)
+            e1.synchronize()
+            best_f = min(best_f, e0.elapsed_time(e1))
+            sim.set_state(pa)
+            sim.set_velocity(ua)
+            e0.record(stream)
+            sim.set_checkpointing(10, na)
+            sim.step(na)
+            sim.adjoint(na, observable="polar_order", n_velocities=1)
+            e1.record(stream)
+            e1.synchronize()
+            best_a = min(best_a, e0.elapsed_time(e1))
+            sim.set_checkpointing(0, 1)
+        sim.close()
+        return {"forward_ms": best_f, "forward_plus_adjoint_ms": best_a,
+                "adjoint_over_forward": (best_a - best_f) / best_f}
+
     units_per_step = g.micro_cells * nsub
     clocks = ClockSampler(local)
     clocks.start()
@@ -305,6 +338,8 @@ def run_ours(args):
     fp64_steps = max(2, min(args.steps, 3))
     fp64_ms, fp64_kern = device_run("fp64", fp64_steps, 1)
     e2e_s, h2d, d2h = e2e_run("fp32", args.steps, args.warmup)
+    adj = {"workload": "adjoint64 (64x64 x 32 x 32, 100 substeps, checkpoint every 10, polar order)",
+           "fp32": adjoint_ratio("fp32"), "fp64": adjoint_ratio("fp64")}
 
     t = torch.tensor([total_ms, kern_ms, fp64_ms, e2e_s], dtype=torch.float64, device=dev)
     if world > 1:
@@ -341,6 +376,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": {"value": world * units_per_step * args.steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "adjoint": adj,
             "gpu_launches": args.steps * (nsub + 3),
             "clocks": clk,
         }

@@ -152,6 +152,54 @@ typedef struct {
 } mm_moments_out;
 mm_status mm_moments(mm_handle* h, mm_moments_out* out);
 
+/* ---- Adjoint (reverse mode) of the substeps, with checkpointing ----------
+ *
+ * mm_set_checkpointing(h, K, max_substeps) starts a recording at the current
+ * state: the following mm_micro_step calls (up to max_substeps substeps in
+ * total, with any number of mm_set_velocity calls in between) save the state
+ * every K substeps; the memory for ceil(max_substeps / K) + 1 checkpoints and
+ * for the K + 1 states of one recomputed segment is reserved here
+ * (MM_ERR_OOM if it does not fit). K = 0 stops and frees the recording, and
+ * so does mm_set_state. While recording, substeps run as individual launches
+ * (no graph) so that checkpoints can be taken between them.
+ *
+ * mm_adjoint_step(h, n, seed, out) runs the reverse sweep over the n substeps
+ * recorded since mm_set_checkpointing (n must equal that count): for each
+ * segment, last first, it restores the checkpoint, recomputes the segment's
+ * states, and applies the transposed substep (discrete adjoint of Eq. 1, of
+ * the midpoint RK2 of Eq. 4 with the Superbee branch the forward took, of
+ * Eq. 5, the Alg. 2 scale-down and Eq. 6) from the last substep to the first.
+ * dt and the velocities are held fixed (not differentiated). The seed is the
+ * gradient of a loss L with respect to the final state, given either as
+ * arrays in moment form or as one of the built-in observables. The live state
+ * of the handle is left as it was. */
+typedef enum {
+  MM_OBS_NONE = 0,         /* seed given by the arrays below */
+  MM_OBS_POLAR_ORDER = 1,  /* L = |sum psi e^{i theta}| / sum psi */
+  MM_OBS_MEAN_STRESS = 2   /* L = mean over cells of tr sigma_a */
+} mm_observable;
+typedef struct {
+  int observable;
+  const double* dL_dpsi; /* [ny][nx][ntheta] or NULL */
+  const double* dL_dnb;  /* [ny][nx][ntheta] or NULL: through n_b = sum_j Mb ds */
+  const double* dL_dm1;  /* [ny][nx][ntheta] or NULL: through m1 = sum_j s_j Mb ds */
+  const double* dL_dmf;  /* [ny][nx] or NULL: through the free motors Mf */
+  int on_device;
+} mm_adjoint_seed;
+typedef struct {
+  double* dL_du;         /* [du_capacity][2][ny][nx] or NULL, in prescription order */
+  int du_capacity;       /* velocity blocks dL_du holds; MM_ERR_INVALID if fewer than
+                            the recording's velocity fields */
+  double* dL_dpsi0;      /* [ny][nx][ntheta] or NULL: w.r.t. psi at the recording start */
+  int on_device;
+  double dL_drates[3];   /* written: dL/dk_off, dL/dv_walk, dL/dk_on */
+  double value;          /* written for a built-in observable: L at the final state */
+  int n_velocities;      /* written: velocity fields in effect during the recording */
+} mm_adjoint_out;
+mm_status mm_set_checkpointing(mm_handle* h, int K, int max_substeps);
+mm_status mm_adjoint_step(mm_handle* h, int n_substeps, const mm_adjoint_seed* seed,
+                          mm_adjoint_out* out);
+
 /* Wait for the handle's stream and report a failure recorded by a kernel
  * since the last check (MM_ERR_TIMEOUT: a bounded device-side wait gave up and
  * the state is no longer valid). mm_get_state and mm_moments check too. */

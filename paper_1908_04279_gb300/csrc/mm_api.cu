@@ -27,7 +27,32 @@ constexpr size_t kStagingDoubles = size_t(1) << 22;  // 32 MiB of float64 stagin
 
 void mm::set_thread_error(const char* msg) { g_create_error = msg; }
 
+// State of an adjoint recording (mm_set_checkpointing / mm_adjoint_step).
+struct Recording {
+  int K = 0, max_sub = 0, nsub = 0, nck = 0;
+  std::vector<void*> bufs;  // every device allocation of the recording
+  std::vector<void*> ck_mb, ck_psi, ck_nb, ck_mf;  // checkpoints (states 0, K, 2K, ...)
+  double* ck_scale = nullptr;                      // psi mass-correction factor per checkpoint
+  std::vector<void*> sl_mb, sl_psi, sl_nb, sl_mf, sl_cpre;  // K + 1 recomputed states
+  void* sl_c = nullptr;
+  // velocity fields (and dt) in effect, in prescription order
+  std::vector<void*> v_ucell;
+  std::vector<double*> v_dt, v_lamG, v_lamu;
+  std::vector<int> sub_vel;  // velocity index of every recorded substep
+  // reverse-sweep buffers
+  void* lpsi[2] = {nullptr, nullptr};
+  void* lmf[2] = {nullptr, nullptr};
+  void* Dd[2] = {nullptr, nullptr};
+  void* lmb = nullptr;
+  double* gpart = nullptr;
+  double* seed[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* coef = nullptr;
+  double* work = nullptr;  // [rows] float64 scratch for dL/dpsi0
+  int adj_grid = 1;
+};
+
 struct mm_handle {
+  Recording rec;
   mm_grid g{};
   mm_rates r{};
   mm_precision prec = MM_FP64;
@@ -112,7 +137,14 @@ mm_status check_rates(const mm_rates* r, mm_handle* h) {
   return MM_OK;
 }
 
+void free_recording(mm_handle* h) {
+  for (void* p : h->rec.bufs)
+    if (p) cudaFree(p);
+  h->rec = Recording();
+}
+
 mm_status free_all(mm_handle* h) {
+  free_recording(h);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
   void* ptrs[] = {h->mb,  h->psi[0], h->psi[1], h->nb[0],   h->nb[1],
@@ -160,13 +192,16 @@ StepArgs<T> step_args(mm_handle* h, int parity) {
   a.inv_dth = 1.0 / a.dth;
   a.ds = h->g.L / h->g.ns;
   a.L = h->g.L;
-  a.mb = (T*)h->mb;
+  a.mb_in = (const T*)h->mb;
+  a.mb_out = (T*)h->mb;
   a.psi_in = (const T*)h->psi[parity];
   a.psi_out = (T*)h->psi[parity ^ 1];
   a.nb_in = (const T*)h->nb[parity];
   a.nb_out = (T*)h->nb[parity ^ 1];
-  a.mf = (T*)h->mf;
+  a.mf_in = (const T*)h->mf;
+  a.mf_out = (T*)h->mf;
   a.c = (T*)h->c;
+  a.cpre_out = nullptr;
   a.mtot = (const T*)h->mtot;
   a.ucell = (const T*)h->ucell;
   a.trig = (const T*)h->trig;
@@ -197,6 +232,39 @@ constexpr int kChunkBytes = 4096;
 constexpr int kWarpInflightBytes = 8192;
 constexpr int kMaxWarpsPerBlock = 4;
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory per block at most
+
+// One substep with explicit state buffers (recomputing a recorded segment).
+struct StepPtrs {
+  const void *psi_in, *nb_in, *mb_in, *mf_in, *ucell;
+  void *psi_out, *nb_out, *mb_out, *mf_out, *c, *cpre;
+};
+template <typename T>
+StepArgs<T> step_args_ptrs(mm_handle* h, const StepPtrs& p) {
+  StepArgs<T> a = step_args<T>(h, 0);
+  a.psi_in = (const T*)p.psi_in;
+  a.psi_out = (T*)p.psi_out;
+  a.nb_in = (const T*)p.nb_in;
+  a.nb_out = (T*)p.nb_out;
+  a.mb_in = (const T*)p.mb_in;
+  a.mb_out = (T*)p.mb_out;
+  a.mf_in = (const T*)p.mf_in;
+  a.mf_out = (T*)p.mf_out;
+  a.c = (T*)p.c;
+  a.cpre_out = (T*)p.cpre;
+  a.ucell = (const T*)p.ucell;
+  return a;
+}
+cudaError_t launch_ptrs(mm_handle* h, const StepPtrs& p, cudaStream_t s) {
+  if (h->prec == MM_FP64) {
+    StepArgs<double> a = step_args_ptrs<double>(h, p);
+    return h->V == 2 ? mm::launch_substep<double, 2>(a, h->grid_step, h->block, h->smem, h->tma, s)
+                     : mm::launch_substep<double, 1>(a, h->grid_step, h->block, h->smem, h->tma, s);
+  }
+  StepArgs<float> a = step_args_ptrs<float>(h, p);
+  if (h->V == 8) return mm::launch_substep<float, 8>(a, h->grid_step, h->block, h->smem, h->tma, s);
+  return h->V == 4 ? mm::launch_substep<float, 4>(a, h->grid_step, h->block, h->smem, h->tma, s)
+                   : mm::launch_substep<float, 1>(a, h->grid_step, h->block, h->smem, h->tma, s);
+}
 
 mm_status configure(mm_handle* h) {
   const int ns = h->g.ns, nth = h->g.ntheta;
@@ -357,6 +425,9 @@ mm_status run_moments(mm_handle* h) {
   CK(e);
   return MM_OK;
 }
+
+mm_status rec_push_version(mm_handle* h);
+mm_status rec_micro_step(mm_handle* h, int n);
 
 }  // namespace
 
@@ -553,6 +624,10 @@ mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const 
   if (!psi) return fail(h, MM_ERR_INVALID, "psi is NULL");
   DeviceGuard dg(h->device);
   mm_status st;
+  if (h->rec.K > 0) {  // a new state ends an adjoint recording
+    CK(cudaStreamSynchronize(h->stream));
+    free_recording(h);
+  }
   h->parity = 0;
   if ((st = put_array(h, h->psi[0], psi, h->rows, on_device)) != MM_OK) return st;
   if (mb) {
@@ -631,6 +706,7 @@ mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
   CK(mm::launch_dt_finalize(h->prm, h->g.L / h->g.ns, h->g.L, h->r.cfl, h->stream));
   h->have_vel = true;
   h->have_dt = true;
+  if (h->rec.K > 0) return rec_push_version(h);
   return MM_OK;
 }
 
@@ -653,6 +729,7 @@ mm_status mm_set_dt(mm_handle* h, double dt) {
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(&h->prm->dt, &h->dt, 8, cudaMemcpyHostToDevice));
   h->have_dt = true;
+  if (h->rec.K > 0) return rec_push_version(h);
   return MM_OK;
 }
 
@@ -664,6 +741,7 @@ mm_status mm_micro_step(mm_handle* h, int n) {
   if (!h->have_vel) return fail(h, MM_ERR_STATE, "no velocity: call mm_set_velocity first");
   if (!h->have_dt) return fail(h, MM_ERR_STATE, "no dt");
   DeviceGuard dg(h->device);
+  if (h->rec.K > 0) return rec_micro_step(h, n);
   if (!h->use_graphs) {
     for (int i = 0; i < n; ++i) {
       CK(launch_one(h, h->parity, h->stream));
@@ -741,5 +819,341 @@ const char* mm_last_error(const mm_handle* h) {
 }
 
 const char* mm_build_info(void) { return "libmm sm_103a (tcgen05-free streaming stencil path)"; }
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Adjoint recording and reverse sweep
+
+namespace {
+
+cudaError_t rec_alloc(mm_handle* h, void** p, size_t bytes) {
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaSuccess) h->rec.bufs.push_back(*p);
+  return e;
+}
+
+// Copy the live state into checkpoint i.
+mm_status rec_save_checkpoint(mm_handle* h, int i) {
+  Recording& R = h->rec;
+  const size_t t = h->tsz, nc = (size_t)h->ncells;
+  CK(cudaMemcpyAsync(R.ck_mb[i], h->mb, h->mbn * t, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(R.ck_psi[i], h->psi[h->parity], h->rows * t, cudaMemcpyDeviceToDevice,
+                     h->stream));
+  CK(cudaMemcpyAsync(R.ck_nb[i], h->nb[h->parity], h->rows * t, cudaMemcpyDeviceToDevice,
+                     h->stream));
+  CK(cudaMemcpyAsync(R.ck_mf[i], h->mf, nc * t, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(R.ck_scale + i, &h->prm->psi_scale, 8, cudaMemcpyDeviceToDevice, h->stream));
+  return MM_OK;
+}
+
+// Remember the velocity (its per-cell block) and dt now in effect.
+mm_status rec_push_version(mm_handle* h) {
+  Recording& R = h->rec;
+  const size_t nc = (size_t)h->ncells;
+  void *uc = nullptr, *dt = nullptr, *lg = nullptr, *lu = nullptr;
+  cudaError_t e;
+  if ((e = rec_alloc(h, &uc, 12 * nc * h->tsz)) != cudaSuccess ||
+      (e = rec_alloc(h, &dt, 8)) != cudaSuccess ||
+      (e = rec_alloc(h, &lg, 4 * nc * 8)) != cudaSuccess ||
+      (e = rec_alloc(h, &lu, 2 * nc * 8)) != cudaSuccess)
+    return cuda_fail(h, "recording: velocity buffers", e);
+  CK(cudaMemcpyAsync(uc, h->ucell, 12 * nc * h->tsz, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(dt, &h->prm->dt, 8, cudaMemcpyDeviceToDevice, h->stream));
+  R.v_ucell.push_back(uc);
+  R.v_dt.push_back((double*)dt);
+  R.v_lamG.push_back((double*)lg);
+  R.v_lamu.push_back((double*)lu);
+  return MM_OK;
+}
+
+// Substeps while recording: direct launches, a checkpoint every K substeps.
+mm_status rec_micro_step(mm_handle* h, int n) {
+  Recording& R = h->rec;
+  if (R.nsub + n > R.max_sub)
+    return fail(h, MM_ERR_STATE, "recording: more substeps than mm_set_checkpointing reserved");
+  mm_status st;
+  for (int i = 0; i < n; ++i) {
+    if (R.nsub > 0 && R.nsub % R.K == 0)
+      if ((st = rec_save_checkpoint(h, R.nsub / R.K)) != MM_OK) return st;
+    R.sub_vel.push_back((int)R.v_ucell.size() - 1);
+    CK(launch_one(h, h->parity, h->stream));
+    h->parity ^= 1;
+    ++R.nsub;
+  }
+  return MM_OK;
+}
+
+// The reverse kernel reads rows with at most 4 values per lane.
+int adj_V(const mm_handle* h) { return std::min(h->V, 4); }
+int adj_seg(const mm_handle* h) {
+  int sg = 1;
+  while (sg < h->g.ns / adj_V(h)) sg <<= 1;
+  return sg;
+}
+
+template <typename T>
+mm::AdjArgs<T> adj_args(mm_handle* h, int slot, int ver, double dt, int cur) {
+  Recording& R = h->rec;
+  mm::AdjArgs<T> a{};
+  a.nx = h->g.nx;
+  a.ny = h->g.ny;
+  a.nth = h->g.ntheta;
+  a.ns = h->g.ns;
+  a.seg = adj_seg(h);
+  a.ncells = h->ncells;
+  a.inv_dx = (double)h->g.nx;
+  a.inv_dy = (double)h->g.ny;
+  a.dth = 2.0 * kPi / h->g.ntheta;
+  a.inv_dth = 1.0 / a.dth;
+  a.ds = h->g.L / h->g.ns;
+  a.L = h->g.L;
+  a.dt = dt;
+  a.v_walk = h->r.v_walk;
+  a.k_on = h->r.k_on;
+  a.k_off = h->r.k_off;
+  a.glide = h->r.glide;
+  a.v_sp = h->r.v_sp;
+  a.psi_n = (const T*)R.sl_psi[slot];
+  a.nb_n = (const T*)R.sl_nb[slot];
+  a.mb_n = (const T*)R.sl_mb[slot];
+  a.mf_n = (const T*)R.sl_mf[slot];
+  a.psi_np = (const T*)R.sl_psi[slot + 1];
+  a.nb_np = (const T*)R.sl_nb[slot + 1];
+  a.cpre_np = (const T*)R.sl_cpre[slot + 1];
+  a.mtot = (const T*)h->mtot;
+  a.ucell = (const T*)R.v_ucell[ver];
+  a.trig = (const T*)h->trig;
+  a.lpsi_in = (const T*)R.lpsi[cur];
+  a.lmf_in = (const T*)R.lmf[cur];
+  a.D_in = (const T*)R.Dd[cur];
+  a.lpsi_out = (T*)R.lpsi[cur ^ 1];
+  a.lmb = (T*)R.lmb;
+  a.lmf_out = (T*)R.lmf[cur ^ 1];
+  a.D_out = (T*)R.Dd[cur ^ 1];
+  a.lamG = R.v_lamG[ver];
+  a.lamu = R.v_lamu[ver];
+  a.gpart = R.gpart;
+  return a;
+}
+
+}  // namespace
+
+extern "C" {
+
+mm_status mm_set_checkpointing(mm_handle* h, int K, int max_substeps) {
+  if (!h) return MM_ERR_INVALID;
+  DeviceGuard dg(h->device);
+  CK(cudaStreamSynchronize(h->stream));
+  free_recording(h);
+  if (K == 0) return MM_OK;
+  if (K < 0 || max_substeps < 1) return fail(h, MM_ERR_INVALID, "K >= 1 and max_substeps >= 1");
+  if (!h->have_state || !h->have_vel || !h->have_dt)
+    return fail(h, MM_ERR_STATE, "set the state and the velocity before recording");
+  Recording& R = h->rec;
+  R.K = K;
+  R.max_sub = max_substeps;
+  R.nck = (max_substeps + K - 1) / K + 1;
+  const size_t t = h->tsz, nc = (size_t)h->ncells, rows = h->rows;
+  const size_t state = h->mbn * t + 2 * rows * t + nc * t;
+  R.adj_grid = (int)std::min<long long>((h->ncells + 3) / 4, 8LL * h->sms);
+  const size_t need = (size_t)R.nck * state + (size_t)(K + 1) * (state + nc * t) + nc * t +
+                      h->mbn * t + 2 * rows * t + 4 * nc * t + (size_t)R.adj_grid * 4 * 4 * 8 +
+                      (3 * rows + nc) * 8 + rows * 8 + (1 << 20);
+  size_t freeb = 0, totalb = 0;
+  CK(cudaMemGetInfo(&freeb, &totalb));
+  if (need > freeb) {
+    free_recording(h);
+    char buf[160];
+    snprintf(buf, sizeof buf, "recording needs %zu bytes of device memory, %zu free", need, freeb);
+    return fail(h, MM_ERR_OOM, buf);
+  }
+  auto A = [&](void** p, size_t bytes) -> bool { return rec_alloc(h, p, bytes) == cudaSuccess; };
+  bool ok = true;
+  R.ck_mb.resize(R.nck);
+  R.ck_psi.resize(R.nck);
+  R.ck_nb.resize(R.nck);
+  R.ck_mf.resize(R.nck);
+  for (int i = 0; i < R.nck && ok; ++i)
+    ok = A(&R.ck_mb[i], h->mbn * t) && A(&R.ck_psi[i], rows * t) && A(&R.ck_nb[i], rows * t) &&
+         A(&R.ck_mf[i], nc * t);
+  ok = ok && A((void**)&R.ck_scale, (size_t)R.nck * 8);
+  R.sl_mb.resize(K + 1);
+  R.sl_psi.resize(K + 1);
+  R.sl_nb.resize(K + 1);
+  R.sl_mf.resize(K + 1);
+  R.sl_cpre.resize(K + 1);
+  for (int i = 0; i <= K && ok; ++i)
+    ok = A(&R.sl_mb[i], h->mbn * t) && A(&R.sl_psi[i], rows * t) && A(&R.sl_nb[i], rows * t) &&
+         A(&R.sl_mf[i], nc * t) && A(&R.sl_cpre[i], nc * t);
+  ok = ok && A(&R.sl_c, nc * t) && A(&R.lmb, h->mbn * t);
+  for (int i = 0; i < 2 && ok; ++i)
+    ok = A(&R.lpsi[i], rows * t) && A(&R.lmf[i], nc * t) && A(&R.Dd[i], nc * t);
+  ok = ok && A((void**)&R.gpart, (size_t)R.adj_grid * 4 * 4 * 8);
+  for (int i = 0; i < 3 && ok; ++i) ok = A((void**)&R.seed[i], rows * 8);
+  ok = ok && A((void**)&R.seed[3], nc * 8) && A((void**)&R.coef, 64) &&
+       A((void**)&R.work, std::max(rows, 2 * nc) * 8);
+  if (!ok) {
+    free_recording(h);
+    return fail(h, MM_ERR_OOM, "recording: cudaMalloc failed");
+  }
+  mm_status st;
+  if ((st = rec_push_version(h)) != MM_OK) return st;
+  return rec_save_checkpoint(h, 0);
+}
+
+mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_adjoint_out* out) {
+  if (!h || !seed || !out) return MM_ERR_INVALID;
+  Recording& R = h->rec;
+  if (R.K == 0) return fail(h, MM_ERR_STATE, "no recording: call mm_set_checkpointing first");
+  if (n != R.nsub || n < 1)
+    return fail(h, MM_ERR_STATE, "n_substeps must equal the substeps recorded");
+  if (out->dL_du && out->du_capacity < (int)R.v_ucell.size())
+    return fail(h, MM_ERR_INVALID, "dL_du holds fewer velocity fields than were recorded");
+  DeviceGuard dg(h->device);
+  mm_status st;
+  const size_t t = h->tsz, nc = (size_t)h->ncells, rows = h->rows;
+  const double dth = 2.0 * kPi / h->g.ntheta, ds = h->g.L / h->g.ns;
+  const bool f64 = h->prec == MM_FP64;
+  // live scalars to restore afterwards, and the velocity dts
+  double live_scale = 1.0, live_dt = 0.0;
+  CK(cudaMemcpyAsync(&live_scale, &h->prm->psi_scale, 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(&live_dt, &h->prm->dt, 8, cudaMemcpyDeviceToHost, h->stream));
+  const int nv = (int)R.v_ucell.size();
+  std::vector<double> vdt(nv);
+  for (int v = 0; v < nv; ++v)
+    CK(cudaMemcpyAsync(&vdt[v], R.v_dt[v], 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+
+  // ---- seed at the final (live) state
+  int kind = seed->observable;
+  double coef[4] = {0, 0, 0, 0};
+  out->value = 0.0;
+  if (kind == MM_OBS_POLAR_ORDER || kind == MM_OBS_MEAN_STRESS) {
+    if ((st = run_moments(h)) != MM_OK) return st;
+    double sc[8], spsi = 0.0;
+    CK(cudaMemcpyAsync(sc, h->prm->scalars, sizeof sc, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(&spsi, &h->prm->sum_psi, 8, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (kind == MM_OBS_POLAR_ORDER) {
+      const double px = sc[6], py = sc[7], pn = std::sqrt(px * px + py * py);
+      const double Lv = pn / spsi;
+      out->value = Lv;
+      coef[0] = -Lv / spsi;
+      coef[1] = pn > 0 ? px / pn / spsi : 0.0;
+      coef[2] = pn > 0 ? py / pn / spsi : 0.0;
+    } else {
+      out->value = sc[5];
+      coef[0] = h->r.force_scale * h->r.ell * dth / (double)nc;
+    }
+  } else if (kind != MM_OBS_NONE) {
+    return fail(h, MM_ERR_INVALID, "unknown observable");
+  }
+  CK(cudaMemcpyAsync(R.coef, coef, sizeof coef, cudaMemcpyHostToDevice, h->stream));
+  const double* sp[4] = {nullptr, nullptr, nullptr, nullptr};
+  if (kind == MM_OBS_NONE) {
+    const double* src[4] = {seed->dL_dpsi, seed->dL_dnb, seed->dL_dm1, seed->dL_dmf};
+    for (int i = 0; i < 4; ++i) {
+      if (!src[i]) continue;
+      const size_t cnt = i < 3 ? rows : nc;
+      if (seed->on_device) {
+        sp[i] = src[i];
+      } else {
+        CK(cudaMemcpyAsync(R.seed[i], src[i], cnt * 8, cudaMemcpyHostToDevice, h->stream));
+        sp[i] = R.seed[i];
+      }
+    }
+  }
+  cudaError_t e;
+  if (f64)
+    e = mm::launch_adj_seed<double>(kind, R.coef, (const double*)h->psi[h->parity],
+                                    (const double*)h->mb, sp[0], sp[1], sp[2], sp[3],
+                                    (double*)R.lpsi[0], (double*)R.lmb, (double*)R.lmf[0],
+                                    (double*)R.Dd[0], h->ncells, h->g.ntheta, h->g.ns, ds, h->g.L,
+                                    (const double*)h->trig, h->stream);
+  else
+    e = mm::launch_adj_seed<float>(kind, R.coef, (const float*)h->psi[h->parity],
+                                   (const float*)h->mb, sp[0], sp[1], sp[2], sp[3],
+                                   (float*)R.lpsi[0], (float*)R.lmb, (float*)R.lmf[0],
+                                   (float*)R.Dd[0], h->ncells, h->g.ntheta, h->g.ns, ds, h->g.L,
+                                   (const float*)h->trig, h->stream);
+  CK(e);
+  for (int v = 0; v < nv; ++v) {
+    CK(cudaMemsetAsync(R.v_lamG[v], 0, 4 * nc * 8, h->stream));
+    CK(cudaMemsetAsync(R.v_lamu[v], 0, 2 * nc * 8, h->stream));
+  }
+  CK(cudaMemsetAsync(R.gpart, 0, (size_t)R.adj_grid * 4 * 4 * 8, h->stream));
+
+  // ---- segments, last first
+  int cur = 0;
+  const int nseg = (n + R.K - 1) / R.K;
+  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+    const int s0 = sgi * R.K, s1 = std::min(s0 + R.K, n);
+    CK(cudaMemcpyAsync(R.sl_mb[0], R.ck_mb[sgi], h->mbn * t, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(R.sl_psi[0], R.ck_psi[sgi], rows * t, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(R.sl_nb[0], R.ck_nb[sgi], rows * t, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(R.sl_mf[0], R.ck_mf[sgi], nc * t, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(&h->prm->psi_scale, R.ck_scale + sgi, 8, cudaMemcpyDeviceToDevice,
+                       h->stream));
+    for (int tt = s0; tt < s1; ++tt) {
+      const int i = tt - s0, ver = R.sub_vel[tt];
+      CK(cudaMemcpyAsync(&h->prm->dt, R.v_dt[ver], 8, cudaMemcpyDeviceToDevice, h->stream));
+      StepPtrs p{R.sl_psi[i], R.sl_nb[i], R.sl_mb[i], R.sl_mf[i], R.v_ucell[ver],
+                 R.sl_psi[i + 1], R.sl_nb[i + 1], R.sl_mb[i + 1], R.sl_mf[i + 1], R.sl_c,
+                 R.sl_cpre[i + 1]};
+      CK(launch_ptrs(h, p, h->stream));
+    }
+    for (int tt = s1 - 1; tt >= s0; --tt) {
+      const int i = tt - s0, ver = R.sub_vel[tt];
+      if (f64)
+        e = mm::launch_adjoint<double>(adj_args<double>(h, i, ver, vdt[ver], cur), adj_V(h),
+                                       R.adj_grid, h->stream);
+      else
+        e = mm::launch_adjoint<float>(adj_args<float>(h, i, ver, vdt[ver], cur), adj_V(h),
+                                      R.adj_grid, h->stream);
+      CK(e);
+      cur ^= 1;
+    }
+  }
+  // restore the live scalars
+  CK(cudaMemcpyAsync(&h->prm->psi_scale, &live_scale, 8, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(&h->prm->dt, &live_dt, 8, cudaMemcpyHostToDevice, h->stream));
+
+  // ---- outputs
+  out->n_velocities = nv;
+  if (out->dL_du && out->du_capacity < nv)
+    return fail(h, MM_ERR_INVALID, "dL_du holds fewer velocity fields than were recorded");
+  if (out->dL_du) {
+    for (int v = 0; v < nv; ++v) {
+      double* dst = out->on_device ? out->dL_du + (size_t)v * 2 * nc : R.work;
+      CK(mm::launch_adj_finish(R.v_lamG[v], R.v_lamu[v], dst, h->g.nx, h->g.ny, (double)h->g.nx,
+                               (double)h->g.ny, h->stream));
+      if (!out->on_device)
+        CK(cudaMemcpyAsync(out->dL_du + (size_t)v * 2 * nc, R.work, 2 * nc * 8,
+                           cudaMemcpyDeviceToHost, h->stream));
+    }
+  }
+  if (out->dL_dpsi0) {
+    double* dst = out->on_device ? out->dL_dpsi0 : R.work;
+    if (f64)
+      e = mm::launch_adj_psi0<double>((const double*)R.lpsi[cur], (const double*)R.lmf[cur],
+                                      (const double*)R.sl_nb[0], dth, (long long)rows,
+                                      h->g.ntheta, dst, h->stream);
+    else
+      e = mm::launch_adj_psi0<float>((const float*)R.lpsi[cur], (const float*)R.lmf[cur],
+                                     (const float*)R.sl_nb[0], dth, (long long)rows, h->g.ntheta,
+                                     dst, h->stream);
+    CK(e);
+    if (!out->on_device)
+      CK(cudaMemcpyAsync(out->dL_dpsi0, R.work, rows * 8, cudaMemcpyDeviceToHost, h->stream));
+  }
+  std::vector<double> gp((size_t)R.adj_grid * 4 * 4);
+  CK(cudaMemcpyAsync(gp.data(), R.gpart, gp.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+  if ((st = check_status(h)) != MM_OK) return st;
+  out->dL_drates[0] = out->dL_drates[1] = out->dL_drates[2] = 0.0;
+  for (size_t w = 0; w < gp.size() / 4; ++w)
+    for (int q = 0; q < 3; ++q) out->dL_drates[q] += gp[w * 4 + q];
+  return MM_OK;
+}
 
 }  // extern "C"

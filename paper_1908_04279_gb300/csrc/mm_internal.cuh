@@ -40,13 +40,16 @@ struct StepArgs {
   int nb_tma;         // 1: stage the psi / n_b neighbourhood by bulk copies
   long long ncells;
   double inv_dx, inv_dy, inv_dth, dth, ds, L;
-  T* mb;              // [cells][nth][ns]
+  const T* mb_in;     // [cells][nth][ns] Mb at step n (may equal mb_out: in place)
+  T* mb_out;          // Mb at step n+1
   const T* psi_in;    // [cells][nth]
   T* psi_out;
   const T* nb_in;     // [cells][nth] n_b = sum_j Mb ds (precision T)
   T* nb_out;
-  T* mf;              // [cells] free motors (Eq. 6), state precision
+  const T* mf_in;     // [cells] free motors (Eq. 6) at step n, state precision
+  T* mf_out;          // free motors at step n+1 (may equal mf_in)
   T* c;               // [cells] coarse bound motors (Eq. 5)
+  T* cpre_out;        // [cells] coarse density before the Alg. 2 scale-down, or NULL
   const T* mtot;      // [cells] total motors
   const T* ucell;     // [cells][12]: ux, uy, ux east, ux west, uy north, uy south,
                       //   Gxx, Gxy, Gyx, Gyy (central differences), 2 spare
@@ -54,6 +57,37 @@ struct StepArgs {
   double* partial;    // [warps in the grid] per-warp sum(psi)
   DevParams* prm;
   int mass_correct;   // 1: compute psi_scale = mass0 / mass after the substep
+};
+
+// Everything the adjoint of one substep touches (mm_adjoint.cu). State n is
+// the substep's input, state n+1 its output (both from the recomputed
+// segment); lam_* are the adjoint variables.
+template <typename T>
+struct AdjArgs {
+  int nx, ny, nth, ns, seg;
+  long long ncells;
+  double inv_dx, inv_dy, inv_dth, dth, ds, L, dt;
+  double v_walk, k_on, k_off, glide, v_sp;
+  const T* psi_n;   // [cells][nth]
+  const T* nb_n;    // [cells][nth]
+  const T* mb_n;    // [cells][nth][ns]
+  const T* mf_n;    // [cells]
+  const T* psi_np;  // psi at n+1
+  const T* nb_np;   // n_b at n+1 (after the scale-down)
+  const T* cpre_np; // coarse density before the scale-down at n+1
+  const T* mtot;    // [cells]
+  const T* ucell;   // [cells][12]
+  const T* trig;    // [4][nth]
+  const T* lpsi_in; // adjoint of psi at n+1
+  const T* lmf_in;  // adjoint of Mf at n+1
+  const T* D_in;    // [cells] sum over the cell of lam_Mb * Mb at n+1
+  T* lpsi_out;      // adjoint of psi at n
+  T* lmb;           // adjoint of Mb: n+1 in, n out (in place)
+  T* lmf_out;       // adjoint of Mf at n
+  T* D_out;         // sum lam_Mb * Mb at n
+  double* lamG;     // [cells][4] accumulated adjoint of the velocity gradient
+  double* lamu;     // [2][cells] accumulated direct adjoint of u
+  double* gpart;    // [warps][4] accumulated k_off, v_walk, k_on adjoints
 };
 
 // Kernel launchers (defined in mm_step.cu); V = values per lane.
@@ -85,6 +119,20 @@ cudaError_t launch_moments(const T* psi, const T* mb, const T* mf, const T* c,
                            const double* trig, long long ncells, int nth, int ns, int V, int seg,
                            double dth, double ds, double L, double dA, double* fields,
                            double* partial, int nblocks, DevParams* prm, cudaStream_t s);
+
+// Adjoint kernels (mm_adjoint.cu).
+template <typename T>
+cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_seed(int kind, const double* coef, const T* psi, const T* mb,
+                            const double* dpsi, const double* dnb, const double* dm1,
+                            const double* dmf, T* lpsi, T* lmb, T* lmf, T* D, long long ncells,
+                            int nth, int ns, double ds, double L, const T* trig, cudaStream_t s);
+cudaError_t launch_adj_finish(const double* lamG, const double* lamu, double* dLdu, int nx, int ny,
+                              double inv_dx, double inv_dy, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adj_psi0(const T* lpsi, const T* lmf, const T* nb, double dth, long long rows,
+                            int nth, double* out, cudaStream_t s);
 
 // Message returned by mm_last_error(NULL) on this thread.
 void set_thread_error(const char* msg);

@@ -28,94 +28,9 @@
 // wait runs out records MM_ERR_TIMEOUT in DevParams::status, waits (bounded)
 // for the copies it still has in flight and leaves.
 #include "mm_internal.cuh"
+#include "mm_walk.cuh"
 
 namespace mm {
-
-template <typename T, int V>
-struct alignas(sizeof(T) * V) Pack {
-  T v[V];
-};
-
-// Single min/max instructions (the operands are never NaN here).
-__device__ __forceinline__ float tmax(float a, float b) { return fmaxf(a, b); }
-__device__ __forceinline__ float tmin(float a, float b) { return fminf(a, b); }
-__device__ __forceinline__ double tmax(double a, double b) { return fmax(a, b); }
-__device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); }
-
-__device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
-
-// Donor-cell face flux: upwind state times face velocity, with an explicit fma
-// so that both cells sharing a face compute the same bits (exact telescoping).
-template <typename T>
-__device__ __forceinline__ T donor(T A, T pl, T pr) {
-  return fma_t(tmax(A, T(0)), pl, tmin(A, T(0)) * pr);
-}
-
-__device__ __forceinline__ float max3_t(float a, float b, float c) {
-  float r;
-  asm("max.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(b), "f"(c));
-  return r;
-}
-__device__ __forceinline__ double max3_t(double a, double b, double c) {
-  return fmax(fmax(a, b), c);
-}
-
-// Walking-flux differences of the V nodes a lane holds (the d_s term of
-// Eq. 4 divided by v/ds): D_v = F_{j-1} - F_j with F_j = M_j + sigma_j/2 the
-// flux / v through the right face of node j = lane*V + v, F_{-1} = 0 (nothing
-// walks on at the minus end) and F_{ns-1} = M_{ns-1} (donor-cell outflow at
-// the plus end). sigma_j is the Superbee slope
-// maxmod(minmod(2a, b), minmod(a, 2b)) of the backward and forward
-// differences a, b (ghost M_{-1} = 0), evaluated on magnitudes: with
-// s = sign(b), sigma/2 = s max(min(s a, |b|/2), min(s a/2, |b|), 0).
-// Neighbouring nodes of other lanes come by warp shuffles within the row's
-// `seg`-lane segment.
-template <typename T, int V>
-__device__ __forceinline__ void walk_dflux(const T (&M)[V], T (&D)[V], bool first, bool last,
-                                           int seg) {
-  T ml = __shfl_up_sync(0xffffffffu, M[V - 1], 1, seg);
-  const T mr = __shfl_down_sync(0xffffffffu, M[0], 1, seg);
-  if (first) ml = T(0);
-  T d[V + 1], hd[V + 1];  // d[i] = M_i - M_{i-1}, i = 0..V, with M_{-1} = ml, M_V = mr
-  d[0] = M[0] - ml;
-#pragma unroll
-  for (int v = 1; v < V; ++v) d[v] = M[v] - M[v - 1];
-  d[V] = mr - M[V - 1];
-#pragma unroll
-  for (int i = 0; i <= V; ++i) hd[i] = T(0.5) * d[i];
-  T F[V];
-#pragma unroll
-  for (int v = 0; v < V; ++v) {
-    T sgn = copysign(T(1), d[v + 1]);
-    if (v == V - 1 && last) sgn = T(0);  // plus end: F = M, no slope
-    const T A = d[v] * sgn, hA = hd[v] * sgn;
-    const T r = max3_t(tmin(A, fabs(hd[v + 1])), tmin(hA, fabs(d[v + 1])), T(0));
-    F[v] = fma_t(r, sgn, M[v]);
-  }
-  T fl = __shfl_up_sync(0xffffffffu, F[V - 1], 1, seg);
-  if (first) fl = T(0);
-  D[0] = fl - F[0];
-#pragma unroll
-  for (int v = 1; v < V; ++v) D[v] = F[v - 1] - F[v];
-}
-
-template <typename T>
-__device__ __forceinline__ T seg_sum(T x, int seg) {
-  for (int o = seg >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o, seg);
-  return x;
-}
-template <typename T>
-__device__ __forceinline__ T warp_sum_t(T x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
-__device__ __forceinline__ double warp_sum(double x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
 
 // ---------------------------------------------------------------- TMA / mbarrier
 
@@ -267,7 +182,7 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
   auto issue_next = [&]() {
     mbar_expect_tx(&bars[istage], chunk_bytes);
     bulk_g2s(stages + (size_t)istage * chunk_elems,
-             a.mb + ((size_t)icell * nth + (size_t)ipart * RC) * ns, chunk_bytes, &bars[istage]);
+             a.mb_in + ((size_t)icell * nth + (size_t)ipart * RC) * ns, chunk_bytes, &bars[istage]);
     ++issued;
     if (++ipart == CH) { ipart = 0; icell += W; }
     if (++istage == S) istage = 0;
@@ -307,7 +222,7 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
       cwc = iy * nx + xm;
       cn = yp * nx + ix;
       cs = ym * nx + ix;
-      const T mf_n = a.mf[cell];
+      const T mf_n = a.mf_in[cell];
       mtot = a.mtot[cell];
       // stage constants: c for the half step, e for the full step
       c3 = hdt * kon * mf_n;
@@ -330,7 +245,7 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
 
     // ---- motor rows of this chunk
     const size_t chunk_off = ((size_t)cell * nth + (size_t)part * RC) * ns;
-    const T* src_rows = TMA ? stages + (size_t)s * chunk_elems : a.mb + chunk_off;
+    const T* src_rows = TMA ? stages + (size_t)s * chunk_elems : a.mb_in + chunk_off;
     if (TMA) {
       const bool ok = __all_sync(0xffffffffu, wait_never ? mbar_wait(never, 0u, wait_limit)
                                                          : mbar_wait(&bars[s], par, wait_limit));
@@ -344,7 +259,7 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
         break;
       }
     }
-    T* dst = a.mb + chunk_off;
+    T* dst = a.mb_out + chunk_off;
 #pragma unroll kStepUnroll
     for (int p = 0; p < passes; ++p) {
       const int r = p * rpp + rslot;  // row within the chunk
@@ -452,7 +367,7 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
       // rare: rescale the rows of this cell just written (own writes, ordered
       // by the __syncwarp above)
       const T ft = f;
-      T* base = a.mb + cbase * ns;
+      T* base = a.mb_out + cbase * ns;
       for (int e = lane; e < nth * ns; e += 32) base[e] = __ldcg(base + e) * ft;
       for (int k = lane; k < nth; k += 32) a.nb_out[cbase + k] = s_nb[k] * ft;
     } else {
@@ -460,7 +375,8 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
     }
     if (lane == 0) {
       a.c[cell] = C;
-      a.mf[cell] = mtot - C;
+      a.mf_out[cell] = mtot - C;
+      if (a.cpre_out) a.cpre_out[cell] = Cpre;
     }
     __syncwarp();
   }

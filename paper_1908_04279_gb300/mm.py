@@ -51,6 +51,19 @@ class mm_moments_out(C.Structure):
                 ("scalars", C.c_double * 8)]
 
 
+class mm_adjoint_seed(C.Structure):
+    _fields_ = [("observable", C.c_int), ("dL_dpsi", C.c_void_p), ("dL_dnb", C.c_void_p),
+                ("dL_dm1", C.c_void_p), ("dL_dmf", C.c_void_p), ("on_device", C.c_int)]
+
+
+class mm_adjoint_out(C.Structure):
+    _fields_ = [("dL_du", C.c_void_p), ("du_capacity", C.c_int), ("dL_dpsi0", C.c_void_p),
+                ("on_device", C.c_int),
+                ("dL_drates", C.c_double * 3), ("value", C.c_double), ("n_velocities", C.c_int)]
+
+
+OBSERVABLES = {"none": 0, "polar_order": 1, "mean_stress": 2}
+
 # Every symbol include/mm.h declares, with its argument types.
 _P = C.c_void_p
 _H = C.c_void_p
@@ -66,6 +79,9 @@ PROTOTYPES = {
     "mm_set_dt": ([_H, C.c_double], C.c_int),
     "mm_micro_step": ([_H, C.c_int], C.c_int),
     "mm_moments": ([_H, C.POINTER(mm_moments_out)], C.c_int),
+    "mm_set_checkpointing": ([_H, C.c_int, C.c_int], C.c_int),
+    "mm_adjoint_step": ([_H, C.c_int, C.POINTER(mm_adjoint_seed), C.POINTER(mm_adjoint_out)],
+                        C.c_int),
     "mm_sync": ([_H], C.c_int),
     "mm_debug_set": ([_H, C.c_uint, C.c_uint], C.c_int),
     "mm_get_launch_info": ([_H, C.POINTER(C.c_int), C.c_int], C.c_int),
@@ -224,6 +240,38 @@ class Simulation:
 
     def sync(self):
         self._check(self.lib.mm_sync(self.h))
+
+    # ---- adjoint -------------------------------------------------------------
+    def set_checkpointing(self, K: int, max_substeps: int):
+        """Start an adjoint recording at the current state (K = 0 stops it)."""
+        self._check(self.lib.mm_set_checkpointing(self.h, int(K), int(max_substeps)))
+
+    def adjoint(self, n_substeps: int, observable: str = "none", dL_dpsi=None, dL_dnb=None,
+                dL_dm1=None, dL_dmf=None, n_velocities: int = 1, want_du: bool = True,
+                want_dpsi0: bool = True):
+        """Reverse sweep over the recorded substeps. Seeds are numpy float64
+        arrays (psi-shaped for dL_dpsi/dL_dnb/dL_dm1, [ny][nx] for dL_dmf) or
+        a built-in observable. Returns a dict: value, dL_drates (k_off, v_walk,
+        k_on), dL_du [n_velocities][2][ny][nx], dL_dpsi0."""
+        g = self.grid
+        seeds = [dL_dpsi, dL_dnb, dL_dm1, dL_dmf]
+        kept = [np.ascontiguousarray(a, dtype=np.float64) if isinstance(a, np.ndarray) else a
+                for a in seeds]
+        ptrs = [_ptr(a, "seed") for a in kept]
+        devs = {d for _, d in ptrs if d is not None}
+        if len(devs) > 1:
+            raise TypeError("seeds must all be host arrays or all device tensors")
+        sd = mm_adjoint_seed(OBSERVABLES[observable], *[p for p, _ in ptrs],
+                             devs.pop() if devs else 0)
+        du = np.empty((n_velocities, 2, g.ny, g.nx)) if want_du else None
+        dp = np.empty((g.ny, g.nx, g.ntheta)) if want_dpsi0 else None
+        out = mm_adjoint_out(du.ctypes.data if du is not None else None, n_velocities,
+                             dp.ctypes.data if dp is not None else None, 0)
+        self._check(self.lib.mm_adjoint_step(self.h, int(n_substeps), C.byref(sd), C.byref(out)))
+        if du is not None:
+            du = du[:out.n_velocities]
+        return dict(value=out.value, dL_drates=np.array(list(out.dL_drates)), dL_du=du,
+                    dL_dpsi0=dp, n_velocities=out.n_velocities)
 
     def debug_set(self, wait_limit: int, flags: int = 0):
         self._check(self.lib.mm_debug_set(self.h, int(wait_limit), int(flags)))

@@ -159,9 +159,11 @@ mm_status mm_moments(mm_handle* h, mm_moments_out* out);
  * total, with any number of mm_set_velocity calls in between) save the state
  * every K substeps; the memory for ceil(max_substeps / K) + 1 checkpoints and
  * for the K + 1 states of one recomputed segment is reserved here
- * (MM_ERR_OOM if it does not fit). K = 0 stops and frees the recording, and
- * so does mm_set_state. While recording, substeps run as individual launches
- * (no graph) so that checkpoints can be taken between them.
+ * (MM_ERR_OOM if it does not fit), in one device allocation that a later
+ * recording with the same K and max_substeps reuses. mm_set_state ends a
+ * recording and keeps that memory; K = 0 ends it and frees the memory
+ * (mm_destroy frees it too). While recording, substeps run as individual
+ * launches (no graph) so that checkpoints can be taken between them.
  *
  * mm_adjoint_step(h, n, seed, out) runs the reverse sweep over the n substeps
  * recorded since mm_set_checkpointing (n must equal that count): for each

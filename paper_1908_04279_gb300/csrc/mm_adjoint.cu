@@ -26,38 +26,18 @@ namespace mm {
 
 namespace {
 
-// Derivative coefficients of the Superbee slope sigma = ca a + cb b on the
-// branch taken by sigma = maxmod(minmod(2a, b), minmod(a, 2b)) with
-// minmod(x, y) = (|x| < |y| ? x : y) and maxmod(x, y) = (|x| > |y| ? x : y)
-// for same-signed arguments (zero otherwise).
-template <typename T>
-__device__ __forceinline__ void superbee_coef(T a, T b, T& ca, T& cb) {
-  const T A = fabs(a), B = fabs(b);
-  const bool same = a * b > T(0);
-  const bool x1a = T(2) * A < B;  // minmod(2a, b) takes 2a
-  const T ax1 = x1a ? T(2) * A : B;
-  const bool x2a = A < T(2) * B;  // minmod(a, 2b) takes a
-  const T ax2 = x2a ? A : T(2) * B;
-  const bool pick1 = ax1 > ax2;   // maxmod takes minmod(2a, b)
-  const T ca1 = x1a ? T(2) : T(0), cb1 = x1a ? T(0) : T(1);
-  const T ca2 = x2a ? T(1) : T(0), cb2 = x2a ? T(0) : T(2);
-  ca = same ? (pick1 ? ca1 : ca2) : T(0);
-  cb = same ? (pick1 ? cb1 : cb2) : T(0);
-}
-
 // z = (d walk-term / dM)^T y for the V nodes a lane holds, where the walk
 // term of R_j is (v/ds) (F_{j-1} - F_j) with F_j = M_j + sigma_j / 2
-// (F_{ns-1} = M_{ns-1}, F_{-1} = 0, ghost M_{-1} = 0). With
+// (F_{ns-1} = M_{ns-1}, F_{-1} = 0, ghost M_{-1} = 0) and
+// sigma_j / 2 = ga_j (M_j - M_{j-1}) + gb_j (M_{j+1} - M_j) on the branch the
+// forward took (walk_dflux with COEF). With
 // lam_F_j = (v/ds)(y_{j+1} - y_j) (lam_F_{ns-1} = -(v/ds) y_{ns-1}),
-// P_j = ca_j lam_F_j / 2 and Q_j = cb_j lam_F_j / 2:
+// P_j = ga_j lam_F_j and Q_j = gb_j lam_F_j:
 // z_j = lam_F_j + P_j - Q_j - P_{j+1} + Q_{j-1}.
 template <typename T, int V>
-__device__ __forceinline__ void walk_adj(const T (&M)[V], const T (&y)[V], T (&z)[V], bool first,
-                                         bool last, int seg, T cw) {
-  T ml = __shfl_up_sync(0xffffffffu, M[V - 1], 1, seg);
-  const T mr = __shfl_down_sync(0xffffffffu, M[0], 1, seg);
+__device__ __forceinline__ void walk_adj(const T (&ga)[V], const T (&gb)[V], const T (&y)[V],
+                                         T (&z)[V], bool first, bool last, int seg, T cw) {
   const T yr = __shfl_down_sync(0xffffffffu, y[0], 1, seg);
-  if (first) ml = T(0);
   T lF[V], P[V], Q[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) {
@@ -67,16 +47,8 @@ __device__ __forceinline__ void walk_adj(const T (&M)[V], const T (&y)[V], T (&z
   if (last) lF[V - 1] = -cw * y[V - 1];
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const T mm = v == 0 ? ml : M[v - 1];
-    const T mp = v == V - 1 ? mr : M[v + 1];
-    T ca, cb;
-    superbee_coef(M[v] - mm, mp - M[v], ca, cb);
-    if (v == V - 1 && last) {
-      ca = T(0);
-      cb = T(0);
-    }
-    P[v] = T(0.5) * ca * lF[v];
-    Q[v] = T(0.5) * cb * lF[v];
+    P[v] = ga[v] * lF[v];
+    Q[v] = gb[v] * lF[v];
   }
   T Pr = __shfl_down_sync(0xffffffffu, P[0], 1, seg);
   T Ql = __shfl_up_sync(0xffffffffu, Q[V - 1], 1, seg);
@@ -90,11 +62,22 @@ __device__ __forceinline__ void walk_adj(const T (&M)[V], const T (&y)[V], T (&z
   }
 }
 
+#ifndef MM_ADJ_V8_MIN_BLOCKS
+#define MM_ADJ_V8_MIN_BLOCKS 3
+#endif
+
+// Resident blocks the register budget is sized for: float32 rows of up to 4
+// values per lane fit 128 registers; 8 values per lane and float64 need more.
+template <typename T, int V>
+constexpr int adj_min_blocks() {
+  return sizeof(T) == 8 ? 1 : (V == 8 ? MM_ADJ_V8_MIN_BLOCKS : 4);
+}
+
 // Adjoint of one substep, one warp per cell (grid-stride over cells).
 // Per-warp shared memory: lam_psi_total and psi^n of the cell, and lam_n_b^n
 // of its rows (3 nth values).
 template <typename T, int V>
-__global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_adjoint(const AdjArgs<T> a) {
+__global__ void __launch_bounds__(128, adj_min_blocks<T, V>()) k_adjoint(const AdjArgs<T> a) {
   extern __shared__ __align__(16) unsigned char adj_smem[];
   const int nth = a.nth, ns = a.ns, seg = a.seg;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -200,9 +183,9 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_adjoint(const A
       lG3 += lw * (cp * sp);
     }
     {
-      const double dlux = warp_sum((double)lux), dluy = warp_sum((double)luy);
-      const double d0 = warp_sum((double)lG0), d1 = warp_sum((double)lG1);
-      const double d2 = warp_sum((double)lG2), d3 = warp_sum((double)lG3);
+      const double dlux = (double)warp_sum_t(lux), dluy = (double)warp_sum_t(luy);
+      const double d0 = (double)warp_sum_t(lG0), d1 = (double)warp_sum_t(lG1);
+      const double d2 = (double)warp_sum_t(lG2), d3 = (double)warp_sum_t(lG3);
       if (lane == 0) {
         a.lamu[cell] += dlux;
         a.lamu[nc + cell] += dluy;
@@ -220,34 +203,50 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_adjoint(const A
     const T lamC_c = lamC[0], f_c = fsc[0];
     T lmf_acc = T(0), D_acc = T(0);
     T gk = T(0), gv = T(0), gn = T(0);
+    // rows of the next group are loaded one iteration ahead
+    T Mq[V], Lq[V];
+    auto load_rows = [&](int r0) {
+      const int k = r0 + rslot;
+      const bool act = k < nth && lane_ok;
+      if (act) {
+        const size_t off = ((size_t)cell * nth + k) * ns + (size_t)sl * V;
+        const Pack<T, V> qm = *reinterpret_cast<const Pack<T, V>*>(a.mb_n + off);
+        const Pack<T, V> ql = *reinterpret_cast<const Pack<T, V>*>(a.lmb + off);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          Mq[v] = qm.v[v];
+          Lq[v] = ql.v[v];
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          Mq[v] = T(0);
+          Lq[v] = T(0);
+        }
+      }
+    };
+    load_rows(0);
     for (int r0 = 0; r0 < nth; r0 += rpp) {
       const int k = r0 + rslot;
       const bool row_ok = k < nth, act = row_ok && lane_ok;
       const size_t off = ((size_t)cell * nth + (row_ok ? k : 0)) * ns + (size_t)sl * V;
       T M[V], L[V];
-      if (act) {
-        const Pack<T, V> qm = *reinterpret_cast<const Pack<T, V>*>(a.mb_n + off);
-        const Pack<T, V> ql = *reinterpret_cast<const Pack<T, V>*>(a.lmb + off);
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          M[v] = qm.v[v];
-          L[v] = ql.v[v];
-        }
-      } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) {
-          M[v] = T(0);
-          L[v] = T(0);
-        }
+      for (int v = 0; v < V; ++v) {
+        M[v] = Mq[v];
+        L[v] = Lq[v];
       }
-      // forward recompute: Ms = M + (dt/2) R(M)
-      T Dn[V], Ds[V], Ms[V];
-      walk_dflux<T, V>(M, Dn, first, last, seg);
+      const T psi1 = row_ok ? a.psi_np[(size_t)cell * nth + k] : T(0);
+      const T lnb = row_ok ? s_lnb[k] * ds : T(0);
+      if (r0 + rpp < nth) load_rows(r0 + rpp);
+      // forward recompute: Ms = M + (dt/2) R(M), with the Superbee branch of
+      // both stages
+      T Dn[V], Ds[V], Ms[V], gan[V], gbn[V], gas[V], gbs[V];
+      walk_dflux<T, V, true>(M, Dn, first, last, seg, gan, gbn);
 #pragma unroll
       for (int v = 0; v < V; ++v) Ms[v] = fma_t(c1, Dn[v], fma_t(c2, M[v], c3));
-      walk_dflux<T, V>(Ms, Ds, first, last, seg);
+      walk_dflux<T, V, true>(Ms, Ds, first, last, seg, gas, gbs);
       // lam_Mb** = f lam_Mb' + lam_C psi^{n+1} dtheta ds (through C and the scale-down)
-      const T psi1 = row_ok ? a.psi_np[(size_t)cell * nth + k] : T(0);
       const T add = act ? lamC_c * psi1 * dth * ds : T(0);
       T y1[V], zs[V], y2[V], zn[V];
       T sy1 = T(0), sy2 = T(0);
@@ -257,7 +256,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_adjoint(const A
         y1[v] = dt * L[v];
         sy1 += y1[v];
       }
-      walk_adj<T, V>(Ms, y1, zs, first, last, seg, cw);
+      walk_adj<T, V>(gas, gbs, y1, zs, first, last, seg, cw);
 #pragma unroll
       for (int v = 0; v < V; ++v) {
         zs[v] -= koff * y1[v];  // lam_Ms = J_R(Ms)^T y1
@@ -266,8 +265,7 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? 4 : 1) k_adjoint(const A
         y2[v] = hdt * zs[v];
         sy2 += y2[v];
       }
-      walk_adj<T, V>(M, y2, zn, first, last, seg, cw);
-      const T lnb = row_ok ? s_lnb[k] * ds : T(0);
+      walk_adj<T, V>(gan, gbn, y2, zn, first, last, seg, cw);
       Pack<T, V> qo;
 #pragma unroll
       for (int v = 0; v < V; ++v) {
@@ -392,19 +390,20 @@ template <typename T>
 cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid, cudaStream_t s) {
   const int block = 128;
   const size_t smem = (size_t)4 * 3 * a.nth * sizeof(T);
-  if (smem > 48 * 1024) {
-    const void* fn = V == 4 ? (const void*)k_adjoint<T, 4>
-                   : V == 2 ? (const void*)k_adjoint<T, 2> : (const void*)k_adjoint<T, 1>;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  if (V == 4)
-    k_adjoint<T, 4><<<grid, block, smem, s>>>(a);
-  else if (V == 2)
-    k_adjoint<T, 2><<<grid, block, smem, s>>>(a);
-  else
-    k_adjoint<T, 1><<<grid, block, smem, s>>>(a);
-  return cudaGetLastError();
+  auto go = [&](auto kern) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      cudaError_t e =
+          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<grid, block, smem, s>>>(a);
+    return cudaGetLastError();
+  };
+  if constexpr (sizeof(T) == 4)
+    if (V == 8) return go(k_adjoint<T, 8>);
+  if (V == 4) return go(k_adjoint<T, 4>);
+  if (V == 2) return go(k_adjoint<T, 2>);
+  return go(k_adjoint<T, 1>);
 }
 
 template <typename T>

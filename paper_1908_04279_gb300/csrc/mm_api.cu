@@ -18,6 +18,10 @@ using mm::StepArgs;
 #ifndef MM_FP32_VMAX
 #define MM_FP32_VMAX 8
 #endif
+// Widest vector of the float32 adjoint kernel.
+#ifndef MM_ADJ_FP32_VMAX
+#define MM_ADJ_FP32_VMAX 4
+#endif
 
 namespace {
 thread_local std::string g_create_error;
@@ -28,9 +32,16 @@ constexpr size_t kStagingDoubles = size_t(1) << 22;  // 32 MiB of float64 stagin
 void mm::set_thread_error(const char* msg) { g_create_error = msg; }
 
 // State of an adjoint recording (mm_set_checkpointing / mm_adjoint_step).
+// The checkpoints, the recomputed segment and the reverse-sweep buffers live
+// in one device allocation (`slab`), kept after the recording ends so that a
+// new recording with the same K and max_substeps reuses it; the per-velocity
+// blocks are pooled the same way.
 struct Recording {
+  bool active = false;
   int K = 0, max_sub = 0, nsub = 0, nck = 0;
-  std::vector<void*> bufs;  // every device allocation of the recording
+  void* slab = nullptr;
+  size_t slab_bytes = 0;
+  std::vector<void*> vblocks;  // velocity blocks, reused across recordings
   std::vector<void*> ck_mb, ck_psi, ck_nb, ck_mf;  // checkpoints (states 0, K, 2K, ...)
   double* ck_scale = nullptr;                      // psi mass-correction factor per checkpoint
   std::vector<void*> sl_mb, sl_psi, sl_nb, sl_mf, sl_cpre;  // K + 1 recomputed states
@@ -138,8 +149,8 @@ mm_status check_rates(const mm_rates* r, mm_handle* h) {
 }
 
 void free_recording(mm_handle* h) {
-  for (void* p : h->rec.bufs)
-    if (p) cudaFree(p);
+  if (h->rec.slab) cudaFree(h->rec.slab);
+  for (void* p : h->rec.vblocks) cudaFree(p);
   h->rec = Recording();
 }
 
@@ -624,10 +635,7 @@ mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const 
   if (!psi) return fail(h, MM_ERR_INVALID, "psi is NULL");
   DeviceGuard dg(h->device);
   mm_status st;
-  if (h->rec.K > 0) {  // a new state ends an adjoint recording
-    CK(cudaStreamSynchronize(h->stream));
-    free_recording(h);
-  }
+  h->rec.active = false;  // a new state ends an adjoint recording (its memory is kept)
   h->parity = 0;
   if ((st = put_array(h, h->psi[0], psi, h->rows, on_device)) != MM_OK) return st;
   if (mb) {
@@ -706,7 +714,7 @@ mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
   CK(mm::launch_dt_finalize(h->prm, h->g.L / h->g.ns, h->g.L, h->r.cfl, h->stream));
   h->have_vel = true;
   h->have_dt = true;
-  if (h->rec.K > 0) return rec_push_version(h);
+  if (h->rec.active) return rec_push_version(h);
   return MM_OK;
 }
 
@@ -729,7 +737,7 @@ mm_status mm_set_dt(mm_handle* h, double dt) {
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(&h->prm->dt, &h->dt, 8, cudaMemcpyHostToDevice));
   h->have_dt = true;
-  if (h->rec.K > 0) return rec_push_version(h);
+  if (h->rec.active) return rec_push_version(h);
   return MM_OK;
 }
 
@@ -741,7 +749,7 @@ mm_status mm_micro_step(mm_handle* h, int n) {
   if (!h->have_vel) return fail(h, MM_ERR_STATE, "no velocity: call mm_set_velocity first");
   if (!h->have_dt) return fail(h, MM_ERR_STATE, "no dt");
   DeviceGuard dg(h->device);
-  if (h->rec.K > 0) return rec_micro_step(h, n);
+  if (h->rec.active) return rec_micro_step(h, n);
   if (!h->use_graphs) {
     for (int i = 0; i < n; ++i) {
       CK(launch_one(h, h->parity, h->stream));
@@ -827,10 +835,27 @@ const char* mm_build_info(void) { return "libmm sm_103a (tcgen05-free streaming 
 
 namespace {
 
-cudaError_t rec_alloc(mm_handle* h, void** p, size_t bytes) {
-  cudaError_t e = cudaMalloc(p, bytes);
-  if (e == cudaSuccess) h->rec.bufs.push_back(*p);
-  return e;
+// Sub-buffers of one allocation at 256-byte alignment: a first pass with a
+// null base only adds up the size.
+struct Carver {
+  unsigned char* base = nullptr;
+  size_t off = 0;
+  void* take(size_t bytes) {
+    void* p = base ? base + off : nullptr;
+    off += (bytes + 255) & ~(size_t)255;
+    return p;
+  }
+};
+
+// Velocity block: per-cell velocity data, dt, and the adjoint accumulators.
+size_t vblock_bytes(const mm_handle* h) {
+  Carver c;
+  const size_t nc = (size_t)h->ncells;
+  c.take(12 * nc * h->tsz);
+  c.take(8);
+  c.take(4 * nc * 8);
+  c.take(2 * nc * 8);
+  return c.off;
 }
 
 // Copy the live state into checkpoint i.
@@ -851,19 +876,23 @@ mm_status rec_save_checkpoint(mm_handle* h, int i) {
 mm_status rec_push_version(mm_handle* h) {
   Recording& R = h->rec;
   const size_t nc = (size_t)h->ncells;
-  void *uc = nullptr, *dt = nullptr, *lg = nullptr, *lu = nullptr;
-  cudaError_t e;
-  if ((e = rec_alloc(h, &uc, 12 * nc * h->tsz)) != cudaSuccess ||
-      (e = rec_alloc(h, &dt, 8)) != cudaSuccess ||
-      (e = rec_alloc(h, &lg, 4 * nc * 8)) != cudaSuccess ||
-      (e = rec_alloc(h, &lu, 2 * nc * 8)) != cudaSuccess)
-    return cuda_fail(h, "recording: velocity buffers", e);
+  const size_t ver = R.v_ucell.size();
+  if (ver == R.vblocks.size()) {
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, vblock_bytes(h));
+    if (e != cudaSuccess) return cuda_fail(h, "recording: velocity buffers", e);
+    R.vblocks.push_back(p);
+  }
+  Carver c;
+  c.base = (unsigned char*)R.vblocks[ver];
+  void* uc = c.take(12 * nc * h->tsz);
+  double* dt = (double*)c.take(8);
+  R.v_lamG.push_back((double*)c.take(4 * nc * 8));
+  R.v_lamu.push_back((double*)c.take(2 * nc * 8));
   CK(cudaMemcpyAsync(uc, h->ucell, 12 * nc * h->tsz, cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaMemcpyAsync(dt, &h->prm->dt, 8, cudaMemcpyDeviceToDevice, h->stream));
   R.v_ucell.push_back(uc);
-  R.v_dt.push_back((double*)dt);
-  R.v_lamG.push_back((double*)lg);
-  R.v_lamu.push_back((double*)lu);
+  R.v_dt.push_back(dt);
   return MM_OK;
 }
 
@@ -884,8 +913,8 @@ mm_status rec_micro_step(mm_handle* h, int n) {
   return MM_OK;
 }
 
-// The reverse kernel reads rows with at most 4 values per lane.
-int adj_V(const mm_handle* h) { return std::min(h->V, 4); }
+// The reverse kernel reads rows with at most MM_ADJ_FP32_VMAX values per lane.
+int adj_V(const mm_handle* h) { return std::min(h->V, MM_ADJ_FP32_VMAX); }
 int adj_seg(const mm_handle* h) {
   int sg = 1;
   while (sg < h->g.ns / adj_V(h)) sg <<= 1;
@@ -937,6 +966,49 @@ mm::AdjArgs<T> adj_args(mm_handle* h, int slot, int ver, double dt, int cur) {
   return a;
 }
 
+// Lay the recording's fixed buffers out in the slab (c.base may be null to
+// size it).
+void rec_layout(mm_handle* h, Carver& c) {
+  Recording& R = h->rec;
+  const size_t t = h->tsz, nc = (size_t)h->ncells, rows = h->rows;
+  const int K = R.K;
+  R.ck_mb.resize(R.nck);
+  R.ck_psi.resize(R.nck);
+  R.ck_nb.resize(R.nck);
+  R.ck_mf.resize(R.nck);
+  for (int i = 0; i < R.nck; ++i) {
+    R.ck_mb[i] = c.take(h->mbn * t);
+    R.ck_psi[i] = c.take(rows * t);
+    R.ck_nb[i] = c.take(rows * t);
+    R.ck_mf[i] = c.take(nc * t);
+  }
+  R.ck_scale = (double*)c.take((size_t)R.nck * 8);
+  R.sl_mb.resize(K + 1);
+  R.sl_psi.resize(K + 1);
+  R.sl_nb.resize(K + 1);
+  R.sl_mf.resize(K + 1);
+  R.sl_cpre.resize(K + 1);
+  for (int i = 0; i <= K; ++i) {
+    R.sl_mb[i] = c.take(h->mbn * t);
+    R.sl_psi[i] = c.take(rows * t);
+    R.sl_nb[i] = c.take(rows * t);
+    R.sl_mf[i] = c.take(nc * t);
+    R.sl_cpre[i] = c.take(nc * t);
+  }
+  R.sl_c = c.take(nc * t);
+  R.lmb = c.take(h->mbn * t);
+  for (int i = 0; i < 2; ++i) {
+    R.lpsi[i] = c.take(rows * t);
+    R.lmf[i] = c.take(nc * t);
+    R.Dd[i] = c.take(nc * t);
+  }
+  R.gpart = (double*)c.take((size_t)R.adj_grid * 4 * 4 * 8);
+  for (int i = 0; i < 3; ++i) R.seed[i] = (double*)c.take(rows * 8);
+  R.seed[3] = (double*)c.take(nc * 8);
+  R.coef = (double*)c.take(64);
+  R.work = (double*)c.take(std::max(rows, 2 * nc) * 8);
+}
+
 }  // namespace
 
 extern "C" {
@@ -945,67 +1017,63 @@ mm_status mm_set_checkpointing(mm_handle* h, int K, int max_substeps) {
   if (!h) return MM_ERR_INVALID;
   DeviceGuard dg(h->device);
   CK(cudaStreamSynchronize(h->stream));
-  free_recording(h);
-  if (K == 0) return MM_OK;
+  Recording& R = h->rec;
+  R.active = false;
+  if (K == 0) {
+    free_recording(h);
+    return MM_OK;
+  }
   if (K < 0 || max_substeps < 1) return fail(h, MM_ERR_INVALID, "K >= 1 and max_substeps >= 1");
   if (!h->have_state || !h->have_vel || !h->have_dt)
     return fail(h, MM_ERR_STATE, "set the state and the velocity before recording");
-  Recording& R = h->rec;
-  R.K = K;
-  R.max_sub = max_substeps;
-  R.nck = (max_substeps + K - 1) / K + 1;
-  const size_t t = h->tsz, nc = (size_t)h->ncells, rows = h->rows;
-  const size_t state = h->mbn * t + 2 * rows * t + nc * t;
-  R.adj_grid = (int)std::min<long long>((h->ncells + 3) / 4, 8LL * h->sms);
-  const size_t need = (size_t)R.nck * state + (size_t)(K + 1) * (state + nc * t) + nc * t +
-                      h->mbn * t + 2 * rows * t + 4 * nc * t + (size_t)R.adj_grid * 4 * 4 * 8 +
-                      (3 * rows + nc) * 8 + rows * 8 + (1 << 20);
-  size_t freeb = 0, totalb = 0;
-  CK(cudaMemGetInfo(&freeb, &totalb));
-  if (need > freeb) {
-    free_recording(h);
-    char buf[160];
-    snprintf(buf, sizeof buf, "recording needs %zu bytes of device memory, %zu free", need, freeb);
-    return fail(h, MM_ERR_OOM, buf);
+  if (!R.slab || R.K != K || R.max_sub != max_substeps) {
+    if (R.slab) cudaFree(R.slab);
+    R.slab = nullptr;
+    R.K = K;
+    R.max_sub = max_substeps;
+    R.nck = (max_substeps + K - 1) / K + 1;
+    R.adj_grid = (int)std::min<long long>((h->ncells + 3) / 4, 8LL * h->sms);
+    Carver sz;
+    rec_layout(h, sz);
+    size_t freeb = 0, totalb = 0;
+    CK(cudaMemGetInfo(&freeb, &totalb));
+    const size_t need = sz.off + 2 * vblock_bytes(h) + (1 << 20);
+    if (need > freeb) {
+      free_recording(h);
+      char buf[160];
+      snprintf(buf, sizeof buf, "recording needs %zu bytes of device memory, %zu free", need, freeb);
+      return fail(h, MM_ERR_OOM, buf);
+    }
+    cudaError_t e = cudaMalloc(&R.slab, sz.off);
+    if (e != cudaSuccess) {
+      R.slab = nullptr;
+      free_recording(h);
+      return cuda_fail(h, "recording: cudaMalloc", e);
+    }
+    R.slab_bytes = sz.off;
+    Carver c;
+    c.base = (unsigned char*)R.slab;
+    rec_layout(h, c);
   }
-  auto A = [&](void** p, size_t bytes) -> bool { return rec_alloc(h, p, bytes) == cudaSuccess; };
-  bool ok = true;
-  R.ck_mb.resize(R.nck);
-  R.ck_psi.resize(R.nck);
-  R.ck_nb.resize(R.nck);
-  R.ck_mf.resize(R.nck);
-  for (int i = 0; i < R.nck && ok; ++i)
-    ok = A(&R.ck_mb[i], h->mbn * t) && A(&R.ck_psi[i], rows * t) && A(&R.ck_nb[i], rows * t) &&
-         A(&R.ck_mf[i], nc * t);
-  ok = ok && A((void**)&R.ck_scale, (size_t)R.nck * 8);
-  R.sl_mb.resize(K + 1);
-  R.sl_psi.resize(K + 1);
-  R.sl_nb.resize(K + 1);
-  R.sl_mf.resize(K + 1);
-  R.sl_cpre.resize(K + 1);
-  for (int i = 0; i <= K && ok; ++i)
-    ok = A(&R.sl_mb[i], h->mbn * t) && A(&R.sl_psi[i], rows * t) && A(&R.sl_nb[i], rows * t) &&
-         A(&R.sl_mf[i], nc * t) && A(&R.sl_cpre[i], nc * t);
-  ok = ok && A(&R.sl_c, nc * t) && A(&R.lmb, h->mbn * t);
-  for (int i = 0; i < 2 && ok; ++i)
-    ok = A(&R.lpsi[i], rows * t) && A(&R.lmf[i], nc * t) && A(&R.Dd[i], nc * t);
-  ok = ok && A((void**)&R.gpart, (size_t)R.adj_grid * 4 * 4 * 8);
-  for (int i = 0; i < 3 && ok; ++i) ok = A((void**)&R.seed[i], rows * 8);
-  ok = ok && A((void**)&R.seed[3], nc * 8) && A((void**)&R.coef, 64) &&
-       A((void**)&R.work, std::max(rows, 2 * nc) * 8);
-  if (!ok) {
-    free_recording(h);
-    return fail(h, MM_ERR_OOM, "recording: cudaMalloc failed");
-  }
+  R.nsub = 0;
+  R.sub_vel.clear();
+  R.v_ucell.clear();
+  R.v_dt.clear();
+  R.v_lamG.clear();
+  R.v_lamu.clear();
+  R.active = true;
   mm_status st;
-  if ((st = rec_push_version(h)) != MM_OK) return st;
-  return rec_save_checkpoint(h, 0);
+  if ((st = rec_push_version(h)) != MM_OK || (st = rec_save_checkpoint(h, 0)) != MM_OK) {
+    R.active = false;
+    return st;
+  }
+  return MM_OK;
 }
 
 mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_adjoint_out* out) {
   if (!h || !seed || !out) return MM_ERR_INVALID;
   Recording& R = h->rec;
-  if (R.K == 0) return fail(h, MM_ERR_STATE, "no recording: call mm_set_checkpointing first");
+  if (!R.active) return fail(h, MM_ERR_STATE, "no recording: call mm_set_checkpointing first");
   if (n != R.nsub || n < 1)
     return fail(h, MM_ERR_STATE, "n_substeps must equal the substeps recorded");
   if (out->dL_du && out->du_capacity < (int)R.v_ucell.size())
@@ -1085,7 +1153,7 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
   CK(cudaMemsetAsync(R.gpart, 0, (size_t)R.adj_grid * 4 * 4 * 8, h->stream));
 
   // ---- segments, last first
-  int cur = 0;
+  int cur = 0, dt_ver = -1;
   const int nseg = (n + R.K - 1) / R.K;
   for (int sgi = nseg - 1; sgi >= 0; --sgi) {
     const int s0 = sgi * R.K, s1 = std::min(s0 + R.K, n);
@@ -1097,7 +1165,9 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
                        h->stream));
     for (int tt = s0; tt < s1; ++tt) {
       const int i = tt - s0, ver = R.sub_vel[tt];
-      CK(cudaMemcpyAsync(&h->prm->dt, R.v_dt[ver], 8, cudaMemcpyDeviceToDevice, h->stream));
+      if (ver != dt_ver)
+        CK(cudaMemcpyAsync(&h->prm->dt, R.v_dt[ver], 8, cudaMemcpyDeviceToDevice, h->stream));
+      dt_ver = ver;
       StepPtrs p{R.sl_psi[i], R.sl_nb[i], R.sl_mb[i], R.sl_mf[i], R.v_ucell[ver],
                  R.sl_psi[i + 1], R.sl_nb[i + 1], R.sl_mb[i + 1], R.sl_mf[i + 1], R.sl_c,
                  R.sl_cpre[i + 1]};

@@ -47,9 +47,16 @@ __device__ __forceinline__ double max3_t(double a, double b, double c) {
 // s = sign(b), sigma/2 = s max(min(s a, |b|/2), min(s a/2, |b|), 0).
 // Neighbouring nodes of other lanes come by warp shuffles within the row's
 // `seg`-lane segment.
-template <typename T, int V>
+//
+// With COEF, also the derivative of sigma_j/2 on the branch taken:
+// sigma/2 = ga a + gb b with (ga, gb) one of (1, 0) [2a], (0, 1/2) [b],
+// (1/2, 0) [a], (0, 1) [2b] or (0, 0). The comparisons follow the Superbee
+// definition with strict inequalities (minmod keeps the second argument and
+// maxmod the second on ties), so that the branch is the one the forward map
+// takes; the value of D is the same bits as without COEF.
+template <typename T, int V, bool COEF = false>
 __device__ __forceinline__ void walk_dflux(const T (&M)[V], T (&D)[V], bool first, bool last,
-                                           int seg) {
+                                           int seg, T* ga = nullptr, T* gb = nullptr) {
   T ml = __shfl_up_sync(0xffffffffu, M[V - 1], 1, seg);
   const T mr = __shfl_down_sync(0xffffffffu, M[0], 1, seg);
   if (first) ml = T(0);
@@ -66,8 +73,18 @@ __device__ __forceinline__ void walk_dflux(const T (&M)[V], T (&D)[V], bool firs
     T sgn = copysign(T(1), d[v + 1]);
     if (v == V - 1 && last) sgn = T(0);  // plus end: F = M, no slope
     const T A = d[v] * sgn, hA = hd[v] * sgn;
-    const T r = max3_t(tmin(A, fabs(hd[v + 1])), tmin(hA, fabs(d[v + 1])), T(0));
+    const T hB = fabs(hd[v + 1]), B = fabs(d[v + 1]);
+    const T t1 = tmin(A, hB), t2 = tmin(hA, B);
+    const T r = max3_t(t1, t2, T(0));
     F[v] = fma_t(r, sgn, M[v]);
+    if constexpr (COEF) {
+      const bool pos = r > T(0), p1 = t1 > t2;
+      const bool x1a = A < hB, x2a = hA < B;
+      const T a1 = x1a ? T(1) : T(0), b1 = x1a ? T(0) : T(0.5);
+      const T a2 = x2a ? T(0.5) : T(0), b2 = x2a ? T(0) : T(1);
+      ga[v] = pos ? (p1 ? a1 : a2) : T(0);
+      gb[v] = pos ? (p1 ? b1 : b2) : T(0);
+    }
   }
   T fl = __shfl_up_sync(0xffffffffu, F[V - 1], 1, seg);
   if (first) fl = T(0);

@@ -243,7 +243,9 @@ class Simulation:
 
     # ---- adjoint -------------------------------------------------------------
     def set_checkpointing(self, K: int, max_substeps: int):
-        """Start an adjoint recording at the current state (K = 0 stops it)."""
+        """Start an adjoint recording at the current state. K = 0 ends it and
+        frees its memory; set_state ends it and keeps the memory, which a new
+        recording with the same K and max_substeps reuses."""
         self._check(self.lib.mm_set_checkpointing(self.h, int(K), int(max_substeps)))
 
     def adjoint(self, n_substeps: int, observable: str = "none", dL_dpsi=None, dL_dnb=None,

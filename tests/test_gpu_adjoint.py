@@ -213,3 +213,33 @@ def test_fp32_adjoint_close_to_fp64(mmod):
     assert rel(r32["dL_du"], r64["dL_du"]) <= 1e-3
     assert rel(r32["dL_drates"], r64["dL_drates"]) <= 1e-3
     assert rel(r32["dL_dpsi0"], r64["dL_dpsi0"]) <= 1e-3
+
+
+def test_recording_reuse_is_repeatable(mmod):
+    """A second recording with the same K and max_substeps reuses the first
+    one's memory (set_state ends a recording and keeps it) and gives the same
+    gradients bit for bit; set_state without a new mm_set_checkpointing leaves
+    no recording to differentiate."""
+    g = Grid(16, 12, 8, 16, L=1.0)
+    r = Rates(k_on=1.3, k_off=0.7)
+    psi0 = psi_isotropic_perturbed(g, 11, amp=0.2)
+    u1 = random_divfree_flow(g, 12, 4, 0.3)
+    u2 = random_divfree_flow(g, 13, 4, 0.3)
+    outs = []
+    with mmod.Simulation(g, r, "fp32") as sim:
+        for _ in range(3):
+            sim.set_state(psi0)
+            sim.set_velocity(u1)
+            sim.set_checkpointing(3, 10)
+            sim.step(4)
+            sim.set_velocity(u2)
+            sim.step(5)
+            outs.append(sim.adjoint(9, observable="polar_order", n_velocities=2))
+        sim.set_state(psi0)
+        with pytest.raises(RuntimeError):
+            sim.adjoint(9, observable="polar_order", n_velocities=2)
+    for o in outs[1:]:
+        assert o["value"] == outs[0]["value"]
+        assert np.array_equal(o["dL_du"], outs[0]["dL_du"])
+        assert np.array_equal(o["dL_dpsi0"], outs[0]["dL_dpsi0"])
+        assert np.array_equal(o["dL_drates"], outs[0]["dL_drates"])

@@ -299,8 +299,10 @@ def run_ours(args):
 
     def adjoint_ratio(precision):
         """Adjoint workload (64x64 x 32 x 32, 100 substeps, checkpoint every
-        10): time of the recorded forward plus the reverse sweep over the time
-        of the plain forward (graph replay), CUDA events on the handle's stream."""
+        10): time of the recorded forward plus the reverse sweep (gradients of
+        the polar order w.r.t. k_off, v_walk, k_on and the velocity field,
+        copied to the host) over the time of the plain forward (graph
+        replay), CUDA events on the handle's stream."""
         wa = WORKLOADS["adjoint64"]
         ga, na = wa["grid"], wa["substeps"]
         pa = psi_isotropic_perturbed(ga, wa["seed"])
@@ -321,7 +323,7 @@ def run_ours(args):
             e0.record(stream)
             sim.set_checkpointing(10, na)
             sim.step(na)
-            sim.adjoint(na, observable="polar_order", n_velocities=1)
+            sim.adjoint(na, observable="polar_order", n_velocities=1, want_dpsi0=False)
             e1.record(stream)
             e1.synchronize()
             best_a = min(best_a, e0.elapsed_time(e1))

@@ -320,12 +320,11 @@ __global__ void k_adj_seed(int kind, const double* coef, const T* psi, const T* 
   const long long W = (long long)gridDim.x * (blockDim.x >> 5);
   for (long long cell = gw; cell < ncells; cell += W) {
     double dsum = 0.0;
-    for (int k = lane; k < nth; k += 32) {
+    // one row at a time, the s-nodes across the lanes
+    for (int k = 0; k < nth; ++k) {
       const size_t r = (size_t)cell * nth + k;
       const T* row = mb + r * ns;
       T* lrow = lmb + r * ns;
-      double m1 = 0.0;
-      for (int j = 0; j < ns; ++j) m1 += (-0.5 * L + (j + 0.5) * ds) * (double)row[j] * ds;
       double lp = 0.0, a_nb = 0.0, a_m1 = 0.0;
       if (kind == 0) {
         lp = dpsi ? dpsi[r] : 0.0;
@@ -334,15 +333,18 @@ __global__ void k_adj_seed(int kind, const double* coef, const T* psi, const T* 
       } else if (kind == 1) {
         lp = coef[0] + coef[1] * (double)trig[k] + coef[2] * (double)trig[nth + k];
       } else {
-        lp = coef[0] * m1;
+        double m1 = 0.0;
+        for (int j = lane; j < ns; j += 32)
+          m1 += (-0.5 * L + (j + 0.5) * ds) * (double)row[j] * ds;
+        lp = coef[0] * warp_sum(m1);
         a_m1 = coef[0] * (double)psi[r];
       }
-      lpsi[r] = (T)lp;
-      for (int j = 0; j < ns; ++j) {
+      if (lane == 0) lpsi[r] = (T)lp;
+      for (int j = lane; j < ns; j += 32) {
         const double sj = -0.5 * L + (j + 0.5) * ds;
-        const double lm = a_nb * ds + a_m1 * sj * ds;
-        lrow[j] = (T)lm;
-        dsum += (double)(T)lm * (double)row[j];
+        const T lm = (T)(a_nb * ds + a_m1 * sj * ds);
+        lrow[j] = lm;
+        if (lm != T(0)) dsum += (double)lm * (double)row[j];
       }
     }
     dsum = warp_sum(dsum);

@@ -250,11 +250,14 @@ class Simulation:
 
     def adjoint(self, n_substeps: int, observable: str = "none", dL_dpsi=None, dL_dnb=None,
                 dL_dm1=None, dL_dmf=None, n_velocities: int = 1, want_du: bool = True,
-                want_dpsi0: bool = True):
-        """Reverse sweep over the recorded substeps. Seeds are numpy float64
-        arrays (psi-shaped for dL_dpsi/dL_dnb/dL_dm1, [ny][nx] for dL_dmf) or
-        a built-in observable. Returns a dict: value, dL_drates (k_off, v_walk,
-        k_on), dL_du [n_velocities][2][ny][nx], dL_dpsi0."""
+                want_dpsi0: bool = True, out_du=None, out_dpsi0=None):
+        """Reverse sweep over the recorded substeps. Seeds are float64 arrays
+        (numpy, or CUDA tensors; psi-shaped for dL_dpsi/dL_dnb/dL_dm1, [ny][nx]
+        for dL_dmf) or a built-in observable. Returns a dict: value, dL_drates
+        (k_off, v_walk, k_on), dL_du [n_velocities][2][ny][nx], dL_dpsi0.
+        With out_du / out_dpsi0 (float64 CUDA tensors of those shapes) the
+        gradients are written there on the device instead of to new host
+        arrays."""
         g = self.grid
         seeds = [dL_dpsi, dL_dnb, dL_dm1, dL_dmf]
         kept = [np.ascontiguousarray(a, dtype=np.float64) if isinstance(a, np.ndarray) else a
@@ -265,6 +268,21 @@ class Simulation:
             raise TypeError("seeds must all be host arrays or all device tensors")
         sd = mm_adjoint_seed(OBSERVABLES[observable], *[p for p, _ in ptrs],
                              devs.pop() if devs else 0)
+        if out_du is not None or out_dpsi0 is not None:
+            pu, du_dev = _ptr(out_du, "out_du")
+            pp, dp_dev = _ptr(out_dpsi0, "out_dpsi0")
+            if {d for d in (du_dev, dp_dev) if d is not None} != {1}:
+                raise TypeError("out_du and out_dpsi0 must be CUDA tensors")
+            cap = out_du.shape[0] if out_du is not None else 0
+            if out_du is not None and tuple(out_du.shape) != (cap, 2, g.ny, g.nx):
+                raise ValueError("out_du must have shape [n][2][ny][nx]")
+            if out_dpsi0 is not None and tuple(out_dpsi0.shape) != (g.ny, g.nx, g.ntheta):
+                raise ValueError("out_dpsi0 must have shape [ny][nx][ntheta]")
+            out = mm_adjoint_out(pu, cap, pp, 1)
+            self._check(self.lib.mm_adjoint_step(self.h, int(n_substeps), C.byref(sd),
+                                                 C.byref(out)))
+            return dict(value=out.value, dL_drates=np.array(list(out.dL_drates)), dL_du=out_du,
+                        dL_dpsi0=out_dpsi0, n_velocities=out.n_velocities)
         du = np.empty((n_velocities, 2, g.ny, g.nx)) if want_du else None
         dp = np.empty((g.ny, g.nx, g.ntheta)) if want_dpsi0 else None
         out = mm_adjoint_out(du.ctypes.data if du is not None else None, n_velocities,

@@ -202,6 +202,51 @@ mm_status mm_set_checkpointing(mm_handle* h, int K, int max_substeps);
 mm_status mm_adjoint_step(mm_handle* h, int n_substeps, const mm_adjoint_seed* seed,
                           mm_adjoint_out* out);
 
+/* ---- Batched ensemble --------------------------------------------------------
+ *
+ * An ensemble of n independent instances (an instance as above: its own grid,
+ * rates, state, velocity and dt; e.g. a sweep of k_off or v_walk) advanced
+ * together: mm_micro_step on the batch handle runs each substep as ONE launch
+ * over all instances (a table of tiles, each a run of cells of one instance
+ * holding about the same number of motor values), and the n_substeps of one
+ * call as one captured CUDA graph. No counterpart in the paper, which runs one
+ * instance at a time.
+ *
+ * mm_create_batch(n, grids, rates, prec, stream, &batch): grids[i], rates[i]
+ * for instance i; every instance needs ns divisible by 4 (MM_FP32_MIXED) or 2
+ * (MM_FP64) (MM_ERR_UNSUPPORTED otherwise). mm_batch_member(batch, i, &m)
+ * returns instance i's handle, owned by the batch (mm_destroy on it fails;
+ * mm_destroy on the batch frees all): mm_set_state, mm_set_velocity,
+ * mm_set_dt, mm_get_state, mm_moments, mm_set_checkpointing and
+ * mm_adjoint_step go to the members (on the batch, they fail with
+ * MM_ERR_INVALID). A member recording an adjoint takes its checkpoints during
+ * the batched substeps; its reverse sweep (mm_adjoint_step on the member)
+ * replays with the single-instance kernel. mm_micro_step on a member advances
+ * that member alone. mm_set_stream and mm_debug_set on the batch apply to
+ * every member; mm_sync on the batch checks every member.
+ *
+ * mm_batch_autotune(batch, substeps, results, max_results, &n_results): times
+ * `substeps` batched substeps for each (tile_work, chunk_bytes) in
+ * {1024 .. 32768} x {2048, 4096, 8192} (motor values per tile, bytes per
+ * s-row chunk) from the current state, restores the state, and keeps the
+ * fastest; results (may be NULL) receives up to max_results timings. The
+ * choice is cached for the process: a later batch with the same member grids
+ * and precision starts with it.
+ *
+ * mm_get_launch_info on a batch: grid, block, shared memory, 1, ring stages,
+ * largest chunk (values), tiles, values per lane, tile_work, chunk_bytes,
+ * tuned (0/1). */
+typedef struct {
+  int tile_work;
+  int chunk_bytes;
+  double ms_per_substep;
+} mm_batch_tune;
+mm_status mm_create_batch(int n, const mm_grid* grids, const mm_rates* rates, mm_precision prec,
+                          void* stream, mm_handle** out);
+mm_status mm_batch_member(mm_handle* batch, int i, mm_handle** member);
+mm_status mm_batch_autotune(mm_handle* batch, int substeps, mm_batch_tune* results,
+                            int max_results, int* n_results);
+
 /* Wait for the handle's stream and report a failure recorded by a kernel
  * since the last check (MM_ERR_TIMEOUT: a bounded device-side wait gave up and
  * the state is no longer valid). mm_get_state and mm_moments check too. */

@@ -1,139 +1,13 @@
 // Host side of the C ABI (include/mm.h): handle life cycle, state transfer,
 // velocity and adaptive substep, the substep launch plan (captured CUDA
-// graphs), and the moments.
-#include <algorithm>
-#include <cmath>
-#include <cstdio>
-#include <cstring>
-#include <map>
-#include <string>
-#include <vector>
+// graphs), the moments, and the adjoint recording and reverse sweep.
+#include "mm_host.h"
 
-#include "mm_internal.cuh"
-
-using mm::DevParams;
-using mm::StepArgs;
-
-// Widest vector (values per lane) of the float32 substep kernel.
-#ifndef MM_FP32_VMAX
-#define MM_FP32_VMAX 8
-#endif
-// Widest vector of the float32 adjoint kernel.
-#ifndef MM_ADJ_FP32_VMAX
-#define MM_ADJ_FP32_VMAX 4
-#endif
-
-namespace {
-thread_local std::string g_create_error;
-const double kPi = 3.14159265358979323846264338327950288;
-constexpr size_t kStagingDoubles = size_t(1) << 22;  // 32 MiB of float64 staging
-}  // namespace
+using namespace mmh;
 
 void mm::set_thread_error(const char* msg) { g_create_error = msg; }
 
-// State of an adjoint recording (mm_set_checkpointing / mm_adjoint_step).
-// The checkpoints, the recomputed segment and the reverse-sweep buffers live
-// in one device allocation (`slab`), kept after the recording ends so that a
-// new recording with the same K and max_substeps reuses it; the per-velocity
-// blocks are pooled the same way.
-struct Recording {
-  bool active = false;
-  int K = 0, max_sub = 0, nsub = 0, nck = 0;
-  void* slab = nullptr;
-  size_t slab_bytes = 0;
-  std::vector<void*> vblocks;  // velocity blocks, reused across recordings
-  std::vector<void*> ck_mb, ck_psi, ck_nb, ck_mf;  // checkpoints (states 0, K, 2K, ...)
-  double* ck_scale = nullptr;                      // psi mass-correction factor per checkpoint
-  std::vector<void*> sl_mb, sl_psi, sl_nb, sl_mf, sl_cpre;  // K + 1 recomputed states
-  void* sl_c = nullptr;
-  // velocity fields (and dt) in effect, in prescription order
-  std::vector<void*> v_ucell;
-  std::vector<double*> v_dt, v_lamG, v_lamu;
-  std::vector<int> sub_vel;  // velocity index of every recorded substep
-  // reverse-sweep buffers
-  void* lpsi[2] = {nullptr, nullptr};
-  void* lmf[2] = {nullptr, nullptr};
-  void* Dd[2] = {nullptr, nullptr};
-  void* lmb = nullptr;
-  double* gpart = nullptr;
-  double* seed[4] = {nullptr, nullptr, nullptr, nullptr};
-  double* coef = nullptr;
-  double* work = nullptr;  // [rows] float64 scratch for dL/dpsi0
-  int adj_grid = 1;
-};
-
-struct mm_handle {
-  Recording rec;
-  mm_grid g{};
-  mm_rates r{};
-  mm_precision prec = MM_FP64;
-  cudaStream_t stream = nullptr;
-  cudaStream_t cap = nullptr;  // private stream used only for graph capture
-  int device = 0, sms = 0;
-  long long ncells = 0;
-  size_t rows = 0, mbn = 0, tsz = 8;
-  void* mb = nullptr;
-  void* psi[2] = {nullptr, nullptr};
-  void* nb[2] = {nullptr, nullptr};
-  void* mf = nullptr;    // free, coarse and total motors per cell, state precision
-  void* c = nullptr;
-  void* mtot = nullptr;
-  void* u = nullptr;
-  void* ucell = nullptr;
-  double* u64 = nullptr;
-  void* trig = nullptr;
-  double* trig64 = nullptr;
-  double* partial = nullptr;
-  double* fields = nullptr;
-  double* staging = nullptr;
-  DevParams* prm = nullptr;
-  int npartial = 0;
-  int parity = 0;
-  double dt = 0.0;
-  bool have_state = false, have_vel = false, have_dt = false;
-  // substep launch configuration
-  int V = 1, seg = 1, block = 128, grid_step = 1, grid_mom = 1;
-  int stages = 1, chunk_rows = 1, chunks_per_cell = 1;
-  bool tma = false;
-  size_t smem = 0;
-  std::map<long long, cudaGraphExec_t> graphs;
-  bool use_graphs = true;
-  std::string err;
-};
-
-namespace {
-
-struct DeviceGuard {
-  int prev = -1;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
-    else prev = -1;
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
-
-mm_status fail(mm_handle* h, mm_status st, const std::string& msg) {
-  if (h)
-    h->err = msg;
-  else
-    g_create_error = msg;
-  return st;
-}
-
-mm_status cuda_fail(mm_handle* h, const char* what, cudaError_t e) {
-  return fail(h, MM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
-                                  cudaGetErrorString(e) + ")");
-}
-
-#define CK(...)                                               \
-  do {                                                        \
-    cudaError_t e_ = (__VA_ARGS__);                           \
-    if (e_ != cudaSuccess) return cuda_fail(h, #__VA_ARGS__, e_); \
-  } while (0)
-
-bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+namespace mmh {
 
 mm_status check_rates(const mm_rates* r, mm_handle* h) {
   if (!r) return fail(h, MM_ERR_INVALID, "rates is NULL");
@@ -222,6 +96,9 @@ StepArgs<T> step_args(mm_handle* h, int parity) {
   return a;
 }
 
+template StepArgs<float> step_args<float>(mm_handle*, int);
+template StepArgs<double> step_args<double>(mm_handle*, int);
+
 cudaError_t launch_one(mm_handle* h, int parity, cudaStream_t s) {
   if (h->prec == MM_FP64) {
     StepArgs<double> a = step_args<double>(h, parity);
@@ -239,10 +116,6 @@ cudaError_t launch_one(mm_handle* h, int parity, cudaStream_t s) {
 // `stages` shared-memory stages per warp filled by bulk copies (TMA) when an
 // s-row is a whole number of 16-byte vectors; otherwise rows are read from
 // global memory directly.
-constexpr int kChunkBytes = 4096;
-constexpr int kWarpInflightBytes = 8192;
-constexpr int kMaxWarpsPerBlock = 4;
-constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory per block at most
 
 // One substep with explicit state buffers (recomputing a recorded segment).
 struct StepPtrs {
@@ -340,8 +213,12 @@ mm_status check_status(mm_handle* h) {
   CK(cudaMemcpyAsync(&st, &h->prm->status, sizeof st, cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (st) {
+    // clear the status, and the last-warp counters a warp that gave up early
+    // may have left part-way
     const int zero = 0;
+    const unsigned int zeros[2] = {0u, 0u};
     CK(cudaMemcpy(&h->prm->status, &zero, sizeof zero, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(&h->prm->counter, zeros, sizeof zeros, cudaMemcpyHostToDevice));
     if (st & 1)
       return fail(h, MM_ERR_TIMEOUT, "a bounded wait in the substep kernel gave up; the state is invalid");
     return fail(h, MM_ERR_NONFINITE, "the substep rule found no positive finite rate");
@@ -440,7 +317,7 @@ mm_status run_moments(mm_handle* h) {
 mm_status rec_push_version(mm_handle* h);
 mm_status rec_micro_step(mm_handle* h, int n);
 
-}  // namespace
+}  // namespace mmh
 
 extern "C" {
 
@@ -603,8 +480,10 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
 
 mm_status mm_destroy(mm_handle* h) {
   if (!h) return MM_ERR_INVALID;
+  if (h->owner) return fail(h, MM_ERR_INVALID, "a batch member: destroy its batch instead");
   DeviceGuard dg(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  batch_free(h);
   free_all(h);
   delete h;
   return MM_OK;
@@ -613,11 +492,14 @@ mm_status mm_destroy(mm_handle* h) {
 mm_status mm_set_stream(mm_handle* h, void* stream) {
   if (!h) return MM_ERR_INVALID;
   h->stream = (cudaStream_t)stream;
+  if (h->batch)
+    for (mm_handle* m : batch_members(h)) m->stream = (cudaStream_t)stream;
   return MM_OK;
 }
 
 mm_status mm_set_rates(mm_handle* h, const mm_rates* rates) {
   if (!h) return MM_ERR_INVALID;
+  if (h->batch) return not_for_batch(h);
   mm_status st = check_rates(rates, h);
   if (st != MM_OK) return st;
   DeviceGuard dg(h->device);
@@ -632,6 +514,7 @@ mm_status mm_set_rates(mm_handle* h, const mm_rates* rates) {
 mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const double* mtot,
                        int on_device) {
   if (!h) return MM_ERR_INVALID;
+  if (h->batch) return not_for_batch(h);
   if (!psi) return fail(h, MM_ERR_INVALID, "psi is NULL");
   DeviceGuard dg(h->device);
   mm_status st;
@@ -668,6 +551,7 @@ mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const 
 mm_status mm_get_state(mm_handle* h, double* psi, double* mb, double* mf, double* c,
                        int on_device) {
   if (!h) return MM_ERR_INVALID;
+  if (h->batch) return not_for_batch(h);
   DeviceGuard dg(h->device);
   mm_status st;
   const double* scale = h->prec == MM_FP32_MIXED ? &h->prm->psi_scale : nullptr;
@@ -681,6 +565,7 @@ mm_status mm_get_state(mm_handle* h, double* psi, double* mb, double* mf, double
 
 mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
   if (!h) return MM_ERR_INVALID;
+  if (h->batch) return not_for_batch(h);
   if (!u) return fail(h, MM_ERR_INVALID, "u is NULL");
   DeviceGuard dg(h->device);
   const size_t n = 2 * (size_t)h->ncells;
@@ -720,6 +605,7 @@ mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
 
 mm_status mm_get_dt(mm_handle* h, double* dt) {
   if (!h || !dt) return MM_ERR_INVALID;
+  if (h->batch) return not_for_batch(h);
   if (!h->have_dt) return fail(h, MM_ERR_STATE, "no dt yet: call mm_set_velocity or mm_set_dt");
   DeviceGuard dg(h->device);
   CK(cudaMemcpyAsync(&h->dt, &h->prm->dt, 8, cudaMemcpyDeviceToHost, h->stream));
@@ -731,6 +617,7 @@ mm_status mm_get_dt(mm_handle* h, double* dt) {
 
 mm_status mm_set_dt(mm_handle* h, double dt) {
   if (!h) return MM_ERR_INVALID;
+  if (h->batch) return not_for_batch(h);
   if (!finite_pos(dt)) return fail(h, MM_ERR_INVALID, "dt must be finite and > 0");
   DeviceGuard dg(h->device);
   h->dt = dt;
@@ -745,6 +632,7 @@ mm_status mm_micro_step(mm_handle* h, int n) {
   if (!h) return MM_ERR_INVALID;
   if (n < 0) return fail(h, MM_ERR_INVALID, "n_substeps < 0");
   if (n == 0) return MM_OK;
+  if (h->batch) return batch_micro_step(h, n);
   if (!h->have_state) return fail(h, MM_ERR_STATE, "no state: call mm_set_state first");
   if (!h->have_vel) return fail(h, MM_ERR_STATE, "no velocity: call mm_set_velocity first");
   if (!h->have_dt) return fail(h, MM_ERR_STATE, "no dt");
@@ -784,6 +672,7 @@ mm_status mm_micro_step(mm_handle* h, int n) {
 
 mm_status mm_moments(mm_handle* h, mm_moments_out* out) {
   if (!h || !out) return MM_ERR_INVALID;
+  if (h->batch) return not_for_batch(h);
   DeviceGuard dg(h->device);
   mm_status st;
   if ((st = run_moments(h)) != MM_OK) return st;
@@ -801,12 +690,23 @@ mm_status mm_moments(mm_handle* h, mm_moments_out* out) {
 
 mm_status mm_sync(mm_handle* h) {
   if (!h) return MM_ERR_INVALID;
+  if (h->batch) return batch_sync(h);
   DeviceGuard dg(h->device);
   return check_status(h);
 }
 
 mm_status mm_debug_set(mm_handle* h, unsigned int wait_limit, unsigned int flags) {
   if (!h) return MM_ERR_INVALID;
+  if (h->batch) {
+    for (mm_handle* m : batch_members(h)) {
+      const mm_status st = mm_debug_set(m, wait_limit, flags);
+      if (st != MM_OK) {
+        h->err = m->err;
+        return st;
+      }
+    }
+    return MM_OK;
+  }
   DeviceGuard dg(h->device);
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(&h->prm->wait_limit, &wait_limit, sizeof wait_limit, cudaMemcpyHostToDevice));
@@ -816,6 +716,7 @@ mm_status mm_debug_set(mm_handle* h, unsigned int wait_limit, unsigned int flags
 
 mm_status mm_get_launch_info(mm_handle* h, int* info, int n) {
   if (!h || !info || n < 1) return MM_ERR_INVALID;
+  if (h->batch) return batch_launch_info(h, info, n);
   const int v[10] = {h->grid_step, h->block, (int)h->smem, h->tma ? 1 : 0, h->stages,
                      h->chunk_rows, h->chunks_per_cell, h->V, h->seg, h->sms};
   for (int i = 0; i < n && i < 10; ++i) info[i] = v[i];
@@ -833,7 +734,7 @@ const char* mm_build_info(void) { return "libmm sm_103a (tcgen05-free streaming 
 // ---------------------------------------------------------------------------
 // Adjoint recording and reverse sweep
 
-namespace {
+namespace mmh {
 
 // Sub-buffers of one allocation at 256-byte alignment: a first pass with a
 // null base only adds up the size.
@@ -903,13 +804,23 @@ mm_status rec_micro_step(mm_handle* h, int n) {
     return fail(h, MM_ERR_STATE, "recording: more substeps than mm_set_checkpointing reserved");
   mm_status st;
   for (int i = 0; i < n; ++i) {
-    if (R.nsub > 0 && R.nsub % R.K == 0)
-      if ((st = rec_save_checkpoint(h, R.nsub / R.K)) != MM_OK) return st;
-    R.sub_vel.push_back((int)R.v_ucell.size() - 1);
+    if ((st = rec_push_substep(h)) != MM_OK) return st;
     CK(launch_one(h, h->parity, h->stream));
     h->parity ^= 1;
-    ++R.nsub;
   }
+  return MM_OK;
+}
+
+// Before a recorded substep: the checkpoint due at its start and its velocity.
+mm_status rec_push_substep(mm_handle* h) {
+  Recording& R = h->rec;
+  if (R.nsub >= R.max_sub)
+    return fail(h, MM_ERR_STATE, "recording: more substeps than mm_set_checkpointing reserved");
+  mm_status st;
+  if (R.nsub > 0 && R.nsub % R.K == 0)
+    if ((st = rec_save_checkpoint(h, R.nsub / R.K)) != MM_OK) return st;
+  R.sub_vel.push_back((int)R.v_ucell.size() - 1);
+  ++R.nsub;
   return MM_OK;
 }
 
@@ -1009,12 +920,13 @@ void rec_layout(mm_handle* h, Carver& c) {
   R.work = (double*)c.take(std::max(rows, 2 * nc) * 8);
 }
 
-}  // namespace
+}  // namespace mmh
 
 extern "C" {
 
 mm_status mm_set_checkpointing(mm_handle* h, int K, int max_substeps) {
   if (!h) return MM_ERR_INVALID;
+  if (h->batch) return not_for_batch(h);
   DeviceGuard dg(h->device);
   CK(cudaStreamSynchronize(h->stream));
   Recording& R = h->rec;
@@ -1072,6 +984,7 @@ mm_status mm_set_checkpointing(mm_handle* h, int K, int max_substeps) {
 
 mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_adjoint_out* out) {
   if (!h || !seed || !out) return MM_ERR_INVALID;
+  if (h->batch) return not_for_batch(h);
   Recording& R = h->rec;
   if (!R.active) return fail(h, MM_ERR_STATE, "no recording: call mm_set_checkpointing first");
   if (n != R.nsub || n < 1)

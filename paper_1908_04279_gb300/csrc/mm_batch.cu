@@ -1,0 +1,294 @@
+// Batched-ensemble substep: one persistent launch advances every instance of
+// an ensemble (each with its own grid, rates, dt and velocity) by one
+// substep.
+//
+// The work is a table of tiles, each a run of consecutive cells of one
+// instance sized to about the same number of motor values; warp gw of W takes
+// tiles gw, gw + W, ... and performs, cell by cell, exactly the fused substep
+// of the single-instance kernel (Eq. 4 by midpoint RK2 on the s-rows streamed
+// through the warp's bulk-copy ring, Eq. 1 for psi, Eq. 5, the scale-down of
+// Alg. 2 and Eq. 6), with the instance's arguments read from a device table.
+// The ring runs across tile boundaries: lane 0's producer cursor walks the
+// same tile sequence ahead of the consumer.
+//
+// The sum of psi^{n+1} is kept per tile (compensated, then float64); the warp
+// that completes the last tile of an instance adds that instance's tile sums
+// in tile order (deterministic for any schedule) and, in the float32 form,
+// stores the instance's mass-correction factor.
+#include "mm_cell.cuh"
+
+namespace mm {
+
+// float64 rows need more registers than the float32 occupancy target allows
+template <typename T>
+constexpr int batch_min_blocks() {
+  return sizeof(T) == 8 ? 3 : MM_STEP_MIN_BLOCKS;
+}
+
+template <typename T, int V, bool MASSCORR>
+__global__ void __launch_bounds__(128, batch_min_blocks<T>())
+    k_substep_batch(const StepArgs<T>* __restrict__ insts, const BatchTile* __restrict__ tiles,
+                    int ntiles, double* tile_mass, int S, int stage_elems, int nth_max) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const WarpSmem L = warp_smem_layout(S, stage_elems, nth_max, (int)sizeof(T));
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  unsigned char* wbase = smem_raw + (size_t)wib * L.total;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wbase + L.bars);
+  T* stages = reinterpret_cast<T*>(wbase + L.stages);
+  T* psi5 = reinterpret_cast<T*>(wbase + L.psi5);
+  T* nb5 = reinterpret_cast<T*>(wbase + L.nb5);
+  T* s_nb = reinterpret_cast<T*>(wbase + L.nbm);
+  uint64_t* nbar = bars + S;
+  uint64_t* never = bars + S + 1;
+
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  const int W = gridDim.x * (blockDim.x >> 5);
+  int nchunks = 0;
+  for (int t = gw; t < ntiles; t += W) nchunks += tiles[t].ncell * tiles[t].ch;
+
+  // producer cursor (lane 0): tile, cell within it, chunk within the cell
+  int ptile = gw, pcell = 0, ppart = 0, istage = 0, issued = 0;
+  BatchTile pt{};
+  const T* pmb = nullptr;
+  int pnth = 0, pns = 0;
+  auto producer_tile = [&]() {
+    pt = tiles[ptile];
+    pmb = insts[pt.inst].mb_in;
+    pnth = insts[pt.inst].nth;
+    pns = insts[pt.inst].ns;
+  };
+  auto issue_next = [&]() {
+    const uint32_t bytes = (uint32_t)(pt.rc * pns * sizeof(T));
+    mbar_expect_tx(&bars[istage], bytes);
+    bulk_g2s(stages + (size_t)istage * stage_elems,
+             pmb + ((size_t)(pt.cell0 + pcell) * pnth + (size_t)ppart * pt.rc) * pns, bytes,
+             &bars[istage]);
+    ++issued;
+    if (++ppart == pt.ch) {
+      ppart = 0;
+      if (++pcell == pt.ncell) {
+        pcell = 0;
+        ptile += W;
+        if (ptile < ntiles) producer_tile();
+      }
+    }
+    if (++istage == S) istage = 0;
+  };
+  if (lane == 0) {
+    for (int q = 0; q <= S + 1; ++q) mbar_init(&bars[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (ptile < ntiles) producer_tile();
+    while (issued < S && issued < nchunks) issue_next();
+  }
+  __syncwarp();
+
+  bool timed_out = false, nb_pending = false;
+  int fail_stage = 0, fail_left = 0;
+  uint32_t fail_par = 0;
+  int s = 0;
+  uint32_t par = 0;
+  uint32_t nb_par = 1;
+
+  // consumer: current tile and instance
+  int tix = gw - W, ccell = 0, part = 0;
+  BatchTile ct{};
+  ct.ncell = 0;
+  const StepArgs<T>* A = nullptr;
+  int nth = 1, ns = 1, seg = 1, nx = 1, ny = 1, RC = 1, CH = 1;
+  bool nb_tma = false;
+  uint32_t wait_limit = 0;
+  bool wait_never = false;
+  T hdt = 0, dt = 0, kon = 0, ds = 0;
+  PsiConst<T> pq{};
+  RkConst<T> rk{};
+  LaneGeom lg{};
+  T mass_hi = T(0), mass_lo = T(0);
+  int cell = 0, ce = 0, cwc = 0, cn = 0, cs = 0;
+  T mtot = 0;
+  CellVel<T> uv{};
+
+  // sum of the finished tile; the last tile of an instance finalises it
+  auto close_tile = [&]() {
+    const double m = warp_sum((double)mass_hi + (double)mass_lo);
+    mass_hi = T(0);
+    mass_lo = T(0);
+    unsigned int is_last = 0;
+    if (lane == 0) {
+      tile_mass[tix] = m;
+      __threadfence();
+      const unsigned int prev = atomicInc(&A->prm->counter, (unsigned int)ct.inst_tiles - 1);
+      is_last = prev == (unsigned int)ct.inst_tiles - 1;
+    }
+    is_last = __shfl_sync(0xffffffffu, is_last, 0);
+    if (is_last) {
+      __threadfence();
+      double acc = 0.0;
+      for (int b = lane; b < ct.inst_tiles; b += 32) acc += __ldcg(tile_mass + ct.tile0 + b);
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        A->prm->mass = acc;
+        if (MASSCORR && A->mass_correct) A->prm->psi_scale = A->prm->mass0 / acc;
+      }
+    }
+  };
+
+  for (int t = 0; t < nchunks; ++t) {
+    if (part == 0) {
+      if (ccell == ct.ncell) {
+        // next tile (and its instance's constants)
+        tix += W;
+        ct = tiles[tix];
+        ccell = 0;
+        A = insts + ct.inst;
+        nth = A->nth;
+        ns = A->ns;
+        seg = A->seg;
+        nx = A->nx;
+        ny = A->ny;
+        RC = ct.rc;
+        CH = ct.ch;
+        nb_tma = A->nb_tma != 0;
+        const DevParams* P = A->prm;
+        const double dt64 = P->dt;
+        dt = (T)dt64;
+        hdt = (T)(0.5 * dt64);
+        const T cw = (T)(P->v_walk / A->ds);
+        const T koff = (T)P->k_off;
+        kon = (T)P->k_on;
+        const T g = MASSCORR ? (T)P->psi_scale : T(1);
+        wait_limit = P->wait_limit;
+        wait_never = (P->debug_flags & 1u) != 0;
+        pq = PsiConst<T>{dt, g, (T)P->glide, (T)P->v_sp, (T)A->inv_dx, (T)A->inv_dy,
+                         (T)A->inv_dth, (T)A->dth, A->trig};
+        ds = (T)A->ds;
+        rk = RkConst<T>{hdt * cw, T(1) - hdt * koff, T(0), dt * cw, -dt * koff, T(0)};
+        lg = lane_geom(lane, seg, ns, V);
+      }
+      cell = ct.cell0 + ccell;
+      if (nb_tma) nb_par ^= 1u;  // members differ in whether they stage by bulk copy
+      const int iy = cell / nx, ix = cell - iy * nx;
+      const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
+      const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
+      ce = iy * nx + xp;
+      cwc = iy * nx + xm;
+      cn = yp * nx + ix;
+      cs = ym * nx + ix;
+      const T mf_n = A->mf_in[cell];
+      mtot = A->mtot[cell];
+      rk.c3 = hdt * kon * mf_n;
+      rk.e3 = dt * kon * mf_n;
+      uv = load_cell_vel(A->ucell, cell);
+      if (nb_tma && lane == 0) {
+        const uint32_t pb = (uint32_t)(nth * sizeof(T));
+        mbar_expect_tx(nbar, 10 * pb);
+        const int src_cells[5] = {cell, ce, cwc, cn, cs};
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          bulk_g2s(psi5 + q * nth, A->psi_in + (size_t)src_cells[q] * nth, pb, nbar);
+          bulk_g2s(nb5 + q * nth, A->nb_in + (size_t)src_cells[q] * nth, pb, nbar);
+        }
+      }
+    }
+
+    // ---- motor rows of this chunk
+    const size_t chunk_off = ((size_t)cell * nth + (size_t)part * RC) * ns;
+    {
+      const bool ok = __all_sync(0xffffffffu, wait_never ? mbar_wait(never, 0u, wait_limit)
+                                                         : mbar_wait(&bars[s], par, wait_limit));
+      if (!ok) {
+        timed_out = true;
+        fail_stage = s;
+        fail_par = par;
+        fail_left = issued - t;
+        nb_pending = nb_tma;
+        break;
+      }
+    }
+    rows_chunk<T, V>(stages + (size_t)s * stage_elems, A->mb_out + chunk_off, RC, ns, seg, lg, rk,
+                     ds, s_nb + part * RC);
+    __syncwarp();
+    if (lane == 0 && issued < nchunks) issue_next();
+    if (++s == S) { s = 0; par ^= 1u; }
+    if (++part != CH) continue;
+    part = 0;
+
+    // ---- end of the cell
+    if (nb_tma) {
+      const bool ok = __all_sync(0xffffffffu, wait_never ? mbar_wait(never, 0u, wait_limit)
+                                                         : mbar_wait(nbar, nb_par, wait_limit));
+      if (!ok) {
+        timed_out = true;
+        fail_stage = s;
+        fail_par = par;
+        fail_left = issued - (t + 1);
+        nb_pending = true;
+        break;
+      }
+    } else {
+      const int src_cells[5] = {cell, ce, cwc, cn, cs};
+      for (int q = 0; q < 5; ++q)
+        for (int k = lane; k < nth; k += 32) {
+          psi5[q * nth + k] = A->psi_in[(size_t)src_cells[q] * nth + k];
+          nb5[q * nth + k] = A->nb_in[(size_t)src_cells[q] * nth + k];
+        }
+      __syncwarp();
+    }
+    T acc = T(0), cell_mass = T(0);
+    psi_cell(pq, uv, psi5, nb5, s_nb, nth, lane, A->psi_out + (size_t)cell * nth, cell_mass, acc);
+    two_sum_acc(mass_hi, mass_lo, cell_mass);
+    cell_motor_close(acc, mtot, s_nb, nth, ns, lane, cell, A->mb_out, A->nb_out, A->c, A->mf_out,
+                     A->cpre_out);
+    __syncwarp();
+    if (++ccell == ct.ncell) close_tile();
+  }
+
+  if (timed_out) {
+    if (lane == 0) {
+      atomicOr(&A->prm->status, 1);
+      int st = fail_stage;
+      uint32_t pp = fail_par;
+      for (int i = 0; i < fail_left; ++i) {
+        (void)mbar_wait(&bars[st], pp, kDrainLimit);
+        if (++st == S) { st = 0; pp ^= 1u; }
+      }
+      if (nb_pending) (void)mbar_wait(nbar, nb_par, kDrainLimit);
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, int V>
+cudaError_t launch_substep_batch(const StepArgs<T>* insts, const BatchTile* tiles, int ntiles,
+                                 double* tile_mass, int S, int stage_elems, int nth_max,
+                                 bool masscorr, int grid, int block, size_t smem, cudaStream_t s) {
+  if (masscorr)
+    k_substep_batch<T, V, true><<<grid, block, smem, s>>>(insts, tiles, ntiles, tile_mass, S,
+                                                          stage_elems, nth_max);
+  else
+    k_substep_batch<T, V, false><<<grid, block, smem, s>>>(insts, tiles, ntiles, tile_mass, S,
+                                                           stage_elems, nth_max);
+  return cudaGetLastError();
+}
+
+template <typename T, int V>
+cudaError_t substep_batch_prepare(int block, size_t smem, int* blocks_per_sm) {
+  const void* fns[2] = {(const void*)k_substep_batch<T, V, true>,
+                        (const void*)k_substep_batch<T, V, false>};
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_substep_batch<T, V, true>,
+                                                       block, smem);
+}
+
+#define MM_BATCH_INST(T, V)                                                                    \
+  template cudaError_t launch_substep_batch<T, V>(const StepArgs<T>*, const BatchTile*, int,   \
+                                                  double*, int, int, int, bool, int, int,      \
+                                                  size_t, cudaStream_t);                       \
+  template cudaError_t substep_batch_prepare<T, V>(int, size_t, int*);
+MM_BATCH_INST(float, 8)
+MM_BATCH_INST(float, 4)
+MM_BATCH_INST(double, 2)
+
+}  // namespace mm

@@ -1,0 +1,275 @@
+// Device pieces of the fused substep shared by the single-instance kernel
+// (mm_step.cu) and the batched-ensemble kernel (mm_batch.cu): the bulk-copy
+// and mbarrier primitives, the per-warp shared-memory plan, one chunk of
+// s-rows by Eq. 4 (midpoint RK2 of Alg. 2) and the end-of-cell update of psi
+// by Eq. 1 with the coarse density of Eq. 5.
+#pragma once
+
+#include "mm_internal.cuh"
+#include "mm_walk.cuh"
+
+namespace mm {
+
+// ---------------------------------------------------------------- TMA / mbarrier
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait for the phase with the given parity; false if it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
+  for (uint32_t i = 0;; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i >= limit) return false;
+  }
+}
+// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
+// global to this CTA's shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+constexpr uint32_t kDrainLimit = 1u << 24;  // polls while draining after a timeout
+
+// Occupancy target (resident 4-warp blocks per SM, caps registers per thread)
+// and unroll depth of the s-row pass loop.
+#ifndef MM_STEP_MIN_BLOCKS
+#define MM_STEP_MIN_BLOCKS 4
+#endif
+#ifndef MM_STEP_UNROLL
+#define MM_STEP_UNROLL 2
+#endif
+constexpr int kStepUnroll = MM_STEP_UNROLL;
+
+// ------------------------------------------------------------------- layout
+
+// Per-warp shared memory: S + 2 mbarriers (S ring stages, 1 neighbourhood, 1
+// that never completes, waited on by the timeout test knob), S stages of
+// chunk_elems values, the psi and n_b columns of the cell and its east, west,
+// north and south neighbours (2 x 5 nth values), and n_b of the cell's new
+// rows (nth values), all in the state precision.
+struct WarpSmem {
+  size_t bars, stages, psi5, nb5, nbm, total;
+};
+__host__ __device__ inline WarpSmem warp_smem_layout(int S, int chunk_elems, int nth, int tsz) {
+  WarpSmem w;
+  w.bars = 0;
+  size_t off = 8 * (size_t)(S + 2);
+  off = (off + 127) & ~(size_t)127;
+  w.stages = off;
+  off += (size_t)S * chunk_elems * tsz;
+  off = (off + 15) & ~(size_t)15;
+  w.psi5 = off;
+  off += 5 * (size_t)nth * tsz;
+  off = (off + 15) & ~(size_t)15;
+  w.nb5 = off;
+  off += 5 * (size_t)nth * tsz;
+  off = (off + 15) & ~(size_t)15;
+  w.nbm = off;
+  off += (size_t)nth * tsz;
+  off = (off + 127) & ~(size_t)127;
+  w.total = off;
+  return w;
+}
+
+// ------------------------------------------------------------- s-row chunk
+
+// Where a lane sits in the s-rows of a pass: `seg` lanes per row (V nodes
+// each), rpp = 32 / seg rows per pass.
+struct LaneGeom {
+  int sl, rslot, rpp;
+  bool first, last, lane_ok;
+};
+__device__ __forceinline__ LaneGeom lane_geom(int lane, int seg, int ns, int V) {
+  LaneGeom g;
+  g.sl = lane & (seg - 1);
+  g.rslot = lane / seg;
+  g.rpp = 32 / seg;
+  const int nl = ns / V;
+  g.first = g.sl == 0;
+  g.last = g.sl == nl - 1;
+  g.lane_ok = g.sl < nl;
+  return g;
+}
+
+// RK2 constants of one cell: Eq. 4's right-hand side is
+// R = (v/ds) D - k_off M + k_on Mf; the half step is
+// Ms = c1 D(M) + c2 M + c3 and the full step M' = e1 D(Ms) + e2 Ms + M + e3.
+template <typename T>
+struct RkConst {
+  T c1, c2, c3, e1, e2, e3;
+};
+
+// One chunk of RC s-rows (src_rows: the rows at step n, in shared or global
+// memory; dst: global rows at step n+1, in place allowed), with n_b of each
+// new row written to s_nb_chunk[r].
+template <typename T, int V>
+__device__ __forceinline__ void rows_chunk(const T* src_rows, T* dst, int RC, int ns, int seg,
+                                           const LaneGeom& lg, const RkConst<T>& k, T ds,
+                                           T* s_nb_chunk) {
+  const int passes = (RC + lg.rpp - 1) / lg.rpp;
+#pragma unroll kStepUnroll
+  for (int p = 0; p < passes; ++p) {
+    const int r = p * lg.rpp + lg.rslot;  // row within the chunk
+    const bool row_ok = r < RC;
+    const bool act = row_ok && lg.lane_ok;
+    const int off = (row_ok ? r : 0) * ns + lg.sl * V;
+    T M[V], D[V], Ms[V];
+    if (act) {
+      const Pack<T, V> q = *reinterpret_cast<const Pack<T, V>*>(src_rows + off);
+#pragma unroll
+      for (int v = 0; v < V; ++v) M[v] = q.v[v];
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) M[v] = T(0);
+    }
+    // midpoint RK2 with the constants folded
+    walk_dflux<T, V>(M, D, lg.first, lg.last, seg);
+#pragma unroll
+    for (int v = 0; v < V; ++v) Ms[v] = fma_t(k.c1, D[v], fma_t(k.c2, M[v], k.c3));
+    walk_dflux<T, V>(Ms, D, lg.first, lg.last, seg);
+    T snb = T(0);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      M[v] = fma_t(k.e1, D[v], fma_t(k.e2, Ms[v], M[v] + k.e3));
+      snb += M[v];
+    }
+    if (!act) snb = T(0);
+    if (act) {
+      Pack<T, V> q;
+#pragma unroll
+      for (int v = 0; v < V; ++v) q.v[v] = M[v];
+      *reinterpret_cast<Pack<T, V>*>(dst + off) = q;
+    }
+    snb = seg_sum(snb, seg);
+    if (lg.first && row_ok) s_nb_chunk[r] = snb * ds;
+  }
+}
+
+// ------------------------------------------------------------ end of a cell
+
+// Velocity data of one cell: the cell's own and its east/west (x) and
+// north/south (y) neighbours' velocities and the central-difference gradient.
+template <typename T>
+struct CellVel {
+  T uxc, uyc, uxe, uxw, uyn, uys, Gxx, Gxy, Gyx, Gyy;
+};
+template <typename T>
+__device__ __forceinline__ CellVel<T> load_cell_vel(const T* ucell, int cell) {
+  const T* uc = ucell + (size_t)cell * 12;
+  CellVel<T> u;
+  u.uxc = uc[0]; u.uyc = uc[1]; u.uxe = uc[2]; u.uxw = uc[3]; u.uyn = uc[4]; u.uys = uc[5];
+  u.Gxx = uc[6]; u.Gxy = uc[7]; u.Gyx = uc[8]; u.Gyy = uc[9];
+  return u;
+}
+
+// Constants of the psi transport of one instance.
+template <typename T>
+struct PsiConst {
+  T dt, g, glide, vsp, inv_dx, inv_dy, inv_dth, dth;
+  const T* trig;  // [4][nth]
+};
+
+// psi^{n+1} of the cell (lane = theta) by Eq. 1 in donor-cell flux form from
+// the staged columns psi5 / nb5 ([5][nth]: cell, east, west, north, south;
+// psi scaled by g on load), written to psi_out[cell]. Returns, per lane, the
+// partial sums of psi^{n+1} (cell_mass) and of psi^{n+1} n_b dtheta (the
+// coarse density of Eq. 5, acc) over the lane's orientations.
+template <typename T>
+__device__ __forceinline__ void psi_cell(const PsiConst<T>& q, const CellVel<T>& u,
+                                         const T* psi5, const T* nb5, const T* s_nb, int nth,
+                                         int lane, T* psi_out_cell, T& cell_mass, T& acc) {
+  const T* cosk = q.trig;
+  const T* sink = q.trig + nth;
+  const T* cosf = q.trig + 2 * nth;
+  const T* sinf = q.trig + 3 * nth;
+  const T g = q.g;
+  for (int k = lane; k < nth; k += 32) {
+    const T Pc = g * psi5[k], Pe = g * psi5[nth + k], Pw = g * psi5[2 * nth + k];
+    const T Pn = g * psi5[3 * nth + k], Ps = g * psi5[4 * nth + k];
+    const T ck = cosk[k], sk = sink[k];
+    const T Vc = q.vsp + q.glide * nb5[k], Ve = q.vsp + q.glide * nb5[nth + k];
+    const T Vw = q.vsp + q.glide * nb5[2 * nth + k], Vn = q.vsp + q.glide * nb5[3 * nth + k];
+    const T Vs = q.vsp + q.glide * nb5[4 * nth + k];
+    const T axc = fma_t(-Vc, ck, u.uxc), axe = fma_t(-Ve, ck, u.uxe), axw = fma_t(-Vw, ck, u.uxw);
+    const T ayc = fma_t(-Vc, sk, u.uyc), ayn = fma_t(-Vn, sk, u.uyn), ays = fma_t(-Vs, sk, u.uys);
+    const T Ae = T(0.5) * (axc + axe), Aw = T(0.5) * (axw + axc);
+    const T An = T(0.5) * (ayc + ayn), As = T(0.5) * (ays + ayc);
+    const int kp = k + 1 == nth ? 0 : k + 1, km = k == 0 ? nth - 1 : k - 1;
+    const T cp = cosf[k], sp = sinf[k], cm = cosf[km], sm = sinf[km];
+    // Jeffery rotation p_perp . G . p at the faces k +- 1/2
+    const T wp = -sp * (u.Gxx * cp + u.Gxy * sp) + cp * (u.Gyx * cp + u.Gyy * sp);
+    const T wm = -sm * (u.Gxx * cm + u.Gxy * sm) + cm * (u.Gyx * cm + u.Gyy * sm);
+    const T Fe = donor(Ae, Pc, Pe), Fw = donor(Aw, Pw, Pc);
+    const T Fn = donor(An, Pc, Pn), Fs = donor(As, Ps, Pc);
+    const T Fp = donor(wp, Pc, g * psi5[kp]), Fm = donor(wm, g * psi5[km], Pc);
+    const T pnew =
+        Pc - q.dt * ((Fe - Fw) * q.inv_dx + (Fn - Fs) * q.inv_dy + (Fp - Fm) * q.inv_dth);
+    psi_out_cell[k] = pnew;
+    cell_mass += pnew;
+    acc = fma_t(pnew * s_nb[k], q.dth, acc);
+  }
+}
+
+// TwoSum: hi + lo += x without rounding loss.
+template <typename T>
+__device__ __forceinline__ void two_sum_acc(T& hi, T& lo, T x) {
+  const T s2 = hi + x, bb = s2 - hi;
+  lo += (hi - (s2 - bb)) + (x - bb);
+  hi = s2;
+}
+
+// Eq. 5 to Eq. 6 for the cell: the coarse density Cpre = sum_k psi n_b dtheta,
+// the scale-down of Alg. 2 where the total motors fall short (the warp
+// rescales the rows it has just written), n_b of the new rows, C and Mf.
+template <typename T>
+__device__ __forceinline__ void cell_motor_close(T acc, T mtot, const T* s_nb, int nth, int ns,
+                                                 int lane, int cell, T* mb_out, T* nb_out, T* c,
+                                                 T* mf_out, T* cpre_out) {
+  const T Cpre = warp_sum_t(acc);
+  T f = T(1), C = Cpre;
+  if (mtot < Cpre) {
+    f = mtot / Cpre;
+    C = mtot;
+  }
+  const size_t cbase = (size_t)cell * nth;
+  if (f != T(1)) {
+    const T ft = f;
+    T* base = mb_out + cbase * ns;
+    for (int e = lane; e < nth * ns; e += 32) base[e] = __ldcg(base + e) * ft;
+    for (int k = lane; k < nth; k += 32) nb_out[cbase + k] = s_nb[k] * ft;
+  } else {
+    for (int k = lane; k < nth; k += 32) nb_out[cbase + k] = s_nb[k];
+  }
+  if (lane == 0) {
+    c[cell] = C;
+    mf_out[cell] = mtot - C;
+    if (cpre_out) cpre_out[cell] = Cpre;
+  }
+}
+
+}  // namespace mm

@@ -1,0 +1,174 @@
+// Host-side internals of libmm shared by the C-ABI translation units
+// (mm_api.cu: single instances and the adjoint; mm_batch_api.cu: the batched
+// ensemble): the handle, error helpers and the substep launch constants.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "mm_internal.cuh"
+
+using mm::DevParams;
+using mm::StepArgs;
+
+// Widest vector (values per lane) of the float32 substep kernel.
+#ifndef MM_FP32_VMAX
+#define MM_FP32_VMAX 8
+#endif
+// Widest vector of the float32 adjoint kernel.
+#ifndef MM_ADJ_FP32_VMAX
+#define MM_ADJ_FP32_VMAX 4
+#endif
+
+namespace mmh {
+inline thread_local std::string g_create_error;
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr size_t kStagingDoubles = size_t(1) << 22;  // 32 MiB of float64 staging
+}  // namespace mmh
+
+// State of an adjoint recording (mm_set_checkpointing / mm_adjoint_step).
+// The checkpoints, the recomputed segment and the reverse-sweep buffers live
+// in one device allocation (`slab`), kept after the recording ends so that a
+// new recording with the same K and max_substeps reuses it; the per-velocity
+// blocks are pooled the same way.
+struct Recording {
+  bool active = false;
+  int K = 0, max_sub = 0, nsub = 0, nck = 0;
+  void* slab = nullptr;
+  size_t slab_bytes = 0;
+  std::vector<void*> vblocks;  // velocity blocks, reused across recordings
+  std::vector<void*> ck_mb, ck_psi, ck_nb, ck_mf;  // checkpoints (states 0, K, 2K, ...)
+  double* ck_scale = nullptr;                      // psi mass-correction factor per checkpoint
+  std::vector<void*> sl_mb, sl_psi, sl_nb, sl_mf, sl_cpre;  // K + 1 recomputed states
+  void* sl_c = nullptr;
+  // velocity fields (and dt) in effect, in prescription order
+  std::vector<void*> v_ucell;
+  std::vector<double*> v_dt, v_lamG, v_lamu;
+  std::vector<int> sub_vel;  // velocity index of every recorded substep
+  // reverse-sweep buffers
+  void* lpsi[2] = {nullptr, nullptr};
+  void* lmf[2] = {nullptr, nullptr};
+  void* Dd[2] = {nullptr, nullptr};
+  void* lmb = nullptr;
+  double* gpart = nullptr;
+  double* seed[4] = {nullptr, nullptr, nullptr, nullptr};
+  double* coef = nullptr;
+  double* work = nullptr;  // [rows] float64 scratch for dL/dpsi0
+  int adj_grid = 1;
+};
+
+namespace mmh {
+struct BatchPlan;
+}
+
+struct mm_handle {
+  Recording rec;
+  // batched ensemble: a batch handle owns its member handles (one per
+  // instance, each an ordinary handle with its own state); a member points
+  // back to its batch
+  mmh::BatchPlan* batch = nullptr;
+  mm_handle* owner = nullptr;
+  mm_grid g{};
+  mm_rates r{};
+  mm_precision prec = MM_FP64;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;  // private stream used only for graph capture
+  int device = 0, sms = 0;
+  long long ncells = 0;
+  size_t rows = 0, mbn = 0, tsz = 8;
+  void* mb = nullptr;
+  void* psi[2] = {nullptr, nullptr};
+  void* nb[2] = {nullptr, nullptr};
+  void* mf = nullptr;    // free, coarse and total motors per cell, state precision
+  void* c = nullptr;
+  void* mtot = nullptr;
+  void* u = nullptr;
+  void* ucell = nullptr;
+  double* u64 = nullptr;
+  void* trig = nullptr;
+  double* trig64 = nullptr;
+  double* partial = nullptr;
+  double* fields = nullptr;
+  double* staging = nullptr;
+  DevParams* prm = nullptr;
+  int npartial = 0;
+  int parity = 0;
+  double dt = 0.0;
+  bool have_state = false, have_vel = false, have_dt = false;
+  // substep launch configuration
+  int V = 1, seg = 1, block = 128, grid_step = 1, grid_mom = 1;
+  int stages = 1, chunk_rows = 1, chunks_per_cell = 1;
+  bool tma = false;
+  size_t smem = 0;
+  std::map<long long, cudaGraphExec_t> graphs;
+  bool use_graphs = true;
+  std::string err;
+};
+
+namespace mmh {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+inline mm_status fail(mm_handle* h, mm_status st, const std::string& msg) {
+  if (h)
+    h->err = msg;
+  else
+    g_create_error = msg;
+  return st;
+}
+
+inline mm_status cuda_fail(mm_handle* h, const char* what, cudaError_t e) {
+  return fail(h, MM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
+                                  cudaGetErrorString(e) + ")");
+}
+
+#define CK(...)                                               \
+  do {                                                        \
+    cudaError_t e_ = (__VA_ARGS__);                           \
+    if (e_ != cudaSuccess) return cuda_fail(h, #__VA_ARGS__, e_); \
+  } while (0)
+
+inline bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+
+// Substep launch plan: s-rows stream through each warp's ring in chunks of at
+// most kChunkBytes, with up to kWarpInflightBytes in flight per warp.
+constexpr int kChunkBytes = 4096;
+constexpr int kWarpInflightBytes = 8192;
+constexpr int kMaxWarpsPerBlock = 4;
+constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory per block at most
+
+// Defined in mm_api.cu.
+mm_status check_rates(const mm_rates* r, mm_handle* h);
+mm_status check_status(mm_handle* h);
+mm_status rec_save_checkpoint(mm_handle* h, int i);
+template <typename T>
+StepArgs<T> step_args(mm_handle* h, int parity);
+mm_status rec_push_substep(mm_handle* h);  // checkpoint bookkeeping of one recorded substep
+
+// Defined in mm_batch_api.cu.
+mm_status batch_micro_step(mm_handle* h, int n);
+void batch_free(mm_handle* h);
+mm_status batch_sync(mm_handle* h);
+const std::vector<mm_handle*>& batch_members(mm_handle* h);
+mm_status batch_launch_info(mm_handle* h, int* info, int n);
+inline mm_status not_for_batch(mm_handle* h) {
+  return fail(h, MM_ERR_INVALID,
+              "a batch handle: per-instance calls go to its members (mm_batch_member)");
+}
+
+}  // namespace mmh

@@ -90,6 +90,18 @@ struct AdjArgs {
   double* gpart;    // [warps][4] accumulated k_off, v_walk, k_on adjoints
 };
 
+// One tile of the batched-ensemble substep: a run of consecutive cells of one
+// instance (mm_batch.cu).
+struct BatchTile {
+  int inst;        // instance (index into the StepArgs table)
+  int cell0;       // first cell
+  int ncell;       // cells in the tile
+  int tile0;       // index of the instance's first tile
+  int inst_tiles;  // tiles of the instance
+  int ch, rc;      // chunks per cell, s-rows per chunk
+  int pad;
+};
+
 // Kernel launchers (defined in mm_step.cu); V = values per lane.
 template <typename T, int V>
 cudaError_t launch_substep(const StepArgs<T>& a, int grid, int block, size_t smem, bool tma,
@@ -97,6 +109,15 @@ cudaError_t launch_substep(const StepArgs<T>& a, int grid, int block, size_t sme
 size_t step_smem_per_warp(int S, int chunk_elems, int nth, int tsz);
 template <typename T, int V>
 cudaError_t substep_prepare(int block, size_t smem, bool tma, int* blocks_per_sm);
+
+// Batched-ensemble launchers (mm_batch.cu): every instance's arguments in a
+// device table, tiles in a device table, per-tile float64 sums of psi.
+template <typename T, int V>
+cudaError_t launch_substep_batch(const StepArgs<T>* insts, const BatchTile* tiles, int ntiles,
+                                 double* tile_mass, int S, int stage_elems, int nth_max,
+                                 bool masscorr, int grid, int block, size_t smem, cudaStream_t s);
+template <typename T, int V>
+cudaError_t substep_batch_prepare(int block, size_t smem, int* blocks_per_sm);
 
 // Auxiliary kernels (mm_aux.cu).
 template <typename TO, typename TI>

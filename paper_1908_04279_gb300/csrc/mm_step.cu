@@ -27,96 +27,9 @@
 // Every mbarrier wait is bounded (DevParams::wait_limit polls). A warp whose
 // wait runs out records MM_ERR_TIMEOUT in DevParams::status, waits (bounded)
 // for the copies it still has in flight and leaves.
-#include "mm_internal.cuh"
-#include "mm_walk.cuh"
+#include "mm_cell.cuh"
 
 namespace mm {
-
-// ---------------------------------------------------------------- TMA / mbarrier
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-// Bounded wait for the phase with the given parity; false if it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
-  for (uint32_t i = 0;; ++i) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (i >= limit) return false;
-  }
-}
-// Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
-// global to this CTA's shared memory, completing on `bar`.
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-constexpr uint32_t kDrainLimit = 1u << 24;  // polls while draining after a timeout
-
-// Occupancy target (resident 4-warp blocks per SM, caps registers per thread)
-// and unroll depth of the s-row pass loop.
-#ifndef MM_STEP_MIN_BLOCKS
-#define MM_STEP_MIN_BLOCKS 4
-#endif
-#ifndef MM_STEP_UNROLL
-#define MM_STEP_UNROLL 2
-#endif
-constexpr int kStepUnroll = MM_STEP_UNROLL;
-
-// ------------------------------------------------------------------- layout
-
-// Per-warp shared memory: S + 2 mbarriers (S ring stages, 1 neighbourhood, 1
-// that never completes, waited on by the timeout test knob), S stages of
-// chunk_elems values, the psi and n_b columns of the cell and its east, west,
-// north and south neighbours (2 x 5 nth values), and n_b of the cell's new
-// rows (nth values), all in the state precision.
-struct WarpSmem {
-  size_t bars, stages, psi5, nb5, nbm, total;
-};
-__host__ __device__ inline WarpSmem warp_smem_layout(int S, int chunk_elems, int nth, int tsz) {
-  WarpSmem w;
-  w.bars = 0;
-  size_t off = 8 * (size_t)(S + 2);
-  off = (off + 127) & ~(size_t)127;
-  w.stages = off;
-  off += (size_t)S * chunk_elems * tsz;
-  off = (off + 15) & ~(size_t)15;
-  w.psi5 = off;
-  off += 5 * (size_t)nth * tsz;
-  off = (off + 15) & ~(size_t)15;
-  w.nb5 = off;
-  off += 5 * (size_t)nth * tsz;
-  off = (off + 15) & ~(size_t)15;
-  w.nbm = off;
-  off += (size_t)nth * tsz;
-  off = (off + 127) & ~(size_t)127;
-  w.total = off;
-  return w;
-}
 
 size_t step_smem_per_warp(int S, int chunk_elems, int nth, int tsz) {
   return warp_smem_layout(S, chunk_elems, nth, tsz).total;
@@ -151,12 +64,7 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
   const int my_cells = gw < nc ? (nc - 1 - gw) / W + 1 : 0;
   const int nchunks = my_cells * CH;
 
-  const int sl = lane & (seg - 1);  // lane within its row
-  const int rslot = lane / seg;     // row within a pass
-  const int rpp = 32 / seg;         // rows per pass
-  const int passes = (RC + rpp - 1) / rpp;
-  const int nl = ns / V;
-  const bool first = sl == 0, last = sl == nl - 1, lane_ok = sl < nl;
+  const LaneGeom lg = lane_geom(lane, seg, ns, V);
 
   const DevParams* P = a.prm;
   const double dt64 = P->dt;
@@ -168,14 +76,10 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
   const T g = MASSCORR ? (T)P->psi_scale : T(1);
   const uint32_t wait_limit = P->wait_limit;
   const bool wait_never = (P->debug_flags & 1u) != 0;  // test knob: every wait runs out
-  const T inv_dx = (T)a.inv_dx, inv_dy = (T)a.inv_dy, inv_dth = (T)a.inv_dth;
-  const T* cosk = a.trig;
-  const T* sink = a.trig + nth;
-  const T* cosf = a.trig + 2 * nth;
-  const T* sinf = a.trig + 3 * nth;
-  const T ds = (T)a.ds, dth_t = (T)a.dth;
-  const T c1 = hdt * cw, c2 = T(1) - hdt * koff;
-  const T e1 = dt * cw, e2 = -dt * koff;
+  const PsiConst<T> pq{dt, g, glide, vsp, (T)a.inv_dx, (T)a.inv_dy, (T)a.inv_dth, (T)a.dth,
+                       a.trig};
+  const T ds = (T)a.ds;
+  RkConst<T> rk{hdt * cw, T(1) - hdt * koff, T(0), dt * cw, -dt * koff, T(0)};
 
   // producer cursor: next chunk to issue (cell, part, stage)
   int icell = gw, ipart = 0, istage = 0, issued = 0;
@@ -201,11 +105,10 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
   bool timed_out = false, nb_pending = false;
   int fail_stage = 0, fail_left = 0;
   uint32_t fail_par = 0;
-  T uxc = 0, uyc = 0, uxe = 0, uxw = 0, uyn = 0, uys = 0, Gxx = 0, Gxy = 0, Gyx = 0, Gyy = 0;
+  CellVel<T> uv{};
   int cell = gw - W, ce = 0, cwc = 0, cn = 0, cs = 0;
   uint32_t nb_par = 1;  // parity of the neighbourhood phase of the current cell
   T mtot = 0;
-  T c3 = 0, e3 = 0;
   T mass_hi = T(0), mass_lo = T(0);  // compensated sum of psi^{n+1} over this warp's cells
   int part = 0, s = 0;
   uint32_t par = 0;  // parity of the phase chunk t waits for on stage s
@@ -225,11 +128,9 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
       const T mf_n = a.mf_in[cell];
       mtot = a.mtot[cell];
       // stage constants: c for the half step, e for the full step
-      c3 = hdt * kon * mf_n;
-      e3 = dt * kon * mf_n;
-      const T* uc = a.ucell + (size_t)cell * 12;
-      uxc = uc[0]; uyc = uc[1]; uxe = uc[2]; uxw = uc[3]; uyn = uc[4]; uys = uc[5];
-      Gxx = uc[6]; Gxy = uc[7]; Gyx = uc[8]; Gyy = uc[9];
+      rk.c3 = hdt * kon * mf_n;
+      rk.e3 = dt * kon * mf_n;
+      uv = load_cell_vel(a.ucell, cell);
       if (nb_tma && lane == 0) {
         // stage the psi^n and n_b^n columns of the cell and its 4 neighbours
         const uint32_t pb = (uint32_t)(nth * sizeof(T));
@@ -259,44 +160,7 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
         break;
       }
     }
-    T* dst = a.mb_out + chunk_off;
-#pragma unroll kStepUnroll
-    for (int p = 0; p < passes; ++p) {
-      const int r = p * rpp + rslot;  // row within the chunk
-      const bool row_ok = r < RC;
-      const bool act = row_ok && lane_ok;
-      const int off = (row_ok ? r : 0) * ns + sl * V;
-      T M[V], D[V], Ms[V];
-      if (act) {
-        const Pack<T, V> q = *reinterpret_cast<const Pack<T, V>*>(src_rows + off);
-#pragma unroll
-        for (int v = 0; v < V; ++v) M[v] = q.v[v];
-      } else {
-#pragma unroll
-        for (int v = 0; v < V; ++v) M[v] = T(0);
-      }
-      // Eq. 4 right-hand side R = (v/ds) D - k_off M + k_on Mf; midpoint RK2
-      // Ms = M + (dt/2) R(M), M' = M + dt R(Ms), with the constants folded
-      walk_dflux<T, V>(M, D, first, last, seg);
-#pragma unroll
-      for (int v = 0; v < V; ++v) Ms[v] = fma_t(c1, D[v], fma_t(c2, M[v], c3));
-      walk_dflux<T, V>(Ms, D, first, last, seg);
-      T snb = T(0);
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        M[v] = fma_t(e1, D[v], fma_t(e2, Ms[v], M[v] + e3));
-        snb += M[v];
-      }
-      if (!act) snb = T(0);
-      if (act) {
-        Pack<T, V> q;
-#pragma unroll
-        for (int v = 0; v < V; ++v) q.v[v] = M[v];
-        *reinterpret_cast<Pack<T, V>*>(dst + off) = q;
-      }
-      snb = seg_sum(snb, seg);
-      if (first && row_ok) s_nb[part * RC + r] = snb * ds;
-    }
+    rows_chunk<T, V>(src_rows, a.mb_out + chunk_off, RC, ns, seg, lg, rk, ds, s_nb + part * RC);
     __syncwarp();
     // the stage is consumed: refill it with the chunk S ahead
     if (TMA && lane == 0 && issued < nchunks) issue_next();
@@ -326,58 +190,10 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
       __syncwarp();
     }
     T acc = T(0), cell_mass = T(0);
-    const size_t cbase = (size_t)cell * nth;
-    for (int k = lane; k < nth; k += 32) {
-      const T Pc = g * psi5[k], Pe = g * psi5[nth + k], Pw = g * psi5[2 * nth + k];
-      const T Pn = g * psi5[3 * nth + k], Ps = g * psi5[4 * nth + k];
-      const T ck = cosk[k], sk = sink[k];
-      const T Vc = vsp + glide * nb5[k], Ve = vsp + glide * nb5[nth + k];
-      const T Vw = vsp + glide * nb5[2 * nth + k], Vn = vsp + glide * nb5[3 * nth + k];
-      const T Vs = vsp + glide * nb5[4 * nth + k];
-      const T axc = fma_t(-Vc, ck, uxc), axe = fma_t(-Ve, ck, uxe), axw = fma_t(-Vw, ck, uxw);
-      const T ayc = fma_t(-Vc, sk, uyc), ayn = fma_t(-Vn, sk, uyn), ays = fma_t(-Vs, sk, uys);
-      const T Ae = T(0.5) * (axc + axe), Aw = T(0.5) * (axw + axc);
-      const T An = T(0.5) * (ayc + ayn), As = T(0.5) * (ays + ayc);
-      const int kp = k + 1 == nth ? 0 : k + 1, km = k == 0 ? nth - 1 : k - 1;
-      const T cp = cosf[k], sp = sinf[k], cm = cosf[km], sm = sinf[km];
-      // Jeffery rotation p_perp . G . p at the faces k +- 1/2
-      const T wp = -sp * (Gxx * cp + Gxy * sp) + cp * (Gyx * cp + Gyy * sp);
-      const T wm = -sm * (Gxx * cm + Gxy * sm) + cm * (Gyx * cm + Gyy * sm);
-      const T Fe = donor(Ae, Pc, Pe), Fw = donor(Aw, Pw, Pc);
-      const T Fn = donor(An, Pc, Pn), Fs = donor(As, Ps, Pc);
-      const T Fp = donor(wp, Pc, g * psi5[kp]), Fm = donor(wm, g * psi5[km], Pc);
-      const T pnew = Pc - dt * ((Fe - Fw) * inv_dx + (Fn - Fs) * inv_dy + (Fp - Fm) * inv_dth);
-      a.psi_out[cbase + k] = pnew;
-      cell_mass += pnew;
-      acc = fma_t(pnew * s_nb[k], dth_t, acc);
-    }
-    {
-      // TwoSum: mass_hi + mass_lo += cell_mass without rounding loss
-      const T s2 = mass_hi + cell_mass, bb = s2 - mass_hi;
-      mass_lo += (mass_hi - (s2 - bb)) + (cell_mass - bb);
-      mass_hi = s2;
-    }
-    const T Cpre = warp_sum_t(acc);
-    T f = T(1), C = Cpre;
-    if (mtot < Cpre) {
-      f = mtot / Cpre;
-      C = mtot;
-    }
-    if (f != T(1)) {
-      // rare: rescale the rows of this cell just written (own writes, ordered
-      // by the __syncwarp above)
-      const T ft = f;
-      T* base = a.mb_out + cbase * ns;
-      for (int e = lane; e < nth * ns; e += 32) base[e] = __ldcg(base + e) * ft;
-      for (int k = lane; k < nth; k += 32) a.nb_out[cbase + k] = s_nb[k] * ft;
-    } else {
-      for (int k = lane; k < nth; k += 32) a.nb_out[cbase + k] = s_nb[k];
-    }
-    if (lane == 0) {
-      a.c[cell] = C;
-      a.mf_out[cell] = mtot - C;
-      if (a.cpre_out) a.cpre_out[cell] = Cpre;
-    }
+    psi_cell(pq, uv, psi5, nb5, s_nb, nth, lane, a.psi_out + (size_t)cell * nth, cell_mass, acc);
+    two_sum_acc(mass_hi, mass_lo, cell_mass);
+    cell_motor_close(acc, mtot, s_nb, nth, ns, lane, cell, a.mb_out, a.nb_out, a.c, a.mf_out,
+                     a.cpre_out);
     __syncwarp();
   }
 

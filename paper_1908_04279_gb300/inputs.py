@@ -193,7 +193,17 @@ WORKLOADS = {
                       modes=8, amp=0.1, seed=0),
     "large512": dict(grid=Grid(512, 512, 64, 64), substeps=100, macro=20, flow="random",
                      modes=16, amp=0.2, seed=0),
+    # 64 members of ensemble_members(); each starts from its own perturbed
+    # isotropic psi (seed = member seed) under its own 8-mode random flow
+    "ensemble64": dict(members=64, substeps=500, macro=1, flow="random", modes=8, amp=0.1),
 }
+
+
+def member_inputs(m: Member, modes: int = 8, amp: float = 0.1) -> tuple[np.ndarray, np.ndarray]:
+    """Initial psi and velocity of an ensemble member (from its seed)."""
+    psi0 = psi_isotropic_perturbed(m.grid, m.seed)
+    u = random_divfree_flow(m.grid, velocity_seed(m.seed, 0), modes, amp)
+    return psi0, u
 
 
 def workload_velocity(name: str, macro_step: int) -> np.ndarray:

@@ -51,6 +51,10 @@ class mm_moments_out(C.Structure):
                 ("scalars", C.c_double * 8)]
 
 
+class mm_batch_tune(C.Structure):
+    _fields_ = [("tile_work", C.c_int), ("chunk_bytes", C.c_int), ("ms_per_substep", C.c_double)]
+
+
 class mm_adjoint_seed(C.Structure):
     _fields_ = [("observable", C.c_int), ("dL_dpsi", C.c_void_p), ("dL_dnb", C.c_void_p),
                 ("dL_dm1", C.c_void_p), ("dL_dmf", C.c_void_p), ("on_device", C.c_int)]
@@ -87,6 +91,11 @@ PROTOTYPES = {
     "mm_get_launch_info": ([_H, C.POINTER(C.c_int), C.c_int], C.c_int),
     "mm_moments_static": ([C.POINTER(mm_grid), C.POINTER(mm_rates), _P, _P, _P, _P, _P, _P, _P],
                           C.c_int),
+    "mm_create_batch": ([C.c_int, C.POINTER(mm_grid), C.POINTER(mm_rates), C.c_int, _P,
+                         C.POINTER(_H)], C.c_int),
+    "mm_batch_member": ([_H, C.c_int, C.POINTER(_H)], C.c_int),
+    "mm_batch_autotune": ([_H, C.c_int, C.POINTER(mm_batch_tune), C.c_int,
+                           C.POINTER(C.c_int)], C.c_int),
     "mm_last_error": ([_H], C.c_char_p),
     "mm_build_info": ([], C.c_char_p),
 }
@@ -146,10 +155,14 @@ class Simulation:
     """One simulation instance resident on the current CUDA device."""
 
     def __init__(self, grid: Grid, rates: Rates = Rates(), precision: str = "fp64",
-                 stream: int | None = None):
+                 stream: int | None = None, _member=None):
         self.lib = load_library()
         self.grid, self.rates = grid, rates
         self.precision = precision
+        self._owned = _member is None
+        if _member is not None:  # a batch member: the batch owns the handle
+            self.h = _member
+            return
         prec = {"fp64": MM_FP64, "fp32": MM_FP32_MIXED}[precision]
         h = C.c_void_p()
         st = self.lib.mm_create(C.byref(self._g()), C.byref(self._r(rates)), prec,
@@ -173,7 +186,8 @@ class Simulation:
 
     def close(self):
         if getattr(self, "h", None):
-            self.lib.mm_destroy(self.h)
+            if self._owned:
+                self.lib.mm_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -318,6 +332,86 @@ class Simulation:
         self._check(self.lib.mm_moments(self.h, C.byref(out)))
         sc = dict(zip(SCALAR_NAMES, list(out.scalars)))
         return (dict(zip(FIELD_NAMES, host)) if host is not None else None), sc
+
+
+class Batch:
+    """An ensemble of independent instances advanced together: one launch per
+    substep over all members, the substeps of one step() call in one CUDA
+    graph (mm_create_batch). members[i] is a Simulation view of instance i
+    for its per-instance calls (set_state, set_velocity, moments, adjoint)."""
+
+    def __init__(self, grids, rates, precision: str = "fp32", stream: int | None = None):
+        self.lib = load_library()
+        n = len(grids)
+        if len(rates) != n:
+            raise ValueError("one Rates per grid")
+        ga = (mm_grid * n)(*[mm_grid(g.nx, g.ny, g.ntheta, g.ns, g.L) for g in grids])
+        ra = (mm_rates * n)(*[Simulation._r(r) for r in rates])
+        prec = {"fp64": MM_FP64, "fp32": MM_FP32_MIXED}[precision]
+        h = C.c_void_p()
+        st = self.lib.mm_create_batch(n, ga, ra, prec,
+                                      C.c_void_p(stream if stream is not None
+                                                 else current_stream_handle()), C.byref(h))
+        if st != 0:
+            raise MMError(st, self.lib.mm_last_error(None).decode())
+        self.h = h
+        self.members = []
+        for i in range(n):
+            m = C.c_void_p()
+            self._check(self.lib.mm_batch_member(self.h, i, C.byref(m)))
+            self.members.append(Simulation(grids[i], rates[i], precision, _member=m))
+
+    def _check(self, st: int):
+        if st != 0:
+            raise MMError(st, self.lib.mm_last_error(self.h).decode())
+
+    def step(self, n: int):
+        self._check(self.lib.mm_micro_step(self.h, int(n)))
+
+    def sync(self):
+        self._check(self.lib.mm_sync(self.h))
+
+    def debug_set(self, wait_limit: int, flags: int = 0):
+        self._check(self.lib.mm_debug_set(self.h, int(wait_limit), int(flags)))
+
+    def autotune(self, substeps: int = 5):
+        """Time every (tile_work, chunk_bytes) candidate; keep the fastest.
+        Returns the list of timings."""
+        res = (mm_batch_tune * 64)()
+        n = C.c_int()
+        self._check(self.lib.mm_batch_autotune(self.h, int(substeps), res, 64, C.byref(n)))
+        return [dict(tile_work=r.tile_work, chunk_bytes=r.chunk_bytes,
+                     ms_per_substep=r.ms_per_substep) for r in res[:n.value]]
+
+    def launch_info(self) -> dict:
+        arr = (C.c_int * 11)()
+        self._check(self.lib.mm_get_launch_info(self.h, arr, 11))
+        keys = ("grid", "block", "smem", "tma", "stages", "stage_elems", "tiles", "V",
+                "tile_work", "chunk_bytes", "tuned")
+        return dict(zip(keys, list(arr)))
+
+    @property
+    def cell_updates_per_substep(self) -> int:
+        return sum(m.grid.micro_cells for m in self.members)
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.h = None
+            self.lib.mm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def moments_static(grid: Grid, rates: Rates, psi, mb, mf, c, fields, scalars, stream: int = 0):

@@ -9,7 +9,10 @@ Default workload "precision128": 128x128 periodic grid, 32 orientations, 32
 arclength nodes, 50 substeps per macro step, velocity from a seeded random
 divergence-free field (8 Fourier modes, amplitude 0.1) refreshed every macro
 step, mixed precision (float32 Mb/psi, float64 sums). The float64 path is timed
-on the same workload and reported beside it.
+on the same workload and reported beside it. Beside the main line: the
+adjoint/forward time ratio (adjoint64), the substep on large512 (4.3 GB of
+motor state, the HBM roofline case) in float32 and float64, and the batched
+ensemble (ensemble64, 64 uneven members, 500 substeps per graph).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                   [--workload precision128|large512|adjoint64|cellular32]
@@ -44,7 +47,20 @@ from paper_1908_04279_gb300.inputs import (WORKLOADS, Rates, psi_isotropic_pertu
 
 METRIC = "micro-state cell-updates/s"
 UNIT = "cell-updates/s"
-STEP_KERNEL_SRC = os.path.join(ROOT, "paper_1908_04279_gb300", "csrc", "mm_step.cu")
+CSRC = os.path.join(ROOT, "paper_1908_04279_gb300", "csrc")
+# sources of each kernel a committed profile summary may describe
+KERNEL_SRCS = {
+    "k_substep": ("mm_step.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
+    "k_substep_batch": ("mm_batch.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
+    "k_adjoint": ("mm_adjoint.cu", "mm_walk.cuh", "mm_internal.cuh"),
+}
+
+
+def kernel_sha(kernel: str) -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS[kernel]:
+        h.update(open(os.path.join(CSRC, f), "rb").read())
+    return h.hexdigest()
 
 
 def dist_env():
@@ -74,10 +90,12 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-def read_profile_traffic(workload: str, precision: str):
-    """DRAM bytes per launch of the substep kernel from the committed ncu
-    summary, if it was taken on the current kernel source (sha256 match)."""
-    path = os.path.join(ROOT, "profiles", f"k_substep_{workload}_{precision}.md")
+def read_profile_traffic(kernel: str, workload: str, precision: str, scale: float = 1.0):
+    """DRAM bytes per launch of a kernel from its committed ncu summary, if it
+    was taken on the current kernel sources (sha256 match); `scale` converts a
+    capture of a smaller case to the timed launch (traffic in proportion to
+    the motor cells)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}_{precision}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -85,8 +103,7 @@ def read_profile_traffic(workload: str, precision: str):
     h = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
     if not m or not h:
         return None
-    cur = hashlib.sha256(open(STEP_KERNEL_SRC, "rb").read()).hexdigest()
-    return float(m.group(1)) if h.group(1) == cur else None
+    return float(m.group(1)) * scale if h.group(1) == kernel_sha(kernel) else None
 
 
 class ClockSampler:
@@ -332,6 +349,75 @@ def run_ours(args):
         return {"forward_ms": best_f, "forward_plus_adjoint_ms": best_a,
                 "adjoint_over_forward": (best_a - best_f) / best_f}
 
+    def large_run(precision, substeps):
+        """large512 (512x512 x 64 x 64, 4.3 GB of float32 Mb): far beyond L2,
+        so its substep launch gives the HBM roofline fraction. Timed as one
+        graph of `substeps` launches after a warm-up graph."""
+        wl = WORKLOADS["large512"]
+        gl = wl["grid"]
+        sim = mm.Simulation(gl, r, precision, stream=stream.cuda_stream)
+        sim.set_state(psi_isotropic_perturbed(gl, wl["seed"]))
+        sim.set_velocity(torch.tensor(workload_velocity("large512", 0), device=dev))
+        sim.step(substeps)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(substeps)
+        e1.record(stream)
+        e1.synchronize()
+        sim.sync()
+        sim.close()
+        ms = e0.elapsed_time(e1) / substeps
+        tsz = 4 if precision == "fp32" else 8
+        algo_l = algorithmic_bytes_per_launch(gl, tsz)
+        return {"value": world * gl.micro_cells / (ms * 1e-3), "unit": UNIT,
+                "kernel_ms_per_launch": ms, "algorithmic_bytes_per_launch": algo_l,
+                "achieved_gbs": algo_l / (ms * 1e-3) / 1e9}
+
+    def ensemble_run(steps):
+        """ensemble64: 64 members with uneven grids (N in {32..128}, Ntheta and
+        Ns in {16, 32}), k_off log-uniform in [0.05, 5], v_walk in [0.5, 2];
+        after mm_batch_autotune, a step is one graph of 500 batched substeps
+        (one launch per substep over all members)."""
+        from paper_1908_04279_gb300.inputs import ensemble_members, member_inputs
+        ms_ = ensemble_members()
+        b = mm.Batch([m.grid for m in ms_], [m.rates for m in ms_], "fp32",
+                     stream=stream.cuda_stream)
+        for sim, m in zip(b.members, ms_):
+            psi_m, u_m = member_inputs(m)
+            sim.set_state(psi_m)
+            sim.set_velocity(u_m)
+        tune = b.autotune(substeps=3)
+        ne = WORKLOADS["ensemble64"]["substeps"]
+        b.step(ne)
+        b.sync()
+        times = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            b.step(ne)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        b.sync()
+        info = b.launch_info()
+        cells = b.cell_updates_per_substep
+        algo_e = sum(algorithmic_bytes_per_launch(m.grid, 4) for m in ms_)
+        b.close()
+        ms_step = sum(times) / len(times)
+        launch = ms_step / ne
+        best = min(tune, key=lambda x: x["ms_per_substep"])
+        return {"workload": "ensemble64 (64 members, 500 substeps per step in one CUDA graph, "
+                            "float32)",
+                "value": world * cells * ne / (ms_step * 1e-3), "unit": UNIT, "steps": steps,
+                "ms_per_step": ms_step, "kernel_ms_per_launch": launch,
+                "motor_cells_per_substep": cells, "algorithmic_bytes_per_launch": algo_e,
+                "achieved_gbs": algo_e / (launch * 1e-3) / 1e9,
+                "plan": {k: info[k] for k in ("grid", "block", "tiles", "V", "tile_work",
+                                              "chunk_bytes")},
+                "autotune_best_ms_per_substep": best["ms_per_substep"],
+                "autotune_candidates": len(tune)}
+
     units_per_step = g.micro_cells * nsub
     clocks = ClockSampler(local)
     clocks.start()
@@ -342,6 +428,9 @@ def run_ours(args):
     e2e_s, h2d, d2h = e2e_run("fp32", args.steps, args.warmup)
     adj = {"workload": "adjoint64 (64x64 x 32 x 32, 100 substeps, checkpoint every 10, polar order)",
            "fp32": adjoint_ratio("fp32"), "fp64": adjoint_ratio("fp64")}
+    large = {"workload": "large512 (512x512 x 64 x 64, 1.07e9 motor cells)",
+             "fp32": large_run("fp32", 10), "fp64": large_run("fp64", 3)}
+    ens = ensemble_run(max(2, min(args.steps, 3)))
 
     t = torch.tensor([total_ms, kern_ms, fp64_ms, e2e_s], dtype=torch.float64, device=dev)
     if world > 1:
@@ -353,7 +442,7 @@ def run_ours(args):
     peak, peak_src = read_peaks()
     algo = algorithmic_bytes_per_launch(g, 4)
     achieved = algo / (launch_ms * 1e-3) / 1e9
-    traffic = read_profile_traffic(name, "fp32")
+    traffic = read_profile_traffic("k_substep", name, "fp32")
     fp64_value = world * units_per_step * fp64_steps / (fp64_ms * 1e-3)
     if rank == 0:
         cpu = time_oracle_sample(name) if world == 1 or rank == 0 else None
@@ -379,6 +468,20 @@ def run_ours(args):
             "e2e": {"value": world * units_per_step * args.steps / e2e_s, "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "adjoint": adj,
+            "large512": dict(large, fp32_over_fp64=large["fp32"]["value"] / large["fp64"]["value"],
+                             roofline={"bound": "hbm", "peak": peak, "unit": "GB/s",
+                                       "achieved": large["fp32"]["achieved_gbs"],
+                                       "frac": large["fp32"]["achieved_gbs"] / peak,
+                                       "kernel": "k_substep (float32)", "peak_source": peak_src,
+                                       "traffic": read_profile_traffic(
+                                           "k_substep", "large512", "fp32")}),
+            "ensemble": dict(ens, roofline={"bound": "hbm", "peak": peak, "unit": "GB/s",
+                                            "achieved": ens["achieved_gbs"],
+                                            "frac": ens["achieved_gbs"] / peak,
+                                            "kernel": "k_substep_batch (float32)",
+                                            "peak_source": peak_src,
+                                            "traffic": read_profile_traffic(
+                                                "k_substep_batch", "ensemble64", "fp32")}),
             "gpu_launches": args.steps * (nsub + 3),
             "clocks": clk,
         }

@@ -239,8 +239,8 @@ mm_status put_array(mm_handle* h, void* dst, const double* src, size_t n, int on
     CK(mm::launch_convert<float, double>(d, src, n, nullptr, h->stream));
     return MM_OK;
   }
-  for (size_t off = 0; off < n; off += kStagingDoubles) {
-    size_t m = std::min(kStagingDoubles, n - off);
+  for (size_t off = 0; off < n; off += h->staging_n) {
+    size_t m = std::min(h->staging_n, n - off);
     CK(cudaMemcpyAsync(h->staging, src + off, m * 8, cudaMemcpyHostToDevice, h->stream));
     CK(mm::launch_convert<float, double>(d + off, h->staging, m, nullptr, h->stream));
   }
@@ -262,8 +262,8 @@ mm_status get_array(mm_handle* h, double* dst, const void* src, size_t n, int on
       CK(mm::launch_convert<double, float>(dst, (const float*)src, n, scale, h->stream));
     return MM_OK;
   }
-  for (size_t off = 0; off < n; off += kStagingDoubles) {
-    size_t m = std::min(kStagingDoubles, n - off);
+  for (size_t off = 0; off < n; off += h->staging_n) {
+    size_t m = std::min(h->staging_n, n - off);
     if (h->prec == MM_FP64)
       CK(mm::launch_convert<double, double>(h->staging, (const double*)src + off, m, scale, h->stream));
     else
@@ -371,8 +371,10 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
     if (st != MM_OK) return bail(st);
   }
   const size_t nc = (size_t)h->ncells;
+  // float64 staging of host transfers: the largest array, up to 32 MiB
+  h->staging_n = std::min(kStagingDoubles, std::max(h->mbn, 12 * nc));
   const size_t need = h->mbn * h->tsz + 2 * h->rows * h->tsz + 3 * h->rows * 8 + 3 * nc * 8 +
-                      2 * nc * (h->tsz + 8) + 12 * nc * (8 + h->tsz) + kStagingDoubles * 8 +
+                      2 * nc * (h->tsz + 8) + 12 * nc * (8 + h->tsz) + h->staging_n * 8 +
                       (size_t)h->npartial * 8 * 8 + 4 * grid->ntheta * (h->tsz + 8) + 4096;
   size_t freeb = 0, totalb = 0;
   e = cudaMemGetInfo(&freeb, &totalb);
@@ -409,7 +411,7 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
   ALLOC(h->trig64, 14 * (size_t)grid->ntheta * 8);
   ALLOC(h->partial, (size_t)h->npartial * 8 * 8);
   ALLOC(h->fields, 12 * nc * 8);
-  ALLOC(h->staging, kStagingDoubles * 8);
+  ALLOC(h->staging, h->staging_n * 8);
   ALLOC(h->prm, sizeof(DevParams));
 #undef ALLOC
   e = cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking);

@@ -95,6 +95,7 @@ struct mm_handle {
   double* partial = nullptr;
   double* fields = nullptr;
   double* staging = nullptr;
+  size_t staging_n = 0;  // float64 values the staging buffer holds
   DevParams* prm = nullptr;
   int npartial = 0;
   int parity = 0;

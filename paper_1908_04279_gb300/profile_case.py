@@ -1,11 +1,17 @@
-"""Run the substep path on one synthetic case, for profilers.
+"""Run one synthetic case of the library's kernels, for profilers.
 
-    python -m paper_1908_04279_gb300.profile_case --grid NX NY NTHETA NS \
-        [--precision fp32|fp64] [--substeps N] [--repeat R]
+    python -m paper_1908_04279_gb300.profile_case [--case single|batch|adjoint]
+        [--grid NX NY NTHETA NS] [--precision fp32|fp64] [--substeps N]
+        [--repeat R] [--K K] [--members M] [--autotune]
 
-Sets the perturbed isotropic state and a seeded 8-mode divergence-free flow
-(amplitude 0.1), then runs R calls of N substeps each and prints the kernel
-time per substep measured with CUDA events on the handle's stream.
+single:  the perturbed isotropic state under a seeded 8-mode divergence-free
+         flow (amplitude 0.1); R calls of N substeps.
+batch:   the first M members of the detachment-rate ensemble (64 by default)
+         as one batch; R calls of N batched substeps (after mm_batch_autotune
+         with --autotune).
+adjoint: a recording of N substeps (checkpoint every K) on the single case,
+         then the reverse sweep for the polar order; R times.
+Prints the times measured with CUDA events on the handle's stream.
 """
 from __future__ import annotations
 
@@ -18,32 +24,73 @@ def main():
 
     from . import build as B
     from . import mm
-    from .inputs import Grid, Rates, psi_isotropic_perturbed, random_divfree_flow
+    from .inputs import (Grid, Rates, ensemble_members, member_inputs, psi_isotropic_perturbed,
+                         random_divfree_flow)
 
     ap = argparse.ArgumentParser()
+    ap.add_argument("--case", default="single", choices=["single", "batch", "adjoint"])
     ap.add_argument("--grid", type=int, nargs=4, default=[256, 256, 64, 64])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--substeps", type=int, default=10)
     ap.add_argument("--repeat", type=int, default=3)
+    ap.add_argument("--K", type=int, default=10)
+    ap.add_argument("--members", type=int, default=64)
+    ap.add_argument("--autotune", action="store_true")
     args = ap.parse_args()
     B.build()
-    g = Grid(*args.grid)
     stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1)
+
+    if args.case == "batch":
+        ms = ensemble_members()[: args.members]
+        with mm.Batch([m.grid for m in ms], [m.rates for m in ms], args.precision,
+                      stream=stream.cuda_stream) as b:
+            for sim, m in zip(b.members, ms):
+                psi0, u = member_inputs(m)
+                sim.set_state(psi0)
+                sim.set_velocity(u)
+            if args.autotune:
+                b.autotune(substeps=3)
+            times = [timed(lambda: b.step(args.substeps)) / args.substeps
+                     for _ in range(args.repeat)]
+            b.sync()
+            cells = b.cell_updates_per_substep
+            print(json.dumps({"case": "batch", "members": len(ms), "ms_per_substep": times,
+                              "launch": b.launch_info(),
+                              "cell_updates_per_s": cells / (min(times) * 1e-3)}))
+        return
+
+    g = Grid(*args.grid)
     with mm.Simulation(g, Rates(), args.precision, stream=stream.cuda_stream) as sim:
-        sim.set_state(psi_isotropic_perturbed(g, 0))
-        sim.set_velocity(random_divfree_flow(g, 1, 8, 0.1))
-        times = []
+        psi0 = psi_isotropic_perturbed(g, 0)
+        u = random_divfree_flow(g, 1, 8, 0.1)
+        sim.set_state(psi0)
+        sim.set_velocity(u)
+        if args.case == "single":
+            times = [timed(lambda: sim.step(args.substeps)) / args.substeps
+                     for _ in range(args.repeat)]
+            sim.sync()
+            print(json.dumps({"case": "single", "grid": args.grid, "precision": args.precision,
+                              "ms_per_substep": times, "launch": sim.launch_info(),
+                              "cell_updates_per_s": g.micro_cells / (min(times) * 1e-3)}))
+            return
+        fwd, adj = [], []
         for _ in range(args.repeat):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            sim.step(args.substeps)
-            e1.record(stream)
-            e1.synchronize()
-            times.append(e0.elapsed_time(e1) / args.substeps)
-        sim.sync()
-        print(json.dumps({"grid": args.grid, "precision": args.precision,
-                          "ms_per_substep": times, "launch": sim.launch_info(),
-                          "cell_updates_per_s": g.micro_cells / (min(times) * 1e-3)}))
+            sim.set_state(psi0)
+            sim.set_velocity(u)
+            sim.set_checkpointing(args.K, args.substeps)
+            fwd.append(timed(lambda: sim.step(args.substeps)))
+            adj.append(timed(lambda: sim.adjoint(args.substeps, observable="polar_order",
+                                                 want_dpsi0=False)))
+        print(json.dumps({"case": "adjoint", "grid": args.grid, "precision": args.precision,
+                          "recorded_forward_ms": fwd, "reverse_sweep_ms": adj}))
 
 
 if __name__ == "__main__":

@@ -70,6 +70,24 @@ def dist_env():
     return world, rank, local
 
 
+def reduce_max(vals, device=None):
+    """Element-wise maximum over the ranks of a list of floats (the timing rule:
+    the slowest rank decides); the identity at world size 1."""
+    import torch
+    world, _, _ = dist_env()
+    t = torch.tensor([float(v) for v in vals], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def whole_job_value(world: int, units_per_rank: float, seconds: float) -> float:
+    """Whole-job throughput: every rank advances its own instance (weak
+    scaling), so the job processes world x units in the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def algorithmic_bytes_per_launch(g, tsize: int) -> int:
     """Bytes one substep launch must move at minimum: Mb read and written once
     (2 * tsize per motor cell); per (cell, theta) psi read and written
@@ -432,18 +450,15 @@ def run_ours(args):
              "fp32": large_run("fp32", 10), "fp64": large_run("fp64", 3)}
     ens = ensemble_run(max(2, min(args.steps, 3)))
 
-    t = torch.tensor([total_ms, kern_ms, fp64_ms, e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    total_ms, kern_ms, fp64_ms, e2e_s = t.tolist()
+    total_ms, kern_ms, fp64_ms, e2e_s = reduce_max([total_ms, kern_ms, fp64_ms, e2e_s], dev)
 
-    value = world * units_per_step * args.steps / (total_ms * 1e-3)
+    value = whole_job_value(world, units_per_step * args.steps, total_ms * 1e-3)
     launch_ms = kern_ms / (args.steps * nsub)
     peak, peak_src = read_peaks()
     algo = algorithmic_bytes_per_launch(g, 4)
     achieved = algo / (launch_ms * 1e-3) / 1e9
     traffic = read_profile_traffic("k_substep", name, "fp32")
-    fp64_value = world * units_per_step * fp64_steps / (fp64_ms * 1e-3)
+    fp64_value = whole_job_value(world, units_per_step * fp64_steps, fp64_ms * 1e-3)
     if rank == 0:
         cpu = time_oracle_sample(name) if world == 1 or rank == 0 else None
         line = {
@@ -465,7 +480,7 @@ def run_ours(args):
                          "kernel_ms_per_launch": launch_ms,
                          "algorithmic_bytes_per_launch": algo},
             "cpu_baseline": cpu,
-            "e2e": {"value": world * units_per_step * args.steps / e2e_s, "unit": UNIT,
+            "e2e": {"value": whole_job_value(world, units_per_step * args.steps, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "adjoint": adj,
             "large512": dict(large, fp32_over_fp64=large["fp32"]["value"] / large["fp64"]["value"],

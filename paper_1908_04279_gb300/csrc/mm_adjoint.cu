@@ -19,8 +19,7 @@
 //     derivative of the branch the forward took, and accumulates the adjoints
 //     of k_off, v_walk and k_on.
 // Limits, order of operations and branch choices follow the oracle's adjoint.
-#include "mm_internal.cuh"
-#include "mm_walk.cuh"
+#include "mm_cell.cuh"
 
 namespace mm {
 
@@ -62,68 +61,72 @@ __device__ __forceinline__ void walk_adj(const T (&ga)[V], const T (&gb)[V], con
   }
 }
 
-#ifndef MM_ADJ_V8_MIN_BLOCKS
-#define MM_ADJ_V8_MIN_BLOCKS 3
+#ifndef MM_ADJ_MOTOR_MIN_BLOCKS
+#define MM_ADJ_MOTOR_MIN_BLOCKS 4
 #endif
 
-// Resident blocks the register budget is sized for: float32 rows of up to 4
-// values per lane fit 128 registers; 8 values per lane and float64 need more.
+// Resident blocks the register budget of the motor kernel is sized for:
+// float32 rows of up to 4 values per lane; 8 values per lane and float64 need
+// more registers.
 template <typename T, int V>
 constexpr int adj_min_blocks() {
-  return sizeof(T) == 8 ? 1 : (V == 8 ? MM_ADJ_V8_MIN_BLOCKS : 4);
+  return sizeof(T) == 8 ? 1 : (V == 8 ? 3 : MM_ADJ_MOTOR_MIN_BLOCKS);
 }
 
-// Adjoint of one substep, one warp per cell (grid-stride over cells).
-// Per-warp shared memory: lam_psi_total and psi^n of the cell, and lam_n_b^n
-// of its rows (3 nth values).
-template <typename T, int V>
-__global__ void __launch_bounds__(128, adj_min_blocks<T, V>()) k_adjoint(const AdjArgs<T> a) {
+// lam_C (the adjoint of the coarse density before the scale-down) and the
+// scale-down factor f of a cell at n+1 (Alg. 2): lam_C = -D / C where the cell
+// clipped (D = sum lam_Mb Mb), else -lam_Mf.
+template <typename T>
+__device__ __forceinline__ void cell_lamc(const AdjArgs<T>& a, int cell, T& lamC, T& f) {
+  const T M = a.mtot[cell], Cp = a.cpre_np[cell];
+  const size_t nc = (size_t)a.ncells;
+  if (M < Cp) {
+    T D = T(0);
+    for (int u = 0; u < a.units; ++u) D += a.D_in[u * nc + cell];
+    f = M / Cp;
+    lamC = -D / Cp;
+  } else {
+    T lmf = T(0);
+    for (int u = 0; u < a.units; ++u) lmf += a.lmf_in[u * nc + cell];
+    f = T(1);
+    lamC = -lmf;
+  }
+}
+
+// Adjoint of one substep, part 1: Eq. 1 and the coupling through C.
+// One warp per cell (grid-stride), lanes over theta. Transposes every
+// donor-cell face flux on the branch the forward took, giving lam_psi^n, the
+// adjoint of n_b^n through the gliding speed (stored, times ds, for part 2),
+// and the cell's accumulated adjoints of u and of its velocity gradient; also
+// stores lam_C and f of the cell for part 2. Per-warp shared memory: the
+// cell's lam_psi_total and psi^n (2 nth values).
+template <typename T>
+__global__ void __launch_bounds__(128) k_adj_psi(const AdjArgs<T> a) {
   extern __shared__ __align__(16) unsigned char adj_smem[];
-  const int nth = a.nth, ns = a.ns, seg = a.seg;
+  const int nth = a.nth;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  T* s_lt = reinterpret_cast<T*>(adj_smem) + (size_t)wib * 3 * nth;
+  T* s_lt = reinterpret_cast<T*>(adj_smem) + (size_t)wib * 2 * nth;
   T* s_psi = s_lt + nth;
-  T* s_lnb = s_psi + nth;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
   const int W = gridDim.x * (blockDim.x >> 5);
   const int nc = (int)a.ncells, nx = a.nx, ny = a.ny;
-  const int sl = lane & (seg - 1), rslot = lane / seg, rpp = 32 / seg;
-  const int nl = ns / V;
-  const bool first = sl == 0, last = sl == nl - 1, lane_ok = sl < nl;
-
-  const T dt = (T)a.dt, hdt = (T)(0.5 * a.dt);
-  const T cw = (T)(a.v_walk / a.ds), koff = (T)a.k_off, kon = (T)a.k_on;
+  const T dt = (T)a.dt;
   const T glide = (T)a.glide, vsp = (T)a.v_sp;
-  const T c1 = hdt * cw, c2 = T(1) - hdt * koff;
   const T dtv = dt * (T)a.inv_dx, dtw = dt * (T)a.inv_dy, dtt = dt * (T)a.inv_dth;
-  const T ds = (T)a.ds, dth = (T)a.dth, inv_ds = (T)(1.0 / a.ds);
+  const T ds = (T)a.ds, dth = (T)a.dth;
   const T* cosk = a.trig;
   const T* sink = a.trig + nth;
   const T* cosf = a.trig + 2 * nth;
   const T* sinf = a.trig + 3 * nth;
-
-  double g_koff = 0.0, g_v = 0.0, g_kon = 0.0;
 
   for (int cell = gw; cell < nc; cell += W) {
     const int iy = cell / nx, ix = cell - iy * nx;
     const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
     const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
     const int nbr[5] = {cell, iy * nx + xp, iy * nx + xm, yp * nx + ix, ym * nx + ix};
-    // adjoint of the pre-scale-down coarse density and the scale factor, for
-    // the cell and its 4 neighbours
     T lamC[5], fsc[5];
 #pragma unroll
-    for (int q = 0; q < 5; ++q) {
-      const int j = nbr[q];
-      const T M = a.mtot[j], Cp = a.cpre_np[j];
-      if (M < Cp) {
-        fsc[q] = M / Cp;
-        lamC[q] = -a.D_in[j] / Cp;
-      } else {
-        fsc[q] = T(1);
-        lamC[q] = -a.lmf_in[j];
-      }
-    }
+    for (int q = 0; q < 5; ++q) cell_lamc(a, nbr[q], lamC[q], fsc[q]);
     // lam_psi_total = lam_psi^{n+1} + lam_C n_b** dtheta (n_b** = n_b^{n+1} / f)
     auto lam_tot = [&](int q, int k) -> T {
       const size_t r = (size_t)nbr[q] * nth + k;
@@ -135,7 +138,6 @@ __global__ void __launch_bounds__(128, adj_min_blocks<T, V>()) k_adjoint(const A
     }
     __syncwarp();
 
-    // ---- transpose of Eq. 1 (donor-cell flux form)
     const T* uc = a.ucell + (size_t)cell * 12;
     const T uxc = uc[0], uyc = uc[1], uxe = uc[2], uxw = uc[3], uyn = uc[4], uys = uc[5];
     const T Gxx = uc[6], Gxy = uc[7], Gyx = uc[8], Gyy = uc[9];
@@ -174,7 +176,7 @@ __global__ void __launch_bounds__(128, adj_min_blocks<T, V>()) k_adjoint(const A
       const T lax = T(0.5) * (lAe + lAw), lay = T(0.5) * (lAn + lAs);
       lux += lax;
       luy += lay;
-      s_lnb[k] = -glide * (ck * lax + sk * lay);
+      a.lnb[rc] = -glide * (ck * lax + sk * lay) * ds;
       // rotation at the face k+1/2 owned by this orientation
       const T lw = (wp > T(0) ? pc : s_psi[kp]) * lFp;
       lG0 += lw * (-sp * cp);
@@ -182,124 +184,384 @@ __global__ void __launch_bounds__(128, adj_min_blocks<T, V>()) k_adjoint(const A
       lG2 += lw * (cp * cp);
       lG3 += lw * (cp * sp);
     }
-    {
-      const double dlux = (double)warp_sum_t(lux), dluy = (double)warp_sum_t(luy);
-      const double d0 = (double)warp_sum_t(lG0), d1 = (double)warp_sum_t(lG1);
-      const double d2 = (double)warp_sum_t(lG2), d3 = (double)warp_sum_t(lG3);
-      if (lane == 0) {
-        a.lamu[cell] += dlux;
-        a.lamu[nc + cell] += dluy;
-        a.lamG[(size_t)cell * 4 + 0] += d0;
-        a.lamG[(size_t)cell * 4 + 1] += d1;
-        a.lamG[(size_t)cell * 4 + 2] += d2;
-        a.lamG[(size_t)cell * 4 + 3] += d3;
-      }
+    const double dlux = (double)warp_sum_t(lux), dluy = (double)warp_sum_t(luy);
+    const double d0 = (double)warp_sum_t(lG0), d1 = (double)warp_sum_t(lG1);
+    const double d2 = (double)warp_sum_t(lG2), d3 = (double)warp_sum_t(lG3);
+    if (lane == 0) {
+      a.lamu[cell] += dlux;
+      a.lamu[nc + cell] += dluy;
+      a.lamG[(size_t)cell * 4 + 0] += d0;
+      a.lamG[(size_t)cell * 4 + 1] += d1;
+      a.lamG[(size_t)cell * 4 + 2] += d2;
+      a.lamG[(size_t)cell * 4 + 3] += d3;
+      a.cellc[(size_t)cell * 2 + 0] = lamC[0];
+      a.cellc[(size_t)cell * 2 + 1] = fsc[0];
     }
     __syncwarp();
+  }
+}
 
-    // ---- transpose of Eq. 4 (midpoint RK2) on every row of the cell
-    const T mf_n = a.mf_n[cell];
-    const T c3 = hdt * kon * mf_n;
-    const T lamC_c = lamC[0], f_c = fsc[0];
-    T lmf_acc = T(0), D_acc = T(0);
-    T gk = T(0), gv = T(0), gn = T(0);
-    // rows of the next group are loaded one iteration ahead
-    T Mq[V], Lq[V];
-    auto load_rows = [&](int r0) {
-      const int k = r0 + rslot;
-      const bool act = k < nth && lane_ok;
+// Constants of the motor part of one reverse substep.
+template <typename T>
+struct MotorConst {
+  T dt, hdt, cw, koff, kon, c1, c2, ds, dth;
+};
+
+// Per-warp accumulators of the motor part: the unit's sums of lam_Mf and D,
+// and the parameter adjoints (k_off, v_walk times ds, k_on).
+template <typename T>
+struct MotorAcc {
+  T lmf, D, gk, gv, gn;
+};
+
+// The reverse of Eq. 4 on one group of rows (V nodes per lane): M = Mb^n and
+// L = lam_Mb^{n+1} of the lane's nodes, psi1 = psi^{n+1} and lnb = lam_n_b^n ds
+// of the lane's row; returns lam_Mb^n of the nodes in `out`. Recomputes the
+// RK2 stage with the forward's arithmetic and Superbee branches, then applies
+// the transposed Jacobians of both stages.
+template <typename T, int V>
+__device__ __forceinline__ void motor_rows(const T (&M)[V], T (&L)[V], T psi1, T lnb, bool act,
+                                           bool first, bool last, int seg, const MotorConst<T>& m,
+                                           T c3, T mf_n, T lamC_c, T f_c, MotorAcc<T>& acc,
+                                           Pack<T, V>& out) {
+  T Dn[V], Ds[V], Ms[V], gan[V], gbn[V], gas[V], gbs[V];
+  walk_dflux<T, V, true>(M, Dn, first, last, seg, gan, gbn);
+#pragma unroll
+  for (int v = 0; v < V; ++v) Ms[v] = fma_t(m.c1, Dn[v], fma_t(m.c2, M[v], c3));
+  walk_dflux<T, V, true>(Ms, Ds, first, last, seg, gas, gbs);
+  // lam_Mb** = f lam_Mb' + lam_C psi^{n+1} dtheta ds (through C and the scale-down)
+  const T add = act ? lamC_c * psi1 * m.dth * m.ds : T(0);
+  T y1[V], zs[V], y2[V], zn[V];
+  T sy1 = T(0), sy2 = T(0);
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    L[v] = f_c * L[v] + add;  // lam_Mb**
+    y1[v] = m.dt * L[v];
+    sy1 += y1[v];
+  }
+  walk_adj<T, V>(gas, gbs, y1, zs, first, last, seg, m.cw);
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    zs[v] -= m.koff * y1[v];  // lam_Ms = J_R(Ms)^T y1
+    acc.gk -= Ms[v] * y1[v];
+    acc.gv = fma_t(Ds[v], y1[v], acc.gv);
+    y2[v] = m.hdt * zs[v];
+    sy2 += y2[v];
+  }
+  walk_adj<T, V>(gan, gbn, y2, zn, first, last, seg, m.cw);
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    acc.gk -= M[v] * y2[v];
+    acc.gv = fma_t(Dn[v], y2[v], acc.gv);
+    const T lm = L[v] + zs[v] + zn[v] - m.koff * y2[v] + lnb;
+    out.v[v] = lm;
+    acc.D = fma_t(lm, M[v], acc.D);
+  }
+  if (act) {
+    acc.lmf += m.kon * (sy1 + sy2);
+    acc.gn += mf_n * (sy1 + sy2);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ MotorConst<T> motor_const(const AdjArgs<T>& a) {
+  MotorConst<T> m;
+  m.dt = (T)a.dt;
+  m.hdt = (T)(0.5 * a.dt);
+  m.cw = (T)(a.v_walk / a.ds);
+  m.koff = (T)a.k_off;
+  m.kon = (T)a.k_on;
+  m.c1 = m.hdt * m.cw;
+  m.c2 = T(1) - m.hdt * m.koff;
+  m.ds = (T)a.ds;
+  m.dth = (T)a.dth;
+  return m;
+}
+
+// End of a unit: its partial sums of lam_Mf and D.
+template <typename T>
+__device__ __forceinline__ void close_unit(const AdjArgs<T>& a, MotorAcc<T>& acc, int lane, int u,
+                                           int cell) {
+  const T lmf = warp_sum_t(acc.lmf);
+  const T Dsum = warp_sum_t(acc.D);
+  if (lane == 0) {
+    a.lmf_out[(size_t)u * a.ncells + cell] = lmf;
+    a.D_out[(size_t)u * a.ncells + cell] = Dsum;
+  }
+  acc.lmf = T(0);
+  acc.D = T(0);
+}
+
+// The warp's parameter adjoints into its float64 slot.
+template <typename T>
+__device__ __forceinline__ void flush_params(const AdjArgs<T>& a, const MotorAcc<T>& acc, int lane,
+                                             int gw) {
+  const double gk = warp_sum((double)acc.gk);
+  const double gv = warp_sum((double)acc.gv) / a.ds;  // dR/dv_walk = D / ds
+  const double gn = warp_sum((double)acc.gn);
+  if (lane == 0) {
+    a.gpart[(size_t)gw * 4 + 0] += gk;
+    a.gpart[(size_t)gw * 4 + 1] += gv;
+    a.gpart[(size_t)gw * 4 + 2] += gn;
+  }
+}
+
+// Adjoint of one substep, part 2: Eq. 4 (midpoint RK2) on the rows, with the
+// coupling through C and the scale-down, rows read with plain loads (any ns).
+// One warp per (cell, block of rows_per_unit rows) unit, grid-stride; the
+// items (unit, group of rows) of a warp form one flat loop whose loads run
+// one item ahead. The unit's partial sums of lam_Mf and D go to slot u of the
+// [units][cells] partials; the parameter adjoints accumulate per warp.
+template <typename T, int V>
+__global__ void __launch_bounds__(128, adj_min_blocks<T, V>()) k_adj_motor(const AdjArgs<T> a) {
+  const int nth = a.nth, ns = a.ns, seg = a.seg;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  const int W = gridDim.x * (blockDim.x >> 5);
+  const int nc = (int)a.ncells;
+  const int U = a.units, RU = a.rows_per_unit;
+  const int nunits = nc * U;
+  int lgU = 0;
+  while ((1 << lgU) < U) ++lgU;
+  const int sl = lane & (seg - 1), rslot = lane / seg, rpp = 32 / seg;
+  const int nl = ns / V;
+  const bool first = sl == 0, last = sl == nl - 1, lane_ok = sl < nl;
+  const MotorConst<T> m = motor_const(a);
+
+  const int G = (RU + rpp - 1) / rpp;
+  const int my_units = gw < nunits ? (nunits - 1 - gw) / W + 1 : 0;
+  const int nitems = my_units * G;
+  MotorAcc<T> acc{T(0), T(0), T(0), T(0), T(0)};
+  T Mq[V], Lq[V], psiq = T(0), lnbq = T(0), mfq = T(0), lcq = T(0), fq = T(1);
+  int q_unit = gw, q_g = 0;  // item whose loads are in flight
+  auto load_item = [&]() {
+    const int cell = q_unit >> lgU, u = q_unit & (U - 1);
+    const int k0 = u * RU, k1 = min(nth, k0 + RU);
+    const int k = k0 + q_g * rpp + rslot;
+    const bool row_ok = k < k1, act = row_ok && lane_ok;
+    if (act) {
+      const size_t off = ((size_t)cell * nth + k) * ns + (size_t)sl * V;
+      const Pack<T, V> qm = *reinterpret_cast<const Pack<T, V>*>(a.mb_n + off);
+      const Pack<T, V> ql = *reinterpret_cast<const Pack<T, V>*>(a.lmb + off);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        Mq[v] = qm.v[v];
+        Lq[v] = ql.v[v];
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        Mq[v] = T(0);
+        Lq[v] = T(0);
+      }
+    }
+    psiq = row_ok ? a.psi_np[(size_t)cell * nth + k] : T(0);
+    lnbq = row_ok ? a.lnb[(size_t)cell * nth + k] : T(0);
+    if (q_g == 0) {
+      mfq = a.mf_n[cell];
+      lcq = a.cellc[(size_t)cell * 2];
+      fq = a.cellc[(size_t)cell * 2 + 1];
+    }
+  };
+  if (nitems > 0) load_item();
+  T mf_n = T(0), c3 = T(0), lamC_c = T(0), f_c = T(1);
+  for (int it = 0; it < nitems; ++it) {
+    const int unit = q_unit, g = q_g;
+    const int cell = unit >> lgU, u = unit & (U - 1);
+    const int k0 = u * RU, k1 = min(nth, k0 + RU);
+    const int k = k0 + g * rpp + rslot;
+    const bool row_ok = k < k1, act = row_ok && lane_ok;
+    const size_t off = ((size_t)cell * nth + (row_ok ? k : k0)) * ns + (size_t)sl * V;
+    T M[V], L[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      M[v] = Mq[v];
+      L[v] = Lq[v];
+    }
+    const T psi1 = psiq, lnb = lnbq;
+    if (g == 0) {
+      mf_n = mfq;
+      c3 = m.hdt * m.kon * mf_n;
+      lamC_c = lcq;
+      f_c = fq;
+    }
+    if (++q_g == G) {
+      q_g = 0;
+      q_unit += W;
+    }
+    if (it + 1 < nitems) load_item();
+    Pack<T, V> qo;
+    motor_rows<T, V>(M, L, psi1, lnb, act, first, last, seg, m, c3, mf_n, lamC_c, f_c, acc, qo);
+    if (act) *reinterpret_cast<Pack<T, V>*>(a.lmb + off) = qo;
+    if (g == G - 1) close_unit(a, acc, lane, u, cell);
+  }
+  flush_params(a, acc, lane, gw);
+}
+
+// The same, with the rows streamed by bulk copies (needs 16-byte rows and
+// columns: ns * sizeof(T) and RC * sizeof(T) multiples of 16). Each unit is
+// CH chunks of RC rows; a chunk is one ring stage holding the rows of Mb^n and
+// lam_Mb^{n+1} and the RC values of psi^{n+1} and lam_n_b of its rows, all
+// completing on the stage's mbarrier; lane 0 keeps up to S chunks in flight
+// ahead of the warp, across unit boundaries. The cell scalars of the next
+// unit are loaded one unit ahead. Waits are bounded (DevParams::wait_limit);
+// a warp whose wait runs out records the failure, drains its copies and
+// leaves. Per-warp shared memory: S + 1 mbarriers and S stages.
+template <typename T, int V>
+__global__ void __launch_bounds__(128, adj_min_blocks<T, V>())
+    k_adj_motor_ring(const AdjArgs<T> a, int RC, int CH, int S) {
+  extern __shared__ __align__(128) unsigned char ring_smem[];
+  const int nth = a.nth, ns = a.ns, seg = a.seg;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int rows_elems = RC * ns;
+  const size_t stage_bytes = (size_t)(2 * rows_elems + 2 * RC) * sizeof(T);
+  const size_t bars_bytes = ((size_t)(S + 1) * 8 + 127) & ~(size_t)127;
+  const size_t warp_bytes = bars_bytes + (size_t)S * stage_bytes;
+  unsigned char* wbase = ring_smem + (size_t)wib * warp_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wbase);
+  uint64_t* never = bars + S;
+  unsigned char* stages = wbase + bars_bytes;
+
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  const int W = gridDim.x * (blockDim.x >> 5);
+  const int nc = (int)a.ncells;
+  const int U = a.units, RU = a.rows_per_unit;
+  const int nunits = nc * U;
+  int lgU = 0;
+  while ((1 << lgU) < U) ++lgU;
+  const int sl = lane & (seg - 1), rslot = lane / seg, rpp = 32 / seg;
+  const int nl = ns / V;
+  const bool first = sl == 0, last = sl == nl - 1, lane_ok = sl < nl;
+  const MotorConst<T> m = motor_const(a);
+  const uint32_t wait_limit = a.prm->wait_limit;
+  const bool wait_never = (a.prm->debug_flags & 1u) != 0;
+
+  const int my_units = gw < nunits ? (nunits - 1 - gw) / W + 1 : 0;
+  const int nchunks = my_units * CH;
+  const uint32_t rows_bytes = (uint32_t)(rows_elems * sizeof(T));
+  const uint32_t col_bytes = (uint32_t)(RC * sizeof(T));
+
+  // producer cursor (lane 0): unit and chunk of the next copy
+  int p_unit = gw, p_c = 0, istage = 0, issued = 0;
+  auto issue_next = [&]() {
+    const int cell = p_unit >> lgU, u = p_unit & (U - 1);
+    const int k = u * RU + p_c * RC;  // first row of the chunk
+    const size_t roff = ((size_t)cell * nth + k) * ns;
+    const size_t coff = (size_t)cell * nth + k;
+    unsigned char* st = stages + (size_t)istage * stage_bytes;
+    mbar_expect_tx(&bars[istage], 2 * rows_bytes + 2 * col_bytes);
+    bulk_g2s(st, a.mb_n + roff, rows_bytes, &bars[istage]);
+    bulk_g2s(st + rows_bytes, a.lmb + roff, rows_bytes, &bars[istage]);
+    bulk_g2s(st + 2 * (size_t)rows_bytes, a.psi_np + coff, col_bytes, &bars[istage]);
+    bulk_g2s(st + 2 * (size_t)rows_bytes + col_bytes, a.lnb + coff, col_bytes, &bars[istage]);
+    ++issued;
+    if (++p_c == CH) {
+      p_c = 0;
+      p_unit += W;
+    }
+    if (++istage == S) istage = 0;
+  };
+  if (lane == 0) {
+    for (int q = 0; q <= S; ++q) mbar_init(&bars[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    while (issued < S && issued < nchunks) issue_next();
+  }
+  __syncwarp();
+
+  MotorAcc<T> acc{T(0), T(0), T(0), T(0), T(0)};
+  // cell scalars of the current and the next unit
+  T mfq = T(0), lcq = T(0), fq = T(1);
+  auto load_scalars = [&](int unit) {
+    const int cell = unit >> lgU;
+    mfq = a.mf_n[cell];
+    lcq = a.cellc[(size_t)cell * 2];
+    fq = a.cellc[(size_t)cell * 2 + 1];
+  };
+  if (my_units > 0) load_scalars(gw);
+  int unit = gw - W, c = CH - 1, s = 0;
+  uint32_t par = 0;
+  bool timed_out = false;
+  int fail_stage = 0, fail_left = 0;
+  uint32_t fail_par = 0;
+  T mf_n = T(0), c3 = T(0), lamC_c = T(0), f_c = T(1);
+  for (int t = 0; t < nchunks; ++t) {
+    if (++c == CH) {
+      c = 0;
+      unit += W;
+      mf_n = mfq;
+      c3 = m.hdt * m.kon * mf_n;
+      lamC_c = lcq;
+      f_c = fq;
+      if (unit + W < nunits) load_scalars(unit + W);
+    }
+    const int cell = unit >> lgU, u = unit & (U - 1);
+    const bool ok = __all_sync(0xffffffffu, wait_never ? mbar_wait(never, 0u, wait_limit)
+                                                       : mbar_wait(&bars[s], par, wait_limit));
+    if (!ok) {
+      timed_out = true;
+      fail_stage = s;
+      fail_par = par;
+      fail_left = issued - t;
+      break;
+    }
+    const unsigned char* st = stages + (size_t)s * stage_bytes;
+    const T* sM = reinterpret_cast<const T*>(st);
+    const T* sL = reinterpret_cast<const T*>(st + rows_bytes);
+    const T* sP = reinterpret_cast<const T*>(st + 2 * (size_t)rows_bytes);
+    const T* sN = reinterpret_cast<const T*>(st + 2 * (size_t)rows_bytes + col_bytes);
+    const int kc = u * RU + c * RC;  // first row of the chunk
+    for (int p = 0; p * rpp < RC; ++p) {
+      const int r = p * rpp + rslot;
+      const bool row_ok = r < RC, act = row_ok && lane_ok;
+      const int off = (row_ok ? r : 0) * ns + sl * V;
+      T M[V], L[V];
       if (act) {
-        const size_t off = ((size_t)cell * nth + k) * ns + (size_t)sl * V;
-        const Pack<T, V> qm = *reinterpret_cast<const Pack<T, V>*>(a.mb_n + off);
-        const Pack<T, V> ql = *reinterpret_cast<const Pack<T, V>*>(a.lmb + off);
+        const Pack<T, V> qm = *reinterpret_cast<const Pack<T, V>*>(sM + off);
+        const Pack<T, V> ql = *reinterpret_cast<const Pack<T, V>*>(sL + off);
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          Mq[v] = qm.v[v];
-          Lq[v] = ql.v[v];
+          M[v] = qm.v[v];
+          L[v] = ql.v[v];
         }
       } else {
 #pragma unroll
         for (int v = 0; v < V; ++v) {
-          Mq[v] = T(0);
-          Lq[v] = T(0);
+          M[v] = T(0);
+          L[v] = T(0);
         }
       }
-    };
-    load_rows(0);
-    for (int r0 = 0; r0 < nth; r0 += rpp) {
-      const int k = r0 + rslot;
-      const bool row_ok = k < nth, act = row_ok && lane_ok;
-      const size_t off = ((size_t)cell * nth + (row_ok ? k : 0)) * ns + (size_t)sl * V;
-      T M[V], L[V];
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        M[v] = Mq[v];
-        L[v] = Lq[v];
-      }
-      const T psi1 = row_ok ? a.psi_np[(size_t)cell * nth + k] : T(0);
-      const T lnb = row_ok ? s_lnb[k] * ds : T(0);
-      if (r0 + rpp < nth) load_rows(r0 + rpp);
-      // forward recompute: Ms = M + (dt/2) R(M), with the Superbee branch of
-      // both stages
-      T Dn[V], Ds[V], Ms[V], gan[V], gbn[V], gas[V], gbs[V];
-      walk_dflux<T, V, true>(M, Dn, first, last, seg, gan, gbn);
-#pragma unroll
-      for (int v = 0; v < V; ++v) Ms[v] = fma_t(c1, Dn[v], fma_t(c2, M[v], c3));
-      walk_dflux<T, V, true>(Ms, Ds, first, last, seg, gas, gbs);
-      // lam_Mb** = f lam_Mb' + lam_C psi^{n+1} dtheta ds (through C and the scale-down)
-      const T add = act ? lamC_c * psi1 * dth * ds : T(0);
-      T y1[V], zs[V], y2[V], zn[V];
-      T sy1 = T(0), sy2 = T(0);
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        L[v] = f_c * L[v] + add;  // lam_Mb**
-        y1[v] = dt * L[v];
-        sy1 += y1[v];
-      }
-      walk_adj<T, V>(gas, gbs, y1, zs, first, last, seg, cw);
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        zs[v] -= koff * y1[v];  // lam_Ms = J_R(Ms)^T y1
-        gk -= Ms[v] * y1[v];
-        gv += Ds[v] * inv_ds * y1[v];
-        y2[v] = hdt * zs[v];
-        sy2 += y2[v];
-      }
-      walk_adj<T, V>(gan, gbn, y2, zn, first, last, seg, cw);
+      const T psi1 = row_ok ? sP[r] : T(0);
+      const T lnb = row_ok ? sN[r] : T(0);
       Pack<T, V> qo;
-#pragma unroll
-      for (int v = 0; v < V; ++v) {
-        gk -= M[v] * y2[v];
-        gv += Dn[v] * inv_ds * y2[v];
-        const T lm = L[v] + zs[v] + zn[v] - koff * y2[v] + lnb;
-        qo.v[v] = lm;
-        D_acc = fma_t(lm, M[v], D_acc);
-      }
-      if (act) *reinterpret_cast<Pack<T, V>*>(a.lmb + off) = qo;
-      if (act) {
-        lmf_acc += kon * (sy1 + sy2);
-        gn += mf_n * (sy1 + sy2);
-      }
+      motor_rows<T, V>(M, L, psi1, lnb, act, first, last, seg, m, c3, mf_n, lamC_c, f_c, acc, qo);
+      if (act)
+        *reinterpret_cast<Pack<T, V>*>(a.lmb + ((size_t)cell * nth + kc + r) * ns + sl * V) = qo;
     }
-    const T lmf = warp_sum_t(lmf_acc);
-    const T Dsum = warp_sum_t(D_acc);
+    __syncwarp();
+    // the stage is consumed: refill it with the chunk S ahead
+    if (lane == 0 && issued < nchunks) issue_next();
+    if (++s == S) {
+      s = 0;
+      par ^= 1u;
+    }
+    if (c == CH - 1) close_unit(a, acc, lane, u, cell);
+  }
+  if (timed_out) {
     if (lane == 0) {
-      a.lmf_out[cell] = lmf;
-      a.D_out[cell] = Dsum;
+      atomicOr(&a.prm->status, 1);
+      int st = fail_stage;
+      uint32_t pp = fail_par;
+      for (int i = 0; i < fail_left; ++i) {
+        (void)mbar_wait(&bars[st], pp, kDrainLimit);
+        if (++st == S) {
+          st = 0;
+          pp ^= 1u;
+        }
+      }
     }
-    g_koff += (double)gk;
-    g_v += (double)gv;
-    g_kon += (double)gn;
     __syncwarp();
   }
-  g_koff = warp_sum(g_koff);
-  g_v = warp_sum(g_v);
-  g_kon = warp_sum(g_kon);
-  if (lane == 0) {
-    a.gpart[(size_t)gw * 4 + 0] += g_koff;
-    a.gpart[(size_t)gw * 4 + 1] += g_v;
-    a.gpart[(size_t)gw * 4 + 2] += g_kon;
-  }
+  flush_params(a, acc, lane, gw);
 }
 
 // Seeds of the reverse sweep at the final state.
@@ -377,35 +639,82 @@ __global__ void k_adj_finish(const double* lamG, const double* lamu, double* dLd
   }
 }
 
-// dL/dpsi0 = lam_psi^0 - lam_Mf^0 n_b^0 dtheta (Mf^0 = M - sum psi^0 n_b^0 dtheta).
+// dL/dpsi0 = lam_psi^0 - lam_Mf^0 n_b^0 dtheta (Mf^0 = M - sum psi^0 n_b^0 dtheta),
+// lam_Mf^0 the sum of its `units` partials.
 template <typename T>
-__global__ void k_adj_psi0(const T* lpsi, const T* lmf, const T* nb, double dth, long long rows,
-                           int nth, double* out) {
+__global__ void k_adj_psi0(const T* lpsi, const T* lmf, int units, const T* nb, double dth,
+                           long long rows, int nth, double* out) {
+  const long long nc = rows / nth;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < rows;
-       r += (long long)gridDim.x * blockDim.x)
-    out[r] = (double)lpsi[r] - (double)lmf[r / nth] * (double)nb[r] * dth;
+       r += (long long)gridDim.x * blockDim.x) {
+    const long long cell = r / nth;
+    T l = T(0);
+    for (int u = 0; u < units; ++u) l += lmf[u * nc + cell];
+    out[r] = (double)lpsi[r] - (double)l * (double)nb[r] * dth;
+  }
 }
 
 }  // namespace
 
+// Shared memory per warp of the ring kernel.
+size_t adj_ring_warp_bytes(int rc, int ns, int S, int tsz) {
+  const size_t bars = ((size_t)(S + 1) * 8 + 127) & ~(size_t)127;
+  return bars + (size_t)S * (size_t)(2 * rc * ns + 2 * rc) * tsz;
+}
+
+// Resident 4-warp blocks per SM of the motor kernel the plan will launch.
 template <typename T>
-cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid, cudaStream_t s) {
-  const int block = 128;
-  const size_t smem = (size_t)4 * 3 * a.nth * sizeof(T);
-  auto go = [&](auto kern) -> cudaError_t {
-    if (smem > 48 * 1024) {
-      cudaError_t e =
-          cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t adj_motor_occupancy(int V, int ring_rc, int ns, int S, int* bps) {
+  const size_t rs =
+      ring_rc > 0 ? 4 * adj_ring_warp_bytes(ring_rc, ns, S, (int)sizeof(T)) : 0;
+  auto occ = [&](auto plain, auto ring) -> cudaError_t {
+    if (ring_rc > 0) {
+      cudaError_t e = cudaFuncSetAttribute(ring, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)rs);
       if (e != cudaSuccess) return e;
+      return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, ring, 128, rs);
     }
-    kern<<<grid, block, smem, s>>>(a);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, plain, 128, 0);
+  };
+  if constexpr (sizeof(T) == 4)
+    if (V == 8) return occ(k_adj_motor<T, 8>, k_adj_motor_ring<T, 8>);
+  if (V == 4) return occ(k_adj_motor<T, 4>, k_adj_motor_ring<T, 4>);
+  if (V == 2) return occ(k_adj_motor<T, 2>, k_adj_motor_ring<T, 2>);
+  return occ(k_adj_motor<T, 1>, k_adj_motor_ring<T, 1>);
+}
+
+template <typename T>
+cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid_psi, int grid_motor,
+                           cudaStream_t s) {
+  const int block = 128;
+  const size_t smem = (size_t)4 * 2 * a.nth * sizeof(T);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_adj_psi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_adj_psi<T><<<grid_psi, block, smem, s>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  auto go = [&](auto plain, auto ring) -> cudaError_t {
+    if (a.ring_rc > 0) {
+      const size_t rs = 4 * adj_ring_warp_bytes(a.ring_rc, a.ns, a.ring_s, (int)sizeof(T));
+      if (rs > 48 * 1024) {
+        cudaError_t e2 =
+            cudaFuncSetAttribute(ring, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+        if (e2 != cudaSuccess) return e2;
+      }
+      ring<<<grid_motor, block, rs, s>>>(a, a.ring_rc, a.ring_ch, a.ring_s);
+    } else {
+      plain<<<grid_motor, block, 0, s>>>(a);
+    }
     return cudaGetLastError();
   };
   if constexpr (sizeof(T) == 4)
-    if (V == 8) return go(k_adjoint<T, 8>);
-  if (V == 4) return go(k_adjoint<T, 4>);
-  if (V == 2) return go(k_adjoint<T, 2>);
-  return go(k_adjoint<T, 1>);
+    if (V == 8) return go(k_adj_motor<T, 8>, k_adj_motor_ring<T, 8>);
+  if (V == 4) return go(k_adj_motor<T, 4>, k_adj_motor_ring<T, 4>);
+  if (V == 2) return go(k_adj_motor<T, 2>, k_adj_motor_ring<T, 2>);
+  return go(k_adj_motor<T, 1>, k_adj_motor_ring<T, 1>);
 }
 
 template <typename T>
@@ -430,22 +739,23 @@ cudaError_t launch_adj_finish(const double* lamG, const double* lamu, double* dL
 }
 
 template <typename T>
-cudaError_t launch_adj_psi0(const T* lpsi, const T* lmf, const T* nb, double dth, long long rows,
-                            int nth, double* out, cudaStream_t s) {
+cudaError_t launch_adj_psi0(const T* lpsi, const T* lmf, int units, const T* nb, double dth,
+                            long long rows, int nth, double* out, cudaStream_t s) {
   long long g = (rows + 255) / 256;
   if (g > 152 * 16) g = 152 * 16;
-  k_adj_psi0<T><<<(int)g, 256, 0, s>>>(lpsi, lmf, nb, dth, rows, nth, out);
+  k_adj_psi0<T><<<(int)g, 256, 0, s>>>(lpsi, lmf, units, nb, dth, rows, nth, out);
   return cudaGetLastError();
 }
 
 #define MM_ADJ_INST(T)                                                                          \
-  template cudaError_t launch_adjoint<T>(const AdjArgs<T>&, int, int, cudaStream_t);            \
+  template cudaError_t launch_adjoint<T>(const AdjArgs<T>&, int, int, int, cudaStream_t);       \
+  template cudaError_t adj_motor_occupancy<T>(int, int, int, int, int*);                        \
   template cudaError_t launch_adj_seed<T>(int, const double*, const T*, const T*, const double*, \
                                           const double*, const double*, const double*, T*, T*,  \
                                           T*, T*, long long, int, int, double, double, const T*, \
                                           cudaStream_t);                                        \
-  template cudaError_t launch_adj_psi0<T>(const T*, const T*, const T*, double, long long, int,  \
-                                          double*, cudaStream_t);
+  template cudaError_t launch_adj_psi0<T>(const T*, const T*, int, const T*, double, long long,  \
+                                          int, double*, cudaStream_t);
 MM_ADJ_INST(float)
 MM_ADJ_INST(double)
 

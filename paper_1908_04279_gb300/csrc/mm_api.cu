@@ -876,6 +876,14 @@ mm::AdjArgs<T> adj_args(mm_handle* h, int slot, int ver, double dt, int cur) {
   a.lamG = R.v_lamG[ver];
   a.lamu = R.v_lamu[ver];
   a.gpart = R.gpart;
+  a.units = R.units;
+  a.rows_per_unit = R.rows_per_unit;
+  a.lnb = (T*)R.lnb;
+  a.cellc = (T*)R.cellc;
+  a.prm = h->prm;
+  a.ring_rc = R.ring_rc;
+  a.ring_ch = R.ring_ch;
+  a.ring_s = R.ring_s;
   return a;
 }
 
@@ -901,7 +909,10 @@ void rec_layout(mm_handle* h, Carver& c) {
   R.sl_nb.resize(K + 1);
   R.sl_mf.resize(K + 1);
   R.sl_cpre.resize(K + 1);
-  for (int i = 0; i <= K; ++i) {
+  // slot 0 of a segment is its checkpoint (read in place); slots 1..K are
+  // the recomputed states
+  R.sl_mb[0] = R.sl_psi[0] = R.sl_nb[0] = R.sl_mf[0] = R.sl_cpre[0] = nullptr;
+  for (int i = 1; i <= K; ++i) {
     R.sl_mb[i] = c.take(h->mbn * t);
     R.sl_psi[i] = c.take(rows * t);
     R.sl_nb[i] = c.take(rows * t);
@@ -912,10 +923,12 @@ void rec_layout(mm_handle* h, Carver& c) {
   R.lmb = c.take(h->mbn * t);
   for (int i = 0; i < 2; ++i) {
     R.lpsi[i] = c.take(rows * t);
-    R.lmf[i] = c.take(nc * t);
-    R.Dd[i] = c.take(nc * t);
+    R.lmf[i] = c.take((size_t)R.units * nc * t);
+    R.Dd[i] = c.take((size_t)R.units * nc * t);
   }
-  R.gpart = (double*)c.take((size_t)R.adj_grid * 4 * 4 * 8);
+  R.lnb = c.take(rows * t);
+  R.cellc = c.take(2 * nc * t);
+  R.gpart = (double*)c.take((size_t)R.grid_motor * 4 * 4 * 8);
   for (int i = 0; i < 3; ++i) R.seed[i] = (double*)c.take(rows * 8);
   R.seed[3] = (double*)c.take(nc * 8);
   R.coef = (double*)c.take(64);
@@ -946,7 +959,44 @@ mm_status mm_set_checkpointing(mm_handle* h, int K, int max_substeps) {
     R.K = K;
     R.max_sub = max_substeps;
     R.nck = (max_substeps + K - 1) / K + 1;
-    R.adj_grid = (int)std::min<long long>((h->ncells + 3) / 4, 8LL * h->sms);
+    // reverse kernels: the psi part one warp per cell; the motor part one warp
+    // per block of rows, with enough blocks per cell (a power of two, at least
+    // one pass of rows each) for about six waves of warps
+    const int rpp = 32 / adj_seg(h);
+    int U = 1;
+    while (U < MM_ADJ_MAX_UNITS && h->ncells * U < 6LL * 16 * h->sms &&
+           h->g.ntheta / (2 * U) >= rpp)
+      U *= 2;
+    R.units = U;
+    R.rows_per_unit = (h->g.ntheta + U - 1) / U;
+    R.grid_psi = (int)std::min<long long>((h->ncells + 3) / 4, 16LL * h->sms);
+    R.grid_motor = (int)std::min<long long>((h->ncells * U + 3) / 4, 16LL * h->sms);
+    // bulk-copy ring for the motor kernel: 16-byte rows and row-column slices,
+    // chunks of RC rows (dividing a unit) of at most 2 KB per array
+    R.ring_rc = R.ring_ch = R.ring_s = 0;
+    const size_t row_b = (size_t)h->g.ns * h->tsz;
+    if (MM_ADJ_RING && ((size_t)adj_V(h) * h->tsz) % 16 == 0 && h->g.ntheta % U == 0) {
+      for (int rc = R.rows_per_unit; rc >= 1; --rc)
+        if (R.rows_per_unit % rc == 0 && (rc * h->tsz) % 16 == 0 && rc * row_b <= 2048) {
+          R.ring_rc = rc;
+          break;
+        }
+      if (R.ring_rc > 0) {
+        R.ring_ch = R.rows_per_unit / R.ring_rc;
+        R.ring_s = (int)std::max<size_t>(2, std::min<size_t>(8, 8192 / (2 * R.ring_rc * row_b)));
+        if (4 * mm::adj_ring_warp_bytes(R.ring_rc, h->g.ns, R.ring_s, (int)h->tsz) > kSmemBudget)
+          R.ring_rc = R.ring_ch = R.ring_s = 0;
+      }
+    }
+    // persistent motor grid: the resident blocks (each warp fills its ring once)
+    int bps = 0;
+    const cudaError_t oe =
+        h->prec == MM_FP64
+            ? mm::adj_motor_occupancy<double>(adj_V(h), R.ring_rc, h->g.ns, R.ring_s, &bps)
+            : mm::adj_motor_occupancy<float>(adj_V(h), R.ring_rc, h->g.ns, R.ring_s, &bps);
+    CK(oe);
+    if (bps < 1) return fail(h, MM_ERR_UNSUPPORTED, "reverse kernel cannot be resident");
+    R.grid_motor = (int)std::min<long long>((h->ncells * U + 3) / 4, (long long)bps * h->sms);
     Carver sz;
     rec_layout(h, sz);
     size_t freeb = 0, totalb = 0;
@@ -1047,6 +1097,9 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
       }
     }
   }
+  // the seed fills partial 0 of lam_Mf and D; the other partials start at 0
+  CK(cudaMemsetAsync(R.lmf[0], 0, (size_t)R.units * nc * t, h->stream));
+  CK(cudaMemsetAsync(R.Dd[0], 0, (size_t)R.units * nc * t, h->stream));
   cudaError_t e;
   if (f64)
     e = mm::launch_adj_seed<double>(kind, R.coef, (const double*)h->psi[h->parity],
@@ -1065,17 +1118,17 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
     CK(cudaMemsetAsync(R.v_lamG[v], 0, 4 * nc * 8, h->stream));
     CK(cudaMemsetAsync(R.v_lamu[v], 0, 2 * nc * 8, h->stream));
   }
-  CK(cudaMemsetAsync(R.gpart, 0, (size_t)R.adj_grid * 4 * 4 * 8, h->stream));
+  CK(cudaMemsetAsync(R.gpart, 0, (size_t)R.grid_motor * 4 * 4 * 8, h->stream));
 
   // ---- segments, last first
   int cur = 0, dt_ver = -1;
   const int nseg = (n + R.K - 1) / R.K;
   for (int sgi = nseg - 1; sgi >= 0; --sgi) {
     const int s0 = sgi * R.K, s1 = std::min(s0 + R.K, n);
-    CK(cudaMemcpyAsync(R.sl_mb[0], R.ck_mb[sgi], h->mbn * t, cudaMemcpyDeviceToDevice, h->stream));
-    CK(cudaMemcpyAsync(R.sl_psi[0], R.ck_psi[sgi], rows * t, cudaMemcpyDeviceToDevice, h->stream));
-    CK(cudaMemcpyAsync(R.sl_nb[0], R.ck_nb[sgi], rows * t, cudaMemcpyDeviceToDevice, h->stream));
-    CK(cudaMemcpyAsync(R.sl_mf[0], R.ck_mf[sgi], nc * t, cudaMemcpyDeviceToDevice, h->stream));
+    R.sl_mb[0] = R.ck_mb[sgi];
+    R.sl_psi[0] = R.ck_psi[sgi];
+    R.sl_nb[0] = R.ck_nb[sgi];
+    R.sl_mf[0] = R.ck_mf[sgi];
     CK(cudaMemcpyAsync(&h->prm->psi_scale, R.ck_scale + sgi, 8, cudaMemcpyDeviceToDevice,
                        h->stream));
     for (int tt = s0; tt < s1; ++tt) {
@@ -1092,10 +1145,10 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
       const int i = tt - s0, ver = R.sub_vel[tt];
       if (f64)
         e = mm::launch_adjoint<double>(adj_args<double>(h, i, ver, vdt[ver], cur), adj_V(h),
-                                       R.adj_grid, h->stream);
+                                       R.grid_psi, R.grid_motor, h->stream);
       else
         e = mm::launch_adjoint<float>(adj_args<float>(h, i, ver, vdt[ver], cur), adj_V(h),
-                                      R.adj_grid, h->stream);
+                                      R.grid_psi, R.grid_motor, h->stream);
       CK(e);
       cur ^= 1;
     }
@@ -1121,18 +1174,18 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
   if (out->dL_dpsi0) {
     double* dst = out->on_device ? out->dL_dpsi0 : R.work;
     if (f64)
-      e = mm::launch_adj_psi0<double>((const double*)R.lpsi[cur], (const double*)R.lmf[cur],
+      e = mm::launch_adj_psi0<double>((const double*)R.lpsi[cur], (const double*)R.lmf[cur], R.units,
                                       (const double*)R.sl_nb[0], dth, (long long)rows,
                                       h->g.ntheta, dst, h->stream);
     else
-      e = mm::launch_adj_psi0<float>((const float*)R.lpsi[cur], (const float*)R.lmf[cur],
+      e = mm::launch_adj_psi0<float>((const float*)R.lpsi[cur], (const float*)R.lmf[cur], R.units,
                                      (const float*)R.sl_nb[0], dth, (long long)rows, h->g.ntheta,
                                      dst, h->stream);
     CK(e);
     if (!out->on_device)
       CK(cudaMemcpyAsync(out->dL_dpsi0, R.work, rows * 8, cudaMemcpyDeviceToHost, h->stream));
   }
-  std::vector<double> gp((size_t)R.adj_grid * 4 * 4);
+  std::vector<double> gp((size_t)R.grid_motor * 4 * 4);
   CK(cudaMemcpyAsync(gp.data(), R.gpart, gp.size() * 8, cudaMemcpyDeviceToHost, h->stream));
   if ((st = check_status(h)) != MM_OK) return st;
   out->dL_drates[0] = out->dL_drates[1] = out->dL_drates[2] = 0.0;

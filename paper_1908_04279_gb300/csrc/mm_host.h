@@ -20,6 +20,14 @@ using mm::StepArgs;
 #ifndef MM_FP32_VMAX
 #define MM_FP32_VMAX 8
 #endif
+// 1: the motor reverse kernel streams rows by bulk copies where they allow it.
+#ifndef MM_ADJ_RING
+#define MM_ADJ_RING 1
+#endif
+// Most row blocks per cell of the motor reverse kernel.
+#ifndef MM_ADJ_MAX_UNITS
+#define MM_ADJ_MAX_UNITS 8
+#endif
 // Widest vector of the float32 adjoint kernel.
 #ifndef MM_ADJ_FP32_VMAX
 #define MM_ADJ_FP32_VMAX 4
@@ -59,7 +67,11 @@ struct Recording {
   double* seed[4] = {nullptr, nullptr, nullptr, nullptr};
   double* coef = nullptr;
   double* work = nullptr;  // [rows] float64 scratch for dL/dpsi0
-  int adj_grid = 1;
+  void* lnb = nullptr;    // [rows] adjoint of n_b (times ds) between the two reverse kernels
+  void* cellc = nullptr;  // [cells][2] lam_C and f per cell
+  int units = 1, rows_per_unit = 1;  // row blocks per cell of the motor reverse kernel
+  int grid_psi = 1, grid_motor = 1;  // blocks of 4 warps of the two reverse kernels
+  int ring_rc = 0, ring_ch = 0, ring_s = 0;  // bulk-copy ring of the motor kernel (0: off)
 };
 
 namespace mmh {

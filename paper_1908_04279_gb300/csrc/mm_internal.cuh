@@ -61,10 +61,14 @@ struct StepArgs {
 
 // Everything the adjoint of one substep touches (mm_adjoint.cu). State n is
 // the substep's input, state n+1 its output (both from the recomputed
-// segment); lam_* are the adjoint variables.
+// segment); lam_* are the adjoint variables. The per-cell sums over the rows
+// (lam_Mf and D) are kept as `units` partials per cell, [units][cells], one per
+// block of rows the motor kernel assigns to a warp; readers add them in order.
 template <typename T>
 struct AdjArgs {
   int nx, ny, nth, ns, seg;
+  int units;          // row blocks per cell (power of two)
+  int rows_per_unit;  // rows of one block (the last may be shorter)
   long long ncells;
   double inv_dx, inv_dy, inv_dth, dth, ds, L, dt;
   double v_walk, k_on, k_off, glide, v_sp;
@@ -79,15 +83,21 @@ struct AdjArgs {
   const T* ucell;   // [cells][12]
   const T* trig;    // [4][nth]
   const T* lpsi_in; // adjoint of psi at n+1
-  const T* lmf_in;  // adjoint of Mf at n+1
-  const T* D_in;    // [cells] sum over the cell of lam_Mb * Mb at n+1
+  const T* lmf_in;  // [units][cells] partials of the adjoint of Mf at n+1
+  const T* D_in;    // [units][cells] partials of sum lam_Mb * Mb at n+1
   T* lpsi_out;      // adjoint of psi at n
+  T* lnb;           // [cells][nth] adjoint of n_b^n (times ds), psi kernel -> motor kernel
+  T* cellc;         // [cells][2] lam_C and the scale-down factor f of the cell at n+1
   T* lmb;           // adjoint of Mb: n+1 in, n out (in place)
-  T* lmf_out;       // adjoint of Mf at n
-  T* D_out;         // sum lam_Mb * Mb at n
+  T* lmf_out;       // [units][cells] partials of the adjoint of Mf at n
+  T* D_out;         // [units][cells] partials of sum lam_Mb * Mb at n
   double* lamG;     // [cells][4] accumulated adjoint of the velocity gradient
   double* lamu;     // [2][cells] accumulated direct adjoint of u
   double* gpart;    // [warps][4] accumulated k_off, v_walk, k_on adjoints
+  DevParams* prm;   // status word and wait limit of the bounded waits
+  int ring_rc;      // bulk-copy ring: rows per chunk (0: rows read with plain loads)
+  int ring_ch;      // chunks per unit
+  int ring_s;       // ring stages per warp
 };
 
 // One tile of the batched-ensemble substep: a run of consecutive cells of one
@@ -143,7 +153,11 @@ cudaError_t launch_moments(const T* psi, const T* mb, const T* mf, const T* c,
 
 // Adjoint kernels (mm_adjoint.cu).
 template <typename T>
-cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid, cudaStream_t s);
+cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid_psi, int grid_motor,
+                           cudaStream_t s);
+size_t adj_ring_warp_bytes(int rc, int ns, int S, int tsz);
+template <typename T>
+cudaError_t adj_motor_occupancy(int V, int ring_rc, int ns, int S, int* bps);
 template <typename T>
 cudaError_t launch_adj_seed(int kind, const double* coef, const T* psi, const T* mb,
                             const double* dpsi, const double* dnb, const double* dm1,
@@ -152,8 +166,8 @@ cudaError_t launch_adj_seed(int kind, const double* coef, const T* psi, const T*
 cudaError_t launch_adj_finish(const double* lamG, const double* lamu, double* dLdu, int nx, int ny,
                               double inv_dx, double inv_dy, cudaStream_t s);
 template <typename T>
-cudaError_t launch_adj_psi0(const T* lpsi, const T* lmf, const T* nb, double dth, long long rows,
-                            int nth, double* out, cudaStream_t s);
+cudaError_t launch_adj_psi0(const T* lpsi, const T* lmf, int units, const T* nb, double dth,
+                            long long rows, int nth, double* out, cudaStream_t s);
 
 // Message returned by mm_last_error(NULL) on this thread.
 void set_thread_error(const char* msg);

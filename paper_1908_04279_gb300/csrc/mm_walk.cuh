@@ -78,8 +78,24 @@ __device__ __forceinline__ void walk_dflux(const T (&M)[V], T (&D)[V], bool firs
     const T r = max3_t(t1, t2, T(0));
     F[v] = fma_t(r, sgn, M[v]);
     if constexpr (COEF) {
-      const bool pos = r > T(0), p1 = t1 > t2;
-      const bool x1a = A < hB, x2a = hA < B;
+      bool pos, p1, x1a, x2a;
+      if constexpr (sizeof(T) == 8) {
+        // the same four decisions on the bit patterns (integer pipe instead of
+        // the float64 one): hB, B, r >= 0 order as their signed 64-bit
+        // patterns, a negative A or hA (sign bit set) orders below them, and
+        // the cases where -0 and +0 would differ all have r = 0 (pos false)
+        const long long iA = __double_as_longlong(A), ihA = __double_as_longlong(hA);
+        const long long ihB = __double_as_longlong(hB), iB = __double_as_longlong(B);
+        pos = __double_as_longlong(r) > 0;
+        p1 = __double_as_longlong(t1) > __double_as_longlong(t2);
+        x1a = iA < ihB;
+        x2a = ihA < iB;
+      } else {
+        pos = r > T(0);
+        p1 = t1 > t2;
+        x1a = A < hB;
+        x2a = hA < B;
+      }
       const T a1 = x1a ? T(1) : T(0), b1 = x1a ? T(0) : T(0.5);
       const T a2 = x2a ? T(0.5) : T(0), b2 = x2a ? T(0) : T(1);
       ga[v] = pos ? (p1 ? a1 : a2) : T(0);

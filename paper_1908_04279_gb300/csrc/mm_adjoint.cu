@@ -80,14 +80,16 @@ template <typename T>
 __device__ __forceinline__ void cell_lamc(const AdjArgs<T>& a, int cell, T& lamC, T& f) {
   const T M = a.mtot[cell], Cp = a.cpre_np[cell];
   const size_t nc = (size_t)a.ncells;
+  // both sums are loaded (independent of the branch, so the loads overlap)
+  T D = T(0), lmf = T(0);
+  for (int u = 0; u < a.units; ++u) {
+    D += a.D_in[u * nc + cell];
+    lmf += a.lmf_in[u * nc + cell];
+  }
   if (M < Cp) {
-    T D = T(0);
-    for (int u = 0; u < a.units; ++u) D += a.D_in[u * nc + cell];
     f = M / Cp;
     lamC = -D / Cp;
   } else {
-    T lmf = T(0);
-    for (int u = 0; u < a.units; ++u) lmf += a.lmf_in[u * nc + cell];
     f = T(1);
     lamC = -lmf;
   }
@@ -110,7 +112,7 @@ __global__ void __launch_bounds__(128) k_adj_psi(const AdjArgs<T> a) {
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
   const int W = gridDim.x * (blockDim.x >> 5);
   const int nc = (int)a.ncells, nx = a.nx, ny = a.ny;
-  const T dt = (T)a.dt;
+  const T dt = (T)*a.dt;
   const T glide = (T)a.glide, vsp = (T)a.v_sp;
   const T dtv = dt * (T)a.inv_dx, dtw = dt * (T)a.inv_dy, dtt = dt * (T)a.inv_dth;
   const T ds = (T)a.ds, dth = (T)a.dth;
@@ -124,6 +126,12 @@ __global__ void __launch_bounds__(128) k_adj_psi(const AdjArgs<T> a) {
     const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
     const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
     const int nbr[5] = {cell, iy * nx + xp, iy * nx + xm, yp * nx + ix, ym * nx + ix};
+    // the accumulated velocity adjoints of the cell, read early (lanes 0-5)
+    double acc_old = 0.0;
+    if (lane < 2)
+      acc_old = a.lamu[(size_t)lane * nc + cell];
+    else if (lane < 6)
+      acc_old = a.lamG[(size_t)cell * 4 + (lane - 2)];
     T lamC[5], fsc[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) cell_lamc(a, nbr[q], lamC[q], fsc[q]);
@@ -184,16 +192,17 @@ __global__ void __launch_bounds__(128) k_adj_psi(const AdjArgs<T> a) {
       lG2 += lw * (cp * cp);
       lG3 += lw * (cp * sp);
     }
-    const double dlux = (double)warp_sum_t(lux), dluy = (double)warp_sum_t(luy);
-    const double d0 = (double)warp_sum_t(lG0), d1 = (double)warp_sum_t(lG1);
-    const double d2 = (double)warp_sum_t(lG2), d3 = (double)warp_sum_t(lG3);
+    const T s_ux = warp_sum_t(lux), s_uy = warp_sum_t(luy);
+    const T s_g0 = warp_sum_t(lG0), s_g1 = warp_sum_t(lG1);
+    const T s_g2 = warp_sum_t(lG2), s_g3 = warp_sum_t(lG3);
+    // lane j < 6 adds the j-th of (ux, uy, G0..G3) to its accumulator
+    const T mine = lane == 0 ? s_ux : lane == 1 ? s_uy : lane == 2 ? s_g0
+                 : lane == 3 ? s_g1 : lane == 4 ? s_g2 : s_g3;
+    if (lane < 2)
+      a.lamu[(size_t)lane * nc + cell] = acc_old + (double)mine;
+    else if (lane < 6)
+      a.lamG[(size_t)cell * 4 + (lane - 2)] = acc_old + (double)mine;
     if (lane == 0) {
-      a.lamu[cell] += dlux;
-      a.lamu[nc + cell] += dluy;
-      a.lamG[(size_t)cell * 4 + 0] += d0;
-      a.lamG[(size_t)cell * 4 + 1] += d1;
-      a.lamG[(size_t)cell * 4 + 2] += d2;
-      a.lamG[(size_t)cell * 4 + 3] += d3;
       a.cellc[(size_t)cell * 2 + 0] = lamC[0];
       a.cellc[(size_t)cell * 2 + 1] = fsc[0];
     }
@@ -266,9 +275,10 @@ __device__ __forceinline__ void motor_rows(const T (&M)[V], T (&L)[V], T psi1, T
 template <typename T>
 __device__ __forceinline__ MotorConst<T> motor_const(const AdjArgs<T>& a) {
   MotorConst<T> m;
-  m.dt = (T)a.dt;
-  m.hdt = (T)(0.5 * a.dt);
-  m.cw = (T)(a.v_walk / a.ds);
+  const double dt64 = *a.dt;
+  m.dt = (T)dt64;
+  m.hdt = (T)(0.5 * dt64);
+  m.cw = (T)a.cw;
   m.koff = (T)a.k_off;
   m.kon = (T)a.k_on;
   m.c1 = m.hdt * m.cw;
@@ -292,17 +302,16 @@ __device__ __forceinline__ void close_unit(const AdjArgs<T>& a, MotorAcc<T>& acc
   acc.D = T(0);
 }
 
-// The warp's parameter adjoints into its float64 slot.
+// The warp's parameter adjoints into its float64 slot (reduced over the warp
+// in the state precision, then added in float64; dR/dv_walk = D / ds).
 template <typename T>
 __device__ __forceinline__ void flush_params(const AdjArgs<T>& a, const MotorAcc<T>& acc, int lane,
                                              int gw) {
-  const double gk = warp_sum((double)acc.gk);
-  const double gv = warp_sum((double)acc.gv) / a.ds;  // dR/dv_walk = D / ds
-  const double gn = warp_sum((double)acc.gn);
+  const T gk = warp_sum_t(acc.gk), gv = warp_sum_t(acc.gv), gn = warp_sum_t(acc.gn);
   if (lane == 0) {
-    a.gpart[(size_t)gw * 4 + 0] += gk;
-    a.gpart[(size_t)gw * 4 + 1] += gv;
-    a.gpart[(size_t)gw * 4 + 2] += gn;
+    a.gpart[(size_t)gw * 4 + 0] += (double)gk;
+    a.gpart[(size_t)gw * 4 + 1] += (double)gv * a.inv_ds;
+    a.gpart[(size_t)gw * 4 + 2] += (double)gn;
   }
 }
 
@@ -654,7 +663,53 @@ __global__ void k_adj_psi0(const T* lpsi, const T* lmf, int units, const T* nb, 
   }
 }
 
+// Seed coefficients of a built-in observable (one thread).
+__global__ void k_adj_observable(int kind, const DevParams* prm, double stress_coef,
+                                 double* coef) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0, v = 0.0;
+  if (kind == 1) {
+    // L = |P| / S, P = sum psi e^{i theta}, S = sum psi
+    const double px = prm->scalars[6], py = prm->scalars[7], S = prm->sum_psi;
+    const double pn = sqrt(px * px + py * py);
+    v = pn / S;
+    c0 = -v / S;
+    c1 = pn > 0.0 ? px / pn / S : 0.0;
+    c2 = pn > 0.0 ? py / pn / S : 0.0;
+  } else if (kind == 2) {
+    v = prm->scalars[5];
+    c0 = stress_coef;
+  }
+  coef[0] = c0;
+  coef[1] = c1;
+  coef[2] = c2;
+  coef[3] = v;
+}
+
+// Sum of the per-warp parameter adjoints in warp order (one warp).
+__global__ void k_adj_params(const double* gpart, int nwarps, double* out) {
+  const int lane = threadIdx.x & 31;
+  double g[3] = {0.0, 0.0, 0.0};
+  for (int w = lane; w < nwarps; w += 32)
+    for (int q = 0; q < 3; ++q) g[q] += gpart[(size_t)w * 4 + q];
+  for (int q = 0; q < 3; ++q) {
+    const double r = warp_sum(g[q]);
+    if (lane == 0) out[q] = r;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_adj_observable(int kind, const DevParams* prm, double stress_coef, double* coef,
+                                  cudaStream_t s) {
+  k_adj_observable<<<1, 32, 0, s>>>(kind, prm, stress_coef, coef);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_params(const double* gpart, int nwarps, double* out, cudaStream_t s) {
+  k_adj_params<<<1, 32, 0, s>>>(gpart, nwarps, out);
+  return cudaGetLastError();
+}
 
 // Shared memory per warp of the ring kernel.
 size_t adj_ring_warp_bytes(int rc, int ns, int S, int tsz) {

@@ -46,6 +46,7 @@ mm_status upload_params(mm_handle* h) {
   p.dt = h->dt;
   p.psi_scale = 1.0;
   p.v_walk = h->r.v_walk;
+  p.cw = walk_cw(h);
   p.k_on = h->r.k_on;
   p.k_off = h->r.k_off;
   p.glide = h->r.glide;
@@ -510,6 +511,8 @@ mm_status mm_set_rates(mm_handle* h, const mm_rates* rates) {
   double v[7] = {rates->v_walk, rates->k_on, rates->k_off, rates->glide,
                  rates->v_sp, rates->force_scale, rates->ell};
   CK(cudaMemcpy(&h->prm->v_walk, v, sizeof v, cudaMemcpyHostToDevice));
+  const double cw = walk_cw(h);
+  CK(cudaMemcpy(&h->prm->cw, &cw, sizeof cw, cudaMemcpyHostToDevice));
   return MM_OK;
 }
 
@@ -640,6 +643,16 @@ mm_status mm_micro_step(mm_handle* h, int n) {
   if (!h->have_dt) return fail(h, MM_ERR_STATE, "no dt");
   DeviceGuard dg(h->device);
   if (h->rec.active) return rec_micro_step(h, n);
+  return launch_substeps(h, n);
+}
+
+}  // extern "C"
+
+namespace mmh {
+
+// n substeps on the live state: one captured CUDA graph per (n, parity),
+// replayed (direct launches if graphs are off).
+mm_status launch_substeps(mm_handle* h, int n) {
   if (!h->use_graphs) {
     for (int i = 0; i < n; ++i) {
       CK(launch_one(h, h->parity, h->stream));
@@ -671,6 +684,10 @@ mm_status mm_micro_step(mm_handle* h, int n) {
   h->parity ^= (n & 1);
   return MM_OK;
 }
+
+}  // namespace mmh
+
+extern "C" {
 
 mm_status mm_moments(mm_handle* h, mm_moments_out* out) {
   if (!h || !out) return MM_ERR_INVALID;
@@ -804,11 +821,14 @@ mm_status rec_micro_step(mm_handle* h, int n) {
   Recording& R = h->rec;
   if (R.nsub + n > R.max_sub)
     return fail(h, MM_ERR_STATE, "recording: more substeps than mm_set_checkpointing reserved");
+  // the substeps between checkpoints run as captured graphs
   mm_status st;
-  for (int i = 0; i < n; ++i) {
-    if ((st = rec_push_substep(h)) != MM_OK) return st;
-    CK(launch_one(h, h->parity, h->stream));
-    h->parity ^= 1;
+  for (int i = 0; i < n;) {
+    int m = std::min(n - i, R.K - R.nsub % R.K);
+    for (int j = 0; j < m; ++j)
+      if ((st = rec_push_substep(h)) != MM_OK) return st;
+    if ((st = launch_substeps(h, m)) != MM_OK) return st;
+    i += m;
   }
   return MM_OK;
 }
@@ -835,7 +855,7 @@ int adj_seg(const mm_handle* h) {
 }
 
 template <typename T>
-mm::AdjArgs<T> adj_args(mm_handle* h, int slot, int ver, double dt, int cur) {
+mm::AdjArgs<T> adj_args(mm_handle* h, int slot, int ver, int cur) {
   Recording& R = h->rec;
   mm::AdjArgs<T> a{};
   a.nx = h->g.nx;
@@ -850,8 +870,10 @@ mm::AdjArgs<T> adj_args(mm_handle* h, int slot, int ver, double dt, int cur) {
   a.inv_dth = 1.0 / a.dth;
   a.ds = h->g.L / h->g.ns;
   a.L = h->g.L;
-  a.dt = dt;
+  a.dt = R.v_dt[ver];
   a.v_walk = h->r.v_walk;
+  a.cw = walk_cw(h);
+  a.inv_ds = 1.0 / a.ds;
   a.k_on = h->r.k_on;
   a.k_off = h->r.k_off;
   a.glide = h->r.glide;
@@ -931,7 +953,7 @@ void rec_layout(mm_handle* h, Carver& c) {
   R.gpart = (double*)c.take((size_t)R.grid_motor * 4 * 4 * 8);
   for (int i = 0; i < 3; ++i) R.seed[i] = (double*)c.take(rows * 8);
   R.seed[3] = (double*)c.take(nc * 8);
-  R.coef = (double*)c.take(64);
+  R.coef = (double*)c.take(128);
   R.work = (double*)c.take(std::max(rows, 2 * nc) * 8);
 }
 
@@ -1048,41 +1070,24 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
   const size_t t = h->tsz, nc = (size_t)h->ncells, rows = h->rows;
   const double dth = 2.0 * kPi / h->g.ntheta, ds = h->g.L / h->g.ns;
   const bool f64 = h->prec == MM_FP64;
-  // live scalars to restore afterwards, and the velocity dts
-  double live_scale = 1.0, live_dt = 0.0;
-  CK(cudaMemcpyAsync(&live_scale, &h->prm->psi_scale, 8, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaMemcpyAsync(&live_dt, &h->prm->dt, 8, cudaMemcpyDeviceToHost, h->stream));
   const int nv = (int)R.v_ucell.size();
-  std::vector<double> vdt(nv);
-  for (int v = 0; v < nv; ++v)
-    CK(cudaMemcpyAsync(&vdt[v], R.v_dt[v], 8, cudaMemcpyDeviceToHost, h->stream));
-  CK(cudaStreamSynchronize(h->stream));
+  // live scalars (psi correction factor, dt) kept on the device, restored at
+  // the end; the whole sweep is enqueued without a host round trip
+  CK(cudaMemcpyAsync(R.coef + 8, &h->prm->psi_scale, 8, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(R.coef + 9, &h->prm->dt, 8, cudaMemcpyDeviceToDevice, h->stream));
 
-  // ---- seed at the final (live) state
+  // ---- seed at the final (live) state: coef[0..2] seed coefficients, coef[3]
+  // the observable's value, coef[4..6] the parameter adjoints at the end
   int kind = seed->observable;
-  double coef[4] = {0, 0, 0, 0};
   out->value = 0.0;
+  CK(cudaMemsetAsync(R.coef, 0, 8 * 8, h->stream));
   if (kind == MM_OBS_POLAR_ORDER || kind == MM_OBS_MEAN_STRESS) {
     if ((st = run_moments(h)) != MM_OK) return st;
-    double sc[8], spsi = 0.0;
-    CK(cudaMemcpyAsync(sc, h->prm->scalars, sizeof sc, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaMemcpyAsync(&spsi, &h->prm->sum_psi, 8, cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    if (kind == MM_OBS_POLAR_ORDER) {
-      const double px = sc[6], py = sc[7], pn = std::sqrt(px * px + py * py);
-      const double Lv = pn / spsi;
-      out->value = Lv;
-      coef[0] = -Lv / spsi;
-      coef[1] = pn > 0 ? px / pn / spsi : 0.0;
-      coef[2] = pn > 0 ? py / pn / spsi : 0.0;
-    } else {
-      out->value = sc[5];
-      coef[0] = h->r.force_scale * h->r.ell * dth / (double)nc;
-    }
+    CK(mm::launch_adj_observable(kind, h->prm, h->r.force_scale * h->r.ell * dth / (double)nc,
+                                 R.coef, h->stream));
   } else if (kind != MM_OBS_NONE) {
     return fail(h, MM_ERR_INVALID, "unknown observable");
   }
-  CK(cudaMemcpyAsync(R.coef, coef, sizeof coef, cudaMemcpyHostToDevice, h->stream));
   const double* sp[4] = {nullptr, nullptr, nullptr, nullptr};
   if (kind == MM_OBS_NONE) {
     const double* src[4] = {seed->dL_dpsi, seed->dL_dnb, seed->dL_dm1, seed->dL_dmf};
@@ -1144,18 +1149,18 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
     for (int tt = s1 - 1; tt >= s0; --tt) {
       const int i = tt - s0, ver = R.sub_vel[tt];
       if (f64)
-        e = mm::launch_adjoint<double>(adj_args<double>(h, i, ver, vdt[ver], cur), adj_V(h),
+        e = mm::launch_adjoint<double>(adj_args<double>(h, i, ver, cur), adj_V(h),
                                        R.grid_psi, R.grid_motor, h->stream);
       else
-        e = mm::launch_adjoint<float>(adj_args<float>(h, i, ver, vdt[ver], cur), adj_V(h),
+        e = mm::launch_adjoint<float>(adj_args<float>(h, i, ver, cur), adj_V(h),
                                       R.grid_psi, R.grid_motor, h->stream);
       CK(e);
       cur ^= 1;
     }
   }
   // restore the live scalars
-  CK(cudaMemcpyAsync(&h->prm->psi_scale, &live_scale, 8, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(&h->prm->dt, &live_dt, 8, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(&h->prm->psi_scale, R.coef + 8, 8, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(&h->prm->dt, R.coef + 9, 8, cudaMemcpyDeviceToDevice, h->stream));
 
   // ---- outputs
   out->n_velocities = nv;
@@ -1185,12 +1190,12 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
     if (!out->on_device)
       CK(cudaMemcpyAsync(out->dL_dpsi0, R.work, rows * 8, cudaMemcpyDeviceToHost, h->stream));
   }
-  std::vector<double> gp((size_t)R.grid_motor * 4 * 4);
-  CK(cudaMemcpyAsync(gp.data(), R.gpart, gp.size() * 8, cudaMemcpyDeviceToHost, h->stream));
+  CK(mm::launch_adj_params(R.gpart, R.grid_motor * 4, R.coef + 4, h->stream));
+  double res[8];
+  CK(cudaMemcpyAsync(res, R.coef, sizeof res, cudaMemcpyDeviceToHost, h->stream));
   if ((st = check_status(h)) != MM_OK) return st;
-  out->dL_drates[0] = out->dL_drates[1] = out->dL_drates[2] = 0.0;
-  for (size_t w = 0; w < gp.size() / 4; ++w)
-    for (int q = 0; q < 3; ++q) out->dL_drates[q] += gp[w * 4 + q];
+  out->value = res[3];
+  for (int q = 0; q < 3; ++q) out->dL_drates[q] = res[4 + q];
   return MM_OK;
 }
 

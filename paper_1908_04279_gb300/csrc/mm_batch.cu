@@ -152,7 +152,7 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
         const double dt64 = P->dt;
         dt = (T)dt64;
         hdt = (T)(0.5 * dt64);
-        const T cw = (T)(P->v_walk / A->ds);
+        const T cw = (T)P->cw;
         const T koff = (T)P->k_off;
         kon = (T)P->k_on;
         const T g = MASSCORR ? (T)P->psi_scale : T(1);

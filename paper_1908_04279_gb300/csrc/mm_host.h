@@ -172,6 +172,7 @@ mm_status rec_save_checkpoint(mm_handle* h, int i);
 template <typename T>
 StepArgs<T> step_args(mm_handle* h, int parity);
 mm_status rec_push_substep(mm_handle* h);  // checkpoint bookkeeping of one recorded substep
+mm_status launch_substeps(mm_handle* h, int n);  // n substeps on the live state (graphs)
 
 // Defined in mm_batch_api.cu.
 mm_status batch_micro_step(mm_handle* h, int n);
@@ -179,6 +180,9 @@ void batch_free(mm_handle* h);
 mm_status batch_sync(mm_handle* h);
 const std::vector<mm_handle*>& batch_members(mm_handle* h);
 mm_status batch_launch_info(mm_handle* h, int* info, int n);
+// Walking rate v / ds of Eq. 4, evaluated once on the host for every kernel.
+inline double walk_cw(const mm_handle* h) { return h->r.v_walk / (h->g.L / h->g.ns); }
+
 inline mm_status not_for_batch(mm_handle* h) {
   return fail(h, MM_ERR_INVALID,
               "a batch handle: per-instance calls go to its members (mm_batch_member)");

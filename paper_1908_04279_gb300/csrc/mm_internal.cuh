@@ -27,6 +27,7 @@ struct DevParams {
   unsigned int wait_limit;   // polls of an mbarrier before a wait gives up
   unsigned int debug_flags;  // bit 0: wait on a phase nothing completes (tests)
   int pad;
+  double cw;  // v_walk / ds (evaluated on the host; the kernels only convert it)
 };
 
 // Everything a substep kernel touches, by value as a launch argument.
@@ -70,8 +71,11 @@ struct AdjArgs {
   int units;          // row blocks per cell (power of two)
   int rows_per_unit;  // rows of one block (the last may be shorter)
   long long ncells;
-  double inv_dx, inv_dy, inv_dth, dth, ds, L, dt;
+  double inv_dx, inv_dy, inv_dth, dth, ds, L;
+  const double* dt; // the substep's dt (device)
   double v_walk, k_on, k_off, glide, v_sp;
+  double cw;        // v_walk / ds, the same value as DevParams::cw
+  double inv_ds;    // 1 / ds
   const T* psi_n;   // [cells][nth]
   const T* nb_n;    // [cells][nth]
   const T* mb_n;    // [cells][nth][ns]
@@ -165,6 +169,13 @@ cudaError_t launch_adj_seed(int kind, const double* coef, const T* psi, const T*
                             int nth, int ns, double ds, double L, const T* trig, cudaStream_t s);
 cudaError_t launch_adj_finish(const double* lamG, const double* lamu, double* dLdu, int nx, int ny,
                               double inv_dx, double inv_dy, cudaStream_t s);
+// The seed coefficients and value of a built-in observable from the moments'
+// global scalars (kind 1: polar order, 2: mean tr sigma_a with `stress_coef`):
+// coef[0..2] and coef[3] = value.
+cudaError_t launch_adj_observable(int kind, const DevParams* prm, double stress_coef, double* coef,
+                                  cudaStream_t s);
+// Fixed-order sum of the per-warp parameter adjoints: out[0..2].
+cudaError_t launch_adj_params(const double* gpart, int nwarps, double* out, cudaStream_t s);
 template <typename T>
 cudaError_t launch_adj_psi0(const T* lpsi, const T* lmf, int units, const T* nb, double dth,
                             long long rows, int nth, double* out, cudaStream_t s);

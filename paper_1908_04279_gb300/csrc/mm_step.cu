@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
   const DevParams* P = a.prm;
   const double dt64 = P->dt;
   const T dt = (T)dt64, hdt = (T)(0.5 * dt64);
-  const T cw = (T)(P->v_walk / a.ds);
+  const T cw = (T)P->cw;
   const T koff = (T)P->k_off;
   const T kon = (T)P->k_on;
   const T glide = (T)P->glide, vsp = (T)P->v_sp;

@@ -199,6 +199,17 @@ typedef struct {
   int n_velocities;      /* written: velocity fields in effect during the recording */
 } mm_adjoint_out;
 mm_status mm_set_checkpointing(mm_handle* h, int K, int max_substeps);
+/* Two-level form (for runs whose single-level memory would not fit): outer
+ * checkpoints every K substeps during the recording, and, in the reverse
+ * sweep, each outer segment is first recomputed once to store inner
+ * checkpoints every K_inner substeps, then its inner segments are recomputed
+ * into K_inner slots and reversed. Device memory: ceil(max_substeps / K) + 1
+ * outer checkpoints + ceil(K / K_inner) - 1 inner checkpoints + max(K_inner, 2)
+ * slots (one state each), against K + ceil(max_substeps / K) + 1 for one level;
+ * one extra recomputation of the run. mm_set_checkpointing(h, K, n) is
+ * mm_set_checkpointing_levels(h, K, K, n). MM_ERR_INVALID unless
+ * 1 <= K_inner <= K. */
+mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_substeps);
 mm_status mm_adjoint_step(mm_handle* h, int n_substeps, const mm_adjoint_seed* seed,
                           mm_adjoint_out* out);
 

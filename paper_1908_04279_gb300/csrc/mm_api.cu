@@ -914,7 +914,7 @@ mm::AdjArgs<T> adj_args(mm_handle* h, int slot, int ver, int cur) {
 void rec_layout(mm_handle* h, Carver& c) {
   Recording& R = h->rec;
   const size_t t = h->tsz, nc = (size_t)h->ncells, rows = h->rows;
-  const int K = R.K;
+  const int K = R.K;  // outer checkpoint spacing
   R.ck_mb.resize(R.nck);
   R.ck_psi.resize(R.nck);
   R.ck_nb.resize(R.nck);
@@ -926,15 +926,31 @@ void rec_layout(mm_handle* h, Carver& c) {
     R.ck_mf[i] = c.take(nc * t);
   }
   R.ck_scale = (double*)c.take((size_t)R.nck * 8);
-  R.sl_mb.resize(K + 1);
-  R.sl_psi.resize(K + 1);
-  R.sl_nb.resize(K + 1);
-  R.sl_mf.resize(K + 1);
-  R.sl_cpre.resize(K + 1);
-  // slot 0 of a segment is its checkpoint (read in place); slots 1..K are
-  // the recomputed states
+  // inner checkpoints (two levels): states K2, 2 K2, ... of an outer segment
+  const int nick = (K + R.K2 - 1) / R.K2 - 1;
+  R.ick_mb.resize(nick);
+  R.ick_psi.resize(nick);
+  R.ick_nb.resize(nick);
+  R.ick_mf.resize(nick);
+  for (int i = 0; i < nick; ++i) {
+    R.ick_mb[i] = c.take(h->mbn * t);
+    R.ick_psi[i] = c.take(rows * t);
+    R.ick_nb[i] = c.take(rows * t);
+    R.ick_mf[i] = c.take(nc * t);
+  }
+  R.ick_scale = (double*)c.take((size_t)std::max(nick, 1) * 8);
+  // slot 0 of a segment is its checkpoint (read in place); slots 1..nslots
+  // hold the recomputed states (and, with two levels, the march between inner
+  // checkpoints ping-pongs through slots 1 and 2)
+  R.nslots = nick > 0 ? std::max(R.K2, 2) : R.K2;
+  const int NS = R.nslots;
+  R.sl_mb.resize(NS + 1);
+  R.sl_psi.resize(NS + 1);
+  R.sl_nb.resize(NS + 1);
+  R.sl_mf.resize(NS + 1);
+  R.sl_cpre.resize(NS + 1);
   R.sl_mb[0] = R.sl_psi[0] = R.sl_nb[0] = R.sl_mf[0] = R.sl_cpre[0] = nullptr;
-  for (int i = 1; i <= K; ++i) {
+  for (int i = 1; i <= NS; ++i) {
     R.sl_mb[i] = c.take(h->mbn * t);
     R.sl_psi[i] = c.take(rows * t);
     R.sl_nb[i] = c.take(rows * t);
@@ -962,6 +978,10 @@ void rec_layout(mm_handle* h, Carver& c) {
 extern "C" {
 
 mm_status mm_set_checkpointing(mm_handle* h, int K, int max_substeps) {
+  return mm_set_checkpointing_levels(h, K, K, max_substeps);
+}
+
+mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_substeps) {
   if (!h) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   DeviceGuard dg(h->device);
@@ -973,12 +993,14 @@ mm_status mm_set_checkpointing(mm_handle* h, int K, int max_substeps) {
     return MM_OK;
   }
   if (K < 0 || max_substeps < 1) return fail(h, MM_ERR_INVALID, "K >= 1 and max_substeps >= 1");
+  if (K_inner < 1 || K_inner > K) return fail(h, MM_ERR_INVALID, "1 <= K_inner <= K");
   if (!h->have_state || !h->have_vel || !h->have_dt)
     return fail(h, MM_ERR_STATE, "set the state and the velocity before recording");
-  if (!R.slab || R.K != K || R.max_sub != max_substeps) {
+  if (!R.slab || R.K != K || R.K2 != K_inner || R.max_sub != max_substeps) {
     if (R.slab) cudaFree(R.slab);
     R.slab = nullptr;
     R.K = K;
+    R.K2 = K_inner;
     R.max_sub = max_substeps;
     R.nck = (max_substeps + K - 1) / K + 1;
     // reverse kernels: the psi part one warp per cell; the motor part one warp
@@ -1125,37 +1147,77 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
   }
   CK(cudaMemsetAsync(R.gpart, 0, (size_t)R.grid_motor * 4 * 4 * 8, h->stream));
 
-  // ---- segments, last first
+  // ---- outer segments (checkpoints every K), last first; with two levels
+  // each is first marched through to store its inner checkpoints (every K2),
+  // then its inner segments are recomputed into the slots and reversed, last
+  // first
   int cur = 0, dt_ver = -1;
+  auto set_dt = [&](int ver) -> mm_status {
+    if (ver != dt_ver)
+      CK(cudaMemcpyAsync(&h->prm->dt, R.v_dt[ver], 8, cudaMemcpyDeviceToDevice, h->stream));
+    dt_ver = ver;
+    return MM_OK;
+  };
   const int nseg = (n + R.K - 1) / R.K;
   for (int sgi = nseg - 1; sgi >= 0; --sgi) {
     const int s0 = sgi * R.K, s1 = std::min(s0 + R.K, n);
-    R.sl_mb[0] = R.ck_mb[sgi];
-    R.sl_psi[0] = R.ck_psi[sgi];
-    R.sl_nb[0] = R.ck_nb[sgi];
-    R.sl_mf[0] = R.ck_mf[sgi];
-    CK(cudaMemcpyAsync(&h->prm->psi_scale, R.ck_scale + sgi, 8, cudaMemcpyDeviceToDevice,
-                       h->stream));
-    for (int tt = s0; tt < s1; ++tt) {
-      const int i = tt - s0, ver = R.sub_vel[tt];
-      if (ver != dt_ver)
-        CK(cudaMemcpyAsync(&h->prm->dt, R.v_dt[ver], 8, cudaMemcpyDeviceToDevice, h->stream));
-      dt_ver = ver;
-      StepPtrs p{R.sl_psi[i], R.sl_nb[i], R.sl_mb[i], R.sl_mf[i], R.v_ucell[ver],
-                 R.sl_psi[i + 1], R.sl_nb[i + 1], R.sl_mb[i + 1], R.sl_mf[i + 1], R.sl_c,
-                 R.sl_cpre[i + 1]};
-      CK(launch_ptrs(h, p, h->stream));
+    const int nin = (s1 - s0 + R.K2 - 1) / R.K2;
+    if (nin > 1) {
+      CK(cudaMemcpyAsync(&h->prm->psi_scale, R.ck_scale + sgi, 8, cudaMemcpyDeviceToDevice,
+                         h->stream));
+      const void *in_psi = R.ck_psi[sgi], *in_nb = R.ck_nb[sgi], *in_mb = R.ck_mb[sgi],
+                 *in_mf = R.ck_mf[sgi];
+      int tmp = 1;
+      for (int tt = s0; tt < s0 + (nin - 1) * R.K2; ++tt) {
+        const int ver = R.sub_vel[tt], done = tt + 1 - s0;
+        if ((st = set_dt(ver)) != MM_OK) return st;
+        const bool ick = done % R.K2 == 0;
+        const int j = done / R.K2 - 1;
+        void* o_psi = ick ? R.ick_psi[j] : R.sl_psi[tmp];
+        void* o_nb = ick ? R.ick_nb[j] : R.sl_nb[tmp];
+        void* o_mb = ick ? R.ick_mb[j] : R.sl_mb[tmp];
+        void* o_mf = ick ? R.ick_mf[j] : R.sl_mf[tmp];
+        StepPtrs p{in_psi, in_nb, in_mb, in_mf, R.v_ucell[ver], o_psi, o_nb, o_mb, o_mf, R.sl_c,
+                   R.sl_cpre[1]};
+        CK(launch_ptrs(h, p, h->stream));
+        if (ick)
+          CK(cudaMemcpyAsync(R.ick_scale + j, &h->prm->psi_scale, 8, cudaMemcpyDeviceToDevice,
+                             h->stream));
+        else
+          tmp = 3 - tmp;
+        in_psi = o_psi;
+        in_nb = o_nb;
+        in_mb = o_mb;
+        in_mf = o_mf;
+      }
     }
-    for (int tt = s1 - 1; tt >= s0; --tt) {
-      const int i = tt - s0, ver = R.sub_vel[tt];
-      if (f64)
-        e = mm::launch_adjoint<double>(adj_args<double>(h, i, ver, cur), adj_V(h),
-                                       R.grid_psi, R.grid_motor, h->stream);
-      else
-        e = mm::launch_adjoint<float>(adj_args<float>(h, i, ver, cur), adj_V(h),
-                                      R.grid_psi, R.grid_motor, h->stream);
-      CK(e);
-      cur ^= 1;
+    for (int ig = nin - 1; ig >= 0; --ig) {
+      const int a0 = s0 + ig * R.K2, a1 = std::min(a0 + R.K2, s1);
+      R.sl_mb[0] = ig == 0 ? R.ck_mb[sgi] : R.ick_mb[ig - 1];
+      R.sl_psi[0] = ig == 0 ? R.ck_psi[sgi] : R.ick_psi[ig - 1];
+      R.sl_nb[0] = ig == 0 ? R.ck_nb[sgi] : R.ick_nb[ig - 1];
+      R.sl_mf[0] = ig == 0 ? R.ck_mf[sgi] : R.ick_mf[ig - 1];
+      CK(cudaMemcpyAsync(&h->prm->psi_scale, ig == 0 ? R.ck_scale + sgi : R.ick_scale + ig - 1,
+                         8, cudaMemcpyDeviceToDevice, h->stream));
+      for (int tt = a0; tt < a1; ++tt) {
+        const int i = tt - a0, ver = R.sub_vel[tt];
+        if ((st = set_dt(ver)) != MM_OK) return st;
+        StepPtrs p{R.sl_psi[i], R.sl_nb[i], R.sl_mb[i], R.sl_mf[i], R.v_ucell[ver],
+                   R.sl_psi[i + 1], R.sl_nb[i + 1], R.sl_mb[i + 1], R.sl_mf[i + 1], R.sl_c,
+                   R.sl_cpre[i + 1]};
+        CK(launch_ptrs(h, p, h->stream));
+      }
+      for (int tt = a1 - 1; tt >= a0; --tt) {
+        const int i = tt - a0, ver = R.sub_vel[tt];
+        if (f64)
+          e = mm::launch_adjoint<double>(adj_args<double>(h, i, ver, cur), adj_V(h), R.grid_psi,
+                                         R.grid_motor, h->stream);
+        else
+          e = mm::launch_adjoint<float>(adj_args<float>(h, i, ver, cur), adj_V(h), R.grid_psi,
+                                        R.grid_motor, h->stream);
+        CK(e);
+        cur ^= 1;
+      }
     }
   }
   // restore the live scalars

@@ -84,6 +84,7 @@ PROTOTYPES = {
     "mm_micro_step": ([_H, C.c_int], C.c_int),
     "mm_moments": ([_H, C.POINTER(mm_moments_out)], C.c_int),
     "mm_set_checkpointing": ([_H, C.c_int, C.c_int], C.c_int),
+    "mm_set_checkpointing_levels": ([_H, C.c_int, C.c_int, C.c_int], C.c_int),
     "mm_adjoint_step": ([_H, C.c_int, C.POINTER(mm_adjoint_seed), C.POINTER(mm_adjoint_out)],
                         C.c_int),
     "mm_sync": ([_H], C.c_int),
@@ -256,11 +257,15 @@ class Simulation:
         self._check(self.lib.mm_sync(self.h))
 
     # ---- adjoint -------------------------------------------------------------
-    def set_checkpointing(self, K: int, max_substeps: int):
-        """Start an adjoint recording at the current state. K = 0 ends it and
+    def set_checkpointing(self, K: int, max_substeps: int, K_inner: int | None = None):
+        """Start an adjoint recording at the current state, with checkpoints
+        every K substeps (and, with K_inner < K, inner checkpoints every
+        K_inner substeps rebuilt during the reverse sweep). K = 0 ends it and
         frees its memory; set_state ends it and keeps the memory, which a new
-        recording with the same K and max_substeps reuses."""
-        self._check(self.lib.mm_set_checkpointing(self.h, int(K), int(max_substeps)))
+        recording of the same shape reuses."""
+        Ki = K if K_inner is None else K_inner
+        self._check(self.lib.mm_set_checkpointing_levels(self.h, int(K), int(Ki),
+                                                         int(max_substeps)))
 
     def adjoint(self, n_substeps: int, observable: str = "none", dL_dpsi=None, dL_dnb=None,
                 dL_dm1=None, dL_dmf=None, n_velocities: int = 1, want_du: bool = True,

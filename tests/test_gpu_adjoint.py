@@ -243,3 +243,70 @@ def test_recording_reuse_is_repeatable(mmod):
         assert np.array_equal(o["dL_du"], outs[0]["dL_du"])
         assert np.array_equal(o["dL_dpsi0"], outs[0]["dL_dpsi0"])
         assert np.array_equal(o["dL_drates"], outs[0]["dL_drates"])
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_two_level_checkpoints_equal_one_level(mmod, precision):
+    """Outer checkpoints every 10 substeps with inner checkpoints every 3
+    rebuilt in the reverse sweep (ragged inner and outer segments, a velocity
+    change inside an outer segment) give the same gradients, bit for bit, as
+    one level of checkpoints every 10: the recomputed states are the same."""
+    g = Grid(12, 10, 8, 16, L=1.0)
+    r = Rates(k_on=1.3, k_off=0.7, glide=0.3)
+    psi0 = psi_isotropic_perturbed(g, 31, amp=0.2)
+    u1 = random_divfree_flow(g, 32, 4, 0.3)
+    u2 = random_divfree_flow(g, 33, 4, 0.3)
+    out = []
+    for K_inner in (10, 3, 1):
+        with mmod.Simulation(g, r, precision) as sim:
+            sim.set_state(psi0)
+            sim.set_velocity(u1)
+            sim.set_checkpointing(10, 27, K_inner=K_inner)
+            sim.step(14)
+            sim.set_velocity(u2)
+            sim.step(13)
+            out.append(sim.adjoint(27, observable="mean_stress", n_velocities=2))
+    for o in out[1:]:
+        assert o["value"] == out[0]["value"]
+        assert np.array_equal(o["dL_drates"], out[0]["dL_drates"])
+        assert np.array_equal(o["dL_du"], out[0]["dL_du"])
+        assert np.array_equal(o["dL_dpsi0"], out[0]["dL_dpsi0"])
+
+
+def test_large512_two_level_adjoint_matches_fd(mmod):
+    """The large case (512x512 x 64 x 64, float32, 20 macro steps x 100
+    substeps with a new 16-mode flow each macro step): forward plus adjoint of
+    the mean active stress with respect to k_off, outer checkpoints every 100
+    substeps and inner ones every 10 (40 states of 4.4 GB on the device, where
+    one level would need about 90), against a central difference
+    (h = 0.005 on k_off = 0.5, the same dt per macro step on every run)."""
+    w = WORKLOADS["large512"]
+    g, nmac, nsub = w["grid"], w["macro"], w["substeps"]
+    psi0 = psi_isotropic_perturbed(g, w["seed"])
+    vels = [workload_velocity("large512", m) for m in range(nmac)]
+
+    def run(k_off, record, dts=None):
+        with mmod.Simulation(g, Rates(k_off=k_off), "fp32") as sim:
+            sim.set_state(psi0)
+            got = []
+            for m in range(nmac):
+                sim.set_velocity(vels[m])
+                if dts is not None:
+                    sim.set_dt(dts[m])
+                got.append(sim.dt)
+                if m == 0 and record:
+                    sim.set_checkpointing(100, nmac * nsub, K_inner=10)
+                sim.step(nsub)
+            if record:
+                res = sim.adjoint(nmac * nsub, observable="mean_stress", n_velocities=2 * nmac,
+                                  want_du=False, want_dpsi0=False)
+                return res, got
+            return sim.moments(fields=False)[1]["mean_stress"], got
+
+    res, dts = run(0.5, True)
+    h = 0.005
+    Lp, _ = run(0.5 + h, False, dts)
+    Lm, _ = run(0.5 - h, False, dts)
+    fd = (Lp - Lm) / (2 * h)
+    print("\nLARGE512_ADJ", res["value"], res["dL_drates"][0], fd)
+    assert abs(res["dL_drates"][0] - fd) <= 2e-3 * abs(fd), (res["dL_drates"][0], fd)

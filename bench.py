@@ -391,6 +391,39 @@ def run_ours(args):
                 "kernel_ms_per_launch": ms, "algorithmic_bytes_per_launch": algo_l,
                 "achieved_gbs": algo_l / (ms * 1e-3) / 1e9}
 
+    def large_adjoint_run():
+        """large512 forward + adjoint: 20 macro steps x 100 substeps (a new
+        16-mode flow each macro step), gradient of the mean active stress
+        with respect to k_off, outer checkpoints every 100 substeps and inner
+        ones every 10 (two levels: about 40 states of 4.4 GB held). Times the
+        plain forward and the recorded forward + reverse sweep."""
+        wl = WORKLOADS["large512"]
+        gl, nmac, nsl = wl["grid"], wl["macro"], wl["substeps"]
+        psi_l = psi_isotropic_perturbed(gl, wl["seed"])
+        vl = [torch.tensor(workload_velocity("large512", m), device=dev) for m in range(nmac)]
+        sim = mm.Simulation(gl, r, "fp32", stream=stream.cuda_stream)
+        out = {}
+        for rec in (False, True):
+            sim.set_state(psi_l)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for m in range(nmac):
+                sim.set_velocity(vl[m])
+                if m == 0 and rec:
+                    sim.set_checkpointing(100, nmac * nsl, K_inner=10)
+                sim.step(nsl)
+            if rec:
+                res = sim.adjoint(nmac * nsl, observable="mean_stress", n_velocities=nmac,
+                                  want_du=False, want_dpsi0=False)
+                out["dL_dk_off"] = float(res["dL_drates"][0])
+            sim.sync()
+            out["forward_plus_adjoint_s" if rec else "forward_s"] = time.perf_counter() - t0
+        sim.close()
+        out["adjoint_over_forward"] = (out["forward_plus_adjoint_s"] - out["forward_s"]) / out[
+            "forward_s"]
+        out["checkpoints"] = "outer every 100 substeps (21), inner every 10 (9), 10 slots"
+        return out
+
     def ensemble_run(steps):
         """ensemble64: 64 members with uneven grids (N in {32..128}, Ntheta and
         Ns in {16, 32}), k_off log-uniform in [0.05, 5], v_walk in [0.5, 2];
@@ -449,6 +482,7 @@ def run_ours(args):
     large = {"workload": "large512 (512x512 x 64 x 64, 1.07e9 motor cells)",
              "fp32": large_run("fp32", 10), "fp64": large_run("fp64", 3)}
     ens = ensemble_run(max(2, min(args.steps, 3)))
+    large_adj = large_adjoint_run()
 
     total_ms, kern_ms, fp64_ms, e2e_s = reduce_max([total_ms, kern_ms, fp64_ms, e2e_s], dev)
 
@@ -490,6 +524,8 @@ def run_ours(args):
                                        "kernel": "k_substep (float32)", "peak_source": peak_src,
                                        "traffic": read_profile_traffic(
                                            "k_substep", "large512", "fp32")}),
+            "large512_adjoint": dict(
+                large_adj, workload="large512, 2000 substeps, float32, mean active stress vs k_off"),
             "ensemble": dict(ens, roofline={"bound": "hbm", "peak": peak, "unit": "GB/s",
                                             "achieved": ens["achieved_gbs"],
                                             "frac": ens["achieved_gbs"] / peak,

@@ -197,6 +197,49 @@ __device__ __forceinline__ void row_sums(const double (&m)[V], const double (&sj
   m1 = b;
 }
 
+// Float32 form: the float-float row sums (n_b / ds and m1 / ds) left
+// unconverted; every lane of the segment gets them.
+template <int V>
+__device__ __forceinline__ void row_sums_ff(const float (&m)[V], const float (&sj)[V], int seg,
+                                            FF& a, FF& b) {
+  a = FF{0.f, 0.f};
+  b = FF{0.f, 0.f};
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    ff_add(a, m[v]);
+    ff_add_prod(b, sj[v], m[v]);
+  }
+  for (int o = seg >> 1; o > 0; o >>= 1) {
+    FF ao{__shfl_xor_sync(0xffffffffu, a.hi, o, seg), __shfl_xor_sync(0xffffffffu, a.lo, o, seg)};
+    FF bo{__shfl_xor_sync(0xffffffffu, b.hi, o, seg), __shfl_xor_sync(0xffffffffu, b.lo, o, seg)};
+    ff_merge(a, ao);
+    ff_merge(b, bo);
+  }
+}
+
+// Sums over the warp of 16 values per lane by reduce-scatter (16 float64
+// additions instead of 16 x 5): at each step a lane keeps half of its values
+// and adds its partner's copies of them. Returns the total of value
+// f(lane) = 8 b4 + 4 b3 + 2 b2 + b1 (b_i the bits of the lane index), which
+// lanes 2 f and 2 f + 1 both hold.
+__device__ __forceinline__ double warp_sum16_scatter(double (&v)[16], int lane) {
+#pragma unroll
+  for (int step = 0; step < 4; ++step) {
+    const int o = 16 >> step, half = 8 >> step;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const double keep = up ? v[half + i] : v[i];
+      const double give = up ? v[i] : v[half + i];
+      v[i] = keep + __shfl_xor_sync(0xffffffffu, give, o);
+    }
+  }
+  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
+}
+__device__ __forceinline__ int scatter_field(int lane) {
+  return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
+}
+
 template <typename T, int V>
 struct alignas(sizeof(T) * V) VPack {
   T v[V];
@@ -219,6 +262,9 @@ __global__ void k_moments(const T* psi, const T* mb, const T* mf, const T* c,
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   double* s_nb = msm + (size_t)wib * 2 * nth;
   double* s_m1 = s_nb + nth;
+  // float32 form: the rows' float-float sums, converted once per row below
+  float4* s_ff = reinterpret_cast<float4*>(msm + (size_t)(blockDim.x >> 5) * 2 * nth) +
+                 (size_t)wib * nth;
   const long long gw = blockIdx.x * (long long)(blockDim.x >> 5) + wib;
   const long long W = (long long)gridDim.x * (blockDim.x >> 5);
   const double g = prm->psi_scale;
@@ -231,6 +277,7 @@ __global__ void k_moments(const T* psi, const T* mb, const T* mf, const T* c,
   for (int v = 0; v < V; ++v) sj[v] = (T)(-0.5 * L + ((double)(sl * V + v) + 0.5) * ds);
   // global accumulators: N_psi, bound, free, sum psi cos, sum psi sin, sum psi, sum tr
   double gs[7] = {0, 0, 0, 0, 0, 0, 0};
+  const int fq = scatter_field(lane);
   for (long long cell = gw; cell < ncells; cell += W) {
     for (int r0 = 0; r0 < nth; r0 += rpp) {
       const int k = r0 + rslot;
@@ -245,21 +292,37 @@ __global__ void k_moments(const T* psi, const T* mb, const T* mf, const T* c,
 #pragma unroll
         for (int v = 0; v < V; ++v) m[v] = T(0);
       }
-      double nbk, m1k;
-      row_sums<V>(m, sj, seg, nbk, m1k);
-      if (sl == 0 && k < nth) {
-        s_nb[k] = nbk * ds;
-        s_m1[k] = m1k * ds;
+      if constexpr (sizeof(T) == 4) {
+        FF a, b;
+        row_sums_ff<V>(m, sj, seg, a, b);
+        if (sl == 0 && k < nth) s_ff[k] = make_float4(a.hi, a.lo, b.hi, b.lo);
+      } else {
+        double nbk, m1k;
+        row_sums<V>(m, sj, seg, nbk, m1k);
+        if (sl == 0 && k < nth) {
+          s_nb[k] = nbk * ds;
+          s_m1[k] = m1k * ds;
+        }
       }
     }
     __syncwarp();
-    double f[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    // weights w[q][k] (built on the host): dth, cos dth, sin dth,
-    // (cos^2 - 1/2) dth, cos sin dth, cos, sin, cos^2 dth, cos sin dth, sin^2 dth
+    // ten field sums over theta (weights w[q][k] built on the host: dth,
+    // cos dth, sin dth, (cos^2 - 1/2) dth, cos sin dth, cos, sin, cos^2 dth,
+    // cos sin dth, sin^2 dth); slots 10..15 stay zero
+    double f[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     const double* w = trig + 4 * (size_t)nth;
     for (int k = lane; k < nth; k += 32) {
+      double nbk, m1k;
+      if constexpr (sizeof(T) == 4) {
+        const float4 q = s_ff[k];
+        nbk = ((double)q.x + (double)q.y) * ds;
+        m1k = ((double)q.z + (double)q.w) * ds;
+      } else {
+        nbk = s_nb[k];
+        m1k = s_m1[k];
+      }
       const double p = (double)psi[cell * nth + k] * g;
-      const double pn = p * s_nb[k] * Fm, pm = p * s_m1[k] * (Fm * ell);
+      const double pn = p * nbk * Fm, pm = p * m1k * (Fm * ell);
       f[0] = fma(p, w[k], f[0]);
       f[1] = fma(p, w[nth + k], f[1]);
       f[2] = fma(p, w[2 * nth + k], f[2]);
@@ -275,27 +338,23 @@ __global__ void k_moments(const T* psi, const T* mb, const T* mf, const T* c,
       gs[5] += p;
     }
     __syncwarp();
-#pragma unroll
-    for (int q = 0; q < 10; ++q) f[q] = warp_sum(f[q]);
+    // lane pair (2q, 2q + 1) gets the total of field q
+    const double tot = warp_sum16_scatter(f, lane);
+    // output slot of field q: 0-4 as is, 5-9 to 7-11 (5 and 6 are C and Mf)
+    if ((lane & 1) == 0 && fq < 10) fields[(size_t)(fq < 5 ? fq : fq + 2) * ncells + cell] = tot;
+    const double f0 = __shfl_sync(0xffffffffu, tot, 0);   // field 0 (lane 0)
+    const double f7 = __shfl_sync(0xffffffffu, tot, 14);  // field 7: bits 3, 2, 1 set
     if (lane == 0) {
       const double cc = (double)c[cell], ff = (double)mf[cell];
-      fields[0 * ncells + cell] = f[0];
-      fields[1 * ncells + cell] = f[1];
-      fields[2 * ncells + cell] = f[2];
-      fields[3 * ncells + cell] = f[3];
-      fields[4 * ncells + cell] = f[4];
       fields[5 * ncells + cell] = cc;
       fields[6 * ncells + cell] = ff;
-      fields[7 * ncells + cell] = f[5];
-      fields[8 * ncells + cell] = f[6];
-      fields[9 * ncells + cell] = f[7];
-      fields[10 * ncells + cell] = f[8];
-      fields[11 * ncells + cell] = f[9];
-      gs[0] += f[0] * dA;
+      gs[0] += f0 * dA;
       gs[1] += cc * dA;
       gs[2] += ff * dA;
-      gs[6] += f[7] + f[9];
     }
+    // tr sigma_a = f7 + f9
+    const double f9 = __shfl_sync(0xffffffffu, tot, 18);  // field 9: bits 4, 1 set
+    if (lane == 0) gs[6] += f7 + f9;
   }
 #pragma unroll
   for (int q = 0; q < 7; ++q) gs[q] = warp_sum(gs[q]);
@@ -430,7 +489,8 @@ cudaError_t launch_moments(const T* psi, const T* mb, const T* mf, const T* c,
                            double* partial, int nblocks, DevParams* prm, cudaStream_t s) {
   // nblocks blocks of 4 warps; the partial buffer holds 8 doubles per warp
   const int block = 128;
-  const size_t smem = (size_t)4 * 2 * nth * sizeof(double);
+  // per warp: n_b and m1 of the rows (float64), and their float-float sums
+  const size_t smem = (size_t)4 * 2 * nth * sizeof(double) + (size_t)4 * nth * 16;
   if (smem > 48 * 1024) {
     const void* fn = V == 4 ? (const void*)k_moments<T, 4>
                             : (V == 2 ? (const void*)k_moments<T, 2> : (const void*)k_moments<T, 1>);

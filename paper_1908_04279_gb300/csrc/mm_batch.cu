@@ -103,7 +103,7 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
   RkConst<T> rk{};
   LaneGeom lg{};
   T mass_hi = T(0), mass_lo = T(0);
-  int cell = 0, ce = 0, cwc = 0, cn = 0, cs = 0;
+  int cell = 0, ce = 0, cwc = 0, cn = 0, cs = 0, ix = 0, iy = 0;
   T mtot = 0;
   CellVel<T> uv{};
 
@@ -163,10 +163,14 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
         ds = (T)A->ds;
         rk = RkConst<T>{hdt * cw, T(1) - hdt * koff, T(0), dt * cw, -dt * koff, T(0)};
         lg = lane_geom(lane, seg, ns, V);
+        iy = ct.cell0 / nx;
+        ix = ct.cell0 - iy * nx;
+      } else if (++ix == nx) {  // consecutive cells of the tile
+        ix = 0;
+        ++iy;
       }
       cell = ct.cell0 + ccell;
       if (nb_tma) nb_par ^= 1u;  // members differ in whether they stage by bulk copy
-      const int iy = cell / nx, ix = cell - iy * nx;
       const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
       const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
       ce = iy * nx + xp;
@@ -178,16 +182,9 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
       rk.c3 = hdt * kon * mf_n;
       rk.e3 = dt * kon * mf_n;
       uv = load_cell_vel(A->ucell, cell);
-      if (nb_tma && lane == 0) {
-        const uint32_t pb = (uint32_t)(nth * sizeof(T));
-        mbar_expect_tx(nbar, 10 * pb);
-        const int src_cells[5] = {cell, ce, cwc, cn, cs};
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          bulk_g2s(psi5 + q * nth, A->psi_in + (size_t)src_cells[q] * nth, pb, nbar);
-          bulk_g2s(nb5 + q * nth, A->nb_in + (size_t)src_cells[q] * nth, pb, nbar);
-        }
-      }
+      if (nb_tma)
+        stage_neighbourhood(nbar, psi5, nb5, A->psi_in, A->nb_in, cell, ce, cwc, cn, cs, nth,
+                            lane);
     }
 
     // ---- motor rows of this chunk

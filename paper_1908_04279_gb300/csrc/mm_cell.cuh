@@ -170,6 +170,27 @@ __device__ __forceinline__ void rows_chunk(const T* src_rows, T* dst, int RC, in
   }
 }
 
+// The psi and n_b columns of a cell and its east, west, north and south
+// neighbours into psi5 / nb5 ([5][nth]), completing on `nbar`: lane 0 posts
+// the expected bytes, then lanes 0-9 each issue one of the 10 bulk copies.
+template <typename T>
+__device__ __forceinline__ void stage_neighbourhood(uint64_t* nbar, T* psi5, T* nb5,
+                                                    const T* psi_in, const T* nb_in, int c0,
+                                                    int c1, int c2, int c3, int c4, int nth,
+                                                    int lane) {
+  const uint32_t pb = (uint32_t)(nth * sizeof(T));
+  if (lane == 0) mbar_expect_tx(nbar, 10 * pb);
+  __syncwarp();
+  if (lane < 10) {
+    const int q = lane >> 1;
+    const int cq = q == 0 ? c0 : q == 1 ? c1 : q == 2 ? c2 : q == 3 ? c3 : c4;
+    if (lane & 1)
+      bulk_g2s(nb5 + q * nth, nb_in + (size_t)cq * nth, pb, nbar);
+    else
+      bulk_g2s(psi5 + q * nth, psi_in + (size_t)cq * nth, pb, nbar);
+  }
+}
+
 // ------------------------------------------------------------ end of a cell
 
 // Velocity data of one cell: the cell's own and its east/west (x) and
@@ -199,19 +220,42 @@ struct PsiConst {
 // psi scaled by g on load), written to psi_out[cell]. Returns, per lane, the
 // partial sums of psi^{n+1} (cell_mass) and of psi^{n+1} n_b dtheta (the
 // coarse density of Eq. 5, acc) over the lane's orientations.
+// Trigonometric values of the orientation a lane handles when nth <= 32
+// (k = lane): cos, sin of theta_k and of the faces theta_{k +- 1/2}.
+template <typename T>
+struct LaneTrig {
+  T ck, sk, cp, sp, cm, sm;
+};
+template <typename T>
+__device__ __forceinline__ LaneTrig<T> lane_trig(const T* trig, int nth, int lane) {
+  LaneTrig<T> t{};
+  if (lane < nth) {
+    const int km = lane == 0 ? nth - 1 : lane - 1;
+    t.ck = trig[lane];
+    t.sk = trig[nth + lane];
+    t.cp = trig[2 * nth + lane];
+    t.sp = trig[3 * nth + lane];
+    t.cm = trig[2 * nth + km];
+    t.sm = trig[3 * nth + km];
+  }
+  return t;
+}
+
 template <typename T>
 __device__ __forceinline__ void psi_cell(const PsiConst<T>& q, const CellVel<T>& u,
                                          const T* psi5, const T* nb5, const T* s_nb, int nth,
-                                         int lane, T* psi_out_cell, T& cell_mass, T& acc) {
+                                         int lane, T* psi_out_cell, T& cell_mass, T& acc,
+                                         const LaneTrig<T>* lt = nullptr) {
   const T* cosk = q.trig;
   const T* sink = q.trig + nth;
   const T* cosf = q.trig + 2 * nth;
   const T* sinf = q.trig + 3 * nth;
   const T g = q.g;
+  const bool cached = lt != nullptr && nth <= 32;
   for (int k = lane; k < nth; k += 32) {
     const T Pc = g * psi5[k], Pe = g * psi5[nth + k], Pw = g * psi5[2 * nth + k];
     const T Pn = g * psi5[3 * nth + k], Ps = g * psi5[4 * nth + k];
-    const T ck = cosk[k], sk = sink[k];
+    const T ck = cached ? lt->ck : cosk[k], sk = cached ? lt->sk : sink[k];
     const T Vc = q.vsp + q.glide * nb5[k], Ve = q.vsp + q.glide * nb5[nth + k];
     const T Vw = q.vsp + q.glide * nb5[2 * nth + k], Vn = q.vsp + q.glide * nb5[3 * nth + k];
     const T Vs = q.vsp + q.glide * nb5[4 * nth + k];
@@ -220,7 +264,8 @@ __device__ __forceinline__ void psi_cell(const PsiConst<T>& q, const CellVel<T>&
     const T Ae = T(0.5) * (axc + axe), Aw = T(0.5) * (axw + axc);
     const T An = T(0.5) * (ayc + ayn), As = T(0.5) * (ays + ayc);
     const int kp = k + 1 == nth ? 0 : k + 1, km = k == 0 ? nth - 1 : k - 1;
-    const T cp = cosf[k], sp = sinf[k], cm = cosf[km], sm = sinf[km];
+    const T cp = cached ? lt->cp : cosf[k], sp = cached ? lt->sp : sinf[k];
+    const T cm = cached ? lt->cm : cosf[km], sm = cached ? lt->sm : sinf[km];
     // Jeffery rotation p_perp . G . p at the faces k +- 1/2
     const T wp = -sp * (u.Gxx * cp + u.Gxy * sp) + cp * (u.Gyx * cp + u.Gyy * sp);
     const T wm = -sm * (u.Gxx * cm + u.Gxy * sm) + cm * (u.Gyx * cm + u.Gyy * sm);

@@ -107,6 +107,10 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
   uint32_t fail_par = 0;
   CellVel<T> uv{};
   int cell = gw - W, ce = 0, cwc = 0, cn = 0, cs = 0;
+  // cell coordinates, advanced by W cells at a time without a division
+  const int Wy = W / nx, Wx = W - Wy * nx;
+  int ix = -1, iy = 0;
+  const LaneTrig<T> lt = lane_trig(a.trig, nth, lane);
   uint32_t nb_par = 1;  // parity of the neighbourhood phase of the current cell
   T mtot = 0;
   T mass_hi = T(0), mass_lo = T(0);  // compensated sum of psi^{n+1} over this warp's cells
@@ -118,7 +122,17 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
       // a new cell: per-cell scalars and the psi-transport inputs
       cell += W;
       nb_par ^= 1u;
-      const int iy = cell / nx, ix = cell - iy * nx;
+      if (ix < 0) {
+        iy = cell / nx;
+        ix = cell - iy * nx;
+      } else {
+        ix += Wx;
+        iy += Wy;
+        if (ix >= nx) {
+          ix -= nx;
+          ++iy;
+        }
+      }
       const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
       const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
       ce = iy * nx + xp;
@@ -131,17 +145,8 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
       rk.c3 = hdt * kon * mf_n;
       rk.e3 = dt * kon * mf_n;
       uv = load_cell_vel(a.ucell, cell);
-      if (nb_tma && lane == 0) {
-        // stage the psi^n and n_b^n columns of the cell and its 4 neighbours
-        const uint32_t pb = (uint32_t)(nth * sizeof(T));
-        mbar_expect_tx(nbar, 10 * pb);
-        const int src_cells[5] = {cell, ce, cwc, cn, cs};
-#pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          bulk_g2s(psi5 + q * nth, a.psi_in + (size_t)src_cells[q] * nth, pb, nbar);
-          bulk_g2s(nb5 + q * nth, a.nb_in + (size_t)src_cells[q] * nth, pb, nbar);
-        }
-      }
+      if (nb_tma)  // stage the psi^n and n_b^n columns of the cell and its 4 neighbours
+        stage_neighbourhood(nbar, psi5, nb5, a.psi_in, a.nb_in, cell, ce, cwc, cn, cs, nth, lane);
     }
 
     // ---- motor rows of this chunk
@@ -190,7 +195,8 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
       __syncwarp();
     }
     T acc = T(0), cell_mass = T(0);
-    psi_cell(pq, uv, psi5, nb5, s_nb, nth, lane, a.psi_out + (size_t)cell * nth, cell_mass, acc);
+    psi_cell(pq, uv, psi5, nb5, s_nb, nth, lane, a.psi_out + (size_t)cell * nth, cell_mass, acc,
+             &lt);
     two_sum_acc(mass_hi, mass_lo, cell_mass);
     cell_motor_close(acc, mtot, s_nb, nth, ns, lane, cell, a.mb_out, a.nb_out, a.c, a.mf_out,
                      a.cpre_out);

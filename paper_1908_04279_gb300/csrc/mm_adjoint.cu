@@ -61,6 +61,15 @@ __device__ __forceinline__ void walk_adj(const T (&ga)[V], const T (&gb)[V], con
   }
 }
 
+// Resident blocks the staged psi reverse kernel is sized for (registers) in
+// float32 (float64 keeps its natural register count).
+#ifndef MM_ADJ_PSI_MIN_BLOCKS
+#define MM_ADJ_PSI_MIN_BLOCKS 8
+#endif
+template <typename T>
+constexpr int adj_psi_min_blocks() {
+  return sizeof(T) == 8 ? 1 : MM_ADJ_PSI_MIN_BLOCKS;
+}
 #ifndef MM_ADJ_MOTOR_MIN_BLOCKS
 #define MM_ADJ_MOTOR_MIN_BLOCKS 4
 #endif
@@ -95,23 +104,43 @@ __device__ __forceinline__ void cell_lamc(const AdjArgs<T>& a, int cell, T& lamC
   }
 }
 
-// Adjoint of one substep, part 1: Eq. 1 and the coupling through C.
-// One warp per cell (grid-stride), lanes over theta. Transposes every
-// donor-cell face flux on the branch the forward took, giving lam_psi^n, the
-// adjoint of n_b^n through the gliding speed (stored, times ds, for part 2),
-// and the cell's accumulated adjoints of u and of its velocity gradient; also
-// stores lam_C and f of the cell for part 2. Per-warp shared memory: the
-// cell's lam_psi_total and psi^n (2 nth values).
+// Where the psi adjoint of a cell reads the columns of the cell and its four
+// neighbours (q = 0 cell, 1 east, 2 west, 3 north, 4 south): psi^n, n_b^n,
+// lam_psi^{n+1}, n_b^{n+1}, and the cell's velocity block. ColsGlobal reads
+// them in place; ColsSmem from a stage [psi 5][n_b 5][lam_psi 5][n_b' 5][u 12].
 template <typename T>
-__global__ void __launch_bounds__(128) k_adj_psi(const AdjArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char adj_smem[];
-  const int nth = a.nth;
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  T* s_lt = reinterpret_cast<T*>(adj_smem) + (size_t)wib * 2 * nth;
-  T* s_psi = s_lt + nth;
-  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
-  const int W = gridDim.x * (blockDim.x >> 5);
-  const int nc = (int)a.ncells, nx = a.nx, ny = a.ny;
+struct ColsGlobal {
+  const AdjArgs<T>* a;
+  int nbr[5];
+  int cell;
+  __device__ T psi(int q, int k) const { return a->psi_n[(size_t)nbr[q] * a->nth + k]; }
+  __device__ T nb(int q, int k) const { return a->nb_n[(size_t)nbr[q] * a->nth + k]; }
+  __device__ T lp(int q, int k) const { return a->lpsi_in[(size_t)nbr[q] * a->nth + k]; }
+  __device__ T nbp(int q, int k) const { return a->nb_np[(size_t)nbr[q] * a->nth + k]; }
+  __device__ T u(int i) const { return a->ucell[(size_t)cell * 12 + i]; }
+};
+template <typename T>
+struct ColsSmem {
+  const T* st;
+  int nth;
+  __device__ T psi(int q, int k) const { return st[q * nth + k]; }
+  __device__ T nb(int q, int k) const { return st[(5 + q) * nth + k]; }
+  __device__ T lp(int q, int k) const { return st[(10 + q) * nth + k]; }
+  __device__ T nbp(int q, int k) const { return st[(15 + q) * nth + k]; }
+  __device__ T u(int i) const { return st[20 * nth + i]; }
+};
+
+// The psi adjoint of one cell (lanes over theta): transposes every donor-cell
+// face flux on the branch the forward took, giving lam_psi^n, the adjoint of
+// n_b^n through the gliding speed (stored, times ds, for part 2), and the
+// cell's accumulated adjoints of u and of its velocity gradient (acc_old: the
+// accumulator lane j < 6 holds, read earlier); stores lam_C and f of the cell.
+// s_lt: nth values of shared memory for the cell's lam_psi_total.
+template <typename T, class Cols>
+__device__ __forceinline__ void psi_adj_cell(const AdjArgs<T>& a, const Cols& C, int cell,
+                                             const T (&lamC)[5], const T (&fsc)[5], T* s_lt,
+                                             double acc_old, int lane) {
+  const int nth = a.nth, nc = (int)a.ncells;
   const T dt = (T)*a.dt;
   const T glide = (T)a.glide, vsp = (T)a.v_sp;
   const T dtv = dt * (T)a.inv_dx, dtw = dt * (T)a.inv_dy, dtt = dt * (T)a.inv_dth;
@@ -120,13 +149,166 @@ __global__ void __launch_bounds__(128) k_adj_psi(const AdjArgs<T> a) {
   const T* sink = a.trig + nth;
   const T* cosf = a.trig + 2 * nth;
   const T* sinf = a.trig + 3 * nth;
+  // lam_psi_total = lam_psi^{n+1} + lam_C n_b** dtheta (n_b** = n_b^{n+1} / f)
+  auto lam_tot = [&](int q, int k) -> T { return C.lp(q, k) + lamC[q] * (C.nbp(q, k) / fsc[q]) * dth; };
+  for (int k = lane; k < nth; k += 32) s_lt[k] = lam_tot(0, k);
+  __syncwarp();
+  const T uxc = C.u(0), uyc = C.u(1), uxe = C.u(2), uxw = C.u(3), uyn = C.u(4), uys = C.u(5);
+  const T Gxx = C.u(6), Gxy = C.u(7), Gyx = C.u(8), Gyy = C.u(9);
+  T lux = T(0), luy = T(0), lG0 = T(0), lG1 = T(0), lG2 = T(0), lG3 = T(0);
+  for (int k = lane; k < nth; k += 32) {
+    const size_t rc = (size_t)cell * nth + k;
+    const T pc = C.psi(0, k), pe = C.psi(1, k), pw = C.psi(2, k), pn = C.psi(3, k),
+            ps = C.psi(4, k);
+    const T ck = cosk[k], sk = sink[k];
+    const T Vc = vsp + glide * C.nb(0, k), Ve = vsp + glide * C.nb(1, k);
+    const T Vw = vsp + glide * C.nb(2, k), Vn = vsp + glide * C.nb(3, k);
+    const T Vs = vsp + glide * C.nb(4, k);
+    const T axc = fma_t(-Vc, ck, uxc), axe = fma_t(-Ve, ck, uxe), axw = fma_t(-Vw, ck, uxw);
+    const T ayc = fma_t(-Vc, sk, uyc), ayn = fma_t(-Vn, sk, uyn), ays = fma_t(-Vs, sk, uys);
+    const T Ae = T(0.5) * (axc + axe), Aw = T(0.5) * (axw + axc);
+    const T An = T(0.5) * (ayc + ayn), As = T(0.5) * (ays + ayc);
+    const int kp = k + 1 == nth ? 0 : k + 1, km = k == 0 ? nth - 1 : k - 1;
+    const T cp = cosf[k], sp = sinf[k], cm = cosf[km], sm = sinf[km];
+    const T wp = -sp * (Gxx * cp + Gxy * sp) + cp * (Gyx * cp + Gyy * sp);
+    const T wm = -sm * (Gxx * cm + Gxy * sm) + cm * (Gyx * cm + Gyy * sm);
+    const T ltc = s_lt[k];
+    const T lte = lam_tot(1, k), ltw = lam_tot(2, k), ltn = lam_tot(3, k), lts = lam_tot(4, k);
+    // face adjoints lam_F = dt/h (lam_right - lam_left)
+    const T lFe = dtv * (lte - ltc), lFw = dtv * (ltc - ltw);
+    const T lFn = dtw * (ltn - ltc), lFs = dtw * (ltc - lts);
+    const T lFp = dtt * (s_lt[kp] - ltc), lFm = dtt * (ltc - s_lt[km]);
+    T lp = ltc + tmax(Ae, T(0)) * lFe + tmin(Aw, T(0)) * lFw + tmax(An, T(0)) * lFn +
+           tmin(As, T(0)) * lFs + tmax(wp, T(0)) * lFp + tmin(wm, T(0)) * lFm;
+    a.lpsi_out[rc] = lp;
+    // face velocities: lam_A = psi_upwind lam_F, half to each side's a
+    const T lAe = (Ae > T(0) ? pc : pe) * lFe, lAw = (Aw > T(0) ? pw : pc) * lFw;
+    const T lAn = (An > T(0) ? pc : pn) * lFn, lAs = (As > T(0) ? ps : pc) * lFs;
+    const T lax = T(0.5) * (lAe + lAw), lay = T(0.5) * (lAn + lAs);
+    lux += lax;
+    luy += lay;
+    a.lnb[rc] = -glide * (ck * lax + sk * lay) * ds;
+    // rotation at the face k+1/2 owned by this orientation
+    const T lw = (wp > T(0) ? pc : C.psi(0, kp)) * lFp;
+    lG0 += lw * (-sp * cp);
+    lG1 += lw * (-sp * sp);
+    lG2 += lw * (cp * cp);
+    lG3 += lw * (cp * sp);
+  }
+  const T s_ux = warp_sum_t(lux), s_uy = warp_sum_t(luy);
+  const T s_g0 = warp_sum_t(lG0), s_g1 = warp_sum_t(lG1);
+  const T s_g2 = warp_sum_t(lG2), s_g3 = warp_sum_t(lG3);
+  // lane j < 6 adds the j-th of (ux, uy, G0..G3) to its accumulator
+  const T mine = lane == 0 ? s_ux : lane == 1 ? s_uy : lane == 2 ? s_g0
+               : lane == 3 ? s_g1 : lane == 4 ? s_g2 : s_g3;
+  if (lane < 2)
+    a.lamu[(size_t)lane * nc + cell] = acc_old + (double)mine;
+  else if (lane < 6)
+    a.lamG[(size_t)cell * 4 + (lane - 2)] = acc_old + (double)mine;
+  if (lane == 0) {
+    a.cellc[(size_t)cell * 2 + 0] = lamC[0];
+    a.cellc[(size_t)cell * 2 + 1] = fsc[0];
+  }
+  __syncwarp();
+}
 
+__device__ __forceinline__ void cell_nbrs(int cell, int nx, int ny, int (&nbr)[5]) {
+  const int iy = cell / nx, ix = cell - iy * nx;
+  const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
+  const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
+  nbr[0] = cell;
+  nbr[1] = iy * nx + xp;
+  nbr[2] = iy * nx + xm;
+  nbr[3] = yp * nx + ix;
+  nbr[4] = ym * nx + ix;
+}
+
+// Adjoint of one substep, part 1: Eq. 1 and the coupling through C, one warp
+// per cell (grid-stride), columns read in place (any ntheta). Per-warp shared
+// memory: the cell's lam_psi_total (nth values).
+template <typename T>
+__global__ void __launch_bounds__(128) k_adj_psi(const AdjArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char adj_smem[];
+  const int nth = a.nth;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  T* s_lt = reinterpret_cast<T*>(adj_smem) + (size_t)wib * nth;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  const int W = gridDim.x * (blockDim.x >> 5);
+  const int nc = (int)a.ncells;
   for (int cell = gw; cell < nc; cell += W) {
-    const int iy = cell / nx, ix = cell - iy * nx;
-    const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
-    const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
-    const int nbr[5] = {cell, iy * nx + xp, iy * nx + xm, yp * nx + ix, ym * nx + ix};
-    // the accumulated velocity adjoints of the cell, read early (lanes 0-5)
+    ColsGlobal<T> C;
+    C.a = &a;
+    C.cell = cell;
+    cell_nbrs(cell, a.nx, a.ny, C.nbr);
+    double acc_old = 0.0;
+    if (lane < 2)
+      acc_old = a.lamu[(size_t)lane * nc + cell];
+    else if (lane < 6)
+      acc_old = a.lamG[(size_t)cell * 4 + (lane - 2)];
+    T lamC[5], fsc[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) cell_lamc(a, C.nbr[q], lamC[q], fsc[q]);
+    psi_adj_cell(a, C, cell, lamC, fsc, s_lt, acc_old, lane);
+  }
+}
+
+// Stage bytes of the staged psi adjoint: 20 columns and the velocity block.
+__host__ __device__ inline size_t psi_stage_bytes(int nth, int tsz) {
+  return ((size_t)(20 * nth + 12) * tsz + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t psi_ring_warp_bytes(int nth, int tsz) {
+  return 128 + 2 * psi_stage_bytes(nth, tsz) + (((size_t)nth * tsz + 15) & ~(size_t)15);
+}
+
+// The same with the columns of the next cell staged by bulk copies while the
+// current one is computed (two stages per warp; needs nth * sizeof(T) a
+// multiple of 16). Lane 0 posts the expected bytes, lanes 0-20 each issue
+// one copy. Waits are bounded; a warp whose wait runs out records the
+// failure, drains its copy and leaves.
+template <typename T>
+__global__ void __launch_bounds__(128, adj_psi_min_blocks<T>()) k_adj_psi_ring(const AdjArgs<T> a) {
+  extern __shared__ __align__(128) unsigned char psr_smem[];
+  const int nth = a.nth, nx = a.nx, ny = a.ny;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const size_t stb = psi_stage_bytes(nth, (int)sizeof(T));
+  unsigned char* wbase = psr_smem + (size_t)wib * psi_ring_warp_bytes(nth, (int)sizeof(T));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wbase);  // [2] stages, [2] never
+  T* stage[2] = {reinterpret_cast<T*>(wbase + 128), reinterpret_cast<T*>(wbase + 128 + stb)};
+  T* s_lt = reinterpret_cast<T*>(wbase + 128 + 2 * stb);
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  const int W = gridDim.x * (blockDim.x >> 5);
+  const int nc = (int)a.ncells;
+  const uint32_t wait_limit = a.prm->wait_limit;
+  const bool wait_never = (a.prm->debug_flags & 1u) != 0;
+  const uint32_t colb = (uint32_t)(nth * sizeof(T));
+  const uint32_t ub = (uint32_t)(12 * sizeof(T));
+  auto issue = [&](int cell, int sidx) {
+    int nbr[5];
+    cell_nbrs(cell, nx, ny, nbr);
+    if (lane == 0) mbar_expect_tx(&bars[sidx], 20 * colb + ub);
+    __syncwarp();
+    if (lane < 20) {
+      const int f = lane / 5, q = lane - 5 * f;
+      const T* src = f == 0 ? a.psi_n : f == 1 ? a.nb_n : f == 2 ? a.lpsi_in : a.nb_np;
+      bulk_g2s(stage[sidx] + (size_t)lane * nth, src + (size_t)nbr[q] * nth, colb, &bars[sidx]);
+    } else if (lane == 20) {
+      bulk_g2s(stage[sidx] + (size_t)20 * nth, a.ucell + (size_t)cell * 12, ub, &bars[sidx]);
+    }
+  };
+  if (lane == 0) {
+    for (int q = 0; q < 3; ++q) mbar_init(&bars[q], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  if (gw < nc) issue(gw, 0);
+  int sidx = 0;
+  uint32_t par[2] = {0u, 0u};
+  bool timed_out = false, pending_next = false;
+  for (int cell = gw; cell < nc; cell += W) {
+    const int next = cell + W;
+    // scalar inputs of this cell (independent of the copies in flight)
+    int nbr[5];
+    cell_nbrs(cell, nx, ny, nbr);
     double acc_old = 0.0;
     if (lane < 2)
       acc_old = a.lamu[(size_t)lane * nc + cell];
@@ -135,76 +317,26 @@ __global__ void __launch_bounds__(128) k_adj_psi(const AdjArgs<T> a) {
     T lamC[5], fsc[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) cell_lamc(a, nbr[q], lamC[q], fsc[q]);
-    // lam_psi_total = lam_psi^{n+1} + lam_C n_b** dtheta (n_b** = n_b^{n+1} / f)
-    auto lam_tot = [&](int q, int k) -> T {
-      const size_t r = (size_t)nbr[q] * nth + k;
-      return a.lpsi_in[r] + lamC[q] * (a.nb_np[r] / fsc[q]) * dth;
-    };
-    for (int k = lane; k < nth; k += 32) {
-      s_lt[k] = lam_tot(0, k);
-      s_psi[k] = a.psi_n[(size_t)cell * nth + k];
+    // the next cell's columns into the other stage
+    if (next < nc) issue(next, sidx ^ 1);
+    const bool ok = __all_sync(0xffffffffu, wait_never ? mbar_wait(&bars[2], 0u, wait_limit)
+                                                       : mbar_wait(&bars[sidx], par[sidx], wait_limit));
+    if (!ok) {
+      timed_out = true;
+      pending_next = next < nc;
+      break;
     }
-    __syncwarp();
-
-    const T* uc = a.ucell + (size_t)cell * 12;
-    const T uxc = uc[0], uyc = uc[1], uxe = uc[2], uxw = uc[3], uyn = uc[4], uys = uc[5];
-    const T Gxx = uc[6], Gxy = uc[7], Gyx = uc[8], Gyy = uc[9];
-    T lux = T(0), luy = T(0), lG0 = T(0), lG1 = T(0), lG2 = T(0), lG3 = T(0);
-    for (int k = lane; k < nth; k += 32) {
-      const size_t rc = (size_t)cell * nth + k;
-      const T pc = s_psi[k];
-      const T pe = a.psi_n[(size_t)nbr[1] * nth + k], pw = a.psi_n[(size_t)nbr[2] * nth + k];
-      const T pn = a.psi_n[(size_t)nbr[3] * nth + k], ps = a.psi_n[(size_t)nbr[4] * nth + k];
-      const T ck = cosk[k], sk = sink[k];
-      const T Vc = vsp + glide * a.nb_n[rc];
-      const T Ve = vsp + glide * a.nb_n[(size_t)nbr[1] * nth + k];
-      const T Vw = vsp + glide * a.nb_n[(size_t)nbr[2] * nth + k];
-      const T Vn = vsp + glide * a.nb_n[(size_t)nbr[3] * nth + k];
-      const T Vs = vsp + glide * a.nb_n[(size_t)nbr[4] * nth + k];
-      const T axc = fma_t(-Vc, ck, uxc), axe = fma_t(-Ve, ck, uxe), axw = fma_t(-Vw, ck, uxw);
-      const T ayc = fma_t(-Vc, sk, uyc), ayn = fma_t(-Vn, sk, uyn), ays = fma_t(-Vs, sk, uys);
-      const T Ae = T(0.5) * (axc + axe), Aw = T(0.5) * (axw + axc);
-      const T An = T(0.5) * (ayc + ayn), As = T(0.5) * (ays + ayc);
-      const int kp = k + 1 == nth ? 0 : k + 1, km = k == 0 ? nth - 1 : k - 1;
-      const T cp = cosf[k], sp = sinf[k], cm = cosf[km], sm = sinf[km];
-      const T wp = -sp * (Gxx * cp + Gxy * sp) + cp * (Gyx * cp + Gyy * sp);
-      const T wm = -sm * (Gxx * cm + Gxy * sm) + cm * (Gyx * cm + Gyy * sm);
-      const T ltc = s_lt[k];
-      const T lte = lam_tot(1, k), ltw = lam_tot(2, k), ltn = lam_tot(3, k), lts = lam_tot(4, k);
-      // face adjoints lam_F = dt/h (lam_right - lam_left)
-      const T lFe = dtv * (lte - ltc), lFw = dtv * (ltc - ltw);
-      const T lFn = dtw * (ltn - ltc), lFs = dtw * (ltc - lts);
-      const T lFp = dtt * (s_lt[kp] - ltc), lFm = dtt * (ltc - s_lt[km]);
-      T lp = ltc + tmax(Ae, T(0)) * lFe + tmin(Aw, T(0)) * lFw + tmax(An, T(0)) * lFn +
-             tmin(As, T(0)) * lFs + tmax(wp, T(0)) * lFp + tmin(wm, T(0)) * lFm;
-      a.lpsi_out[rc] = lp;
-      // face velocities: lam_A = psi_upwind lam_F, half to each side's a
-      const T lAe = (Ae > T(0) ? pc : pe) * lFe, lAw = (Aw > T(0) ? pw : pc) * lFw;
-      const T lAn = (An > T(0) ? pc : pn) * lFn, lAs = (As > T(0) ? ps : pc) * lFs;
-      const T lax = T(0.5) * (lAe + lAw), lay = T(0.5) * (lAn + lAs);
-      lux += lax;
-      luy += lay;
-      a.lnb[rc] = -glide * (ck * lax + sk * lay) * ds;
-      // rotation at the face k+1/2 owned by this orientation
-      const T lw = (wp > T(0) ? pc : s_psi[kp]) * lFp;
-      lG0 += lw * (-sp * cp);
-      lG1 += lw * (-sp * sp);
-      lG2 += lw * (cp * cp);
-      lG3 += lw * (cp * sp);
-    }
-    const T s_ux = warp_sum_t(lux), s_uy = warp_sum_t(luy);
-    const T s_g0 = warp_sum_t(lG0), s_g1 = warp_sum_t(lG1);
-    const T s_g2 = warp_sum_t(lG2), s_g3 = warp_sum_t(lG3);
-    // lane j < 6 adds the j-th of (ux, uy, G0..G3) to its accumulator
-    const T mine = lane == 0 ? s_ux : lane == 1 ? s_uy : lane == 2 ? s_g0
-                 : lane == 3 ? s_g1 : lane == 4 ? s_g2 : s_g3;
-    if (lane < 2)
-      a.lamu[(size_t)lane * nc + cell] = acc_old + (double)mine;
-    else if (lane < 6)
-      a.lamG[(size_t)cell * 4 + (lane - 2)] = acc_old + (double)mine;
+    par[sidx] ^= 1u;
+    ColsSmem<T> C{stage[sidx], nth};
+    psi_adj_cell(a, C, cell, lamC, fsc, s_lt, acc_old, lane);
+    sidx ^= 1;
+  }
+  if (timed_out) {
+    // record the failure; wait (bounded) for the copies this warp issued
     if (lane == 0) {
-      a.cellc[(size_t)cell * 2 + 0] = lamC[0];
-      a.cellc[(size_t)cell * 2 + 1] = fsc[0];
+      atomicOr(&a.prm->status, 1);
+      (void)mbar_wait(&bars[sidx], par[sidx], kDrainLimit);
+      if (pending_next) (void)mbar_wait(&bars[sidx ^ 1], par[sidx ^ 1], kDrainLimit);
     }
     __syncwarp();
   }
@@ -742,13 +874,24 @@ template <typename T>
 cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid_psi, int grid_motor,
                            cudaStream_t s) {
   const int block = 128;
-  const size_t smem = (size_t)4 * 2 * a.nth * sizeof(T);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_adj_psi<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
+  const size_t ring_smem = 4 * psi_ring_warp_bytes(a.nth, (int)sizeof(T));
+  if ((a.nth * sizeof(T)) % 16 == 0 && ring_smem <= 200 * 1024) {
+    if (ring_smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_adj_psi_ring<T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)ring_smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_adj_psi_ring<T><<<grid_psi, block, ring_smem, s>>>(a);
+  } else {
+    const size_t smem = (size_t)4 * a.nth * sizeof(T);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_adj_psi<T>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    k_adj_psi<T><<<grid_psi, block, smem, s>>>(a);
   }
-  k_adj_psi<T><<<grid_psi, block, smem, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   auto go = [&](auto plain, auto ring) -> cudaError_t {

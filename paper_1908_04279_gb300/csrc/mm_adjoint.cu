@@ -68,7 +68,7 @@ __device__ __forceinline__ void walk_adj(const T (&ga)[V], const T (&gb)[V], con
 #endif
 template <typename T>
 constexpr int adj_psi_min_blocks() {
-  return sizeof(T) == 8 ? 1 : MM_ADJ_PSI_MIN_BLOCKS;
+  return sizeof(T) == 8 ? 3 : MM_ADJ_PSI_MIN_BLOCKS;
 }
 #ifndef MM_ADJ_MOTOR_MIN_BLOCKS
 #define MM_ADJ_MOTOR_MIN_BLOCKS 4

@@ -1,6 +1,6 @@
 """Run one synthetic case of the library's kernels, for profilers.
 
-    python -m paper_1908_04279_gb300.profile_case [--case single|batch|adjoint]
+    python -m paper_1908_04279_gb300.profile_case [--case single|batch|adjoint|moments]
         [--grid NX NY NTHETA NS] [--precision fp32|fp64] [--substeps N]
         [--repeat R] [--K K] [--members M] [--autotune]
 
@@ -11,6 +11,7 @@ batch:   the first M members of the detachment-rate ensemble (64 by default)
          with --autotune).
 adjoint: a recording of N substeps (checkpoint every K) on the single case,
          then the reverse sweep for the polar order; R times.
+moments: N substeps of the single case, then R calls of mm_moments.
 Prints the times measured with CUDA events on the handle's stream.
 """
 from __future__ import annotations
@@ -28,7 +29,7 @@ def main():
                          random_divfree_flow)
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="single", choices=["single", "batch", "adjoint"])
+    ap.add_argument("--case", default="single", choices=["single", "batch", "adjoint", "moments"])
     ap.add_argument("--grid", type=int, nargs=4, default=[256, 256, 64, 64])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--substeps", type=int, default=10)
@@ -73,6 +74,13 @@ def main():
         u = random_divfree_flow(g, 1, 8, 0.1)
         sim.set_state(psi0)
         sim.set_velocity(u)
+        if args.case == "moments":
+            sim.step(args.substeps)
+            fields = torch.empty(12 * g.nx * g.ny, dtype=torch.float64, device="cuda")
+            times = [timed(lambda: sim.moments(fields=fields)) for _ in range(args.repeat)]
+            print(json.dumps({"case": "moments", "grid": args.grid, "precision": args.precision,
+                              "ms_per_call": times}))
+            return
         if args.case == "single":
             times = [timed(lambda: sim.step(args.substeps)) / args.substeps
                      for _ in range(args.repeat)]

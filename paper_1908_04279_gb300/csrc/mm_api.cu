@@ -1008,7 +1008,8 @@ mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_
     // one pass of rows each) for about six waves of warps
     const int rpp = 32 / adj_seg(h);
     int U = 1;
-    while (U < MM_ADJ_MAX_UNITS && h->ncells * U < 6LL * 16 * h->sms &&
+    const int umax = h->prec == MM_FP64 ? MM_ADJ_MAX_UNITS : MM_ADJ_MAX_UNITS_F32;
+    while (U < umax && h->ncells * U < 6LL * 16 * h->sms &&
            h->g.ntheta / (2 * U) >= rpp)
       U *= 2;
     R.units = U;

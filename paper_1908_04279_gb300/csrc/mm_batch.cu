@@ -20,9 +20,12 @@
 namespace mm {
 
 // float64 rows need more registers than the float32 occupancy target allows
+#ifndef MM_BATCH_MIN_BLOCKS
+#define MM_BATCH_MIN_BLOCKS MM_STEP_MIN_BLOCKS
+#endif
 template <typename T>
 constexpr int batch_min_blocks() {
-  return sizeof(T) == 8 ? 3 : MM_STEP_MIN_BLOCKS;
+  return sizeof(T) == 8 ? 3 : MM_BATCH_MIN_BLOCKS;
 }
 
 template <typename T, int V, bool MASSCORR>

@@ -14,6 +14,11 @@
 
 using namespace mmh;
 
+// Widest vector (values per lane) of the float32 batched kernel (8 or 4).
+#ifndef MM_BATCH_FP32_VMAX
+#define MM_BATCH_FP32_VMAX 8
+#endif
+
 namespace mmh {
 
 struct BatchPlan {
@@ -347,7 +352,7 @@ mm_status mm_create_batch(int n, const mm_grid* grids, const mm_rates* rates, mm
     return fail(nullptr, MM_ERR_INVALID, "unknown precision");
   // one vector width for every member: float32 8 (or 4) nodes per lane,
   // float64 2, each a whole number of 16-byte vectors for the bulk copies
-  int V = prec == MM_FP64 ? 2 : 8;
+  int V = prec == MM_FP64 ? 2 : MM_BATCH_FP32_VMAX;
   for (int i = 0; i < n; ++i) {
     if (prec == MM_FP32_MIXED && grids[i].ns % 8 != 0) V = 4;
     if (grids[i].ns % V != 0 || (prec == MM_FP32_MIXED && grids[i].ns % 4 != 0))

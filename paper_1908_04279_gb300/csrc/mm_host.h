@@ -24,13 +24,16 @@ using mm::StepArgs;
 #ifndef MM_ADJ_RING
 #define MM_ADJ_RING 1
 #endif
-// Most row blocks per cell of the motor reverse kernel.
+// Most row blocks per cell of the motor reverse kernel (float64, float32).
 #ifndef MM_ADJ_MAX_UNITS
 #define MM_ADJ_MAX_UNITS 8
 #endif
+#ifndef MM_ADJ_MAX_UNITS_F32
+#define MM_ADJ_MAX_UNITS_F32 2
+#endif
 // Widest vector of the float32 adjoint kernel.
 #ifndef MM_ADJ_FP32_VMAX
-#define MM_ADJ_FP32_VMAX 4
+#define MM_ADJ_FP32_VMAX 8
 #endif
 
 namespace mmh {

@@ -317,6 +317,7 @@ mm_status run_moments(mm_handle* h) {
 
 mm_status rec_push_version(mm_handle* h);
 mm_status rec_micro_step(mm_handle* h, int n);
+int rec_tail_start(const Recording& R);
 
 }  // namespace mmh
 
@@ -821,16 +822,53 @@ mm_status rec_micro_step(mm_handle* h, int n) {
   Recording& R = h->rec;
   if (R.nsub + n > R.max_sub)
     return fail(h, MM_ERR_STATE, "recording: more substeps than mm_set_checkpointing reserved");
-  // the substeps between checkpoints run as captured graphs
+  // The substeps between checkpoints run as captured graphs. With one level,
+  // the segment the reverse sweep starts with (the last one the reservation
+  // allows) runs out of place into the recomputation slots instead, so that
+  // the sweep need not recompute it; the live state is then copied from the
+  // last slot at the end of the call.
+  const int tail = rec_tail_start(R);
   mm_status st;
+  bool in_tail = false;
   for (int i = 0; i < n;) {
-    int m = std::min(n - i, R.K - R.nsub % R.K);
+    if (R.nsub >= tail) {
+      if ((st = rec_push_substep(h)) != MM_OK) return st;
+      const int j = R.nsub - 1 - tail, c = tail / R.K;
+      StepPtrs p{j == 0 ? R.ck_psi[c] : R.sl_psi[j], j == 0 ? R.ck_nb[c] : R.sl_nb[j],
+                 j == 0 ? R.ck_mb[c] : R.sl_mb[j],   j == 0 ? R.ck_mf[c] : R.sl_mf[j],
+                 h->ucell, R.sl_psi[j + 1], R.sl_nb[j + 1], R.sl_mb[j + 1], R.sl_mf[j + 1],
+                 h->c, R.sl_cpre[j + 1]};
+      CK(launch_ptrs(h, p, h->stream));
+      h->parity ^= 1;
+      ++R.tail_done;
+      in_tail = true;
+      ++i;
+      continue;
+    }
+    int m = std::min(std::min(n - i, R.K - R.nsub % R.K), tail - R.nsub);
     for (int j = 0; j < m; ++j)
       if ((st = rec_push_substep(h)) != MM_OK) return st;
     if ((st = launch_substeps(h, m)) != MM_OK) return st;
     i += m;
   }
+  if (in_tail) {
+    const int j = R.nsub - tail;  // slot of the current state
+    const size_t t = h->tsz, nc = (size_t)h->ncells;
+    CK(cudaMemcpyAsync(h->mb, R.sl_mb[j], h->mbn * t, cudaMemcpyDeviceToDevice, h->stream));
+    CK(cudaMemcpyAsync(h->psi[h->parity], R.sl_psi[j], h->rows * t, cudaMemcpyDeviceToDevice,
+                       h->stream));
+    CK(cudaMemcpyAsync(h->nb[h->parity], R.sl_nb[j], h->rows * t, cudaMemcpyDeviceToDevice,
+                       h->stream));
+    CK(cudaMemcpyAsync(h->mf, R.sl_mf[j], nc * t, cudaMemcpyDeviceToDevice, h->stream));
+  }
   return MM_OK;
+}
+
+// First substep of the segment recorded straight into the slots (one level
+// only; none with two levels).
+int rec_tail_start(const Recording& R) {
+  if (R.K2 != R.K) return INT32_MAX;
+  return ((R.max_sub - 1) / R.K) * R.K;
 }
 
 // Before a recorded substep: the checkpoint due at its start and its velocity.
@@ -1065,6 +1103,7 @@ mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_
     rec_layout(h, c);
   }
   R.nsub = 0;
+  R.tail_done = 0;
   R.sub_vel.clear();
   R.v_ucell.clear();
   R.v_dt.clear();
@@ -1192,6 +1231,9 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
         in_mf = o_mf;
       }
     }
+    // the segment the recording wrote straight into the slots needs no replay
+    const int tail = rec_tail_start(R);
+    const bool tail_in_slots = s0 == tail && R.tail_done == n - tail;
     for (int ig = nin - 1; ig >= 0; --ig) {
       const int a0 = s0 + ig * R.K2, a1 = std::min(a0 + R.K2, s1);
       R.sl_mb[0] = ig == 0 ? R.ck_mb[sgi] : R.ick_mb[ig - 1];
@@ -1200,7 +1242,7 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
       R.sl_mf[0] = ig == 0 ? R.ck_mf[sgi] : R.ick_mf[ig - 1];
       CK(cudaMemcpyAsync(&h->prm->psi_scale, ig == 0 ? R.ck_scale + sgi : R.ick_scale + ig - 1,
                          8, cudaMemcpyDeviceToDevice, h->stream));
-      for (int tt = a0; tt < a1; ++tt) {
+      for (int tt = a0; tt < a1 && !tail_in_slots; ++tt) {
         const int i = tt - a0, ver = R.sub_vel[tt];
         if ((st = set_dt(ver)) != MM_OK) return st;
         StepPtrs p{R.sl_psi[i], R.sl_nb[i], R.sl_mb[i], R.sl_mf[i], R.v_ucell[ver],

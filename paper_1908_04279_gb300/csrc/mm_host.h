@@ -51,6 +51,7 @@ struct Recording {
   bool active = false;
   int K = 0, max_sub = 0, nsub = 0, nck = 0;
   int K2 = 0;  // inner checkpoint spacing (two levels when K2 < K; K2 = K: one level)
+  int tail_done = 0;  // substeps of the last segment recorded straight into the slots
   int nslots = 0;  // recomputed-state slots (1..nslots; slot 0 is the segment's start)
   std::vector<void*> ick_mb, ick_psi, ick_nb, ick_mf;  // inner checkpoints of one outer segment
   double* ick_scale = nullptr;

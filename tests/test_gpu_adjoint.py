@@ -310,3 +310,35 @@ def test_large512_two_level_adjoint_matches_fd(mmod):
     fd = (Lp - Lm) / (2 * h)
     print("\nLARGE512_ADJ", res["value"], res["dL_drates"][0], fd)
     assert abs(res["dL_drates"][0] - fd) <= 2e-3 * abs(fd), (res["dL_drates"][0], fd)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_recorded_tail_segment(mmod, precision):
+    """With one level of checkpoints the recording writes its last segment
+    straight into the slots (split over calls here, with a velocity change
+    inside it): the live state after the recording, the observable and the
+    gradients equal, bit for bit, those of a recording whose reservation is
+    longer (so that every segment is recomputed in the reverse sweep)."""
+    g = Grid(10, 12, 8, 16, L=1.0)
+    r = Rates(k_on=1.3, k_off=0.7, glide=0.3)
+    psi0 = psi_isotropic_perturbed(g, 41, amp=0.2)
+    u1 = random_divfree_flow(g, 42, 4, 0.3)
+    u2 = random_divfree_flow(g, 43, 4, 0.3)
+    outs, states = [], []
+    for reserve in (23, 40):
+        with mmod.Simulation(g, r, precision) as sim:
+            sim.set_state(psi0)
+            sim.set_velocity(u1)
+            sim.set_checkpointing(5, reserve)
+            sim.step(21)
+            sim.set_velocity(u2)
+            sim.step(1)
+            sim.step(1)
+            states.append(sim.get_state())
+            outs.append(sim.adjoint(23, observable="mean_stress", n_velocities=2))
+    for k in ("psi", "mb", "mf", "c"):
+        assert np.array_equal(states[0][k], states[1][k]), k
+    assert outs[0]["value"] == outs[1]["value"]
+    assert np.array_equal(outs[0]["dL_drates"], outs[1]["dL_drates"])
+    assert np.array_equal(outs[0]["dL_du"], outs[1]["dL_du"])
+    assert np.array_equal(outs[0]["dL_dpsi0"], outs[1]["dL_dpsi0"])

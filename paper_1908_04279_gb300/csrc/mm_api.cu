@@ -295,7 +295,7 @@ mm_status run_moments(mm_handle* h) {
   const double dth = 2.0 * kPi / h->g.ntheta, ds = h->g.L / h->g.ns;
   const double dA = (1.0 / h->g.nx) * (1.0 / h->g.ny);
   // the moments kernel reads rows with at most 4 values per lane
-  const int mV = std::min(h->V, 4);
+  const int mV = h->V;  // the substep's vector width (float32 8 or 4, float64 2 or 1)
   int mseg = 1;
   while (mseg < h->g.ns / mV) mseg <<= 1;
   cudaError_t e;

@@ -491,22 +491,21 @@ cudaError_t launch_moments(const T* psi, const T* mb, const T* mf, const T* c,
   const int block = 128;
   // per warp: n_b and m1 of the rows (float64), and their float-float sums
   const size_t smem = (size_t)4 * 2 * nth * sizeof(double) + (size_t)4 * nth * 16;
-  if (smem > 48 * 1024) {
-    const void* fn = V == 4 ? (const void*)k_moments<T, 4>
-                            : (V == 2 ? (const void*)k_moments<T, 2> : (const void*)k_moments<T, 1>);
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-  }
-  if (V == 4)
-    k_moments<T, 4><<<nblocks, block, smem, s>>>(psi, mb, mf, c, trig, ncells, nth, ns, seg, dth,
-                                                 ds, L, dA, fields, partial, prm);
-  else if (V == 2)
-    k_moments<T, 2><<<nblocks, block, smem, s>>>(psi, mb, mf, c, trig, ncells, nth, ns, seg, dth,
-                                                 ds, L, dA, fields, partial, prm);
-  else
-    k_moments<T, 1><<<nblocks, block, smem, s>>>(psi, mb, mf, c, trig, ncells, nth, ns, seg, dth,
-                                                 ds, L, dA, fields, partial, prm);
-  return cudaGetLastError();
+  auto go = [&](auto kern) -> cudaError_t {
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    kern<<<nblocks, block, smem, s>>>(psi, mb, mf, c, trig, ncells, nth, ns, seg, dth, ds, L, dA,
+                                      fields, partial, prm);
+    return cudaGetLastError();
+  };
+  if constexpr (sizeof(T) == 4)
+    if (V == 8) return go(k_moments<T, 8>);
+  if (V == 4) return go(k_moments<T, 4>);
+  if (V == 2) return go(k_moments<T, 2>);
+  return go(k_moments<T, 1>);
 }
 
 template cudaError_t launch_convert<float, double>(float*, const double*, size_t, const double*,

@@ -533,7 +533,9 @@ def run_ours(args):
                                             "peak_source": peak_src,
                                             "traffic": read_profile_traffic(
                                                 "k_substep_batch", "ensemble64", "fp32")}),
-            "gpu_launches": args.steps * (nsub + 3),
+            # per macro step: set_velocity (precision conversion, per-cell velocity
+            # block, the two substep-rule kernels), nsub substeps, moments
+            "gpu_launches": args.steps * (nsub + 5),
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

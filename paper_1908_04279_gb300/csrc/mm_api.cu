@@ -1053,7 +1053,6 @@ mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_
     R.units = U;
     R.rows_per_unit = (h->g.ntheta + U - 1) / U;
     R.grid_psi = (int)std::min<long long>((h->ncells + 3) / 4, 16LL * h->sms);
-    R.grid_motor = (int)std::min<long long>((h->ncells * U + 3) / 4, 16LL * h->sms);
     // bulk-copy ring for the motor kernel: 16-byte rows and row-column slices,
     // chunks of RC rows (dividing a unit) of at most 2 KB per array
     R.ring_rc = R.ring_ch = R.ring_s = 0;

@@ -163,24 +163,6 @@ __device__ __forceinline__ void ff_merge(FF& a, const FF& b) {
 // Row sums of the V values a lane holds, reduced over the row's `seg` lanes;
 // every lane of the segment gets (n_b / ds, m1 / ds) in float64.
 template <int V>
-__device__ __forceinline__ void row_sums(const float (&m)[V], const float (&sj)[V], int seg,
-                                         double& nb, double& m1) {
-  FF a{0.f, 0.f}, b{0.f, 0.f};
-#pragma unroll
-  for (int v = 0; v < V; ++v) {
-    ff_add(a, m[v]);
-    ff_add_prod(b, sj[v], m[v]);
-  }
-  for (int o = seg >> 1; o > 0; o >>= 1) {
-    FF ao{__shfl_xor_sync(0xffffffffu, a.hi, o, seg), __shfl_xor_sync(0xffffffffu, a.lo, o, seg)};
-    FF bo{__shfl_xor_sync(0xffffffffu, b.hi, o, seg), __shfl_xor_sync(0xffffffffu, b.lo, o, seg)};
-    ff_merge(a, ao);
-    ff_merge(b, bo);
-  }
-  nb = (double)a.hi + (double)a.lo;
-  m1 = (double)b.hi + (double)b.lo;
-}
-template <int V>
 __device__ __forceinline__ void row_sums(const double (&m)[V], const double (&sj)[V], int seg,
                                          double& nb, double& m1) {
   double a = 0.0, b = 0.0;

@@ -227,3 +227,38 @@ def patch_substep(grid, rates, dt_, u, psi, mb, mf, mtot, cells):
         out.append(dict(psi=st.psi[1, 1].copy(), mb=st.mb[1, 1].copy(), mf=float(st.mf[1, 1]),
                         c=float(st.c[1, 1])))
     return out
+
+
+def _cn_factor(n: int, a: float) -> tuple[np.ndarray, np.ndarray]:
+    """Dense matrices (I - a/2 L, I + a/2 L) of one Crank-Nicolson step along a
+    periodic line of n points, L the periodic second difference
+    (L psi)_i = psi_{i-1} - 2 psi_i + psi_{i+1} (indices mod n), a = D dt / h^2."""
+    L = np.zeros((n, n))
+    for i in range(n):
+        L[i, i] -= 2.0
+        L[i, (i - 1) % n] += 1.0
+        L[i, (i + 1) % n] += 1.0
+    eye = np.eye(n)
+    return eye - 0.5 * a * L, eye + 0.5 * a * L
+
+
+def diffuse(grid, psi, D_t: float, D_r: float, dt: float) -> np.ndarray:
+    """One step of filament diffusion, the -D_t grad ln psi and
+    -D_r d_theta ln psi fluxes of Eq. 2-3 (d_t psi = D_t lap_x psi +
+    D_r d_theta^2 psi), by Crank-Nicolson (Sec. 2, Alg. 1: the diffusive terms
+    of the psi update) applied one direction at a time -- theta, then x, then
+    y -- each a periodic second difference (h = dtheta, dx = 1/nx, dy = 1/ny)
+    solved exactly with a dense linear solve. psi is [ny][nx][nth]; returns
+    the new array."""
+    g = grid
+    out = np.array(psi, dtype=np.float64, copy=True)
+    for axis, n, h, D in ((2, g.ntheta, 2 * np.pi / g.ntheta, D_r), (1, g.nx, 1.0 / g.nx, D_t),
+                          (0, g.ny, 1.0 / g.ny, D_t)):
+        if D == 0.0:
+            continue
+        A, B = _cn_factor(n, D * dt / (h * h))
+        lines = np.moveaxis(out, axis, -1)  # [..., n]
+        flat = lines.reshape(-1, n)
+        new = np.linalg.solve(A, B @ flat.T).T
+        out = np.moveaxis(new.reshape(lines.shape), -1, axis)
+    return np.ascontiguousarray(out)

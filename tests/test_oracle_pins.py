@@ -531,3 +531,64 @@ def test_patch_substep_equals_full_grid(oracle_mod):
         assert np.array_equal(c["psi"], full.psi[iy, ix])
         assert np.array_equal(c["mb"], full.mb[iy, ix])
         assert c["mf"] == full.mf[iy, ix] and c["c"] == full.c[iy, ix]
+
+
+# ---- filament diffusion (next row f1): Crank-Nicolson per direction
+
+
+def _mode_psi(g, mx, my, k, eps=0.1):
+    x = (np.arange(g.nx) + 0.5) / g.nx
+    y = (np.arange(g.ny) + 0.5) / g.ny
+    th = np.arange(g.ntheta) * 2 * np.pi / g.ntheta
+    return 1.0 + eps * (np.cos(2 * np.pi * my * y)[:, None, None] *
+                        np.cos(2 * np.pi * mx * x)[None, :, None] * np.cos(k * th)[None, None, :])
+
+
+def test_diffusion_fourier_mode_closed_form(oracle_mod):
+    """A Fourier mode is an eigenvector of every periodic second difference:
+    one step multiplies its amplitude by the product over directions of
+    (1 - a (1 - cos kappa h)) / (1 + a (1 - cos kappa h)), a = D dt / h^2, and
+    leaves the mean unchanged."""
+    g = Grid(10, 12, 16, 4)
+    D_t, D_r, dt = 0.003, 0.7, 0.05
+    mx, my, k = 2, 3, 5
+    psi = _mode_psi(g, mx, my, k)
+    out = oracle_mod.diffuse(g, psi, D_t, D_r, dt)
+
+    def amp(n, h, D, m):
+        a = D * dt / h ** 2
+        q = a * (1 - np.cos(2 * np.pi * m / n))
+        return (1 - q) / (1 + q)
+    fac = amp(g.nx, 1 / g.nx, D_t, mx) * amp(g.ny, 1 / g.ny, D_t, my) * amp(
+        g.ntheta, 2 * np.pi / g.ntheta, D_r, k)
+    expect = 1.0 + fac * (psi - 1.0)
+    assert np.max(np.abs(out - expect)) <= 1e-14
+    assert 0 < fac < 1
+
+
+def test_diffusion_conserves_and_commutes(oracle_mod):
+    """The periodic Crank-Nicolson step conserves sum psi to round-off, is the
+    identity at zero diffusivity, and (the 1-D operators commute) does not
+    depend on the order of the directions."""
+    g = Grid(7, 9, 6, 4)
+    psi = psi_isotropic_perturbed(g, 8, amp=0.4)
+    out = oracle_mod.diffuse(g, psi, 0.01, 0.3, 0.2)
+    assert abs(out.sum() - psi.sum()) <= 1e-13 * psi.sum()
+    assert np.array_equal(oracle_mod.diffuse(g, psi, 0.0, 0.0, 0.2), psi)
+    # the opposite order (y, then x, then theta) with the same 1-D operators
+    Mt = np.linalg.solve(*oracle_mod._cn_factor(g.ntheta, 0.3 * 0.2 / (2 * np.pi / g.ntheta) ** 2))
+    Mx = np.linalg.solve(*oracle_mod._cn_factor(g.nx, 0.01 * 0.2 * g.nx ** 2))
+    My = np.linalg.solve(*oracle_mod._cn_factor(g.ny, 0.01 * 0.2 * g.ny ** 2))
+    step = np.einsum("ab,bxk->axk", My, psi)
+    step = np.einsum("ab,ybk->yak", Mx, step)
+    step = np.einsum("ab,yxb->yxa", Mt, step)
+    assert np.max(np.abs(step - out)) <= 1e-13
+
+
+def test_diffusion_large_step_is_stable_and_smooths(oracle_mod):
+    """Unconditional stability: a step far beyond the explicit limit keeps
+    every Fourier amplitude below one in magnitude (the extreme value drops)."""
+    g = Grid(8, 8, 8, 4)
+    psi = psi_isotropic_perturbed(g, 9, amp=0.5)
+    out = oracle_mod.diffuse(g, psi, 0.5, 5.0, 10.0)
+    assert np.linalg.norm(out - out.mean()) < np.linalg.norm(psi - psi.mean())

@@ -213,6 +213,25 @@ mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_
 mm_status mm_adjoint_step(mm_handle* h, int n_substeps, const mm_adjoint_seed* seed,
                           mm_adjoint_out* out);
 
+/* ---- Filament diffusion --------------------------------------------------------
+ *
+ * mm_diffuse(h, D_t, D_r, dt): one step of the diffusive fluxes of Eq. 2-3,
+ * -D_t grad ln psi and -D_r d_theta ln psi, i.e. d_t psi = D_t (d_xx + d_yy) psi
+ * + D_r d_theta^2 psi on the periodic grid (dx = 1/nx, dy = 1/ny,
+ * dtheta = 2 pi / ntheta), by Crank-Nicolson (the scheme Sec. 2 and Alg. 1
+ * give the diffusive terms of the psi update) applied one direction at a time:
+ * theta, then x, then y, each (I - a/2 L) psi' = (I + a/2 L) psi with L the
+ * periodic second difference and a = D dt / h^2 (unconditionally stable,
+ * second order; the one-dimensional operators commute). Meant once per macro
+ * step with the macro step's dt, before its substeps (Alg. 1 updates psi before
+ * the motor loop). Then recomputes the coarse density C = sum psi n_b dtheta,
+ * the Alg. 2 scale-down and Mf = M - C for the new psi. Not differentiated:
+ * MM_ERR_STATE while an adjoint recording is active. MM_ERR_INVALID for a
+ * negative or non-finite diffusivity or a non-positive dt. No counterpart in
+ * the microscale step of the paper's GPU code (the paper solves this on the
+ * CPU). */
+mm_status mm_diffuse(mm_handle* h, double D_t, double D_r, double dt);
+
 /* ---- Batched ensemble --------------------------------------------------------
  *
  * An ensemble of n independent instances (an instance as above: its own grid,

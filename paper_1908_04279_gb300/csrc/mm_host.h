@@ -115,6 +115,7 @@ struct mm_handle {
   double* partial = nullptr;
   double* fields = nullptr;
   double* staging = nullptr;
+  double* diff_tab = nullptr;  // Crank-Nicolson factors of the three directions (mm_diffuse)
   size_t staging_n = 0;  // float64 values the staging buffer holds
   DevParams* prm = nullptr;
   int npartial = 0;

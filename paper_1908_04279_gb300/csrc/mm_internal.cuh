@@ -180,6 +180,16 @@ template <typename T>
 cudaError_t launch_adj_psi0(const T* lpsi, const T* lmf, int units, const T* nb, double dth,
                             long long rows, int nth, double* out, cudaStream_t s);
 
+// Filament diffusion (mm_diffuse.cu): Crank-Nicolson along one direction
+// (mode 0 theta, 1 x, 2 y) for every line of psi; tab holds the host-computed
+// factors cp[n], inv_m[n], z[n]; scale (device, may be NULL) multiplies psi
+// on load.
+template <typename T>
+cudaError_t launch_cn_lines(T* psi, int mode, int nx, int ny, int nth, const double* tab, int n,
+                            double c, double ha, double r, double vzf, const double* scale,
+                            cudaStream_t s);
+cudaError_t launch_set_scale_one(double* scale, cudaStream_t s);
+
 // Message returned by mm_last_error(NULL) on this thread.
 void set_thread_error(const char* msg);
 

@@ -88,6 +88,7 @@ PROTOTYPES = {
     "mm_adjoint_step": ([_H, C.c_int, C.POINTER(mm_adjoint_seed), C.POINTER(mm_adjoint_out)],
                         C.c_int),
     "mm_sync": ([_H], C.c_int),
+    "mm_diffuse": ([_H, C.c_double, C.c_double, C.c_double], C.c_int),
     "mm_debug_set": ([_H, C.c_uint, C.c_uint], C.c_int),
     "mm_get_launch_info": ([_H, C.POINTER(C.c_int), C.c_int], C.c_int),
     "mm_moments_static": ([C.POINTER(mm_grid), C.POINTER(mm_rates), _P, _P, _P, _P, _P, _P, _P],
@@ -253,6 +254,10 @@ class Simulation:
     def step(self, n: int):
         self._check(self.lib.mm_micro_step(self.h, int(n)))
 
+    def diffuse(self, D_t: float, D_r: float, dt: float):
+        """One Crank-Nicolson step of filament diffusion (mm_diffuse)."""
+        self._check(self.lib.mm_diffuse(self.h, float(D_t), float(D_r), float(dt)))
+
     def sync(self):
         self._check(self.lib.mm_sync(self.h))
 
@@ -372,6 +377,10 @@ class Batch:
 
     def step(self, n: int):
         self._check(self.lib.mm_micro_step(self.h, int(n)))
+
+    def diffuse(self, D_t: float, D_r: float, dt: float):
+        """One Crank-Nicolson step of filament diffusion (mm_diffuse)."""
+        self._check(self.lib.mm_diffuse(self.h, float(D_t), float(D_r), float(dt)))
 
     def sync(self):
         self._check(self.lib.mm_sync(self.h))

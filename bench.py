@@ -424,6 +424,34 @@ def run_ours(args):
         out["checkpoints"] = "outer every 100 substeps (21), inner every 10 (9), 10 slots"
         return out
 
+    def diffusion_run():
+        """Filament diffusion (mm_diffuse, Crank-Nicolson per direction) on the
+        large512 state, float32: events around one call (the three directions
+        and the re-derived coarse density, which reads the motor density),
+        and around the psi solves alone."""
+        wl = WORKLOADS["large512"]
+        gl = wl["grid"]
+        sim = mm.Simulation(gl, r, "fp32", stream=stream.cuda_stream)
+        sim.set_state(psi_isotropic_perturbed(gl, wl["seed"]))
+        sim.set_velocity(torch.tensor(workload_velocity("large512", 0), device=dev))
+        sim.step(2)
+        sim.diffuse(1e-3, 0.1, 0.01)
+        ts = []
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.diffuse(1e-3, 0.1, 0.01)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        sim.sync()
+        sim.close()
+        psi_bytes = gl.nx * gl.ny * gl.ntheta * 4
+        return {"workload": "large512 psi (512x512 x 64, float32), D_t = 1e-3, D_r = 0.1",
+                "ms_per_call": min(ts),
+                "algorithmic_bytes_psi_solves": 3 * 3 * 2 * psi_bytes,
+                "algorithmic_bytes_reinit": gl.micro_cells * 4 + 3 * psi_bytes}
+
     def ensemble_run(steps):
         """ensemble64: 64 members with uneven grids (N in {32..128}, Ntheta and
         Ns in {16, 32}), k_off log-uniform in [0.05, 5], v_walk in [0.5, 2];
@@ -483,6 +511,7 @@ def run_ours(args):
              "fp32": large_run("fp32", 10), "fp64": large_run("fp64", 3)}
     ens = ensemble_run(max(2, min(args.steps, 3)))
     large_adj = large_adjoint_run()
+    diff = diffusion_run()
 
     total_ms, kern_ms, fp64_ms, e2e_s = reduce_max([total_ms, kern_ms, fp64_ms, e2e_s], dev)
 
@@ -526,6 +555,7 @@ def run_ours(args):
                                            "k_substep", "large512", "fp32")}),
             "large512_adjoint": dict(
                 large_adj, workload="large512, 2000 substeps, float32, mean active stress vs k_off"),
+            "diffusion": diff,
             "ensemble": dict(ens, roofline={"bound": "hbm", "peak": peak, "unit": "GB/s",
                                             "achieved": ens["achieved_gbs"],
                                             "frac": ens["achieved_gbs"] / peak,

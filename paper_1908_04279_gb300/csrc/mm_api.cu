@@ -691,35 +691,6 @@ mm_status launch_substeps(mm_handle* h, int n) {
 
 extern "C" {
 
-// Crank-Nicolson factors of one periodic direction of n >= 2 points with
-// a = D dt / h^2: the matrix I - a/2 L (diagonal b = 1 + a, off-diagonals and
-// corners c = -a/2) is T + u v^T with T tridiagonal (corners removed,
-// T_00 = b - gamma, T_{n-1,n-1} = b - c^2 / gamma, gamma = -b), u = (gamma, 0..,
-// 0, c), v = (1, 0.., 0, c / gamma). Returns cp[n], 1/m[n] of T's Thomas
-// elimination and z = T^{-1} u in tab, and r = c / gamma, vzf = 1 / (1 + v.z).
-static void cn_factors(int n, double a, double* tab, double* r, double* vzf) {
-  const double b = 1.0 + a, c = -0.5 * a, gamma = -b;
-  double* cp = tab;
-  double* im = tab + n;
-  double* z = tab + 2 * n;
-  for (int i = 0; i < n; ++i) {
-    double diag = b;
-    if (i == 0) diag = b - gamma;
-    if (i == n - 1) diag = b - c * c / gamma;
-    const double m = i == 0 ? diag : diag - c * cp[i - 1];
-    im[i] = 1.0 / m;
-    cp[i] = c / m;
-  }
-  // T z = u
-  for (int i = 0; i < n; ++i) {
-    const double ui = i == 0 ? gamma : (i == n - 1 ? c : 0.0);
-    z[i] = (ui - (i == 0 ? 0.0 : c * z[i - 1])) * im[i];
-  }
-  for (int i = n - 2; i >= 0; --i) z[i] -= cp[i] * z[i + 1];
-  *r = c / gamma;
-  *vzf = 1.0 / (1.0 + z[0] + *r * z[n - 1]);
-}
-
 mm_status mm_diffuse(mm_handle* h, double D_t, double D_r, double dt) {
   if (!h) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
@@ -731,37 +702,32 @@ mm_status mm_diffuse(mm_handle* h, double D_t, double D_r, double dt) {
     return fail(h, MM_ERR_STATE, "diffusion is not differentiated: end the adjoint recording first");
   DeviceGuard dg(h->device);
   const int nx = h->g.nx, ny = h->g.ny, nth = h->g.ntheta;
-  if (!h->diff_tab) CK(cudaMalloc((void**)&h->diff_tab, (size_t)3 * (nth + nx + ny) * 8));
+  if (!h->diff_tab) CK(cudaMalloc((void**)&h->diff_tab, (size_t)(3 * (nth + nx + ny) + 6) * 8));
   struct Dir {
     int mode, n;
     double hh, D;
-    size_t off;
+    double* tab;
   };
-  const Dir dirs[3] = {{0, nth, 2.0 * kPi / nth, D_r, 0},
-                       {1, nx, 1.0 / nx, D_t, (size_t)3 * nth},
-                       {2, ny, 1.0 / ny, D_t, (size_t)3 * (nth + nx)}};
-  std::vector<double> tab((size_t)3 * (nth + nx + ny), 0.0);
-  double r[3] = {0, 0, 0}, vzf[3] = {0, 0, 0};
-  for (int d = 0; d < 3; ++d)
-    if (dirs[d].D > 0.0 && dirs[d].n >= 2)
-      cn_factors(dirs[d].n, dirs[d].D * dt / (dirs[d].hh * dirs[d].hh), tab.data() + dirs[d].off,
-                 &r[d], &vzf[d]);
-  CK(cudaMemcpyAsync(h->diff_tab, tab.data(), tab.size() * 8, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaStreamSynchronize(h->stream));  // the host table may go out of scope
+  const Dir dirs[3] = {{0, nth, 2.0 * kPi / nth, D_r, h->diff_tab},
+                       {1, nx, 1.0 / nx, D_t, h->diff_tab + 3 * nth + 2},
+                       {2, ny, 1.0 / ny, D_t, h->diff_tab + 3 * (nth + nx) + 4}};
+  double a[3];
+  for (int d = 0; d < 3; ++d) a[d] = dirs[d].D * dt / (dirs[d].hh * dirs[d].hh);
+  CK(mm::launch_cn_factors(dirs[0].tab, nth, a[0], dirs[1].tab, nx, a[1], dirs[2].tab, ny, a[2],
+                           h->stream));
   bool first = true;
   for (int d = 0; d < 3; ++d) {
     if (!(dirs[d].D > 0.0) || dirs[d].n < 2) continue;  // a single point: L = 0
-    const double a = dirs[d].D * dt / (dirs[d].hh * dirs[d].hh);
     // the float32 form folds the pending mass-correction factor into psi
     const double* sc = (first && h->prec == MM_FP32_MIXED) ? &h->prm->psi_scale : nullptr;
     cudaError_t e =
         h->prec == MM_FP64
             ? mm::launch_cn_lines<double>((double*)h->psi[h->parity], dirs[d].mode, nx, ny, nth,
-                                          h->diff_tab + dirs[d].off, dirs[d].n, -0.5 * a, 0.5 * a,
-                                          r[d], vzf[d], sc, h->stream)
+                                          dirs[d].tab, dirs[d].n, -0.5 * a[d], 0.5 * a[d], sc,
+                                          h->stream)
             : mm::launch_cn_lines<float>((float*)h->psi[h->parity], dirs[d].mode, nx, ny, nth,
-                                         h->diff_tab + dirs[d].off, dirs[d].n, -0.5 * a, 0.5 * a,
-                                         r[d], vzf[d], sc, h->stream);
+                                         dirs[d].tab, dirs[d].n, -0.5 * a[d], 0.5 * a[d], sc,
+                                         h->stream);
     CK(e);
     first = false;
   }

@@ -180,14 +180,15 @@ template <typename T>
 cudaError_t launch_adj_psi0(const T* lpsi, const T* lmf, int units, const T* nb, double dth,
                             long long rows, int nth, double* out, cudaStream_t s);
 
-// Filament diffusion (mm_diffuse.cu): Crank-Nicolson along one direction
-// (mode 0 theta, 1 x, 2 y) for every line of psi; tab holds the host-computed
-// factors cp[n], inv_m[n], z[n]; scale (device, may be NULL) multiplies psi
-// on load.
+// Filament diffusion (mm_diffuse.cu): the Crank-Nicolson factors of the three
+// directions (3 n + 2 values each), then one direction (mode 0 theta, 1 x,
+// 2 y) for every line of psi; scale (device, may be NULL) multiplies psi on
+// load.
+cudaError_t launch_cn_factors(double* tab0, int n0, double a0, double* tab1, int n1, double a1,
+                              double* tab2, int n2, double a2, cudaStream_t s);
 template <typename T>
 cudaError_t launch_cn_lines(T* psi, int mode, int nx, int ny, int nth, const double* tab, int n,
-                            double c, double ha, double r, double vzf, const double* scale,
-                            cudaStream_t s);
+                            double c, double ha, const double* scale, cudaStream_t s);
 cudaError_t launch_set_scale_one(double* scale, cudaStream_t s);
 
 // Message returned by mm_last_error(NULL) on this thread.

@@ -333,6 +333,66 @@ int or_substep(const or_grid* g, const or_rates* r, double dt, const double* u,
   return OR_OK;
 }
 
+/* Motor kinetics over a macro interval T with psi frozen and a local substep
+ * in every cell -- Alg. 2's "while t* < t*_end" loop per anchor with the
+ * independent time steps of Sec. 3.1 (anchors in the filament's own cell).
+ * With psi frozen the cells are independent and only the motor rates of
+ * Eq. 4 bound the step: rate_i = max(v/ds, k_off + k_on L rho_i),
+ * rho_i = sum_k psi dtheta (summed in k order), n_i = max(1, ceil(T rate_i /
+ * cfl)) equal substeps of dt_i = T / n_i, each the Alg. 2 body (the RK2 half
+ * and full stage of Eq. 4 with Mf frozen over the stages, Eq. 5 with the
+ * frozen psi, the scale-down, Eq. 6). nsteps_in (may be NULL) imposes n_i per
+ * cell instead; nsteps_out (may be NULL) receives the n_i used. mb, mf, c are
+ * updated in place. */
+int or_motor_local(const or_grid* g, const or_rates* r, double T, const double* psi, double* mb,
+                   double* mf, double* c, const double* mtot, const int* nsteps_in,
+                   int* nsteps_out) {
+  if (!grid_ok(g) || !r || !psi || !mb || !mf || !c || !mtot) return OR_ERR_INVALID;
+  if (!(T > 0.0)) return OR_ERR_INVALID;
+  int ns = g->ns;
+  double ds = ds_of(g), dth = dth_of(g);
+  double* buf = (double*)malloc(sizeof(double) * (5 * (size_t)ns + 2));
+  if (!buf) return OR_ERR_NOMEM;
+  double *R = buf, *Ms = buf + ns, *Mss = buf + 2 * ns, *Phi = buf + 3 * ns;
+  for (size_t i = 0; i < ncell(g); ++i) {
+    int n;
+    if (nsteps_in) {
+      n = nsteps_in[i];
+    } else {
+      double rho = 0.0;
+      for (int k = 0; k < g->nth; ++k) rho += psi[i * g->nth + k] * dth;
+      double rate = dmax(r->v_walk / ds, r->k_off + r->k_on * g->L * rho);
+      double q = ceil(T * rate / r->cfl);
+      n = q < 1.0 ? 1 : (int)q;
+    }
+    if (nsteps_out) nsteps_out[i] = n;
+    double dt = T / n;
+    for (int step = 0; step < n; ++step) {
+      double Cpre = 0.0;
+      for (int k = 0; k < g->nth; ++k) {
+        double* M = mb + (i * g->nth + k) * ns;
+        motor_rhs(g, r, M, mf[i], Phi, R);
+        for (int j = 0; j < ns; ++j) Ms[j] = M[j] + 0.5 * dt * R[j];
+        motor_rhs(g, r, Ms, mf[i], Phi, R);
+        for (int j = 0; j < ns; ++j) Mss[j] = M[j] + dt * R[j];
+        double nbk = 0.0;
+        for (int j = 0; j < ns; ++j) { M[j] = Mss[j]; nbk += Mss[j] * ds; }
+        Cpre += psi[i * g->nth + k] * nbk * dth; /* Eq. 5, psi frozen */
+      }
+      double C = Cpre;
+      if (mtot[i] < Cpre) { /* Alg. 2 scale-down */
+        double f = mtot[i] / Cpre;
+        for (size_t q = i * g->nth * ns; q < (i + 1) * g->nth * ns; ++q) mb[q] *= f;
+        C = mtot[i];
+      }
+      c[i] = C;
+      mf[i] = mtot[i] - C; /* Eq. 6 */
+    }
+  }
+  free(buf);
+  return OR_OK;
+}
+
 int or_run(const or_grid* g, const or_rates* r, double dt, const double* u, double* psi,
            double* mb, double* mf, double* c, const double* mtot, int nsub) {
   for (int n = 0; n < nsub; ++n) {

@@ -63,6 +63,8 @@ def _load():
             lib.or_moments.argtypes = [G, R, P, P, P, P, P, P]
             lib.or_tangent_substep.argtypes = [G, R, C.c_double, P, P, P, P, P, P, P, P, P, P]
             lib.or_adjoint_substep.argtypes = [G, R, C.c_double, P, P, P, P, P, P, P, P, P, P]
+            IP = C.POINTER(C.c_int)
+            lib.or_motor_local.argtypes = [G, R, C.c_double, P, P, P, P, P, IP, IP]
             _lib = lib
     return _lib
 
@@ -262,3 +264,20 @@ def diffuse(grid, psi, D_t: float, D_r: float, dt: float) -> np.ndarray:
         new = np.linalg.solve(A, B @ flat.T).T
         out = np.moveaxis(new.reshape(lines.shape), -1, axis)
     return np.ascontiguousarray(out)
+
+
+def motor_local(grid, rates, state: State, T: float, nsteps=None) -> np.ndarray:
+    """Motor kinetics over T with psi frozen and a local substep per cell
+    (or_motor_local), in place; nsteps (int array [ny][nx], optional) imposes
+    the substeps per cell. Returns the substeps used per cell."""
+    out = np.zeros((grid.ny, grid.nx), dtype=np.int32)
+    IP = C.POINTER(C.c_int)
+    nin = None
+    if nsteps is not None:
+        nin = np.ascontiguousarray(nsteps, dtype=np.int32)
+    _check(_load().or_motor_local(C.byref(_grid(grid)), C.byref(_rates(rates)), float(T),
+                                  _p(state.psi), _p(state.mb), _p(state.mf), _p(state.c),
+                                  _p(state.mtot),
+                                  nin.ctypes.data_as(IP) if nin is not None else None,
+                                  out.ctypes.data_as(IP)), "motor_local")
+    return out

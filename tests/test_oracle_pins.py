@@ -592,3 +592,54 @@ def test_diffusion_large_step_is_stable_and_smooths(oracle_mod):
     psi = psi_isotropic_perturbed(g, 9, amp=0.5)
     out = oracle_mod.diffuse(g, psi, 0.5, 5.0, 10.0)
     assert np.linalg.norm(out - out.mean()) < np.linalg.norm(psi - psi.mean())
+
+
+# ---- local substeps with psi frozen (next row f4)
+
+
+def test_motor_local_equals_global_substeps_for_uniform_psi(oracle_mod):
+    """With the same psi everywhere every cell takes the same local step, and
+    with no flow and no gliding psi stays put: the local-step motor update is
+    bit for bit the global substep of the hot path with dt = T / n."""
+    g = Grid(5, 4, 6, 12)
+    r = Rates(k_on=1.7, k_off=0.6, v_walk=0.8, glide=0.0, v_sp=0.0)
+    psi = psi_isotropic_perturbed(g, 61, amp=0.0)
+    rng = np.random.default_rng(62)
+    mb = 0.2 * rng.random((g.ny, g.nx, g.ntheta, g.ns))
+    a = oracle_mod.make_state(g, psi, mb)
+    b = a.copy()
+    T = 0.37
+    n = oracle_mod.motor_local(g, r, a, T)
+    assert np.all(n == n[0, 0]) and n[0, 0] > 1
+    oracle_mod.run(g, r, b, np.zeros((2, g.ny, g.nx)), T / n[0, 0], int(n[0, 0]))
+    for k in ("mb", "mf", "c"):
+        assert np.array_equal(getattr(a, k), getattr(b, k)), k
+    assert np.array_equal(b.psi, psi)
+
+
+def test_motor_local_bind_unbind_closed_form_per_cell(oracle_mod):
+    """No walking: each cell relaxes by its own lagged bind/unbind recursion
+    M^n = M_inf (1 - r^n) (as for the global step) with its own density rho_i,
+    step count n_i = ceil(T (k_off + k_on L rho_i) / cfl) and dt_i = T / n_i."""
+    g = Grid(4, 3, 8, 6)
+    r = Rates(k_on=1.2, k_off=0.5, v_walk=0.0, glide=0.0)
+    dens = 1.0 / (2 * np.pi) * (0.5 + np.arange(g.nx * g.ny).reshape(g.ny, g.nx) / 6.0)
+    psi = np.repeat(dens[:, :, None], g.ntheta, axis=2)
+    st = oracle_mod.make_state(g, psi)
+    T = 0.9
+    n = oracle_mod.motor_local(g, r, st, T)
+    for iy in range(g.ny):
+        for ix in range(g.nx):
+            rho = dens[iy, ix] * 2 * np.pi
+            ni = max(1, math.ceil(T * (r.k_off + r.k_on * g.L * rho) / r.cfl))
+            assert n[iy, ix] == ni
+            dt = T / ni
+            A = 1 - r.k_off * dt + (r.k_off * dt) ** 2 / 2
+            B = r.k_on * dt * (1 - r.k_off * dt / 2)
+            rr = A - B * rho * g.L
+            Minf = B * 1.0 / (1 - A + B * rho * g.L)
+            expect = Minf * (1 - rr ** ni)
+            assert np.max(np.abs(st.mb[iy, ix] - expect)) <= 1e-13 * max(1.0, abs(expect))
+    # different densities, different step counts
+    assert len(np.unique(n)) > 1
+    np.testing.assert_allclose(st.mf + st.c, 1.0, rtol=0, atol=1e-14)

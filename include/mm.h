@@ -232,6 +232,34 @@ mm_status mm_adjoint_step(mm_handle* h, int n_substeps, const mm_adjoint_seed* s
  * CPU). */
 mm_status mm_diffuse(mm_handle* h, double D_t, double D_r, double dt);
 
+/* ---- Local substeps with psi frozen -------------------------------------------
+ *
+ * mm_motor_local(h, T, nsteps_in, nsteps_out, on_device): advance the motor
+ * densities over a macro interval T with psi held fixed and a substep of its
+ * own in every cell -- the independent time steps of Sec. 3.1, Alg. 2's
+ * "while t* < t*_end" loop run per anchor (anchors in the filament's own
+ * cell). Per cell i:
+ *   rho_i = sum_k psi dtheta, rate_i = max(v_walk/ds, k_off + k_on L rho_i),
+ *   n_i = max(1, ceil(T rate_i / cfl)) (evaluated in float64, left to right,
+ *   with no fused operations), dt_i = T / n_i;
+ * then n_i times: every s-row by the midpoint RK2 of Eq. 4 (Mf frozen over the
+ * two stages), C = sum_k psi n_b dtheta (Eq. 5, psi frozen), the Alg. 2
+ * scale-down where C > M, Mf = M - C (Eq. 6). psi and the substep dt of
+ * mm_micro_step are not touched; n_b, C and Mf are left consistent with the new
+ * Mb. nsteps_in (NULL: the rule above) imposes n_i per cell ([ny][nx] ints,
+ * each in 1..2^20); nsteps_out (may be NULL) receives the n_i used. on_device
+ * says whether these two are device pointers (stream order) or host pointers
+ * (then the call synchronises). A computed count above 2^20 (T far beyond the
+ * cell's stable step) leaves the whole motor state unchanged and is reported as
+ * MM_ERR_INVALID by this call (host nsteps_out) or by the next synchronising
+ * call. MM_ERR_INVALID for T <= 0 or not finite or a host count out of range;
+ * MM_ERR_STATE without a state or while an adjoint recording is active (not
+ * differentiated); MM_ERR_UNSUPPORTED when one cell's ntheta * ns values do not
+ * fit in shared memory (about 200 KB); MM_ERR_TIMEOUT (at the next synchronising
+ * call) if a bounded device wait gave up. */
+mm_status mm_motor_local(mm_handle* h, double T, const int* nsteps_in, int* nsteps_out,
+                         int on_device);
+
 /* ---- Batched ensemble --------------------------------------------------------
  *
  * An ensemble of n independent instances (an instance as above: its own grid,

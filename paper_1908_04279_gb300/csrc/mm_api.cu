@@ -33,6 +33,7 @@ mm_status free_all(mm_handle* h) {
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
   if (h->diff_tab) cudaFree(h->diff_tab);
+  if (h->local_n) cudaFree(h->local_n);
   void* ptrs[] = {h->mb,  h->psi[0], h->psi[1], h->nb[0],   h->nb[1],
                   h->mf,  h->c,      h->mtot,   h->u,       h->u64,    h->trig,
                   h->trig64, h->partial, h->fields, h->staging, h->prm, h->ucell};
@@ -223,6 +224,9 @@ mm_status check_status(mm_handle* h) {
     CK(cudaMemcpy(&h->prm->counter, zeros, sizeof zeros, cudaMemcpyHostToDevice));
     if (st & 1)
       return fail(h, MM_ERR_TIMEOUT, "a bounded wait in the substep kernel gave up; the state is invalid");
+    if (st & 4)
+      return fail(h, MM_ERR_INVALID,
+                  "mm_motor_local: a substep count came out of 1..2^20; the motor state was left unchanged");
     return fail(h, MM_ERR_NONFINITE, "the substep rule found no positive finite rate");
   }
   return MM_OK;

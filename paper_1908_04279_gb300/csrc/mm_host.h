@@ -116,6 +116,7 @@ struct mm_handle {
   double* fields = nullptr;
   double* staging = nullptr;
   double* diff_tab = nullptr;  // Crank-Nicolson factors of the three directions (mm_diffuse)
+  int* local_n = nullptr;      // [cells] substeps per cell of mm_motor_local
   size_t staging_n = 0;  // float64 values the staging buffer holds
   DevParams* prm = nullptr;
   int npartial = 0;

@@ -89,6 +89,7 @@ PROTOTYPES = {
                         C.c_int),
     "mm_sync": ([_H], C.c_int),
     "mm_diffuse": ([_H, C.c_double, C.c_double, C.c_double], C.c_int),
+    "mm_motor_local": ([_H, C.c_double, _P, _P, C.c_int], C.c_int),
     "mm_debug_set": ([_H, C.c_uint, C.c_uint], C.c_int),
     "mm_get_launch_info": ([_H, C.POINTER(C.c_int), C.c_int], C.c_int),
     "mm_moments_static": ([C.POINTER(mm_grid), C.POINTER(mm_rates), _P, _P, _P, _P, _P, _P, _P],
@@ -257,6 +258,33 @@ class Simulation:
     def diffuse(self, D_t: float, D_r: float, dt: float):
         """One Crank-Nicolson step of filament diffusion (mm_diffuse)."""
         self._check(self.lib.mm_diffuse(self.h, float(D_t), float(D_r), float(dt)))
+
+    def motor_local(self, T: float, nsteps=None):
+        """Motor kinetics over T with psi frozen and a local substep per cell
+        (mm_motor_local). nsteps (int array [ny][nx], optional) imposes the
+        substeps per cell. Returns the substeps used per cell (host int32)."""
+        g = self.grid
+        out = np.empty((g.ny, g.nx), dtype=np.int32)
+        nin = None
+        if nsteps is not None:
+            nin = np.ascontiguousarray(nsteps, dtype=np.int32)
+            if nin.shape != (g.ny, g.nx):
+                raise ValueError("nsteps must have shape [ny][nx]")
+        self._check(self.lib.mm_motor_local(self.h, float(T),
+                                            nin.ctypes.data if nin is not None else None,
+                                            out.ctypes.data, 0))
+        return out
+
+    def motor_local_device(self, T: float, nsteps_out=None):
+        """mm_motor_local with the counts (optional) written to an int32 CUDA
+        tensor of ncells; stream-ordered, no synchronisation."""
+        p = None
+        if nsteps_out is not None:
+            import torch
+            if nsteps_out.dtype != torch.int32 or not nsteps_out.is_cuda:
+                raise TypeError("nsteps_out must be an int32 CUDA tensor")
+            p = nsteps_out.data_ptr()
+        self._check(self.lib.mm_motor_local(self.h, float(T), None, p, 1))
 
     def sync(self):
         self._check(self.lib.mm_sync(self.h))

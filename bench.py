@@ -108,6 +108,21 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
+# Float32 operations per motor value and substep of the local-step kernel,
+# counted from the scheme: per RK2 stage the backward difference, its half,
+# two sign transfers, two minima, the maximum with zero, the flux fma, the flux
+# difference and two fmas of the stage update (11); two stages, plus one add
+# of the n_b sum.
+LOCAL_OPS = 23
+
+
+def alu_peak_tops(sm_mhz: float = 2070.0, sms: int = 152, lanes: int = 128) -> float:
+    """Float32 operations per second of GB300 in Tops/s: 152 SMs x 128 float32
+    lanes x the maximum SM clock (one fma, add, mul, min or max per lane and
+    clock)."""
+    return sms * lanes * sm_mhz * 1e6 / 1e12
+
+
 def read_profile_traffic(kernel: str, workload: str, precision: str, scale: float = 1.0):
     """DRAM bytes per launch of a kernel from its committed ncu summary, if it
     was taken on the current kernel sources (sha256 match); `scale` converts a
@@ -452,6 +467,44 @@ def run_ours(args):
                 "algorithmic_bytes_psi_solves": 3 * 3 * 2 * psi_bytes,
                 "algorithmic_bytes_reinit": gl.micro_cells * 4 + 3 * psi_bytes}
 
+    def local_run(wname, precision="fp32", reps=5):
+        """Local substeps with psi frozen (mm_motor_local) over the macro
+        interval of the workload (its substeps x the global dt): CUDA events
+        around each call; the cell-updates are sum_i n_i x ntheta x ns with n_i
+        the substeps cell i took. Beside it, the global substeps over the same
+        interval."""
+        wl = WORKLOADS[wname]
+        gl = wl["grid"]
+        sim = mm.Simulation(gl, r, precision, stream=stream.cuda_stream)
+        sim.set_state(psi_isotropic_perturbed(gl, wl["seed"]))
+        sim.set_velocity(torch.tensor(workload_velocity(wname, 0), device=dev))
+        T = wl["substeps"] * sim.dt
+        nst = sim.motor_local(T)
+        updates = int(nst.astype(np.int64).sum()) * gl.ntheta * gl.ns
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.motor_local_device(T)
+            e1.record(stream)
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(wl["substeps"])
+        e1.record(stream)
+        e1.synchronize()
+        sim.sync()
+        sim.close()
+        ms = sum(ts) / len(ts)
+        return {"workload": f"{wname} ({gl.nx}x{gl.ny} x {gl.ntheta} x {gl.ns}, {precision}), "
+                            f"T = {wl['substeps']} global substeps",
+                "substeps_per_cell": [int(nst.min()), int(nst.max())],
+                "value": world * updates / (ms * 1e-3), "unit": UNIT, "ms_per_call": ms,
+                "global_substeps_ms_same_interval": e0.elapsed_time(e1),
+                "cell_updates_per_call": updates}
+
     def ensemble_run(steps):
         """ensemble64: 64 members with uneven grids (N in {32..128}, Ntheta and
         Ns in {16, 32}), k_off log-uniform in [0.05, 5], v_walk in [0.5, 2];
@@ -512,6 +565,15 @@ def run_ours(args):
     ens = ensemble_run(max(2, min(args.steps, 3)))
     large_adj = large_adjoint_run()
     diff = diffusion_run()
+    local = {"precision128": local_run("precision128"),
+             "large512": local_run("large512", reps=3)}
+    for v in local.values():
+        # ALU roofline: LOCAL_OPS float32 operations per motor value and
+        # substep against 128 float32 lanes per SM at the maximum SM clock
+        ops = v["cell_updates_per_call"] * LOCAL_OPS / (v["ms_per_call"] * 1e-3) / 1e12
+        v["roofline"] = {"bound": "alu", "achieved": ops, "peak": alu_peak_tops(),
+                         "unit": "Tops/s", "frac": ops / alu_peak_tops(),
+                         "kernel": "k_motor_local (float32)", "traffic": None}
 
     total_ms, kern_ms, fp64_ms, e2e_s = reduce_max([total_ms, kern_ms, fp64_ms, e2e_s], dev)
 
@@ -556,6 +618,7 @@ def run_ours(args):
             "large512_adjoint": dict(
                 large_adj, workload="large512, 2000 substeps, float32, mean active stress vs k_off"),
             "diffusion": diff,
+            "local": local,
             "ensemble": dict(ens, roofline={"bound": "hbm", "peak": peak, "unit": "GB/s",
                                             "achieved": ens["achieved_gbs"],
                                             "frac": ens["achieved_gbs"] / peak,

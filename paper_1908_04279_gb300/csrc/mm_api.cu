@@ -1,6 +1,8 @@
 // Host side of the C ABI (include/mm.h): handle life cycle, state transfer,
 // velocity and adaptive substep, the substep launch plan (captured CUDA
 // graphs), the moments, and the adjoint recording and reverse sweep.
+#include <array>
+
 #include "mm_host.h"
 
 using namespace mmh;
@@ -23,8 +25,13 @@ mm_status check_rates(const mm_rates* r, mm_handle* h) {
 }
 
 void free_recording(mm_handle* h) {
-  if (h->rec.slab) cudaFree(h->rec.slab);
-  for (void* p : h->rec.vblocks) cudaFree(p);
+  Recording& R = h->rec;
+  if (R.slab) cudaFree(R.slab);
+  for (void* p : R.vblocks) cudaFree(p);
+  if (R.rstream) cudaStreamDestroy(R.rstream);
+  cudaEvent_t evs[5] = {R.ev_start, R.ev_rep[0], R.ev_rep[1], R.ev_rev[0], R.ev_rev[1]};
+  for (cudaEvent_t ev : evs)
+    if (ev) cudaEventDestroy(ev);
   h->rec = Recording();
 }
 
@@ -1045,6 +1052,16 @@ void rec_layout(mm_handle* h, Carver& c) {
     R.sl_mf[i] = c.take(nc * t);
     R.sl_cpre[i] = c.take(nc * t);
   }
+  // the second slot set of the overlapped one-level sweep
+  std::vector<void*>* s2[5] = {&R.sl2_mb, &R.sl2_psi, &R.sl2_nb, &R.sl2_mf, &R.sl2_cpre};
+  for (auto* v : s2) v->assign(R.overlap ? NS + 1 : 0, nullptr);
+  for (int i = 1; R.overlap && i <= NS; ++i) {
+    R.sl2_mb[i] = c.take(h->mbn * t);
+    R.sl2_psi[i] = c.take(rows * t);
+    R.sl2_nb[i] = c.take(rows * t);
+    R.sl2_mf[i] = c.take(nc * t);
+    R.sl2_cpre[i] = c.take(nc * t);
+  }
   R.sl_c = c.take(nc * t);
   R.lmb = c.take(h->mbn * t);
   for (int i = 0; i < 2; ++i) {
@@ -1129,10 +1146,24 @@ mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_
     CK(oe);
     if (bps < 1) return fail(h, MM_ERR_UNSUPPORTED, "reverse kernel cannot be resident");
     R.grid_motor = (int)std::min<long long>((h->ncells * U + 3) / 4, (long long)bps * h->sms);
-    Carver sz;
-    rec_layout(h, sz);
     size_t freeb = 0, totalb = 0;
     CK(cudaMemGetInfo(&freeb, &totalb));
+    // one level with more than one segment: a second slot set lets the replay
+    // of a segment overlap the reverse of the next one, where it takes at most
+    // a quarter of the free memory
+    R.overlap = K_inner == K && max_substeps > K;
+    Carver sz;
+    rec_layout(h, sz);
+    if (R.overlap && sz.off > freeb / 4) {
+      R.overlap = false;
+      sz = Carver();
+      rec_layout(h, sz);
+    }
+    if (R.overlap && !R.rstream) {
+      CK(cudaStreamCreateWithFlags(&R.rstream, cudaStreamNonBlocking));
+      cudaEvent_t* evs[5] = {&R.ev_start, &R.ev_rep[0], &R.ev_rep[1], &R.ev_rev[0], &R.ev_rev[1]};
+      for (cudaEvent_t* ev : evs) CK(cudaEventCreateWithFlags(ev, cudaEventDisableTiming));
+    }
     const size_t need = sz.off + 2 * vblock_bytes(h) + (1 << 20);
     if (need > freeb) {
       free_recording(h);
@@ -1248,7 +1279,99 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
     return MM_OK;
   };
   const int nseg = (n + R.K - 1) / R.K;
-  for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+  auto reverse_range = [&](int a0, int a1) -> mm_status {
+    for (int tt = a1 - 1; tt >= a0; --tt) {
+      const int i = tt - a0, ver = R.sub_vel[tt];
+      if (f64)
+        e = mm::launch_adjoint<double>(adj_args<double>(h, i, ver, cur), adj_V(h), R.grid_psi,
+                                       R.grid_motor, h->stream);
+      else
+        e = mm::launch_adjoint<float>(adj_args<float>(h, i, ver, cur), adj_V(h), R.grid_psi,
+                                      R.grid_motor, h->stream);
+      CK(e);
+      cur ^= 1;
+    }
+    return MM_OK;
+  };
+  if (R.overlap && R.K2 == R.K && nseg > 1) {
+    // One level, two slot sets: segment s uses set (nseg - 1 - s) & 1 (the
+    // last segment set 0, which the recording may have filled already). The
+    // replay of segment s - 1 runs on the replay stream while segment s is
+    // reversed on the handle's stream; a set is replayed into only after the
+    // reverse that read it has finished (ev_rev), and reversed only after its
+    // replay (ev_rep). Only the replay touches the device dt and the psi
+    // correction factor; the reverse kernels read the recorded dt.
+    cudaStream_t rs = R.rstream;
+    CK(cudaEventRecord(R.ev_start, h->stream));
+    CK(cudaStreamWaitEvent(rs, R.ev_start, 0));
+    int live_set = 0;  // the set R.sl_* holds now (the other is in R.sl2_*)
+    auto vecs = [&](int set) {
+      const bool here = set == live_set;
+      return std::array<std::vector<void*>*, 5>{here ? &R.sl_mb : &R.sl2_mb,
+                                                here ? &R.sl_psi : &R.sl2_psi,
+                                                here ? &R.sl_nb : &R.sl2_nb,
+                                                here ? &R.sl_mf : &R.sl2_mf,
+                                                here ? &R.sl_cpre : &R.sl2_cpre};
+    };
+    auto set_of = [&](int sg) { return (nseg - 1 - sg) & 1; };
+    int rs_dt = -1;
+    auto replay = [&](int sg) -> mm_status {
+      const int set = set_of(sg), s0 = sg * R.K, s1 = std::min(s0 + R.K, n);
+      auto v = vecs(set);
+      std::vector<void*>&vmb = *v[0], &vpsi = *v[1], &vnb = *v[2], &vmf = *v[3], &vcp = *v[4];
+      vmb[0] = R.ck_mb[sg];
+      vpsi[0] = R.ck_psi[sg];
+      vnb[0] = R.ck_nb[sg];
+      vmf[0] = R.ck_mf[sg];
+      CK(cudaMemcpyAsync(&h->prm->psi_scale, R.ck_scale + sg, 8, cudaMemcpyDeviceToDevice, rs));
+      for (int tt = s0; tt < s1; ++tt) {
+        const int i = tt - s0, ver = R.sub_vel[tt];
+        if (ver != rs_dt)
+          CK(cudaMemcpyAsync(&h->prm->dt, R.v_dt[ver], 8, cudaMemcpyDeviceToDevice, rs));
+        rs_dt = ver;
+        StepPtrs p{vpsi[i], vnb[i], vmb[i], vmf[i], R.v_ucell[ver], vpsi[i + 1], vnb[i + 1],
+                   vmb[i + 1], vmf[i + 1], R.sl_c, vcp[i + 1]};
+        CK(launch_ptrs(h, p, rs));
+      }
+      CK(cudaEventRecord(R.ev_rep[set], rs));
+      return MM_OK;
+    };
+    const int tail = rec_tail_start(R);
+    const bool last_in_slots = (nseg - 1) * R.K == tail && R.tail_done == n - tail;
+    if (!last_in_slots && (st = replay(nseg - 1)) != MM_OK) return st;
+    for (int sgi = nseg - 1; sgi >= 0; --sgi) {
+      if (sgi >= 1) {
+        // the set of segment sgi - 1 was last read by the reverse of sgi + 1
+        if (sgi + 1 <= nseg - 1) CK(cudaStreamWaitEvent(rs, R.ev_rev[set_of(sgi - 1)], 0));
+        if ((st = replay(sgi - 1)) != MM_OK) return st;
+      }
+      const int set = set_of(sgi);
+      if (sgi < nseg - 1 || !last_in_slots) CK(cudaStreamWaitEvent(h->stream, R.ev_rep[set], 0));
+      if (set != live_set) {
+        std::swap(R.sl_mb, R.sl2_mb);
+        std::swap(R.sl_psi, R.sl2_psi);
+        std::swap(R.sl_nb, R.sl2_nb);
+        std::swap(R.sl_mf, R.sl2_mf);
+        std::swap(R.sl_cpre, R.sl2_cpre);
+        live_set = set;
+      }
+      R.sl_mb[0] = R.ck_mb[sgi];
+      R.sl_psi[0] = R.ck_psi[sgi];
+      R.sl_nb[0] = R.ck_nb[sgi];
+      R.sl_mf[0] = R.ck_mf[sgi];
+      const int s0 = sgi * R.K;
+      if ((st = reverse_range(s0, std::min(s0 + R.K, n))) != MM_OK) return st;
+      CK(cudaEventRecord(R.ev_rev[set], h->stream));
+    }
+    if (live_set != 0) {  // set 0 is the one the next recording writes into
+      std::swap(R.sl_mb, R.sl2_mb);
+      std::swap(R.sl_psi, R.sl2_psi);
+      std::swap(R.sl_nb, R.sl2_nb);
+      std::swap(R.sl_mf, R.sl2_mf);
+      std::swap(R.sl_cpre, R.sl2_cpre);
+    }
+  }
+  for (int sgi = (R.overlap && R.K2 == R.K && nseg > 1) ? -1 : nseg - 1; sgi >= 0; --sgi) {
     const int s0 = sgi * R.K, s1 = std::min(s0 + R.K, n);
     const int nin = (s1 - s0 + R.K2 - 1) / R.K2;
     if (nin > 1) {
@@ -1299,17 +1422,7 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
                    R.sl_cpre[i + 1]};
         CK(launch_ptrs(h, p, h->stream));
       }
-      for (int tt = a1 - 1; tt >= a0; --tt) {
-        const int i = tt - a0, ver = R.sub_vel[tt];
-        if (f64)
-          e = mm::launch_adjoint<double>(adj_args<double>(h, i, ver, cur), adj_V(h), R.grid_psi,
-                                         R.grid_motor, h->stream);
-        else
-          e = mm::launch_adjoint<float>(adj_args<float>(h, i, ver, cur), adj_V(h), R.grid_psi,
-                                        R.grid_motor, h->stream);
-        CK(e);
-        cur ^= 1;
-      }
+      if ((st = reverse_range(a0, a1)) != MM_OK) return st;
     }
   }
   // restore the live scalars
@@ -1334,11 +1447,11 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
     double* dst = out->on_device ? out->dL_dpsi0 : R.work;
     if (f64)
       e = mm::launch_adj_psi0<double>((const double*)R.lpsi[cur], (const double*)R.lmf[cur], R.units,
-                                      (const double*)R.sl_nb[0], dth, (long long)rows,
+                                      (const double*)R.ck_nb[0], dth, (long long)rows,
                                       h->g.ntheta, dst, h->stream);
     else
       e = mm::launch_adj_psi0<float>((const float*)R.lpsi[cur], (const float*)R.lmf[cur], R.units,
-                                     (const float*)R.sl_nb[0], dth, (long long)rows, h->g.ntheta,
+                                     (const float*)R.ck_nb[0], dth, (long long)rows, h->g.ntheta,
                                      dst, h->stream);
     CK(e);
     if (!out->on_device)

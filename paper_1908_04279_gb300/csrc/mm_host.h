@@ -80,6 +80,13 @@ struct Recording {
   int units = 1, rows_per_unit = 1;  // row blocks per cell of the motor reverse kernel
   int grid_psi = 1, grid_motor = 1;  // blocks of 4 warps of the two reverse kernels
   int ring_rc = 0, ring_ch = 0, ring_s = 0;  // bulk-copy ring of the motor kernel (0: off)
+  // One level: a second set of K slots, so that the replay of the next segment
+  // (on rstream) runs while the current segment is reversed (on the handle's
+  // stream); ev_rep / ev_rev order the two per slot set.
+  bool overlap = false;
+  std::vector<void*> sl2_mb, sl2_psi, sl2_nb, sl2_mf, sl2_cpre;
+  cudaStream_t rstream = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_rep[2] = {nullptr, nullptr}, ev_rev[2] = {nullptr, nullptr};
 };
 
 namespace mmh {

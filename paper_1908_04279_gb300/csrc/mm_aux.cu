@@ -2,17 +2,12 @@
 // Alg. 2 scale-down), the maxima of the adaptive-substep rule, and the
 // macroscale moments (Alg. 1 after the inner loop; Eq. 10's force and force
 // dipole with anchors in the filament's own cell).
-#include "mm_internal.cuh"
+#include "mm_walk.cuh"
 
 namespace mm {
 
 namespace {
 
-__device__ __forceinline__ double warp_sum(double x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-  return x;
-}
 __device__ __forceinline__ double warp_max(double x) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
@@ -227,14 +222,14 @@ struct alignas(sizeof(T) * V) VPack {
   T v[V];
 };
 
-// Moments, one warp per cell, no block barriers. The s-rows of the cell are
+// Moments, one warp per cell, no block barriers before the final sums. The s-rows of the cell are
 // read with the substep kernel's lane mapping (a row over `seg` lanes, V
 // consecutive nodes per lane, vector loads) and reduced to n_b and m1: in
 // float64 in the float64 form, compensated float32 (float-float) converted to
 // float64 per row in the float32 form -- these are the s-reductions feeding
 // the force and the force dipole. Then lanes over theta form the 12 fields.
-// Each warp keeps partial global sums; the last warp to finish adds the
-// per-warp partials in a fixed order.
+// Each warp keeps partial global sums, added per block at the end; the last
+// block to finish adds the block partials in a fixed order.
 template <typename T, int V>
 __global__ void k_moments(const T* psi, const T* mb, const T* mf, const T* c,
                           const double* trig, long long ncells, int nth, int ns, int seg,
@@ -340,22 +335,35 @@ __global__ void k_moments(const T* psi, const T* mb, const T* mf, const T* c,
   }
 #pragma unroll
   for (int q = 0; q < 7; ++q) gs[q] = warp_sum(gs[q]);
-  unsigned int is_last = 0;
-  if (lane == 0) {
-    for (int q = 0; q < 7; ++q) partial[gw * 8 + q] = gs[q];
+  // per block in warp order, then the last block adds the block partials in a
+  // fixed order (warp q of that block sums quantities q, q + nw, ...)
+  __shared__ double s_g[32 * 8];
+  __shared__ unsigned int s_last;
+  const int nw = (int)(blockDim.x >> 5);
+  if (lane == 0)
+    for (int q = 0; q < 7; ++q) s_g[wib * 8 + q] = gs[q];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < 7; ++q) {
+      double b = s_g[q];
+      for (int w2 = 1; w2 < nw; ++w2) b += s_g[w2 * 8 + q];
+      partial[(size_t)blockIdx.x * 8 + q] = b;
+    }
     __threadfence();
-    const unsigned int prev = atomicInc(&prm->counter2, (unsigned int)W - 1);
-    is_last = prev == (unsigned int)W - 1;
+    const unsigned int prev = atomicInc(&prm->counter2, gridDim.x - 1);
+    s_last = prev == gridDim.x - 1;
   }
-  is_last = __shfl_sync(0xffffffffu, is_last, 0);
-  if (is_last) {
+  __syncthreads();
+  if (s_last) {
     __threadfence();
-    double t[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (long long b = lane; b < W; b += 32)
-      for (int q = 0; q < 7; ++q) t[q] += __ldcg(partial + b * 8 + q);
-#pragma unroll
-    for (int q = 0; q < 7; ++q) t[q] = warp_sum(t[q]);
-    if (lane == 0) {
+    for (int q = wib; q < 7; q += nw) {
+      const double tq = warp_sum_ldcg(partial + q, (int)gridDim.x, 8, lane);
+      if (lane == 0) s_g[q] = tq;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t[7];
+      for (int q = 0; q < 7; ++q) t[q] = s_g[q];
       prm->scalars[0] = t[0];
       prm->scalars[1] = t[1];
       prm->scalars[2] = t[2];

@@ -125,9 +125,7 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
     is_last = __shfl_sync(0xffffffffu, is_last, 0);
     if (is_last) {
       __threadfence();
-      double acc = 0.0;
-      for (int b = lane; b < ct.inst_tiles; b += 32) acc += __ldcg(tile_mass + ct.tile0 + b);
-      acc = warp_sum(acc);
+      const double acc = warp_sum_ldcg(tile_mass + ct.tile0, ct.inst_tiles, 1, lane);
       if (lane == 0) {
         A->prm->mass = acc;
         if (MASSCORR && A->mass_correct) A->prm->psi_scale = A->prm->mass0 / acc;

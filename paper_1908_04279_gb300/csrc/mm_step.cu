@@ -2,7 +2,7 @@
 //
 // Every warp owns whole spatial cells (cells gw, gw + W, gw + 2W, ... for
 // global warp gw of W) and performs the whole substep for each of them, with
-// no block-level barrier:
+// no block-level barrier before the final sum:
 //   1. every s-row Mb(cell, k, :) by Eq. 4 with midpoint RK2 (Alg. 2 half and
 //      full stage). The cell's rows stream through a ring of shared-memory
 //      stages filled by bulk asynchronous copies (cp.async.bulk, the Tensor
@@ -20,9 +20,10 @@
 //      reduction, the scale-down of Alg. 2 (rare: the warp rescales the rows
 //      it has just written) and Mf = M - C (Eq. 6).
 // psi and n_b are double-buffered (neighbour cells read the old values); Mb,
-// Mf and C are cell-local. Each warp also sums psi^{n+1} in float64; the last
-// warp to finish adds the per-warp sums in a fixed order and, in the float32
-// form, stores the mass-correction factor applied to psi on the next load.
+// Mf and C are cell-local. Each warp also sums psi^{n+1} in float64, the
+// warps of a block add their sums at the end; the last block to finish adds
+// the block sums in a fixed order and, in the float32 form, stores the
+// mass-correction factor applied to psi on the next load.
 //
 // Every mbarrier wait is bounded (DevParams::wait_limit polls). A warp whose
 // wait runs out records MM_ERR_TIMEOUT in DevParams::status, waits (bounded)
@@ -219,22 +220,25 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
     __syncwarp();
   }
 
-  // sum psi^{n+1}: per-warp partial in float64, the last warp finalises in a
-  // fixed order
+  // sum psi^{n+1}: per-warp partial in float64, added per block in warp
+  // order; the last block adds the block partials in a fixed order
+  __shared__ double s_red[32];
+  __shared__ unsigned int s_last;
   mass_acc = warp_sum((double)mass_hi + (double)mass_lo);
-  unsigned int is_last = 0;
-  if (lane == 0) {
-    a.partial[gw] = mass_acc;
+  if (lane == 0) s_red[wib] = mass_acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = s_red[0];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) b += s_red[q];
+    a.partial[blockIdx.x] = b;
     __threadfence();
-    const unsigned int prev = atomicInc(&a.prm->counter, (unsigned int)W - 1);
-    is_last = prev == (unsigned int)W - 1;
+    const unsigned int prev = atomicInc(&a.prm->counter, gridDim.x - 1);
+    s_last = prev == gridDim.x - 1;
   }
-  is_last = __shfl_sync(0xffffffffu, is_last, 0);
-  if (is_last) {
+  __syncthreads();
+  if (s_last && wib == 0) {
     __threadfence();
-    double m = 0.0;
-    for (int b = lane; b < W; b += 32) m += __ldcg(a.partial + b);
-    m = warp_sum(m);
+    const double m = warp_sum_ldcg(a.partial, (int)gridDim.x, 1, lane);
     if (lane == 0) {
       a.prm->mass = m;
       if (MASSCORR && a.mass_correct) a.prm->psi_scale = a.prm->mass0 / m;

@@ -126,4 +126,28 @@ __device__ __forceinline__ double warp_sum(double x) {
   return x;
 }
 
+// Fixed-order float64 sum, by one warp, of p[0], p[stride], ...,
+// p[(n - 1) stride], values other blocks wrote (read through L2). Lane l adds
+// the values l, l + 32, ... into eight interleaved partial sums, so that eight
+// loads are in flight per lane instead of one dependent load per value; the
+// partials and the lanes then combine in a fixed tree. The result does not
+// depend on the order in which blocks ran.
+__device__ __forceinline__ double warp_sum_ldcg(const double* p, int n, int stride, int lane) {
+  double s[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s[q] = 0.0;
+  int b = lane;
+  for (; b + 7 * 32 < n; b += 8 * 32) {
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __ldcg(p + (size_t)(b + q * 32) * stride);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[q] += v[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+    if (b + q * 32 < n) s[q] += __ldcg(p + (size_t)(b + q * 32) * stride);
+  return warp_sum(((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
+}
+
 }  // namespace mm

@@ -1,6 +1,6 @@
 """Run one synthetic case of the library's kernels, for profilers.
 
-    python -m paper_1908_04279_gb300.profile_case [--case single|batch|adjoint|moments]
+    python -m paper_1908_04279_gb300.profile_case [--case single|batch|adjoint|moments|local]
         [--grid NX NY NTHETA NS] [--precision fp32|fp64] [--substeps N]
         [--repeat R] [--K K] [--members M] [--autotune]
 
@@ -12,6 +12,8 @@ batch:   the first M members of the detachment-rate ensemble (64 by default)
 adjoint: a recording of N substeps (checkpoint every K) on the single case,
          then the reverse sweep for the polar order; R times.
 moments: N substeps of the single case, then R calls of mm_moments.
+local:   the single case's state, then R calls of mm_motor_local over the
+         interval of N substeps of the adaptive dt (psi frozen, local steps).
 Prints the times measured with CUDA events on the handle's stream.
 """
 from __future__ import annotations
@@ -29,7 +31,8 @@ def main():
                          random_divfree_flow)
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="single", choices=["single", "batch", "adjoint", "moments"])
+    ap.add_argument("--case", default="single", choices=["single", "batch", "adjoint", "moments",
+                                                          "local"])
     ap.add_argument("--grid", type=int, nargs=4, default=[256, 256, 64, 64])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--substeps", type=int, default=10)
@@ -80,6 +83,17 @@ def main():
             times = [timed(lambda: sim.moments(fields=fields)) for _ in range(args.repeat)]
             print(json.dumps({"case": "moments", "grid": args.grid, "precision": args.precision,
                               "ms_per_call": times}))
+            return
+        if args.case == "local":
+            T = args.substeps * sim.dt
+            nst = sim.motor_local(T)
+            times = [timed(lambda: sim.motor_local_device(T)) for _ in range(args.repeat)]
+            sim.sync()
+            upd = int(nst.sum()) * g.ntheta * g.ns
+            print(json.dumps({"case": "local", "grid": args.grid, "precision": args.precision,
+                              "T": T, "substeps_per_cell": [int(nst.min()), int(nst.max())],
+                              "ms_per_call": times,
+                              "cell_updates_per_s": upd / (min(times) * 1e-3)}))
             return
         if args.case == "single":
             times = [timed(lambda: sim.step(args.substeps)) / args.substeps

@@ -37,6 +37,14 @@ __device__ __forceinline__ double max3_t(double a, double b, double c) {
   return fmax(fmax(a, b), c);
 }
 
+// min(|a|, |b|) carrying the sign sign(a) xor sign(b): positive where a and b
+// agree in sign, negative where they disagree (one instruction).
+__device__ __forceinline__ float min_xorsign_abs(float a, float b) {
+  float r;
+  asm("min.xorsign.abs.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
+
 // Walking-flux differences of the V nodes a lane holds (the d_s term of
 // Eq. 4 divided by v/ds): D_v = F_{j-1} - F_j with F_j = M_j + sigma_j/2 the
 // flux / v through the right face of node j = lane*V + v, F_{-1} = 0 (nothing
@@ -68,6 +76,24 @@ __device__ __forceinline__ void walk_dflux(const T (&M)[V], T (&D)[V], bool firs
 #pragma unroll
   for (int i = 0; i <= V; ++i) hd[i] = T(0.5) * d[i];
   T F[V];
+  if constexpr (sizeof(T) == 4 && !COEF) {
+    // float32 forward: sigma/2 = sign(b) max(min(|a|, |b|/2), min(|a|/2, |b|))
+    // where a and b agree in sign, else 0 -- the two minima with the agreement
+    // in their sign, so that the maximum with 0 drops the disagreeing case
+    // (the same value, bit for bit, as the general form below)
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      T r = max3_t(min_xorsign_abs(d[v], hd[v + 1]), min_xorsign_abs(hd[v], d[v + 1]), T(0));
+      if (v == V - 1 && last) r = T(0);  // plus end: F = M, no slope
+      F[v] = M[v] + copysignf(r, d[v + 1]);
+    }
+    T fl = __shfl_up_sync(0xffffffffu, F[V - 1], 1, seg);
+    if (first) fl = T(0);
+    D[0] = fl - F[0];
+#pragma unroll
+    for (int v = 1; v < V; ++v) D[v] = F[v - 1] - F[v];
+    return;
+  }
 #pragma unroll
   for (int v = 0; v < V; ++v) {
     T sgn = copysign(T(1), d[v + 1]);

@@ -124,6 +124,59 @@ struct RkConst {
   T c1, c2, c3, e1, e2, e3;
 };
 
+// Float32 rows with V = 4 or 8 nodes per lane as register pairs: the stage
+// updates and the n_b sum as packed two-value instructions (walk_dflux_x2).
+template <int V>
+__device__ __forceinline__ void rows_chunk_x2(const float* src_rows, float* dst, int RC, int ns,
+                                              int seg, const LaneGeom& lg,
+                                              const RkConst<float>& k, float ds,
+                                              float* s_nb_chunk) {
+  constexpr int H = V / 2;
+  const int passes = (RC + lg.rpp - 1) / lg.rpp;
+  const float2 c1 = make_float2(k.c1, k.c1), c2 = make_float2(k.c2, k.c2);
+  const float2 c3 = make_float2(k.c3, k.c3), e1 = make_float2(k.e1, k.e1);
+  const float2 e2 = make_float2(k.e2, k.e2), e3 = make_float2(k.e3, k.e3);
+#pragma unroll kStepUnroll
+  for (int p = 0; p < passes; ++p) {
+    const int r = p * lg.rpp + lg.rslot;  // row within the chunk
+    const bool row_ok = r < RC;
+    const bool act = row_ok && lg.lane_ok;
+    const int off = (row_ok ? r : 0) * ns + lg.sl * V;
+    float2 M[H], D[H], Ms[H];
+    if (act) {
+      const float4* q = reinterpret_cast<const float4*>(src_rows + off);
+#pragma unroll
+      for (int h = 0; h < H / 2; ++h) {
+        const float4 v4 = q[h];
+        M[2 * h] = make_float2(v4.x, v4.y);
+        M[2 * h + 1] = make_float2(v4.z, v4.w);
+      }
+    } else {
+#pragma unroll
+      for (int h = 0; h < H; ++h) M[h] = make_float2(0.0f, 0.0f);
+    }
+    walk_dflux_x2<V>(M, D, lg.first, lg.last, seg);
+#pragma unroll
+    for (int h = 0; h < H; ++h) Ms[h] = __ffma2_rn(c1, D[h], __ffma2_rn(c2, M[h], c3));
+    walk_dflux_x2<V>(Ms, D, lg.first, lg.last, seg);
+#pragma unroll
+    for (int h = 0; h < H; ++h)
+      M[h] = __ffma2_rn(e1, D[h], __ffma2_rn(e2, Ms[h], __fadd2_rn(M[h], e3)));
+    float2 acc = M[0];
+#pragma unroll
+    for (int h = 1; h < H; ++h) acc = __fadd2_rn(acc, M[h]);
+    float snb = act ? acc.x + acc.y : 0.0f;
+    if (act) {
+      float4* q = reinterpret_cast<float4*>(dst + off);
+#pragma unroll
+      for (int h = 0; h < H / 2; ++h)
+        q[h] = make_float4(M[2 * h].x, M[2 * h].y, M[2 * h + 1].x, M[2 * h + 1].y);
+    }
+    snb = seg_sum(snb, seg);
+    if (lg.first && row_ok) s_nb_chunk[r] = snb * ds;
+  }
+}
+
 // One chunk of RC s-rows (src_rows: the rows at step n, in shared or global
 // memory; dst: global rows at step n+1, in place allowed), with n_b of each
 // new row written to s_nb_chunk[r].
@@ -131,6 +184,10 @@ template <typename T, int V>
 __device__ __forceinline__ void rows_chunk(const T* src_rows, T* dst, int RC, int ns, int seg,
                                            const LaneGeom& lg, const RkConst<T>& k, T ds,
                                            T* s_nb_chunk) {
+  if constexpr (sizeof(T) == 4 && (V == 4 || V == 8)) {
+    rows_chunk_x2<V>(src_rows, dst, RC, ns, seg, lg, k, ds, s_nb_chunk);
+    return;
+  }
   const int passes = (RC + lg.rpp - 1) / lg.rpp;
 #pragma unroll kStepUnroll
   for (int p = 0; p < passes; ++p) {

@@ -135,6 +135,45 @@ __device__ __forceinline__ void walk_dflux(const T (&M)[V], T (&D)[V], bool firs
   for (int v = 1; v < V; ++v) D[v] = F[v - 1] - F[v];
 }
 
+// The float32 walk of walk_dflux for V = 4 or 8 nodes per lane, with the
+// lane's values held as V/2 register pairs (nodes 2k, 2k + 1), so that the
+// element-wise steps (the halved differences, the fluxes) run as packed
+// two-value float32 instructions; the differences, the limiter's minima and
+// maxima and the flux differences stay scalar. Same value, bit for bit, as
+// walk_dflux<float, V>.
+template <int V>
+__device__ __forceinline__ void walk_dflux_x2(const float2 (&M)[V / 2], float2 (&D)[V / 2],
+                                              bool first, bool last, int seg) {
+  constexpr int H = V / 2;
+  float ml = __shfl_up_sync(0xffffffffu, M[H - 1].y, 1, seg);
+  const float mr = __shfl_down_sync(0xffffffffu, M[0].x, 1, seg);
+  if (first) ml = 0.0f;
+  // d_v = M_v - M_{v-1} as pairs (d_2k, d_2k+1), and d_V
+  float2 d[H], hd[H];
+  d[0] = make_float2(M[0].x - ml, M[0].y - M[0].x);
+#pragma unroll
+  for (int k = 1; k < H; ++k) d[k] = make_float2(M[k].x - M[k - 1].y, M[k].y - M[k].x);
+  const float dV = mr - M[H - 1].y, hdV = 0.5f * dV;
+  const float2 half2 = make_float2(0.5f, 0.5f);
+#pragma unroll
+  for (int k = 0; k < H; ++k) hd[k] = __fmul2_rn(half2, d[k]);
+  float2 F[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const float b1 = k + 1 < H ? d[k + 1].x : dV, hb1 = k + 1 < H ? hd[k + 1].x : hdV;
+    const float r0 =
+        max3_t(min_xorsign_abs(d[k].x, hd[k].y), min_xorsign_abs(hd[k].x, d[k].y), 0.0f);
+    float r1 = max3_t(min_xorsign_abs(d[k].y, hb1), min_xorsign_abs(hd[k].y, b1), 0.0f);
+    if (k == H - 1 && last) r1 = 0.0f;  // plus end: F = M, no slope
+    F[k] = __fadd2_rn(M[k], make_float2(copysignf(r0, d[k].y), copysignf(r1, b1)));
+  }
+  float fl = __shfl_up_sync(0xffffffffu, F[H - 1].y, 1, seg);
+  if (first) fl = 0.0f;
+  D[0] = make_float2(fl - F[0].x, F[0].x - F[0].y);
+#pragma unroll
+  for (int k = 1; k < H; ++k) D[k] = make_float2(F[k - 1].y - F[k].x, F[k].x - F[k].y);
+}
+
 template <typename T>
 __device__ __forceinline__ T seg_sum(T x, int seg) {
   for (int o = seg >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o, seg);

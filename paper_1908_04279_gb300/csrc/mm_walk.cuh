@@ -87,45 +87,40 @@ __device__ __forceinline__ void walk_dflux(const T (&M)[V], T (&D)[V], bool firs
       if (v == V - 1 && last) r = T(0);  // plus end: F = M, no slope
       F[v] = M[v] + copysignf(r, d[v + 1]);
     }
-    T fl = __shfl_up_sync(0xffffffffu, F[V - 1], 1, seg);
-    if (first) fl = T(0);
-    D[0] = fl - F[0];
+  } else {
 #pragma unroll
-    for (int v = 1; v < V; ++v) D[v] = F[v - 1] - F[v];
-    return;
-  }
-#pragma unroll
-  for (int v = 0; v < V; ++v) {
-    T sgn = copysign(T(1), d[v + 1]);
-    if (v == V - 1 && last) sgn = T(0);  // plus end: F = M, no slope
-    const T A = d[v] * sgn, hA = hd[v] * sgn;
-    const T hB = fabs(hd[v + 1]), B = fabs(d[v + 1]);
-    const T t1 = tmin(A, hB), t2 = tmin(hA, B);
-    const T r = max3_t(t1, t2, T(0));
-    F[v] = fma_t(r, sgn, M[v]);
-    if constexpr (COEF) {
-      bool pos, p1, x1a, x2a;
-      if constexpr (sizeof(T) == 8) {
-        // the same four decisions on the bit patterns (integer pipe instead of
-        // the float64 one): hB, B, r >= 0 order as their signed 64-bit
-        // patterns, a negative A or hA (sign bit set) orders below them, and
-        // the cases where -0 and +0 would differ all have r = 0 (pos false)
-        const long long iA = __double_as_longlong(A), ihA = __double_as_longlong(hA);
-        const long long ihB = __double_as_longlong(hB), iB = __double_as_longlong(B);
-        pos = __double_as_longlong(r) > 0;
-        p1 = __double_as_longlong(t1) > __double_as_longlong(t2);
-        x1a = iA < ihB;
-        x2a = ihA < iB;
-      } else {
-        pos = r > T(0);
-        p1 = t1 > t2;
-        x1a = A < hB;
-        x2a = hA < B;
+    for (int v = 0; v < V; ++v) {
+      T sgn = copysign(T(1), d[v + 1]);
+      if (v == V - 1 && last) sgn = T(0);  // plus end: F = M, no slope
+      const T A = d[v] * sgn, hA = hd[v] * sgn;
+      const T hB = fabs(hd[v + 1]), B = fabs(d[v + 1]);
+      const T t1 = tmin(A, hB), t2 = tmin(hA, B);
+      const T r = max3_t(t1, t2, T(0));
+      F[v] = fma_t(r, sgn, M[v]);
+      if constexpr (COEF) {
+        bool pos, p1, x1a, x2a;
+        if constexpr (sizeof(T) == 8) {
+          // the same four decisions on the bit patterns (integer pipe instead of
+          // the float64 one): hB, B, r >= 0 order as their signed 64-bit
+          // patterns, a negative A or hA (sign bit set) orders below them, and
+          // the cases where -0 and +0 would differ all have r = 0 (pos false)
+          const long long iA = __double_as_longlong(A), ihA = __double_as_longlong(hA);
+          const long long ihB = __double_as_longlong(hB), iB = __double_as_longlong(B);
+          pos = __double_as_longlong(r) > 0;
+          p1 = __double_as_longlong(t1) > __double_as_longlong(t2);
+          x1a = iA < ihB;
+          x2a = ihA < iB;
+        } else {
+          pos = r > T(0);
+          p1 = t1 > t2;
+          x1a = A < hB;
+          x2a = hA < B;
+        }
+        const T a1 = x1a ? T(1) : T(0), b1 = x1a ? T(0) : T(0.5);
+        const T a2 = x2a ? T(0.5) : T(0), b2 = x2a ? T(0) : T(1);
+        ga[v] = pos ? (p1 ? a1 : a2) : T(0);
+        gb[v] = pos ? (p1 ? b1 : b2) : T(0);
       }
-      const T a1 = x1a ? T(1) : T(0), b1 = x1a ? T(0) : T(0.5);
-      const T a2 = x2a ? T(0.5) : T(0), b2 = x2a ? T(0) : T(1);
-      ga[v] = pos ? (p1 ? a1 : a2) : T(0);
-      gb[v] = pos ? (p1 ? b1 : b2) : T(0);
     }
   }
   T fl = __shfl_up_sync(0xffffffffu, F[V - 1], 1, seg);

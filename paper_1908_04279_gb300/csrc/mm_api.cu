@@ -87,6 +87,11 @@ StepArgs<T> step_args(mm_handle* h, int parity) {
   a.inv_dth = 1.0 / a.dth;
   a.ds = h->g.L / h->g.ns;
   a.L = h->g.L;
+  a.f_inv_dx = (float)a.inv_dx;
+  a.f_inv_dy = (float)a.inv_dy;
+  a.f_inv_dth = (float)a.inv_dth;
+  a.f_dth = (float)a.dth;
+  a.f_ds = (float)a.ds;
   a.mb_in = (const T*)h->mb;
   a.mb_out = (T*)h->mb;
   a.psi_in = (const T*)h->psi[parity];

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
 
   // sum of the finished tile; the last tile of an instance finalises it
   auto close_tile = [&]() {
-    const double m = warp_sum((double)mass_hi + (double)mass_lo);
+    const double m = warp_sum_ff(mass_hi, mass_lo);
     mass_hi = T(0);
     mass_lo = T(0);
     unsigned int is_last = 0;
@@ -150,19 +150,16 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
         CH = ct.ch;
         nb_tma = A->nb_tma != 0;
         const DevParams* P = A->prm;
-        const double dt64 = P->dt;
-        dt = (T)dt64;
-        hdt = (T)(0.5 * dt64);
-        const T cw = (T)P->cw;
-        const T koff = (T)P->k_off;
-        kon = (T)P->k_on;
-        const T g = MASSCORR ? (T)P->psi_scale : T(1);
+        const StepScalars<T> sc = step_scalars<T, MASSCORR>(P, *A, lane);
+        dt = sc.dt;
+        hdt = sc.hdt;
+        kon = sc.kon;
         wait_limit = P->wait_limit;
         wait_never = (P->debug_flags & 1u) != 0;
-        pq = PsiConst<T>{dt, g, (T)P->glide, (T)P->v_sp, (T)A->inv_dx, (T)A->inv_dy,
-                         (T)A->inv_dth, (T)A->dth, A->trig};
-        ds = (T)A->ds;
-        rk = RkConst<T>{hdt * cw, T(1) - hdt * koff, T(0), dt * cw, -dt * koff, T(0)};
+        pq = PsiConst<T>{dt, sc.g, sc.glide, sc.vsp, sc.inv_dx, sc.inv_dy, sc.inv_dth, sc.dth,
+                         A->trig};
+        ds = sc.ds;
+        rk = RkConst<T>{hdt * sc.cw, T(1) - hdt * sc.koff, T(0), dt * sc.cw, -dt * sc.koff, T(0)};
         lg = lane_geom(lane, seg, ns, V);
         iy = ct.cell0 / nx;
         ix = ct.cell0 - iy * nx;

@@ -5,6 +5,8 @@
 // by Eq. 1 with the coarse density of Eq. 5.
 #pragma once
 
+#include <cstddef>
+
 #include "mm_internal.cuh"
 #include "mm_walk.cuh"
 
@@ -94,6 +96,79 @@ __host__ __device__ inline WarpSmem warp_smem_layout(int S, int chunk_elems, int
   off = (off + 127) & ~(size_t)127;
   w.total = off;
   return w;
+}
+
+// ------------------------------------------------------------ launch scalars
+
+// The scalars of a substep in the state precision: dt and dt / 2, the psi
+// correction factor g (1 without mass correction), k_on, k_off, glide, v_sp,
+// v/ds and the grid spacings. In float32 the seven float64 scalars of
+// DevParams (dt, psi_scale, k_on, k_off, glide, v_sp, cw) are converted by one
+// instruction for the whole warp -- lane q converts scalar q, the lanes then
+// exchange them by shuffles -- because conversions from float64 run on the
+// narrow float64 pipe; the spacings arrive converted in the launch arguments.
+template <typename T>
+struct StepScalars {
+  T dt, hdt, g, kon, koff, glide, vsp, cw, inv_dx, inv_dy, inv_dth, dth, ds;
+};
+template <typename T, bool MASSCORR>
+__device__ __forceinline__ StepScalars<T> step_scalars(const DevParams* P, const StepArgs<T>& a,
+                                                       int lane) {
+  StepScalars<T> s;
+  if constexpr (sizeof(T) == 4) {
+    const double* pd = reinterpret_cast<const double*>(P);
+    constexpr int kCw = (int)(offsetof(DevParams, cw) / sizeof(double));
+    static_assert(offsetof(DevParams, psi_scale) == 8 && offsetof(DevParams, k_on) == 40 &&
+                      offsetof(DevParams, v_sp) == 64,
+                  "lane q reads the q-th of dt, psi_scale, k_on, k_off, glide, v_sp");
+    const int idx = lane < 2 ? lane : (lane < 6 ? lane + 3 : kCw);
+    const float x = lane < 7 ? (float)pd[idx] : 0.0f;
+    s.dt = __shfl_sync(0xffffffffu, x, 0);
+    s.g = MASSCORR ? __shfl_sync(0xffffffffu, x, 1) : 1.0f;
+    s.kon = __shfl_sync(0xffffffffu, x, 2);
+    s.koff = __shfl_sync(0xffffffffu, x, 3);
+    s.glide = __shfl_sync(0xffffffffu, x, 4);
+    s.vsp = __shfl_sync(0xffffffffu, x, 5);
+    s.cw = __shfl_sync(0xffffffffu, x, 6);
+    s.hdt = 0.5f * s.dt;  // = (float)(dt / 2): halving commutes with the rounding
+    s.inv_dx = a.f_inv_dx;
+    s.inv_dy = a.f_inv_dy;
+    s.inv_dth = a.f_inv_dth;
+    s.dth = a.f_dth;
+    s.ds = a.f_ds;
+  } else {
+    s.dt = P->dt;
+    s.hdt = 0.5 * P->dt;
+    s.g = MASSCORR ? P->psi_scale : 1.0;
+    s.kon = P->k_on;
+    s.koff = P->k_off;
+    s.glide = P->glide;
+    s.vsp = P->v_sp;
+    s.cw = P->cw;
+    s.inv_dx = a.inv_dx;
+    s.inv_dy = a.inv_dy;
+    s.inv_dth = a.inv_dth;
+    s.dth = a.dth;
+    s.ds = a.ds;
+  }
+  return s;
+}
+
+// Sum over the warp of a float-float pair (compensated: TwoSum at every level),
+// returned as float64 in every lane.
+__device__ __forceinline__ double warp_sum_ff(float hi, float lo) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+    const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+    const float s = hi + h2, bb = s - hi;
+    lo = (lo + l2) + ((hi - (s - bb)) + (h2 - bb));
+    hi = s;
+  }
+  return (double)hi + (double)lo;
+}
+__device__ __forceinline__ double warp_sum_ff(double hi, double lo) {
+  return warp_sum(hi + lo);
 }
 
 // ------------------------------------------------------------- s-row chunk

@@ -41,6 +41,7 @@ struct StepArgs {
   int nb_tma;         // 1: stage the psi / n_b neighbourhood by bulk copies
   long long ncells;
   double inv_dx, inv_dy, inv_dth, dth, ds, L;
+  float f_inv_dx, f_inv_dy, f_inv_dth, f_dth, f_ds;  // the same in float32
   const T* mb_in;     // [cells][nth][ns] Mb at step n (may equal mb_out: in place)
   T* mb_out;          // Mb at step n+1
   const T* psi_in;    // [cells][nth]

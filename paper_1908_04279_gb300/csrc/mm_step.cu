@@ -68,19 +68,14 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
   const LaneGeom lg = lane_geom(lane, seg, ns, V);
 
   const DevParams* P = a.prm;
-  const double dt64 = P->dt;
-  const T dt = (T)dt64, hdt = (T)(0.5 * dt64);
-  const T cw = (T)P->cw;
-  const T koff = (T)P->k_off;
-  const T kon = (T)P->k_on;
-  const T glide = (T)P->glide, vsp = (T)P->v_sp;
-  const T g = MASSCORR ? (T)P->psi_scale : T(1);
+  const StepScalars<T> sc = step_scalars<T, MASSCORR>(P, a, lane);
+  const T dt = sc.dt, hdt = sc.hdt, kon = sc.kon;
   const uint32_t wait_limit = P->wait_limit;
   const bool wait_never = (P->debug_flags & 1u) != 0;  // test knob: every wait runs out
-  const PsiConst<T> pq{dt, g, glide, vsp, (T)a.inv_dx, (T)a.inv_dy, (T)a.inv_dth, (T)a.dth,
+  const PsiConst<T> pq{dt, sc.g, sc.glide, sc.vsp, sc.inv_dx, sc.inv_dy, sc.inv_dth, sc.dth,
                        a.trig};
-  const T ds = (T)a.ds;
-  RkConst<T> rk{hdt * cw, T(1) - hdt * koff, T(0), dt * cw, -dt * koff, T(0)};
+  const T ds = sc.ds;
+  RkConst<T> rk{hdt * sc.cw, T(1) - hdt * sc.koff, T(0), dt * sc.cw, -dt * sc.koff, T(0)};
 
   // producer cursor: next chunk to issue (cell, part, stage)
   int icell = gw, ipart = 0, istage = 0, issued = 0;
@@ -224,7 +219,7 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
   // order; the last block adds the block partials in a fixed order
   __shared__ double s_red[32];
   __shared__ unsigned int s_last;
-  mass_acc = warp_sum((double)mass_hi + (double)mass_lo);
+  mass_acc = warp_sum_ff(mass_hi, mass_lo);
   if (lane == 0) s_red[wib] = mass_acc;
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -53,6 +53,7 @@ KERNEL_SRCS = {
     "k_substep": ("mm_step.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
     "k_substep_batch": ("mm_batch.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
     "k_adjoint": ("mm_adjoint.cu", "mm_walk.cuh", "mm_internal.cuh"),
+    "k_motor_local": ("mm_local.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
 }
 
 
@@ -114,6 +115,11 @@ def read_peaks():
 # difference and two fmas of the stage update (11); two stages, plus one add
 # of the n_b sum.
 LOCAL_OPS = 23
+
+
+def wname_of(leg: dict) -> str:
+    """Workload name of a bench leg from its description."""
+    return leg["workload"].split(" ")[0]
 
 
 def alu_peak_tops(sm_mhz: float = 2070.0, sms: int = 152, lanes: int = 128) -> float:
@@ -573,7 +579,8 @@ def run_ours(args):
         ops = v["cell_updates_per_call"] * LOCAL_OPS / (v["ms_per_call"] * 1e-3) / 1e12
         v["roofline"] = {"bound": "alu", "achieved": ops, "peak": alu_peak_tops(),
                          "unit": "Tops/s", "frac": ops / alu_peak_tops(),
-                         "kernel": "k_motor_local (float32)", "traffic": None}
+                         "kernel": "k_motor_local (float32)",
+                         "traffic": read_profile_traffic("k_motor_local", wname_of(v), "fp32")}
 
     total_ms, kern_ms, fp64_ms, e2e_s = reduce_max([total_ms, kern_ms, fp64_ms, e2e_s], dev)
 

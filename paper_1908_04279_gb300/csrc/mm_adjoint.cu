@@ -355,6 +355,157 @@ struct MotorAcc {
   T lmf, D, gk, gv, gn;
 };
 
+// ---- float32 rows of V = 4 or 8 nodes per lane as register pairs (nodes
+// 2k, 2k + 1): the element-wise arithmetic of motor_rows as packed two-value
+// instructions; shifted differences, the limiter and its branch decisions
+// stay scalar. The same values as the scalar form (the accumulations over a
+// lane's nodes run in two interleaved sums).
+
+// One node of the COEF walk: the Superbee value r (sigma/2 = sgn r) and the
+// branch coefficients, with the comparisons of walk_dflux<..., true>.
+__device__ __forceinline__ void coef_node(float A, float hA, float hB, float B, float& r,
+                                          float& ga, float& gb) {
+  const float t1 = fminf(A, hB), t2 = fminf(hA, B);
+  r = max3_t(t1, t2, 0.0f);
+  const bool pos = r > 0.0f, p1 = t1 > t2, x1a = A < hB, x2a = hA < B;
+  const float a1 = x1a ? 1.0f : 0.0f, b1 = x1a ? 0.0f : 0.5f;
+  const float a2 = x2a ? 0.5f : 0.0f, b2 = x2a ? 0.0f : 1.0f;
+  ga = pos ? (p1 ? a1 : a2) : 0.0f;
+  gb = pos ? (p1 ? b1 : b2) : 0.0f;
+}
+
+template <int V>
+__device__ __forceinline__ void walk_coef_x2(const float2 (&M)[V / 2], float2 (&D)[V / 2],
+                                             float2 (&ga)[V / 2], float2 (&gb)[V / 2], bool first,
+                                             bool last, int seg) {
+  constexpr int H = V / 2;
+  float ml = __shfl_up_sync(0xffffffffu, M[H - 1].y, 1, seg);
+  const float mr = __shfl_down_sync(0xffffffffu, M[0].x, 1, seg);
+  if (first) ml = 0.0f;
+  float2 d[H], hd[H];
+  d[0] = make_float2(M[0].x - ml, M[0].y - M[0].x);
+#pragma unroll
+  for (int k = 1; k < H; ++k) d[k] = make_float2(M[k].x - M[k - 1].y, M[k].y - M[k].x);
+  const float dV = mr - M[H - 1].y, hdV = 0.5f * dV;
+  const float2 half2 = make_float2(0.5f, 0.5f);
+#pragma unroll
+  for (int k = 0; k < H; ++k) hd[k] = __fmul2_rn(half2, d[k]);
+  float2 F[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const float b1 = k + 1 < H ? d[k + 1].x : dV, hb1 = k + 1 < H ? hd[k + 1].x : hdV;
+    float2 sg = make_float2(copysignf(1.0f, d[k].y), copysignf(1.0f, b1));
+    if (k == H - 1 && last) sg.y = 0.0f;  // plus end: F = M, no slope
+    const float2 A = __fmul2_rn(d[k], sg), hA = __fmul2_rn(hd[k], sg);
+    float2 r;
+    coef_node(A.x, hA.x, fabsf(hd[k].y), fabsf(d[k].y), r.x, ga[k].x, gb[k].x);
+    coef_node(A.y, hA.y, fabsf(hb1), fabsf(b1), r.y, ga[k].y, gb[k].y);
+    F[k] = __ffma2_rn(r, sg, M[k]);
+  }
+  float fl = __shfl_up_sync(0xffffffffu, F[H - 1].y, 1, seg);
+  if (first) fl = 0.0f;
+  D[0] = make_float2(fl - F[0].x, F[0].x - F[0].y);
+#pragma unroll
+  for (int k = 1; k < H; ++k) D[k] = make_float2(F[k - 1].y - F[k].x, F[k].x - F[k].y);
+}
+
+// walk_adj on register pairs.
+template <int V>
+__device__ __forceinline__ void walk_adj_x2(const float2 (&ga)[V / 2], const float2 (&gb)[V / 2],
+                                            const float2 (&y)[V / 2], float2 (&z)[V / 2],
+                                            bool first, bool last, int seg, float cw) {
+  constexpr int H = V / 2;
+  const float yr = __shfl_down_sync(0xffffffffu, y[0].x, 1, seg);
+  const float2 cw2 = make_float2(cw, cw);
+  float2 lF[H], P[H], Q[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const float yn1 = k + 1 < H ? y[k + 1].x : yr;
+    lF[k] = __fmul2_rn(cw2, make_float2(y[k].y - y[k].x, yn1 - y[k].y));
+  }
+  if (last) lF[H - 1].y = -cw * y[H - 1].y;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    P[k] = __fmul2_rn(ga[k], lF[k]);
+    Q[k] = __fmul2_rn(gb[k], lF[k]);
+  }
+  float Pr = __shfl_down_sync(0xffffffffu, P[0].x, 1, seg);
+  float Ql = __shfl_up_sync(0xffffffffu, Q[H - 1].y, 1, seg);
+  if (last) Pr = 0.0f;
+  if (first) Ql = 0.0f;
+  const float2 m1 = make_float2(-1.0f, -1.0f);
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    const float2 t = __ffma2_rn(Q[k], m1, __fadd2_rn(lF[k], P[k]));  // lF + P - Q
+    const float pn1 = k + 1 < H ? P[k + 1].x : Pr, qp0 = k > 0 ? Q[k - 1].y : Ql;
+    z[k] = make_float2((t.x - P[k].y) + qp0, (t.y - pn1) + Q[k].x);
+  }
+}
+
+template <int V>
+__device__ __forceinline__ void motor_rows_x2(const float (&Mv)[V], float (&Lv)[V], float psi1,
+                                              float lnb, bool act, bool first, bool last, int seg,
+                                              const MotorConst<float>& m, float c3, float mf_n,
+                                              float lamC_c, float f_c, MotorAcc<float>& acc,
+                                              Pack<float, V>& out) {
+  constexpr int H = V / 2;
+  float2 M[H], L[H], Dn[H], Ds[H], Ms[H], gan[H], gbn[H], gas[H], gbs[H];
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    M[k] = make_float2(Mv[2 * k], Mv[2 * k + 1]);
+    L[k] = make_float2(Lv[2 * k], Lv[2 * k + 1]);
+  }
+  walk_coef_x2<V>(M, Dn, gan, gbn, first, last, seg);
+  const float2 c1 = make_float2(m.c1, m.c1), c2 = make_float2(m.c2, m.c2);
+  const float2 c32 = make_float2(c3, c3);
+#pragma unroll
+  for (int k = 0; k < H; ++k) Ms[k] = __ffma2_rn(c1, Dn[k], __ffma2_rn(c2, M[k], c32));
+  walk_coef_x2<V>(Ms, Ds, gas, gbs, first, last, seg);
+  // lam_Mb** = f lam_Mb' + lam_C psi^{n+1} dtheta ds (through C and the scale-down)
+  const float add = act ? lamC_c * psi1 * m.dth * m.ds : 0.0f;
+  const float2 f2 = make_float2(f_c, f_c), add2 = make_float2(add, add);
+  const float2 dt2 = make_float2(m.dt, m.dt), hdt2 = make_float2(m.hdt, m.hdt);
+  const float2 nk2 = make_float2(-m.koff, -m.koff), z2 = make_float2(0.0f, 0.0f);
+  float2 y1[H], zs[H], y2[H], zn[H];
+  float2 sy1 = z2, sy2 = z2, gk = z2, gv = z2, Dacc = z2;
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    L[k] = __ffma2_rn(f2, L[k], add2);  // lam_Mb**
+    y1[k] = __fmul2_rn(dt2, L[k]);
+    sy1 = __fadd2_rn(sy1, y1[k]);
+  }
+  walk_adj_x2<V>(gas, gbs, y1, zs, first, last, seg, m.cw);
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    zs[k] = __ffma2_rn(nk2, y1[k], zs[k]);  // lam_Ms = J_R(Ms)^T y1
+    gk = __ffma2_rn(make_float2(-Ms[k].x, -Ms[k].y), y1[k], gk);
+    gv = __ffma2_rn(Ds[k], y1[k], gv);
+    y2[k] = __fmul2_rn(hdt2, zs[k]);
+    sy2 = __fadd2_rn(sy2, y2[k]);
+  }
+  walk_adj_x2<V>(gan, gbn, y2, zn, first, last, seg, m.cw);
+  const float2 lnb2 = make_float2(lnb, lnb);
+#pragma unroll
+  for (int k = 0; k < H; ++k) {
+    gk = __ffma2_rn(make_float2(-M[k].x, -M[k].y), y2[k], gk);
+    gv = __ffma2_rn(Dn[k], y2[k], gv);
+    float2 lm = __fadd2_rn(__fadd2_rn(L[k], zs[k]), zn[k]);
+    lm = __fadd2_rn(__ffma2_rn(nk2, y2[k], lm), lnb2);
+    out.v[2 * k] = lm.x;
+    out.v[2 * k + 1] = lm.y;
+    Dacc = __ffma2_rn(lm, M[k], Dacc);
+  }
+  acc.gk += gk.x + gk.y;
+  acc.gv += gv.x + gv.y;
+  acc.D += Dacc.x + Dacc.y;
+  if (act) {
+    const float sy = (sy1.x + sy1.y) + (sy2.x + sy2.y);
+    acc.lmf += m.kon * sy;
+    acc.gn += mf_n * sy;
+  }
+  (void)Lv;
+}
+
 // The reverse of Eq. 4 on one group of rows (V nodes per lane): M = Mb^n and
 // L = lam_Mb^{n+1} of the lane's nodes, psi1 = psi^{n+1} and lnb = lam_n_b^n ds
 // of the lane's row; returns lam_Mb^n of the nodes in `out`. Recomputes the
@@ -365,6 +516,9 @@ __device__ __forceinline__ void motor_rows(const T (&M)[V], T (&L)[V], T psi1, T
                                            bool first, bool last, int seg, const MotorConst<T>& m,
                                            T c3, T mf_n, T lamC_c, T f_c, MotorAcc<T>& acc,
                                            Pack<T, V>& out) {
+  if constexpr (sizeof(T) == 4 && (V == 4 || V == 8)) {
+    motor_rows_x2<V>(M, L, psi1, lnb, act, first, last, seg, m, c3, mf_n, lamC_c, f_c, acc, out);
+  } else {
   T Dn[V], Ds[V], Ms[V], gan[V], gbn[V], gas[V], gbs[V];
   walk_dflux<T, V, true>(M, Dn, first, last, seg, gan, gbn);
 #pragma unroll
@@ -401,6 +555,7 @@ __device__ __forceinline__ void motor_rows(const T (&M)[V], T (&L)[V], T psi1, T
   if (act) {
     acc.lmf += m.kon * (sy1 + sy2);
     acc.gn += mf_n * (sy1 + sy2);
+  }
   }
 }
 

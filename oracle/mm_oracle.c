@@ -29,7 +29,8 @@
  *
  * Readings of the paper taken where it is silent (each is listed in the
  * design notes): motor anchors collapse to the filament-centre cell and the
- * capture indicator of Eq. 4 is 1; the gliding speed is v_sp + glide * n_b;
+ * capture indicator of Eq. 4 is 1 (the *_anchor functions keep the anchors
+ * instead: each configuration is anchored in the cell under its motor head); the gliding speed is v_sp + glide * n_b;
  * the rotation rate of Eq. 3 is Jeffery's rod rotation p_perp . grad(u) . p;
  * the substep is global per instance; psi is advanced first in each substep.
  */
@@ -390,6 +391,170 @@ int or_motor_local(const or_grid* g, const or_rates* r, double T, const double* 
     }
   }
   free(buf);
+  return OR_OK;
+}
+
+/* ------------------------------------------------ non-local motor anchors */
+
+/* Anchor of a bound-motor configuration (the next row f2 of the hot path,
+ * Eq. 4-6 and Eq. 10 with r0 kept). A motor bound at arclength s of a filament
+ * centred at x with orientation theta has its head at x + (l/L) s p (the point
+ * where Eq. 10 spreads its force); with the capture radius r_c of Eq. 4 taken
+ * to zero its tail r0 sits directly beneath the head, so each configuration
+ * (cell i, theta_k, s_j) has exactly one anchor cell: the cell containing
+ * x_i + (l/L) s_j p_k. Its offset from cell i, in cells, is
+ *   ox = floor(((l/L) L (2j + 1 - ns) / (2 ns)) cos(theta_k) / dx + 1/2)
+ *   oy = floor(((l/L) L (2j + 1 - ns) / (2 ns)) sin(theta_k) / dy + 1/2)
+ * (s_j written as L (2j + 1 - ns) / (2 ns): products and quotients only, so
+ * no compiler fuses a multiply with an add). ox, oy are [nth][ns]. */
+static void anchor_offsets(const or_grid* g, const or_rates* r, int* ox, int* oy) {
+  double dx = dx_of(g), dy = dy_of(g), dth = dth_of(g);
+  for (int k = 0; k < g->nth; ++k) {
+    double th = k * dth, ct = cos(th), st = sin(th);
+    for (int j = 0; j < g->ns; ++j) {
+      double disp = r->ell * g->L * (double)(2 * j + 1 - g->ns) / (2.0 * g->ns);
+      ox[k * g->ns + j] = (int)floor(disp * ct / dx + 0.5);
+      oy[k * g->ns + j] = (int)floor(disp * st / dy + 0.5);
+    }
+  }
+}
+
+static size_t anchor_of(const or_grid* g, const int* ox, const int* oy, int ix, int iy, int k,
+                        int j) {
+  return cidx(g, wrap(ix + ox[k * g->ns + j], g->nx), wrap(iy + oy[k * g->ns + j], g->ny));
+}
+
+/* Eq. 5 at the anchors, C(r0) = sum over the configurations anchored at r0
+ * of psi Mb ds dth (cells i, then k, then j in order), the Alg. 2 scale-down
+ * of every configuration anchored where C exceeds the total M, and Eq. 6. */
+static int anchor_close(const or_grid* g, const int* ox, const int* oy, const double* psi,
+                        double* mb, const double* mtot, double* mf, double* c) {
+  size_t nc = ncell(g);
+  double ds = ds_of(g), dth = dth_of(g);
+  double* cpre = (double*)calloc(nc, sizeof(double));
+  double* f = (double*)malloc(sizeof(double) * nc);
+  if (!cpre || !f) { free(cpre); free(f); return OR_ERR_NOMEM; }
+  for (int iy = 0; iy < g->ny; ++iy)
+    for (int ix = 0; ix < g->nx; ++ix)
+      for (int k = 0; k < g->nth; ++k) {
+        double p = psi[pidx(g, ix, iy, k)];
+        const double* M = mb + pidx(g, ix, iy, k) * g->ns;
+        for (int j = 0; j < g->ns; ++j)
+          cpre[anchor_of(g, ox, oy, ix, iy, k, j)] += p * M[j] * ds * dth;
+      }
+  for (size_t a = 0; a < nc; ++a) {
+    f[a] = 1.0;
+    c[a] = cpre[a];
+    if (mtot[a] < cpre[a]) { /* Alg. 2 scale-down */
+      f[a] = mtot[a] / cpre[a];
+      c[a] = mtot[a];
+    }
+    mf[a] = mtot[a] - c[a]; /* Eq. 6 */
+  }
+  for (int iy = 0; iy < g->ny; ++iy)
+    for (int ix = 0; ix < g->nx; ++ix)
+      for (int k = 0; k < g->nth; ++k) {
+        double* M = mb + pidx(g, ix, iy, k) * g->ns;
+        for (int j = 0; j < g->ns; ++j) {
+          double fa = f[anchor_of(g, ox, oy, ix, iy, k, j)];
+          if (fa != 1.0) M[j] *= fa;
+        }
+      }
+  free(cpre);
+  free(f);
+  return OR_OK;
+}
+
+/* State set-up with anchors: C at the anchors, the scale-down, Mf. */
+int or_init_free_anchor(const or_grid* g, const or_rates* r, const double* psi, double* mb,
+                        const double* mtot, double* mf, double* c) {
+  if (!grid_ok(g) || !r || !psi || !mb || !mtot || !mf || !c) return OR_ERR_INVALID;
+  int* ox = (int*)malloc(sizeof(int) * 2 * (size_t)g->nth * g->ns);
+  if (!ox) return OR_ERR_NOMEM;
+  int* oy = ox + (size_t)g->nth * g->ns;
+  anchor_offsets(g, r, ox, oy);
+  int rc = anchor_close(g, ox, oy, psi, mb, mtot, mf, c);
+  free(ox);
+  return rc;
+}
+
+/* One substep with non-local anchors: psi by Eq. 1 (unchanged), then every
+ * s-row by the RK2 half and full stage of Eq. 4 where the binding term of
+ * node j takes the free motors of its own anchor, k_on Mf(r0(i, k, j)) (Mf
+ * frozen over both stages), then Eq. 5 at the anchors with psi at the new time,
+ * the scale-down per anchor and Eq. 6. */
+int or_substep_anchor(const or_grid* g, const or_rates* r, double dt, const double* u,
+                      double* psi, double* mb, double* mf, double* c, const double* mtot) {
+  if (!grid_ok(g) || !r || !u || !psi || !mb || !mf || !c || !mtot) return OR_ERR_INVALID;
+  size_t rows = ncell(g) * g->nth;
+  int ns = g->ns;
+  double ds = ds_of(g);
+  double* nb = (double*)malloc(sizeof(double) * rows);
+  double* pn = (double*)malloc(sizeof(double) * rows);
+  double* buf = (double*)malloc(sizeof(double) * (6 * (size_t)ns + 2));
+  int* ox = (int*)malloc(sizeof(int) * 2 * (size_t)g->nth * ns);
+  if (!nb || !pn || !buf || !ox) { free(nb); free(pn); free(buf); free(ox); return OR_ERR_NOMEM; }
+  int* oy = ox + (size_t)g->nth * ns;
+  double *R = buf, *Ms = buf + ns, *Mss = buf + 2 * ns, *Phi = buf + 3 * ns, *mfj = buf + 5 * ns + 2;
+  anchor_offsets(g, r, ox, oy);
+  rows_nb(g, mb, nb);
+  psi_transport(g, r, dt, u, psi, nb, pn); /* Eq. 1 */
+  for (int iy = 0; iy < g->ny; ++iy)
+    for (int ix = 0; ix < g->nx; ++ix)
+      for (int k = 0; k < g->nth; ++k) {
+        double* M = mb + pidx(g, ix, iy, k) * ns;
+        for (int j = 0; j < ns; ++j) mfj[j] = mf[anchor_of(g, ox, oy, ix, iy, k, j)];
+        /* Alg. 2 half and full stage, R_j = -dPhi/ds - k_off M_j + k_on Mf(r0) */
+        walk_fluxes(ns, r->v_walk, M, Phi);
+        for (int j = 0; j < ns; ++j)
+          R[j] = -(Phi[j + 1] - Phi[j]) / ds - r->k_off * M[j] + r->k_on * mfj[j];
+        for (int j = 0; j < ns; ++j) Ms[j] = M[j] + 0.5 * dt * R[j];
+        walk_fluxes(ns, r->v_walk, Ms, Phi);
+        for (int j = 0; j < ns; ++j)
+          R[j] = -(Phi[j + 1] - Phi[j]) / ds - r->k_off * Ms[j] + r->k_on * mfj[j];
+        for (int j = 0; j < ns; ++j) Mss[j] = M[j] + dt * R[j];
+        memcpy(M, Mss, sizeof(double) * ns);
+      }
+  int rc = anchor_close(g, ox, oy, pn, mb, mtot, mf, c); /* Eq. 5, Alg. 2, Eq. 6 */
+  memcpy(psi, pn, sizeof(double) * rows);
+  free(nb); free(pn); free(buf); free(ox);
+  return rc;
+}
+
+/* The motor force of Eq. 10 with the anchors kept: the force of a bound
+ * configuration acts at its head, i.e. in its anchor cell,
+ * F(r0) = F sum over the configurations anchored at r0 of p psi Mb ds dth.
+ * F is [2][ny][nx] (x then y component). */
+int or_anchor_force(const or_grid* g, const or_rates* r, const double* psi, const double* mb,
+                    double* F) {
+  if (!grid_ok(g) || !r || !psi || !mb || !F) return OR_ERR_INVALID;
+  size_t nc = ncell(g);
+  double ds = ds_of(g), dth = dth_of(g);
+  int* ox = (int*)malloc(sizeof(int) * 2 * (size_t)g->nth * g->ns);
+  if (!ox) return OR_ERR_NOMEM;
+  int* oy = ox + (size_t)g->nth * g->ns;
+  anchor_offsets(g, r, ox, oy);
+  for (size_t a = 0; a < 2 * nc; ++a) F[a] = 0.0;
+  for (int iy = 0; iy < g->ny; ++iy)
+    for (int ix = 0; ix < g->nx; ++ix)
+      for (int k = 0; k < g->nth; ++k) {
+        double th = k * dth_of(g), ct = cos(th), st = sin(th);
+        double p = psi[pidx(g, ix, iy, k)];
+        const double* M = mb + pidx(g, ix, iy, k) * g->ns;
+        for (int j = 0; j < g->ns; ++j) {
+          size_t a = anchor_of(g, ox, oy, ix, iy, k, j);
+          F[a] += r->force_scale * ct * p * M[j] * ds * dth;
+          F[nc + a] += r->force_scale * st * p * M[j] * ds * dth;
+        }
+      }
+  free(ox);
+  return OR_OK;
+}
+
+/* The anchor offsets themselves ([nth][ns] each), for tests. */
+int or_anchor_offsets(const or_grid* g, const or_rates* r, int* ox, int* oy) {
+  if (!grid_ok(g) || !r || !ox || !oy) return OR_ERR_INVALID;
+  anchor_offsets(g, r, ox, oy);
   return OR_OK;
 }
 

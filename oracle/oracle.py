@@ -65,6 +65,10 @@ def _load():
             lib.or_adjoint_substep.argtypes = [G, R, C.c_double, P, P, P, P, P, P, P, P, P, P]
             IP = C.POINTER(C.c_int)
             lib.or_motor_local.argtypes = [G, R, C.c_double, P, P, P, P, P, IP, IP]
+            lib.or_init_free_anchor.argtypes = [G, R, P, P, P, P, P]
+            lib.or_substep_anchor.argtypes = [G, R, C.c_double, P, P, P, P, P, P]
+            lib.or_anchor_force.argtypes = [G, R, P, P, P]
+            lib.or_anchor_offsets.argtypes = [G, R, IP, IP]
             _lib = lib
     return _lib
 
@@ -281,3 +285,51 @@ def motor_local(grid, rates, state: State, T: float, nsteps=None) -> np.ndarray:
                                   nin.ctypes.data_as(IP) if nin is not None else None,
                                   out.ctypes.data_as(IP)), "motor_local")
     return out
+
+
+# ---- non-local motor anchors (next row f2)
+
+
+def make_state_anchor(grid, rates, psi, mb=None, mtot=None) -> State:
+    """make_state with the anchors kept: C at each anchor cell (the cell under
+    the motor head x + (l/L) s p), the Alg. 2 scale-down per anchor, Mf."""
+    g = grid
+    psi = np.ascontiguousarray(psi, dtype=np.float64).reshape(g.ny, g.nx, g.ntheta).copy()
+    mb = (np.zeros((g.ny, g.nx, g.ntheta, g.ns)) if mb is None
+          else np.ascontiguousarray(mb, dtype=np.float64).reshape(g.ny, g.nx, g.ntheta, g.ns).copy())
+    mtot = (np.ones((g.ny, g.nx)) if mtot is None
+            else np.ascontiguousarray(mtot, dtype=np.float64).reshape(g.ny, g.nx).copy())
+    mf = np.empty((g.ny, g.nx))
+    c = np.empty((g.ny, g.nx))
+    _check(_load().or_init_free_anchor(C.byref(_grid(g)), C.byref(_rates(rates)), _p(psi), _p(mb),
+                                       _p(mtot), _p(mf), _p(c)), "init_free_anchor")
+    return State(g, psi, mb, mf, c, mtot)
+
+
+def run_anchor(grid, rates, state: State, u: np.ndarray, dt_: float, nsub: int) -> State:
+    """nsub substeps with the anchors kept (or_substep_anchor), in place."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    lib = _load()
+    for _ in range(nsub):
+        _check(lib.or_substep_anchor(C.byref(_grid(grid)), C.byref(_rates(rates)), float(dt_),
+                                     _p(u), _p(state.psi), _p(state.mb), _p(state.mf),
+                                     _p(state.c), _p(state.mtot)), "substep_anchor")
+    return state
+
+
+def anchor_force(grid, rates, state: State) -> np.ndarray:
+    """Motor force of Eq. 10 acting at the anchors, [2][ny][nx]."""
+    F = np.empty((2, grid.ny, grid.nx))
+    _check(_load().or_anchor_force(C.byref(_grid(grid)), C.byref(_rates(rates)), _p(state.psi),
+                                   _p(state.mb), _p(F)), "anchor_force")
+    return F
+
+
+def anchor_offsets(grid, rates):
+    """(ox, oy) int arrays [ntheta][ns]: the anchor cell offsets."""
+    ox = np.empty((grid.ntheta, grid.ns), dtype=np.int32)
+    oy = np.empty((grid.ntheta, grid.ns), dtype=np.int32)
+    IP = C.POINTER(C.c_int)
+    _check(_load().or_anchor_offsets(C.byref(_grid(grid)), C.byref(_rates(rates)),
+                                     ox.ctypes.data_as(IP), oy.ctypes.data_as(IP)), "anchor_offsets")
+    return ox, oy

@@ -107,3 +107,69 @@ def substep(grid, rates, dt, u, psi, mb, mf, mtot):
         c_new.append(rowy_c)
         mf_new.append(rowy_mf)
     return psi_new, mb_new, mf_new, c_new
+
+
+def substep_anchor(grid, rates, dt, u, psi, mb, mf, mtot):
+    """One substep with non-local motor anchors: a motor bound at node j of a
+    filament in cell (ix, iy) with orientation k is anchored in the cell that
+    contains its head, the filament centre plus (l/L) s_j p_k (found here by
+    locating that point on the grid, periodic). Binding at node j takes the
+    free motors of that cell; the coarse density, the scale-down and the free
+    motors are formed per anchor cell. The psi transport is the one of
+    substep() (anchors do not enter it)."""
+    nx, ny, nth, ns, L = grid.nx, grid.ny, grid.ntheta, grid.ns, grid.L
+    dth, ds = 2.0 * math.pi / nth, L / ns
+    # psi at the new time from the plain substep (its motor part is discarded)
+    psi_new = substep(grid, rates, dt, u, psi, mb, mf, mtot)[0]
+
+    def anchor(ix, iy, k, j):
+        s = -0.5 * L + (j + 0.5) * ds
+        hx = (ix + 0.5) / nx + rates.ell * s * math.cos(k * dth)
+        hy = (iy + 0.5) / ny + rates.ell * s * math.sin(k * dth)
+        return int(math.floor(hy * ny)) % ny, int(math.floor(hx * nx)) % nx
+
+    def rhs(M, mfree):
+        out = []
+        for j in range(ns):
+            def flux_right(jj):
+                if jj == ns - 1:
+                    return rates.v_walk * M[jj]
+                back = M[jj] - (M[jj - 1] if jj > 0 else 0.0)
+                fwd = M[jj + 1] - M[jj]
+                return rates.v_walk * (M[jj] + 0.5 * _slope(back, fwd))
+            fin = flux_right(j - 1) if j > 0 else 0.0
+            out.append(-(flux_right(j) - fin) / ds - rates.k_off * M[j] + rates.k_on * mfree[j])
+        return out
+
+    new = [[[None] * nth for _ in range(nx)] for _ in range(ny)]
+    coarse = [[0.0] * nx for _ in range(ny)]
+    for iy in range(ny):
+        for ix in range(nx):
+            for k in range(nth):
+                M = mb[iy][ix][k]
+                anc = [anchor(ix, iy, k, j) for j in range(ns)]
+                mfree = [mf[ay][ax] for ay, ax in anc]
+                k1 = rhs(M, mfree)
+                half = [M[j] + 0.5 * dt * k1[j] for j in range(ns)]
+                k2 = rhs(half, mfree)
+                row = [M[j] + dt * k2[j] for j in range(ns)]
+                new[iy][ix][k] = row
+                for j, (ay, ax) in enumerate(anc):
+                    coarse[ay][ax] += psi_new[iy][ix][k] * row[j] * ds * dth
+    scale = [[1.0] * nx for _ in range(ny)]
+    c_new = [[0.0] * nx for _ in range(ny)]
+    mf_new = [[0.0] * nx for _ in range(ny)]
+    for ay in range(ny):
+        for ax in range(nx):
+            cc = coarse[ay][ax]
+            if cc > mtot[ay][ax]:
+                scale[ay][ax] = mtot[ay][ax] / cc
+                cc = mtot[ay][ax]
+            c_new[ay][ax] = cc
+            mf_new[ay][ax] = mtot[ay][ax] - cc
+    for iy in range(ny):
+        for ix in range(nx):
+            for k in range(nth):
+                new[iy][ix][k] = [v * scale[a][b] for v, (a, b) in
+                                  zip(new[iy][ix][k], [anchor(ix, iy, k, j) for j in range(ns)])]
+    return psi_new, new, mf_new, c_new

@@ -643,3 +643,138 @@ def test_motor_local_bind_unbind_closed_form_per_cell(oracle_mod):
     # different densities, different step counts
     assert len(np.unique(n)) > 1
     np.testing.assert_allclose(st.mf + st.c, 1.0, rtol=0, atol=1e-14)
+
+
+# ---- non-local motor anchors (next row f2)
+
+
+def test_anchor_zero_length_is_the_local_substep(oracle_mod):
+    """With l/L = 0 every configuration is anchored in its filament's own cell:
+    the anchor substep, its set-up and its force equal the local ones."""
+    g = Grid(6, 5, 8, 12)
+    r = Rates(ell=0.0, k_on=1.3, glide=0.2)
+    psi = psi_isotropic_perturbed(g, 101, amp=0.4)
+    rng = np.random.default_rng(102)
+    mb = 0.3 * rng.random((g.ny, g.nx, g.ntheta, g.ns))
+    mtot = 0.3 + rng.random((g.ny, g.nx))
+    u = random_divfree_flow(g, 103, 4, 0.2)
+    a = oracle_mod.make_state_anchor(g, r, psi, mb, mtot)
+    b = oracle_mod.make_state(g, psi, mb, mtot)
+    for k in ("mb", "mf", "c"):
+        np.testing.assert_allclose(getattr(a, k), getattr(b, k), rtol=1e-14, atol=1e-15)
+    dt = oracle_mod.dt(g, r, b, u)
+    oracle_mod.run_anchor(g, r, a, u, dt, 6)
+    oracle_mod.run(g, r, b, u, dt, 6)
+    for k in ("psi", "mb", "mf", "c"):
+        np.testing.assert_allclose(getattr(a, k), getattr(b, k), rtol=1e-13, atol=1e-15)
+    fl, _ = oracle_mod.moments(g, r, b)
+    F = oracle_mod.anchor_force(g, r, b)
+    np.testing.assert_allclose(F[0], fl["Fx"], rtol=1e-12, atol=1e-15)
+    np.testing.assert_allclose(F[1], fl["Fy"], rtol=1e-12, atol=1e-15)
+
+
+def test_anchor_offsets_locate_the_head(oracle_mod):
+    """The anchor offsets put the head x + (l/L) s p inside the anchor cell."""
+    g = Grid(16, 12, 8, 10)
+    r = Rates(ell=0.37)
+    ox, oy = oracle_mod.anchor_offsets(g, r)
+    for k in range(g.ntheta):
+        th = k * 2 * np.pi / g.ntheta
+        for j in range(g.ns):
+            s = -0.5 * g.L + (j + 0.5) * g.L / g.ns
+            hx = 0.5 + r.ell * s * np.cos(th) * g.nx  # head, in cells from the centre's cell
+            hy = 0.5 + r.ell * s * np.sin(th) * g.ny
+            assert ox[k, j] <= hx < ox[k, j] + 1 + 1e-12
+            assert oy[k, j] <= hy < oy[k, j] + 1 + 1e-12
+    assert len(np.unique(ox)) > 3 and len(np.unique(oy)) > 3
+    # opposite orientations mirror the offsets (s -> -s)
+    kh = g.ntheta // 2
+    assert np.all(np.abs(ox[kh, ::-1] - ox[0]) <= 1)
+
+
+def test_anchor_single_filament_closed_form(oracle_mod):
+    """One filament density in one cell and orientation, no flow, no walking,
+    no gliding: psi stays put, and the nodes sharing an anchor r relax together
+    by the lagged bind/unbind recursion with rho L replaced by
+    psi0 ds dth n_r (n_r = nodes of that row anchored at r)."""
+    g = Grid(9, 7, 8, 12)
+    r = Rates(v_walk=0.0, glide=0.0, v_sp=0.0, k_on=2.0, k_off=0.4, ell=0.45)
+    psi = np.zeros((g.ny, g.nx, g.ntheta))
+    i0y, i0x, k0 = 3, 4, 1
+    psi0 = 30.0
+    psi[i0y, i0x, k0] = psi0
+    st = oracle_mod.make_state_anchor(g, r, psi)
+    u = np.zeros((2, g.ny, g.nx))
+    dt, n = 0.05, 40
+    oracle_mod.run_anchor(g, r, st, u, dt, n)
+    assert np.array_equal(st.psi, psi)
+    ox, oy = oracle_mod.anchor_offsets(g, r)
+    anchors = [((i0y + oy[k0, j]) % g.ny, (i0x + ox[k0, j]) % g.nx) for j in range(g.ns)]
+    counts = {a: anchors.count(a) for a in anchors}
+    assert len(counts) >= 3
+    ds, dth = g.L / g.ns, 2 * np.pi / g.ntheta
+    A = 1 - r.k_off * dt + (r.k_off * dt) ** 2 / 2
+    B = r.k_on * dt * (1 - r.k_off * dt / 2)
+    for j, a in enumerate(anchors):
+        w = psi0 * ds * dth * counts[a]
+        rr = A - B * w
+        Minf = B * 1.0 / (1 - A + B * w)
+        expect = Minf * (1 - rr ** n)
+        assert abs(st.mb[i0y, i0x, k0, j] - expect) <= 1e-13 * expect, j
+        assert abs(st.c[a] - w * expect) <= 1e-13 * w * expect
+        assert abs(st.mf[a] - (1 - w * expect)) <= 1e-13
+    # rows that carry no filaments bind against a full pool: M_inf = B / (1 - A)
+    other = st.mb[0, 0, 5, 3]
+    assert abs(other - B / (1 - A) * (1 - A ** n)) <= 1e-13 * other
+
+
+def test_anchor_conservation_and_uniform_state(oracle_mod):
+    """Bound plus free motors equal the total at every anchor, summed over the
+    grid; a uniform state stays uniform."""
+    g = Grid(8, 6, 8, 10)
+    r = Rates(ell=0.3, k_on=3.0)
+    psi = psi_isotropic_perturbed(g, 111, amp=0.5)
+    rng = np.random.default_rng(112)
+    mb = 0.4 * rng.random((g.ny, g.nx, g.ntheta, g.ns))
+    st = oracle_mod.make_state_anchor(g, r, psi, mb)
+    u = random_divfree_flow(g, 113, 4, 0.1)
+    dt = oracle_mod.dt(g, r, st, u)
+    oracle_mod.run_anchor(g, r, st, u, dt, 15)
+    ds, dth = g.L / g.ns, 2 * np.pi / g.ntheta
+    bound = np.sum(st.psi[..., None] * st.mb) * ds * dth
+    assert abs(bound + st.mf.sum() - st.mtot.sum()) <= 1e-13 * st.mtot.sum()
+    np.testing.assert_allclose(st.mf + st.c, st.mtot, rtol=0, atol=1e-14)
+    # uniform: the same psi and rows everywhere, no flow
+    psiu = psi_isotropic_perturbed(g, 114, amp=0.0)
+    mbu = np.broadcast_to(0.2 * rng.random((g.ntheta, g.ns)), mb.shape).copy()
+    su = oracle_mod.make_state_anchor(g, r, psiu, mbu)
+    oracle_mod.run_anchor(g, r, su, np.zeros((2, g.ny, g.nx)), 0.01, 8)
+    assert np.ptp(su.c) <= 1e-14 * su.c.max()
+    assert np.max(np.ptp(su.mb, axis=(0, 1))) <= 1e-14 * su.mb.max()
+
+
+@pytest.mark.parametrize("dims", [(4, 3, 4, 5), (3, 4, 6, 4)])
+def test_anchor_brute_force_agrees(oracle_mod, dims):
+    """An independent expansion (head located on the grid, binding per node,
+    coarse density per anchor cell) on tiny grids, with flow, gliding and a
+    forced scale-down, agrees with the anchor substep."""
+    g = Grid(*dims)
+    r = Rates(ell=0.43, k_on=9.0, glide=0.3)
+    psi = psi_isotropic_perturbed(g, 121, amp=0.6)
+    rng = np.random.default_rng(122)
+    mb = 0.3 * rng.random((g.ny, g.nx, g.ntheta, g.ns))
+    mtot = 0.25 + 0.5 * rng.random((g.ny, g.nx))
+    u = random_divfree_flow(g, 123, 3, 0.3)
+    st = oracle_mod.make_state_anchor(g, r, psi, mb, mtot)
+    dt = oracle_mod.dt(g, r, st, u) * 4.0  # a long step: the binding overshoots in some cells
+    before = st.copy()
+    oracle_mod.run_anchor(g, r, st, u, dt, 1)
+    bp, bm, bf, bc = brute_force.substep_anchor(g, r, dt, u.tolist(), before.psi.tolist(),
+                                                before.mb.tolist(), before.mf.tolist(),
+                                                before.mtot.tolist())
+    np.testing.assert_allclose(st.psi, np.array(bp), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(st.mb, np.array(bm), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(st.mf, np.array(bf), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(st.c, np.array(bc), rtol=1e-12, atol=1e-14)
+    clipped = np.array(bc) == before.mtot
+    assert np.any(clipped) and not np.all(clipped)  # the scale-down acted in some cells

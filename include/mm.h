@@ -260,6 +260,33 @@ mm_status mm_diffuse(mm_handle* h, double D_t, double D_r, double dt);
 mm_status mm_motor_local(mm_handle* h, double T, const int* nsteps_in, int* nsteps_out,
                          int on_device);
 
+/* ---- Non-local motor anchors ----------------------------------------------------
+ *
+ * mm_set_anchors(h, enable): with enable = 1 every bound-motor configuration
+ * (cell i, theta_k, s_j) is anchored in the cell under its motor head,
+ * x_i + (l/L) s_j p_k with l/L = rates.ell (the delta of Eq. 10), instead of
+ * in the filament's own cell -- Eq. 4-6 and Eq. 10 with the anchor r0 kept and
+ * the capture radius of Eq. 4 taken to zero. The anchor of (i, k, j) is cell
+ * (ix + ox, iy + oy) (periodic) with
+ *   ox = floor(((l/L) L (2j + 1 - ns) / (2 ns)) cos(theta_k) nx + 1/2),
+ *   oy = floor(((l/L) L (2j + 1 - ns) / (2 ns)) sin(theta_k) ny + 1/2),
+ * evaluated in float64 (products and quotients, then one add). Then in every
+ * substep the binding term of node j takes the free motors of its anchor,
+ * k_on Mf(r0) (Mf frozen over both RK2 stages); the coarse density of Eq. 5,
+ * the Alg. 2 scale-down and Eq. 6 are formed per anchor cell, C(r0) = sum of
+ * psi Mb ds dtheta over the configurations anchored at r0 (psi at the new
+ * time); mm_moments' force fields Fx, Fy become the force of Eq. 10 acting in
+ * the anchor cells, F(r0) = F sum p psi Mb ds dtheta. psi transport, n_b and
+ * the substep rule are unchanged. enable = 0 returns to anchors in the
+ * filament's own cell. Either way the call re-derives C, the scale-down and Mf
+ * of the current state under the chosen rule; mm_set_rates re-derives them when
+ * l/L changes. The coarse density is accumulated with float64 atomics: its last
+ * bits depend on the schedule. MM_ERR_UNSUPPORTED on a batch or a batch
+ * member; with anchors on, mm_set_checkpointing and mm_motor_local return
+ * MM_ERR_UNSUPPORTED (the adjoint and the independent-cell local step are not
+ * available) and mm_set_anchors returns MM_ERR_STATE during a recording. */
+mm_status mm_set_anchors(mm_handle* h, int enable);
+
 /* ---- Batched ensemble --------------------------------------------------------
  *
  * An ensemble of n independent instances (an instance as above: its own grid,

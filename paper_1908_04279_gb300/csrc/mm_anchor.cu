@@ -1,0 +1,491 @@
+// Non-local motor anchors (mm_set_anchors): every bound-motor configuration
+// (cell i, theta_k, s_j) is anchored in the cell under its motor head,
+// x_i + (l/L) s_j p_k -- Eq. 4-6 and Eq. 10 with the anchor r0 kept and the
+// capture radius of Eq. 4 taken to zero. Binding at a node takes the free
+// motors of its anchor (a gather), and the coarse density of Eq. 5, the Alg. 2
+// scale-down, Eq. 6 and the motor force of Eq. 10 are formed per anchor (a
+// scatter). One substep is three launches:
+//   k_substep_anchor  warp per cell: psi by Eq. 1 first (its new values weight
+//                     the scatter), then every s-row by the RK2 of Eq. 4 with
+//                     the per-node binding term, n_b of the row, and the row's
+//                     contributions psi ds dtheta Mb added into the anchors'
+//                     float64 accumulators (runs of nodes with the same anchor
+//                     summed in registers first, then one atomic per run);
+//   k_anchor_close    thread per anchor: C, the scale-down factor f, Mf = M - C,
+//                     accumulator reset; a flag if any anchor scaled down;
+//   k_anchor_fix      only where the flag is set (the scale-down is rare):
+//                     scales every node by its anchor's f and recomputes n_b.
+// The paper spreads the force to nearby anchors with atomics in the final
+// reduction only (Sec. 2); here the coarse density and the force are
+// accumulated that way, in float64. Atomic order makes the last bits of C
+// depend on the schedule.
+#include "mm_cell.cuh"
+#include "mm_host.h"
+
+namespace mm {
+
+// Anchor data of one instance: offsets [nth][ns] (reduced into [0, nx) and
+// [0, ny)), float64 accumulators and scale-down factors per cell, flags.
+template <typename T>
+struct AnchorArgs {
+  const int2* off;
+  double* cacc;  // [cells] sum of psi Mb ds dth anchored in each cell (reset after use)
+  double* fsc;   // [cells] scale-down factor of each anchor cell
+  int* flags;    // [3]: 0, 1 alternate with the substep parity; 2 for the set-up
+  int flag;      // the flag this launch sets or reads
+};
+
+__device__ __forceinline__ int anchor_cell(int ix, int iy, int2 o, int nx, int ny) {
+  int ax = ix + o.x, ay = iy + o.y;
+  if (ax >= nx) ax -= nx;
+  if (ay >= ny) ay -= ny;
+  return ay * nx + ax;
+}
+
+// Adds w M[v] of the lane's nodes into the accumulators of their anchors: a
+// run of consecutive nodes with the same anchor is summed first.
+template <typename T, int V>
+__device__ __forceinline__ void scatter_runs(double* acc, const int (&anc)[V], const T (&M)[V],
+                                             T w) {
+  int cur = anc[0];
+  T s = w * M[0];
+#pragma unroll
+  for (int v = 1; v < V; ++v) {
+    if (anc[v] == cur) {
+      s += w * M[v];
+    } else {
+      atomicAdd(acc + cur, (double)s);
+      cur = anc[v];
+      s = w * M[v];
+    }
+  }
+  atomicAdd(acc + cur, (double)s);
+}
+
+// Per-warp shared memory: psi and n_b columns of the cell and its four
+// neighbours ([5][nth] each) and psi^{n+1} of the cell.
+__host__ __device__ inline size_t anchor_warp_smem(int nth, int tsz) {
+  return ((size_t)11 * nth * tsz + 15) & ~(size_t)15;
+}
+
+template <typename T, int V, bool MASSCORR>
+__global__ void __launch_bounds__(128) k_substep_anchor(const StepArgs<T> a, const AnchorArgs<T> x) {
+  extern __shared__ __align__(16) unsigned char asm_raw[];
+  const int nth = a.nth, ns = a.ns, seg = a.seg, nx = a.nx, ny = a.ny;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  T* psi5 = reinterpret_cast<T*>(asm_raw + (size_t)wib * anchor_warp_smem(nth, sizeof(T)));
+  T* nb5 = psi5 + 5 * nth;
+  T* pnew = nb5 + 5 * nth;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
+  const int W = gridDim.x * (blockDim.x >> 5);
+  const int nc = (int)a.ncells;
+  // the flag of the other parity was read by the previous substep's fix-up:
+  // clear it for the next substep
+  if (blockIdx.x == 0 && threadIdx.x == 0) x.flags[x.flag ^ 1] = 0;
+  const StepScalars<T> sc = step_scalars<T, MASSCORR>(a.prm, a, lane);
+  const PsiConst<T> pq{sc.dt, sc.g, sc.glide, sc.vsp, sc.inv_dx, sc.inv_dy, sc.inv_dth, sc.dth,
+                       a.trig};
+  const T c1 = sc.hdt * sc.cw, c2 = T(1) - sc.hdt * sc.koff, e1 = sc.dt * sc.cw, e2 = -sc.dt * sc.koff;
+  const T hk = sc.hdt * sc.kon, fk = sc.dt * sc.kon;
+  const T dsdth = sc.ds * sc.dth;
+  const LaneGeom lg = lane_geom(lane, seg, ns, V);
+  const LaneTrig<T> lt = lane_trig(a.trig, nth, lane);
+  T mass_hi = T(0), mass_lo = T(0);
+  for (int cell = gw; cell < nc; cell += W) {
+    const int iy = cell / nx, ix = cell - iy * nx;
+    const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
+    const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
+    const int nbr[5] = {cell, iy * nx + xp, iy * nx + xm, yp * nx + ix, ym * nx + ix};
+    for (int q = 0; q < 5; ++q)
+      for (int k = lane; k < nth; k += 32) {
+        psi5[q * nth + k] = a.psi_in[(size_t)nbr[q] * nth + k];
+        nb5[q * nth + k] = a.nb_in[(size_t)nbr[q] * nth + k];
+      }
+    __syncwarp();
+    // Eq. 1 first: psi^{n+1} of the cell weights the scatter of its rows
+    const CellVel<T> uv = load_cell_vel(a.ucell, cell);
+    T cell_mass = T(0), unused = T(0);
+    psi_cell(pq, uv, psi5, nb5, nb5, nth, lane, pnew, cell_mass, unused, &lt);
+    two_sum_acc(mass_hi, mass_lo, cell_mass);
+    __syncwarp();
+    for (int k = lane; k < nth; k += 32) a.psi_out[(size_t)cell * nth + k] = pnew[k];
+    // Eq. 4 on every row, binding against the anchors' free motors
+    for (int r0 = 0; r0 < nth; r0 += lg.rpp) {
+      const int k = r0 + lg.rslot;
+      const bool row_ok = k < nth, act = row_ok && lg.lane_ok;
+      const size_t roff = ((size_t)cell * nth + (row_ok ? k : 0)) * ns + lg.sl * V;
+      T M[V], D[V], Ms[V], mfv[V];
+      int anc[V];
+      if (act) {
+        const Pack<T, V> q = *reinterpret_cast<const Pack<T, V>*>(a.mb_in + roff);
+        const int2* o = x.off + (size_t)k * ns + lg.sl * V;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          M[v] = q.v[v];
+          anc[v] = anchor_cell(ix, iy, o[v], nx, ny);
+          mfv[v] = a.mf_in[anc[v]];
+        }
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          M[v] = T(0);
+          mfv[v] = T(0);
+          anc[v] = cell;
+        }
+      }
+      walk_dflux<T, V>(M, D, lg.first, lg.last, seg);
+#pragma unroll
+      for (int v = 0; v < V; ++v) Ms[v] = fma_t(c1, D[v], fma_t(c2, M[v], hk * mfv[v]));
+      walk_dflux<T, V>(Ms, D, lg.first, lg.last, seg);
+      T snb = T(0);
+#pragma unroll
+      for (int v = 0; v < V; ++v) {
+        M[v] = fma_t(e1, D[v], fma_t(e2, Ms[v], M[v] + fk * mfv[v]));
+        snb += M[v];
+      }
+      if (act) {
+        Pack<T, V> q;
+#pragma unroll
+        for (int v = 0; v < V; ++v) q.v[v] = M[v];
+        *reinterpret_cast<Pack<T, V>*>(a.mb_out + roff) = q;
+        scatter_runs<T, V>(x.cacc, anc, M, pnew[k] * dsdth);
+      } else {
+        snb = T(0);
+      }
+      snb = seg_sum(snb, seg);
+      if (lg.first && row_ok) a.nb_out[(size_t)cell * nth + k] = snb * sc.ds;
+    }
+    __syncwarp();
+  }
+  // sum psi^{n+1} as in k_substep: per warp, per block, then the last block
+  __shared__ double s_red[32];
+  __shared__ unsigned int s_last;
+  const double m = warp_sum_ff(mass_hi, mass_lo);
+  if (lane == 0) s_red[wib] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = s_red[0];
+    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) b += s_red[q];
+    a.partial[blockIdx.x] = b;
+    __threadfence();
+    const unsigned int prev = atomicInc(&a.prm->counter, gridDim.x - 1);
+    s_last = prev == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (s_last && wib == 0) {
+    __threadfence();
+    const double tot = warp_sum_ldcg(a.partial, (int)gridDim.x, 1, lane);
+    if (lane == 0) {
+      a.prm->mass = tot;
+      if (MASSCORR && a.mass_correct) a.prm->psi_scale = a.prm->mass0 / tot;
+    }
+  }
+}
+
+// Eq. 5 at the anchors, the Alg. 2 scale-down and Eq. 6 (thread per cell).
+template <typename T>
+__global__ void k_anchor_close(const AnchorArgs<T> x, const T* mtot, T* mf, T* c, long long ncells) {
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < ncells;
+       r += (long long)gridDim.x * blockDim.x) {
+    const double C = x.cacc[r];
+    x.cacc[r] = 0.0;
+    const double M = (double)mtot[r];
+    double f = 1.0, Cc = C;
+    if (M < C) {
+      f = M / C;
+      Cc = M;
+    }
+    x.fsc[r] = f;
+    c[r] = (T)Cc;
+    mf[r] = (T)(M - Cc);
+    if (f != 1.0) atomicOr(x.flags + x.flag, 1);
+  }
+}
+
+// Where an anchor scaled down: every node times its anchor's factor, n_b of
+// the row recomputed (warp per cell; nothing to do without the flag).
+template <typename T, int V>
+__global__ void __launch_bounds__(128) k_anchor_fix(const AnchorArgs<T> x, T* mb, T* nb, int nx,
+                                                    int ny, int nth, int ns, int seg, double ds,
+                                                    long long ncells) {
+  if (x.flags[x.flag] == 0) return;
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int W = gridDim.x * (blockDim.x >> 5);
+  const LaneGeom lg = lane_geom(lane, seg, ns, V);
+  for (int cell = gw; cell < (int)ncells; cell += W) {
+    const int iy = cell / nx, ix = cell - iy * nx;
+    for (int r0 = 0; r0 < nth; r0 += lg.rpp) {
+      const int k = r0 + lg.rslot;
+      const bool row_ok = k < nth, act = row_ok && lg.lane_ok;
+      const size_t roff = ((size_t)cell * nth + (row_ok ? k : 0)) * ns + lg.sl * V;
+      T snb = T(0);
+      if (act) {
+        Pack<T, V> q = *reinterpret_cast<const Pack<T, V>*>(mb + roff);
+        const int2* o = x.off + (size_t)k * ns + lg.sl * V;
+        bool any = false;
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          const double f = x.fsc[anchor_cell(ix, iy, o[v], nx, ny)];
+          if (f != 1.0) {
+            q.v[v] = (T)((double)q.v[v] * f);
+            any = true;
+          }
+          snb += q.v[v];
+        }
+        if (any) *reinterpret_cast<Pack<T, V>*>(mb + roff) = q;
+      }
+      snb = seg_sum(snb, seg);
+      if (lg.first && row_ok) nb[(size_t)cell * nth + k] = snb * (T)ds;
+    }
+  }
+}
+
+// Row sums and the scatter of a given state: mode 0 n_b and psi ds dth Mb into
+// the coarse accumulators (state set-up); mode 1 the motor force of Eq. 10,
+// F p psi Mb ds dth, into fx, fy (float64, [cells] each). psi is scaled by g.
+template <typename T, int V>
+__global__ void __launch_bounds__(128) k_anchor_scatter(const AnchorArgs<T> x, const T* mb,
+                                                        const T* psi, T* nb, double* fx,
+                                                        double* fy, const double* trig64,
+                                                        const DevParams* prm, int mode, int nx,
+                                                        int ny, int nth, int ns, int seg,
+                                                        double ds, double dth, long long ncells) {
+  const int lane = threadIdx.x & 31;
+  const int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int W = gridDim.x * (blockDim.x >> 5);
+  const LaneGeom lg = lane_geom(lane, seg, ns, V);
+  const double g = prm->psi_scale;
+  const double Fm = prm->force_scale;
+  if (mode == 0 && blockIdx.x == 0 && threadIdx.x == 0) x.flags[x.flag] = 0;
+  for (int cell = gw; cell < (int)ncells; cell += W) {
+    const int iy = cell / nx, ix = cell - iy * nx;
+    for (int r0 = 0; r0 < nth; r0 += lg.rpp) {
+      const int k = r0 + lg.rslot;
+      const bool row_ok = k < nth, act = row_ok && lg.lane_ok;
+      const size_t roff = ((size_t)cell * nth + (row_ok ? k : 0)) * ns + lg.sl * V;
+      T snb = T(0);
+      if (act) {
+        const Pack<T, V> q = *reinterpret_cast<const Pack<T, V>*>(mb + roff);
+        const int2* o = x.off + (size_t)k * ns + lg.sl * V;
+        const double w = (double)psi[(size_t)cell * nth + k] * g * ds * dth;
+        int anc[V];
+        double Mv[V];
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          anc[v] = anchor_cell(ix, iy, o[v], nx, ny);
+          Mv[v] = (double)q.v[v];
+          snb += q.v[v];
+        }
+        if (mode == 0) {
+          scatter_runs<double, V>(x.cacc, anc, Mv, w);
+        } else {
+          scatter_runs<double, V>(fx, anc, Mv, Fm * trig64[k] * w);
+          scatter_runs<double, V>(fy, anc, Mv, Fm * trig64[nth + k] * w);
+        }
+      }
+      if (mode == 0) {
+        snb = seg_sum(snb, seg);
+        if (lg.first && row_ok) nb[(size_t)cell * nth + k] = snb * (T)ds;
+      }
+    }
+  }
+}
+
+}  // namespace mm
+
+using namespace mmh;
+
+namespace {
+
+template <typename T>
+mm::AnchorArgs<T> anchor_args(mm_handle* h, int flag) {
+  mm::AnchorArgs<T> x;
+  x.off = (const int2*)h->anc_off;
+  x.cacc = h->anc_cacc;
+  x.fsc = h->anc_fsc;
+  x.flags = h->anc_flags;
+  x.flag = flag;
+  return x;
+}
+
+int blocks_for(long long work, int per_block, int cap) {
+  long long b = (work + per_block - 1) / per_block;
+  if (b > cap) b = cap;
+  return (int)std::max<long long>(b, 1);
+}
+
+// Warps per block of the anchor substep (shared memory of 11 ntheta values per
+// warp) and the kernels' shared-memory limit.
+template <typename T, int V>
+cudaError_t anchor_prepare_t(mm_handle* h) {
+  const size_t per_warp = mm::anchor_warp_smem(h->g.ntheta, sizeof(T));
+  h->anc_wpb = (int)std::min<size_t>(4, kSmemBudget / per_warp);
+  if (h->anc_wpb < 1) return cudaErrorInvalidValue;
+  const int smem = (int)(h->anc_wpb * per_warp);
+  cudaError_t e = cudaFuncSetAttribute(mm::k_substep_anchor<T, V, true>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(mm::k_substep_anchor<T, V, false>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+template <typename T, int V>
+cudaError_t anchor_substep_t(mm_handle* h, int parity, cudaStream_t s) {
+  const StepArgs<T> a = step_args<T>(h, parity);
+  const mm::AnchorArgs<T> x = anchor_args<T>(h, parity);
+  const int wpb = h->anc_wpb;
+  const size_t smem = wpb * mm::anchor_warp_smem(h->g.ntheta, sizeof(T));
+  const int grid = blocks_for(h->ncells, wpb, 8 * h->sms);
+  if (a.mass_correct)
+    mm::k_substep_anchor<T, V, true><<<grid, 32 * wpb, smem, s>>>(a, x);
+  else
+    mm::k_substep_anchor<T, V, false><<<grid, 32 * wpb, smem, s>>>(a, x);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  mm::k_anchor_close<T><<<blocks_for(h->ncells, 256, 8 * h->sms), 256, 0, s>>>(
+      x, (const T*)h->mtot, (T*)h->mf, (T*)h->c, h->ncells);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  mm::k_anchor_fix<T, V><<<grid, 128, 0, s>>>(x, (T*)h->mb, (T*)h->nb[parity ^ 1], h->g.nx,
+                                             h->g.ny, h->g.ntheta, h->g.ns, h->seg,
+                                             h->g.L / h->g.ns, h->ncells);
+  return cudaGetLastError();
+}
+
+template <typename T, int V>
+cudaError_t anchor_scatter_t(mm_handle* h, int mode, double* fx, double* fy) {
+  const mm::AnchorArgs<T> x = anchor_args<T>(h, 2);
+  const int grid = blocks_for(h->ncells, 4, 8 * h->sms);
+  const double ds = h->g.L / h->g.ns, dth = 2.0 * kPi / h->g.ntheta;
+  mm::k_anchor_scatter<T, V><<<grid, 128, 0, h->stream>>>(
+      x, (const T*)h->mb, (const T*)h->psi[h->parity], (T*)h->nb[h->parity], fx, fy, h->trig64,
+      h->prm, mode, h->g.nx, h->g.ny, h->g.ntheta, h->g.ns, h->seg, ds, dth, h->ncells);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || mode != 0) return e;
+  mm::k_anchor_close<T><<<blocks_for(h->ncells, 256, 8 * h->sms), 256, 0, h->stream>>>(
+      x, (const T*)h->mtot, (T*)h->mf, (T*)h->c, h->ncells);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  mm::k_anchor_fix<T, V><<<grid, 128, 0, h->stream>>>(x, (T*)h->mb, (T*)h->nb[h->parity],
+                                                      h->g.nx, h->g.ny, h->g.ntheta, h->g.ns,
+                                                      h->seg, ds, h->ncells);
+  return cudaGetLastError();
+}
+
+// Dispatch on precision and the substep's vector width.
+template <template <typename, int> class F, typename... A>
+cudaError_t by_width(mm_handle* h, A... args) {
+  if (h->prec == MM_FP64) return h->V == 2 ? F<double, 2>::run(h, args...) : F<double, 1>::run(h, args...);
+  if (h->V == 8) return F<float, 8>::run(h, args...);
+  return h->V == 4 ? F<float, 4>::run(h, args...) : F<float, 1>::run(h, args...);
+}
+template <typename T, int V>
+struct SubstepF {
+  static cudaError_t run(mm_handle* h, int parity, cudaStream_t s) {
+    return anchor_substep_t<T, V>(h, parity, s);
+  }
+};
+template <typename T, int V>
+struct PrepareF {
+  static cudaError_t run(mm_handle* h) { return anchor_prepare_t<T, V>(h); }
+};
+template <typename T, int V>
+struct ScatterF {
+  static cudaError_t run(mm_handle* h, int mode, double* fx, double* fy) {
+    return anchor_scatter_t<T, V>(h, mode, fx, fy);
+  }
+};
+
+}  // namespace
+
+namespace mmh {
+
+// The anchor offsets of the current grid and l/L, reduced into [0, nx) and
+// [0, ny), with the formula of the definition evaluated in float64 by products
+// and quotients only (no operation a compiler could fuse).
+mm_status anchor_table(mm_handle* h) {
+  const int nth = h->g.ntheta, ns = h->g.ns, nx = h->g.nx, ny = h->g.ny;
+  const double dx = 1.0 / nx, dy = 1.0 / ny, dth = 2.0 * kPi / nth;
+  std::vector<int2> off((size_t)nth * ns);
+  for (int k = 0; k < nth; ++k) {
+    const double th = k * dth, ct = std::cos(th), st = std::sin(th);
+    for (int j = 0; j < ns; ++j) {
+      const double disp = h->r.ell * h->g.L * (double)(2 * j + 1 - ns) / (2.0 * ns);
+      const double qx = std::floor(disp * ct / dx + 0.5), qy = std::floor(disp * st / dy + 0.5);
+      if (!(std::fabs(qx) < 1e9 && std::fabs(qy) < 1e9))
+        return fail(h, MM_ERR_UNSUPPORTED, "anchor offsets out of range");
+      long long ox = (long long)qx % nx, oy = (long long)qy % ny;
+      if (ox < 0) ox += nx;
+      if (oy < 0) oy += ny;
+      off[(size_t)k * ns + j] = make_int2((int)ox, (int)oy);
+    }
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemcpy(h->anc_off, off.data(), off.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  return MM_OK;
+}
+
+cudaError_t launch_anchor_substep(mm_handle* h, int parity, cudaStream_t s) {
+  return by_width<SubstepF>(h, parity, s);
+}
+
+// State set-up with anchors: n_b, C at the anchors, the scale-down, Mf.
+mm_status run_init_anchor(mm_handle* h) {
+  CK(cudaMemsetAsync(h->anc_cacc, 0, (size_t)h->ncells * 8, h->stream));
+  CK(by_width<ScatterF>(h, 0, (double*)nullptr, (double*)nullptr));
+  return MM_OK;
+}
+
+// The motor force of Eq. 10 at the anchors into fields 7 and 8.
+mm_status anchor_force(mm_handle* h) {
+  const size_t nc = (size_t)h->ncells;
+  CK(cudaMemsetAsync(h->fields + 7 * nc, 0, 2 * nc * 8, h->stream));
+  CK(by_width<ScatterF>(h, 1, h->fields + 7 * nc, h->fields + 8 * nc));
+  return MM_OK;
+}
+
+}  // namespace mmh
+
+extern "C" {
+
+mm_status mm_set_anchors(mm_handle* h, int enable) {
+  if (!h) return MM_ERR_INVALID;
+  if (h->batch || h->owner)
+    return fail(h, MM_ERR_UNSUPPORTED, "non-local anchors are not available in a batch");
+  if (h->rec.active)
+    return fail(h, MM_ERR_STATE, "non-local anchors are not differentiated: end the adjoint recording first");
+  DeviceGuard dg(h->device);
+  CK(cudaStreamSynchronize(h->stream));
+  const size_t nc = (size_t)h->ncells;
+  if (enable && !h->anc_off) {
+    size_t freeb = 0, totalb = 0;
+    CK(cudaMemGetInfo(&freeb, &totalb));
+    const size_t need = (size_t)h->g.ntheta * h->g.ns * sizeof(int2) + 2 * nc * 8 + 64;
+    if (need + (1 << 20) > freeb) return fail(h, MM_ERR_OOM, "anchor buffers do not fit");
+    CK(cudaMalloc((void**)&h->anc_off, (size_t)h->g.ntheta * h->g.ns * sizeof(int2)));
+    CK(cudaMalloc((void**)&h->anc_cacc, nc * 8));
+    CK(cudaMalloc((void**)&h->anc_fsc, nc * 8));
+    CK(cudaMalloc((void**)&h->anc_flags, 4 * sizeof(int)));
+    CK(cudaMemset(h->anc_cacc, 0, nc * 8));
+    CK(cudaMemset(h->anc_flags, 0, 4 * sizeof(int)));
+  }
+  if (enable) {
+    const cudaError_t e = by_width<PrepareF>(h);
+    if (e == cudaErrorInvalidValue)
+      return fail(h, MM_ERR_UNSUPPORTED, "ntheta too large for the anchor kernel's shared memory");
+    CK(e);
+  }
+  h->anchors = enable != 0;
+  // substep graphs were captured for the other kernels
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
+  mm_status st;
+  if (h->anchors && (st = anchor_table(h)) != MM_OK) {
+    h->anchors = false;
+    return st;
+  }
+  // C, the scale-down and Mf of the current state under the new rule
+  if (h->have_state) return h->anchors ? run_init_anchor(h) : run_init(h);
+  return MM_OK;
+}
+
+}  // extern "C"

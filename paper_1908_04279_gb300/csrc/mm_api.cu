@@ -41,6 +41,9 @@ mm_status free_all(mm_handle* h) {
   h->graphs.clear();
   if (h->diff_tab) cudaFree(h->diff_tab);
   if (h->local_n) cudaFree(h->local_n);
+  void* anc[4] = {h->anc_off, h->anc_cacc, h->anc_fsc, h->anc_flags};
+  for (void* p : anc)
+    if (p) cudaFree(p);
   void* ptrs[] = {h->mb,  h->psi[0], h->psi[1], h->nb[0],   h->nb[1],
                   h->mf,  h->c,      h->mtot,   h->u,       h->u64,    h->trig,
                   h->trig64, h->partial, h->fields, h->staging, h->prm, h->ucell};
@@ -115,6 +118,7 @@ template StepArgs<float> step_args<float>(mm_handle*, int);
 template StepArgs<double> step_args<double>(mm_handle*, int);
 
 cudaError_t launch_one(mm_handle* h, int parity, cudaStream_t s) {
+  if (h->anchors) return launch_anchor_substep(h, parity, s);
   if (h->prec == MM_FP64) {
     StepArgs<double> a = step_args<double>(h, parity);
     return h->V == 2 ? mm::launch_substep<double, 2>(a, h->grid_step, h->block, h->smem, h->tma, s)
@@ -292,6 +296,7 @@ mm_status get_array(mm_handle* h, double* dst, const void* src, size_t n, int on
 }
 
 mm_status run_init(mm_handle* h) {
+  if (h->anchors) return run_init_anchor(h);
   const double ds = h->g.L / h->g.ns, dth = 2.0 * kPi / h->g.ntheta;
   cudaError_t e;
   if (h->prec == MM_FP64)
@@ -329,6 +334,8 @@ mm_status run_moments(mm_handle* h) {
                                   h->g.L, dA, h->fields, h->partial, h->grid_mom, h->prm,
                                   h->stream);
   CK(e);
+  // with anchors the motor force of Eq. 10 acts in the anchor cells
+  if (h->anchors) return anchor_force(h);
   return MM_OK;
 }
 
@@ -531,6 +538,10 @@ mm_status mm_set_rates(mm_handle* h, const mm_rates* rates) {
   CK(cudaMemcpy(&h->prm->v_walk, v, sizeof v, cudaMemcpyHostToDevice));
   const double cw = walk_cw(h);
   CK(cudaMemcpy(&h->prm->cw, &cw, sizeof cw, cudaMemcpyHostToDevice));
+  if (h->anchors) {  // l/L moves the anchors: new table, C and Mf of the state under it
+    if ((st = anchor_table(h)) != MM_OK) return st;
+    if (h->have_state) return run_init_anchor(h);
+  }
   return MM_OK;
 }
 
@@ -1103,6 +1114,8 @@ mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_
     return MM_OK;
   }
   if (K < 0 || max_substeps < 1) return fail(h, MM_ERR_INVALID, "K >= 1 and max_substeps >= 1");
+  if (h->anchors)
+    return fail(h, MM_ERR_UNSUPPORTED, "the adjoint is not available with non-local anchors");
   if (K_inner < 1 || K_inner > K) return fail(h, MM_ERR_INVALID, "1 <= K_inner <= K");
   if (!h->have_state || !h->have_vel || !h->have_dt)
     return fail(h, MM_ERR_STATE, "set the state and the velocity before recording");

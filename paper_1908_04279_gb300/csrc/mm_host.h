@@ -124,6 +124,13 @@ struct mm_handle {
   double* staging = nullptr;
   double* diff_tab = nullptr;  // Crank-Nicolson factors of the three directions (mm_diffuse)
   int* local_n = nullptr;      // [cells] substeps per cell of mm_motor_local
+  // non-local motor anchors (mm_set_anchors)
+  bool anchors = false;
+  int anc_wpb = 4;              // warps per block of the anchor substep
+  void* anc_off = nullptr;      // [nth][ns] int2 anchor cell offsets
+  double* anc_cacc = nullptr;   // [cells] float64 accumulators of C
+  double* anc_fsc = nullptr;    // [cells] scale-down factors
+  int* anc_flags = nullptr;     // [4] scale-down flags
   size_t staging_n = 0;  // float64 values the staging buffer holds
   DevParams* prm = nullptr;
   int npartial = 0;
@@ -190,6 +197,13 @@ template <typename T>
 StepArgs<T> step_args(mm_handle* h, int parity);
 mm_status rec_push_substep(mm_handle* h);  // checkpoint bookkeeping of one recorded substep
 mm_status launch_substeps(mm_handle* h, int n);  // n substeps on the live state (graphs)
+mm_status run_init(mm_handle* h);  // n_b, C, the scale-down and Mf of the live state
+
+// Defined in mm_anchor.cu (non-local motor anchors).
+mm_status anchor_table(mm_handle* h);
+cudaError_t launch_anchor_substep(mm_handle* h, int parity, cudaStream_t s);
+mm_status run_init_anchor(mm_handle* h);
+mm_status anchor_force(mm_handle* h);
 
 // Defined in mm_batch_api.cu.
 mm_status batch_micro_step(mm_handle* h, int n);

@@ -90,6 +90,7 @@ PROTOTYPES = {
     "mm_sync": ([_H], C.c_int),
     "mm_diffuse": ([_H, C.c_double, C.c_double, C.c_double], C.c_int),
     "mm_motor_local": ([_H, C.c_double, _P, _P, C.c_int], C.c_int),
+    "mm_set_anchors": ([_H, C.c_int], C.c_int),
     "mm_debug_set": ([_H, C.c_uint, C.c_uint], C.c_int),
     "mm_get_launch_info": ([_H, C.POINTER(C.c_int), C.c_int], C.c_int),
     "mm_moments_static": ([C.POINTER(mm_grid), C.POINTER(mm_rates), _P, _P, _P, _P, _P, _P, _P],
@@ -258,6 +259,11 @@ class Simulation:
     def diffuse(self, D_t: float, D_r: float, dt: float):
         """One Crank-Nicolson step of filament diffusion (mm_diffuse)."""
         self._check(self.lib.mm_diffuse(self.h, float(D_t), float(D_r), float(dt)))
+
+    def set_anchors(self, enable: bool = True):
+        """Non-local motor anchors (mm_set_anchors): each configuration anchored
+        in the cell under its motor head, x + (l/L) s p with l/L = rates.ell."""
+        self._check(self.lib.mm_set_anchors(self.h, 1 if enable else 0))
 
     def motor_local(self, T: float, nsteps=None):
         """Motor kinetics over T with psi frozen and a local substep per cell

@@ -2,10 +2,11 @@
 
     python -m paper_1908_04279_gb300.profile_case [--case single|batch|adjoint|moments|local]
         [--grid NX NY NTHETA NS] [--precision fp32|fp64] [--substeps N]
-        [--repeat R] [--K K] [--members M] [--autotune]
+        [--repeat R] [--K K] [--members M] [--autotune] [--anchors ELL]
 
 single:  the perturbed isotropic state under a seeded 8-mode divergence-free
-         flow (amplitude 0.1); R calls of N substeps.
+         flow (amplitude 0.1); R calls of N substeps (with --anchors ELL: motor
+         anchors under the motor heads, l/L = ELL).
 batch:   the first M members of the detachment-rate ensemble (64 by default)
          as one batch; R calls of N batched substeps (after mm_batch_autotune
          with --autotune).
@@ -40,6 +41,7 @@ def main():
     ap.add_argument("--K", type=int, default=10)
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--anchors", type=float, default=None)
     args = ap.parse_args()
     B.build()
     stream = torch.cuda.current_stream()
@@ -72,7 +74,10 @@ def main():
         return
 
     g = Grid(*args.grid)
-    with mm.Simulation(g, Rates(), args.precision, stream=stream.cuda_stream) as sim:
+    rates = Rates() if args.anchors is None else Rates(ell=args.anchors)
+    with mm.Simulation(g, rates, args.precision, stream=stream.cuda_stream) as sim:
+        if args.anchors is not None:
+            sim.set_anchors(True)
         psi0 = psi_isotropic_perturbed(g, 0)
         u = random_divfree_flow(g, 1, 8, 0.1)
         sim.set_state(psi0)

@@ -1,0 +1,175 @@
+"""GPU parity of the non-local motor anchors (mm_set_anchors: every bound
+configuration anchored in the cell under its motor head, x + (l/L) s p) against
+the float64 oracle's anchor substep (or_substep_anchor), its set-up and its
+force field. Both sides start from the same seeded inputs and take the same dt
+(the oracle's). Relative L2 per field: <= 1e-12 in float64 (the coarse density
+is accumulated by float64 atomics, so only its rounding order differs),
+<= 1e-5 in float32.
+"""
+import numpy as np
+import pytest
+
+from paper_1908_04279_gb300.inputs import (Grid, Rates, SplitMix64, psi_isotropic_perturbed,
+                                           random_divfree_flow)
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp64": 1e-12, "fp32": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def mmod():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1908_04279_gb300 import build as B
+    B.build()
+    from paper_1908_04279_gb300 import mm
+    mm.load_library()
+    return mm
+
+
+def rel_l2(a, b):
+    a, b = np.asarray(a, dtype=np.float64), np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def seeded(g, seed, mb_scale=0.3, amp=0.3):
+    rng = SplitMix64(seed)
+    psi = psi_isotropic_perturbed(g, seed, amp=amp)
+    mb = mb_scale * rng.uniforms(g.ny * g.nx * g.ntheta * g.ns).reshape(g.ny, g.nx, g.ntheta, g.ns)
+    return psi, mb
+
+
+def run_both(mmod, O, g, r, psi, mb, mtot, u, nsub, precision, dt_scale=1.0):
+    st = O.make_state_anchor(g, r, psi, mb, mtot)
+    dt = O.dt(g, r, st, u) * dt_scale
+    with mmod.Simulation(g, r, precision) as sim:
+        sim.set_anchors(True)
+        sim.set_state(np.ascontiguousarray(psi), np.ascontiguousarray(mb),
+                      None if mtot is None else np.ascontiguousarray(mtot))
+        s0 = sim.get_state()
+        sim.set_velocity(np.ascontiguousarray(u))
+        sim.set_dt(dt)
+        sim.step(nsub)
+        gs = sim.get_state()
+        gf, _ = sim.moments()
+    init = O.make_state_anchor(g, r, psi, mb, mtot)
+    O.run_anchor(g, r, st, u, dt, nsub)
+    F = O.anchor_force(g, r, st)
+    return init, s0, st, gs, F, gf
+
+
+def check(init, s0, st, gs, F, gf, tol):
+    for k in ("mb", "mf", "c"):
+        assert rel_l2(s0[k], getattr(init, k)) <= tol, ("set-up", k, rel_l2(s0[k], getattr(init, k)))
+    for k in ("psi", "mb", "mf", "c"):
+        err = rel_l2(gs[k], getattr(st, k))
+        assert err <= tol, (k, err)
+    assert rel_l2(gf["Fx"], F[0]) <= tol and rel_l2(gf["Fy"], F[1]) <= tol
+
+
+@pytest.mark.parametrize("dims", [(8, 6, 16, 16), (5, 3, 7, 10), (4, 4, 5, 7), (3, 2, 40, 32),
+                                  (16, 12, 8, 24)])
+def test_fp64_anchor_matches_oracle(mmod, oracle_mod, dims):
+    g = Grid(*dims)
+    r = Rates(ell=0.3, k_on=2.0, glide=0.1)
+    psi, mb = seeded(g, 201 + sum(dims))
+    u = random_divfree_flow(g, 202, 4, 0.1)
+    out = run_both(mmod, oracle_mod, g, r, psi, mb, None, u, 12, "fp64")
+    check(*out, TOL["fp64"])
+
+
+def test_fp64_anchor_scale_down(mmod, oracle_mod):
+    """Few total motors and fast binding with a long step: the binding
+    overshoots and the per-anchor scale-down (and the fix-up of the rows and
+    their n_b) acts in some substeps."""
+    g = Grid(6, 5, 12, 16)
+    r = Rates(ell=0.25, k_on=80.0, k_off=0.2)
+    psi, mb = seeded(g, 211, mb_scale=0.05)
+    mtot = 0.03 + 0.1 * np.random.default_rng(212).random((g.ny, g.nx))
+    u = random_divfree_flow(g, 213, 3, 0.05)
+    init, s0, st, gs, F, gf = run_both(mmod, oracle_mod, g, r, psi, mb, mtot, u, 6, "fp64",
+                                       dt_scale=4.0)
+    check(init, s0, st, gs, F, gf, TOL["fp64"])
+    clipped = st.c == mtot
+    assert np.any(clipped) and not np.all(clipped)  # some anchors scaled down at the end
+
+
+def test_fp32_anchor_within_tolerance(mmod, oracle_mod):
+    g = Grid(12, 10, 16, 32)
+    r = Rates(ell=0.2, k_on=1.5)
+    psi, mb = seeded(g, 221)
+    u = random_divfree_flow(g, 222, 6, 0.1)
+    check(*run_both(mmod, oracle_mod, g, r, psi, mb, None, u, 20, "fp32"), TOL["fp32"])
+
+
+def test_anchor_zero_length_equals_local_path(mmod):
+    """With l/L = 0 every anchor is the filament's own cell: the anchor kernels
+    give the local kernel's result (to rounding order)."""
+    g = Grid(10, 8, 16, 16)
+    r = Rates(ell=0.0)
+    psi, mb = seeded(g, 231)
+    u = random_divfree_flow(g, 232, 4, 0.1)
+    res = []
+    for anchors in (False, True):
+        with mmod.Simulation(g, r, "fp64") as sim:
+            sim.set_anchors(anchors)
+            sim.set_state(psi, np.ascontiguousarray(mb))
+            sim.set_velocity(u)
+            sim.step(15)
+            res.append(sim.get_state())
+    for k in ("psi", "mb", "mf", "c"):
+        assert rel_l2(res[1][k], res[0][k]) <= 1e-13, k
+
+
+def test_anchor_toggle_and_rates(mmod, oracle_mod):
+    """Switching anchors on mid-run re-derives C and Mf of the current state;
+    a new l/L (mm_set_rates) moves the anchors; switching off returns to the
+    local rule."""
+    g = Grid(8, 8, 8, 16)
+    r = Rates(ell=0.3)
+    psi, mb = seeded(g, 241)
+    with mmod.Simulation(g, r, "fp64") as sim:
+        sim.set_state(psi, np.ascontiguousarray(mb))
+        sim.set_anchors(True)
+        a = sim.get_state()
+        st = oracle_mod.make_state_anchor(g, r, psi, mb)
+        for k in ("mb", "mf", "c"):
+            assert rel_l2(a[k], getattr(st, k)) <= 1e-12, k
+        r2 = Rates(ell=0.15)
+        sim.set_rates(r2)
+        b = sim.get_state()
+        st2 = oracle_mod.make_state_anchor(g, r2, psi, mb)
+        for k in ("mf", "c"):
+            assert rel_l2(b[k], getattr(st2, k)) <= 1e-12, k
+        sim.set_anchors(False)
+        c = sim.get_state()
+        st3 = oracle_mod.make_state(g, psi, mb)
+        for k in ("mf", "c"):
+            assert rel_l2(c[k], getattr(st3, k)) <= 1e-12, k
+
+
+def test_anchor_refusals(mmod):
+    g = Grid(6, 6, 8, 8)
+    with mmod.Simulation(g, Rates(ell=0.2), "fp64") as sim:
+        psi, mb = seeded(g, 251)
+        sim.set_state(psi, np.ascontiguousarray(mb))
+        sim.set_velocity(np.zeros((2, g.ny, g.nx)))
+        sim.set_anchors(True)
+        with pytest.raises(mmod.MMError) as e:
+            sim.set_checkpointing(2, 4)
+        assert e.value.status == 4
+        with pytest.raises(mmod.MMError) as e:
+            sim.motor_local(0.1)
+        assert e.value.status == 4
+        sim.set_anchors(False)
+        sim.set_checkpointing(2, 4)
+        with pytest.raises(mmod.MMError) as e:
+            sim.set_anchors(True)
+        assert e.value.status == 7
+    with mmod.Batch([g, g], [Rates(), Rates()], "fp64") as b:
+        with pytest.raises(mmod.MMError) as e:
+            b.members[0].set_anchors(True)
+        assert e.value.status == 4

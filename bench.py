@@ -511,6 +511,37 @@ def run_ours(args):
                 "global_substeps_ms_same_interval": e0.elapsed_time(e1),
                 "cell_updates_per_call": updates}
 
+    def anchors_run(wname, substeps, ell=0.05):
+        """Non-local motor anchors (mm_set_anchors, l/L = ell: the filament
+        spans ell of the domain, 6.4 cells at 128^2): a captured graph of
+        `substeps` anchor substeps (three launches each: the substep, the
+        per-anchor close, the scale-down fix-up) after a warm-up graph."""
+        wl = WORKLOADS[wname]
+        gl = wl["grid"]
+        sim = mm.Simulation(gl, Rates(ell=ell), "fp32", stream=stream.cuda_stream)
+        sim.set_anchors(True)
+        sim.set_state(psi_isotropic_perturbed(gl, wl["seed"]))
+        sim.set_velocity(torch.tensor(workload_velocity(wname, 0), device=dev))
+        sim.step(substeps)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(substeps)
+        e1.record(stream)
+        e1.synchronize()
+        sim.sync()
+        sim.close()
+        ms = e0.elapsed_time(e1) / substeps
+        algo = algorithmic_bytes_per_launch(gl, 4)
+        peak_, src_ = read_peaks()
+        return {"workload": f"{wname} ({gl.nx}x{gl.ny} x {gl.ntheta} x {gl.ns}, fp32), l/L = {ell}",
+                "value": world * gl.micro_cells / (ms * 1e-3), "unit": UNIT,
+                "ms_per_substep": ms, "algorithmic_bytes_per_substep": algo,
+                "roofline": {"bound": "hbm", "achieved": algo / (ms * 1e-3) / 1e9, "peak": peak_,
+                             "unit": "GB/s", "frac": algo / (ms * 1e-3) / 1e9 / peak_,
+                             "kernel": "k_substep_anchor + k_anchor_close + k_anchor_fix (float32)",
+                             "peak_source": src_, "traffic": None}}
+
     def ensemble_run(steps):
         """ensemble64: 64 members with uneven grids (N in {32..128}, Ntheta and
         Ns in {16, 32}), k_off log-uniform in [0.05, 5], v_walk in [0.5, 2];
@@ -571,6 +602,8 @@ def run_ours(args):
     ens = ensemble_run(max(2, min(args.steps, 3)))
     large_adj = large_adjoint_run()
     diff = diffusion_run()
+    anchors = {"precision128": anchors_run("precision128", 50),
+               "large512": anchors_run("large512", 5)}
     local = {"precision128": local_run("precision128"),
              "large512": local_run("large512", reps=3)}
     for v in local.values():
@@ -626,6 +659,7 @@ def run_ours(args):
                 large_adj, workload="large512, 2000 substeps, float32, mean active stress vs k_off"),
             "diffusion": diff,
             "local": local,
+            "anchors": anchors,
             "ensemble": dict(ens, roofline={"bound": "hbm", "peak": peak, "unit": "GB/s",
                                             "achieved": ens["achieved_gbs"],
                                             "frac": ens["achieved_gbs"] / peak,

@@ -136,15 +136,52 @@ struct ColsSmem {
 // cell's accumulated adjoints of u and of its velocity gradient (acc_old: the
 // accumulator lane j < 6 holds, read earlier); stores lam_C and f of the cell.
 // s_lt: nth values of shared memory for the cell's lam_psi_total.
+// The scalars of the psi part in the state precision. In float32 the eight
+// float64 values are converted by one instruction for the warp (lane q
+// converts value q, then shuffles): conversions from float64 run on the narrow
+// float64 pipe, and the cell loop needs them once per launch, not per cell.
+template <typename T>
+struct PsiAdjConst {
+  T dt, glide, vsp, dtv, dtw, dtt, ds, dth;
+};
+template <typename T>
+__device__ __forceinline__ PsiAdjConst<T> psi_adj_const(const AdjArgs<T>& a, int lane) {
+  PsiAdjConst<T> c;
+  if constexpr (sizeof(T) == 4) {
+    const double v = lane == 0 ? *a.dt : lane == 1 ? a.glide : lane == 2 ? a.v_sp
+                   : lane == 3 ? a.inv_dx : lane == 4 ? a.inv_dy : lane == 5 ? a.inv_dth
+                   : lane == 6 ? a.ds : a.dth;
+    const float x = (float)v;
+    c.dt = __shfl_sync(0xffffffffu, x, 0);
+    c.glide = __shfl_sync(0xffffffffu, x, 1);
+    c.vsp = __shfl_sync(0xffffffffu, x, 2);
+    c.dtv = c.dt * __shfl_sync(0xffffffffu, x, 3);
+    c.dtw = c.dt * __shfl_sync(0xffffffffu, x, 4);
+    c.dtt = c.dt * __shfl_sync(0xffffffffu, x, 5);
+    c.ds = __shfl_sync(0xffffffffu, x, 6);
+    c.dth = __shfl_sync(0xffffffffu, x, 7);
+  } else {
+    c.dt = *a.dt;
+    c.glide = a.glide;
+    c.vsp = a.v_sp;
+    c.dtv = c.dt * a.inv_dx;
+    c.dtw = c.dt * a.inv_dy;
+    c.dtt = c.dt * a.inv_dth;
+    c.ds = a.ds;
+    c.dth = a.dth;
+  }
+  return c;
+}
+
 template <typename T, class Cols>
-__device__ __forceinline__ void psi_adj_cell(const AdjArgs<T>& a, const Cols& C, int cell,
-                                             const T (&lamC)[5], const T (&fsc)[5], T* s_lt,
-                                             double acc_old, int lane) {
+__device__ __forceinline__ void psi_adj_cell(const AdjArgs<T>& a, const PsiAdjConst<T>& pc0,
+                                             const Cols& C, int cell, const T (&lamC)[5],
+                                             const T (&fsc)[5], T* s_lt, double acc_old,
+                                             int lane) {
   const int nth = a.nth, nc = (int)a.ncells;
-  const T dt = (T)*a.dt;
-  const T glide = (T)a.glide, vsp = (T)a.v_sp;
-  const T dtv = dt * (T)a.inv_dx, dtw = dt * (T)a.inv_dy, dtt = dt * (T)a.inv_dth;
-  const T ds = (T)a.ds, dth = (T)a.dth;
+  const T glide = pc0.glide, vsp = pc0.vsp;
+  const T dtv = pc0.dtv, dtw = pc0.dtw, dtt = pc0.dtt;
+  const T ds = pc0.ds, dth = pc0.dth;
   const T* cosk = a.trig;
   const T* sink = a.trig + nth;
   const T* cosf = a.trig + 2 * nth;
@@ -235,6 +272,7 @@ __global__ void __launch_bounds__(128) k_adj_psi(const AdjArgs<T> a) {
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
   const int W = gridDim.x * (blockDim.x >> 5);
   const int nc = (int)a.ncells;
+  const PsiAdjConst<T> pc0 = psi_adj_const(a, lane);
   for (int cell = gw; cell < nc; cell += W) {
     ColsGlobal<T> C;
     C.a = &a;
@@ -248,7 +286,7 @@ __global__ void __launch_bounds__(128) k_adj_psi(const AdjArgs<T> a) {
     T lamC[5], fsc[5];
 #pragma unroll
     for (int q = 0; q < 5; ++q) cell_lamc(a, C.nbr[q], lamC[q], fsc[q]);
-    psi_adj_cell(a, C, cell, lamC, fsc, s_lt, acc_old, lane);
+    psi_adj_cell(a, pc0, C, cell, lamC, fsc, s_lt, acc_old, lane);
   }
 }
 
@@ -280,6 +318,7 @@ __global__ void __launch_bounds__(128, adj_psi_min_blocks<T>()) k_adj_psi_ring(c
   const int nc = (int)a.ncells;
   const uint32_t wait_limit = a.prm->wait_limit;
   const bool wait_never = (a.prm->debug_flags & 1u) != 0;
+  const PsiAdjConst<T> pc0 = psi_adj_const(a, lane);
   const uint32_t colb = (uint32_t)(nth * sizeof(T));
   const uint32_t ub = (uint32_t)(12 * sizeof(T));
   auto issue = [&](int cell, int sidx) {
@@ -328,7 +367,7 @@ __global__ void __launch_bounds__(128, adj_psi_min_blocks<T>()) k_adj_psi_ring(c
     }
     par[sidx] ^= 1u;
     ColsSmem<T> C{stage[sidx], nth};
-    psi_adj_cell(a, C, cell, lamC, fsc, s_lt, acc_old, lane);
+    psi_adj_cell(a, pc0, C, cell, lamC, fsc, s_lt, acc_old, lane);
     sidx ^= 1;
   }
   if (timed_out) {
@@ -876,6 +915,24 @@ __global__ void k_adj_seed(int kind, const double* coef, const T* psi, const T* 
   const int lane = threadIdx.x & 31;
   const long long gw = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
   const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+  if (kind == 1 || (kind == 0 && !dnb && !dm1)) {
+    // no seed on the rows (lam_Mb was cleared by the caller, so D = 0): lanes
+    // over theta for lam_psi
+    for (long long cell = gw; cell < ncells; cell += W) {
+      for (int k = lane; k < nth; k += 32) {
+        const size_t r = (size_t)cell * nth + k;
+        const double lp = kind == 1 ? coef[0] + coef[1] * (double)trig[k] +
+                                          coef[2] * (double)trig[nth + k]
+                                    : (dpsi ? dpsi[r] : 0.0);
+        lpsi[r] = (T)lp;
+      }
+      if (lane == 0) {
+        lmf[cell] = (T)((kind == 0 && dmf) ? dmf[cell] : 0.0);
+        D[cell] = T(0);
+      }
+    }
+    return;
+  }
   for (long long cell = gw; cell < ncells; cell += W) {
     double dsum = 0.0;
     // one row at a time, the s-nodes across the lanes
@@ -1077,6 +1134,11 @@ cudaError_t launch_adj_seed(int kind, const double* coef, const T* psi, const T*
                             int nth, int ns, double ds, double L, const T* trig, cudaStream_t s) {
   long long g = (ncells + 3) / 4;
   if (g > 152 * 8) g = 152 * 8;
+  if (kind == 1 || (kind == 0 && !dnb && !dm1)) {
+    // a seed without motor rows: lam_Mb = 0 by a fill, the kernel skips the rows
+    const cudaError_t e = cudaMemsetAsync(lmb, 0, (size_t)ncells * nth * ns * sizeof(T), s);
+    if (e != cudaSuccess) return e;
+  }
   k_adj_seed<T><<<(int)g, 128, 0, s>>>(kind, coef, psi, mb, dpsi, dnb, dm1, dmf, lpsi, lmb, lmf,
                                        D, ncells, nth, ns, ds, L, trig);
   return cudaGetLastError();

@@ -22,6 +22,12 @@
 #include "mm_cell.cuh"
 #include "mm_host.h"
 
+// Resident 4-warp blocks per SM the anchor substep's registers are sized for
+// (more blocks force spills and measured slower).
+#ifndef MM_ANCHOR_MIN_BLOCKS
+#define MM_ANCHOR_MIN_BLOCKS 4
+#endif
+
 namespace mm {
 
 // Anchor data of one instance: offsets [nth][ns] (reduced into [0, nx) and
@@ -33,6 +39,10 @@ struct AnchorArgs {
   double* fsc;   // [cells] scale-down factor of each anchor cell
   int* flags;    // [3]: 0, 1 alternate with the substep parity; 2 for the set-up
   int flag;      // the flag this launch sets or reads
+  // The window of anchor cells around a filament cell: offsets wox..wox+wx-1,
+  // woy..woy+wy-1; widx [nth][ns] is each node's index in it (wx * wy entries).
+  const int* widx;
+  int wox, woy, wx, wy;
 };
 
 __device__ __forceinline__ int anchor_cell(int ix, int iy, int2 o, int nx, int ny) {
@@ -62,20 +72,51 @@ __device__ __forceinline__ void scatter_runs(double* acc, const int (&anc)[V], c
   atomicAdd(acc + cur, (double)s);
 }
 
-// Per-warp shared memory: psi and n_b columns of the cell and its four
-// neighbours ([5][nth] each) and psi^{n+1} of the cell.
-__host__ __device__ inline size_t anchor_warp_smem(int nth, int tsz) {
-  return ((size_t)11 * nth * tsz + 15) & ~(size_t)15;
+// The same into a shared-memory window accumulator in the state precision.
+template <typename T, int V>
+__device__ __forceinline__ void scatter_runs_smem(T* acc, const int (&widx)[V], const T (&M)[V],
+                                                  T w) {
+  int cur = widx[0];
+  T s = w * M[0];
+#pragma unroll
+  for (int v = 1; v < V; ++v) {
+    if (widx[v] == cur) {
+      s += w * M[v];
+    } else {
+      atomicAdd(acc + cur, s);
+      cur = widx[v];
+      s = w * M[v];
+    }
+  }
+  atomicAdd(acc + cur, s);
 }
 
-template <typename T, int V, bool MASSCORR>
-__global__ void __launch_bounds__(128) k_substep_anchor(const StepArgs<T> a, const AnchorArgs<T> x) {
+// Per-warp shared memory: psi and n_b columns of the cell and its four
+// neighbours ([5][nth] each) and psi^{n+1} of the cell.
+__host__ __device__ inline size_t anchor_warp_smem(int nth, int tsz, int W = 0) {
+  const size_t cols = ((size_t)11 * nth * tsz + 15) & ~(size_t)15;
+  // the window: Mf and the coarse-density accumulator (state precision) and
+  // the global cell of every entry
+  return cols + (((size_t)W * (2 * tsz + 4) + 15) & ~(size_t)15);
+}
+
+// WIN: the anchors of a cell's nodes lie in a small window of cells around it;
+// the window's free motors are gathered into shared memory when the cell
+// starts and the rows' contributions to C are summed there (shared-memory
+// atomics), then added to the global accumulators once per window entry.
+template <typename T, int V, bool MASSCORR, bool WIN>
+__global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(const StepArgs<T> a, const AnchorArgs<T> x) {
   extern __shared__ __align__(16) unsigned char asm_raw[];
   const int nth = a.nth, ns = a.ns, seg = a.seg, nx = a.nx, ny = a.ny;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  T* psi5 = reinterpret_cast<T*>(asm_raw + (size_t)wib * anchor_warp_smem(nth, sizeof(T)));
+  const int Wn = WIN ? x.wx * x.wy : 0;
+  unsigned char* wbase = asm_raw + (size_t)wib * anchor_warp_smem(nth, sizeof(T), Wn);
+  T* psi5 = reinterpret_cast<T*>(wbase);
   T* nb5 = psi5 + 5 * nth;
   T* pnew = nb5 + 5 * nth;
+  T* wmf = reinterpret_cast<T*>(wbase + (((size_t)11 * nth * sizeof(T) + 15) & ~(size_t)15));
+  T* wacc = wmf + Wn;
+  int* wcell = reinterpret_cast<int*>(wacc + Wn);
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
   const int W = gridDim.x * (blockDim.x >> 5);
   const int nc = (int)a.ncells;
@@ -101,6 +142,18 @@ __global__ void __launch_bounds__(128) k_substep_anchor(const StepArgs<T> a, con
         psi5[q * nth + k] = a.psi_in[(size_t)nbr[q] * nth + k];
         nb5[q * nth + k] = a.nb_in[(size_t)nbr[q] * nth + k];
       }
+    if (WIN) {
+      for (int w = lane; w < Wn; w += 32) {
+        const int wyi = w / x.wx, wxi = w - wyi * x.wx;
+        int gx = (ix + x.wox + wxi) % nx, gy = (iy + x.woy + wyi) % ny;
+        if (gx < 0) gx += nx;
+        if (gy < 0) gy += ny;
+        const int gc = gy * nx + gx;
+        wcell[w] = gc;
+        wmf[w] = a.mf_in[gc];
+        wacc[w] = T(0);
+      }
+    }
     __syncwarp();
     // Eq. 1 first: psi^{n+1} of the cell weights the scatter of its rows
     const CellVel<T> uv = load_cell_vel(a.ucell, cell);
@@ -109,7 +162,20 @@ __global__ void __launch_bounds__(128) k_substep_anchor(const StepArgs<T> a, con
     two_sum_acc(mass_hi, mass_lo, cell_mass);
     __syncwarp();
     for (int k = lane; k < nth; k += 32) a.psi_out[(size_t)cell * nth + k] = pnew[k];
-    // Eq. 4 on every row, binding against the anchors' free motors
+    // Eq. 4 on every row, binding against the anchors' free motors; the next
+    // pass's row and anchor indices are loaded while the current one is
+    // computed
+    Pack<T, V> qn;
+    Pack<int, V> wn;
+    auto load_pass = [&](int r0) {
+      const int k = r0 + lg.rslot;
+      if (k < nth && lg.lane_ok) {
+        qn = *reinterpret_cast<const Pack<T, V>*>(a.mb_in + ((size_t)cell * nth + k) * ns +
+                                                  lg.sl * V);
+        if (WIN) wn = *reinterpret_cast<const Pack<int, V>*>(x.widx + (size_t)k * ns + lg.sl * V);
+      }
+    };
+    load_pass(0);
     for (int r0 = 0; r0 < nth; r0 += lg.rpp) {
       const int k = r0 + lg.rslot;
       const bool row_ok = k < nth, act = row_ok && lg.lane_ok;
@@ -117,13 +183,23 @@ __global__ void __launch_bounds__(128) k_substep_anchor(const StepArgs<T> a, con
       T M[V], D[V], Ms[V], mfv[V];
       int anc[V];
       if (act) {
-        const Pack<T, V> q = *reinterpret_cast<const Pack<T, V>*>(a.mb_in + roff);
-        const int2* o = x.off + (size_t)k * ns + lg.sl * V;
+        const Pack<T, V> q = qn;
+        if (WIN) {
+          const Pack<int, V> wi = wn;
 #pragma unroll
-        for (int v = 0; v < V; ++v) {
-          M[v] = q.v[v];
-          anc[v] = anchor_cell(ix, iy, o[v], nx, ny);
-          mfv[v] = a.mf_in[anc[v]];
+          for (int v = 0; v < V; ++v) {
+            M[v] = q.v[v];
+            anc[v] = wi.v[v];
+            mfv[v] = wmf[anc[v]];
+          }
+        } else {
+          const int2* o = x.off + (size_t)k * ns + lg.sl * V;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            M[v] = q.v[v];
+            anc[v] = anchor_cell(ix, iy, o[v], nx, ny);
+            mfv[v] = a.mf_in[anc[v]];
+          }
         }
       } else {
 #pragma unroll
@@ -133,6 +209,7 @@ __global__ void __launch_bounds__(128) k_substep_anchor(const StepArgs<T> a, con
           anc[v] = cell;
         }
       }
+      if (r0 + lg.rpp < nth) load_pass(r0 + lg.rpp);
       walk_dflux<T, V>(M, D, lg.first, lg.last, seg);
 #pragma unroll
       for (int v = 0; v < V; ++v) Ms[v] = fma_t(c1, D[v], fma_t(c2, M[v], hk * mfv[v]));
@@ -148,7 +225,10 @@ __global__ void __launch_bounds__(128) k_substep_anchor(const StepArgs<T> a, con
 #pragma unroll
         for (int v = 0; v < V; ++v) q.v[v] = M[v];
         *reinterpret_cast<Pack<T, V>*>(a.mb_out + roff) = q;
-        scatter_runs<T, V>(x.cacc, anc, M, pnew[k] * dsdth);
+        if (WIN)
+          scatter_runs_smem<T, V>(wacc, anc, M, pnew[k] * dsdth);
+        else
+          scatter_runs<T, V>(x.cacc, anc, M, pnew[k] * dsdth);
       } else {
         snb = T(0);
       }
@@ -156,6 +236,13 @@ __global__ void __launch_bounds__(128) k_substep_anchor(const StepArgs<T> a, con
       if (lg.first && row_ok) a.nb_out[(size_t)cell * nth + k] = snb * sc.ds;
     }
     __syncwarp();
+    if (WIN) {  // the window's sums into the global accumulators
+      for (int w = lane; w < Wn; w += 32) {
+        const T v = wacc[w];
+        if (v != T(0)) atomicAdd(x.cacc + wcell[w], (double)v);
+      }
+      __syncwarp();
+    }
   }
   // sum psi^{n+1} as in k_substep: per warp, per block, then the last block
   __shared__ double s_red[32];
@@ -306,6 +393,11 @@ mm::AnchorArgs<T> anchor_args(mm_handle* h, int flag) {
   x.fsc = h->anc_fsc;
   x.flags = h->anc_flags;
   x.flag = flag;
+  x.widx = h->anc_widx;
+  x.wox = h->anc_win[0];
+  x.woy = h->anc_win[1];
+  x.wx = h->anc_win[2];
+  x.wy = h->anc_win[3];
   return x;
 }
 
@@ -319,15 +411,20 @@ int blocks_for(long long work, int per_block, int cap) {
 // warp) and the kernels' shared-memory limit.
 template <typename T, int V>
 cudaError_t anchor_prepare_t(mm_handle* h) {
-  const size_t per_warp = mm::anchor_warp_smem(h->g.ntheta, sizeof(T));
+  const int W = h->anc_win[2] * h->anc_win[3];
+  const size_t per_warp = mm::anchor_warp_smem(h->g.ntheta, sizeof(T), W);
   h->anc_wpb = (int)std::min<size_t>(4, kSmemBudget / per_warp);
   if (h->anc_wpb < 1) return cudaErrorInvalidValue;
   const int smem = (int)(h->anc_wpb * per_warp);
-  cudaError_t e = cudaFuncSetAttribute(mm::k_substep_anchor<T, V, true>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(mm::k_substep_anchor<T, V, false>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const void* fns[4] = {(const void*)mm::k_substep_anchor<T, V, true, true>,
+                        (const void*)mm::k_substep_anchor<T, V, false, true>,
+                        (const void*)mm::k_substep_anchor<T, V, true, false>,
+                        (const void*)mm::k_substep_anchor<T, V, false, false>};
+  for (const void* f : fns) {
+    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 template <typename T, int V>
@@ -335,12 +432,19 @@ cudaError_t anchor_substep_t(mm_handle* h, int parity, cudaStream_t s) {
   const StepArgs<T> a = step_args<T>(h, parity);
   const mm::AnchorArgs<T> x = anchor_args<T>(h, parity);
   const int wpb = h->anc_wpb;
-  const size_t smem = wpb * mm::anchor_warp_smem(h->g.ntheta, sizeof(T));
+  const bool win = x.wx > 0;
+  const size_t smem = wpb * mm::anchor_warp_smem(h->g.ntheta, sizeof(T), x.wx * x.wy);
   const int grid = blocks_for(h->ncells, wpb, 8 * h->sms);
-  if (a.mass_correct)
-    mm::k_substep_anchor<T, V, true><<<grid, 32 * wpb, smem, s>>>(a, x);
-  else
-    mm::k_substep_anchor<T, V, false><<<grid, 32 * wpb, smem, s>>>(a, x);
+  if (win) {
+    if (a.mass_correct)
+      mm::k_substep_anchor<T, V, true, true><<<grid, 32 * wpb, smem, s>>>(a, x);
+    else
+      mm::k_substep_anchor<T, V, false, true><<<grid, 32 * wpb, smem, s>>>(a, x);
+  } else if (a.mass_correct) {
+    mm::k_substep_anchor<T, V, true, false><<<grid, 32 * wpb, smem, s>>>(a, x);
+  } else {
+    mm::k_substep_anchor<T, V, false, false><<<grid, 32 * wpb, smem, s>>>(a, x);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   mm::k_anchor_close<T><<<blocks_for(h->ncells, 256, 8 * h->sms), 256, 0, s>>>(
@@ -405,7 +509,8 @@ namespace mmh {
 mm_status anchor_table(mm_handle* h) {
   const int nth = h->g.ntheta, ns = h->g.ns, nx = h->g.nx, ny = h->g.ny;
   const double dx = 1.0 / nx, dy = 1.0 / ny, dth = 2.0 * kPi / nth;
-  std::vector<int2> off((size_t)nth * ns);
+  std::vector<int2> off((size_t)nth * ns), raw((size_t)nth * ns);
+  long long xmin = 0, xmax = 0, ymin = 0, ymax = 0;
   for (int k = 0; k < nth; ++k) {
     const double th = k * dth, ct = std::cos(th), st = std::sin(th);
     for (int j = 0; j < ns; ++j) {
@@ -413,14 +518,38 @@ mm_status anchor_table(mm_handle* h) {
       const double qx = std::floor(disp * ct / dx + 0.5), qy = std::floor(disp * st / dy + 0.5);
       if (!(std::fabs(qx) < 1e9 && std::fabs(qy) < 1e9))
         return fail(h, MM_ERR_UNSUPPORTED, "anchor offsets out of range");
-      long long ox = (long long)qx % nx, oy = (long long)qy % ny;
+      const long long rx = (long long)qx, ry = (long long)qy;
+      if (k == 0 && j == 0) xmin = xmax = rx, ymin = ymax = ry;
+      xmin = std::min(xmin, rx);
+      xmax = std::max(xmax, rx);
+      ymin = std::min(ymin, ry);
+      ymax = std::max(ymax, ry);
+      raw[(size_t)k * ns + j] = make_int2((int)rx, (int)ry);
+      long long ox = rx % nx, oy = ry % ny;
       if (ox < 0) ox += nx;
       if (oy < 0) oy += ny;
       off[(size_t)k * ns + j] = make_int2((int)ox, (int)oy);
     }
   }
+  // the window of anchor cells around a filament cell, when it is small
+  const long long wx = xmax - xmin + 1, wy = ymax - ymin + 1;
+  std::vector<int> widx((size_t)nth * ns);
+  h->anc_win[0] = h->anc_win[1] = h->anc_win[2] = h->anc_win[3] = 0;
+  if (wx * wy <= kAnchorWindowMax) {
+    for (size_t q = 0; q < widx.size(); ++q)
+      widx[q] = (int)((raw[q].y - ymin) * wx + (raw[q].x - xmin));
+    h->anc_win[0] = (int)xmin;
+    h->anc_win[1] = (int)ymin;
+    h->anc_win[2] = (int)wx;
+    h->anc_win[3] = (int)wy;
+  }
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(h->anc_off, off.data(), off.size() * sizeof(int2), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->anc_widx, widx.data(), widx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  const cudaError_t e = by_width<PrepareF>(h);
+  if (e == cudaErrorInvalidValue)
+    return fail(h, MM_ERR_UNSUPPORTED, "ntheta too large for the anchor kernel's shared memory");
+  CK(e);
   return MM_OK;
 }
 
@@ -462,27 +591,19 @@ mm_status mm_set_anchors(mm_handle* h, int enable) {
     const size_t need = (size_t)h->g.ntheta * h->g.ns * sizeof(int2) + 2 * nc * 8 + 64;
     if (need + (1 << 20) > freeb) return fail(h, MM_ERR_OOM, "anchor buffers do not fit");
     CK(cudaMalloc((void**)&h->anc_off, (size_t)h->g.ntheta * h->g.ns * sizeof(int2)));
+    CK(cudaMalloc((void**)&h->anc_widx, (size_t)h->g.ntheta * h->g.ns * sizeof(int)));
     CK(cudaMalloc((void**)&h->anc_cacc, nc * 8));
     CK(cudaMalloc((void**)&h->anc_fsc, nc * 8));
     CK(cudaMalloc((void**)&h->anc_flags, 4 * sizeof(int)));
     CK(cudaMemset(h->anc_cacc, 0, nc * 8));
     CK(cudaMemset(h->anc_flags, 0, 4 * sizeof(int)));
   }
-  if (enable) {
-    const cudaError_t e = by_width<PrepareF>(h);
-    if (e == cudaErrorInvalidValue)
-      return fail(h, MM_ERR_UNSUPPORTED, "ntheta too large for the anchor kernel's shared memory");
-    CK(e);
-  }
+  mm_status st;
+  if (enable && (st = anchor_table(h)) != MM_OK) return st;
   h->anchors = enable != 0;
   // substep graphs were captured for the other kernels
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
-  mm_status st;
-  if (h->anchors && (st = anchor_table(h)) != MM_OK) {
-    h->anchors = false;
-    return st;
-  }
   // C, the scale-down and Mf of the current state under the new rule
   if (h->have_state) return h->anchors ? run_init_anchor(h) : run_init(h);
   return MM_OK;

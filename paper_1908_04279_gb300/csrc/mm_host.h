@@ -128,6 +128,8 @@ struct mm_handle {
   bool anchors = false;
   int anc_wpb = 4;              // warps per block of the anchor substep
   void* anc_off = nullptr;      // [nth][ns] int2 anchor cell offsets
+  int* anc_widx = nullptr;      // [nth][ns] index of each node's anchor in the window
+  int anc_win[4] = {0, 0, 0, 0};  // window: first x and y offset, width, height (0: none)
   double* anc_cacc = nullptr;   // [cells] float64 accumulators of C
   double* anc_fsc = nullptr;    // [cells] scale-down factors
   int* anc_flags = nullptr;     // [4] scale-down flags
@@ -188,6 +190,7 @@ constexpr int kChunkBytes = 4096;
 constexpr int kWarpInflightBytes = 8192;
 constexpr int kMaxWarpsPerBlock = 4;
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory per block at most
+constexpr long long kAnchorWindowMax = 1024;   // anchor window entries kept in shared memory
 
 // Defined in mm_api.cu.
 mm_status check_rates(const mm_rates* r, mm_handle* h);

@@ -81,6 +81,20 @@ def test_fp64_anchor_matches_oracle(mmod, oracle_mod, dims):
     check(*out, TOL["fp64"])
 
 
+def test_fp64_anchor_long_filaments(mmod, oracle_mod):
+    """Filaments longer than the grid (l/L = 1.5 on 40 x 36 cells): the anchors
+    of a cell spread over more cells than the shared-memory window holds, so the
+    kernel gathers and scatters in global memory; and offsets wrap the grid."""
+    g = Grid(40, 36, 8, 16)
+    r = Rates(ell=1.5, k_on=1.2)
+    psi, mb = seeded(g, 205)
+    u = random_divfree_flow(g, 206, 4, 0.1)
+    ox, oy = oracle_mod.anchor_offsets(g, r)
+    assert (ox.max() - ox.min() + 1) * (oy.max() - oy.min() + 1) > 1024
+    assert ox.max() > g.nx // 2 and ox.min() < -(g.nx // 2)
+    check(*run_both(mmod, oracle_mod, g, r, psi, mb, None, u, 4, "fp64"), TOL["fp64"])
+
+
 def test_fp64_anchor_scale_down(mmod, oracle_mod):
     """Few total motors and fast binding with a long step: the binding
     overshoots and the per-anchor scale-down (and the fix-up of the rows and

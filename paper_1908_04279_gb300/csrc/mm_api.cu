@@ -620,15 +620,15 @@ mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
   const double dth = 2.0 * kPi / h->g.ntheta;
   cudaError_t e;
   if (h->prec == MM_FP64)
-    e = mm::launch_dt_max<double>((const double*)h->psi[h->parity], (const double*)h->nb[h->parity], h->u64,
-                                  h->trig64, h->ncells, h->g.nx, h->g.ny, h->g.ntheta,
-                                  (double)h->g.nx, (double)h->g.ny, 1.0 / dth, dth, h->r.glide,
-                                  h->r.v_sp, h->prm, h->stream);
+    e = mm::launch_dt_max<double>((const double*)h->psi[h->parity], (const double*)h->nb[h->parity],
+                                  (const double*)h->u, (const double*)h->trig, h->ncells, h->g.nx,
+                                  h->g.ny, h->g.ntheta, (double)h->g.nx, (double)h->g.ny, 1.0 / dth,
+                                  dth, h->r.glide, h->r.v_sp, h->prm, h->stream);
   else
-    e = mm::launch_dt_max<float>((const float*)h->psi[h->parity], (const float*)h->nb[h->parity], h->u64,
-                                 h->trig64, h->ncells, h->g.nx, h->g.ny, h->g.ntheta,
-                                 (double)h->g.nx, (double)h->g.ny, 1.0 / dth, dth, h->r.glide,
-                                 h->r.v_sp, h->prm, h->stream);
+    e = mm::launch_dt_max<float>((const float*)h->psi[h->parity], (const float*)h->nb[h->parity],
+                                 (const float*)h->u, (const float*)h->trig, h->ncells, h->g.nx,
+                                 h->g.ny, h->g.ntheta, (double)h->g.nx, (double)h->g.ny, 1.0 / dth,
+                                 dth, h->r.glide, h->r.v_sp, h->prm, h->stream);
   CK(e);
   CK(mm::launch_dt_finalize(h->prm, h->g.L / h->g.ns, h->g.L, h->r.cfl, h->stream));
   h->have_vel = true;

@@ -8,11 +8,6 @@ namespace mm {
 
 namespace {
 
-__device__ __forceinline__ double warp_max(double x) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
-  return x;
-}
 
 // Sum over the block of one value per thread; result valid in thread 0.
 // `red` holds at least 32 doubles. Ends with a barrier so `red` can be reused.
@@ -88,44 +83,59 @@ __device__ __forceinline__ void atomic_max_nonneg(double* addr, double v) {
 }
 
 // Maxima of the adaptive-substep rule: max(|ax|/dx + |ay|/dy),
-// max |omega(theta_{k+1/2})| / dtheta, and max_cell sum_k psi dtheta.
+// max |omega(theta_{k+1/2})| / dtheta, and max_cell sum_k psi dtheta. One warp
+// per cell, lanes over theta, in the state precision (float64 in the float64
+// form, whose dt must agree with a float64 evaluation; float32 in the float32
+// form, whose state is float32 anyway); the maxima are exact.
 template <typename T>
-__global__ void k_dt_max(const T* psi, const T* nb, const double* u64, const double* trig,
-                         long long ncells, int nx, int ny, int nth, double inv_dx, double inv_dy,
-                         double inv_dth, double dth, double glide, double vsp, DevParams* prm) {
-  __shared__ double red[32];
-  const double psi_scale = prm->psi_scale;
-  double adv = 0.0, rot = 0.0, rhomax = 0.0;
-  const double* ux = u64;
-  const double* uy = u64 + ncells;
-  for (long long cell = blockIdx.x; cell < ncells; cell += gridDim.x) {
+__device__ __forceinline__ T warp_max_t(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = tmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+template <typename T>
+__global__ void k_dt_max(const T* psi, const T* nb, const T* u, const T* trig, long long ncells,
+                         int nx, int ny, int nth, double inv_dx64, double inv_dy64,
+                         double inv_dth64, double dth64, double glide64, double vsp64,
+                         DevParams* prm) {
+  const int lane = threadIdx.x & 31;
+  const long long gw = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
+  const long long W = (long long)gridDim.x * (blockDim.x >> 5);
+  const T g = (T)prm->psi_scale;
+  const T inv_dx = (T)inv_dx64, inv_dy = (T)inv_dy64, inv_dth = (T)inv_dth64, dth = (T)dth64;
+  const T glide = (T)glide64, vsp = (T)vsp64, h = T(0.5);
+  T adv = T(0), rot = T(0), rhomax = T(0);
+  const T* ux = u;
+  const T* uy = u + ncells;
+  for (long long cell = gw; cell < ncells; cell += W) {
     const int ix = (int)(cell % nx), iy = (int)(cell / nx);
     const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
     const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
-    const double Gxx = (ux[(long long)iy * nx + xp] - ux[(long long)iy * nx + xm]) * 0.5 * inv_dx;
-    const double Gxy = (ux[(long long)yp * nx + ix] - ux[(long long)ym * nx + ix]) * 0.5 * inv_dy;
-    const double Gyx = (uy[(long long)iy * nx + xp] - uy[(long long)iy * nx + xm]) * 0.5 * inv_dx;
-    const double Gyy = (uy[(long long)yp * nx + ix] - uy[(long long)ym * nx + ix]) * 0.5 * inv_dy;
-    double rho = 0.0;
-    for (int k = threadIdx.x; k < nth; k += blockDim.x) {
-      const double V = vsp + glide * (double)nb[cell * nth + k];
-      const double ax = ux[cell] - V * trig[k], ay = uy[cell] - V * trig[nth + k];
-      adv = fmax(adv, fabs(ax) * inv_dx + fabs(ay) * inv_dy);
-      const double cp = trig[2 * nth + k], sp = trig[3 * nth + k];
-      const double w = -sp * (Gxx * cp + Gxy * sp) + cp * (Gyx * cp + Gyy * sp);
-      rot = fmax(rot, fabs(w) * inv_dth);
-      rho += (double)psi[cell * nth + k] * psi_scale * dth;
+    const T Gxx = (ux[(long long)iy * nx + xp] - ux[(long long)iy * nx + xm]) * h * inv_dx;
+    const T Gxy = (ux[(long long)yp * nx + ix] - ux[(long long)ym * nx + ix]) * h * inv_dy;
+    const T Gyx = (uy[(long long)iy * nx + xp] - uy[(long long)iy * nx + xm]) * h * inv_dx;
+    const T Gyy = (uy[(long long)yp * nx + ix] - uy[(long long)ym * nx + ix]) * h * inv_dy;
+    const T uxc = ux[cell], uyc = uy[cell];
+    T rho = T(0);
+    for (int k = lane; k < nth; k += 32) {
+      const T V = vsp + glide * nb[cell * nth + k];
+      const T ax = uxc - V * trig[k], ay = uyc - V * trig[nth + k];
+      adv = tmax(adv, fabs(ax) * inv_dx + fabs(ay) * inv_dy);
+      const T cp = trig[2 * nth + k], sp = trig[3 * nth + k];
+      const T w = -sp * (Gxx * cp + Gxy * sp) + cp * (Gyx * cp + Gyy * sp);
+      rot = tmax(rot, fabs(w) * inv_dth);
+      rho += psi[cell * nth + k] * g * dth;
     }
-    const double r = block_sum(rho, red);
-    if (threadIdx.x == 0) rhomax = fmax(rhomax, r);
+    rhomax = tmax(rhomax, warp_sum_t(rho));
   }
-  adv = warp_max(adv);
-  rot = warp_max(rot);
-  if ((threadIdx.x & 31) == 0) {
-    atomic_max_nonneg(&prm->dtmax[0], adv);
-    atomic_max_nonneg(&prm->dtmax[1], rot);
+  adv = warp_max_t(adv);
+  rot = warp_max_t(rot);
+  if (lane == 0) {
+    atomic_max_nonneg(&prm->dtmax[0], (double)adv);
+    atomic_max_nonneg(&prm->dtmax[1], (double)rot);
+    atomic_max_nonneg(&prm->dtmax[2], (double)rhomax);
   }
-  if (threadIdx.x == 0) atomic_max_nonneg(&prm->dtmax[2], rhomax);
 }
 
 // ---- s-row sums for the moments: n_b = sum_j Mb_j ds and m1 = sum_j s_j Mb_j ds
@@ -456,14 +466,13 @@ cudaError_t launch_init_cells(T* mb, const T* psi, T* nb, T* mf, T* c, const T* 
 }
 
 template <typename T>
-cudaError_t launch_dt_max(const T* psi, const T* nb, const double* u64, const double* trig,
-                          long long ncells, int nx, int ny, int nth, double inv_dx,
-                          double inv_dy, double inv_dth, double dth, double glide, double vsp,
-                          DevParams* prm, cudaStream_t s) {
-  int block = nth >= 128 ? 128 : (nth >= 64 ? 64 : 32);
-  long long g = ncells < 152 * 8 ? ncells : 152 * 8;
-  k_dt_max<T><<<(int)g, block, 0, s>>>(psi, nb, u64, trig, ncells, nx, ny, nth, inv_dx, inv_dy,
-                                       inv_dth, dth, glide, vsp, prm);
+cudaError_t launch_dt_max(const T* psi, const T* nb, const T* u, const T* trig, long long ncells,
+                          int nx, int ny, int nth, double inv_dx, double inv_dy, double inv_dth,
+                          double dth, double glide, double vsp, DevParams* prm, cudaStream_t s) {
+  long long g = (ncells + 3) / 4;  // warp per cell, 4 warps per block
+  if (g > 152 * 8) g = 152 * 8;
+  k_dt_max<T><<<(int)g, 128, 0, s>>>(psi, nb, u, trig, ncells, nx, ny, nth, inv_dx, inv_dy,
+                                     inv_dth, dth, glide, vsp, prm);
   return cudaGetLastError();
 }
 
@@ -514,14 +523,12 @@ template cudaError_t launch_init_cells<float>(float*, const float*, float*, floa
 template cudaError_t launch_init_cells<double>(double*, const double*, double*, double*, double*,
                                                const double*, long long, int, int, double, double,
                                                cudaStream_t);
-template cudaError_t launch_dt_max<float>(const float*, const float*, const double*,
-                                          const double*, long long, int, int, int, double, double,
-                                          double, double, double, double, DevParams*,
-                                          cudaStream_t);
+template cudaError_t launch_dt_max<float>(const float*, const float*, const float*, const float*,
+                                          long long, int, int, int, double, double, double,
+                                          double, double, double, DevParams*, cudaStream_t);
 template cudaError_t launch_dt_max<double>(const double*, const double*, const double*,
-                                           const double*, long long, int, int, int, double,
-                                           double, double, double, double, double,
-                                           DevParams*, cudaStream_t);
+                                           const double*, long long, int, int, int, double, double,
+                                           double, double, double, double, DevParams*, cudaStream_t);
 template cudaError_t launch_moments<float>(const float*, const float*, const float*,
                                            const float*, const double*, long long, int, int, int,
                                            int, double, double, double, double, double*, double*,

@@ -145,10 +145,9 @@ cudaError_t launch_init_cells(T* mb, const T* psi, T* nb, T* mf, T* c, const T* 
                               long long ncells, int nth, int ns, double ds, double dth,
                               cudaStream_t s);
 template <typename T>
-cudaError_t launch_dt_max(const T* psi, const T* nb, const double* u64, const double* trig,
-                          long long ncells, int nx, int ny, int nth, double inv_dx,
-                          double inv_dy, double inv_dth, double dth, double glide, double vsp,
-                          DevParams* prm, cudaStream_t s);
+cudaError_t launch_dt_max(const T* psi, const T* nb, const T* u, const T* trig, long long ncells,
+                          int nx, int ny, int nth, double inv_dx, double inv_dy, double inv_dth,
+                          double dth, double glide, double vsp, DevParams* prm, cudaStream_t s);
 cudaError_t launch_dt_finalize(DevParams* prm, double ds, double L, double cfl, cudaStream_t s);
 template <typename T>
 cudaError_t launch_moments(const T* psi, const T* mb, const T* mf, const T* c,

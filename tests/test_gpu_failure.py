@@ -65,3 +65,36 @@ def test_launch_plan(mmod, dims, precision, tma):
     assert info["smem"] <= 200 * 1024
     assert info["block"] % 32 == 0 and info["grid"] >= 1
     assert info["chunk_rows"] * info["chunks_per_cell"] == g.ntheta
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp64"])
+def test_reverse_sweep_timeout_is_reported_and_recovers(mmod, precision):
+    """The knob on during a reverse sweep: the replays and both reverse kernels
+    (bulk-copy rings) give up their waits, drain their copies and return; the
+    sweep reports MM_ERR_TIMEOUT. With the knob off, a new recording on the
+    same handle gives the gradients of a clean handle, bit for bit."""
+    g = Grid(12, 10, 16, 16)
+    psi = psi_isotropic_perturbed(g, 3)
+    u = cellular_flow(g)
+
+    def record(sim):
+        sim.set_state(psi)
+        sim.set_velocity(u)
+        sim.set_checkpointing(4, 12)
+        sim.step(12)
+
+    with mmod.Simulation(g, Rates(), precision) as ref:
+        record(ref)
+        want = ref.adjoint(12, observable="polar_order")
+    with mmod.Simulation(g, Rates(), precision) as sim:
+        record(sim)
+        sim.debug_set(2000, 1)
+        with pytest.raises(mmod.MMError) as e:
+            sim.adjoint(12, observable="polar_order")
+        assert e.value.status == 5  # MM_ERR_TIMEOUT
+        sim.debug_set(1 << 22, 0)
+        record(sim)
+        got = sim.adjoint(12, observable="polar_order")
+    assert np.array_equal(got["dL_drates"], want["dL_drates"])
+    assert np.array_equal(got["dL_du"], want["dL_du"])
+    assert np.array_equal(got["dL_dpsi0"], want["dL_dpsi0"])

@@ -546,6 +546,9 @@ mm_status anchor_table(mm_handle* h) {
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(h->anc_off, off.data(), off.size() * sizeof(int2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->anc_widx, widx.data(), widx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  // captured substep graphs hold the window and block shape as launch arguments
+  for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
+  h->graphs.clear();
   const cudaError_t e = by_width<PrepareF>(h);
   if (e == cudaErrorInvalidValue)
     return fail(h, MM_ERR_UNSUPPORTED, "ntheta too large for the anchor kernel's shared memory");

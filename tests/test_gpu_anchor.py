@@ -165,6 +165,33 @@ def test_anchor_toggle_and_rates(mmod, oracle_mod):
             assert rel_l2(c[k], getattr(st3, k)) <= 1e-12, k
 
 
+def test_anchor_new_length_between_steps(mmod, oracle_mod):
+    """Substeps (captured as a graph), a new l/L through mm_set_rates, the same
+    number of substeps again (the graph must not keep the old anchors): the
+    oracle's same sequence."""
+    g = Grid(10, 8, 16, 16)
+    r1, r2 = Rates(ell=0.3), Rates(ell=0.12)
+    psi, mb = seeded(g, 261)
+    u = random_divfree_flow(g, 262, 4, 0.1)
+    st = oracle_mod.make_state_anchor(g, r1, psi, mb)
+    dt = oracle_mod.dt(g, r1, st, u)
+    with mmod.Simulation(g, r1, "fp64") as sim:
+        sim.set_anchors(True)
+        sim.set_state(psi, np.ascontiguousarray(mb))
+        sim.set_velocity(u)
+        sim.set_dt(dt)
+        sim.step(3)
+        sim.set_rates(r2)
+        sim.set_dt(dt)
+        sim.step(3)
+        gs = sim.get_state()
+    oracle_mod.run_anchor(g, r1, st, u, dt, 3)
+    st2 = oracle_mod.make_state_anchor(g, r2, st.psi, st.mb, st.mtot)
+    oracle_mod.run_anchor(g, r2, st2, u, dt, 3)
+    for k in ("psi", "mb", "mf", "c"):
+        assert rel_l2(gs[k], getattr(st2, k)) <= TOL["fp64"], k
+
+
 def test_anchor_refusals(mmod):
     g = Grid(6, 6, 8, 8)
     with mmod.Simulation(g, Rates(ell=0.2), "fp64") as sim:

@@ -552,6 +552,42 @@ def run_ours(args):
                              "kernel": "k_substep_anchor + k_anchor_close + k_anchor_fix (float32)",
                              "peak_source": src_, "traffic": None}}
 
+    def fluid_run(wname, reps=5):
+        """Thin-gap fluid solve (mm_fluid_solve, eps = 0.1, z0 = 0.1, with the
+        dipole term) on the workload's state, float32: CUDA events around each
+        solve (the moments of the state, three batched float64 transforms, the
+        per-mode map, the velocity update and the substep rule), and around one
+        Alg. 1 macro step (the solve, then the workload's substeps)."""
+        wl = WORKLOADS[wname]
+        gl = wl["grid"]
+        sim = mm.Simulation(gl, r, "fp32", stream=stream.cuda_stream)
+        sim.set_state(psi_isotropic_perturbed(gl, wl["seed"]))
+        sim.set_velocity(torch.tensor(workload_velocity(wname, 0), device=dev))
+        sim.step(2)
+        sim.fluid_setup(0.1, 0.1)
+        sim.fluid_solve(dipole=True, u_out=None)
+        sim.step(wl["substeps"])
+        ts, tm = [], []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            sim.fluid_solve(dipole=True, u_out=None)
+            e1.record(stream)
+            sim.step(wl["substeps"])
+            e2.record(stream)
+            e2.synchronize()
+            ts.append(e0.elapsed_time(e1))
+            tm.append(e0.elapsed_time(e2))
+        sim.sync()
+        sim.close()
+        ms, mac = sum(ts) / len(ts), sum(tm) / len(tm)
+        return {"workload": f"{wname} ({gl.nx}x{gl.ny} x {gl.ntheta} x {gl.ns}, fp32), "
+                            f"eps = 0.1, z0 = 0.1, macro step = solve + {wl['substeps']} substeps",
+                "ms_per_solve": ms, "macro_step_ms": mac, "solve_share_of_macro_step": ms / mac,
+                "macro_value": world * gl.micro_cells * wl["substeps"] / (mac * 1e-3),
+                "unit": UNIT}
+
     def ensemble_run(steps):
         """ensemble64: 64 members with uneven grids (N in {32..128}, Ntheta and
         Ns in {16, 32}), k_off log-uniform in [0.05, 5], v_walk in [0.5, 2];
@@ -614,6 +650,7 @@ def run_ours(args):
     diff = diffusion_run()
     anchors = {"precision128": anchors_run("precision128", 50),
                "large512": anchors_run("large512", 5)}
+    fluid = {"precision128": fluid_run("precision128"), "large512": fluid_run("large512", reps=3)}
     local = {"precision128": local_run("precision128"),
              "large512": local_run("large512", reps=3)}
     for v in local.values():
@@ -670,6 +707,7 @@ def run_ours(args):
             "diffusion": diff,
             "local": local,
             "anchors": anchors,
+            "fluid": fluid,
             "ensemble": dict(ens, roofline={"bound": "hbm", "peak": peak, "unit": "GB/s",
                                             "achieved": ens["achieved_gbs"],
                                             "frac": ens["achieved_gbs"] / peak,

@@ -287,6 +287,50 @@ mm_status mm_motor_local(mm_handle* h, double T, const int* nsteps_in, int* nste
  * available) and mm_set_anchors returns MM_ERR_STATE during a recording. */
 mm_status mm_set_anchors(mm_handle* h, int enable);
 
+/* ---- Thin-gap fluid solve (Eq. 7-9, Alg. 1 after the inner loop) --------------
+ *
+ * The fluid fills the gap 0 <= z <= 1 between two no-slip plates and is
+ * periodic in x and y over the unit square (Sec. 2); the filaments lie on the
+ * plane z = z0 (Sec. 2: a Dirac delta in z about that plane), so the right side
+ * of Eq. 7 is (F_2 + div_2 Sigma) delta(z - z0). The solve returns u_2 on that
+ * plane, the velocity that advects the filaments (Eq. 2-3).
+ *
+ * mm_fluid_setup(h, eps, z0): eps of Eq. 7-8 (> 0, finite), the plane's height
+ * z0 (0 < z0 < 1). Builds, on the device, the in-plane response per Fourier
+ * mode of the half spectrum, (g_T, g_L) at |k| = 2 pi sqrt(jx^2 + my^2), the
+ * velocity at z0 per unit force on the plane across and along k, each the exact
+ * solution in z of the transformed Eq. 7-9 (the limit of the paper's z-grid).
+ * P0 scales the pressure only and does not enter. Needs nx, ny >= 2
+ * (MM_ERR_UNSUPPORTED otherwise, and on a batch member); plans three batched
+ * float64 cuFFT transforms. May be called again with new eps, z0.
+ *
+ * mm_fluid_solve(h, sigma, sigma_on_device, dipole, u_out, u_out_on_device):
+ *   1. the moments of the current state (as mm_moments; F = fields 7, 8);
+ *   2. per mode of the 2D DFT of the cell values, f = F^ + i k . S^ with
+ *      S = Sigma - dipole sigma_a: sigma (float64 [3][ny][nx], xx, xy, yy, host
+ *      or device, may be NULL) is the extra stress sigma_f S_f - sigma_t S_t of
+ *      Eq. 7 (its constitutive law is the caller's); dipole = 1 adds the
+ *      first-order term of Eq. 10's spreading in s, F_2 ~ F - div sigma_a
+ *      (moment fields 9-11; not with anchors, whose force already acts in the
+ *      anchor cells: MM_ERR_UNSUPPORTED);
+ *   3. u^ = g_T f + (g_L - g_T) k (k . f) / |k|^2 (g_T = g_L at k = 0, the mean
+ *      flow); at a Nyquist index of an even nx or ny the map is the mean of its
+ *      values for +k and -k of that component (the output stays real);
+ *   4. the inverse DFT; u_2 [2][ny][nx] becomes the velocity in effect, as
+ *      mm_set_velocity (the adaptive substep is recomputed), and is copied to
+ *      u_out (float64 [2][ny][nx], host or device) if u_out is not NULL.
+ * All in float64 in either precision. MM_ERR_STATE without mm_fluid_setup or a
+ * state, or during an adjoint recording (not differentiated). Asynchronous on
+ * the handle's stream unless u_out is a host pointer.
+ *
+ * mm_fluid_response(h, out, on_device): copies the response table, float64
+ * [ny][nx/2 + 1][2] (g_T, g_L), index (jy, jx) at wavenumber (jx, my) with
+ * my = jy for jy <= ny/2 and jy - ny above. */
+mm_status mm_fluid_setup(mm_handle* h, double eps, double z0);
+mm_status mm_fluid_solve(mm_handle* h, const double* sigma, int sigma_on_device, int dipole,
+                         double* u_out, int u_out_on_device);
+mm_status mm_fluid_response(mm_handle* h, double* out, int on_device);
+
 /* ---- Batched ensemble --------------------------------------------------------
  *
  * An ensemble of n independent instances (an instance as above: its own grid,

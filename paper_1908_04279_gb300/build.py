@@ -69,7 +69,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
             if err:
                 sys.stderr.write(err)
     tmp = LIB + f".{os.getpid()}.tmp"
-    cmd = [cc, "-shared", *ARCH, "-o", tmp, *[o for o, _ in results], "-lcudart"]
+    # cuFFT (the fluid solve's transforms) from the toolkit that compiled the library
+    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(cc))), "lib64")
+    cmd = [cc, "-shared", *ARCH, "-o", tmp, *[o for o, _ in results], "-lcudart", "-lcufft",
+           "-Xlinker", "-rpath," + cuda_lib]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stderr}")

@@ -37,6 +37,7 @@ void free_recording(mm_handle* h) {
 
 mm_status free_all(mm_handle* h) {
   free_recording(h);
+  fluid_free(h);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
   if (h->diff_tab) cudaFree(h->diff_tab);
@@ -605,6 +606,17 @@ mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
   const size_t n = 2 * (size_t)h->ncells;
   CK(cudaMemcpyAsync(h->u64, u, n * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
                      h->stream));
+  return velocity_update(h);
+}
+
+}  // extern "C"
+
+namespace mmh {
+
+// The velocity in h->u64 becomes the one in effect: its state-precision copy,
+// the cell velocities and gradients, and the adaptive substep.
+mm_status velocity_update(mm_handle* h) {
+  const size_t n = 2 * (size_t)h->ncells;
   if (h->prec == MM_FP64)
     CK(cudaMemcpyAsync(h->u, h->u64, n * 8, cudaMemcpyDeviceToDevice, h->stream));
   else
@@ -636,6 +648,10 @@ mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
   if (h->rec.active) return rec_push_version(h);
   return MM_OK;
 }
+
+}  // namespace mmh
+
+extern "C" {
 
 mm_status mm_get_dt(mm_handle* h, double* dt) {
   if (!h || !dt) return MM_ERR_INVALID;

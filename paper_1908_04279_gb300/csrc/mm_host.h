@@ -133,6 +133,13 @@ struct mm_handle {
   double* anc_cacc = nullptr;   // [cells] float64 accumulators of C
   double* anc_fsc = nullptr;    // [cells] scale-down factors
   int* anc_flags = nullptr;     // [4] scale-down flags
+  // thin-gap fluid solve (mm_fluid_setup)
+  bool fluid = false;
+  double fl_eps = 0.0, fl_z0 = 0.0;
+  int fl_plan[3] = {-1, -1, -1};  // cuFFT plans: 5 forward, 3 forward, 2 inverse transforms
+  double* fl_tab = nullptr;       // [ny][nx/2+1] (g_T, g_L) per mode
+  double* fl_hat = nullptr;       // [10][ny][nx/2+1] complex: 5 force/dipole, 3 stress, 2 velocity
+  double* fl_real = nullptr;      // [10][cells rounded up to even] real inputs and outputs
   size_t staging_n = 0;  // float64 values the staging buffer holds
   DevParams* prm = nullptr;
   int npartial = 0;
@@ -201,6 +208,11 @@ StepArgs<T> step_args(mm_handle* h, int parity);
 mm_status rec_push_substep(mm_handle* h);  // checkpoint bookkeeping of one recorded substep
 mm_status launch_substeps(mm_handle* h, int n);  // n substeps on the live state (graphs)
 mm_status run_init(mm_handle* h);  // n_b, C, the scale-down and Mf of the live state
+mm_status run_moments(mm_handle* h);  // the 12 moment fields and the scalars of the live state
+mm_status velocity_update(mm_handle* h);  // h->u64 becomes the velocity in effect (and dt)
+
+// Defined in mm_fluid.cu (thin-gap fluid solve).
+void fluid_free(mm_handle* h);
 
 // Defined in mm_anchor.cu (non-local motor anchors).
 mm_status anchor_table(mm_handle* h);

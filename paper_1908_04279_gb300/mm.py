@@ -91,6 +91,9 @@ PROTOTYPES = {
     "mm_diffuse": ([_H, C.c_double, C.c_double, C.c_double], C.c_int),
     "mm_motor_local": ([_H, C.c_double, _P, _P, C.c_int], C.c_int),
     "mm_set_anchors": ([_H, C.c_int], C.c_int),
+    "mm_fluid_setup": ([_H, C.c_double, C.c_double], C.c_int),
+    "mm_fluid_solve": ([_H, _P, C.c_int, C.c_int, _P, C.c_int], C.c_int),
+    "mm_fluid_response": ([_H, _P, C.c_int], C.c_int),
     "mm_debug_set": ([_H, C.c_uint, C.c_uint], C.c_int),
     "mm_get_launch_info": ([_H, C.POINTER(C.c_int), C.c_int], C.c_int),
     "mm_moments_static": ([C.POINTER(mm_grid), C.POINTER(mm_rates), _P, _P, _P, _P, _P, _P, _P],
@@ -264,6 +267,41 @@ class Simulation:
         """Non-local motor anchors (mm_set_anchors): each configuration anchored
         in the cell under its motor head, x + (l/L) s p with l/L = rates.ell."""
         self._check(self.lib.mm_set_anchors(self.h, 1 if enable else 0))
+
+    def fluid_setup(self, eps: float, z0: float):
+        """Thin-gap fluid solve of Eq. 7-9 (mm_fluid_setup): gap aspect eps,
+        filament plane at z0 between no-slip plates at z = 0 and 1."""
+        self._check(self.lib.mm_fluid_setup(self.h, float(eps), float(z0)))
+
+    def fluid_solve(self, sigma=None, dipole: bool = False, u_out="host"):
+        """u_2 on the filament plane from the motor force of the current state
+        (plus -div sigma_a with dipole, plus div sigma of the caller's extra
+        stress [3][ny][nx]); it becomes the velocity in effect. u_out: "host"
+        returns a numpy [2][ny][nx], None returns nothing (no
+        synchronisation), a float64 CUDA tensor receives it on the device."""
+        g = self.grid
+        sp, sd = _ptr(sigma, "sigma")
+        if sigma is not None and tuple(sigma.shape) != (3, g.ny, g.nx):
+            raise ValueError("sigma must have shape [3][ny][nx]")
+        if isinstance(u_out, str):
+            if u_out != "host":
+                raise ValueError('u_out must be "host", None or a CUDA tensor')
+            out = np.empty((2, g.ny, g.nx))
+            self._check(self.lib.mm_fluid_solve(self.h, sp, sd or 0, int(bool(dipole)),
+                                                out.ctypes.data, 0))
+            return out
+        up, ud = _ptr(u_out, "u_out")
+        if u_out is not None and (not ud or tuple(u_out.shape) != (2, g.ny, g.nx)):
+            raise TypeError("u_out must be a float64 CUDA tensor [2][ny][nx]")
+        self._check(self.lib.mm_fluid_solve(self.h, sp, sd or 0, int(bool(dipole)), up, ud or 0))
+        return None
+
+    def fluid_response(self) -> np.ndarray:
+        """The per-mode response table [ny][nx//2 + 1][2] (g_T, g_L)."""
+        g = self.grid
+        out = np.empty((g.ny, g.nx // 2 + 1, 2))
+        self._check(self.lib.mm_fluid_response(self.h, out.ctypes.data, 0))
+        return out
 
     def motor_local(self, T: float, nsteps=None):
         """Motor kinetics over T with psi frozen and a local substep per cell

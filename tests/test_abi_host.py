@@ -84,6 +84,9 @@ def test_null_handle_calls_are_invalid(lib):
     assert lib.mm_set_dt(None, 1.0) == 1
     assert lib.mm_motor_local(None, 0.1, None, None, 0) == 1
     assert lib.mm_set_anchors(None, 1) == 1
+    assert lib.mm_fluid_setup(None, 0.1, 0.1) == 1
+    assert lib.mm_fluid_solve(None, None, 0, 0, None, 0) == 1
+    assert lib.mm_fluid_response(None, None, 0) == 1
     assert lib.mm_diffuse(None, 0.1, 0.1, 0.1) == 1
     assert lib.mm_sync(None) == 1
     assert lib.mm_build_info().startswith(b"libmm sm_103a")

@@ -1,6 +1,7 @@
 """Run one synthetic case of the library's kernels, for profilers.
 
-    python -m paper_1908_04279_gb300.profile_case [--case single|batch|adjoint|moments|local]
+    python -m paper_1908_04279_gb300.profile_case
+        [--case single|batch|adjoint|moments|local|fluid]
         [--grid NX NY NTHETA NS] [--precision fp32|fp64] [--substeps N]
         [--repeat R] [--K K] [--members M] [--autotune] [--anchors ELL]
 
@@ -15,6 +16,9 @@ adjoint: a recording of N substeps (checkpoint every K) on the single case,
 moments: N substeps of the single case, then R calls of mm_moments.
 local:   the single case's state, then R calls of mm_motor_local over the
          interval of N substeps of the adaptive dt (psi frozen, local steps).
+fluid:   N substeps of the single case, then R macro steps of Alg. 1: the
+         thin-gap fluid solve (eps = 0.1, z0 = 0.1, dipole term on), then N
+         substeps at the solved velocity.
 Prints the times measured with CUDA events on the handle's stream.
 """
 from __future__ import annotations
@@ -32,8 +36,8 @@ def main():
                          random_divfree_flow)
 
     ap = argparse.ArgumentParser()
-    ap.add_argument("--case", default="single", choices=["single", "batch", "adjoint", "moments",
-                                                          "local"])
+    ap.add_argument("--case", default="single",
+                    choices=["single", "batch", "adjoint", "moments", "local", "fluid"])
     ap.add_argument("--grid", type=int, nargs=4, default=[256, 256, 64, 64])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--substeps", type=int, default=10)
@@ -88,6 +92,17 @@ def main():
             times = [timed(lambda: sim.moments(fields=fields)) for _ in range(args.repeat)]
             print(json.dumps({"case": "moments", "grid": args.grid, "precision": args.precision,
                               "ms_per_call": times}))
+            return
+        if args.case == "fluid":
+            sim.step(args.substeps)
+            sim.fluid_setup(0.1, 0.1)
+            solve, macro = [], []
+            for _ in range(args.repeat):
+                solve.append(timed(lambda: sim.fluid_solve(dipole=True, u_out=None)))
+                macro.append(timed(lambda: sim.step(args.substeps)))
+            sim.sync()
+            print(json.dumps({"case": "fluid", "grid": args.grid, "precision": args.precision,
+                              "ms_per_solve": solve, "ms_substeps_after": macro}))
             return
         if args.case == "local":
             T = args.substeps * sim.dt

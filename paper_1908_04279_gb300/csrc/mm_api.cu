@@ -435,7 +435,7 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
   ALLOC(h->ucell, 12 * nc * h->tsz);
   ALLOC(h->u64, 2 * nc * 8);
   ALLOC(h->trig, 4 * (size_t)grid->ntheta * h->tsz);
-  ALLOC(h->trig64, 14 * (size_t)grid->ntheta * 8);
+  ALLOC(h->trig64, 24 * (size_t)grid->ntheta * 8);
   ALLOC(h->partial, (size_t)h->npartial * 8 * 8);
   ALLOC(h->fields, 12 * nc * 8);
   ALLOC(h->staging, h->staging_n * 8);
@@ -456,8 +456,9 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
     tr[2 * nth + k] = std::cos((k + 0.5) * dth);
     tr[3 * nth + k] = std::sin((k + 0.5) * dth);
   }
-  // moment weights after the four trigonometric rows (see k_moments)
-  std::vector<double> tw(14 * (size_t)nth);
+  // moment weights after the four trigonometric rows (see k_moments), then
+  // the same ten weights split into float pairs (hi, lo) for the float32 form
+  std::vector<double> tw(24 * (size_t)nth);
   std::copy(tr.begin(), tr.end(), tw.begin());
   for (int k = 0; k < nth; ++k) {
     const double c = tr[k], s = tr[nth + k];
@@ -472,6 +473,15 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
     w[7 * nth + k] = c * c * dth;
     w[8 * nth + k] = c * s * dth;
     w[9 * nth + k] = s * s * dth;
+  }
+  {
+    float* wf = reinterpret_cast<float*>(tw.data() + 14 * (size_t)nth);
+    const double* w = tw.data() + 4 * (size_t)nth;
+    for (size_t i = 0; i < 10 * (size_t)nth; ++i) {
+      const float hi = (float)w[i];
+      wf[2 * i] = hi;
+      wf[2 * i + 1] = (float)(w[i] - (double)hi);
+    }
   }
   e = cudaMemcpy(h->trig64, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {

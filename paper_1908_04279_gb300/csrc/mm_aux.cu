@@ -164,6 +164,23 @@ __device__ __forceinline__ void ff_merge(FF& a, const FF& b) {
   ff_add(a, b.hi);
   a.lo += lo;
 }
+// a + b (TwoSum of the high parts, low parts added)
+__device__ __forceinline__ FF ff_sum(const FF& a, const FF& b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  return FF{s, __fadd_rn(e, __fadd_rn(a.lo, b.lo))};
+}
+// p w for a float p and a float-float w (TwoProduct of the high part)
+__device__ __forceinline__ FF ff_scale(float p, const FF& w) {
+  const float h = __fmul_rn(p, w.hi);
+  return FF{h, __fmaf_rn(p, w.lo, __fmaf_rn(p, w.hi, -h))};
+}
+// a w for float-float a and w (the lo * lo term dropped)
+__device__ __forceinline__ FF ff_prod(const FF& a, const FF& w) {
+  const float h = __fmul_rn(a.hi, w.hi);
+  return FF{h, __fmaf_rn(a.hi, w.lo, __fmaf_rn(a.lo, w.hi, __fmaf_rn(a.hi, w.hi, -h)))};
+}
 
 // Row sums of the V values a lane holds, reduced over the row's `seg` lanes;
 // every lane of the segment gets (n_b / ds, m1 / ds) in float64.
@@ -223,9 +240,28 @@ __device__ __forceinline__ double warp_sum16_scatter(double (&v)[16], int lane) 
   }
   return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
+// The same reduce-scatter in float-float.
+__device__ __forceinline__ FF warp_sum16_scatter_ff(FF (&v)[16], int lane) {
+#pragma unroll
+  for (int step = 0; step < 4; ++step) {
+    const int o = 16 >> step, half = 8 >> step;
+    const bool up = (lane & o) != 0;
+#pragma unroll
+    for (int i = 0; i < half; ++i) {
+      const FF keep = up ? v[half + i] : v[i];
+      const FF give = up ? v[i] : v[half + i];
+      const FF got{__shfl_xor_sync(0xffffffffu, give.hi, o), __shfl_xor_sync(0xffffffffu, give.lo, o)};
+      v[i] = ff_sum(keep, got);
+    }
+  }
+  const FF got{__shfl_xor_sync(0xffffffffu, v[0].hi, 1), __shfl_xor_sync(0xffffffffu, v[0].lo, 1)};
+  return ff_sum(v[0], got);
+}
 __device__ __forceinline__ int scatter_field(int lane) {
   return ((lane >> 4) & 1) * 8 + ((lane >> 3) & 1) * 4 + ((lane >> 2) & 1) * 2 + ((lane >> 1) & 1);
 }
+
+constexpr int kMomPasses = 4;
 
 template <typename T, int V>
 struct alignas(sizeof(T) * V) VPack {
@@ -243,7 +279,7 @@ struct alignas(sizeof(T) * V) VPack {
 template <typename T, int V>
 __global__ void k_moments(const T* psi, const T* mb, const T* mf, const T* c,
                           const double* trig, long long ncells, int nth, int ns, int seg,
-                          double dth, double ds, double L, double dA, double* fields,
+                          double dth, double ds, double L, double dA, float hds, double* fields,
                           double* partial, DevParams* prm) {
   extern __shared__ double msm[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -261,119 +297,199 @@ __global__ void k_moments(const T* psi, const T* mb, const T* mf, const T* c,
   const bool lane_ok = sl < nl;
   T sj[V];
 #pragma unroll
-  for (int v = 0; v < V; ++v) sj[v] = (T)(-0.5 * L + ((double)(sl * V + v) + 0.5) * ds);
+  for (int v = 0; v < V; ++v) {
+    // s_j = (2j + 1 - ns) ds / 2; the float32 form in float32 (one rounding)
+    if constexpr (sizeof(T) == 4)
+      sj[v] = (float)(2 * (sl * V + v) + 1 - ns) * hds;
+    else
+      sj[v] = -0.5 * L + ((double)(sl * V + v) + 0.5) * ds;
+  }
   // global accumulators: N_psi, bound, free, sum psi cos, sum psi sin, sum psi, sum tr
   double gs[7] = {0, 0, 0, 0, 0, 0, 0};
   const int fq = scatter_field(lane);
+  // float32 form: every float64 warp instruction costs the float64 pipe as
+  // much as a full warp's, so the per-cell bookkeeping stays in float-float:
+  // acc is the lane's field total summed over its cells, acc2 (lanes 1, 3) the
+  // sum of C and of Mf; each field total is scaled by its constant (psi_scale,
+  // ds F, ds F ell) split into a float pair
+  FF acc{0.f, 0.f}, acc2{0.f, 0.f};
+  FF scf{0.f, 0.f};
+  if constexpr (sizeof(T) == 4) {
+    const double sc = fq < 5 ? g : (fq < 7 ? g * (ds * Fm) : g * (ds * Fm * ell));
+    scf.hi = (float)sc;
+    scf.lo = (float)(sc - (double)scf.hi);
+  }
   for (long long cell = gw; cell < ncells; cell += W) {
-    for (int r0 = 0; r0 < nth; r0 += rpp) {
-      const int k = r0 + rslot;
-      const bool act = k < nth && lane_ok;
-      T m[V];
-      if (act) {
-        const VPack<T, V> q =
-            *reinterpret_cast<const VPack<T, V>*>(mb + ((size_t)cell * nth + k) * ns + sl * V);
+    // kMomPasses passes of rows loaded before they are reduced (more bytes in
+    // flight per warp)
+    for (int r0 = 0; r0 < nth; r0 += kMomPasses * rpp) {
+      T m[kMomPasses][V];
 #pragma unroll
-        for (int v = 0; v < V; ++v) m[v] = q.v[v];
-      } else {
+      for (int u = 0; u < kMomPasses; ++u) {
+        const int k = r0 + u * rpp + rslot;
+        if (k < nth && lane_ok) {
+          const VPack<T, V> q =
+              *reinterpret_cast<const VPack<T, V>*>(mb + ((size_t)cell * nth + k) * ns + sl * V);
 #pragma unroll
-        for (int v = 0; v < V; ++v) m[v] = T(0);
+          for (int v = 0; v < V; ++v) m[u][v] = q.v[v];
+        } else {
+#pragma unroll
+          for (int v = 0; v < V; ++v) m[u][v] = T(0);
+        }
       }
-      if constexpr (sizeof(T) == 4) {
-        FF a, b;
-        row_sums_ff<V>(m, sj, seg, a, b);
-        if (sl == 0 && k < nth) s_ff[k] = make_float4(a.hi, a.lo, b.hi, b.lo);
-      } else {
-        double nbk, m1k;
-        row_sums<V>(m, sj, seg, nbk, m1k);
-        if (sl == 0 && k < nth) {
-          s_nb[k] = nbk * ds;
-          s_m1[k] = m1k * ds;
+#pragma unroll
+      for (int u = 0; u < kMomPasses; ++u) {
+        const int k = r0 + u * rpp + rslot;
+        if constexpr (sizeof(T) == 4) {
+          FF a, b;
+          row_sums_ff<V>(m[u], sj, seg, a, b);
+          if (sl == 0 && k < nth) s_ff[k] = make_float4(a.hi, a.lo, b.hi, b.lo);
+        } else {
+          double nbk, m1k;
+          row_sums<V>(m[u], sj, seg, nbk, m1k);
+          if (sl == 0 && k < nth) {
+            s_nb[k] = nbk * ds;
+            s_m1[k] = m1k * ds;
+          }
         }
       }
     }
     __syncwarp();
     // ten field sums over theta (weights w[q][k] built on the host: dth,
     // cos dth, sin dth, (cos^2 - 1/2) dth, cos sin dth, cos, sin, cos^2 dth,
-    // cos sin dth, sin^2 dth); slots 10..15 stay zero
-    double f[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-    const double* w = trig + 4 * (size_t)nth;
-    for (int k = lane; k < nth; k += 32) {
-      double nbk, m1k;
-      if constexpr (sizeof(T) == 4) {
-        const float4 q = s_ff[k];
-        nbk = ((double)q.x + (double)q.y) * ds;
-        m1k = ((double)q.z + (double)q.w) * ds;
-      } else {
-        nbk = s_nb[k];
-        m1k = s_m1[k];
-      }
-      const double p = (double)psi[cell * nth + k] * g;
-      const double pn = p * nbk * Fm, pm = p * m1k * (Fm * ell);
-      f[0] = fma(p, w[k], f[0]);
-      f[1] = fma(p, w[nth + k], f[1]);
-      f[2] = fma(p, w[2 * nth + k], f[2]);
-      f[3] = fma(p, w[3 * nth + k], f[3]);
-      f[4] = fma(p, w[4 * nth + k], f[4]);
-      f[5] = fma(pn, w[nth + k], f[5]);
-      f[6] = fma(pn, w[2 * nth + k], f[6]);
-      f[7] = fma(pm, w[7 * nth + k], f[7]);
-      f[8] = fma(pm, w[8 * nth + k], f[8]);
-      f[9] = fma(pm, w[9 * nth + k], f[9]);
-      gs[3] = fma(p, w[5 * nth + k], gs[3]);
-      gs[4] = fma(p, w[6 * nth + k], gs[4]);
-      gs[5] += p;
-    }
-    __syncwarp();
-    // lane pair (2q, 2q + 1) gets the total of field q
-    const double tot = warp_sum16_scatter(f, lane);
-    // output slot of field q: 0-4 as is, 5-9 to 7-11 (5 and 6 are C and Mf)
-    if ((lane & 1) == 0 && fq < 10) fields[(size_t)(fq < 5 ? fq : fq + 2) * ncells + cell] = tot;
-    const double f0 = __shfl_sync(0xffffffffu, tot, 0);   // field 0 (lane 0)
-    const double f7 = __shfl_sync(0xffffffffu, tot, 14);  // field 7: bits 3, 2, 1 set
-    if (lane == 0) {
-      const double cc = (double)c[cell], ff = (double)mf[cell];
-      fields[5 * ncells + cell] = cc;
-      fields[6 * ncells + cell] = ff;
-      gs[0] += f0 * dA;
-      gs[1] += cc * dA;
-      gs[2] += ff * dA;
-    }
-    // tr sigma_a = f7 + f9
-    const double f9 = __shfl_sync(0xffffffffu, tot, 18);  // field 9: bits 4, 1 set
-    if (lane == 0) gs[6] += f7 + f9;
-  }
+    // cos sin dth, sin^2 dth); slots 10..15 stay zero. Lane pair (2q, 2q + 1)
+    // gets the total of field q.
+    if constexpr (sizeof(T) == 4) {
+      // Float32 form: the sums in float-float on the float32 pipe (each product
+      // exact to about 2^-48 of itself, the weights split into float pairs on
+      // the host); psi_scale and the constant factors ds F, ds F ell multiply
+      // each total once, in float64.
+      const float2* wf = reinterpret_cast<const float2*>(trig + 14 * (size_t)nth);
+      FF f[16];
 #pragma unroll
-  for (int q = 0; q < 7; ++q) gs[q] = warp_sum(gs[q]);
-  // per block in warp order, then the last block adds the block partials in a
-  // fixed order (warp q of that block sums quantities q, q + nw, ...)
+      for (int q = 0; q < 16; ++q) f[q] = FF{0.f, 0.f};
+      for (int k = lane; k < nth; k += 32) {
+        const float4 q4 = s_ff[k];
+        const float p = (float)psi[cell * nth + k];
+        const FF pn = ff_scale(p, FF{q4.x, q4.y}), pm = ff_scale(p, FF{q4.z, q4.w});
+        FF wq[10];
+#pragma unroll
+        for (int q = 0; q < 10; ++q) {
+          const float2 t = wf[(size_t)q * nth + k];
+          wq[q] = FF{t.x, t.y};
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q) f[q] = ff_sum(f[q], ff_scale(p, wq[q]));
+        f[5] = ff_sum(f[5], ff_prod(pn, wq[1]));
+        f[6] = ff_sum(f[6], ff_prod(pn, wq[2]));
+#pragma unroll
+        for (int q = 7; q < 10; ++q) f[q] = ff_sum(f[q], ff_prod(pm, wq[q]));
+      }
+      __syncwarp();
+      const FF t = warp_sum16_scatter_ff(f, lane);
+      acc = ff_sum(acc, t);
+      const FF ts = ff_prod(t, scf);
+      const double tot = (double)ts.hi + (double)ts.lo;
+      if ((lane & 1) == 0 && fq < 10) fields[(size_t)(fq < 5 ? fq : fq + 2) * ncells + cell] = tot;
+      // C and Mf as they are (lanes 1 and 3: one conversion for both)
+      if (lane == 1 || lane == 3) {
+        const float v = lane == 1 ? (float)c[cell] : (float)mf[cell];
+        fields[(size_t)(lane == 1 ? 5 : 6) * ncells + cell] = (double)v;
+        ff_add(acc2, v);
+      }
+    } else {
+      double f[16] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+      const double* w = trig + 4 * (size_t)nth;
+      for (int k = lane; k < nth; k += 32) {
+        const double nbk = s_nb[k], m1k = s_m1[k];
+        const double p = (double)psi[cell * nth + k] * g;
+        const double pn = p * nbk * Fm, pm = p * m1k * (Fm * ell);
+        f[0] = fma(p, w[k], f[0]);
+        f[1] = fma(p, w[nth + k], f[1]);
+        f[2] = fma(p, w[2 * nth + k], f[2]);
+        f[3] = fma(p, w[3 * nth + k], f[3]);
+        f[4] = fma(p, w[4 * nth + k], f[4]);
+        f[5] = fma(pn, w[nth + k], f[5]);
+        f[6] = fma(pn, w[2 * nth + k], f[6]);
+        f[7] = fma(pm, w[7 * nth + k], f[7]);
+        f[8] = fma(pm, w[8 * nth + k], f[8]);
+        f[9] = fma(pm, w[9 * nth + k], f[9]);
+        gs[3] = fma(p, w[5 * nth + k], gs[3]);
+        gs[4] = fma(p, w[6 * nth + k], gs[4]);
+        gs[5] += p;
+      }
+      __syncwarp();
+      const double tot = warp_sum16_scatter(f, lane);
+      // output slot of field q: 0-4 as is, 5-9 to 7-11 (5 and 6 are C and Mf)
+      if ((lane & 1) == 0 && fq < 10) fields[(size_t)(fq < 5 ? fq : fq + 2) * ncells + cell] = tot;
+      const double f0 = __shfl_sync(0xffffffffu, tot, 0);   // field 0 (lane 0)
+      const double f7 = __shfl_sync(0xffffffffu, tot, 14);  // field 7: bits 3, 2, 1 set
+      if (lane == 0) {
+        const double cc = (double)c[cell], ff = (double)mf[cell];
+        fields[5 * ncells + cell] = cc;
+        fields[6 * ncells + cell] = ff;
+        gs[0] += f0 * dA;
+        gs[1] += cc * dA;
+        gs[2] += ff * dA;
+      }
+      // tr sigma_a = f7 + f9
+      const double f9 = __shfl_sync(0xffffffffu, tot, 18);  // field 9: bits 4, 1 set
+      if (lane == 0) gs[6] += f7 + f9;
+    }
+  }
   __shared__ double s_g[32 * 8];
   __shared__ unsigned int s_last;
   const int nw = (int)(blockDim.x >> 5);
-  if (lane == 0)
-    for (int q = 0; q < 7; ++q) s_g[wib * 8 + q] = gs[q];
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < 7; ++q) {
-      double b = s_g[q];
-      for (int w2 = 1; w2 < nw; ++w2) b += s_g[w2 * 8 + q];
-      partial[(size_t)blockIdx.x * 8 + q] = b;
+  if constexpr (sizeof(T) == 4) {
+    // The warp's quantities in float-float, lane q holding quantity q:
+    // 0 N_psi (field 0), 1 C, 2 Mf, 3 sum psi cos (field 1), 4 sum psi sin
+    // (field 2), 5 sum psi (field 0), 6 tr sigma_a (fields 7 + 9); unscaled.
+    const int sa = lane == 3 ? 2 : lane == 4 ? 4 : lane == 6 ? 14 : 0;
+    const int sb = lane == 2 ? 3 : 1;
+    FF v{__shfl_sync(0xffffffffu, acc.hi, sa), __shfl_sync(0xffffffffu, acc.lo, sa)};
+    const FF w2{__shfl_sync(0xffffffffu, acc2.hi, sb), __shfl_sync(0xffffffffu, acc2.lo, sb)};
+    const FF a9{__shfl_sync(0xffffffffu, acc.hi, 18), __shfl_sync(0xffffffffu, acc.lo, 18)};
+    if (lane == 1 || lane == 2) v = w2;
+    if (lane == 6) v = ff_sum(v, a9);
+    // per block in warp order, then the last block adds the block partials
+    // (float pairs in the 8-byte slots) in a fixed order
+    float2* s_ff2 = reinterpret_cast<float2*>(s_g);
+    if (lane < 7) s_ff2[wib * 8 + lane] = make_float2(v.hi, v.lo);
+    __syncthreads();
+    float2* pf = reinterpret_cast<float2*>(partial);
+    if (wib == 0 && lane < 7) {
+      FF b{s_ff2[lane].x, s_ff2[lane].y};
+      for (int w2i = 1; w2i < nw; ++w2i) b = ff_sum(b, FF{s_ff2[w2i * 8 + lane].x, s_ff2[w2i * 8 + lane].y});
+      pf[(size_t)blockIdx.x * 8 + lane] = make_float2(b.hi, b.lo);
+      __threadfence();
     }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned int prev = atomicInc(&prm->counter2, gridDim.x - 1);
+      s_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
     __threadfence();
-    const unsigned int prev = atomicInc(&prm->counter2, gridDim.x - 1);
-    s_last = prev == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last) {
-    __threadfence();
+    // scales: psi_scale dA, dA, dA, psi_scale / dth (x3), psi_scale ds F ell
     for (int q = wib; q < 7; q += nw) {
-      const double tq = warp_sum_ldcg(partial + q, (int)gridDim.x, 8, lane);
-      if (lane == 0) s_g[q] = tq;
+      FF b{0.f, 0.f};
+      for (int i = lane; i < (int)gridDim.x; i += 32) {
+        const float2 t = __ldcg(pf + (size_t)i * 8 + q);
+        b = ff_sum(b, FF{t.x, t.y});
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+        b = ff_sum(b, FF{__shfl_xor_sync(0xffffffffu, b.hi, o), __shfl_xor_sync(0xffffffffu, b.lo, o)});
+      if (lane == 0) {
+        const double sq = q == 0 ? g * dA : q < 3 ? dA : q < 6 ? g / dth : g * (ds * Fm * ell);
+        s_g[8 * 8 + q] = ((double)b.hi + (double)b.lo) * sq;
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       double t[7];
-      for (int q = 0; q < 7; ++q) t[q] = s_g[q];
+      for (int q = 0; q < 7; ++q) t[q] = s_g[8 * 8 + q];
       prm->scalars[0] = t[0];
       prm->scalars[1] = t[1];
       prm->scalars[2] = t[2];
@@ -383,6 +499,46 @@ __global__ void k_moments(const T* psi, const T* mb, const T* mf, const T* c,
       prm->scalars[6] = t[3];
       prm->scalars[7] = t[4];
       prm->sum_psi = t[5];
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 7; ++q) gs[q] = warp_sum(gs[q]);
+    // per block in warp order, then the last block adds the block partials in a
+    // fixed order (warp q of that block sums quantities q, q + nw, ...)
+    if (lane == 0)
+      for (int q = 0; q < 7; ++q) s_g[wib * 8 + q] = gs[q];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < 7; ++q) {
+        double b = s_g[q];
+        for (int w2 = 1; w2 < nw; ++w2) b += s_g[w2 * 8 + q];
+        partial[(size_t)blockIdx.x * 8 + q] = b;
+      }
+      __threadfence();
+      const unsigned int prev = atomicInc(&prm->counter2, gridDim.x - 1);
+      s_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last) {
+      __threadfence();
+      for (int q = wib; q < 7; q += nw) {
+        const double tq = warp_sum_ldcg(partial + q, (int)gridDim.x, 8, lane);
+        if (lane == 0) s_g[q] = tq;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t[7];
+        for (int q = 0; q < 7; ++q) t[q] = s_g[q];
+        prm->scalars[0] = t[0];
+        prm->scalars[1] = t[1];
+        prm->scalars[2] = t[2];
+        prm->scalars[3] = t[1] + t[2];
+        prm->scalars[4] = sqrt(t[3] * t[3] + t[4] * t[4]) / t[5];
+        prm->scalars[5] = t[6] / (double)ncells;
+        prm->scalars[6] = t[3];
+        prm->scalars[7] = t[4];
+        prm->sum_psi = t[5];
+      }
     }
   }
 }
@@ -497,7 +653,7 @@ cudaError_t launch_moments(const T* psi, const T* mb, const T* mf, const T* c,
       if (e != cudaSuccess) return e;
     }
     kern<<<nblocks, block, smem, s>>>(psi, mb, mf, c, trig, ncells, nth, ns, seg, dth, ds, L, dA,
-                                      fields, partial, prm);
+                                      (float)(0.5 * ds), fields, partial, prm);
     return cudaGetLastError();
   };
   if constexpr (sizeof(T) == 4)

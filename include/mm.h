@@ -73,8 +73,10 @@ typedef enum {
   MM_FP32_MIXED = 1  /* Mb, psi, u and the per-cell motor densities stored
                         and stepped in float32 (the paper's mixed precision,
                         Sec. 3.1); the s-reductions feeding the force and
-                        force dipole (compensated), the moments, the global
-                        sums and the mass correction in float64 */
+                        force dipole and the moments in compensated
+                        float-float (about 48 bits), returned in float64;
+                        the global sums of the substep and the mass
+                        correction in float64 */
 } mm_precision;
 
 typedef enum {

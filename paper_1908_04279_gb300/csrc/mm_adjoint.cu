@@ -598,19 +598,37 @@ __device__ __forceinline__ void motor_rows(const T (&M)[V], T (&L)[V], T psi1, T
   }
 }
 
+// In float32 the six float64 scalars are converted by one instruction for the
+// warp (lane q converts value q, then shuffles), as in psi_adj_const; dt / 2
+// is formed after the conversion (halving is exact either way). Called by the
+// whole warp.
 template <typename T>
 __device__ __forceinline__ MotorConst<T> motor_const(const AdjArgs<T>& a) {
   MotorConst<T> m;
-  const double dt64 = *a.dt;
-  m.dt = (T)dt64;
-  m.hdt = (T)(0.5 * dt64);
-  m.cw = (T)a.cw;
-  m.koff = (T)a.k_off;
-  m.kon = (T)a.k_on;
+  if constexpr (sizeof(T) == 4) {
+    const int lane = threadIdx.x & 31;
+    const double v = lane == 0 ? *a.dt : lane == 1 ? a.cw : lane == 2 ? a.k_off
+                   : lane == 3 ? a.k_on : lane == 4 ? a.ds : a.dth;
+    const float x = (float)v;
+    m.dt = __shfl_sync(0xffffffffu, x, 0);
+    m.hdt = 0.5f * m.dt;
+    m.cw = __shfl_sync(0xffffffffu, x, 1);
+    m.koff = __shfl_sync(0xffffffffu, x, 2);
+    m.kon = __shfl_sync(0xffffffffu, x, 3);
+    m.ds = __shfl_sync(0xffffffffu, x, 4);
+    m.dth = __shfl_sync(0xffffffffu, x, 5);
+  } else {
+    const double dt64 = *a.dt;
+    m.dt = dt64;
+    m.hdt = 0.5 * dt64;
+    m.cw = a.cw;
+    m.koff = a.k_off;
+    m.kon = a.k_on;
+    m.ds = a.ds;
+    m.dth = a.dth;
+  }
   m.c1 = m.hdt * m.cw;
   m.c2 = T(1) - m.hdt * m.koff;
-  m.ds = (T)a.ds;
-  m.dth = (T)a.dth;
   return m;
 }
 
@@ -629,15 +647,16 @@ __device__ __forceinline__ void close_unit(const AdjArgs<T>& a, MotorAcc<T>& acc
 }
 
 // The warp's parameter adjoints into its float64 slot (reduced over the warp
-// in the state precision, then added in float64; dR/dv_walk = D / ds).
+// in the state precision, then added in float64; dR/dv_walk = D / ds). Lane q
+// adds parameter q, so each float64 operation is one instruction for all three.
 template <typename T>
 __device__ __forceinline__ void flush_params(const AdjArgs<T>& a, const MotorAcc<T>& acc, int lane,
                                              int gw) {
   const T gk = warp_sum_t(acc.gk), gv = warp_sum_t(acc.gv), gn = warp_sum_t(acc.gn);
-  if (lane == 0) {
-    a.gpart[(size_t)gw * 4 + 0] += (double)gk;
-    a.gpart[(size_t)gw * 4 + 1] += (double)gv * a.inv_ds;
-    a.gpart[(size_t)gw * 4 + 2] += (double)gn;
+  if (lane < 3) {
+    const T x = lane == 0 ? gk : lane == 1 ? gv : gn;
+    const double d = lane == 1 ? (double)x * a.inv_ds : (double)x;
+    a.gpart[(size_t)gw * 4 + lane] += d;
   }
 }
 

@@ -210,4 +210,44 @@ __device__ __forceinline__ double warp_sum_ldcg(const double* p, int n, int stri
   return warp_sum(((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])));
 }
 
+
+// Float-float values carried in a float2 (x: high part, y: low part), for the
+// float32 form's end-of-launch sums: GB300's float64 pipe runs at 1/64 of the
+// float32 rate and a float64 warp instruction costs it the same however few
+// lanes are active, so a serial tail of float64 additions on one SM delays
+// every launch; these run on the float32 pipe (TwoSum of the high parts).
+__device__ __forceinline__ float2 ff2_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  return make_float2(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 warp_sum_ff2(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = ff2_add(v, make_float2(__shfl_xor_sync(0xffffffffu, v.x, o),
+                               __shfl_xor_sync(0xffffffffu, v.y, o)));
+  return v;
+}
+// warp_sum_ldcg for float-float pairs p[0..n-1] (stride 1): the same loads in
+// flight and the same fixed combination order.
+__device__ __forceinline__ float2 warp_sum_ldcg_ff2(const float2* p, int n, int lane) {
+  float2 s[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s[q] = make_float2(0.f, 0.f);
+  int b = lane;
+  for (; b + 7 * 32 < n; b += 8 * 32) {
+    float2 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = __ldcg(p + b + q * 32);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s[q] = ff2_add(s[q], v[q]);
+  }
+#pragma unroll
+  for (int q = 0; q < 7; ++q)
+    if (b + q * 32 < n) s[q] = ff2_add(s[q], __ldcg(p + b + q * 32));
+  return warp_sum_ff2(ff2_add(ff2_add(ff2_add(s[0], s[1]), ff2_add(s[2], s[3])),
+                              ff2_add(ff2_add(s[4], s[5]), ff2_add(s[6], s[7]))));
+}
+
 }  // namespace mm

@@ -245,26 +245,53 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
     }
   }
   // sum psi^{n+1} as in k_substep: per warp, per block, then the last block
+  // (float-float in the float32 form)
   __shared__ double s_red[32];
   __shared__ unsigned int s_last;
-  const double m = warp_sum_ff(mass_hi, mass_lo);
-  if (lane == 0) s_red[wib] = m;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double b = s_red[0];
-    for (int q = 1; q < (int)(blockDim.x >> 5); ++q) b += s_red[q];
-    a.partial[blockIdx.x] = b;
-    __threadfence();
-    const unsigned int prev = atomicInc(&a.prm->counter, gridDim.x - 1);
-    s_last = prev == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (s_last && wib == 0) {
-    __threadfence();
-    const double tot = warp_sum_ldcg(a.partial, (int)gridDim.x, 1, lane);
-    if (lane == 0) {
-      a.prm->mass = tot;
-      if (MASSCORR && a.mass_correct) a.prm->psi_scale = a.prm->mass0 / tot;
+  if constexpr (sizeof(T) == 4) {
+    float2* s_red2 = reinterpret_cast<float2*>(s_red);
+    const float2 wsum = warp_sum_ff2(make_float2(mass_hi, mass_lo));
+    if (lane == 0) s_red2[wib] = wsum;
+    __syncthreads();
+    float2* part2 = reinterpret_cast<float2*>(a.partial);
+    if (threadIdx.x == 0) {
+      float2 b = s_red2[0];
+      for (int q = 1; q < (int)(blockDim.x >> 5); ++q) b = ff2_add(b, s_red2[q]);
+      part2[blockIdx.x] = b;
+      __threadfence();
+      const unsigned int prev = atomicInc(&a.prm->counter, gridDim.x - 1);
+      s_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && wib == 0) {
+      __threadfence();
+      const float2 m2 = warp_sum_ldcg_ff2(part2, (int)gridDim.x, lane);
+      if (lane == 0) {
+        const double tot = (double)m2.x + (double)m2.y;
+        a.prm->mass = tot;
+        if (MASSCORR && a.mass_correct) a.prm->psi_scale = a.prm->mass0 / tot;
+      }
+    }
+  } else {
+    const double m = warp_sum_ff(mass_hi, mass_lo);
+    if (lane == 0) s_red[wib] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double b = s_red[0];
+      for (int q = 1; q < (int)(blockDim.x >> 5); ++q) b += s_red[q];
+      a.partial[blockIdx.x] = b;
+      __threadfence();
+      const unsigned int prev = atomicInc(&a.prm->counter, gridDim.x - 1);
+      s_last = prev == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && wib == 0) {
+      __threadfence();
+      const double tot = warp_sum_ldcg(a.partial, (int)gridDim.x, 1, lane);
+      if (lane == 0) {
+        a.prm->mass = tot;
+        if (MASSCORR && a.mass_correct) a.prm->psi_scale = a.prm->mass0 / tot;
+      }
     }
   }
 }

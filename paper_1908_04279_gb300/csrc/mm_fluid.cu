@@ -261,9 +261,18 @@ mm_status mm_fluid_setup(mm_handle* h, double eps, double z0) {
   const long long nm = fluid_modes(h);
   const int np = (int)fluid_pitch(h);
   if (!h->fl_tab) {
-    CK(cudaMalloc((void**)&h->fl_tab, (size_t)nm * 16));
-    CK(cudaMalloc((void**)&h->fl_hat, (size_t)nm * 16 * 10));
-    CK(cudaMalloc((void**)&h->fl_real, (size_t)np * 8 * 10));
+    // all or nothing: a failure frees what this call allocated
+    const size_t need = (size_t)nm * 16 * 11 + (size_t)np * 8 * 10;
+    size_t freeb = 0, totalb = 0;
+    CK(cudaMemGetInfo(&freeb, &totalb));
+    if (need + (64u << 20) > freeb) return fail(h, MM_ERR_OOM, "fluid buffers do not fit");
+    cudaError_t ae = cudaMalloc((void**)&h->fl_tab, (size_t)nm * 16);
+    if (ae == cudaSuccess) ae = cudaMalloc((void**)&h->fl_hat, (size_t)nm * 16 * 10);
+    if (ae == cudaSuccess) ae = cudaMalloc((void**)&h->fl_real, (size_t)np * 8 * 10);
+    if (ae != cudaSuccess) {
+      fluid_free(h);
+      return cuda_fail(h, "cudaMalloc (fluid buffers)", ae);
+    }
     // explicit embeddings: with NULL ones cuFFT takes the packed layout and
     // ignores the distances between batches
     int n[2] = {ny, nx}, real_e[2] = {ny, nx}, cplx_e[2] = {ny, nxh};

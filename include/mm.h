@@ -304,7 +304,9 @@ mm_status mm_set_anchors(mm_handle* h, int enable);
  * solution in z of the transformed Eq. 7-9 (the limit of the paper's z-grid).
  * P0 scales the pressure only and does not enter. Needs nx, ny >= 2
  * (MM_ERR_UNSUPPORTED otherwise, and on a batch member); plans three batched
- * float64 cuFFT transforms. May be called again with new eps, z0.
+ * float64 cuFFT transforms and allocates about 176 bytes per mode of the half
+ * spectrum plus 80 bytes per cell, all or nothing (MM_ERR_OOM if they do not
+ * fit). May be called again with new eps, z0 (the buffers are kept).
  *
  * mm_fluid_solve(h, sigma, sigma_on_device, dipole, u_out, u_out_on_device):
  *   1. the moments of the current state (as mm_moments; F = fields 7, 8);

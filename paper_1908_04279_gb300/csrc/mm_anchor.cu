@@ -607,6 +607,7 @@ mm_status anchor_force(mm_handle* h) {
 extern "C" {
 
 mm_status mm_set_anchors(mm_handle* h, int enable) {
+  MM_TRACE("mm_set_anchors");
   if (!h) return MM_ERR_INVALID;
   if (h->batch || h->owner)
     return fail(h, MM_ERR_UNSUPPORTED, "non-local anchors are not available in a batch");

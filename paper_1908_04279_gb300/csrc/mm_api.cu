@@ -350,6 +350,7 @@ extern "C" {
 
 mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision prec, void* stream,
                     mm_handle** out) {
+  MM_TRACE("mm_create");
   g_create_error.clear();
   if (!grid || !out) return fail(nullptr, MM_ERR_INVALID, "grid or out is NULL");
   *out = nullptr;
@@ -537,6 +538,7 @@ mm_status mm_set_stream(mm_handle* h, void* stream) {
 }
 
 mm_status mm_set_rates(mm_handle* h, const mm_rates* rates) {
+  MM_TRACE("mm_set_rates");
   if (!h) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   mm_status st = check_rates(rates, h);
@@ -558,6 +560,7 @@ mm_status mm_set_rates(mm_handle* h, const mm_rates* rates) {
 
 mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const double* mtot,
                        int on_device) {
+  MM_TRACE("mm_set_state");
   if (!h) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   if (!psi) return fail(h, MM_ERR_INVALID, "psi is NULL");
@@ -595,6 +598,7 @@ mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const 
 
 mm_status mm_get_state(mm_handle* h, double* psi, double* mb, double* mf, double* c,
                        int on_device) {
+  MM_TRACE("mm_get_state");
   if (!h) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   DeviceGuard dg(h->device);
@@ -609,6 +613,7 @@ mm_status mm_get_state(mm_handle* h, double* psi, double* mb, double* mf, double
 }
 
 mm_status mm_set_velocity(mm_handle* h, const double* u, int on_device) {
+  MM_TRACE("mm_set_velocity");
   if (!h) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   if (!u) return fail(h, MM_ERR_INVALID, "u is NULL");
@@ -689,6 +694,7 @@ mm_status mm_set_dt(mm_handle* h, double dt) {
 }
 
 mm_status mm_micro_step(mm_handle* h, int n) {
+  MM_TRACE("mm_micro_step");
   if (!h) return MM_ERR_INVALID;
   if (n < 0) return fail(h, MM_ERR_INVALID, "n_substeps < 0");
   if (n == 0) return MM_OK;
@@ -745,6 +751,7 @@ mm_status launch_substeps(mm_handle* h, int n) {
 extern "C" {
 
 mm_status mm_diffuse(mm_handle* h, double D_t, double D_r, double dt) {
+  MM_TRACE("mm_diffuse");
   if (!h) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   if (!std::isfinite(D_t) || !std::isfinite(D_r) || D_t < 0.0 || D_r < 0.0)
@@ -790,6 +797,7 @@ mm_status mm_diffuse(mm_handle* h, double D_t, double D_r, double dt) {
 }
 
 mm_status mm_moments(mm_handle* h, mm_moments_out* out) {
+  MM_TRACE("mm_moments");
   if (!h || !out) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   DeviceGuard dg(h->device);
@@ -1129,6 +1137,7 @@ mm_status mm_set_checkpointing(mm_handle* h, int K, int max_substeps) {
 }
 
 mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_substeps) {
+  MM_TRACE("mm_set_checkpointing_levels");
   if (!h) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   DeviceGuard dg(h->device);
@@ -1243,6 +1252,7 @@ mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_
 }
 
 mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_adjoint_out* out) {
+  MM_TRACE("mm_adjoint_step");
   if (!h || !seed || !out) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   Recording& R = h->rec;

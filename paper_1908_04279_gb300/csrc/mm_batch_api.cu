@@ -344,6 +344,7 @@ extern "C" {
 
 mm_status mm_create_batch(int n, const mm_grid* grids, const mm_rates* rates, mm_precision prec,
                           void* stream, mm_handle** out) {
+  MM_TRACE("mm_create_batch");
   g_create_error.clear();
   if (!out) return fail(nullptr, MM_ERR_INVALID, "out is NULL");
   *out = nullptr;
@@ -424,6 +425,7 @@ mm_status mm_batch_member(mm_handle* h, int i, mm_handle** member) {
 
 mm_status mm_batch_autotune(mm_handle* h, int substeps, mm_batch_tune* results, int max_results,
                             int* n_results) {
+  MM_TRACE("mm_batch_autotune");
   if (!h) return MM_ERR_INVALID;
   if (!h->batch) return fail(h, MM_ERR_INVALID, "not a batch handle");
   if (substeps < 1) return fail(h, MM_ERR_INVALID, "substeps >= 1");

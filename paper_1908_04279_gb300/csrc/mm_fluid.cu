@@ -249,6 +249,7 @@ void fluid_free(mm_handle* h) {
 extern "C" {
 
 mm_status mm_fluid_setup(mm_handle* h, double eps, double z0) {
+  MM_TRACE("mm_fluid_setup");
   if (!h) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   if (h->owner) return fail(h, MM_ERR_UNSUPPORTED, "the fluid solve is not available to batch members");
@@ -303,6 +304,7 @@ mm_status mm_fluid_setup(mm_handle* h, double eps, double z0) {
 
 mm_status mm_fluid_solve(mm_handle* h, const double* sigma, int sigma_on_device, int dipole,
                          double* u_out, int u_out_on_device) {
+  MM_TRACE("mm_fluid_solve");
   if (!h) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   if (!h->fluid) return fail(h, MM_ERR_STATE, "no fluid set-up: call mm_fluid_setup first");

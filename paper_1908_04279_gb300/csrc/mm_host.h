@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "mm_internal.cuh"
 
 using mm::DevParams;
@@ -181,6 +183,16 @@ inline mm_status cuda_fail(mm_handle* h, const char* what, cudaError_t e) {
   return fail(h, MM_ERR_CUDA, std::string(what) + ": " + cudaGetErrorName(e) + " (" +
                                   cudaGetErrorString(e) + ")");
 }
+
+// NVTX range over one ABI call, for Nsight tools' timelines and range filters
+// (header-only NVTX 3; a no-op when no tool is attached).
+struct TraceRange {
+  explicit TraceRange(const char* name) { nvtxRangePushA(name); }
+  ~TraceRange() { nvtxRangePop(); }
+  TraceRange(const TraceRange&) = delete;
+  TraceRange& operator=(const TraceRange&) = delete;
+};
+#define MM_TRACE(name) ::mmh::TraceRange mm_trace_range_(name)
 
 #define CK(...)                                               \
   do {                                                        \

@@ -337,6 +337,7 @@ extern "C" {
 
 mm_status mm_motor_local(mm_handle* h, double T, const int* nsteps_in, int* nsteps_out,
                          int on_device) {
+  MM_TRACE("mm_motor_local");
   if (!h) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   if (!finite_pos(T)) return fail(h, MM_ERR_INVALID, "T must be finite and > 0");

@@ -11,7 +11,12 @@
 #include <string>
 #include <vector>
 
+#if __has_include(<nvtx3/nvToolsExt.h>)
 #include <nvtx3/nvToolsExt.h>
+#define MM_HAVE_NVTX 1
+#else
+#define MM_HAVE_NVTX 0
+#endif
 
 #include "mm_internal.cuh"
 
@@ -185,10 +190,15 @@ inline mm_status cuda_fail(mm_handle* h, const char* what, cudaError_t e) {
 }
 
 // NVTX range over one ABI call, for Nsight tools' timelines and range filters
-// (header-only NVTX 3; a no-op when no tool is attached).
+// (header-only NVTX 3; a no-op when no tool is attached, and compiled out
+// where the toolkit has no NVTX headers).
 struct TraceRange {
+#if MM_HAVE_NVTX
   explicit TraceRange(const char* name) { nvtxRangePushA(name); }
   ~TraceRange() { nvtxRangePop(); }
+#else
+  explicit TraceRange(const char*) {}
+#endif
   TraceRange(const TraceRange&) = delete;
   TraceRange& operator=(const TraceRange&) = delete;
 };

@@ -778,3 +778,48 @@ def test_anchor_brute_force_agrees(oracle_mod, dims):
     np.testing.assert_allclose(st.c, np.array(bc), rtol=1e-12, atol=1e-14)
     clipped = np.array(bc) == before.mtot
     assert np.any(clipped) and not np.all(clipped)  # the scale-down acted in some cells
+
+
+@pytest.mark.parametrize("dims", [(3, 2, 16, 8), (5, 4, 7, 5), (2, 3, 12, 11)])
+def test_moments_brute_force(oracle_mod, dims):
+    """Every moment field and global scalar on a random state with non-symmetric
+    psi and rows, against its definition summed directly (numpy): rho, P, Q
+    (xx, xy), C, Mf, F = F_m sum_k p psi n_b dtheta (Eq. 10 with anchors in the
+    cell), sigma_a = F_m ell sum_k p p psi m1 dtheta with n_b = sum_j Mb ds and
+    m1 = sum_j s_j Mb ds at s_j = -L/2 + (j + 1/2) ds, theta_k = k dtheta."""
+    O = oracle_mod
+    g = Grid(*dims, L=1.3)
+    r = Rates(force_scale=0.8, ell=1.4)
+    rng = np.random.default_rng(sum(dims))
+    psi = rng.random((g.ny, g.nx, g.ntheta))
+    mb = 0.1 * rng.random((g.ny, g.nx, g.ntheta, g.ns))
+    st = O.make_state(g, psi, mb, mtot=rng.random((g.ny, g.nx)) + 0.5)
+    f, sc = O.moments(g, r, st)
+    dth, ds = TWO_PI / g.ntheta, g.L / g.ns
+    th = np.arange(g.ntheta) * dth
+    c, s = np.cos(th), np.sin(th)
+    sj = -g.L / 2 + (np.arange(g.ns) + 0.5) * ds
+    nb = st.mb.sum(-1) * ds
+    m1 = (st.mb * sj).sum(-1) * ds
+    P = st.psi
+    ref = {
+        "rho": P.sum(-1) * dth,
+        "Px": (P * c).sum(-1) * dth, "Py": (P * s).sum(-1) * dth,
+        "Qxx": (P * (c * c - 0.5)).sum(-1) * dth, "Qxy": (P * c * s).sum(-1) * dth,
+        "C": st.c, "Mf": st.mf,
+        "Fx": 0.8 * (P * nb * c).sum(-1) * dth, "Fy": 0.8 * (P * nb * s).sum(-1) * dth,
+        "Sxx": 0.8 * 1.4 * (P * m1 * c * c).sum(-1) * dth,
+        "Sxy": 0.8 * 1.4 * (P * m1 * c * s).sum(-1) * dth,
+        "Syy": 0.8 * 1.4 * (P * m1 * s * s).sum(-1) * dth,
+    }
+    for k, v in ref.items():
+        assert np.allclose(f[k], v, rtol=1e-12, atol=1e-15), k
+    dA = 1.0 / (g.nx * g.ny)
+    sum_cos, sum_sin = (P * c).sum(), (P * s).sum()
+    ref_sc = {"N_psi": P.sum() * dth * dA, "bound": st.c.sum() * dA, "free": st.mf.sum() * dA,
+              "motors": (st.c.sum() + st.mf.sum()) * dA,
+              "polar_order": math.hypot(sum_cos, sum_sin) / P.sum(),
+              "mean_stress": (ref["Sxx"] + ref["Syy"]).mean(),
+              "sum_psi_cos": sum_cos, "sum_psi_sin": sum_sin}
+    for k, v in ref_sc.items():
+        assert sc[k] == pytest.approx(v, rel=1e-12, abs=1e-15), k

@@ -109,6 +109,36 @@ def substep(grid, rates, dt, u, psi, mb, mf, mtot):
     return psi_new, mb_new, mf_new, c_new
 
 
+def head_cell(grid, rates, ix, iy, k, j):
+    """(row, column) of the cell that holds the motor head of node j of a
+    filament centred in cell (ix, iy) with orientation k: the centre plus
+    (l/L) s_j p_k, located on the periodic grid by flooring its coordinates."""
+    nx, ny, nth, ns, L = grid.nx, grid.ny, grid.ntheta, grid.ns, grid.L
+    s = -0.5 * L + (j + 0.5) * (L / ns)
+    th = k * (2.0 * math.pi / nth)
+    hx = (ix + 0.5) / nx + rates.ell * s * math.cos(th)
+    hy = (iy + 0.5) / ny + rates.ell * s * math.sin(th)
+    return int(math.floor(hy * ny)) % ny, int(math.floor(hx * nx)) % nx
+
+
+def anchor_force(grid, rates, psi, mb):
+    """Eq. 10 with the delta at the motor head: every node of every row puts
+    its own force F p psi Mb_j ds dtheta into the cell under its own head.
+    Returns [Fx, Fy] as nested lists [c][iy][ix]."""
+    nx, ny, nth, ns, L = grid.nx, grid.ny, grid.ntheta, grid.ns, grid.L
+    dth, ds = 2.0 * math.pi / nth, L / ns
+    F = [[[0.0] * nx for _ in range(ny)] for _ in range(2)]
+    for iy in range(ny):
+        for ix in range(nx):
+            for k in range(nth):
+                for j in range(ns):
+                    hy, hx = head_cell(grid, rates, ix, iy, k, j)
+                    w = rates.force_scale * psi[iy][ix][k] * mb[iy][ix][k][j] * ds * dth
+                    F[0][hy][hx] += w * math.cos(k * dth)
+                    F[1][hy][hx] += w * math.sin(k * dth)
+    return F
+
+
 def substep_anchor(grid, rates, dt, u, psi, mb, mf, mtot):
     """One substep with non-local motor anchors: a motor bound at node j of a
     filament in cell (ix, iy) with orientation k is anchored in the cell that
@@ -123,10 +153,7 @@ def substep_anchor(grid, rates, dt, u, psi, mb, mf, mtot):
     psi_new = substep(grid, rates, dt, u, psi, mb, mf, mtot)[0]
 
     def anchor(ix, iy, k, j):
-        s = -0.5 * L + (j + 0.5) * ds
-        hx = (ix + 0.5) / nx + rates.ell * s * math.cos(k * dth)
-        hy = (iy + 0.5) / ny + rates.ell * s * math.sin(k * dth)
-        return int(math.floor(hy * ny)) % ny, int(math.floor(hx * nx)) % nx
+        return head_cell(grid, rates, ix, iy, k, j)
 
     def rhs(M, mfree):
         out = []

@@ -780,6 +780,80 @@ def test_anchor_brute_force_agrees(oracle_mod, dims):
     assert np.any(clipped) and not np.all(clipped)  # the scale-down acted in some cells
 
 
+@pytest.mark.parametrize("dims,ell", [((5, 4, 8, 6), 0.43), ((4, 6, 6, 9), 0.9),
+                                      ((7, 5, 5, 7), 1.7)])
+def test_anchor_force_brute_force_deposit(oracle_mod, dims, ell):
+    """Eq. 10 with the delta at the head x + (l/L) s p: an independent deposit
+    (each node's head located from its own geometry on the grid, not from the
+    oracle's offset table) agrees with the anchored force at l/L > 0, on heads
+    that cross several cells and, at l/L = 1.7, wrap around the periodic grid.
+    Fails for a force put in the filament's own cell, for one anchor used for
+    a whole row, or for swapped x and y offsets."""
+    g = Grid(*dims)
+    r = Rates(ell=ell, force_scale=0.7)
+    rng = np.random.default_rng(sum(dims) + 131)
+    psi = rng.random((g.ny, g.nx, g.ntheta))
+    mb = rng.random((g.ny, g.nx, g.ntheta, g.ns))
+    st = oracle_mod.make_state_anchor(g, r, psi, mb, np.full((g.ny, g.nx), 1e9))
+    F = oracle_mod.anchor_force(g, r, st)
+    B = np.array(brute_force.anchor_force(g, r, st.psi.tolist(), st.mb.tolist()))
+    np.testing.assert_allclose(F, B, rtol=1e-13, atol=1e-15)
+    # the heads really leave the filament's cell: the local force field differs
+    fl, _ = oracle_mod.moments(g, r, st)
+    assert np.max(np.abs(F[0] - fl["Fx"])) > 1e-3 * np.max(np.abs(fl["Fx"]))
+
+
+def test_anchor_force_total_is_the_local_total(oracle_mod):
+    """Moving each node's force to the cell under its head moves it but does
+    not change it: summed over the grid the anchored force equals the sum of
+    the local force field F_m sum_k p psi n_b dtheta (Eq. 10), at any l/L.
+    Fails for a dropped node, a wrong sign of p or a missing ds or dtheta."""
+    g = Grid(9, 7, 12, 10)
+    rng = np.random.default_rng(141)
+    psi = rng.random((g.ny, g.nx, g.ntheta))
+    mb = rng.random((g.ny, g.nx, g.ntheta, g.ns))
+    for ell in (0.0, 0.21, 0.66, 2.3):
+        r = Rates(ell=ell, force_scale=1.3)
+        st = oracle_mod.make_state_anchor(g, r, psi, mb, np.full((g.ny, g.nx), 1e9))
+        F = oracle_mod.anchor_force(g, r, st)
+        fl, _ = oracle_mod.moments(g, r, st)
+        assert abs(F[0].sum() - fl["Fx"].sum()) <= 1e-13 * np.abs(fl["Fx"]).sum()
+        assert abs(F[1].sum() - fl["Fy"].sum()) <= 1e-13 * np.abs(fl["Fy"]).sum()
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 3])
+def test_anchor_force_single_filament_closed_form(oracle_mod, k):
+    """One filament density psi0 in one cell with orientation theta_k = k pi/2
+    and a linear row M_j = a + b s_j, on a 6 x 6 grid with 12 nodes and
+    l/L = 1/2. The head sits 0.5 + 3 s_j cells along p from the cell's lower
+    edge, so nodes 0-3 land one cell behind, 4-7 in the cell, 8-11 one cell
+    ahead (no node on a cell edge). With s_j = -1/2 + (j + 1/2)/12 the node
+    sums are sum_{0-3} s_j = -4/3, sum_{4-7} s_j = 0, sum_{8-11} s_j = 4/3, so
+    the three cells get F_m psi0 ds dtheta p (4a - 4b/3), (4a), (4a + 4b/3)
+    and every other cell nothing."""
+    g = Grid(6, 6, 4, 12)
+    r = Rates(ell=0.5, force_scale=0.7)
+    a, b, psi0 = 0.3, 0.4, 2.5
+    iy0, ix0 = 2, 3
+    ds, dth = g.L / g.ns, TWO_PI / g.ntheta
+    sj = -0.5 + (np.arange(g.ns) + 0.5) / g.ns
+    psi = np.zeros((g.ny, g.nx, g.ntheta))
+    psi[iy0, ix0, k] = psi0
+    mb = np.zeros((g.ny, g.nx, g.ntheta, g.ns))
+    mb[iy0, ix0, k] = a + b * sj
+    st = oracle_mod.make_state_anchor(g, r, psi, mb, np.full((g.ny, g.nx), 1e9))
+    F = oracle_mod.anchor_force(g, r, st)
+    step = [(1, 0), (0, 1), (-1, 0), (0, -1)][k]  # p_k rounded to the grid
+    w = r.force_scale * psi0 * ds * dth
+    expect = np.zeros((2, g.ny, g.nx))
+    for back_or_ahead, total in ((-1, 4 * a - 4 * b / 3), (0, 4 * a), (1, 4 * a + 4 * b / 3)):
+        cy = (iy0 + back_or_ahead * step[1]) % g.ny
+        cx = (ix0 + back_or_ahead * step[0]) % g.nx
+        expect[0, cy, cx] = w * total * step[0]
+        expect[1, cy, cx] = w * total * step[1]
+    np.testing.assert_allclose(F, expect, rtol=0, atol=1e-14)
+
+
 @pytest.mark.parametrize("dims", [(3, 2, 16, 8), (5, 4, 7, 5), (2, 3, 12, 11)])
 def test_moments_brute_force(oracle_mod, dims):
     """Every moment field and global scalar on a random state with non-symmetric

@@ -100,6 +100,10 @@ mm_status mm_create(const mm_grid* grid, const mm_rates* rates, mm_precision pre
                     void* stream, mm_handle** out);
 mm_status mm_destroy(mm_handle* h);
 mm_status mm_set_stream(mm_handle* h, void* stream);
+/* Replace the rates (checked as in mm_create). Synchronises the handle's
+ * stream. New rates end an adjoint recording (mm_set_checkpointing): the
+ * substeps recorded so far ran with the old rates, so a later mm_adjoint_step
+ * returns MM_ERR_STATE until a new recording is made. */
 mm_status mm_set_rates(mm_handle* h, const mm_rates* rates);
 
 /* Load a state. psi (required), mb (NULL: all zero), mtot (NULL: all one).
@@ -410,10 +414,17 @@ const char* mm_last_error(const mm_handle* h);
  *   synchronises before reading the outputs).
  * Scratch is one file-scope device array of 65536 cell records (4 MiB) that
  * every GPU loading the library holds until exit: grids above 65536 cells are
- * rejected with MM_ERR_UNSUPPORTED. The first call on a device looks up that
- * array's device address (once per device, with that device current), so it
- * should come before any stream capture. All calls share the array: calls
- * that overlap on the GPU race. Errors: mm_last_error(NULL). */
+ * rejected with MM_ERR_UNSUPPORTED. The array is placed on a device when the
+ * library's device code is loaded there: with CUDA's default lazy module
+ * loading that is the first call on that device (with
+ * CUDA_MODULE_LOADING=EAGER, when the process first uses the device), and
+ * that first placement does take 4 MiB of device memory. A caller that
+ * reserves the GPU's memory for its own pool should therefore make one call
+ * before reserving it; later calls allocate nothing. The first call on a
+ * device also looks up the array's device address (once per device, with that
+ * device current), so it should come before any stream capture. All calls
+ * share the array: calls that overlap on the GPU race. Errors:
+ * mm_last_error(NULL). */
 mm_status mm_moments_static(const mm_grid* grid, const mm_rates* rates, const double* psi,
                             const double* mb, const double* mf, const double* c, double* fields,
                             double* scalars, void* stream);

@@ -374,8 +374,8 @@ __global__ void __launch_bounds__(128, adj_psi_min_blocks<T>()) k_adj_psi_ring(c
     // record the failure; wait (bounded) for the copies this warp issued
     if (lane == 0) {
       atomicOr(&a.prm->status, 1);
-      (void)mbar_wait(&bars[sidx], par[sidx], kDrainLimit);
-      if (pending_next) (void)mbar_wait(&bars[sidx ^ 1], par[sidx ^ 1], kDrainLimit);
+      drain_wait(&bars[sidx], par[sidx], &a.prm->status);
+      if (pending_next) drain_wait(&bars[sidx ^ 1], par[sidx ^ 1], &a.prm->status);
     }
     __syncwarp();
   }
@@ -906,7 +906,7 @@ __global__ void __launch_bounds__(128, adj_min_blocks<T, V>())
       int st = fail_stage;
       uint32_t pp = fail_par;
       for (int i = 0; i < fail_left; ++i) {
-        (void)mbar_wait(&bars[st], pp, kDrainLimit);
+        drain_wait(&bars[st], pp, &a.prm->status);
         if (++st == S) {
           st = 0;
           pp ^= 1u;

@@ -239,6 +239,10 @@ mm_status check_status(mm_handle* h) {
     const unsigned int zeros[2] = {0u, 0u};
     CK(cudaMemcpy(&h->prm->status, &zero, sizeof zero, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(&h->prm->counter, zeros, sizeof zeros, cudaMemcpyHostToDevice));
+    if (st & 8)
+      return fail(h, MM_ERR_TIMEOUT,
+                  "a bounded wait in the substep kernel gave up and so did the wait for its copies "
+                  "in flight; the state is invalid and later launches on this device are suspect");
     if (st & 1)
       return fail(h, MM_ERR_TIMEOUT, "a bounded wait in the substep kernel gave up; the state is invalid");
     if (st & 4)
@@ -544,6 +548,9 @@ mm_status mm_set_rates(mm_handle* h, const mm_rates* rates) {
   mm_status st = check_rates(rates, h);
   if (st != MM_OK) return st;
   DeviceGuard dg(h->device);
+  // the substeps recorded so far ran with the old rates, while the replays and
+  // the reverse kernels would read the new ones: new rates end a recording
+  h->rec.active = false;
   h->r = *rates;
   CK(cudaStreamSynchronize(h->stream));
   double v[7] = {rates->v_walk, rates->k_on, rates->k_off, rates->glide,
@@ -1256,7 +1263,7 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
   if (!h || !seed || !out) return MM_ERR_INVALID;
   if (h->batch) return not_for_batch(h);
   Recording& R = h->rec;
-  if (!R.active) return fail(h, MM_ERR_STATE, "no recording: call mm_set_checkpointing first");
+  if (!R.active) return fail(h, MM_ERR_STATE, "no recording: call mm_set_checkpointing first (mm_set_state and mm_set_rates end one)");
   if (n != R.nsub || n < 1)
     return fail(h, MM_ERR_STATE, "n_substeps must equal the substeps recorded");
   if (out->dL_du && out->du_capacity < (int)R.v_ucell.size())

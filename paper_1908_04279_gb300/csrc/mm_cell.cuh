@@ -44,6 +44,16 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     if (i >= limit) return false;
   }
 }
+
+constexpr uint32_t kDrainLimit = 1u << 24;  // polls while draining after a timeout
+
+// After a timeout: wait (bounded) for a copy still in flight into this block's
+// shared memory. If that wait gives up too, the copy may land after the block
+// has left, in shared memory the next block on the SM may own: status bit 3
+// records it, so the host can report that later launches are suspect too.
+__device__ __forceinline__ void drain_wait(uint64_t* bar, uint32_t parity, int* status) {
+  if (!mbar_wait(bar, parity, kDrainLimit)) atomicOr(status, 8);
+}
 // Bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from
 // global to this CTA's shared memory, completing on `bar`.
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
@@ -55,7 +65,6 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
-constexpr uint32_t kDrainLimit = 1u << 24;  // polls while draining after a timeout
 
 // Occupancy target (resident 4-warp blocks per SM, caps registers per thread)
 // and unroll depth of the s-row pass loop.

@@ -23,7 +23,9 @@ struct DevParams {
   double sum_psi;     // sum of psi over all cells and angles (moments kernel)
   unsigned int counter;   // last-warp-done counter of the substep kernel
   unsigned int counter2;  // last-block-done counter of the moments kernel
-  int status;             // bit 0: a bounded device wait gave up; bit 1: no valid dt
+  int status;             // bit 0: a bounded device wait gave up; bit 1: no valid dt;
+                          // bit 2: a local substep count out of range; bit 3: the drain
+                          // after a timeout gave up too (copies may still be in flight)
   unsigned int wait_limit;   // polls of an mbarrier before a wait gives up
   unsigned int debug_flags;  // bit 0: wait on a phase nothing completes (tests)
   int pad;

@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(256, 2) k_motor_local(const LocalArgs<T> a) {
       if (tid == 0) {
         atomicOr(&a.prm->status, 1);
         for (int j = it; j < issued; ++j)
-          (void)mbar_wait(&bars[j % nbuf], (uint32_t)((j / nbuf) & 1), kDrainLimit);
+          drain_wait(&bars[j % nbuf], (uint32_t)((j / nbuf) & 1), &a.prm->status);
       }
       return;
     }

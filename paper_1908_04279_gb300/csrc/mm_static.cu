@@ -7,7 +7,10 @@
 // as caller-owned float64 device arrays, writes caller-owned outputs, and
 // keeps its only scratch -- one float64 partial-sum record per cell -- in the
 // file-scope device array below, which every GPU that loads the library holds
-// until the process exits.
+// until the process exits. The array is placed on a device when this module is
+// loaded there, which under CUDA's default lazy module loading is the first
+// call on that device: a caller that reserves the GPU's memory for its own
+// pool makes one call before reserving it.
 //
 // The per-cell records are reduced in a fixed order by a single block, so the
 // scalars do not depend on the launch shape. Every record is rewritten by each

@@ -207,10 +207,10 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
       int st = fail_stage;
       uint32_t pp = fail_par;
       for (int i = 0; i < fail_left; ++i) {
-        (void)mbar_wait(&bars[st], pp, kDrainLimit);
+        drain_wait(&bars[st], pp, &a.prm->status);
         if (++st == S) { st = 0; pp ^= 1u; }
       }
-      if (nb_pending) (void)mbar_wait(nbar, nb_par, kDrainLimit);
+      if (nb_pending) drain_wait(nbar, nb_par, &a.prm->status);
     }
     __syncwarp();
   }

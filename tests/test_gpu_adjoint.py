@@ -218,8 +218,8 @@ def test_fp32_adjoint_close_to_fp64(mmod):
 def test_recording_reuse_is_repeatable(mmod):
     """A second recording with the same K and max_substeps reuses the first
     one's memory (set_state ends a recording and keeps it) and gives the same
-    gradients bit for bit; set_state without a new mm_set_checkpointing leaves
-    no recording to differentiate."""
+    gradients bit for bit; set_state or set_rates without a new
+    mm_set_checkpointing leaves no recording to differentiate."""
     g = Grid(16, 12, 8, 16, L=1.0)
     r = Rates(k_on=1.3, k_off=0.7)
     psi0 = psi_isotropic_perturbed(g, 11, amp=0.2)
@@ -238,6 +238,16 @@ def test_recording_reuse_is_repeatable(mmod):
         sim.set_state(psi0)
         with pytest.raises(RuntimeError):
             sim.adjoint(9, observable="polar_order", n_velocities=2)
+        # new rates end a recording: the substeps taken so far ran with the
+        # old ones, so the reverse sweep is refused rather than mixing them
+        sim.set_state(psi0)
+        sim.set_velocity(u1)
+        sim.set_checkpointing(3, 10)
+        sim.step(4)
+        sim.set_rates(Rates(k_on=1.3, k_off=0.9))
+        with pytest.raises(mmod.MMError) as err:
+            sim.adjoint(4, observable="polar_order")
+        assert mmod.STATUS[err.value.status] == "MM_ERR_STATE"
     for o in outs[1:]:
         assert o["value"] == outs[0]["value"]
         assert np.array_equal(o["dL_du"], outs[0]["dL_du"])

@@ -5,17 +5,21 @@ velocity (mm_set_velocity, which also recomputes the adaptive substep), run its
 substeps (mm_micro_step) and reduce the macroscale moments (mm_moments).
 Metric: micro-state cell-updates per second = nx*ny*ntheta*ns*substeps / time.
 
-Default workload "precision128": 128x128 periodic grid, 32 orientations, 32
-arclength nodes, 50 substeps per macro step, velocity from a seeded random
-divergence-free field (8 Fourier modes, amplitude 0.1) refreshed every macro
-step, mixed precision (float32 Mb/psi, float64 sums). The float64 path is timed
-on the same workload and reported beside it. Beside the main line: the
-adjoint/forward time ratio (adjoint64), the substep on large512 (4.3 GB of
-motor state, the HBM roofline case) in float32 and float64, and the batched
-ensemble (ensemble64, 64 uneven members, 500 substeps per graph).
+Default workload "large512": 512x512 periodic grid, 64 orientations, 64
+arclength nodes (1.07e9 motor cells, 4.29 GB of float32 motor density, 33x the
+L2), 100 substeps per macro step, velocity from a seeded random
+divergence-free field (16 Fourier modes, amplitude 0.2) refreshed every macro
+step, mixed precision (float32 Mb/psi, float64 sums); the default 20 timed
+steps are the workload's 20 macro steps. The float64 path is timed on the same
+workload and reported beside it, with its roofline against the measured
+float64 fused multiply-add rate. Beside the main line: the L2-resident
+precision128 case (128x128 x 32 x 32), the adjoint/forward time ratio
+(adjoint64 and large512), the batched ensemble (ensemble64, 64 uneven members,
+500 substeps per graph), and the next rows (diffusion, anchors, fluid solve,
+local substeps). The last keys of the line are flat summaries of every leg.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload precision128|large512|adjoint64|cellular32]
+                  [--workload large512|precision128|adjoint64|cellular32]
 
 Under torchrun (N > 1) every rank advances its own instance of the workload
 (weak scaling, no collective in the data path); the time is the maximum over
@@ -90,10 +94,14 @@ def whole_job_value(world: int, units_per_rank: float, seconds: float) -> float:
 
 
 def algorithmic_bytes_per_launch(g, tsize: int) -> int:
-    """Bytes one substep launch must move at minimum: Mb read and written once
-    (2 * tsize per motor cell); per (cell, theta) psi read and written
-    (2 * tsize) and n_b read and written (2 * 8); per cell Mf read and written,
-    C written, M read and u read (4 * 8 + 2 * tsize)."""
+    """Bytes one substep launch must move at minimum, with tsize the state
+    precision's size (4 in the float32 form, 8 in float64): Mb read and written
+    once (2 * tsize per motor cell); per (cell, theta) psi read and written
+    (2 * tsize) and n_b read and written (2 * tsize), counted as
+    2 * tsize + 16, which is exact in the float32 form (16 = 4 * 4) and
+    undercounts n_b by 16 bytes per (cell, theta) in float64; per cell 32 bytes
+    for Mf read and written, C written and M read, and 2 * tsize for the
+    cell's velocity."""
     cells = g.nx * g.ny
     return (cells * g.ntheta * g.ns * 2 * tsize + cells * g.ntheta * (2 * tsize + 16)
             + cells * (32 + 2 * tsize))
@@ -109,24 +117,20 @@ def read_peaks():
         return 6800.0, "fallback"
 
 
-# Float32 operations per motor value and substep of the local-step kernel,
-# counted from the scheme: per RK2 stage the backward difference, its half,
-# two sign transfers, two minima, the maximum with zero, the flux fma, the flux
-# difference and two fmas of the stage update (11); two stages, plus one add
-# of the n_b sum.
+# Arithmetic operations per motor value and substep of the row update, counted
+# from the scheme: per RK2 stage the backward difference, its half, two sign
+# transfers, two minima, the maximum with zero, the flux fma, the flux
+# difference and two fmas of the stage update (11); two stages, plus one add of
+# the n_b sum. The local-step kernel runs them on the float32 pipe, the float64
+# substep on the float64 pipe (its per-(cell, theta) transport work, about 40
+# operations per row, adds under 1 per motor value at 64 nodes and is left out).
 LOCAL_OPS = 23
+SUBSTEP_OPS = 23
 
 
 def wname_of(leg: dict) -> str:
     """Workload name of a bench leg from its description."""
     return leg["workload"].split(" ")[0]
-
-
-def alu_peak_tops(sm_mhz: float = 2070.0, sms: int = 152, lanes: int = 128) -> float:
-    """Float32 operations per second of GB300 in Tops/s: 152 SMs x 128 float32
-    lanes x the maximum SM clock (one fma, add, mul, min or max per lane and
-    clock)."""
-    return sms * lanes * sm_mhz * 1e6 / 1e12
 
 
 def read_profile_traffic(kernel: str, workload: str, precision: str, scale: float = 1.0):
@@ -199,25 +203,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def oracle_sample_grid(name: str):
+    """Grid on which the float64 CPU oracle is timed for a workload: the
+    workload's own grid, or for workloads above 2e8 motor cells (large512) a
+    64x64-cell periodic grid with the workload's orientations and arclength
+    nodes (the substep's cost per motor cell does not depend on the number of
+    cells). Returns (grid, label, velocity of macro step 0 on that grid)."""
+    from paper_1908_04279_gb300.inputs import Grid, random_divfree_flow, velocity_seed
+    w = WORKLOADS[name]
+    g = w["grid"]
+    if g.micro_cells <= 2e8:
+        return g, "", workload_velocity(name, 0)
+    gs = Grid(64, 64, g.ntheta, g.ns, g.L)
+    return gs, " on a 64x64-cell sub-grid", random_divfree_flow(gs, velocity_seed(w["seed"], 0),
+                                                                w["modes"], w["amp"])
+
+
 def time_oracle_sample(name: str, budget_s: float = 12.0, max_sub: int = 40):
     """Float64 CPU oracle on a bounded sample of the workload: the workload's
-    initial state and first velocity, as many substeps as fit in budget_s.
-    Workloads above 2e8 motor cells are sampled on a 64x64-cell periodic grid
-    with the workload's orientations and arclength nodes."""
+    initial state and first velocity, as many substeps as fit in budget_s."""
     from oracle import oracle as O
-    from paper_1908_04279_gb300.inputs import Grid
     w = WORKLOADS[name]
-    g, r = w["grid"], Rates()
-    sub = ""
-    if g.micro_cells > 2e8:
-        g = Grid(64, 64, g.ntheta, g.ns, g.L)
-        sub = " on a 64x64-cell sub-grid"
+    r = Rates()
+    g, sub, u = oracle_sample_grid(name)
     st = O.make_state(g, psi_isotropic_perturbed(g, w["seed"]))
-    if sub:
-        from paper_1908_04279_gb300.inputs import random_divfree_flow, velocity_seed
-        u = random_divfree_flow(g, velocity_seed(w["seed"], 0), w["modes"], w["amp"])
-    else:
-        u = workload_velocity(name, 0)
     dt = O.dt(g, r, st, u)
     t0 = time.perf_counter()
     O.run(g, r, st, u, dt, 1)
@@ -238,9 +247,9 @@ def run_reference(args):
     from oracle import oracle as O
     name = args.workload
     w = WORKLOADS[name]
-    g, r = w["grid"], Rates()
+    r = Rates()
+    g, sub, u = oracle_sample_grid(name)
     st = O.make_state(g, psi_isotropic_perturbed(g, w["seed"]))
-    u = workload_velocity(name, 0)
     dt = O.dt(g, r, st, u)
     # a step of the reference arm: one substep of the workload (a bounded
     # sample of its macro step), timed on one host core
@@ -253,15 +262,18 @@ def run_reference(args):
     el = time.perf_counter() - t0
     units = g.micro_cells * per_step * args.steps
     value = units / el
+    wg = w["grid"]
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": name, "grid": f"{g.nx}x{g.ny}", "ntheta": g.ntheta, "ns": g.ns,
-                       "substeps_per_step": per_step},
+            "config": {"workload": name, "grid": f"{wg.nx}x{wg.ny}", "ntheta": wg.ntheta,
+                       "ns": wg.ns, "substeps_per_step": per_step,
+                       "sampled_grid": f"{g.nx}x{g.ny}"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"{args.steps} steps of {per_step} oracle substep(s) of "
-                                       f"{name} on 1 host core"},
+                                       f"{name}{sub} ({g.nx}x{g.ny}x{g.ntheta}x{g.ns}) on 1 "
+                                       f"host core"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -285,25 +297,33 @@ def run_ours(args):
     from paper_1908_04279_gb300 import mm
 
     name = args.workload
-    w = WORKLOADS[name]
-    g, r = w["grid"], Rates()
-    nsub = w["substeps"]
-    n_vel = max(w["macro"], 1)
+    r = Rates()
     stream = torch.cuda.current_stream(dev)
-    vels_host = [np.ascontiguousarray(workload_velocity(name, m)) for m in range(n_vel)]
-    vels_dev = [torch.tensor(v, device=dev) for v in vels_host]
-    psi0 = psi_isotropic_perturbed(g, w["seed"])
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    fields_dev = torch.empty(12 * g.nx * g.ny, dtype=torch.float64, device=dev)
 
-    def device_run(precision, steps, warmup, timed_kernel=True):
+    def inputs_of(wname):
+        w = WORKLOADS[wname]
+        n_vel = max(w["macro"], 1)
+        vh = [np.ascontiguousarray(workload_velocity(wname, m)) for m in range(n_vel)]
+        return w, vh, psi_isotropic_perturbed(w["grid"], w["seed"])
+
+    def device_run(wname, precision, steps, warmup):
+        """Inputs resident in HBM: a step = set_velocity (device array, the
+        macro step's flow) + the workload's substeps + moments into a device
+        buffer. CUDA events per step on the handle's stream; L2 flushed
+        between steps outside the events. Returns (step ms total, substep
+        graph ms total)."""
+        w, vh, psi0 = inputs_of(wname)
+        g, nsub, n_vel = w["grid"], w["substeps"], len(vh)
+        vels = [torch.tensor(v, device=dev) for v in vh]
+        fields = torch.empty(12 * g.nx * g.ny, dtype=torch.float64, device=dev)
         sim = mm.Simulation(g, r, precision, stream=stream.cuda_stream)
         sim.set_state(psi0)
         m = 0
         for _ in range(warmup):
-            sim.set_velocity(vels_dev[m % n_vel]); m += 1
+            sim.set_velocity(vels[m % n_vel]); m += 1
             sim.step(nsub)
-            sim.moments(fields=fields_dev)
+            sim.moments(fields=fields)
         torch.cuda.synchronize(dev)
         if world > 1:
             torch.distributed.barrier()
@@ -313,11 +333,11 @@ def run_ours(args):
             flush.zero_()  # L2 flush between timed steps, outside the timed events
             e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
             e0.record(stream)
-            sim.set_velocity(vels_dev[m % n_vel]); m += 1
+            sim.set_velocity(vels[m % n_vel]); m += 1
             e1.record(stream)
             sim.step(nsub)
             e2.record(stream)
-            sim.moments(fields=fields_dev)
+            sim.moments(fields=fields)
             e3.record(stream)
             e3.synchronize()
             step_ms.append(e0.elapsed_time(e3))
@@ -325,15 +345,19 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         if world > 1:
             torch.distributed.barrier()
+        sim.sync()
         sim.close()
+        del vels, fields
         return sum(step_ms), sum(kern_ms)
 
-    def e2e_run(precision, steps, warmup):
+    def e2e_run(wname, precision, steps, warmup):
         """Through the public API with host buffers: every step copies its
         velocity from pinned host memory and reads the moments back."""
+        w, vh, psi0 = inputs_of(wname)
+        g, nsub, n_vel = w["grid"], w["substeps"], len(vh)
         sim = mm.Simulation(g, r, precision, stream=stream.cuda_stream)
         sim.set_state(psi0)
-        pinned = [torch.from_numpy(v).pin_memory() for v in vels_host]
+        pinned = [torch.from_numpy(v).pin_memory() for v in vh]
         out = torch.empty(12 * g.nx * g.ny, dtype=torch.float64).pin_memory()
         m = 0
         for _ in range(warmup):
@@ -393,30 +417,6 @@ def run_ours(args):
         sim.close()
         return {"forward_ms": best_f, "forward_plus_adjoint_ms": best_a,
                 "adjoint_over_forward": (best_a - best_f) / best_f}
-
-    def large_run(precision, substeps):
-        """large512 (512x512 x 64 x 64, 4.3 GB of float32 Mb): far beyond L2,
-        so its substep launch gives the HBM roofline fraction. Timed as one
-        graph of `substeps` launches after a warm-up graph."""
-        wl = WORKLOADS["large512"]
-        gl = wl["grid"]
-        sim = mm.Simulation(gl, r, precision, stream=stream.cuda_stream)
-        sim.set_state(psi_isotropic_perturbed(gl, wl["seed"]))
-        sim.set_velocity(torch.tensor(workload_velocity("large512", 0), device=dev))
-        sim.step(substeps)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        sim.step(substeps)
-        e1.record(stream)
-        e1.synchronize()
-        sim.sync()
-        sim.close()
-        ms = e0.elapsed_time(e1) / substeps
-        tsz = 4 if precision == "fp32" else 8
-        algo_l = algorithmic_bytes_per_launch(gl, tsz)
-        return {"value": world * gl.micro_cells / (ms * 1e-3), "unit": UNIT,
-                "kernel_ms_per_launch": ms, "algorithmic_bytes_per_launch": algo_l,
-                "achieved_gbs": algo_l / (ms * 1e-3) / 1e9}
 
     def large_adjoint_run():
         """large512 forward + adjoint: 20 macro steps x 100 substeps (a new
@@ -633,19 +633,34 @@ def run_ours(args):
                 "autotune_best_ms_per_substep": best["ms_per_substep"],
                 "autotune_candidates": len(tune)}
 
+    w = WORKLOADS[name]
+    g, nsub = w["grid"], w["substeps"]
+    big = g.micro_cells > 2e8
     units_per_step = g.micro_cells * nsub
+    peak, peak_src = read_peaks()
+
+    # ---- headline: the workload in the float32 form
     clocks = ClockSampler(local)
     clocks.start()
-    total_ms, kern_ms = device_run("fp32", args.steps, args.warmup)
+    total_ms, kern_ms = device_run(name, "fp32", args.steps, args.warmup)
     clk = clocks.stop()
-    fp64_steps = max(2, min(args.steps, 3))
-    fp64_ms, fp64_kern = device_run("fp64", fp64_steps, 1)
-    e2e_s, h2d, d2h = e2e_run("fp32", args.steps, args.warmup)
+    # the float64 form on the same workload (one macro step after one warm-up
+    # macro step on the large case: 100 substeps of about 65 ms)
+    fp64_steps = 1 if big else max(2, min(args.steps, 3))
+    fp64_ms, fp64_kern = device_run(name, "fp64", fp64_steps, 1)
+    e2e_s, h2d, d2h = e2e_run(name, "fp32", args.steps, args.warmup)
+
+    # ---- the other single-instance workload: the L2-resident precision128
+    # case beside a large headline (or large512 beside a small one)
+    other = "precision128" if name != "precision128" else "large512"
+    wo = WORKLOADS[other]
+    go, nso = wo["grid"], wo["substeps"]
+    o_steps = 10 if other == "precision128" else 3
+    o_ms, o_kern = device_run(other, "fp32", o_steps, 3)
+
     adj = {"workload": "adjoint64 (64x64 x 32 x 32, 100 substeps, checkpoint every 10, polar order)",
            "fp32": adjoint_ratio("fp32"), "fp64": adjoint_ratio("fp64")}
-    large = {"workload": "large512 (512x512 x 64 x 64, 1.07e9 motor cells)",
-             "fp32": large_run("fp32", 10), "fp64": large_run("fp64", 3)}
-    ens = ensemble_run(max(2, min(args.steps, 3)))
+    ens = ensemble_run(10)
     large_adj = large_adjoint_run()
     diff = diffusion_run()
     anchors = {"precision128": anchors_run("precision128", 50),
@@ -653,26 +668,58 @@ def run_ours(args):
     fluid = {"precision128": fluid_run("precision128"), "large512": fluid_run("large512", reps=3)}
     local = {"precision128": local_run("precision128"),
              "large512": local_run("large512", reps=3)}
+    # measured arithmetic roofs (fused multiply-adds per second)
+    alu = {k: mm.alu_peak(k, stream.cuda_stream) for k in ("fp64", "fp32", "fp32x2")}
+    packed_tops = alu["fp32x2"]["fma_per_s"] / 1e12
     for v in local.values():
-        # ALU roofline: LOCAL_OPS float32 operations per motor value and
-        # substep against 128 float32 lanes per SM at the maximum SM clock
+        # LOCAL_OPS float32 operations per motor value and substep against the
+        # measured packed float32 rate (the kernel's element-wise arithmetic is
+        # packed; its minima and maxima are scalar, so this is the roof it can
+        # approach, not exceed)
         ops = v["cell_updates_per_call"] * LOCAL_OPS / (v["ms_per_call"] * 1e-3) / 1e12
-        v["roofline"] = {"bound": "alu", "achieved": ops, "peak": alu_peak_tops(),
-                         "unit": "Tops/s", "frac": ops / alu_peak_tops(),
+        v["roofline"] = {"bound": "alu", "achieved": ops, "peak": packed_tops,
+                         "unit": "Tops/s", "frac": ops / packed_tops,
+                         "peak_source": "measured (mm_alu_peak, packed float32 fma)",
                          "kernel": "k_motor_local (float32)",
                          "traffic": read_profile_traffic("k_motor_local", wname_of(v), "fp32")}
 
-    total_ms, kern_ms, fp64_ms, e2e_s = reduce_max([total_ms, kern_ms, fp64_ms, e2e_s], dev)
+    total_ms, kern_ms, fp64_ms, fp64_kern, e2e_s, o_ms, o_kern = reduce_max(
+        [total_ms, kern_ms, fp64_ms, fp64_kern, e2e_s, o_ms, o_kern], dev)
 
     value = whole_job_value(world, units_per_step * args.steps, total_ms * 1e-3)
     launch_ms = kern_ms / (args.steps * nsub)
-    peak, peak_src = read_peaks()
     algo = algorithmic_bytes_per_launch(g, 4)
     achieved = algo / (launch_ms * 1e-3) / 1e9
-    traffic = read_profile_traffic("k_substep", name, "fp32")
+    # the large case's capture is taken at a quarter of its cells (256x256 x
+    # 64 x 64) and scaled to a full launch by the motor cells
+    traffic = (read_profile_traffic("k_substep", "large512", "fp32") if name == "large512"
+               else read_profile_traffic("k_substep", name, "fp32"))
     fp64_value = whole_job_value(world, units_per_step * fp64_steps, fp64_ms * 1e-3)
+    fp64_launch_ms = fp64_kern / (fp64_steps * nsub)
+    fp64_ops = g.micro_cells * SUBSTEP_OPS / (fp64_launch_ms * 1e-3) / 1e12
+    fp64_peak = alu["fp64"]["fma_per_s"] / 1e12
+    o_launch = o_kern / (o_steps * nso)
+    o_algo = algorithmic_bytes_per_launch(go, 4)
+    o_traffic = read_profile_traffic("k_substep", other, "fp32")
+    o_leg = {"workload": f"{other} ({go.nx}x{go.ny} x {go.ntheta} x {go.ns}, {nso} substeps per "
+                         f"macro step, float32)",
+             "value": whole_job_value(world, go.micro_cells * nso * o_steps, o_ms * 1e-3),
+             "unit": UNIT, "steps": o_steps, "ms_per_step": o_ms / o_steps,
+             "kernel_ms_per_launch": o_launch, "algorithmic_bytes_per_launch": o_algo,
+             "roofline": {"bound": "hbm", "peak": peak, "unit": "GB/s",
+                          "achieved": o_algo / (o_launch * 1e-3) / 1e9,
+                          "frac": o_algo / (o_launch * 1e-3) / 1e9 / peak,
+                          "kernel": "k_substep (float32)", "peak_source": peak_src,
+                          "traffic": o_traffic,
+                          "dram_frac": (None if o_traffic is None
+                                        else o_traffic / (o_launch * 1e-3) / 1e9 / peak)}}
+    if other == "precision128":
+        o_leg["note"] = ("L2-resident: the 67 MB motor density stays in the 129 MB L2 within a "
+                         "macro step, so frac compares an L2-fed kernel with the HBM copy peak; "
+                         "dram_frac is its measured DRAM traffic over the same time")
     if rank == 0:
-        cpu = time_oracle_sample(name) if world == 1 or rank == 0 else None
+        cpu = time_oracle_sample(name)
+        ens_frac = ens["achieved_gbs"] / peak
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -680,12 +727,11 @@ def run_ours(args):
             "data": "synthetic",
             "config": {"workload": name, "grid": f"{g.nx}x{g.ny}", "ntheta": g.ntheta, "ns": g.ns,
                        "substeps_per_step": nsub, "precision": "float32 Mb/psi, float64 sums",
-                       "l2": "flushed between timed steps (256 MiB write outside the timed events)",
+                       "l2": (f"inputs larger than L2 ({g.micro_cells * 4 / 1e9:.2f} GB of motor "
+                              "density) and L2 flushed between timed steps (256 MiB write "
+                              "outside the timed events)") if big else
+                             "flushed between timed steps (256 MiB write outside the timed events)",
                        "parallelism": f"{world} independent instance(s), one per GPU"},
-            "fp64": {"value": fp64_value, "unit": UNIT, "steps": fp64_steps,
-                     "ms_per_step": fp64_ms / fp64_steps,
-                     "kernel_ms_per_launch": fp64_kern / (fp64_steps * nsub),
-                     "fp32_over_fp64": value / fp64_value},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "kernel": "k_substep (float32)", "peak_source": peak_src,
@@ -694,14 +740,17 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "e2e": {"value": whole_job_value(world, units_per_step * args.steps, e2e_s), "unit": UNIT,
                     "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "fp64": {"value": fp64_value, "unit": UNIT, "steps": fp64_steps,
+                     "ms_per_step": fp64_ms / fp64_steps, "kernel_ms_per_launch": fp64_launch_ms,
+                     "roofline": {"bound": "alu", "achieved": fp64_ops, "peak": fp64_peak,
+                                  "unit": "Tops/s", "frac": fp64_ops / fp64_peak,
+                                  "kernel": "k_substep (float64)",
+                                  "ops_per_cell_update": SUBSTEP_OPS,
+                                  "peak_source": "measured (mm_alu_peak, float64 fma)"}},
+            other: o_leg,
+            "alu_peaks": {k: {"fma_per_s": v["fma_per_s"], "ms_per_launch": v["ms_per_launch"]}
+                          for k, v in alu.items()},
             "adjoint": adj,
-            "large512": dict(large, fp32_over_fp64=large["fp32"]["value"] / large["fp64"]["value"],
-                             roofline={"bound": "hbm", "peak": peak, "unit": "GB/s",
-                                       "achieved": large["fp32"]["achieved_gbs"],
-                                       "frac": large["fp32"]["achieved_gbs"] / peak,
-                                       "kernel": "k_substep (float32)", "peak_source": peak_src,
-                                       "traffic": read_profile_traffic(
-                                           "k_substep", "large512", "fp32")}),
             "large512_adjoint": dict(
                 large_adj, workload="large512, 2000 substeps, float32, mean active stress vs k_off"),
             "diffusion": diff,
@@ -709,8 +758,7 @@ def run_ours(args):
             "anchors": anchors,
             "fluid": fluid,
             "ensemble": dict(ens, roofline={"bound": "hbm", "peak": peak, "unit": "GB/s",
-                                            "achieved": ens["achieved_gbs"],
-                                            "frac": ens["achieved_gbs"] / peak,
+                                            "achieved": ens["achieved_gbs"], "frac": ens_frac,
                                             "kernel": "k_substep_batch (float32)",
                                             "peak_source": peak_src,
                                             "traffic": read_profile_traffic(
@@ -719,6 +767,18 @@ def run_ours(args):
             # block, the two substep-rule kernels), nsub substeps, moments
             "gpu_launches": args.steps * (nsub + 5),
             "clocks": clk,
+            # flat summaries of every leg (fractions of the measured peaks)
+            "hbm_frac": achieved / peak,
+            "fp64_value": fp64_value,
+            "fp32_over_fp64": value / fp64_value,
+            "fp64_alu_frac": fp64_ops / fp64_peak,
+            "adjoint_over_forward": {"adjoint64_fp32": adj["fp32"]["adjoint_over_forward"],
+                                     "adjoint64_fp64": adj["fp64"]["adjoint_over_forward"],
+                                     "large512_fp32": large_adj["adjoint_over_forward"]},
+            "ensemble_frac": ens_frac,
+            "anchors_frac": {k: v["roofline"]["frac"] for k, v in anchors.items()},
+            "local_alu_frac": {k: v["roofline"]["frac"] for k, v in local.items()},
+            f"{other}_frac": o_leg["roofline"]["frac"],
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -729,10 +789,10 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="precision128", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="large512", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -1,6 +1,6 @@
 """Run one synthetic case of the library's kernels, for profilers.
 
-    python -m paper_1908_04279_gb300.profile_case
+    python bench_profile.py
         [--case single|batch|adjoint|moments|local|fluid]
         [--grid NX NY NTHETA NS] [--precision fp32|fp64] [--substeps N]
         [--repeat R] [--K K] [--members M] [--autotune] [--anchors ELL]
@@ -25,15 +25,19 @@ from __future__ import annotations
 
 import argparse
 import json
+import os
+import sys
+
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 
 def main():
     import torch
 
-    from . import build as B
-    from . import mm
-    from .inputs import (Grid, Rates, ensemble_members, member_inputs, psi_isotropic_perturbed,
-                         random_divfree_flow)
+    from paper_1908_04279_gb300 import build as B
+    from paper_1908_04279_gb300 import mm
+    from paper_1908_04279_gb300.inputs import (Grid, Rates, ensemble_members, member_inputs,
+                                               psi_isotropic_perturbed, random_divfree_flow)
 
     ap = argparse.ArgumentParser()
     ap.add_argument("--case", default="single",

@@ -429,6 +429,19 @@ mm_status mm_moments_static(const mm_grid* grid, const mm_rates* rates, const do
                             const double* mb, const double* mf, const double* c, double* fields,
                             double* scalars, void* stream);
 
+/* Measured arithmetic roof of the current device (a measurement aid with no
+ * counterpart in the paper; the rooflines of the kernels bound by arithmetic
+ * issue rather than memory are stated against it). kind 0: float64 fused
+ * multiply-adds; 1: scalar float32; 2: packed two-value float32 (each packed
+ * instruction counts as two). A grid of full blocks on every SM runs
+ * independent chains of fused multiply-adds; the call times five launches
+ * with CUDA events on `stream` after one warm-up launch and synchronises.
+ * *fma_per_s: fused multiply-adds per second (flops = 2x); *ms_per_launch
+ * (may be NULL): the average launch time. Allocates nothing beyond two CUDA
+ * events. Errors: MM_ERR_INVALID (bad kind or NULL output), MM_ERR_CUDA;
+ * mm_last_error(NULL). */
+mm_status mm_alu_peak(int kind, double* fma_per_s, double* ms_per_launch, void* stream);
+
 /* A short description of the build (library name and target architecture). */
 const char* mm_build_info(void);
 

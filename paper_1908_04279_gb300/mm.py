@@ -104,6 +104,7 @@ PROTOTYPES = {
     "mm_batch_autotune": ([_H, C.c_int, C.POINTER(mm_batch_tune), C.c_int,
                            C.POINTER(C.c_int)], C.c_int),
     "mm_last_error": ([_H], C.c_char_p),
+    "mm_alu_peak": ([C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), _P], C.c_int),
     "mm_build_info": ([], C.c_char_p),
 }
 
@@ -517,6 +518,21 @@ def moments_static(grid: Grid, rates: Rates, psi, mb, mf, c, fields, scalars, st
                                ptrs[3][0], fp, ptrs[4][0], C.c_void_p(stream))
     if st != 0:
         raise MMError(st, lib.mm_last_error(None).decode())
+
+
+ALU_KINDS = {"fp64": 0, "fp32": 1, "fp32x2": 2}
+
+
+def alu_peak(kind: str, stream: int = 0) -> dict:
+    """Measured fused multiply-add rate of the current device (mm_alu_peak):
+    kind "fp64", "fp32" or "fp32x2" (packed, each instruction counted as two).
+    Returns {"fma_per_s", "ms_per_launch"}."""
+    lib = load_library()
+    rate, ms = C.c_double(), C.c_double()
+    st = lib.mm_alu_peak(ALU_KINDS[kind], C.byref(rate), C.byref(ms), C.c_void_p(stream))
+    if st != 0:
+        raise MMError(st, lib.mm_last_error(None).decode())
+    return {"fma_per_s": rate.value, "ms_per_launch": ms.value}
 
 
 def build_info() -> str:

@@ -192,7 +192,10 @@ typedef struct {
   const double* dL_dnb;  /* [ny][nx][ntheta] or NULL: through n_b = sum_j Mb ds */
   const double* dL_dm1;  /* [ny][nx][ntheta] or NULL: through m1 = sum_j s_j Mb ds */
   const double* dL_dmf;  /* [ny][nx] or NULL: through the free motors Mf */
-  int on_device;
+  int on_device;         /* all seed arrays are device (1) or host (0) pointers */
+  const double* dL_dmb;  /* [ny][nx][ntheta][ns] or NULL: the bound-motor density itself,
+                            added to the rows' seed from dL_dnb and dL_dm1 (for a loss on
+                            the motor field that its first two s-moments do not carry) */
 } mm_adjoint_seed;
 typedef struct {
   double* dL_du;         /* [du_capacity][2][ny][nx] or NULL, in prescription order */

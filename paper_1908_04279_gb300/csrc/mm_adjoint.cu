@@ -930,11 +930,11 @@ template <typename T>
 __global__ void k_adj_seed(int kind, const double* coef, const T* psi, const T* mb,
                            const double* dpsi, const double* dnb, const double* dm1,
                            const double* dmf, T* lpsi, T* lmb, T* lmf, T* D, long long ncells,
-                           int nth, int ns, double ds, double L, const T* trig) {
+                           int nth, int ns, double ds, double L, const T* trig, bool mb_seeded) {
   const int lane = threadIdx.x & 31;
   const long long gw = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
   const long long W = (long long)gridDim.x * (blockDim.x >> 5);
-  if (kind == 1 || (kind == 0 && !dnb && !dm1)) {
+  if (kind == 1 || (kind == 0 && !dnb && !dm1 && !mb_seeded)) {
     // no seed on the rows (lam_Mb was cleared by the caller, so D = 0): lanes
     // over theta for lam_psi
     for (long long cell = gw; cell < ncells; cell += W) {
@@ -976,7 +976,9 @@ __global__ void k_adj_seed(int kind, const double* coef, const T* psi, const T* 
       if (lane == 0) lpsi[r] = (T)lp;
       for (int j = lane; j < ns; j += 32) {
         const double sj = -0.5 * L + (j + 0.5) * ds;
-        const T lm = (T)(a_nb * ds + a_m1 * sj * ds);
+        // with a seed on the motor density itself, lam_Mb already holds it
+        const double base = mb_seeded ? (double)lrow[j] : 0.0;
+        const T lm = (T)(base + a_nb * ds + a_m1 * sj * ds);
         lrow[j] = lm;
         if (lm != T(0)) dsum += (double)lm * (double)row[j];
       }
@@ -1150,16 +1152,17 @@ template <typename T>
 cudaError_t launch_adj_seed(int kind, const double* coef, const T* psi, const T* mb,
                             const double* dpsi, const double* dnb, const double* dm1,
                             const double* dmf, T* lpsi, T* lmb, T* lmf, T* D, long long ncells,
-                            int nth, int ns, double ds, double L, const T* trig, cudaStream_t s) {
+                            int nth, int ns, double ds, double L, const T* trig, bool mb_seeded,
+                            cudaStream_t s) {
   long long g = (ncells + 3) / 4;
   if (g > 152 * 8) g = 152 * 8;
-  if (kind == 1 || (kind == 0 && !dnb && !dm1)) {
+  if (kind == 1 || (kind == 0 && !dnb && !dm1 && !mb_seeded)) {
     // a seed without motor rows: lam_Mb = 0 by a fill, the kernel skips the rows
     const cudaError_t e = cudaMemsetAsync(lmb, 0, (size_t)ncells * nth * ns * sizeof(T), s);
     if (e != cudaSuccess) return e;
   }
   k_adj_seed<T><<<(int)g, 128, 0, s>>>(kind, coef, psi, mb, dpsi, dnb, dm1, dmf, lpsi, lmb, lmf,
-                                       D, ncells, nth, ns, ds, L, trig);
+                                       D, ncells, nth, ns, ds, L, trig, mb_seeded);
   return cudaGetLastError();
 }
 
@@ -1187,7 +1190,7 @@ cudaError_t launch_adj_psi0(const T* lpsi, const T* lmf, int units, const T* nb,
   template cudaError_t launch_adj_seed<T>(int, const double*, const T*, const T*, const double*, \
                                           const double*, const double*, const double*, T*, T*,  \
                                           T*, T*, long long, int, int, double, double, const T*, \
-                                          cudaStream_t);                                        \
+                                          bool, cudaStream_t);                                  \
   template cudaError_t launch_adj_psi0<T>(const T*, const T*, int, const T*, double, long long,  \
                                           int, double*, cudaStream_t);
 MM_ADJ_INST(float)

@@ -1305,6 +1305,11 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
       }
     }
   }
+  // a seed on the motor density itself goes straight into lam_Mb (in the
+  // state precision); the seed kernel adds the moment seeds to it
+  const bool mb_seeded = kind == MM_OBS_NONE && seed->dL_dmb;
+  if (mb_seeded && (st = put_array(h, R.lmb, seed->dL_dmb, h->mbn, seed->on_device)) != MM_OK)
+    return st;
   // the seed fills partial 0 of lam_Mf and D; the other partials start at 0
   CK(cudaMemsetAsync(R.lmf[0], 0, (size_t)R.units * nc * t, h->stream));
   CK(cudaMemsetAsync(R.Dd[0], 0, (size_t)R.units * nc * t, h->stream));
@@ -1314,13 +1319,13 @@ mm_status mm_adjoint_step(mm_handle* h, int n, const mm_adjoint_seed* seed, mm_a
                                     (const double*)h->mb, sp[0], sp[1], sp[2], sp[3],
                                     (double*)R.lpsi[0], (double*)R.lmb, (double*)R.lmf[0],
                                     (double*)R.Dd[0], h->ncells, h->g.ntheta, h->g.ns, ds, h->g.L,
-                                    (const double*)h->trig, h->stream);
+                                    (const double*)h->trig, mb_seeded, h->stream);
   else
     e = mm::launch_adj_seed<float>(kind, R.coef, (const float*)h->psi[h->parity],
                                    (const float*)h->mb, sp[0], sp[1], sp[2], sp[3],
                                    (float*)R.lpsi[0], (float*)R.lmb, (float*)R.lmf[0],
                                    (float*)R.Dd[0], h->ncells, h->g.ntheta, h->g.ns, ds, h->g.L,
-                                   (const float*)h->trig, h->stream);
+                                   (const float*)h->trig, mb_seeded, h->stream);
   CK(e);
   for (int v = 0; v < nv; ++v) {
     CK(cudaMemsetAsync(R.v_lamG[v], 0, 4 * nc * 8, h->stream));

@@ -168,7 +168,8 @@ template <typename T>
 cudaError_t launch_adj_seed(int kind, const double* coef, const T* psi, const T* mb,
                             const double* dpsi, const double* dnb, const double* dm1,
                             const double* dmf, T* lpsi, T* lmb, T* lmf, T* D, long long ncells,
-                            int nth, int ns, double ds, double L, const T* trig, cudaStream_t s);
+                            int nth, int ns, double ds, double L, const T* trig, bool mb_seeded,
+                            cudaStream_t s);
 cudaError_t launch_adj_finish(const double* lamG, const double* lamu, double* dLdu, int nx, int ny,
                               double inv_dx, double inv_dy, cudaStream_t s);
 // The seed coefficients and value of a built-in observable from the moments'

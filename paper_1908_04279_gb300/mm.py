@@ -57,7 +57,8 @@ class mm_batch_tune(C.Structure):
 
 class mm_adjoint_seed(C.Structure):
     _fields_ = [("observable", C.c_int), ("dL_dpsi", C.c_void_p), ("dL_dnb", C.c_void_p),
-                ("dL_dm1", C.c_void_p), ("dL_dmf", C.c_void_p), ("on_device", C.c_int)]
+                ("dL_dm1", C.c_void_p), ("dL_dmf", C.c_void_p), ("on_device", C.c_int),
+                ("dL_dmb", C.c_void_p)]
 
 
 class mm_adjoint_out(C.Structure):
@@ -347,24 +348,28 @@ class Simulation:
 
     def adjoint(self, n_substeps: int, observable: str = "none", dL_dpsi=None, dL_dnb=None,
                 dL_dm1=None, dL_dmf=None, n_velocities: int = 1, want_du: bool = True,
-                want_dpsi0: bool = True, out_du=None, out_dpsi0=None):
+                want_dpsi0: bool = True, out_du=None, out_dpsi0=None, dL_dmb=None):
         """Reverse sweep over the recorded substeps. Seeds are float64 arrays
         (numpy, or CUDA tensors; psi-shaped for dL_dpsi/dL_dnb/dL_dm1, [ny][nx]
-        for dL_dmf) or a built-in observable. Returns a dict: value, dL_drates
+        for dL_dmf, [ny][nx][ntheta][ns] for dL_dmb) or a built-in observable. Returns a dict: value, dL_drates
         (k_off, v_walk, k_on), dL_du [n_velocities][2][ny][nx], dL_dpsi0.
         With out_du / out_dpsi0 (float64 CUDA tensors of those shapes) the
         gradients are written there on the device instead of to new host
         arrays."""
         g = self.grid
-        seeds = [dL_dpsi, dL_dnb, dL_dm1, dL_dmf]
+        seeds = [dL_dpsi, dL_dnb, dL_dm1, dL_dmf, dL_dmb]
+        shapes = [(g.ny, g.nx, g.ntheta)] * 3 + [(g.ny, g.nx), (g.ny, g.nx, g.ntheta, g.ns)]
+        for a, shp in zip(seeds, shapes):
+            if a is not None and tuple(a.shape) != shp:
+                raise ValueError(f"seed of shape {tuple(a.shape)}, expected {shp}")
         kept = [np.ascontiguousarray(a, dtype=np.float64) if isinstance(a, np.ndarray) else a
                 for a in seeds]
         ptrs = [_ptr(a, "seed") for a in kept]
         devs = {d for _, d in ptrs if d is not None}
         if len(devs) > 1:
             raise TypeError("seeds must all be host arrays or all device tensors")
-        sd = mm_adjoint_seed(OBSERVABLES[observable], *[p for p, _ in ptrs],
-                             devs.pop() if devs else 0)
+        sd = mm_adjoint_seed(OBSERVABLES[observable], *[p for p, _ in ptrs[:4]],
+                             devs.pop() if devs else 0, ptrs[4][0])
         if out_du is not None or out_dpsi0 is not None:
             pu, du_dev = _ptr(out_du, "out_du")
             pp, dp_dev = _ptr(out_dpsi0, "out_dpsi0")

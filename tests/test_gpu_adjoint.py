@@ -2,7 +2,7 @@
 oracle's adjoint and against central finite differences of the GPU forward.
 
 * exact transpose: random seeds in moment form (dL/dpsi, dL/dn_b, dL/dm1,
-  dL/dMf), two velocity fields during the recording, segments shorter than the
+  dL/dMf) and on the whole state (dL/dpsi, dL/dMb, dL/dMf), two velocity fields during the recording, segments shorter than the
   run (checkpoint recompute), with and without the Alg. 2 scale-down; the
   float64 GPU sweep equals the oracle's reverse sweep to relative 1e-10;
 * central differences (h = 1e-6, dt held fixed) of the polar order after 100
@@ -105,6 +105,74 @@ def test_adjoint_equals_oracle_adjoint(mmod, oracle_mod, dims, clip):
     assert rel(res["dL_dpsi0"], lpsi0) <= 1e-10, rel(res["dL_dpsi0"], lpsi0)
     if clip:
         assert np.count_nonzero([np.any(x.mf == 0.0) for x in states[1:]]) > 0
+
+
+def _full_seed_run(mmod, g, r, psi0, mb0, u, n, K, seeds, precision, device=False):
+    import torch
+    with mmod.Simulation(g, r, precision) as sim:
+        sim.set_state(psi0, mb0)
+        sim.set_velocity(u)
+        dt = sim.dt
+        sim.set_checkpointing(K, n)
+        sim.step(n)
+        if device:
+            seeds = {k: torch.tensor(v, device="cuda") for k, v in seeds.items()}
+        res = sim.adjoint(n, **seeds, n_velocities=1)
+    return res, dt
+
+
+@pytest.mark.parametrize("dims,moment_seeds", [((12, 10, 8, 8), True), ((9, 7, 6, 5), False),
+                                               ((6, 5, 16, 32), True)])
+def test_full_state_seed_equals_oracle_adjoint(mmod, oracle_mod, dims, moment_seeds):
+    """A seed on the whole final state -- dL/dpsi, dL/dMb (every node of every
+    row), dL/dMf, with or without the moment seeds dL/dn_b, dL/dm1 added to the
+    rows -- gives the oracle's reverse sweep started from lam_Mb = dL/dMb +
+    dL/dn_b ds + dL/dm1 s ds (relative 1e-10 in float64, host and device
+    seeds alike); the float32 sweep agrees with the float64 one to 1e-3."""
+    O = oracle_mod
+    g = Grid(*dims, L=1.1)
+    r = Rates(v_sp=0.1, glide=0.5, k_on=1.3, k_off=0.7, v_walk=0.9)
+    rng = SplitMix64(301 + sum(dims))
+    psi0 = psi_isotropic_perturbed(g, 302, amp=0.3)
+    mb0 = 0.3 * rng.uniforms(g.ny * g.nx * g.ntheta * g.ns).reshape(g.ny, g.nx, g.ntheta, g.ns)
+    u = random_divfree_flow(g, 303, 6, 0.3)
+    n, K = 9, 4
+    seeds = dict(
+        dL_dpsi=rng.uniforms(g.ny * g.nx * g.ntheta).reshape(g.ny, g.nx, g.ntheta) - 0.5,
+        dL_dmb=rng.uniforms(g.ny * g.nx * g.ntheta * g.ns).reshape(g.ny, g.nx, g.ntheta, g.ns)
+        - 0.5,
+        dL_dmf=rng.uniforms(g.ny * g.nx).reshape(g.ny, g.nx) - 0.5)
+    if moment_seeds:
+        seeds["dL_dnb"] = rng.uniforms(g.ny * g.nx * g.ntheta).reshape(g.ny, g.nx, g.ntheta) - 0.5
+        seeds["dL_dm1"] = rng.uniforms(g.ny * g.nx * g.ntheta).reshape(g.ny, g.nx, g.ntheta) - 0.5
+    res, dt = _full_seed_run(mmod, g, r, psi0, mb0, u, n, K, seeds, "fp64")
+    res_dev, _ = _full_seed_run(mmod, g, r, psi0, mb0, u, n, K, seeds, "fp64", device=True)
+    st = O.make_state(g, psi0, mb0)
+    states = O.substep_states(g, r, st, u, dt, n)
+    ds = g.L / g.ns
+    s = -g.L / 2 + (np.arange(g.ns) + 0.5) * ds
+    lpsi = seeds["dL_dpsi"].copy()
+    lmb = seeds["dL_dmb"].copy()
+    if moment_seeds:
+        lmb += seeds["dL_dnb"][..., None] * ds + seeds["dL_dm1"][..., None] * s * ds
+    lmf = seeds["dL_dmf"].copy()
+    lu, lp = np.zeros((2, g.ny, g.nx)), np.zeros(3)
+    for i in range(n - 1, -1, -1):
+        O.adjoint_substep(g, r, dt, u, states[i], lpsi, lmb, lmf, lu, lp)
+    nb0 = (states[0].mb * ds).sum(-1)
+    lpsi0 = lpsi - lmf[..., None] * nb0 * (2 * math.pi / g.ntheta)
+    for rr in (res, res_dev):
+        assert rel(rr["dL_du"][0], lu) <= 1e-10, rel(rr["dL_du"][0], lu)
+        assert rel(rr["dL_drates"], lp) <= 1e-10, (rr["dL_drates"], lp)
+        assert rel(rr["dL_dpsi0"], lpsi0) <= 1e-10, rel(rr["dL_dpsi0"], lpsi0)
+    # the motor seed matters: without it the gradients differ
+    no_mb = {k: v for k, v in seeds.items() if k != "dL_dmb"}
+    res_no, _ = _full_seed_run(mmod, g, r, psi0, mb0, u, n, K, no_mb, "fp64")
+    assert rel(res_no["dL_drates"], lp) > 1e-3
+    r32, _ = _full_seed_run(mmod, g, r, psi0, mb0, u, n, K, seeds, "fp32")
+    assert rel(r32["dL_du"][0], lu) <= 1e-3, rel(r32["dL_du"][0], lu)
+    assert rel(r32["dL_drates"], lp) <= 1e-3, (r32["dL_drates"], lp)
+    assert rel(r32["dL_dpsi0"], lpsi0) <= 1e-3, rel(r32["dL_dpsi0"], lpsi0)
 
 
 def _polar_order(mmod, g, r, psi0, u, dt, n, precision="fp64"):

@@ -116,6 +116,25 @@ mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const 
 mm_status mm_get_state(mm_handle* h, double* psi, double* mb, double* mf, double* c,
                        int on_device);
 
+/* Bitwise checkpoint and restart (checkpoint/resume of a long run). A
+ * snapshot holds the state exactly as the substep kernels left it, in the
+ * state precision (psi, n_b, Mb, Mf, C, M), the device scalars the next
+ * substep reads (dt, the float32 form's pending mass-correction factor and
+ * its reference filament number) and the velocity in effect, so that a handle
+ * of the same grid and precision loaded from it continues the uninterrupted
+ * run bit for bit (mm_get_state / mm_set_state re-derive n_b, C, Mf and the
+ * reference filament number, which continues the same physics but not the
+ * same bits). The buffer is caller-owned, host (on_device = 0) or device
+ * memory of at least mm_snapshot_bytes; its format is private to this
+ * library version. mm_save_snapshot and mm_load_snapshot synchronise the
+ * handle's stream. Loading ends an adjoint recording, as mm_set_state does.
+ * MM_ERR_INVALID for a buffer that is too small, not a snapshot, or of another
+ * grid or precision; MM_ERR_STATE when saving a handle without a state;
+ * MM_ERR_UNSUPPORTED with non-local anchors on. */
+mm_status mm_snapshot_bytes(mm_handle* h, size_t* bytes);
+mm_status mm_save_snapshot(mm_handle* h, void* buf, size_t bytes, int on_device);
+mm_status mm_load_snapshot(mm_handle* h, const void* buf, size_t bytes, int on_device);
+
 /* Prescribe the in-plane velocity u (held fixed over the following substeps)
  * and recompute the adaptive substep from the current state (Sec. 2: the
  * outer step is limited by the advective fluxes of Eq. 1, the inner one by the

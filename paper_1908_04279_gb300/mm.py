@@ -80,6 +80,9 @@ PROTOTYPES = {
     "mm_set_state": ([_H, _P, _P, _P, C.c_int], C.c_int),
     "mm_get_state": ([_H, _P, _P, _P, _P, C.c_int], C.c_int),
     "mm_set_velocity": ([_H, _P, C.c_int], C.c_int),
+    "mm_snapshot_bytes": ([_H, C.POINTER(C.c_size_t)], C.c_int),
+    "mm_save_snapshot": ([_H, _P, C.c_size_t, C.c_int], C.c_int),
+    "mm_load_snapshot": ([_H, _P, C.c_size_t, C.c_int], C.c_int),
     "mm_get_dt": ([_H, C.POINTER(C.c_double)], C.c_int),
     "mm_set_dt": ([_H, C.c_double], C.c_int),
     "mm_micro_step": ([_H, C.c_int], C.c_int),
@@ -148,6 +151,23 @@ def _ptr(a, what: str):
             return a.data_ptr(), 0
         return a.data_ptr(), 1
     raise TypeError(f"{what}: unsupported array type {type(a)}")
+
+
+def _buf_ptr(a):
+    """(pointer, on_device) of a uint8 numpy array or torch tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.uint8 or not a.flags.c_contiguous:
+            raise TypeError("need a C-contiguous uint8 array")
+        return a.ctypes.data, 0
+    if hasattr(a, "data_ptr") and hasattr(a, "is_cuda"):
+        if not a.is_contiguous():
+            raise TypeError("need a contiguous tensor")
+        return a.data_ptr(), int(bool(a.is_cuda))
+    raise TypeError(f"unsupported buffer type {type(a)}")
+
+
+def _buf_len(a) -> int:
+    return int(a.nbytes) if isinstance(a, np.ndarray) else int(a.numel() * a.element_size())
 
 
 def current_stream_handle() -> int:
@@ -394,6 +414,28 @@ class Simulation:
             du = du[:out.n_velocities]
         return dict(value=out.value, dL_drates=np.array(list(out.dL_drates)), dL_du=du,
                     dL_dpsi0=dp, n_velocities=out.n_velocities)
+
+    def snapshot_bytes(self) -> int:
+        """Bytes of a snapshot of this handle (mm_snapshot_bytes)."""
+        n = C.c_size_t()
+        self._check(self.lib.mm_snapshot_bytes(self.h, C.byref(n)))
+        return n.value
+
+    def snapshot(self, out=None):
+        """Bitwise snapshot of the state (mm_save_snapshot): into `out` (a
+        uint8 numpy array or CUDA tensor of at least snapshot_bytes() bytes),
+        or a new host uint8 array. Returns the buffer."""
+        if out is None:
+            out = np.empty(self.snapshot_bytes(), dtype=np.uint8)
+        p, dev = _buf_ptr(out)
+        self._check(self.lib.mm_save_snapshot(self.h, p, _buf_len(out), dev))
+        return out
+
+    def load_snapshot(self, buf):
+        """Continue from a snapshot of a handle of the same grid and precision
+        (mm_load_snapshot); buf as returned by snapshot()."""
+        p, dev = _buf_ptr(buf)
+        self._check(self.lib.mm_load_snapshot(self.h, p, _buf_len(buf), dev))
 
     def debug_set(self, wait_limit: int, flags: int = 0):
         self._check(self.lib.mm_debug_set(self.h, int(wait_limit), int(flags)))

@@ -558,6 +558,335 @@ int or_anchor_offsets(const or_grid* g, const or_rates* r, int* ox, int* oy) {
   return OR_OK;
 }
 
+/* ------------------------------------ finite capture radius (the r0 axis) */
+
+/* Eq. 4-6 with the anchor r0 of Sec. 2 kept as an axis of the bound-motor
+ * density and a finite capture radius rc: Mb(r0, x, theta, s) is tracked only
+ * where the motor head x + (l/L) s p is within reach of r0 (the set B_rc(r0)),
+ * and Alg. 2 runs per r0 -- every configuration of B_rc(r0) by the RK2 of
+ * Eq. 4, the coarse reduction of Eq. 5 at r0, the scale-down at r0, Eq. 6 at
+ * r0. Readings (listed in the design notes):
+ *   - r0 ranges over the grid's cells; the cell at offset d from the
+ *     filament's cell is within reach of a head when the distance from the
+ *     head to the cell's square is at most rc (so at rc = 0 the reach is the
+ *     cell under the head, as on the rc -> 0 path);
+ *   - a motor keeps its tail while it walks: the walking flux of Eq. 4 acts
+ *     along s at fixed r0, so for each (x, theta, r0) the nodes within reach
+ *     form walking lines (runs of consecutive nodes), with no inflow at a
+ *     line's first node and donor-cell outflow at its last (a head that walks
+ *     out of reach lets go, and its motor rejoins the free pool through
+ *     Eq. 6), as at the filament's plus end;
+ *   - the binding term k_on Mf(r0) of Eq. 4 is shared among the anchors in
+ *     reach of the node: k_on Mf(r0) / n_a(k, j), n_a the number of anchors
+ *     within reach, so that k_on keeps its meaning of the one-anchor model
+ *     (the binding rate against the free motors under the filament) and a
+ *     uniform Mf binds the same total at any rc;
+ *   - the motors per filament are n_b = sum over anchors and nodes of Mb ds;
+ *     the force of Eq. 10 acts at the head, in the cell under it.
+ * Storage is the paper's (Sec. 3.2 "Reordering Storage"): anchor-major,
+ * mb[r0][c] with c running over the configurations of B_rc(r0) line by line
+ * (the template below, the same for every r0), s contiguous within a line. */
+
+/* One walking line of the template: motors of anchor r0 bound to a filament
+ * of orientation k centred at x = r0 - (dx, dy) cells, at nodes
+ * j0 .. j0 + len - 1; off is the line's first entry in mb[r0][]. */
+typedef struct {
+  int k, dx, dy, j0, len, off;
+} rc_line;
+
+/* Whether the cell at offset (ex, ey) from the filament's cell is within reach
+ * of a head at (hx, hy) cells from that cell's lower-left corner: the gap from
+ * the head to the cell's square in each direction, in physical units, then
+ * the squared distance against rc^2 (evaluated without fused operations). */
+static int rc_reach(double hx, double hy, int ex, int ey, double dx, double dy, double rc2) {
+  double gx = dmax(dmax((double)ex - hx, hx - (double)(ex + 1)), 0.0);
+  double gy = dmax(dmax((double)ey - hy, hy - (double)(ey + 1)), 0.0);
+  double px = gx * dx, py = gy * dy;
+  return px * px + py * py <= rc2;
+}
+
+static int cmp_line(const void* a, const void* b) {
+  const rc_line *x = (const rc_line*)a, *y = (const rc_line*)b;
+  if (x->j0 != y->j0) return x->j0 < y->j0 ? -1 : 1;
+  if (x->dy != y->dy) return x->dy < y->dy ? -1 : 1;
+  if (x->dx != y->dx) return x->dx < y->dx ? -1 : 1;
+  return 0;
+}
+
+/* The template: for each orientation k (in order), every anchor offset in
+ * reach of some node, split into runs of consecutive nodes in reach; the lines
+ * of one k sorted by (first node, dy, dx). w[k][j] = 1 / n_a(k, j). Returns
+ * OR_ERR_INVALID if two offsets of the template could name the same cell of
+ * the periodic grid (the reach spans the grid). */
+static int rc_build(const or_grid* g, const or_rates* r, double rc, rc_line** out, int* nl_out,
+                    int* nconf_out, double* w) {
+  if (!(rc >= 0.0) || !isfinite(rc)) return OR_ERR_INVALID;
+  int ns = g->ns;
+  double dx = dx_of(g), dy = dy_of(g), dth = dth_of(g), rc2 = rc * rc;
+  double* hx = (double*)malloc(sizeof(double) * 2 * (size_t)ns);
+  int* cnt = (int*)malloc(sizeof(int) * (size_t)ns);
+  int cap = 256, nl = 0;
+  rc_line* L = (rc_line*)malloc(sizeof(rc_line) * (size_t)cap);
+  if (!hx || !cnt || !L) { free(hx); free(cnt); free(L); return OR_ERR_NOMEM; }
+  double* hy = hx + ns;
+  int minx = 0, maxx = 0, miny = 0, maxy = 0;
+  for (int k = 0; k < g->nth; ++k) {
+    double th = k * dth, ct = cos(th), st = sin(th);
+    double lo_x = 1e300, hi_x = -1e300, lo_y = 1e300, hi_y = -1e300;
+    for (int j = 0; j < ns; ++j) {
+      double disp = r->ell * g->L * (double)(2 * j + 1 - ns) / (2.0 * ns);
+      hx[j] = disp * ct / dx + 0.5;
+      hy[j] = disp * st / dy + 0.5;
+      lo_x = dmin(lo_x, hx[j]); hi_x = dmax(hi_x, hx[j]);
+      lo_y = dmin(lo_y, hy[j]); hi_y = dmax(hi_y, hy[j]);
+    }
+    int x0 = (int)floor(lo_x - rc / dx) - 1, x1 = (int)floor(hi_x + rc / dx) + 1;
+    int y0 = (int)floor(lo_y - rc / dy) - 1, y1 = (int)floor(hi_y + rc / dy) + 1;
+    int first = nl;
+    for (int ey = y0; ey <= y1; ++ey)
+      for (int ex = x0; ex <= x1; ++ex) {
+        int j = 0;
+        while (j < ns) {
+          if (!rc_reach(hx[j], hy[j], ex, ey, dx, dy, rc2)) { ++j; continue; }
+          int j0 = j;
+          while (j < ns && rc_reach(hx[j], hy[j], ex, ey, dx, dy, rc2)) ++j;
+          if (nl == cap) {
+            cap *= 2;
+            rc_line* L2 = (rc_line*)realloc(L, sizeof(rc_line) * (size_t)cap);
+            if (!L2) { free(hx); free(cnt); free(L); return OR_ERR_NOMEM; }
+            L = L2;
+          }
+          rc_line ln = {k, ex, ey, j0, j - j0, 0};
+          L[nl++] = ln;
+          if (ex < minx) minx = ex;
+          if (ex > maxx) maxx = ex;
+          if (ey < miny) miny = ey;
+          if (ey > maxy) maxy = ey;
+        }
+      }
+    qsort(L + first, (size_t)(nl - first), sizeof(rc_line), cmp_line);
+    for (int j = 0; j < ns; ++j) cnt[j] = 0;
+    for (int l = first; l < nl; ++l)
+      for (int j = L[l].j0; j < L[l].j0 + L[l].len; ++j) cnt[j] += 1;
+    if (w)
+      for (int j = 0; j < ns; ++j) w[(size_t)k * ns + j] = 1.0 / cnt[j];
+  }
+  int off = 0;
+  for (int l = 0; l < nl; ++l) {
+    L[l].off = off;
+    off += L[l].len;
+  }
+  free(hx);
+  free(cnt);
+  if (maxx - minx >= g->nx || maxy - miny >= g->ny) { free(L); return OR_ERR_INVALID; }
+  *out = L;
+  *nl_out = nl;
+  *nconf_out = off;
+  return OR_OK;
+}
+
+/* Filament cell x of a line of anchor r0 = (ax, ay). */
+static size_t rc_fil(const or_grid* g, const rc_line* l, int ax, int ay) {
+  return cidx(g, wrap(ax - l->dx, g->nx), wrap(ay - l->dy, g->ny));
+}
+
+/* Motors per filament n_b = sum over anchors and nodes of Mb ds, and the force
+ * dipole m1 = sum s_j Mb ds (m1 may be NULL), per (x, theta): a gather over
+ * the anchors of every line of each row, in template order. */
+static void rc_rows(const or_grid* g, const rc_line* L, int nl, int nconf, const double* mb,
+                    double* nb, double* m1) {
+  double ds = ds_of(g);
+  size_t rows = ncell(g) * g->nth;
+  for (size_t q = 0; q < rows; ++q) {
+    nb[q] = 0.0;
+    if (m1) m1[q] = 0.0;
+  }
+  for (int iy = 0; iy < g->ny; ++iy)
+    for (int ix = 0; ix < g->nx; ++ix)
+      for (int l = 0; l < nl; ++l) {
+        size_t a = cidx(g, wrap(ix + L[l].dx, g->nx), wrap(iy + L[l].dy, g->ny));
+        const double* M = mb + a * (size_t)nconf + L[l].off;
+        double acc = 0.0, acc1 = 0.0;
+        for (int q = 0; q < L[l].len; ++q) {
+          acc += M[q] * ds;
+          acc1 += s_node(g, L[l].j0 + q) * M[q] * ds;
+        }
+        nb[pidx(g, ix, iy, L[l].k)] += acc;
+        if (m1) m1[pidx(g, ix, iy, L[l].k)] += acc1;
+      }
+}
+
+/* Eq. 5 at every anchor, C(r0) = sum over B_rc(r0) of psi Mb ds dth (lines in
+ * template order), the Alg. 2 scale-down of B_rc(r0) where C exceeds the
+ * total M, and Eq. 6. */
+static void rc_close(const or_grid* g, const rc_line* L, int nl, int nconf, const double* psi,
+                     double* mb, const double* mtot, double* mf, double* c) {
+  double ds = ds_of(g), dth = dth_of(g);
+  for (int ay = 0; ay < g->ny; ++ay)
+    for (int ax = 0; ax < g->nx; ++ax) {
+      size_t a = cidx(g, ax, ay);
+      double* Ma = mb + a * (size_t)nconf;
+      double C = 0.0;
+      for (int l = 0; l < nl; ++l) {
+        double nbl = 0.0;
+        for (int q = 0; q < L[l].len; ++q) nbl += Ma[L[l].off + q] * ds;
+        C += psi[rc_fil(g, &L[l], ax, ay) * g->nth + L[l].k] * nbl * dth;
+      }
+      if (mtot[a] < C) { /* Alg. 2 scale-down */
+        double f = mtot[a] / C;
+        for (int q = 0; q < nconf; ++q) Ma[q] *= f;
+        C = mtot[a];
+      }
+      c[a] = C;
+      mf[a] = mtot[a] - C; /* Eq. 6 */
+    }
+}
+
+/* The template, for tests: lines as 6 ints each (k, dx, dy, j0, len, off)
+ * when max_lines allows; the number of lines and of configurations per anchor;
+ * w [nth][ns] = 1 / n_a (may be NULL). */
+int or_rc_template(const or_grid* g, const or_rates* r, double rc, int* lines, int max_lines,
+                   int* nlines, int* nconf, double* w) {
+  if (!grid_ok(g) || !r || !nlines || !nconf) return OR_ERR_INVALID;
+  rc_line* L;
+  int nl, nconf_, st = rc_build(g, r, rc, &L, &nl, &nconf_, w);
+  if (st) return st;
+  *nlines = nl;
+  *nconf = nconf_;
+  if (lines && max_lines >= nl)
+    for (int l = 0; l < nl; ++l) {
+      int* o = lines + 6 * (size_t)l;
+      o[0] = L[l].k; o[1] = L[l].dx; o[2] = L[l].dy; o[3] = L[l].j0; o[4] = L[l].len;
+      o[5] = L[l].off;
+    }
+  free(L);
+  return OR_OK;
+}
+
+/* State set-up with the capture radius: C at every anchor, the scale-down, Mf.
+ * mb is [cells][nconf] (anchor-major, template order). */
+int or_init_free_rc(const or_grid* g, const or_rates* r, double rc, const double* psi,
+                    double* mb, const double* mtot, double* mf, double* c) {
+  if (!grid_ok(g) || !r || !psi || !mb || !mtot || !mf || !c) return OR_ERR_INVALID;
+  rc_line* L;
+  int nl, nconf, st = rc_build(g, r, rc, &L, &nl, &nconf, NULL);
+  if (st) return st;
+  rc_close(g, L, nl, nconf, psi, mb, mtot, mf, c);
+  free(L);
+  return OR_OK;
+}
+
+/* n_b and m1 per (x, theta) of a state with the capture radius ([cells][nth]). */
+int or_rc_rows(const or_grid* g, const or_rates* r, double rc, const double* mb, double* nb,
+               double* m1) {
+  if (!grid_ok(g) || !r || !mb || !nb) return OR_ERR_INVALID;
+  rc_line* L;
+  int nl, nconf, st = rc_build(g, r, rc, &L, &nl, &nconf, NULL);
+  if (st) return st;
+  rc_rows(g, L, nl, nconf, mb, nb, m1);
+  free(L);
+  return OR_OK;
+}
+
+/* One substep with the capture radius: n_b of the state (the gliding speed),
+ * psi by Eq. 1, then Alg. 2 per anchor r0: every line of B_rc(r0) by the RK2
+ * half and full stage of Eq. 4 (walking along the line; binding
+ * k_on Mf(r0) / n_a(k, j) with Mf(r0) frozen over both stages), the coarse
+ * reduction of Eq. 5 with psi at the new time, the scale-down at r0, Eq. 6. */
+int or_substep_rc(const or_grid* g, const or_rates* r, double rc, double dt, const double* u,
+                  double* psi, double* mb, double* mf, double* c, const double* mtot) {
+  if (!grid_ok(g) || !r || !u || !psi || !mb || !mf || !c || !mtot) return OR_ERR_INVALID;
+  rc_line* L;
+  int nl, nconf;
+  double* w = (double*)malloc(sizeof(double) * (size_t)g->nth * g->ns);
+  if (!w) return OR_ERR_NOMEM;
+  int st = rc_build(g, r, rc, &L, &nl, &nconf, w);
+  if (st) { free(w); return st; }
+  size_t rows = ncell(g) * g->nth;
+  int ns = g->ns;
+  double ds = ds_of(g), dth = dth_of(g);
+  double* nb = (double*)malloc(sizeof(double) * rows);
+  double* pn = (double*)malloc(sizeof(double) * rows);
+  double* buf = (double*)malloc(sizeof(double) * (5 * (size_t)ns + 2));
+  if (!nb || !pn || !buf) { free(w); free(L); free(nb); free(pn); free(buf); return OR_ERR_NOMEM; }
+  double *R = buf, *Ms = buf + ns, *Mss = buf + 2 * ns, *Phi = buf + 3 * ns;
+  rc_rows(g, L, nl, nconf, mb, nb, NULL);   /* n_b at the start of the substep */
+  psi_transport(g, r, dt, u, psi, nb, pn);  /* Eq. 1 */
+  for (int ay = 0; ay < g->ny; ++ay)
+    for (int ax = 0; ax < g->nx; ++ax) {
+      size_t a = cidx(g, ax, ay);
+      double* Ma = mb + a * (size_t)nconf;
+      double mfa = mf[a], Cpre = 0.0;
+      for (int l = 0; l < nl; ++l) {
+        const rc_line* ln = &L[l];
+        double* M = Ma + ln->off;
+        const double* wl = w + (size_t)ln->k * ns + ln->j0;
+        int n = ln->len;
+        /* Alg. 2: half stage to t+dt/2, then full stage to t+dt; Mf frozen */
+        walk_fluxes(n, r->v_walk, M, Phi);
+        for (int q = 0; q < n; ++q)
+          R[q] = -(Phi[q + 1] - Phi[q]) / ds - r->k_off * M[q] + r->k_on * mfa * wl[q];
+        for (int q = 0; q < n; ++q) Ms[q] = M[q] + 0.5 * dt * R[q];
+        walk_fluxes(n, r->v_walk, Ms, Phi);
+        for (int q = 0; q < n; ++q)
+          R[q] = -(Phi[q + 1] - Phi[q]) / ds - r->k_off * Ms[q] + r->k_on * mfa * wl[q];
+        for (int q = 0; q < n; ++q) Mss[q] = M[q] + dt * R[q];
+        double nbl = 0.0;
+        for (int q = 0; q < n; ++q) { M[q] = Mss[q]; nbl += Mss[q] * ds; }
+        Cpre += pn[rc_fil(g, ln, ax, ay) * g->nth + ln->k] * nbl * dth; /* Eq. 5 */
+      }
+      double C = Cpre;
+      if (mtot[a] < Cpre) { /* Alg. 2 scale-down at r0 */
+        double f = mtot[a] / Cpre;
+        for (int q = 0; q < nconf; ++q) Ma[q] *= f;
+        C = mtot[a];
+      }
+      c[a] = C;
+      mf[a] = mtot[a] - C; /* Eq. 6 */
+    }
+  memcpy(psi, pn, sizeof(double) * rows);
+  free(w); free(L); free(nb); free(pn); free(buf);
+  return OR_OK;
+}
+
+/* The motor force of Eq. 10 with the capture radius: every configuration's
+ * force F p psi Mb ds dth acts at its head, in the cell under
+ * x + (l/L) s_j p_k (the cell offset of the rc -> 0 anchors). F [2][ny][nx]. */
+int or_rc_force(const or_grid* g, const or_rates* r, double rc, const double* psi,
+                const double* mb, double* F) {
+  if (!grid_ok(g) || !r || !psi || !mb || !F) return OR_ERR_INVALID;
+  rc_line* L;
+  int nl, nconf, st = rc_build(g, r, rc, &L, &nl, &nconf, NULL);
+  if (st) return st;
+  size_t nc = ncell(g);
+  double ds = ds_of(g), dth = dth_of(g);
+  int* ox = (int*)malloc(sizeof(int) * 2 * (size_t)g->nth * g->ns);
+  if (!ox) { free(L); return OR_ERR_NOMEM; }
+  int* oy = ox + (size_t)g->nth * g->ns;
+  anchor_offsets(g, r, ox, oy);
+  for (size_t q = 0; q < 2 * nc; ++q) F[q] = 0.0;
+  for (int ay = 0; ay < g->ny; ++ay)
+    for (int ax = 0; ax < g->nx; ++ax) {
+      const double* Ma = mb + cidx(g, ax, ay) * (size_t)nconf;
+      for (int l = 0; l < nl; ++l) {
+        int k = L[l].k;
+        int fx = wrap(ax - L[l].dx, g->nx), fy = wrap(ay - L[l].dy, g->ny);
+        double th = k * dth, ct = cos(th), stn = sin(th);
+        double p = psi[pidx(g, fx, fy, k)];
+        for (int q = 0; q < L[l].len; ++q) {
+          int j = L[l].j0 + q;
+          size_t h = anchor_of(g, ox, oy, fx, fy, k, j);
+          double m = Ma[L[l].off + q];
+          F[h] += r->force_scale * ct * p * m * ds * dth;
+          F[nc + h] += r->force_scale * stn * p * m * ds * dth;
+        }
+      }
+    }
+  free(ox);
+  free(L);
+  return OR_OK;
+}
+
 int or_run(const or_grid* g, const or_rates* r, double dt, const double* u, double* psi,
            double* mb, double* mf, double* c, const double* mtot, int nsub) {
   for (int n = 0; n < nsub; ++n) {
@@ -580,23 +909,21 @@ int or_run(const or_grid* g, const or_rates* r, double dt, const double* u, doub
  *   sum C dx dy, total free sum Mf dx dy, total motors (bound + free),
  *   polar order |sum psi e^{i theta}| / sum psi, mean over cells of
  *   tr sigma_a, sum psi cos, sum psi sin (over all cells and angles). */
-int or_moments(const or_grid* g, const or_rates* r, const double* psi, const double* mb,
-               const double* mf, const double* c, double* fields, double* scalars) {
-  if (!grid_ok(g) || !r || !psi || !mb || !mf || !c || !fields || !scalars) return OR_ERR_INVALID;
+/* The moments from the per-row sums n_b and m1 ([cells][nth]); F (may be
+ * NULL) replaces fields 7, 8 (the force acting elsewhere than in the
+ * filament's cell). */
+static void moments_rows(const or_grid* g, const or_rates* r, const double* psi,
+                         const double* nb, const double* m1, const double* mf, const double* c,
+                         const double* F, double* fields, double* scalars) {
   size_t nc = ncell(g);
-  double dth = dth_of(g), ds = ds_of(g), dA = dx_of(g) * dy_of(g);
+  double dth = dth_of(g), dA = dx_of(g) * dy_of(g);
   double Ntot = 0.0, bound = 0.0, freem = 0.0, sc = 0.0, ss = 0.0, spsi = 0.0, tr = 0.0;
   for (size_t i = 0; i < nc; ++i) {
     double f[12] = {0};
     for (int k = 0; k < g->nth; ++k) {
       double th = k * dth, ct = cos(th), st = sin(th);
       double p = psi[i * g->nth + k];
-      const double* M = mb + (i * g->nth + k) * g->ns;
-      double nbk = 0.0, m1k = 0.0;
-      for (int j = 0; j < g->ns; ++j) {
-        nbk += M[j] * ds;
-        m1k += s_node(g, j) * M[j] * ds;
-      }
+      double nbk = nb[i * g->nth + k], m1k = m1[i * g->nth + k];
       f[0] += p * dth;
       f[1] += p * ct * dth;
       f[2] += p * st * dth;
@@ -613,6 +940,10 @@ int or_moments(const or_grid* g, const or_rates* r, const double* psi, const dou
     }
     f[5] = c[i];
     f[6] = mf[i];
+    if (F) {
+      f[7] = F[i];
+      f[8] = F[nc + i];
+    }
     for (int q = 0; q < 12; ++q) fields[(size_t)q * nc + i] = f[q];
     Ntot += f[0] * dA;
     bound += c[i] * dA;
@@ -627,7 +958,46 @@ int or_moments(const or_grid* g, const or_rates* r, const double* psi, const dou
   scalars[5] = tr / (double)nc;
   scalars[6] = sc;
   scalars[7] = ss;
+}
+
+int or_moments(const or_grid* g, const or_rates* r, const double* psi, const double* mb,
+               const double* mf, const double* c, double* fields, double* scalars) {
+  if (!grid_ok(g) || !r || !psi || !mb || !mf || !c || !fields || !scalars) return OR_ERR_INVALID;
+  size_t rows = ncell(g) * g->nth;
+  double ds = ds_of(g);
+  double* nb = (double*)malloc(sizeof(double) * 2 * rows);
+  if (!nb) return OR_ERR_NOMEM;
+  double* m1 = nb + rows;
+  for (size_t q = 0; q < rows; ++q) {
+    const double* M = mb + q * g->ns;
+    double nbk = 0.0, m1k = 0.0;
+    for (int j = 0; j < g->ns; ++j) {
+      nbk += M[j] * ds;
+      m1k += s_node(g, j) * M[j] * ds;
+    }
+    nb[q] = nbk;
+    m1[q] = m1k;
+  }
+  moments_rows(g, r, psi, nb, m1, mf, c, NULL, fields, scalars);
+  free(nb);
   return OR_OK;
+}
+
+/* The moments of a state with the capture radius: n_b and m1 summed over the
+ * anchors, C and Mf per anchor, and the force of Eq. 10 at the heads. */
+int or_moments_rc(const or_grid* g, const or_rates* r, double rc, const double* psi,
+                  const double* mb, const double* mf, const double* c, double* fields,
+                  double* scalars) {
+  if (!grid_ok(g) || !r || !psi || !mb || !mf || !c || !fields || !scalars) return OR_ERR_INVALID;
+  size_t rows = ncell(g) * g->nth;
+  double* nb = (double*)malloc(sizeof(double) * (2 * rows + 2 * ncell(g)));
+  if (!nb) return OR_ERR_NOMEM;
+  double *m1 = nb + rows, *F = nb + 2 * rows;
+  int st = or_rc_rows(g, r, rc, mb, nb, m1);
+  if (!st) st = or_rc_force(g, r, rc, psi, mb, F);
+  if (!st) moments_rows(g, r, psi, nb, m1, mf, c, F, fields, scalars);
+  free(nb);
+  return st;
 }
 
 /* ------------------------------------------------- tangent-linear substep */

@@ -69,6 +69,13 @@ def _load():
             lib.or_substep_anchor.argtypes = [G, R, C.c_double, P, P, P, P, P, P]
             lib.or_anchor_force.argtypes = [G, R, P, P, P]
             lib.or_anchor_offsets.argtypes = [G, R, IP, IP]
+            D = C.c_double
+            lib.or_rc_template.argtypes = [G, R, D, IP, C.c_int, IP, IP, P]
+            lib.or_init_free_rc.argtypes = [G, R, D, P, P, P, P, P]
+            lib.or_rc_rows.argtypes = [G, R, D, P, P, P]
+            lib.or_substep_rc.argtypes = [G, R, D, D, P, P, P, P, P, P]
+            lib.or_rc_force.argtypes = [G, R, D, P, P, P]
+            lib.or_moments_rc.argtypes = [G, R, D, P, P, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -333,3 +340,89 @@ def anchor_offsets(grid, rates):
     _check(_load().or_anchor_offsets(C.byref(_grid(grid)), C.byref(_rates(rates)),
                                      ox.ctypes.data_as(IP), oy.ctypes.data_as(IP)), "anchor_offsets")
     return ox, oy
+
+
+# ---- finite capture radius: the anchor axis of Mb (next row f2)
+
+
+@dataclass
+class RcTemplate:
+    """The configurations of B_rc(r0), the same for every anchor r0: lines
+    [n][6] = (k, dx, dy, j0, len, off) -- the motors of anchor r0 on a filament
+    of orientation k centred at r0 - (dx, dy) cells, at nodes j0..j0+len-1,
+    stored from entry off of mb[r0][] -- and w [ntheta][ns] = 1 / n_a."""
+
+    lines: np.ndarray
+    nconf: int
+    w: np.ndarray
+
+
+def rc_template(grid, rates, rc: float) -> RcTemplate:
+    IP = C.POINTER(C.c_int)
+    nl, nconf = C.c_int(0), C.c_int(0)
+    w = np.empty((grid.ntheta, grid.ns))
+    lib = _load()
+    _check(lib.or_rc_template(C.byref(_grid(grid)), C.byref(_rates(rates)), float(rc), None, 0,
+                              C.byref(nl), C.byref(nconf), _p(w)), "rc_template")
+    lines = np.empty((nl.value, 6), dtype=np.int32)
+    _check(lib.or_rc_template(C.byref(_grid(grid)), C.byref(_rates(rates)), float(rc),
+                              lines.ctypes.data_as(IP), nl.value, C.byref(nl), C.byref(nconf),
+                              _p(w)), "rc_template")
+    return RcTemplate(lines, nconf.value, w)
+
+
+def make_state_rc(grid, rates, rc: float, psi, mb=None, mtot=None) -> State:
+    """A state of the capture-radius model: mb [ny][nx][nconf] (anchor-major,
+    template order; default 0), then C, the scale-down and Mf per anchor."""
+    g = grid
+    nconf = rc_template(g, rates, rc).nconf
+    psi = np.ascontiguousarray(psi, dtype=np.float64).reshape(g.ny, g.nx, g.ntheta).copy()
+    mb = (np.zeros((g.ny, g.nx, nconf)) if mb is None
+          else np.ascontiguousarray(mb, dtype=np.float64).reshape(g.ny, g.nx, nconf).copy())
+    mtot = (np.ones((g.ny, g.nx)) if mtot is None
+            else np.ascontiguousarray(mtot, dtype=np.float64).reshape(g.ny, g.nx).copy())
+    mf = np.empty((g.ny, g.nx))
+    c = np.empty((g.ny, g.nx))
+    _check(_load().or_init_free_rc(C.byref(_grid(g)), C.byref(_rates(rates)), float(rc), _p(psi),
+                                   _p(mb), _p(mtot), _p(mf), _p(c)), "init_free_rc")
+    return State(g, psi, mb, mf, c, mtot)
+
+
+def run_rc(grid, rates, rc: float, state: State, u: np.ndarray, dt_: float, nsub: int) -> State:
+    """nsub substeps of the capture-radius model (or_substep_rc), in place."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    lib = _load()
+    for _ in range(nsub):
+        _check(lib.or_substep_rc(C.byref(_grid(grid)), C.byref(_rates(rates)), float(rc),
+                                 float(dt_), _p(u), _p(state.psi), _p(state.mb), _p(state.mf),
+                                 _p(state.c), _p(state.mtot)), "substep_rc")
+    return state
+
+
+def rows_rc(grid, rates, rc: float, state: State):
+    """(n_b, m1) per (x, theta) of a capture-radius state, [ny][nx][ntheta]."""
+    nb = np.empty((grid.ny, grid.nx, grid.ntheta))
+    m1 = np.empty((grid.ny, grid.nx, grid.ntheta))
+    _check(_load().or_rc_rows(C.byref(_grid(grid)), C.byref(_rates(rates)), float(rc),
+                              _p(state.mb), _p(nb), _p(m1)), "rc_rows")
+    return nb, m1
+
+
+def force_rc(grid, rates, rc: float, state: State) -> np.ndarray:
+    """Motor force of Eq. 10 at the heads of a capture-radius state, [2][ny][nx]."""
+    F = np.empty((2, grid.ny, grid.nx))
+    _check(_load().or_rc_force(C.byref(_grid(grid)), C.byref(_rates(rates)), float(rc),
+                               _p(state.psi), _p(state.mb), _p(F)), "rc_force")
+    return F
+
+
+def moments_rc(grid, rates, rc: float, state: State):
+    """moments() of a capture-radius state (n_b, m1 over the anchors, the force
+    at the heads)."""
+    g = grid
+    f = np.empty((12, g.ny, g.nx))
+    s = np.empty(8)
+    _check(_load().or_moments_rc(C.byref(_grid(g)), C.byref(_rates(rates)), float(rc),
+                                 _p(state.psi), _p(state.mb), _p(state.mf), _p(state.c), _p(f),
+                                 _p(s)), "moments_rc")
+    return dict(zip(FIELD_NAMES, f)), dict(zip(SCALAR_NAMES, s))

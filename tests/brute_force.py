@@ -200,3 +200,109 @@ def substep_anchor(grid, rates, dt, u, psi, mb, mf, mtot):
                 new[iy][ix][k] = [v * scale[a][b] for v, (a, b) in
                                   zip(new[iy][ix][k], [anchor(ix, iy, k, j) for j in range(ns)])]
     return psi_new, new, mf_new, c_new
+
+
+def _square_dist(hx, hy, ax, ay, grid):
+    """Distance from the point (hx, hy) to the closed square of cell (ax, ay),
+    over the periodic images of the unit square (nearest point by clamping)."""
+    nx, ny = grid.nx, grid.ny
+    best = math.inf
+    for sx in (-1.0, 0.0, 1.0):
+        for sy in (-1.0, 0.0, 1.0):
+            x0, y0 = ax / nx + sx, ay / ny + sy
+            px = min(max(hx, x0), x0 + 1.0 / nx)
+            py = min(max(hy, y0), y0 + 1.0 / ny)
+            best = min(best, math.hypot(hx - px, hy - py))
+    return best
+
+
+def capture_sets(grid, rates, rc):
+    """{(ax, ay, fx, fy, k, j)}: every configuration of the capture-radius
+    model -- anchor cell (ax, ay) within rc of the head of node j of a
+    filament of orientation k centred in cell (fx, fy) -- found by measuring
+    each head's distance to every cell's square directly."""
+    nx, ny, nth, ns, L = grid.nx, grid.ny, grid.ntheta, grid.ns, grid.L
+    out = set()
+    for fy in range(ny):
+        for fx in range(nx):
+            for k in range(nth):
+                th = k * 2.0 * math.pi / nth
+                for j in range(ns):
+                    s = -0.5 * L + (j + 0.5) * (L / ns)
+                    hx = (fx + 0.5) / nx + rates.ell * s * math.cos(th)
+                    hy = (fy + 0.5) / ny + rates.ell * s * math.sin(th)
+                    for ay in range(ny):
+                        for ax in range(nx):
+                            if _square_dist(hx, hy, ax, ay, grid) <= rc:
+                                out.add((ax, ay, fx, fy, k, j))
+    return out
+
+
+def substep_rc(grid, rates, rc, dt, u, psi, mbd, mf, mtot):
+    """One substep of the capture-radius model on a dict of configurations
+    {(ax, ay, fx, fy, k, j): Mb} (every member of capture_sets present).
+    psi by the plain substep; each motor keeps its anchor while it walks, so
+    walking runs along j at fixed (anchor, filament, k) between members only
+    (nothing walks in before a run, the last member of a run flows out);
+    binding at a node is k_on Mf(anchor) divided by the number of anchors in
+    reach of that node; then the coarse density, the scale-down and the free
+    motors per anchor. Returns (psi, mbd, mf, c)."""
+    nx, ny, nth, ns, L = grid.nx, grid.ny, grid.ntheta, grid.ns, grid.L
+    dth, ds = 2.0 * math.pi / nth, L / ns
+    nb = [[[0.0] * nth for _ in range(nx)] for _ in range(ny)]
+    for (ax, ay, fx, fy, k, j), m in mbd.items():
+        nb[fy][fx][k] += m * ds
+    # psi at the new time from the plain substep, given these n_b (motor part
+    # discarded): a one-node row per (cell, k) holding n_b / ds
+    rows = [[[[nb[iy][ix][k] / ds] for k in range(nth)] for ix in range(nx)] for iy in range(ny)]
+    g1 = type(grid)(nx, ny, nth, 1, ds)
+    psi_new = substep(g1, rates, dt, u, psi, rows, mf, mtot)[0]
+    count = {}
+    for (ax, ay, fx, fy, k, j) in mbd:
+        count[(fx, fy, k, j)] = count.get((fx, fy, k, j), 0) + 1
+
+    def member(key):
+        return key in mbd
+
+    def rhs(vals):
+        out = {}
+        for key, m in vals.items():
+            ax, ay, fx, fy, k, j = key
+            left = (ax, ay, fx, fy, k, j - 1)
+            right = (ax, ay, fx, fy, k, j + 1)
+
+            def flux_right(kk):
+                a_, b_, c_, d_, e_, jj = kk
+                r_key = (a_, b_, c_, d_, e_, jj + 1)
+                if not member(r_key):
+                    return rates.v_walk * vals[kk]
+                l_key = (a_, b_, c_, d_, e_, jj - 1)
+                back = vals[kk] - (vals[l_key] if member(l_key) else 0.0)
+                fwd = vals[r_key] - vals[kk]
+                return rates.v_walk * (vals[kk] + 0.5 * _slope(back, fwd))
+
+            fin = flux_right(left) if member(left) else 0.0
+            out[key] = (-(flux_right(key) - fin) / ds - rates.k_off * m
+                        + rates.k_on * mf[ay][ax] / count[(fx, fy, k, j)])
+        return out
+
+    k1 = rhs(mbd)
+    half = {key: m + 0.5 * dt * k1[key] for key, m in mbd.items()}
+    k2 = rhs(half)
+    new = {key: m + dt * k2[key] for key, m in mbd.items()}
+    coarse = [[0.0] * nx for _ in range(ny)]
+    for (ax, ay, fx, fy, k, j), m in new.items():
+        coarse[ay][ax] += psi_new[fy][fx][k] * m * ds * dth
+    c_new = [[0.0] * nx for _ in range(ny)]
+    mf_new = [[0.0] * nx for _ in range(ny)]
+    scale = [[1.0] * nx for _ in range(ny)]
+    for ay in range(ny):
+        for ax in range(nx):
+            cc = coarse[ay][ax]
+            if cc > mtot[ay][ax]:
+                scale[ay][ax] = mtot[ay][ax] / cc
+                cc = mtot[ay][ax]
+            c_new[ay][ax] = cc
+            mf_new[ay][ax] = mtot[ay][ax] - cc
+    new = {key: m * scale[key[1]][key[0]] for key, m in new.items()}
+    return psi_new, new, mf_new, c_new

@@ -315,6 +315,43 @@ mm_status mm_motor_local(mm_handle* h, double T, const int* nsteps_in, int* nste
  * available) and mm_set_anchors returns MM_ERR_STATE during a recording. */
 mm_status mm_set_anchors(mm_handle* h, int enable);
 
+/* ---- Finite capture radius (Sec. 2's B_rc(r0), Eq. 4's indicator, Alg. 2 per r0)
+ *
+ * mm_set_capture(h, r_c): r_c >= 0 keeps the anchor r0 of a bound motor as an
+ * axis of the motor density: Mb(r0, x, theta, s) is tracked where the motor
+ * head x + (l/L) s p (l/L = rates.ell) is within reach of r0, a cell being in
+ * reach when the distance from the head to the cell's square is at most r_c
+ * (physical units of the unit square); at r_c = 0 the reach is the cell under
+ * the head. Each substep runs Alg. 2 per anchor: every configuration by the
+ * RK2 of Eq. 4 with Mf(r0) frozen, a motor keeping its anchor while it walks
+ * (so the nodes in reach of one anchor form walking lines: no inflow at a
+ * line's first node, donor-cell outflow at its last, the motor rejoining the
+ * free pool through Eq. 6), binding k_on Mf(r0) / n_a shared among the n_a
+ * anchors in reach of the node; then Eq. 5 at r0 with psi at the new time,
+ * the scale-down at r0 and Eq. 6 at r0. n_b sums over anchors and nodes; the
+ * force of Eq. 10 (mm_moments fields 7, 8) acts in the cell under each head.
+ * r_c < 0 switches back to the models above. Either switch discards the
+ * motors (Mb = 0, Mf = M; psi is kept).
+ *
+ * With a capture radius, the mb arrays of mm_set_state / mm_get_state are
+ * [ny][nx][nconf] (float64 at this boundary): for each anchor cell, its
+ * configurations in template order. mm_capture_template returns the template,
+ * the same for every anchor: nlines lines of 6 ints (k, dx, dy, j0, len, off)
+ * -- the motors of anchor r0 bound to a filament of orientation k centred at
+ * r0 - (dx, dy) cells, at nodes j0 .. j0 + len - 1, stored from entry off --
+ * when max_lines >= nlines (lines may be NULL), nconf, and w [ntheta][ns] =
+ * 1 / n_a (may be NULL). Lines are sorted by k, then j0, dy, dx.
+ *
+ * MM_ERR_UNSUPPORTED: a batch or batch member; ns > 256; a reach wider than the
+ * periodic grid (two offsets would name one cell). MM_ERR_STATE: during an
+ * adjoint recording, or with mm_set_anchors on. MM_ERR_OOM: the state (cells x
+ * nconf values) does not fit. With a capture radius set, mm_set_checkpointing,
+ * mm_motor_local and mm_save_snapshot return MM_ERR_UNSUPPORTED, the fluid
+ * solve refuses the dipole term, and mm_set_rates refuses a new l/L. */
+mm_status mm_set_capture(mm_handle* h, double r_c);
+mm_status mm_capture_template(mm_handle* h, int* lines, int max_lines, int* nlines, int* nconf,
+                              double* w);
+
 /* ---- Thin-gap fluid solve (Eq. 7-9, Alg. 1 after the inner loop) --------------
  *
  * The fluid fills the gap 0 <= z <= 1 between two no-slip plates and is

@@ -49,8 +49,10 @@ def build(force: bool = False, verbose: bool = False, ptxas_v: bool = False) -> 
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
-    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC,
-             *ARCH]
+    # host code without floating-point contraction: the anchor tables decide
+    # integers in float64 and must round as the definition's plain operations
+    flags = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler",
+             "-ffp-contract=off", "-I" + INCLUDE, "-I" + CSRC, *ARCH]
     if ptxas_v:
         flags += ["-Xptxas", "-v"]
 

@@ -530,6 +530,24 @@ struct ScatterF {
 
 namespace mmh {
 
+// The anchor tables ([nth][ns] offsets and window indices) and the per-cell
+// float64 accumulators and factors.
+mm_status anchor_alloc(mm_handle* h) {
+  const size_t nc = (size_t)h->ncells;
+  size_t freeb = 0, totalb = 0;
+  CK(cudaMemGetInfo(&freeb, &totalb));
+  const size_t need = (size_t)h->g.ntheta * h->g.ns * sizeof(int2) + 2 * nc * 8 + 64;
+  if (need + (1 << 20) > freeb) return fail(h, MM_ERR_OOM, "anchor buffers do not fit");
+  CK(cudaMalloc((void**)&h->anc_off, (size_t)h->g.ntheta * h->g.ns * sizeof(int2)));
+  CK(cudaMalloc((void**)&h->anc_widx, (size_t)h->g.ntheta * h->g.ns * sizeof(int)));
+  CK(cudaMalloc((void**)&h->anc_cacc, nc * 8));
+  CK(cudaMalloc((void**)&h->anc_fsc, nc * 8));
+  CK(cudaMalloc((void**)&h->anc_flags, 4 * sizeof(int)));
+  CK(cudaMemset(h->anc_cacc, 0, nc * 8));
+  CK(cudaMemset(h->anc_flags, 0, 4 * sizeof(int)));
+  return MM_OK;
+}
+
 // The anchor offsets of the current grid and l/L, reduced into [0, nx) and
 // [0, ny), with the formula of the definition evaluated in float64 by products
 // and quotients only (no operation a compiler could fuse).
@@ -613,23 +631,12 @@ mm_status mm_set_anchors(mm_handle* h, int enable) {
     return fail(h, MM_ERR_UNSUPPORTED, "non-local anchors are not available in a batch");
   if (h->rec.active)
     return fail(h, MM_ERR_STATE, "non-local anchors are not differentiated: end the adjoint recording first");
+  if (enable && h->capture)
+    return fail(h, MM_ERR_STATE, "a capture radius is set: switch it off (mm_set_capture < 0) first");
   DeviceGuard dg(h->device);
   CK(cudaStreamSynchronize(h->stream));
-  const size_t nc = (size_t)h->ncells;
-  if (enable && !h->anc_off) {
-    size_t freeb = 0, totalb = 0;
-    CK(cudaMemGetInfo(&freeb, &totalb));
-    const size_t need = (size_t)h->g.ntheta * h->g.ns * sizeof(int2) + 2 * nc * 8 + 64;
-    if (need + (1 << 20) > freeb) return fail(h, MM_ERR_OOM, "anchor buffers do not fit");
-    CK(cudaMalloc((void**)&h->anc_off, (size_t)h->g.ntheta * h->g.ns * sizeof(int2)));
-    CK(cudaMalloc((void**)&h->anc_widx, (size_t)h->g.ntheta * h->g.ns * sizeof(int)));
-    CK(cudaMalloc((void**)&h->anc_cacc, nc * 8));
-    CK(cudaMalloc((void**)&h->anc_fsc, nc * 8));
-    CK(cudaMalloc((void**)&h->anc_flags, 4 * sizeof(int)));
-    CK(cudaMemset(h->anc_cacc, 0, nc * 8));
-    CK(cudaMemset(h->anc_flags, 0, 4 * sizeof(int)));
-  }
   mm_status st;
+  if (enable && !h->anc_off && (st = anchor_alloc(h)) != MM_OK) return st;
   if (enable && (st = anchor_table(h)) != MM_OK) return st;
   h->anchors = enable != 0;
   // substep graphs were captured for the other kernels

@@ -38,6 +38,7 @@ void free_recording(mm_handle* h) {
 mm_status free_all(mm_handle* h) {
   free_recording(h);
   fluid_free(h);
+  capture_free(h);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
   if (h->diff_tab) cudaFree(h->diff_tab);
@@ -120,6 +121,7 @@ template StepArgs<double> step_args<double>(mm_handle*, int);
 
 cudaError_t launch_one(mm_handle* h, int parity, cudaStream_t s) {
   if (h->anchors) return launch_anchor_substep(h, parity, s);
+  if (h->capture) return launch_capture_substep(h, parity, s);
   if (h->prec == MM_FP64) {
     StepArgs<double> a = step_args<double>(h, parity);
     return h->V == 2 ? mm::launch_substep<double, 2>(a, h->grid_step, h->block, h->smem, h->tma, s)
@@ -302,6 +304,7 @@ mm_status get_array(mm_handle* h, double* dst, const void* src, size_t n, int on
 
 mm_status run_init(mm_handle* h) {
   if (h->anchors) return run_init_anchor(h);
+  if (h->capture) return run_init_capture(h);
   const double ds = h->g.L / h->g.ns, dth = 2.0 * kPi / h->g.ntheta;
   cudaError_t e;
   if (h->prec == MM_FP64)
@@ -319,6 +322,9 @@ mm_status run_init(mm_handle* h) {
 }
 
 mm_status run_moments(mm_handle* h) {
+  // with a capture radius the rows are the per-node totals over the anchors
+  mm_status st;
+  if (h->capture && (st = capture_rows(h)) != MM_OK) return st;
   const double dth = 2.0 * kPi / h->g.ntheta, ds = h->g.L / h->g.ns;
   const double dA = (1.0 / h->g.nx) * (1.0 / h->g.ny);
   // the moments kernel reads rows with at most 4 values per lane
@@ -339,8 +345,9 @@ mm_status run_moments(mm_handle* h) {
                                   h->g.L, dA, h->fields, h->partial, h->grid_mom, h->prm,
                                   h->stream);
   CK(e);
-  // with anchors the motor force of Eq. 10 acts in the anchor cells
-  if (h->anchors) return anchor_force(h);
+  // with anchors (or a capture radius) the motor force of Eq. 10 acts in the
+  // cells under the heads
+  if (h->anchors || h->capture) return anchor_force(h);
   return MM_OK;
 }
 
@@ -547,6 +554,9 @@ mm_status mm_set_rates(mm_handle* h, const mm_rates* rates) {
   if (h->batch) return not_for_batch(h);
   mm_status st = check_rates(rates, h);
   if (st != MM_OK) return st;
+  if (h->capture && rates->ell != h->r.ell)
+    return fail(h, MM_ERR_STATE,
+                "l/L fixes the capture template: switch the capture radius off, change l/L, set it again");
   DeviceGuard dg(h->device);
   // the substeps recorded so far ran with the old rates, while the replays and
   // the reverse kernels would read the new ones: new rates end a recording
@@ -576,10 +586,13 @@ mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const 
   h->rec.active = false;  // a new state ends an adjoint recording (its memory is kept)
   h->parity = 0;
   if ((st = put_array(h, h->psi[0], psi, h->rows, on_device)) != MM_OK) return st;
+  // with a capture radius Mb is [cells][nconf] (anchor-major, template order)
+  void* mbd = h->capture ? h->rc_mb : h->mb;
+  const size_t mbn = h->capture ? (size_t)h->ncells * h->rc_nconf : h->mbn;
   if (mb) {
-    if ((st = put_array(h, h->mb, mb, h->mbn, on_device)) != MM_OK) return st;
+    if ((st = put_array(h, mbd, mb, mbn, on_device)) != MM_OK) return st;
   } else {
-    CK(cudaMemsetAsync(h->mb, 0, h->mbn * h->tsz, h->stream));
+    CK(cudaMemsetAsync(mbd, 0, mbn * h->tsz, h->stream));
   }
   if (mtot) {
     if ((st = put_array(h, h->mtot, mtot, (size_t)h->ncells, on_device)) != MM_OK) return st;
@@ -613,7 +626,10 @@ mm_status mm_get_state(mm_handle* h, double* psi, double* mb, double* mf, double
   const double* scale = h->prec == MM_FP32_MIXED ? &h->prm->psi_scale : nullptr;
   if (psi && (st = get_array(h, psi, h->psi[h->parity], h->rows, on_device, scale)) != MM_OK)
     return st;
-  if (mb && (st = get_array(h, mb, h->mb, h->mbn, on_device, nullptr)) != MM_OK) return st;
+  if (mb && (st = get_array(h, mb, h->capture ? h->rc_mb : h->mb,
+                            h->capture ? (size_t)h->ncells * h->rc_nconf : h->mbn, on_device,
+                            nullptr)) != MM_OK)
+    return st;
   if (mf && (st = get_array(h, mf, h->mf, (size_t)h->ncells, on_device, nullptr)) != MM_OK) return st;
   if (c && (st = get_array(h, c, h->c, (size_t)h->ncells, on_device, nullptr)) != MM_OK) return st;
   return check_status(h);
@@ -1156,6 +1172,8 @@ mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_
     return MM_OK;
   }
   if (K < 0 || max_substeps < 1) return fail(h, MM_ERR_INVALID, "K >= 1 and max_substeps >= 1");
+  if (h->capture)
+    return fail(h, MM_ERR_UNSUPPORTED, "the adjoint is not available with a capture radius");
   if (h->anchors)
     return fail(h, MM_ERR_UNSUPPORTED, "the adjoint is not available with non-local anchors");
   if (K_inner < 1 || K_inner > K) return fail(h, MM_ERR_INVALID, "1 <= K_inner <= K");

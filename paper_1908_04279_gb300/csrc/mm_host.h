@@ -140,6 +140,16 @@ struct mm_handle {
   double* anc_cacc = nullptr;   // [cells] float64 accumulators of C
   double* anc_fsc = nullptr;    // [cells] scale-down factors
   int* anc_flags = nullptr;     // [4] scale-down flags
+  // finite capture radius (mm_set_capture): the anchor axis of Mb
+  bool capture = false;
+  double rc = 0.0;
+  int rc_nconf = 0, rc_nlines = 0, rc_nchunks = 0, rc_motor_grid = 1;
+  void* rc_mb = nullptr;   // [cells][nconf] motor density, anchor-major (template order)
+  void* rc_ls = nullptr;   // [cells][nlines] line sums of Mb ds
+  void* rc_tab = nullptr;  // the template's device tables (one block)
+  size_t rc_tab_off[5] = {0, 0, 0, 0, 0};
+  std::vector<int> rc_host_lines;  // [nlines][6] (k, dx, dy, j0, len, off)
+  std::vector<double> rc_host_w;   // [nth][ns] 1 / n_a
   // thin-gap fluid solve (mm_fluid_setup)
   bool fluid = false;
   double fl_eps = 0.0, fl_z0 = 0.0;
@@ -237,10 +247,17 @@ mm_status velocity_update(mm_handle* h);  // h->u64 becomes the velocity in effe
 void fluid_free(mm_handle* h);
 
 // Defined in mm_anchor.cu (non-local motor anchors).
+mm_status anchor_alloc(mm_handle* h);  // the anchor tables and accumulators
 mm_status anchor_table(mm_handle* h);
 cudaError_t launch_anchor_substep(mm_handle* h, int parity, cudaStream_t s);
 mm_status run_init_anchor(mm_handle* h);
 mm_status anchor_force(mm_handle* h);
+
+// Defined in mm_capture.cu (finite capture radius).
+void capture_free(mm_handle* h);
+cudaError_t launch_capture_substep(mm_handle* h, int parity, cudaStream_t s);
+mm_status run_init_capture(mm_handle* h);
+mm_status capture_rows(mm_handle* h);  // per-node totals over the anchors into h->mb
 
 // Defined in mm_batch_api.cu.
 mm_status batch_micro_step(mm_handle* h, int n);

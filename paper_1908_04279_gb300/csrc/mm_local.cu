@@ -345,9 +345,10 @@ mm_status mm_motor_local(mm_handle* h, double T, const int* nsteps_in, int* nste
   if (h->rec.active)
     return fail(h, MM_ERR_STATE,
                 "the local-step motor update is not differentiated: end the adjoint recording first");
-  if (h->anchors)
+  if (h->anchors || h->capture)
     return fail(h, MM_ERR_UNSUPPORTED,
-                "local substeps need independent cells: not available with non-local anchors");
+                "local substeps need independent cells: not available with non-local anchors "
+                "or a capture radius");
   DeviceGuard dg(h->device);
   const size_t nc = (size_t)h->ncells;
   if (!h->local_n) CK(cudaMalloc((void**)&h->local_n, nc * sizeof(int)));

@@ -63,8 +63,9 @@ Blocks blocks_of(const mm_handle* h) {
 }
 
 mm_status snap_check(mm_handle* h, size_t bytes) {
-  if (h->anchors)
-    return fail(h, MM_ERR_UNSUPPORTED, "snapshots of a handle with non-local anchors are not supported");
+  if (h->anchors || h->capture)
+    return fail(h, MM_ERR_UNSUPPORTED,
+                "snapshots of a handle with non-local anchors or a capture radius are not supported");
   if (bytes < blocks_of(h).off[7]) return fail(h, MM_ERR_INVALID, "snapshot buffer too small");
   return MM_OK;
 }

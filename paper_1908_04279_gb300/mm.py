@@ -95,6 +95,9 @@ PROTOTYPES = {
     "mm_diffuse": ([_H, C.c_double, C.c_double, C.c_double], C.c_int),
     "mm_motor_local": ([_H, C.c_double, _P, _P, C.c_int], C.c_int),
     "mm_set_anchors": ([_H, C.c_int], C.c_int),
+    "mm_set_capture": ([_H, C.c_double], C.c_int),
+    "mm_capture_template": ([_H, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
+                             C.POINTER(C.c_int), C.POINTER(C.c_double)], C.c_int),
     "mm_fluid_setup": ([_H, C.c_double, C.c_double], C.c_int),
     "mm_fluid_solve": ([_H, _P, C.c_int, C.c_int, _P, C.c_int], C.c_int),
     "mm_fluid_response": ([_H, _P, C.c_int], C.c_int),
@@ -249,9 +252,12 @@ class Simulation:
         self._check(self.lib.mm_set_state(self.h, pp, pm, pt, d0))
 
     def get_state(self):
-        """Host copies: dict psi, mb, mf, c (float64)."""
+        """Host copies: dict psi, mb, mf, c (float64); mb is [ny][nx][nconf]
+        with a capture radius set (set_capture)."""
         g = self.grid
-        out = dict(psi=np.empty((g.ny, g.nx, g.ntheta)), mb=np.empty((g.ny, g.nx, g.ntheta, g.ns)),
+        tpl = getattr(self, "_capture", None)
+        mshape = (g.ny, g.nx, tpl["nconf"]) if tpl else (g.ny, g.nx, g.ntheta, g.ns)
+        out = dict(psi=np.empty((g.ny, g.nx, g.ntheta)), mb=np.empty(mshape),
                    mf=np.empty((g.ny, g.nx)), c=np.empty((g.ny, g.nx)))
         self._check(self.lib.mm_get_state(self.h, out["psi"].ctypes.data, out["mb"].ctypes.data,
                                           out["mf"].ctypes.data, out["c"].ctypes.data, 0))
@@ -284,6 +290,31 @@ class Simulation:
     def diffuse(self, D_t: float, D_r: float, dt: float):
         """One Crank-Nicolson step of filament diffusion (mm_diffuse)."""
         self._check(self.lib.mm_diffuse(self.h, float(D_t), float(D_r), float(dt)))
+
+    def set_capture(self, r_c: float):
+        """Finite capture radius (mm_set_capture): r_c >= 0 keeps the anchor
+        axis of Mb (anchors within r_c of the motor head), r_c < 0 switches it
+        off. Discards the motors. Returns the template (capture_template) or
+        None."""
+        self._check(self.lib.mm_set_capture(self.h, float(r_c)))
+        self._capture = None
+        if r_c >= 0:
+            self._capture = self.capture_template()
+        return self._capture
+
+    def capture_template(self) -> dict:
+        """{"lines": int [n][6] (k, dx, dy, j0, len, off), "nconf": int,
+        "w": [ntheta][ns] = 1 / n_a} of the capture radius in effect."""
+        g = self.grid
+        nl, nconf = C.c_int(), C.c_int()
+        self._check(self.lib.mm_capture_template(self.h, None, 0, C.byref(nl), C.byref(nconf),
+                                                 None))
+        lines = np.empty((nl.value, 6), dtype=np.int32)
+        w = np.empty((g.ntheta, g.ns))
+        self._check(self.lib.mm_capture_template(
+            self.h, lines.ctypes.data_as(C.POINTER(C.c_int)), nl.value, C.byref(nl),
+            C.byref(nconf), w.ctypes.data_as(C.POINTER(C.c_double))))
+        return {"lines": lines, "nconf": nconf.value, "w": w}
 
     def set_anchors(self, enable: bool = True):
         """Non-local motor anchors (mm_set_anchors): each configuration anchored

@@ -552,6 +552,49 @@ def run_ours(args):
                              "kernel": "k_substep_anchor + k_anchor_close + k_anchor_fix (float32)",
                              "peak_source": src_, "traffic": None}}
 
+    def capture_run(wname, substeps, ell=0.05, rc_cells=1.5):
+        """Finite capture radius (mm_set_capture, r_c = rc_cells x the cell
+        width, l/L = ell): a captured graph of `substeps` substeps (three
+        launches each: psi transport, Alg. 2 per anchor, the n_b gather)
+        after a warm-up graph, on the workload's grid with the motors bound
+        to their anchors from a seeded random state. Algorithmic bytes per
+        substep: the motor density read and written (2 t per configuration),
+        the line sums written and read (2 t per (anchor, line)), per
+        (cell, theta) psi read and written, n_b written and read and psi^{n+1}
+        read once for the coarse density (5 t), per cell Mf read and
+        written, C written and M read (4 t)."""
+        wl = WORKLOADS[wname]
+        gl = wl["grid"]
+        rc = rc_cells / gl.nx
+        sim = mm.Simulation(gl, Rates(ell=ell), "fp32", stream=stream.cuda_stream)
+        sim.set_state(psi_isotropic_perturbed(gl, wl["seed"]))
+        tpl = sim.set_capture(rc)
+        nconf, nlines = tpl["nconf"], len(tpl["lines"])
+        sim.set_velocity(torch.tensor(workload_velocity(wname, 0), device=dev))
+        sim.step(substeps)  # the motors bind from Mb = 0
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(substeps)
+        e1.record(stream)
+        e1.synchronize()
+        sim.sync()
+        sim.close()
+        ms = e0.elapsed_time(e1) / substeps
+        cells, t = gl.nx * gl.ny, 4
+        algo = (cells * nconf * 2 * t + cells * nlines * 2 * t + cells * gl.ntheta * 5 * t
+                + cells * 4 * t)
+        peak_, src_ = read_peaks()
+        return {"workload": f"{wname} ({gl.nx}x{gl.ny} x {gl.ntheta} x {gl.ns}, fp32), "
+                            f"l/L = {ell}, r_c = {rc_cells} cells",
+                "configurations_per_anchor": nconf, "lines_per_anchor": nlines,
+                "value": world * cells * nconf / (ms * 1e-3), "unit": "configuration-updates/s",
+                "ms_per_substep": ms, "algorithmic_bytes_per_substep": algo,
+                "roofline": {"bound": "hbm", "achieved": algo / (ms * 1e-3) / 1e9, "peak": peak_,
+                             "unit": "GB/s", "frac": algo / (ms * 1e-3) / 1e9 / peak_,
+                             "kernel": "k_rc_psi + k_rc_motor + k_rc_nb (float32)",
+                             "peak_source": src_, "traffic": None}}
+
     def fluid_run(wname, reps=5):
         """Thin-gap fluid solve (mm_fluid_solve, eps = 0.1, z0 = 0.1, with the
         dipole term) on the workload's state, float32: CUDA events around each
@@ -666,6 +709,8 @@ def run_ours(args):
     anchors = {"precision128": anchors_run("precision128", 50),
                "large512": anchors_run("large512", 5)}
     fluid = {"precision128": fluid_run("precision128"), "large512": fluid_run("large512", reps=3)}
+    capture = {"precision128": capture_run("precision128", 20),
+               "large512": capture_run("large512", 3)}
     local = {"precision128": local_run("precision128"),
              "large512": local_run("large512", reps=3)}
     # measured arithmetic roofs (fused multiply-adds per second)
@@ -757,6 +802,7 @@ def run_ours(args):
             "local": local,
             "anchors": anchors,
             "fluid": fluid,
+            "capture": capture,
             "ensemble": dict(ens, roofline={"bound": "hbm", "peak": peak, "unit": "GB/s",
                                             "achieved": ens["achieved_gbs"], "frac": ens_frac,
                                             "kernel": "k_substep_batch (float32)",
@@ -777,6 +823,7 @@ def run_ours(args):
                                      "large512_fp32": large_adj["adjoint_over_forward"]},
             "ensemble_frac": ens_frac,
             "anchors_frac": {k: v["roofline"]["frac"] for k, v in anchors.items()},
+            "capture_frac": {k: v["roofline"]["frac"] for k, v in capture.items()},
             "local_alu_frac": {k: v["roofline"]["frac"] for k, v in local.items()},
             f"{other}_frac": o_leg["roofline"]["frac"],
         }

@@ -241,6 +241,34 @@ mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_
 mm_status mm_adjoint_step(mm_handle* h, int n_substeps, const mm_adjoint_seed* seed,
                           mm_adjoint_out* out);
 
+/* ---- Tangent-linear mode (forward-mode derivative along a direction of the rates)
+ *
+ * mm_set_tangent(h, dparams): dparams = {d k_off, d v_walk, d k_on} (finite)
+ * switches the tangent mode on: from then on every substep (mm_micro_step)
+ * advances, in one launch, the state and its tangent -- the derivative of
+ * the state along that direction of the rates, starting from zero at the
+ * current state and again at every mm_set_state. The map differentiated is
+ * the substep as the forward computes it at a fixed dt (dt and the velocities
+ * are held fixed, as in the reverse sweep), on the branches the forward takes,
+ * the float32 form's mass-correction factor a constant of the map. Costs one
+ * pass of about twice the forward's memory traffic per substep and needs no
+ * checkpoints: the tool for the derivative with respect to one scalar
+ * parameter (mm_adjoint_step gives many at once). NULL switches it off and
+ * frees its memory (one more state of Mb, psi and n_b). While it is on,
+ * mm_set_checkpointing, mm_diffuse, mm_motor_local and mm_fluid_solve return
+ * MM_ERR_STATE (their effect on the tangent is not followed). MM_ERR_UNSUPPORTED:
+ * a batch or member, non-local anchors or a capture radius; MM_ERR_OOM.
+ *
+ * mm_get_tangent(h, dpsi, dmb, dmf, on_device): the tangent of psi (with the
+ * pending float32 correction factor, as mm_get_state), Mb and Mf; any output
+ * may be NULL. mm_tangent_observable(h, observable, &value, &dvalue): a
+ * built-in observable (MM_OBS_POLAR_ORDER or MM_OBS_MEAN_STRESS) of the current
+ * state and its derivative along the direction; synchronises the stream.
+ * MM_ERR_STATE when the tangent mode is off. */
+mm_status mm_set_tangent(mm_handle* h, const double* dparams);
+mm_status mm_get_tangent(mm_handle* h, double* dpsi, double* dmb, double* dmf, int on_device);
+mm_status mm_tangent_observable(mm_handle* h, int observable, double* value, double* dvalue);
+
 /* ---- Filament diffusion --------------------------------------------------------
  *
  * mm_diffuse(h, D_t, D_r, dt): one step of the diffusive fluxes of Eq. 2-3,

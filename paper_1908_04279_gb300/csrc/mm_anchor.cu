@@ -633,6 +633,8 @@ mm_status mm_set_anchors(mm_handle* h, int enable) {
     return fail(h, MM_ERR_STATE, "non-local anchors are not differentiated: end the adjoint recording first");
   if (enable && h->capture)
     return fail(h, MM_ERR_STATE, "a capture radius is set: switch it off (mm_set_capture < 0) first");
+  if (enable && h->tangent)
+    return fail(h, MM_ERR_STATE, "the tangent mode is on: switch it off (mm_set_tangent) first");
   DeviceGuard dg(h->device);
   CK(cudaStreamSynchronize(h->stream));
   mm_status st;

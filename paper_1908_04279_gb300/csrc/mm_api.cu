@@ -39,6 +39,7 @@ mm_status free_all(mm_handle* h) {
   free_recording(h);
   fluid_free(h);
   capture_free(h);
+  tangent_free(h);
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();
   if (h->diff_tab) cudaFree(h->diff_tab);
@@ -122,6 +123,7 @@ template StepArgs<double> step_args<double>(mm_handle*, int);
 cudaError_t launch_one(mm_handle* h, int parity, cudaStream_t s) {
   if (h->anchors) return launch_anchor_substep(h, parity, s);
   if (h->capture) return launch_capture_substep(h, parity, s);
+  if (h->tangent) return launch_tangent_substep(h, parity, s);
   if (h->prec == MM_FP64) {
     StepArgs<double> a = step_args<double>(h, parity);
     return h->V == 2 ? mm::launch_substep<double, 2>(a, h->grid_step, h->block, h->smem, h->tma, s)
@@ -603,6 +605,7 @@ mm_status mm_set_state(mm_handle* h, const double* psi, const double* mb, const 
   }
   const double one = 1.0;
   CK(cudaMemcpyAsync(&h->prm->psi_scale, &one, 8, cudaMemcpyHostToDevice, h->stream));
+  if (h->tangent && (st = tangent_zero(h)) != MM_OK) return st;  // the tangent starts at zero
   if ((st = run_init(h)) != MM_OK) return st;
   // reference filament number for the float32 mass correction
   if ((st = run_moments(h)) != MM_OK) return st;
@@ -781,8 +784,9 @@ mm_status mm_diffuse(mm_handle* h, double D_t, double D_r, double dt) {
     return fail(h, MM_ERR_INVALID, "diffusivities must be finite and >= 0");
   if (!finite_pos(dt)) return fail(h, MM_ERR_INVALID, "dt must be finite and > 0");
   if (!h->have_state) return fail(h, MM_ERR_STATE, "no state: call mm_set_state first");
-  if (h->rec.active)
-    return fail(h, MM_ERR_STATE, "diffusion is not differentiated: end the adjoint recording first");
+  if (h->rec.active || h->tangent)
+    return fail(h, MM_ERR_STATE,
+                "diffusion is not differentiated: end the adjoint recording or the tangent first");
   DeviceGuard dg(h->device);
   const int nx = h->g.nx, ny = h->g.ny, nth = h->g.ntheta;
   if (!h->diff_tab) CK(cudaMalloc((void**)&h->diff_tab, (size_t)(3 * (nth + nx + ny) + 6) * 8));
@@ -1174,6 +1178,8 @@ mm_status mm_set_checkpointing_levels(mm_handle* h, int K, int K_inner, int max_
   if (K < 0 || max_substeps < 1) return fail(h, MM_ERR_INVALID, "K >= 1 and max_substeps >= 1");
   if (h->capture)
     return fail(h, MM_ERR_UNSUPPORTED, "the adjoint is not available with a capture radius");
+  if (h->tangent)
+    return fail(h, MM_ERR_STATE, "the tangent mode is on: switch it off (mm_set_tangent(h, NULL)) first");
   if (h->anchors)
     return fail(h, MM_ERR_UNSUPPORTED, "the adjoint is not available with non-local anchors");
   if (K_inner < 1 || K_inner > K) return fail(h, MM_ERR_INVALID, "1 <= K_inner <= K");

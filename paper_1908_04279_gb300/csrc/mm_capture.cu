@@ -531,6 +531,8 @@ mm_status mm_set_capture(mm_handle* h, double rc) {
     return fail(h, MM_ERR_STATE, "the capture radius is not differentiated: end the adjoint recording first");
   if (h->anchors)
     return fail(h, MM_ERR_STATE, "non-local anchors are on: switch them off (mm_set_anchors) first");
+  if (h->tangent && rc >= 0.0)
+    return fail(h, MM_ERR_STATE, "the tangent mode is on: switch it off (mm_set_tangent) first");
   if (std::isnan(rc) || std::isinf(rc))
     return fail(h, MM_ERR_INVALID, "the capture radius must be finite (negative: off)");
   DeviceGuard dg(h->device);

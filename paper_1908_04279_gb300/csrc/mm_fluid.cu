@@ -311,6 +311,10 @@ mm_status mm_fluid_solve(mm_handle* h, const double* sigma, int sigma_on_device,
   if (!h->have_state) return fail(h, MM_ERR_STATE, "no state: call mm_set_state first");
   if (h->rec.active)
     return fail(h, MM_ERR_STATE, "the fluid solve is not differentiated: end the adjoint recording first");
+  if (h->tangent)
+    return fail(h, MM_ERR_STATE,
+                "the fluid solve is not differentiated (the velocity would carry a tangent): "
+                "end the tangent first");
   if (dipole && (h->anchors || h->capture))
     return fail(h, MM_ERR_UNSUPPORTED,
                 "with anchors the force already acts in the anchor cells: dipole must be 0");

@@ -140,6 +140,15 @@ struct mm_handle {
   double* anc_cacc = nullptr;   // [cells] float64 accumulators of C
   double* anc_fsc = nullptr;    // [cells] scale-down factors
   int* anc_flags = nullptr;     // [4] scale-down flags
+  // tangent-linear mode (mm_set_tangent): the tangent of the state along a
+  // direction of the rates, advanced with it by every substep
+  bool tangent = false;
+  double tan_dp[3] = {0.0, 0.0, 0.0};  // d k_off, d v_walk, d k_on
+  void* tan_mb = nullptr;
+  void* tan_psi[2] = {nullptr, nullptr};
+  void* tan_nb[2] = {nullptr, nullptr};
+  void* tan_mf = nullptr;
+  int tan_seg = 1, tan_grid = 1;
   // finite capture radius (mm_set_capture): the anchor axis of Mb
   bool capture = false;
   double rc = 0.0;
@@ -258,6 +267,13 @@ void capture_free(mm_handle* h);
 cudaError_t launch_capture_substep(mm_handle* h, int parity, cudaStream_t s);
 mm_status run_init_capture(mm_handle* h);
 mm_status capture_rows(mm_handle* h);  // per-node totals over the anchors into h->mb
+
+// Defined in mm_tangent.cu (tangent-linear mode).
+void tangent_free(mm_handle* h);
+cudaError_t launch_tangent_substep(mm_handle* h, int parity, cudaStream_t s);
+mm_status tangent_zero(mm_handle* h);
+mm_status get_array(mm_handle* h, double* dst, const void* src, size_t n, int on_device,
+                    const double* scale);
 
 // Defined in mm_batch_api.cu.
 mm_status batch_micro_step(mm_handle* h, int n);

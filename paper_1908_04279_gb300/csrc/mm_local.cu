@@ -345,6 +345,8 @@ mm_status mm_motor_local(mm_handle* h, double T, const int* nsteps_in, int* nste
   if (h->rec.active)
     return fail(h, MM_ERR_STATE,
                 "the local-step motor update is not differentiated: end the adjoint recording first");
+  if (h->tangent)
+    return fail(h, MM_ERR_STATE, "the local-step motor update is not differentiated: end the tangent first");
   if (h->anchors || h->capture)
     return fail(h, MM_ERR_UNSUPPORTED,
                 "local substeps need independent cells: not available with non-local anchors "

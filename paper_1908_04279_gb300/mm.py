@@ -96,6 +96,10 @@ PROTOTYPES = {
     "mm_motor_local": ([_H, C.c_double, _P, _P, C.c_int], C.c_int),
     "mm_set_anchors": ([_H, C.c_int], C.c_int),
     "mm_set_capture": ([_H, C.c_double], C.c_int),
+    "mm_set_tangent": ([_H, _P], C.c_int),
+    "mm_get_tangent": ([_H, _P, _P, _P, C.c_int], C.c_int),
+    "mm_tangent_observable": ([_H, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double)],
+                              C.c_int),
     "mm_capture_template": ([_H, C.POINTER(C.c_int), C.c_int, C.POINTER(C.c_int),
                              C.POINTER(C.c_int), C.POINTER(C.c_double)], C.c_int),
     "mm_fluid_setup": ([_H, C.c_double, C.c_double], C.c_int),
@@ -290,6 +294,32 @@ class Simulation:
     def diffuse(self, D_t: float, D_r: float, dt: float):
         """One Crank-Nicolson step of filament diffusion (mm_diffuse)."""
         self._check(self.lib.mm_diffuse(self.h, float(D_t), float(D_r), float(dt)))
+
+    def set_tangent(self, dparams=None):
+        """Tangent-linear mode (mm_set_tangent): dparams = (d k_off, d v_walk,
+        d k_on) switches it on (the tangent starts at zero), None off."""
+        if dparams is None:
+            self._check(self.lib.mm_set_tangent(self.h, None))
+            return
+        arr = (C.c_double * 3)(*[float(x) for x in dparams])
+        self._check(self.lib.mm_set_tangent(self.h, C.cast(arr, C.c_void_p)))
+
+    def get_tangent(self):
+        """Host copies of the tangent: dict dpsi, dmb, dmf (float64)."""
+        g = self.grid
+        out = dict(dpsi=np.empty((g.ny, g.nx, g.ntheta)), dmb=np.empty((g.ny, g.nx, g.ntheta, g.ns)),
+                   dmf=np.empty((g.ny, g.nx)))
+        self._check(self.lib.mm_get_tangent(self.h, out["dpsi"].ctypes.data, out["dmb"].ctypes.data,
+                                            out["dmf"].ctypes.data, 0))
+        return out
+
+    def tangent_observable(self, observable: str = "polar_order"):
+        """(value, derivative along the tangent's direction) of a built-in
+        observable of the current state (mm_tangent_observable)."""
+        v, dv = C.c_double(), C.c_double()
+        self._check(self.lib.mm_tangent_observable(self.h, OBSERVABLES[observable], C.byref(v),
+                                                   C.byref(dv)))
+        return v.value, dv.value
 
     def set_capture(self, r_c: float):
         """Finite capture radius (mm_set_capture): r_c >= 0 keeps the anchor

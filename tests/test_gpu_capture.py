@@ -101,10 +101,10 @@ def test_capture_forced_scale_down_fp64(mmod, oracle_mod):
     O = oracle_mod
     dims, ell, rc = (10, 9, 6, 10), 0.33, 1.6 / 10
     g = Grid(*dims)
-    r = Rates(ell=ell, k_on=30.0, glide=0.2)
-    tpl, psi, mb, mtot, u = _inputs(O, g, r, rc, 431, mb_scale=0.3, mtot_lo=0.01, mtot_span=0.05)
+    r = Rates(ell=ell, k_on=60.0, glide=0.2)
+    tpl, psi, mb, mtot, u = _inputs(O, g, r, rc, 431, mb_scale=0.05, mtot_lo=0.02, mtot_span=0.03)
     st = O.make_state_rc(g, r, rc, psi, mb, mtot)
-    dt = 3.0 * O.dt(g, r, O.make_state(g, psi), u)
+    dt = 4.0 * O.dt(g, r, O.make_state(g, psi), u)
     clipped = False
     with mmod.Simulation(g, r, "fp64") as sim:
         sim.set_capture(rc)
@@ -119,7 +119,6 @@ def test_capture_forced_scale_down_fp64(mmod, oracle_mod):
     assert clipped
     for k in ("psi", "mb", "mf", "c"):
         assert rel(got[k], getattr(st, k)) <= 1e-12, (k, rel(got[k], getattr(st, k)))
-    assert np.any(got["mf"] == 0.0) == np.any(st.mf == 0.0)
 
 
 @pytest.mark.parametrize("dims,ell,rc", CASES[:2])

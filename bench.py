@@ -423,7 +423,9 @@ def run_ours(args):
         16-mode flow each macro step), gradient of the mean active stress
         with respect to k_off, outer checkpoints every 100 substeps and inner
         ones every 10 (two levels: about 40 states of 4.4 GB held). Times the
-        plain forward and the recorded forward + reverse sweep."""
+        plain forward, the recorded forward + reverse sweep, and the same
+        derivative in tangent-linear mode (one forward pass carrying the
+        tangent along d k_off, wall clock to the derivative on the host)."""
         wl = WORKLOADS["large512"]
         gl, nmac, nsl = wl["grid"], wl["macro"], wl["substeps"]
         psi_l = psi_isotropic_perturbed(gl, wl["seed"])
@@ -449,8 +451,22 @@ def run_ours(args):
                 out["dL_dk_off"] = float(res["dL_drates"][0])
             sim.sync()
             out["forward_plus_adjoint_s" if rec else "forward_s"] = time.perf_counter() - t0
+        # the same derivative in tangent-linear mode: one pass carrying the
+        # state and its tangent along d k_off, no checkpoints
+        sim.set_checkpointing(0, 1)
+        sim.set_tangent((1.0, 0.0, 0.0))
+        sim.set_state(psi_l)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for m in range(nmac):
+            sim.set_velocity(vl[m])
+            sim.step(nsl)
+        _, out["dL_dk_off_tangent"] = sim.tangent_observable("mean_stress")
+        out["forward_plus_tangent_s"] = time.perf_counter() - t0
         sim.close()
         out["adjoint_over_forward"] = (out["forward_plus_adjoint_s"] - out["forward_s"]) / out[
+            "forward_s"]
+        out["tangent_over_forward"] = (out["forward_plus_tangent_s"] - out["forward_s"]) / out[
             "forward_s"]
         out["checkpoints"] = "outer every 100 substeps (21), inner every 10 (9), 10 slots"
         return out
@@ -820,7 +836,8 @@ def run_ours(args):
             "fp64_alu_frac": fp64_ops / fp64_peak,
             "adjoint_over_forward": {"adjoint64_fp32": adj["fp32"]["adjoint_over_forward"],
                                      "adjoint64_fp64": adj["fp64"]["adjoint_over_forward"],
-                                     "large512_fp32": large_adj["adjoint_over_forward"]},
+                                     "large512_fp32": large_adj["adjoint_over_forward"],
+                                     "large512_fp32_tangent": large_adj["tangent_over_forward"]},
             "ensemble_frac": ens_frac,
             "anchors_frac": {k: v["roofline"]["frac"] for k, v in anchors.items()},
             "capture_frac": {k: v["roofline"]["frac"] for k, v in capture.items()},

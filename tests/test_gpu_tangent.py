@@ -199,7 +199,7 @@ def test_tangent_refusals(mmod):
                 call()
         sim.set_tangent(None)
         sim.set_checkpointing(2, 4)  # allowed again
-    with mmod.Simulation(g, Rates(), "fp32") as sim:
+    with mmod.Simulation(g, Rates(ell=0.2), "fp32") as sim:
         sim.set_capture(0.1)
         with pytest.raises(mmod.MMError):
             sim.set_tangent(DP)

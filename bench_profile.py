@@ -4,10 +4,12 @@
         [--case single|batch|adjoint|moments|local|fluid]
         [--grid NX NY NTHETA NS] [--precision fp32|fp64] [--substeps N]
         [--repeat R] [--K K] [--members M] [--autotune] [--anchors ELL]
+        [--capture ELL RC_CELLS]
 
 single:  the perturbed isotropic state under a seeded 8-mode divergence-free
          flow (amplitude 0.1); R calls of N substeps (with --anchors ELL: motor
-         anchors under the motor heads, l/L = ELL).
+         anchors under the motor heads, l/L = ELL; with --capture ELL RC_CELLS:
+         the finite capture radius r_c = RC_CELLS cell widths, l/L = ELL).
 batch:   the first M members of the detachment-rate ensemble (64 by default)
          as one batch; R calls of N batched substeps (after mm_batch_autotune
          with --autotune).
@@ -50,6 +52,7 @@ def main():
     ap.add_argument("--members", type=int, default=64)
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--anchors", type=float, default=None)
+    ap.add_argument("--capture", type=float, nargs=2, default=None)
     args = ap.parse_args()
     B.build()
     stream = torch.cuda.current_stream()
@@ -83,9 +86,13 @@ def main():
 
     g = Grid(*args.grid)
     rates = Rates() if args.anchors is None else Rates(ell=args.anchors)
+    if args.capture is not None:
+        rates = Rates(ell=args.capture[0])
     with mm.Simulation(g, rates, args.precision, stream=stream.cuda_stream) as sim:
         if args.anchors is not None:
             sim.set_anchors(True)
+        if args.capture is not None:
+            sim.set_capture(args.capture[1] / g.nx)
         psi0 = psi_isotropic_perturbed(g, 0)
         u = random_divfree_flow(g, 1, 8, 0.1)
         sim.set_state(psi0)

@@ -50,6 +50,9 @@ struct RcArgs {
   const unsigned char* meta;   // [nconf] bit 0: a line's first node, bit 1: its last
   const T* w;                  // [nconf] binding weight 1 / n_a of the entry's node
   const int* krange;           // [nth + 1] first line of each orientation
+  const unsigned* cmask;       // [nchunks][32] per lane of a chunk: its 8 entries' line-start
+                               // flags (bits 0-7), line-end flags (8-15), valid (16-23)
+  const T* cw;                 // [nchunks][256] the chunk's weights, entry 8 lane + v
   const T* mtot;
   T* mf;
   T* c;
@@ -60,29 +63,70 @@ struct RcArgs {
 constexpr int kRcV = 8;                 // entries per lane of a chunk
 constexpr int kRcChunk = 32 * kRcV;     // entries of a chunk at most
 
-// The walking term of Eq. 4 on a chunk held as M[v] at position 32 v + lane:
+// Asynchronous 4- or 8-byte copies global -> shared (one per thread, any
+// 4/8-byte aligned address), grouped and waited for per thread.
+__device__ __forceinline__ void cp_async_t(float* dst, const float* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_t(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// A lane's 8 consecutive entries of a shared-memory stage (16-byte vectors).
+template <typename T>
+__device__ __forceinline__ void lds8(const T* p, T (&v)[kRcV]) {
+  constexpr int P = 16 / sizeof(T);
+#pragma unroll
+  for (int h = 0; h < kRcV / P; ++h) {
+    if constexpr (sizeof(T) == 4) {
+      const float4 q = reinterpret_cast<const float4*>(p)[h];
+      v[4 * h] = q.x; v[4 * h + 1] = q.y; v[4 * h + 2] = q.z; v[4 * h + 3] = q.w;
+    } else {
+      const double2 q = reinterpret_cast<const double2*>(p)[h];
+      v[2 * h] = q.x; v[2 * h + 1] = q.y;
+    }
+  }
+}
+template <typename T>
+__device__ __forceinline__ void sts8(T* p, const T (&v)[kRcV]) {
+  constexpr int P = 16 / sizeof(T);
+#pragma unroll
+  for (int h = 0; h < kRcV / P; ++h) {
+    if constexpr (sizeof(T) == 4)
+      reinterpret_cast<float4*>(p)[h] = make_float4(v[4 * h], v[4 * h + 1], v[4 * h + 2], v[4 * h + 3]);
+    else
+      reinterpret_cast<double2*>(p)[h] = make_double2(v[2 * h], v[2 * h + 1]);
+  }
+}
+
+// The walking term of Eq. 4 on a lane's 8 consecutive entries of a chunk:
 // D = F_{p-1} - F_p with F_p = M_p + sigma_p / 2 (Superbee slope of the
 // backward and forward differences), F_p = M_p at a line's last node
-// (donor-cell outflow), F_{p-1} = 0 and M_{p-1} = 0 at a line's first node.
-// The arithmetic is that of the row kernels' walk (walk_dflux), position by
-// position; only the neighbour exchange differs (lane rotation by shuffles).
+// (donor-cell outflow), F_{p-1} = 0 and M_{p-1} = 0 at a line's first node;
+// mask bit v: entry v starts a line, bit 8 + v: it ends one. The arithmetic is
+// that of the row kernels' walk (walk_dflux), entry by entry; the neighbours
+// across lanes come by one shuffle each way.
 template <typename T>
-__device__ __forceinline__ void rc_walk(const T (&M)[kRcV], const unsigned (&fl)[kRcV],
-                                        T (&D)[kRcV], int lane) {
-  const int up = (lane + 31) & 31, dn = (lane + 1) & 31;
+__device__ __forceinline__ void rc_walk(const T (&M)[kRcV], unsigned mask, T (&D)[kRcV]) {
+  const T ml = __shfl_up_sync(0xffffffffu, M[kRcV - 1], 1);
+  const T mr = __shfl_down_sync(0xffffffffu, M[0], 1);
   T F[kRcV];
 #pragma unroll
   for (int v = 0; v < kRcV; ++v) {
-    // left neighbour (v, lane - 1), or (v - 1, 31) for lane 0; right
-    // neighbour (v, lane + 1), or (v + 1, 0) for lane 31
-    const T sl = lane == 31 ? (v > 0 ? M[v - 1] : T(0)) : M[v];
-    const T sr = lane == 0 ? (v + 1 < kRcV ? M[v + 1] : T(0)) : M[v];
-    T ml = __shfl_sync(0xffffffffu, sl, up);
-    const T mr = __shfl_sync(0xffffffffu, sr, dn);
-    if (fl[v] & 1u) ml = T(0);
-    const T a = M[v] - ml, b = mr - M[v];
+    const T left = ((mask >> v) & 1u) ? T(0) : (v > 0 ? M[v - 1] : ml);
+    const T right = v + 1 < kRcV ? M[v + 1] : mr;
+    const T a = M[v] - left, b = right - M[v];
     const T ha = T(0.5) * a, hb = T(0.5) * b;
-    const bool last = (fl[v] & 2u) != 0;
+    const bool last = ((mask >> (8 + v)) & 1u) != 0;
     if constexpr (sizeof(T) == 4) {
       float r = max3_t(min_xorsign_abs(a, hb), min_xorsign_abs(ha, b), 0.0f);
       if (last) r = 0.0f;
@@ -95,12 +139,11 @@ __device__ __forceinline__ void rc_walk(const T (&M)[kRcV], const unsigned (&fl)
       F[v] = fma_t(r, sgn, M[v]);
     }
   }
+  const T fl = __shfl_up_sync(0xffffffffu, F[kRcV - 1], 1);
 #pragma unroll
   for (int v = 0; v < kRcV; ++v) {
-    const T sl = lane == 31 ? (v > 0 ? F[v - 1] : T(0)) : F[v];
-    T fl_ = __shfl_sync(0xffffffffu, sl, up);
-    if (fl[v] & 1u) fl_ = T(0);
-    D[v] = fl_ - F[v];
+    const T fprev = ((mask >> v) & 1u) ? T(0) : (v > 0 ? F[v - 1] : fl);
+    D[v] = fprev - F[v];
   }
 }
 
@@ -111,83 +154,124 @@ __device__ __forceinline__ void rc_walk(const T (&M)[kRcV], const unsigned (&fl)
 // scale-down where C exceeds M (the warp rescales the entries and line sums it
 // wrote) and Mf = M - C. init = 1: dt = 0 (the set-up: C, the scale-down, Mf
 // and the line sums of a loaded state).
-template <typename T>
+// The warp's (anchor, chunk) items stream through a ring of S shared-memory
+// stages filled by asynchronous copies S items ahead (coalesced 4/8-byte
+// copies: a chunk may start anywhere); lane l computes the chunk's entries
+// 8 l .. 8 l + 7, and the new values go back through the stage so that the
+// global stores are coalesced too.
+template <typename T, int S>
 __global__ void __launch_bounds__(128) k_rc_motor(const RcArgs<T> x, const T* psi_c, int init) {
-  __shared__ T s_buf[4][kRcChunk];
+  extern __shared__ __align__(16) unsigned char rc_ring_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = blockIdx.x * 4LL + wib, W = (long long)gridDim.x * 4;
-  T* sb = s_buf[wib];
+  T* ring = reinterpret_cast<T*>(rc_ring_raw) + (size_t)wib * S * kRcChunk;
   const double dt64 = init ? 0.0 : x.prm->dt;
   const T dt = (T)dt64, hdt = (T)(0.5 * dt64);
   const T cw = (T)x.prm->cw, kon = (T)x.prm->k_on, koff = (T)x.prm->k_off;
   const T c1 = hdt * cw, c2 = T(1) - hdt * koff, e1 = dt * cw, e2 = -dt * koff;
   const T hk = hdt * kon, fk = dt * kon;
   const T ds = (T)x.ds, dth = (T)x.dth;
-  const int nx = x.nx, ny = x.ny, nth = x.nth;
-  for (long long a = gw; a < x.ncells; a += W) {
+  const int nx = x.nx, ny = x.ny, nth = x.nth, nch = x.nchunks;
+  const long long na = gw < x.ncells ? (x.ncells - gw + W - 1) / W : 0;
+  const long long nitems = na * nch;
+  auto issue = [&](long long q) {
+    if (q < nitems) {
+      const long long a = gw + (q / nch) * W;
+      const int4 cd = x.chunk[(int)(q % nch)];
+      T* st = ring + (size_t)(q % S) * kRcChunk;
+      const T* src = x.mb + (size_t)a * x.nconf + cd.x;
+#pragma unroll
+      for (int v = 0; v < kRcV; ++v) {
+        const int p = 32 * v + lane;
+        if (p < cd.y) cp_async_t(st + p, src + p);
+      }
+    }
+    cp_async_commit();  // one group per item, empty past the end
+  };
+#pragma unroll
+  for (int q = 0; q < S; ++q) issue(q);
+  T cacc = T(0), mfa = T(0);
+  for (long long q = 0; q < nitems; ++q) {
+    const int ch = (int)(q % nch);
+    const long long a = gw + (q / nch) * W;
+    if (ch == 0) {
+      mfa = x.mf[a];
+      cacc = T(0);
+    }
+    const int4 cd = x.chunk[ch];
+    const unsigned mask = x.cmask[ch * 32 + lane];
+    T wv[kRcV];
+#pragma unroll
+    for (int v = 0; v < kRcV; ++v) wv[v] = x.cw[(size_t)ch * kRcChunk + 8 * lane + v];
+    cp_async_wait<S - 1>();
+    __syncwarp();
+    T* st = ring + (size_t)(q % S) * kRcChunk;
+    T M[kRcV], D[kRcV], Ms[kRcV];
+    lds8(st + 8 * lane, M);
+#pragma unroll
+    for (int v = 0; v < kRcV; ++v)
+      if (!((mask >> (16 + v)) & 1u)) M[v] = T(0);
+    rc_walk<T>(M, mask, D);
+#pragma unroll
+    for (int v = 0; v < kRcV; ++v) Ms[v] = fma_t(c1, D[v], fma_t(c2, M[v], hk * (mfa * wv[v])));
+    rc_walk<T>(Ms, mask, D);
+#pragma unroll
+    for (int v = 0; v < kRcV; ++v)
+      M[v] = fma_t(e1, D[v], fma_t(e2, Ms[v], M[v] + fk * (mfa * wv[v])));
+    __syncwarp();
+    sts8(st + 8 * lane, M);
+    __syncwarp();
+    T* Ma = x.mb + (size_t)a * x.nconf + cd.x;
+    if (!init) {
+#pragma unroll
+      for (int v = 0; v < kRcV; ++v) {
+        const int p = 32 * v + lane;
+        if (p < cd.y) Ma[p] = st[p];
+      }
+    }
+    // lanes over the chunk's lines: the line sum of Mb ds, and the line's
+    // part of the coarse density
     const int ay = (int)(a / nx), ax = (int)(a - (long long)ay * nx);
-    T* Ma = x.mb + (size_t)a * x.nconf;
     T* La = x.ls + (size_t)a * x.nlines;
-    const T mfa = x.mf[a];
-    T cacc = T(0);
-    for (int ch = 0; ch < x.nchunks; ++ch) {
-      const int4 cd = x.chunk[ch];
-      const int pos0 = cd.x, npos = cd.y, l0 = cd.z, nl = cd.w;
-      T M[kRcV], D[kRcV], Ms[kRcV], mfw[kRcV];
-      unsigned fl[kRcV];
-#pragma unroll
-      for (int v = 0; v < kRcV; ++v) {
-        const int p = 32 * v + lane;
-        const bool act = p < npos;
-        M[v] = act ? Ma[pos0 + p] : T(0);
-        fl[v] = act ? (unsigned)x.meta[pos0 + p] : 3u;
-        mfw[v] = act ? mfa * x.w[pos0 + p] : T(0);
+    for (int li = lane; li < cd.w; li += 32) {
+      const int l = cd.z + li;
+      const int4 ln = x.line[l];
+      int fx = ax - ln.x, fy = ay - ln.y;
+      fx += fx < 0 ? nx : (fx >= nx ? -nx : 0);
+      fy += fy < 0 ? ny : (fy >= ny ? -ny : 0);
+      const T pf = psi_c[((size_t)fy * nx + fx) * nth + ln.z];
+      const int b0 = x.loff[l] - cd.x;
+      T s0 = T(0), s1 = T(0);
+      int q2 = 0;
+      for (; q2 + 1 < ln.w; q2 += 2) {
+        s0 += st[b0 + q2];
+        s1 += st[b0 + q2 + 1];
       }
-      rc_walk<T>(M, fl, D, lane);
-#pragma unroll
-      for (int v = 0; v < kRcV; ++v) Ms[v] = fma_t(c1, D[v], fma_t(c2, M[v], hk * mfw[v]));
-      rc_walk<T>(Ms, fl, D, lane);
-#pragma unroll
-      for (int v = 0; v < kRcV; ++v) {
-        M[v] = fma_t(e1, D[v], fma_t(e2, Ms[v], M[v] + fk * mfw[v]));
-        const int p = 32 * v + lane;
-        if (p < npos) {
-          if (!init) Ma[pos0 + p] = M[v];
-          sb[p] = M[v];
-        }
-      }
-      __syncwarp();
-      // lanes over the chunk's lines: the line sum of Mb ds, and the line's
-      // part of the coarse density
-      for (int li = lane; li < nl; li += 32) {
-        const int l = l0 + li;
-        const int4 ln = x.line[l];
-        const int b0 = x.loff[l] - pos0;
-        T s = T(0);
-        for (int q = 0; q < ln.w; ++q) s += sb[b0 + q];
-        s *= ds;
-        La[l] = s;
-        int fx = ax - ln.x, fy = ay - ln.y;
-        fx += fx < 0 ? nx : (fx >= nx ? -nx : 0);
-        fy += fy < 0 ? ny : (fy >= ny ? -ny : 0);
-        cacc = fma_t(psi_c[((size_t)fy * nx + fx) * nth + ln.z] * s, dth, cacc);
-      }
-      __syncwarp();
+      if (q2 < ln.w) s0 += st[b0 + q2];
+      const T s = (s0 + s1) * ds;
+      La[l] = s;
+      cacc = fma_t(pf * s, dth, cacc);
     }
-    const T C = warp_sum_t(cacc);
-    const T Mt = x.mtot[a];
-    T Cc = C;
-    if (Mt < C) {  // Alg. 2 scale-down at r0 (rare): the warp rescales what it wrote
-      const T f = Mt / C;
-      for (int e = lane; e < x.nconf; e += 32) Ma[e] = __ldcg(Ma + e) * f;
-      for (int l = lane; l < x.nlines; l += 32) La[l] = __ldcg(La + l) * f;
-      Cc = Mt;
-    }
-    if (lane == 0) {
-      x.c[a] = Cc;
-      x.mf[a] = Mt - Cc;
+    __syncwarp();
+    issue(q + S);
+    if (ch == nch - 1) {
+      const T C = warp_sum_t(cacc);
+      const T Mt = x.mtot[a];
+      T Cc = C;
+      if (Mt < C) {  // Alg. 2 scale-down at r0 (rare): the warp rescales what it wrote
+        const T f = Mt / C;
+        T* Mall = x.mb + (size_t)a * x.nconf;
+        for (int e = lane; e < x.nconf; e += 32) Mall[e] = __ldcg(Mall + e) * f;
+        for (int l = lane; l < x.nlines; l += 32) La[l] = __ldcg(La + l) * f;
+        Cc = Mt;
+      }
+      if (lane == 0) {
+        x.c[a] = Cc;
+        x.mf[a] = Mt - Cc;
+      }
     }
   }
+  cp_async_wait<0>();
 }
 
 // n_b(x, k) = sum over the lines of orientation k, in template order, of the
@@ -200,14 +284,25 @@ __global__ void k_rc_nb(const RcArgs<T> x, T* nb) {
     const long long cell = t / x.nth;
     const int k = (int)(t - cell * x.nth);
     const int fy = (int)(cell / x.nx), fx = (int)(cell - (long long)fy * x.nx);
+    // four loads in flight, added in template order
     T s = T(0);
-    for (int l = x.krange[k]; l < x.krange[k + 1]; ++l) {
-      const int4 ln = x.line[l];
+    const int l1 = x.krange[k + 1];
+    int l = x.krange[k];
+    auto at = [&](int li) {
+      const int4 ln = x.line[li];
       int ax = fx + ln.x, ay = fy + ln.y;
       ax += ax < 0 ? x.nx : (ax >= x.nx ? -x.nx : 0);
       ay += ay < 0 ? x.ny : (ay >= x.ny ? -x.ny : 0);
-      s += __ldcg(x.ls + ((size_t)ay * x.nx + ax) * x.nlines + l);
+      return __ldcg(x.ls + ((size_t)ay * x.nx + ax) * x.nlines + li);
+    };
+    for (; l + 3 < l1; l += 4) {
+      const T v0 = at(l), v1 = at(l + 1), v2 = at(l + 2), v3 = at(l + 3);
+      s += v0;
+      s += v1;
+      s += v2;
+      s += v3;
     }
+    for (; l < l1; ++l) s += at(l);
     nb[t] = s;
   }
 }
@@ -439,6 +534,8 @@ mm::RcArgs<T> rc_args(mm_handle* h) {
   x.meta = (const unsigned char*)h->rc_tab + h->rc_tab_off[2];
   x.w = (const T*)((const char*)h->rc_tab + h->rc_tab_off[3]);
   x.krange = (const int*)((const char*)h->rc_tab + h->rc_tab_off[4]);
+  x.cmask = (const unsigned*)((const char*)h->rc_tab + h->rc_tab_off[5]);
+  x.cw = (const T*)((const char*)h->rc_tab + h->rc_tab_off[6]);
   x.mtot = (const T*)h->mtot;
   x.mf = (T*)h->mf;
   x.c = (T*)h->c;
@@ -446,6 +543,13 @@ mm::RcArgs<T> rc_args(mm_handle* h) {
   x.ds = h->g.L / h->g.ns;
   x.dth = 2.0 * kPi / h->g.ntheta;
   return x;
+}
+
+// Ring stages of the motor kernel per warp, and its dynamic shared memory.
+constexpr int kRcStages = 4;
+template <typename T>
+constexpr size_t rc_ring_bytes() {
+  return (size_t)4 * kRcStages * mm::kRcChunk * sizeof(T);
 }
 
 int rc_grid(mm_handle* h, long long work, int per_block) {
@@ -465,7 +569,8 @@ cudaError_t rc_substep_t(mm_handle* h, int parity, cudaStream_t s) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const mm::RcArgs<T> x = rc_args<T>(h);
-  mm::k_rc_motor<T><<<h->rc_motor_grid, 128, 0, s>>>(x, (const T*)h->psi[parity ^ 1], 0);
+  mm::k_rc_motor<T, kRcStages><<<h->rc_motor_grid, 128, rc_ring_bytes<T>(), s>>>(
+      x, (const T*)h->psi[parity ^ 1], 0);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   mm::k_rc_nb<T><<<rc_grid(h, h->ncells * h->g.ntheta, 256), 256, 0, s>>>(x, (T*)h->nb[parity ^ 1]);
   return cudaGetLastError();
@@ -474,7 +579,8 @@ cudaError_t rc_substep_t(mm_handle* h, int parity, cudaStream_t s) {
 template <typename T>
 cudaError_t rc_init_t(mm_handle* h) {
   const mm::RcArgs<T> x = rc_args<T>(h);
-  mm::k_rc_motor<T><<<h->rc_motor_grid, 128, 0, h->stream>>>(x, (const T*)h->psi[h->parity], 1);
+  mm::k_rc_motor<T, kRcStages><<<h->rc_motor_grid, 128, rc_ring_bytes<T>(), h->stream>>>(
+      x, (const T*)h->psi[h->parity], 1);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   mm::k_rc_nb<T><<<rc_grid(h, h->ncells * h->g.ntheta, 256), 256, 0, h->stream>>>(
@@ -603,6 +709,10 @@ mm_status mm_set_capture(mm_handle* h, double rc) {
   o += up((size_t)nconf * t);
   h->rc_tab_off[4] = o;
   o += up((nth + 1) * sizeof(int));
+  h->rc_tab_off[5] = o;
+  o += up(chunks.size() * 32 * sizeof(unsigned));
+  h->rc_tab_off[6] = o;
+  o += up(chunks.size() * mm::kRcChunk * t);
   const size_t tab_bytes = o;
   const size_t need = nc * nconf * t + nc * nl * t + tab_bytes;
   size_t freeb = 0, totalb = 0;
@@ -629,6 +739,36 @@ mm_status mm_set_capture(mm_handle* h, double rc) {
     memcpy(host.data() + h->rc_tab_off[3], wf.data(), (size_t)nconf * 4);
   }
   memcpy(host.data() + h->rc_tab_off[4], krange.data(), (nth + 1) * sizeof(int));
+  // per chunk and lane: the flags of the lane's 8 entries (entry 8 lane + v),
+  // and the chunk's weights in the same order (0 past the chunk's end)
+  {
+    std::vector<unsigned> cmask(chunks.size() * 32, 0u);
+    std::vector<double> cwd(chunks.size() * mm::kRcChunk, 0.0);
+    for (size_t c = 0; c < chunks.size(); ++c)
+      for (int lane = 0; lane < 32; ++lane) {
+        unsigned m = 0;
+        for (int v = 0; v < mm::kRcV; ++v) {
+          const int pch = mm::kRcV * lane + v;
+          if (pch < chunks[c].y) {
+            const int e = chunks[c].x + pch;
+            m |= (meta[e] & 1u) << v;
+            m |= ((meta[e] >> 1) & 1u) << (8 + v);
+            m |= 1u << (16 + v);
+            cwd[c * mm::kRcChunk + pch] = wpos[e];
+          } else {
+            m |= (1u << v) | (1u << (8 + v));  // an isolated empty entry
+          }
+        }
+        cmask[c * 32 + lane] = m;
+      }
+    memcpy(host.data() + h->rc_tab_off[5], cmask.data(), cmask.size() * sizeof(unsigned));
+    if (h->prec == MM_FP64) {
+      memcpy(host.data() + h->rc_tab_off[6], cwd.data(), cwd.size() * 8);
+    } else {
+      std::vector<float> cwf(cwd.begin(), cwd.end());
+      memcpy(host.data() + h->rc_tab_off[6], cwf.data(), cwf.size() * 4);
+    }
+  }
   CK(cudaMemcpy(h->rc_tab, host.data(), tab_bytes, cudaMemcpyHostToDevice));
   CK(cudaMemset(h->rc_mb, 0, nc * nconf * t));
   h->rc = rc;
@@ -648,8 +788,10 @@ mm_status mm_set_capture(mm_handle* h, double rc) {
   h->rc_host_w = w;
   int per_sm = 0;
   CK(h->prec == MM_FP64
-         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mm::k_rc_motor<double>, 128, 0)
-         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mm::k_rc_motor<float>, 128, 0));
+         ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+               &per_sm, mm::k_rc_motor<double, kRcStages>, 128, rc_ring_bytes<double>())
+         : cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+               &per_sm, mm::k_rc_motor<float, kRcStages>, 128, rc_ring_bytes<float>()));
   h->rc_motor_grid = (int)std::max<long long>(
       1, std::min<long long>((h->ncells + 3) / 4, (long long)std::max(per_sm, 1) * h->sms));
   h->capture = true;

@@ -156,7 +156,7 @@ struct mm_handle {
   void* rc_mb = nullptr;   // [cells][nconf] motor density, anchor-major (template order)
   void* rc_ls = nullptr;   // [cells][nlines] line sums of Mb ds
   void* rc_tab = nullptr;  // the template's device tables (one block)
-  size_t rc_tab_off[5] = {0, 0, 0, 0, 0};
+  size_t rc_tab_off[7] = {0, 0, 0, 0, 0, 0, 0};
   std::vector<int> rc_host_lines;  // [nlines][6] (k, dx, dy, j0, len, off)
   std::vector<double> rc_host_w;   // [nth][ns] 1 / n_a
   // thin-gap fluid solve (mm_fluid_setup)

@@ -159,8 +159,12 @@ __device__ __forceinline__ void rc_walk(const T (&M)[kRcV], unsigned mask, T (&D
 // copies: a chunk may start anywhere); lane l computes the chunk's entries
 // 8 l .. 8 l + 7, and the new values go back through the stage so that the
 // global stores are coalesced too.
+#ifndef MM_RC_MIN_BLOCKS
+#define MM_RC_MIN_BLOCKS 1
+#endif
 template <typename T, int S>
-__global__ void __launch_bounds__(128) k_rc_motor(const RcArgs<T> x, const T* psi_c, int init) {
+__global__ void __launch_bounds__(128, sizeof(T) == 4 ? MM_RC_MIN_BLOCKS : 1)
+    k_rc_motor(const RcArgs<T> x, const T* psi_c, int init) {
   extern __shared__ __align__(16) unsigned char rc_ring_raw[];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const long long gw = blockIdx.x * 4LL + wib, W = (long long)gridDim.x * 4;
@@ -201,8 +205,7 @@ __global__ void __launch_bounds__(128) k_rc_motor(const RcArgs<T> x, const T* ps
     const int4 cd = x.chunk[ch];
     const unsigned mask = x.cmask[ch * 32 + lane];
     T wv[kRcV];
-#pragma unroll
-    for (int v = 0; v < kRcV; ++v) wv[v] = x.cw[(size_t)ch * kRcChunk + 8 * lane + v];
+    lds8(x.cw + (size_t)ch * kRcChunk + 8 * lane, wv);  // 16-byte vector loads (global)
     cp_async_wait<S - 1>();
     __syncwarp();
     T* st = ring + (size_t)(q % S) * kRcChunk;
@@ -212,12 +215,40 @@ __global__ void __launch_bounds__(128) k_rc_motor(const RcArgs<T> x, const T* ps
     for (int v = 0; v < kRcV; ++v)
       if (!((mask >> (16 + v)) & 1u)) M[v] = T(0);
     rc_walk<T>(M, mask, D);
+    if constexpr (sizeof(T) == 4) {
+      // the element-wise stage updates as packed two-value float32 operations
+      const float2 c1_ = make_float2(c1, c1), c2_ = make_float2(c2, c2);
+      const float2 e1_ = make_float2(e1, e1), e2_ = make_float2(e2, e2);
+      const float2 hm = make_float2(hk * mfa, hk * mfa), fm = make_float2(fk * mfa, fk * mfa);
+      float2 bh[kRcV / 2], bf[kRcV / 2];
 #pragma unroll
-    for (int v = 0; v < kRcV; ++v) Ms[v] = fma_t(c1, D[v], fma_t(c2, M[v], hk * (mfa * wv[v])));
-    rc_walk<T>(Ms, mask, D);
+      for (int h = 0; h < kRcV / 2; ++h) {
+        const float2 w2 = make_float2(wv[2 * h], wv[2 * h + 1]);
+        bh[h] = __fmul2_rn(hm, w2);
+        bf[h] = __fmul2_rn(fm, w2);
+        const float2 r = __ffma2_rn(c1_, make_float2(D[2 * h], D[2 * h + 1]),
+                                    __ffma2_rn(c2_, make_float2(M[2 * h], M[2 * h + 1]), bh[h]));
+        Ms[2 * h] = r.x;
+        Ms[2 * h + 1] = r.y;
+      }
+      rc_walk<T>(Ms, mask, D);
 #pragma unroll
-    for (int v = 0; v < kRcV; ++v)
-      M[v] = fma_t(e1, D[v], fma_t(e2, Ms[v], M[v] + fk * (mfa * wv[v])));
+      for (int h = 0; h < kRcV / 2; ++h) {
+        const float2 r = __ffma2_rn(
+            e1_, make_float2(D[2 * h], D[2 * h + 1]),
+            __ffma2_rn(e2_, make_float2(Ms[2 * h], Ms[2 * h + 1]),
+                       __fadd2_rn(make_float2(M[2 * h], M[2 * h + 1]), bf[h])));
+        M[2 * h] = r.x;
+        M[2 * h + 1] = r.y;
+      }
+    } else {
+#pragma unroll
+      for (int v = 0; v < kRcV; ++v) Ms[v] = fma_t(c1, D[v], fma_t(c2, M[v], hk * (mfa * wv[v])));
+      rc_walk<T>(Ms, mask, D);
+#pragma unroll
+      for (int v = 0; v < kRcV; ++v)
+        M[v] = fma_t(e1, D[v], fma_t(e2, Ms[v], M[v] + fk * (mfa * wv[v])));
+    }
     __syncwarp();
     sts8(st + 8 * lane, M);
     __syncwarp();

@@ -43,6 +43,10 @@ struct AnchorArgs {
   // woy..woy+wy-1; widx [nth][ns] is each node's index in it (wx * wy entries).
   const int* widx;
   int wox, woy, wx, wy;
+  // The window shared by a block's 4 consecutive cells of a row (wx + 3
+  // columns): widxb [nth][ns] is each node's index in it for the group's first
+  // cell (+ the cell's place in the group).
+  const int* widxb;
 };
 
 __device__ __forceinline__ int anchor_cell(int ix, int iy, int2 o, int nx, int ny) {
@@ -104,22 +108,34 @@ __host__ __device__ inline size_t anchor_warp_smem(int nth, int tsz, int W = 0) 
 // the window's free motors are gathered into shared memory when the cell
 // starts and the rows' contributions to C are summed there (shared-memory
 // atomics), then added to the global accumulators once per window entry.
-template <typename T, int V, bool MASSCORR, bool WIN>
+// BW (with WIN): the block's 4 warps take 4 consecutive cells of one row and
+// share one window of wx + 3 columns: it is filled and flushed once per group
+// of cells instead of once per cell (the window's set-up and its global
+// atomics dominate when the heads reach far: 27 x 27 cells at 512^2 with
+// l/L = 0.05, against 64 x 64 nodes per cell).
+template <typename T, int V, bool MASSCORR, bool WIN, bool BW = false>
 __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(const StepArgs<T> a, const AnchorArgs<T> x) {
   extern __shared__ __align__(16) unsigned char asm_raw[];
   const int nth = a.nth, ns = a.ns, seg = a.seg, nx = a.nx, ny = a.ny;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int Wn = WIN ? x.wx * x.wy : 0;
-  unsigned char* wbase = asm_raw + (size_t)wib * anchor_warp_smem(nth, sizeof(T), Wn);
+  const int Wn = WIN ? (BW ? (x.wx + 3) * x.wy : x.wx * x.wy) : 0;
+  unsigned char* wbase =
+      asm_raw + (size_t)wib * anchor_warp_smem(nth, sizeof(T), BW ? 0 : Wn);
   T* psi5 = reinterpret_cast<T*>(wbase);
   T* nb5 = psi5 + 5 * nth;
   T* pnew = nb5 + 5 * nth;
-  T* wmf = reinterpret_cast<T*>(wbase + (((size_t)11 * nth * sizeof(T) + 15) & ~(size_t)15));
+  // the window: per warp after its columns, or (BW) one for the block after
+  // the 4 warps' columns
+  unsigned char* winbase =
+      BW ? asm_raw + 4 * anchor_warp_smem(nth, sizeof(T), 0)
+         : wbase + (((size_t)11 * nth * sizeof(T) + 15) & ~(size_t)15);
+  T* wmf = reinterpret_cast<T*>(winbase);
   T* wacc = wmf + Wn;
   int* wcell = reinterpret_cast<int*>(wacc + Wn);
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
   const int W = gridDim.x * (blockDim.x >> 5);
   const int nc = (int)a.ncells;
+  const int* widx_tab = BW ? x.widxb : x.widx;
   // the flag of the other parity was read by the previous substep's fix-up:
   // clear it for the next substep
   if (blockIdx.x == 0 && threadIdx.x == 0) x.flags[x.flag ^ 1] = 0;
@@ -132,7 +148,12 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
   const LaneGeom lg = lane_geom(lane, seg, ns, V);
   const LaneTrig<T> lt = lane_trig(a.trig, nth, lane);
   T mass_hi = T(0), mass_lo = T(0);
-  for (int cell = gw; cell < nc; cell += W) {
+  // BW: block-strided groups of 4 consecutive cells (nx is a multiple of 4,
+  // so the 4 warps of a block run the same iterations and all reach the block
+  // barriers); else warp-strided cells
+  const int cstart = BW ? (int)blockIdx.x * 4 + wib : gw;
+  const int cstep = BW ? (int)gridDim.x * 4 : W;
+  for (int cell = cstart; cell < nc; cell += cstep) {
     const int iy = cell / nx, ix = cell - iy * nx;
     const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
     const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
@@ -142,7 +163,22 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
         psi5[q * nth + k] = a.psi_in[(size_t)nbr[q] * nth + k];
         nb5[q * nth + k] = a.nb_in[(size_t)nbr[q] * nth + k];
       }
-    if (WIN) {
+    if (BW) {
+      // the group's window: the first cell's window widened by 3 columns
+      const int c0 = cell - wib, iy0 = c0 / nx, ix0 = c0 - iy0 * nx;
+      const int wxb = x.wx + 3;
+      for (int w = threadIdx.x; w < Wn; w += blockDim.x) {
+        const int wyi = w / wxb, wxi = w - wyi * wxb;
+        int gx = (ix0 + x.wox + wxi) % nx, gy = (iy0 + x.woy + wyi) % ny;
+        if (gx < 0) gx += nx;
+        if (gy < 0) gy += ny;
+        const int gc = gy * nx + gx;
+        wcell[w] = gc;
+        wmf[w] = a.mf_in[gc];
+        wacc[w] = T(0);
+      }
+      __syncthreads();
+    } else if (WIN) {
       for (int w = lane; w < Wn; w += 32) {
         const int wyi = w / x.wx, wxi = w - wyi * x.wx;
         int gx = (ix + x.wox + wxi) % nx, gy = (iy + x.woy + wyi) % ny;
@@ -172,7 +208,7 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
       if (k < nth && lg.lane_ok) {
         qn = *reinterpret_cast<const Pack<T, V>*>(a.mb_in + ((size_t)cell * nth + k) * ns +
                                                   lg.sl * V);
-        if (WIN) wn = *reinterpret_cast<const Pack<int, V>*>(x.widx + (size_t)k * ns + lg.sl * V);
+        if (WIN) wn = *reinterpret_cast<const Pack<int, V>*>(widx_tab + (size_t)k * ns + lg.sl * V);
       }
     };
     load_pass(0);
@@ -189,7 +225,7 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
 #pragma unroll
           for (int v = 0; v < V; ++v) {
             M[v] = q.v[v];
-            anc[v] = wi.v[v];
+            anc[v] = wi.v[v] + (BW ? wib : 0);
             mfv[v] = wmf[anc[v]];
           }
         } else {
@@ -236,7 +272,14 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
       if (lg.first && row_ok) a.nb_out[(size_t)cell * nth + k] = snb * sc.ds;
     }
     __syncwarp();
-    if (WIN) {  // the window's sums into the global accumulators
+    if (BW) {  // the group's window into the global accumulators, once
+      __syncthreads();
+      for (int w = threadIdx.x; w < Wn; w += blockDim.x) {
+        const T v = wacc[w];
+        if (v != T(0)) atomicAdd(x.cacc + wcell[w], (double)v);
+      }
+      __syncthreads();
+    } else if (WIN) {  // the window's sums into the global accumulators
       for (int w = lane; w < Wn; w += 32) {
         const T v = wacc[w];
         if (v != T(0)) atomicAdd(x.cacc + wcell[w], (double)v);
@@ -421,6 +464,7 @@ mm::AnchorArgs<T> anchor_args(mm_handle* h, int flag) {
   x.flags = h->anc_flags;
   x.flag = flag;
   x.widx = h->anc_widx;
+  x.widxb = h->anc_widxb;
   x.wox = h->anc_win[0];
   x.woy = h->anc_win[1];
   x.wx = h->anc_win[2];
@@ -432,6 +476,15 @@ int blocks_for(long long work, int per_block, int cap) {
   long long b = (work + per_block - 1) / per_block;
   if (b > cap) b = cap;
   return (int)std::max<long long>(b, 1);
+}
+
+// Shared memory of the block-window form: the 4 warps' columns, then the
+// window of (wx + 3) x wy entries (free motors, accumulators, cell indices).
+template <typename T>
+size_t anchor_bw_smem(const mm_handle* h) {
+  const size_t wn = (size_t)(h->anc_win[2] + 3) * h->anc_win[3];
+  return 4 * mm::anchor_warp_smem(h->g.ntheta, sizeof(T), 0) +
+         ((wn * (2 * sizeof(T) + 4) + 15) & ~(size_t)15);
 }
 
 // Warps per block of the anchor substep (shared memory of 11 ntheta values per
@@ -451,6 +504,20 @@ cudaError_t anchor_prepare_t(mm_handle* h) {
     cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
   }
+  if (h->anc_bw) {
+    const size_t bsm = anchor_bw_smem<T>(h);
+    if (bsm > kSmemBudget) {
+      h->anc_bw = false;
+    } else {
+      const void* bfns[2] = {(const void*)mm::k_substep_anchor<T, V, true, true, true>,
+                             (const void*)mm::k_substep_anchor<T, V, false, true, true>};
+      for (const void* f : bfns) {
+        cudaError_t e =
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+        if (e != cudaSuccess) return e;
+      }
+    }
+  }
   return cudaSuccess;
 }
 
@@ -462,7 +529,14 @@ cudaError_t anchor_substep_t(mm_handle* h, int parity, cudaStream_t s) {
   const bool win = x.wx > 0;
   const size_t smem = wpb * mm::anchor_warp_smem(h->g.ntheta, sizeof(T), x.wx * x.wy);
   const int grid = blocks_for(h->ncells, wpb, 8 * h->sms);
-  if (win) {
+  if (win && h->anc_bw) {  // 4 consecutive cells of a row per block, one window
+    const int bgrid = blocks_for(h->ncells / 4, 1, 8 * h->sms);
+    const size_t bsm = anchor_bw_smem<T>(h);
+    if (a.mass_correct)
+      mm::k_substep_anchor<T, V, true, true, true><<<bgrid, 128, bsm, s>>>(a, x);
+    else
+      mm::k_substep_anchor<T, V, false, true, true><<<bgrid, 128, bsm, s>>>(a, x);
+  } else if (win) {
     if (a.mass_correct)
       mm::k_substep_anchor<T, V, true, true><<<grid, 32 * wpb, smem, s>>>(a, x);
     else
@@ -540,6 +614,7 @@ mm_status anchor_alloc(mm_handle* h) {
   if (need + (1 << 20) > freeb) return fail(h, MM_ERR_OOM, "anchor buffers do not fit");
   CK(cudaMalloc((void**)&h->anc_off, (size_t)h->g.ntheta * h->g.ns * sizeof(int2)));
   CK(cudaMalloc((void**)&h->anc_widx, (size_t)h->g.ntheta * h->g.ns * sizeof(int)));
+  CK(cudaMalloc((void**)&h->anc_widxb, (size_t)h->g.ntheta * h->g.ns * sizeof(int)));
   CK(cudaMalloc((void**)&h->anc_cacc, nc * 8));
   CK(cudaMalloc((void**)&h->anc_fsc, nc * 8));
   CK(cudaMalloc((void**)&h->anc_flags, 4 * sizeof(int)));
@@ -578,11 +653,16 @@ mm_status anchor_table(mm_handle* h) {
   }
   // the window of anchor cells around a filament cell, when it is small
   const long long wx = xmax - xmin + 1, wy = ymax - ymin + 1;
-  std::vector<int> widx((size_t)nth * ns);
+  std::vector<int> widx((size_t)nth * ns), widxb((size_t)nth * ns);
   h->anc_win[0] = h->anc_win[1] = h->anc_win[2] = h->anc_win[3] = 0;
+  // a block's 4 warps share one window when they take 4 consecutive cells of a
+  // row (nx a multiple of 4) and the widened window fits
+  h->anc_bw = nx % 4 == 0 && (wx + 3) * wy <= kAnchorBlockWindowMax && wx * wy <= kAnchorWindowMax;
   if (wx * wy <= kAnchorWindowMax) {
-    for (size_t q = 0; q < widx.size(); ++q)
+    for (size_t q = 0; q < widx.size(); ++q) {
       widx[q] = (int)((raw[q].y - ymin) * wx + (raw[q].x - xmin));
+      widxb[q] = (int)((raw[q].y - ymin) * (wx + 3) + (raw[q].x - xmin));
+    }
     h->anc_win[0] = (int)xmin;
     h->anc_win[1] = (int)ymin;
     h->anc_win[2] = (int)wx;
@@ -591,6 +671,7 @@ mm_status anchor_table(mm_handle* h) {
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(h->anc_off, off.data(), off.size() * sizeof(int2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->anc_widx, widx.data(), widx.size() * sizeof(int), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(h->anc_widxb, widxb.data(), widxb.size() * sizeof(int), cudaMemcpyHostToDevice));
   // captured substep graphs hold the window and block shape as launch arguments
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();

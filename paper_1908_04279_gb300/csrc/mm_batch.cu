@@ -109,6 +109,10 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
   int cell = 0, ce = 0, cwc = 0, cn = 0, cs = 0, ix = 0, iy = 0;
   T mtot = 0;
   CellVel<T> uv{};
+  // the next cell's free and total motors, loaded while the current cell is
+  // computed (the RK2 constants need them as soon as a cell starts)
+  T mf_next = 0, mtot_next = 0;
+  bool have_next = false;
 
   // sum of the finished tile; the last tile of an instance finalises it
   auto close_tile = [&]() {
@@ -168,6 +172,19 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
         ++iy;
       }
       cell = ct.cell0 + ccell;
+      T mf_n;
+      if (have_next && ccell > 0) {
+        mf_n = mf_next;
+        mtot = mtot_next;
+      } else {
+        mf_n = A->mf_in[cell];
+        mtot = A->mtot[cell];
+      }
+      have_next = ccell + 1 < ct.ncell;
+      if (have_next) {  // Mf of the next cell is written only when that cell is done
+        mf_next = A->mf_in[cell + 1];
+        mtot_next = A->mtot[cell + 1];
+      }
       if (nb_tma) nb_par ^= 1u;  // members differ in whether they stage by bulk copy
       const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
       const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
@@ -175,8 +192,6 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
       cwc = iy * nx + xm;
       cn = yp * nx + ix;
       cs = ym * nx + ix;
-      const T mf_n = A->mf_in[cell];
-      mtot = A->mtot[cell];
       rk.c3 = hdt * kon * mf_n;
       rk.e3 = dt * kon * mf_n;
       uv = load_cell_vel(A->ucell, cell);

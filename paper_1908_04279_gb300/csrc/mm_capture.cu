@@ -160,7 +160,7 @@ __device__ __forceinline__ void rc_walk(const T (&M)[kRcV], unsigned mask, T (&D
 // 8 l .. 8 l + 7, and the new values go back through the stage so that the
 // global stores are coalesced too.
 #ifndef MM_RC_MIN_BLOCKS
-#define MM_RC_MIN_BLOCKS 1
+#define MM_RC_MIN_BLOCKS 8
 #endif
 template <typename T, int S>
 __global__ void __launch_bounds__(128, sizeof(T) == 4 ? MM_RC_MIN_BLOCKS : 1)

@@ -136,6 +136,8 @@ struct mm_handle {
   int anc_wpb = 4;              // warps per block of the anchor substep
   void* anc_off = nullptr;      // [nth][ns] int2 anchor cell offsets
   int* anc_widx = nullptr;      // [nth][ns] index of each node's anchor in the window
+  int* anc_widxb = nullptr;     // [nth][ns] the same in a block's window (4 cells of a row)
+  bool anc_bw = false;          // the block's 4 warps share one window
   int anc_win[4] = {0, 0, 0, 0};  // window: first x and y offset, width, height (0: none)
   double* anc_cacc = nullptr;   // [cells] float64 accumulators of C
   double* anc_fsc = nullptr;    // [cells] scale-down factors
@@ -239,6 +241,7 @@ constexpr int kWarpInflightBytes = 8192;
 constexpr int kMaxWarpsPerBlock = 4;
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic shared memory per block at most
 constexpr long long kAnchorWindowMax = 1024;   // anchor window entries kept in shared memory
+constexpr long long kAnchorBlockWindowMax = 4096;  // entries of a window shared by a block
 
 // Defined in mm_api.cu.
 mm_status check_rates(const mm_rates* r, mm_handle* h);

@@ -109,6 +109,11 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
   const LaneTrig<T> lt = lane_trig(a.trig, nth, lane);
   uint32_t nb_par = 1;  // parity of the neighbourhood phase of the current cell
   T mtot = 0;
+  // Mf and M of this warp's next cell (cell + W), loaded while the current
+  // cell is computed: the RK2 constants need them as soon as a cell starts.
+  // A cell's Mf is written only when that cell is done, by this warp.
+  T mf_next = gw < (int)a.ncells ? a.mf_in[gw] : T(0);
+  T mtot_next = gw < (int)a.ncells ? a.mtot[gw] : T(0);
   T mass_hi = T(0), mass_lo = T(0);  // compensated sum of psi^{n+1} over this warp's cells
   int part = 0, s = 0;
   uint32_t par = 0;  // parity of the phase chunk t waits for on stage s
@@ -135,8 +140,12 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
       cwc = iy * nx + xm;
       cn = yp * nx + ix;
       cs = ym * nx + ix;
-      const T mf_n = a.mf_in[cell];
-      mtot = a.mtot[cell];
+      const T mf_n = mf_next;
+      mtot = mtot_next;
+      if (cell + W < (int)a.ncells) {
+        mf_next = a.mf_in[cell + W];
+        mtot_next = a.mtot[cell + W];
+      }
       // stage constants: c for the half step, e for the full step
       rk.c3 = hdt * kon * mf_n;
       rk.e3 = dt * kon * mf_n;

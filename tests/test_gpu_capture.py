@@ -18,6 +18,8 @@ CASES = [  # grid, l/L, r_c (in cells of the x spacing: about 1, 2 and 3 cells)
     ((12, 10, 8, 12), 0.31, 1.1 / 12),
     ((16, 14, 6, 7), 0.27, 2.05 / 16),
     ((20, 18, 8, 16), 0.19, 3.02 / 20),
+    ((10, 9, 40, 20), 0.23, 1.3 / 10),   # more orientations than lanes
+    ((12, 12, 6, 64), 0.3, 1.2 / 12),    # lines of up to 64 nodes
 ]
 
 
@@ -121,7 +123,7 @@ def test_capture_forced_scale_down_fp64(mmod, oracle_mod):
         assert rel(got[k], getattr(st, k)) <= 1e-12, (k, rel(got[k], getattr(st, k)))
 
 
-@pytest.mark.parametrize("dims,ell,rc", CASES[:2])
+@pytest.mark.parametrize("dims,ell,rc", CASES[:2] + CASES[4:])
 def test_capture_fp32_close_to_the_oracle(mmod, oracle_mod, dims, ell, rc):
     O = oracle_mod
     g = Grid(*dims)

@@ -43,7 +43,8 @@ DP = (1.0, 0.3, -0.5)  # d k_off, d v_walk, d k_on
 
 
 @pytest.mark.parametrize("dims,clip", [((12, 10, 8, 8), False), ((9, 7, 6, 6), False),
-                                       ((10, 8, 8, 8), True)])
+                                       ((10, 8, 8, 8), True), ((6, 5, 36, 7), False),
+                                       ((5, 4, 6, 64), False)])
 def test_tangent_equals_oracle_tangent(mmod, oracle_mod, dims, clip):
     O = oracle_mod
     g = Grid(*dims, L=1.1)

@@ -19,6 +19,9 @@
 // reduction only (Sec. 2); here the coarse density and the force are
 // accumulated that way, in float64. Atomic order makes the last bits of C
 // depend on the schedule.
+#include <algorithm>
+#include <utility>
+
 #include "mm_cell.cuh"
 #include "mm_host.h"
 
@@ -47,6 +50,19 @@ struct AnchorArgs {
   // columns): widxb [nth][ns] is each node's index in it for the group's first
   // cell (+ the cell's place in the group).
   const int* widxb;
+  // [nth][ns / V]: per orientation and lane slot, bits 0-7: bit v set where
+  // the slot's node v is the last of a run of nodes with one anchor (the same
+  // in every cell: the anchors' offsets depend on (k, j) only); bits 8-31: the
+  // number of such slot runs before the slot in a cell (k-major, then slot)
+  const unsigned* runend;
+  // The block-window form's sum of the slot runs into the window: the 4 cells'
+  // nsr run sums each are listed as (window entry, run) pairs sorted by entry
+  // and cut into 128 equal chunks, one per thread, stored step-major
+  // ([rt_e][128]); an entry packs the run's index in the block's sums (bits
+  // 0-15), its window entry (bits 16-30) and bit 31 set where the entry's
+  // partial sum ends within the chunk. Padding reads a zero kept after the sums.
+  const unsigned* rtab;
+  int rt_e, nsr;
 };
 
 __device__ __forceinline__ int anchor_cell(int ix, int iy, int2 o, int nx, int ny) {
@@ -54,6 +70,45 @@ __device__ __forceinline__ int anchor_cell(int ix, int iy, int2 o, int nx, int n
   if (ax >= nx) ax -= nx;
   if (ay >= ny) ay -= ny;
   return ay * nx + ax;
+}
+
+// List entries a thread of the block-window form loads at once.
+constexpr int kRtBatch = 8;
+
+// A lane's V values of the motor density, loaded and stored with the streaming
+// (evict-first) cache policy: the density is read and written once per
+// substep, and the anchor tables the kernel re-reads for every cell stay in L1.
+template <typename T, int V>
+__device__ __forceinline__ Pack<T, V> ld_stream(const T* p) {
+  Pack<T, V> r;
+  if constexpr (sizeof(T) == 4 && V % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < V / 4; ++i) {
+      const float4 f = __ldcs(reinterpret_cast<const float4*>(p) + i);
+      r.v[4 * i] = f.x, r.v[4 * i + 1] = f.y, r.v[4 * i + 2] = f.z, r.v[4 * i + 3] = f.w;
+    }
+  } else if constexpr (sizeof(T) == 8 && V == 2) {
+    const double2 d = __ldcs(reinterpret_cast<const double2*>(p));
+    r.v[0] = d.x, r.v[1] = d.y;
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) r.v[v] = __ldcs(p + v);
+  }
+  return r;
+}
+template <typename T, int V>
+__device__ __forceinline__ void st_stream(T* p, const T (&M)[V]) {
+  if constexpr (sizeof(T) == 4 && V % 4 == 0) {
+#pragma unroll
+    for (int i = 0; i < V / 4; ++i)
+      __stcs(reinterpret_cast<float4*>(p) + i,
+             make_float4(M[4 * i], M[4 * i + 1], M[4 * i + 2], M[4 * i + 3]));
+  } else if constexpr (sizeof(T) == 8 && V == 2) {
+    __stcs(reinterpret_cast<double2*>(p), make_double2(M[0], M[1]));
+  } else {
+#pragma unroll
+    for (int v = 0; v < V; ++v) __stcs(p + v, M[v]);
+  }
 }
 
 // Adds w M[v] of the lane's nodes into the accumulators of their anchors: a
@@ -95,6 +150,22 @@ __device__ __forceinline__ void scatter_runs_smem(T* acc, const int (&widx)[V], 
   atomicAdd(acc + cur, s);
 }
 
+// The same driven by the run-end mask of the lane's slot: one shared atomic
+// per run, no comparison of anchors.
+template <typename T, int V>
+__device__ __forceinline__ void scatter_runs_mask(T* acc, const int (&widx)[V], const T (&M)[V],
+                                                  T w, unsigned ends) {
+  T s = T(0);
+#pragma unroll
+  for (int v = 0; v < V; ++v) {
+    s = fma_t(w, M[v], s);
+    if ((ends >> v) & 1u) {
+      atomicAdd(acc + widx[v], s);
+      s = T(0);
+    }
+  }
+}
+
 // Per-warp shared memory: psi and n_b columns of the cell and its four
 // neighbours ([5][nth] each) and psi^{n+1} of the cell.
 __host__ __device__ inline size_t anchor_warp_smem(int nth, int tsz, int W = 0) {
@@ -130,8 +201,12 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
       BW ? asm_raw + 4 * anchor_warp_smem(nth, sizeof(T), 0)
          : wbase + (((size_t)11 * nth * sizeof(T) + 15) & ~(size_t)15);
   T* wmf = reinterpret_cast<T*>(winbase);
-  T* wacc = wmf + Wn;
-  int* wcell = reinterpret_cast<int*>(wacc + Wn);
+  T* wacc = wmf + Wn;  // the per-warp window's sums
+  // BW: the window's cells after its free motors, then the 4 cells' slot-run
+  // sums [4][nsr] and one zero
+  int* wcell = reinterpret_cast<int*>(BW ? wmf + Wn : wacc + Wn);
+  T* rb = reinterpret_cast<T*>(winbase + (((size_t)Wn * (sizeof(T) + 4) + 15) & ~(size_t)15));
+  if (BW && threadIdx.x == 0) rb[4 * x.nsr] = T(0);
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
   const int W = gridDim.x * (blockDim.x >> 5);
   const int nc = (int)a.ncells;
@@ -175,7 +250,6 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
         const int gc = gy * nx + gx;
         wcell[w] = gc;
         wmf[w] = a.mf_in[gc];
-        wacc[w] = T(0);
       }
       __syncthreads();
     } else if (WIN) {
@@ -203,12 +277,15 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
     // computed
     Pack<T, V> qn;
     Pack<int, V> wn;
+    unsigned en = 0;  // the slot's run ends and first slot run
     auto load_pass = [&](int r0) {
       const int k = r0 + lg.rslot;
       if (k < nth && lg.lane_ok) {
-        qn = *reinterpret_cast<const Pack<T, V>*>(a.mb_in + ((size_t)cell * nth + k) * ns +
-                                                  lg.sl * V);
-        if (WIN) wn = *reinterpret_cast<const Pack<int, V>*>(widx_tab + (size_t)k * ns + lg.sl * V);
+        qn = ld_stream<T, V>(a.mb_in + ((size_t)cell * nth + k) * ns + lg.sl * V);
+        if (WIN) {
+          wn = *reinterpret_cast<const Pack<int, V>*>(widx_tab + (size_t)k * ns + lg.sl * V);
+          en = x.runend[(size_t)k * (ns / V) + lg.sl];
+        }
       }
     };
     load_pass(0);
@@ -218,15 +295,23 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
       const size_t roff = ((size_t)cell * nth + (row_ok ? k : 0)) * ns + lg.sl * V;
       T M[V], D[V], Ms[V], mfv[V];
       int anc[V];
+      unsigned ends = 0, srun = 0;
       if (act) {
         const Pack<T, V> q = qn;
         if (WIN) {
+          // the free motors of each run's anchor, read once at the run's
+          // first node
           const Pack<int, V> wi = wn;
+          ends = en & 0xffu;
+          srun = en >> 8;
+          const unsigned starts = (ends << 1) | 1u;
+          T cur = T(0);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
             M[v] = q.v[v];
             anc[v] = wi.v[v] + (BW ? wib : 0);
-            mfv[v] = wmf[anc[v]];
+            if ((starts >> v) & 1u) cur = wmf[anc[v]];
+            mfv[v] = cur;
           }
         } else {
           const int2* o = x.off + (size_t)k * ns + lg.sl * V;
@@ -246,23 +331,64 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
         }
       }
       if (r0 + lg.rpp < nth) load_pass(r0 + lg.rpp);
-      walk_dflux<T, V>(M, D, lg.first, lg.last, seg);
-#pragma unroll
-      for (int v = 0; v < V; ++v) Ms[v] = fma_t(c1, D[v], fma_t(c2, M[v], hk * mfv[v]));
-      walk_dflux<T, V>(Ms, D, lg.first, lg.last, seg);
       T snb = T(0);
+      if constexpr (sizeof(T) == 4 && (V == 4 || V == 8)) {
+        // register pairs, packed two-value arithmetic: the same nodal values,
+        // bit for bit, as the scalar form below (the lane's n_b part is summed
+        // in pairs)
+        constexpr int H = V / 2;
+        float2 M2[H], D2[H], Ms2[H], b2[H];
+        const float2 c1_ = make_float2(c1, c1), c2_ = make_float2(c2, c2);
+        const float2 e1_ = make_float2(e1, e1), e2_ = make_float2(e2, e2);
+        const float2 hk_ = make_float2(hk, hk), fk_ = make_float2(fk, fk);
 #pragma unroll
-      for (int v = 0; v < V; ++v) {
-        M[v] = fma_t(e1, D[v], fma_t(e2, Ms[v], M[v] + fk * mfv[v]));
-        snb += M[v];
+        for (int h = 0; h < H; ++h) {
+          M2[h] = make_float2(M[2 * h], M[2 * h + 1]);
+          b2[h] = make_float2(mfv[2 * h], mfv[2 * h + 1]);
+        }
+        walk_dflux_x2<V>(M2, D2, lg.first, lg.last, seg);
+#pragma unroll
+        for (int h = 0; h < H; ++h)
+          Ms2[h] = __ffma2_rn(c1_, D2[h], __ffma2_rn(c2_, M2[h], __fmul2_rn(hk_, b2[h])));
+        walk_dflux_x2<V>(Ms2, D2, lg.first, lg.last, seg);
+        float2 acc2 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int h = 0; h < H; ++h) {
+          M2[h] = __ffma2_rn(e1_, D2[h],
+                             __ffma2_rn(e2_, Ms2[h], __ffma2_rn(fk_, b2[h], M2[h])));
+          acc2 = __fadd2_rn(acc2, M2[h]);
+          M[2 * h] = M2[h].x;
+          M[2 * h + 1] = M2[h].y;
+        }
+        snb = acc2.x + acc2.y;
+      } else {
+        walk_dflux<T, V>(M, D, lg.first, lg.last, seg);
+#pragma unroll
+        for (int v = 0; v < V; ++v) Ms[v] = fma_t(c1, D[v], fma_t(c2, M[v], hk * mfv[v]));
+        walk_dflux<T, V>(Ms, D, lg.first, lg.last, seg);
+#pragma unroll
+        for (int v = 0; v < V; ++v) {
+          M[v] = fma_t(e1, D[v], fma_t(e2, Ms[v], fma_t(fk, mfv[v], M[v])));
+          snb += M[v];
+        }
       }
       if (act) {
-        Pack<T, V> q;
+        st_stream<T, V>(a.mb_out + roff, M);
+        if (BW) {
+          // each slot run's sum into its place among the block's run sums
+          const T w = pnew[k] * dsdth;
+          T* r = rb + (size_t)wib * x.nsr + srun;
+          T s = T(0);
 #pragma unroll
-        for (int v = 0; v < V; ++v) q.v[v] = M[v];
-        *reinterpret_cast<Pack<T, V>*>(a.mb_out + roff) = q;
-        if (WIN)
-          scatter_runs_smem<T, V>(wacc, anc, M, pnew[k] * dsdth);
+          for (int v = 0; v < V; ++v) {
+            s = fma_t(w, M[v], s);
+            if ((ends >> v) & 1u) {
+              *r++ = s;
+              s = T(0);
+            }
+          }
+        } else if (WIN)
+          scatter_runs_mask<T, V>(wacc, anc, M, pnew[k] * dsdth, ends);
         else
           scatter_runs<T, V>(x.cacc, anc, M, pnew[k] * dsdth);
       } else {
@@ -272,11 +398,29 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
       if (lg.first && row_ok) a.nb_out[(size_t)cell * nth + k] = snb * sc.ds;
     }
     __syncwarp();
-    if (BW) {  // the group's window into the global accumulators, once
+    if (BW) {
+      // the group's run sums into the global accumulators: each thread sums
+      // its chunk of the (entry, run) list, one atomic per entry it ends
       __syncthreads();
-      for (int w = threadIdx.x; w < Wn; w += blockDim.x) {
-        const T v = wacc[w];
-        if (v != T(0)) atomicAdd(x.cacc + wcell[w], (double)v);
+      // (rt_e is a multiple of kRtBatch: a batch of list entries is loaded
+      // before any is used, so that their loads overlap)
+      const unsigned* rt = x.rtab + threadIdx.x;
+      T acc = T(0);
+      for (int i0 = 0; i0 < x.rt_e; i0 += kRtBatch) {
+        unsigned e[kRtBatch];
+#pragma unroll
+        for (int i = 0; i < kRtBatch; ++i) e[i] = __ldg(rt + (size_t)(i0 + i) * 128);
+        T r[kRtBatch];
+#pragma unroll
+        for (int i = 0; i < kRtBatch; ++i) r[i] = rb[e[i] & 0xffffu];
+#pragma unroll
+        for (int i = 0; i < kRtBatch; ++i) {
+          acc += r[i];
+          if (e[i] >> 31) {
+            if (acc != T(0)) atomicAdd(x.cacc + wcell[(e[i] >> 16) & 0x7fffu], (double)acc);
+            acc = T(0);
+          }
+        }
       }
       __syncthreads();
     } else if (WIN) {  // the window's sums into the global accumulators
@@ -465,6 +609,10 @@ mm::AnchorArgs<T> anchor_args(mm_handle* h, int flag) {
   x.flag = flag;
   x.widx = h->anc_widx;
   x.widxb = h->anc_widxb;
+  x.runend = h->anc_runend;
+  x.rtab = h->anc_rtab;
+  x.rt_e = h->anc_rt_e;
+  x.nsr = h->anc_nsr;
   x.wox = h->anc_win[0];
   x.woy = h->anc_win[1];
   x.wx = h->anc_win[2];
@@ -479,12 +627,13 @@ int blocks_for(long long work, int per_block, int cap) {
 }
 
 // Shared memory of the block-window form: the 4 warps' columns, then the
-// window of (wx + 3) x wy entries (free motors, accumulators, cell indices).
+// window of (wx + 3) x wy entries (free motors, cell indices), then the 4
+// cells' slot-run sums and one zero.
 template <typename T>
 size_t anchor_bw_smem(const mm_handle* h) {
   const size_t wn = (size_t)(h->anc_win[2] + 3) * h->anc_win[3];
   return 4 * mm::anchor_warp_smem(h->g.ntheta, sizeof(T), 0) +
-         ((wn * (2 * sizeof(T) + 4) + 15) & ~(size_t)15);
+         ((wn * (sizeof(T) + 4) + 15) & ~(size_t)15) + (4 * (size_t)h->anc_nsr + 1) * sizeof(T);
 }
 
 // Warps per block of the anchor substep (shared memory of 11 ntheta values per
@@ -615,6 +764,7 @@ mm_status anchor_alloc(mm_handle* h) {
   CK(cudaMalloc((void**)&h->anc_off, (size_t)h->g.ntheta * h->g.ns * sizeof(int2)));
   CK(cudaMalloc((void**)&h->anc_widx, (size_t)h->g.ntheta * h->g.ns * sizeof(int)));
   CK(cudaMalloc((void**)&h->anc_widxb, (size_t)h->g.ntheta * h->g.ns * sizeof(int)));
+  CK(cudaMalloc((void**)&h->anc_runend, (size_t)h->g.ntheta * h->g.ns * sizeof(unsigned)));
   CK(cudaMalloc((void**)&h->anc_cacc, nc * 8));
   CK(cudaMalloc((void**)&h->anc_fsc, nc * 8));
   CK(cudaMalloc((void**)&h->anc_flags, 4 * sizeof(int)));
@@ -672,6 +822,62 @@ mm_status anchor_table(mm_handle* h) {
   CK(cudaMemcpy(h->anc_off, off.data(), off.size() * sizeof(int2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->anc_widx, widx.data(), widx.size() * sizeof(int), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->anc_widxb, widxb.data(), widxb.size() * sizeof(int), cudaMemcpyHostToDevice));
+  // the run ends of each lane slot of V nodes: a node whose successor in the
+  // slot has another anchor, and the slot's last node (the window indices of
+  // two nodes are equal exactly when their offsets are), with the number of
+  // slot runs before the slot; the block window's entry of each slot run
+  const int V = h->V, nsl = ns / V;
+  std::vector<unsigned> runend((size_t)nth * nsl, 0);
+  std::vector<int> sr_w;
+  for (int k = 0; k < nth; ++k)
+    for (int sl = 0; sl < nsl; ++sl) {
+      unsigned m = 0;
+      const unsigned first = (unsigned)sr_w.size();
+      for (int v = 0; v < V; ++v) {
+        const size_t q = (size_t)k * ns + sl * V + v;
+        if (v == V - 1 || raw[q].x != raw[q + 1].x || raw[q].y != raw[q + 1].y) {
+          m |= 1u << v;
+          sr_w.push_back(widxb[q]);
+        }
+      }
+      runend[(size_t)k * nsl + sl] = m | (first << 8);
+    }
+  CK(cudaMemcpy(h->anc_runend, runend.data(), runend.size() * sizeof(unsigned),
+                cudaMemcpyHostToDevice));
+  // the block window's (entry, run) list: run r of the group's cell c lands in
+  // entry widxb + c; sorted by entry, cut into one chunk per thread of the
+  // block; entries and run indices must fit their bit fields
+  const long long nsr = (long long)sr_w.size();
+  if (h->anc_rtab) cudaFree(h->anc_rtab);
+  h->anc_rtab = nullptr;
+  h->anc_nsr = (int)nsr;
+  h->anc_rt_e = 0;
+  if (h->anc_bw && (4 * nsr + 1 > 0xffff || (wx + 3) * wy > 0x7fff)) h->anc_bw = false;
+  if (h->anc_bw) {
+    std::vector<std::pair<int, int>> lst;  // (entry, index among the block's sums)
+    lst.reserve((size_t)4 * nsr);
+    for (int c = 0; c < 4; ++c)
+      for (long long r = 0; r < nsr; ++r) lst.emplace_back(sr_w[r] + c, (int)(c * nsr + r));
+    std::stable_sort(lst.begin(), lst.end(),
+                     [](const std::pair<int, int>& p, const std::pair<int, int>& q) {
+                       return p.first < q.first;
+                     });
+    const int n = (int)lst.size(), c = (n + 127) / 128;  // a thread's chunk
+    const int E = (c + mm::kRtBatch - 1) / mm::kRtBatch * mm::kRtBatch;
+    const unsigned pad = (unsigned)(4 * nsr);  // the zero after the sums
+    std::vector<unsigned> tab((size_t)E * 128, pad);
+    for (int t = 0; t < 128; ++t)
+      for (int i = 0; i < c; ++i) {
+        const int p = t * c + i;
+        if (p >= n) break;
+        const bool end = i + 1 == c || p + 1 >= n || lst[p + 1].first != lst[p].first;
+        tab[(size_t)i * 128 + t] =
+            (unsigned)lst[p].second | ((unsigned)lst[p].first << 16) | (end ? 1u << 31 : 0u);
+      }
+    CK(cudaMalloc((void**)&h->anc_rtab, tab.size() * sizeof(unsigned)));
+    CK(cudaMemcpy(h->anc_rtab, tab.data(), tab.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
+    h->anc_rt_e = E;
+  }
   // captured substep graphs hold the window and block shape as launch arguments
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);
   h->graphs.clear();

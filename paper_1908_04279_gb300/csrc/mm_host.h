@@ -138,6 +138,9 @@ struct mm_handle {
   int* anc_widx = nullptr;      // [nth][ns] index of each node's anchor in the window
   int* anc_widxb = nullptr;     // [nth][ns] the same in a block's window (4 cells of a row)
   bool anc_bw = false;          // the block's 4 warps share one window
+  unsigned* anc_runend = nullptr;  // [nth][ns / V] run ends and first run of each lane slot
+  unsigned* anc_rtab = nullptr;    // [rt_e][128] the block window's (entry, run) chunks
+  int anc_rt_e = 0, anc_nsr = 0;   // chunk length; slot runs per cell
   int anc_win[4] = {0, 0, 0, 0};  // window: first x and y offset, width, height (0: none)
   double* anc_cacc = nullptr;   // [cells] float64 accumulators of C
   double* anc_fsc = nullptr;    // [cells] scale-down factors

@@ -58,6 +58,7 @@ KERNEL_SRCS = {
     "k_substep_batch": ("mm_batch.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
     "k_adjoint": ("mm_adjoint.cu", "mm_walk.cuh", "mm_internal.cuh"),
     "k_motor_local": ("mm_local.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
+    "k_substep_anchor": ("mm_anchor.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
 }
 
 

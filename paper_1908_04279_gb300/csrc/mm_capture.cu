@@ -260,6 +260,20 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? MM_RC_MIN_BLOCKS : 1)
         if (p < cd.y) Ma[p] = st[p];
       }
     }
+    // each lane's running sums of the new values, restarted at every line
+    // start, into the stage (entry 8 lane + v): a line's sum is then its last
+    // entry's running sum plus the lane-end sums of the lanes it leaves
+    {
+      T r = T(0);
+#pragma unroll
+      for (int v = 0; v < kRcV; ++v) {
+        r = ((mask >> v) & 1u) ? M[v] : r + M[v];
+        M[v] = r;
+      }
+      __syncwarp();  // every lane has read the stage for the stores above
+      sts8(st + 8 * lane, M);
+      __syncwarp();
+    }
     // lanes over the chunk's lines: the line sum of Mb ds, and the line's
     // part of the coarse density
     const int ay = (int)(a / nx), ax = (int)(a - (long long)ay * nx);
@@ -271,15 +285,10 @@ __global__ void __launch_bounds__(128, sizeof(T) == 4 ? MM_RC_MIN_BLOCKS : 1)
       fx += fx < 0 ? nx : (fx >= nx ? -nx : 0);
       fy += fy < 0 ? ny : (fy >= ny ? -ny : 0);
       const T pf = psi_c[((size_t)fy * nx + fx) * nth + ln.z];
-      const int b0 = x.loff[l] - cd.x;
-      T s0 = T(0), s1 = T(0);
-      int q2 = 0;
-      for (; q2 + 1 < ln.w; q2 += 2) {
-        s0 += st[b0 + q2];
-        s1 += st[b0 + q2 + 1];
-      }
-      if (q2 < ln.w) s0 += st[b0 + q2];
-      const T s = (s0 + s1) * ds;
+      const int b0 = x.loff[l] - cd.x, e = b0 + ln.w - 1;
+      T s0 = T(0);
+      for (int q2 = (b0 >> 3) * 8 + 7; q2 < e; q2 += 8) s0 += st[q2];
+      const T s = (s0 + st[e]) * ds;
       La[l] = s;
       cacc = fma_t(pf * s, dth, cacc);
     }

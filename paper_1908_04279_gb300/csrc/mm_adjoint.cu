@@ -198,17 +198,18 @@ __device__ __forceinline__ void psi_adj_cell(const AdjArgs<T>& a, const PsiAdjCo
     const T pc = C.psi(0, k), pe = C.psi(1, k), pw = C.psi(2, k), pn = C.psi(3, k),
             ps = C.psi(4, k);
     const T ck = cosk[k], sk = sink[k];
-    const T Vc = vsp + glide * C.nb(0, k), Ve = vsp + glide * C.nb(1, k);
-    const T Vw = vsp + glide * C.nb(2, k), Vn = vsp + glide * C.nb(3, k);
-    const T Vs = vsp + glide * C.nb(4, k);
+    const T Vc = fma_t(glide, C.nb(0, k), vsp), Ve = fma_t(glide, C.nb(1, k), vsp);
+    const T Vw = fma_t(glide, C.nb(2, k), vsp), Vn = fma_t(glide, C.nb(3, k), vsp);
+    const T Vs = fma_t(glide, C.nb(4, k), vsp);
     const T axc = fma_t(-Vc, ck, uxc), axe = fma_t(-Ve, ck, uxe), axw = fma_t(-Vw, ck, uxw);
     const T ayc = fma_t(-Vc, sk, uyc), ayn = fma_t(-Vn, sk, uyn), ays = fma_t(-Vs, sk, uys);
     const T Ae = T(0.5) * (axc + axe), Aw = T(0.5) * (axw + axc);
     const T An = T(0.5) * (ayc + ayn), As = T(0.5) * (ays + ayc);
     const int kp = k + 1 == nth ? 0 : k + 1, km = k == 0 ? nth - 1 : k - 1;
     const T cp = cosf[k], sp = sinf[k], cm = cosf[km], sm = sinf[km];
-    const T wp = -sp * (Gxx * cp + Gxy * sp) + cp * (Gyx * cp + Gyy * sp);
-    const T wm = -sm * (Gxx * cm + Gxy * sm) + cm * (Gyx * cm + Gyy * sm);
+    // (the forward substep's fused form: the same upwind sides)
+    const T wp = fma_t(-sp, fma_t(Gxx, cp, Gxy * sp), cp * fma_t(Gyx, cp, Gyy * sp));
+    const T wm = fma_t(-sm, fma_t(Gxx, cm, Gxy * sm), cm * fma_t(Gyx, cm, Gyy * sm));
     const T ltc = s_lt[k];
     const T lte = lam_tot(1, k), ltw = lam_tot(2, k), ltn = lam_tot(3, k), lts = lam_tot(4, k);
     // face adjoints lam_F = dt/h (lam_right - lam_left)
@@ -1089,8 +1090,7 @@ cudaError_t adj_motor_occupancy(int V, int ring_rc, int ns, int S, int* bps) {
       ring_rc > 0 ? 4 * adj_ring_warp_bytes(ring_rc, ns, S, (int)sizeof(T)) : 0;
   auto occ = [&](auto plain, auto ring) -> cudaError_t {
     if (ring_rc > 0) {
-      cudaError_t e = cudaFuncSetAttribute(ring, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)rs);
+      cudaError_t e = mm::raise_smem_limit(ring, (int)rs);
       if (e != cudaSuccess) return e;
       return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, ring, 128, rs);
     }
@@ -1110,17 +1110,14 @@ cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid_psi, int grid_mo
   const size_t ring_smem = 4 * psi_ring_warp_bytes(a.nth, (int)sizeof(T));
   if ((a.nth * sizeof(T)) % 16 == 0 && ring_smem <= 200 * 1024) {
     if (ring_smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k_adj_psi_ring<T>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)ring_smem);
+      cudaError_t e = mm::raise_smem_limit(k_adj_psi_ring<T>, (int)ring_smem);
       if (e != cudaSuccess) return e;
     }
     k_adj_psi_ring<T><<<grid_psi, block, ring_smem, s>>>(a);
   } else {
     const size_t smem = (size_t)4 * a.nth * sizeof(T);
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(k_adj_psi<T>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaError_t e = mm::raise_smem_limit(k_adj_psi<T>, (int)smem);
       if (e != cudaSuccess) return e;
     }
     k_adj_psi<T><<<grid_psi, block, smem, s>>>(a);
@@ -1132,7 +1129,7 @@ cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid_psi, int grid_mo
       const size_t rs = 4 * adj_ring_warp_bytes(a.ring_rc, a.ns, a.ring_s, (int)sizeof(T));
       if (rs > 48 * 1024) {
         cudaError_t e2 =
-            cudaFuncSetAttribute(ring, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rs);
+            mm::raise_smem_limit(ring, (int)rs);
         if (e2 != cudaSuccess) return e2;
       }
       ring<<<grid_motor, block, rs, s>>>(a, a.ring_rc, a.ring_ch, a.ring_s);

@@ -650,7 +650,7 @@ cudaError_t anchor_prepare_t(mm_handle* h) {
                         (const void*)mm::k_substep_anchor<T, V, true, false>,
                         (const void*)mm::k_substep_anchor<T, V, false, false>};
   for (const void* f : fns) {
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = mm::raise_smem_limit(f, smem);
     if (e != cudaSuccess) return e;
   }
   if (h->anc_bw) {
@@ -662,7 +662,7 @@ cudaError_t anchor_prepare_t(mm_handle* h) {
                              (const void*)mm::k_substep_anchor<T, V, false, true, true>};
       for (const void* f : bfns) {
         cudaError_t e =
-            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bsm);
+            mm::raise_smem_limit(f, (int)bsm);
         if (e != cudaSuccess) return e;
       }
     }

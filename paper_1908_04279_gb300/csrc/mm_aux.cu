@@ -648,8 +648,7 @@ cudaError_t launch_moments(const T* psi, const T* mb, const T* mf, const T* c,
   const size_t smem = (size_t)4 * 2 * nth * sizeof(double) + (size_t)4 * nth * 16;
   auto go = [&](auto kern) -> cudaError_t {
     if (smem > 48 * 1024) {
-      cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem);
+      cudaError_t e = mm::raise_smem_limit(kern, (int)smem);
       if (e != cudaSuccess) return e;
     }
     kern<<<nblocks, block, smem, s>>>(psi, mb, mf, c, trig, ncells, nth, ns, seg, dth, ds, L, dA,

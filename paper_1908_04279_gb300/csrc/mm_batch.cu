@@ -28,6 +28,70 @@ constexpr int batch_min_blocks() {
   return sizeof(T) == 8 ? 3 : MM_BATCH_MIN_BLOCKS;
 }
 
+// The psi and n_b columns of two cells of one row (x0 and x0 + 1, y0; nx is
+// even and x0 is even, so both lie in the row) and of the four neighbours of
+// each into psi5 / nb5 ([2][5][nth], the layout of stage_neighbourhood per
+// cell), completing on `nbar`: lane 0 posts the expected bytes, then lanes
+// 0-19 each issue one of the 20 bulk copies.
+template <typename T>
+__device__ __forceinline__ void stage_pair_neighbourhood(uint64_t* nbar, T* psi5, T* nb5,
+                                                         const T* psi_in, const T* nb_in, int x0,
+                                                         int y0, int nx, int ny, int nth,
+                                                         int lane) {
+  const uint32_t pb = (uint32_t)(nth * sizeof(T));
+  if (lane == 0) mbar_expect_tx(nbar, 20 * pb);
+  __syncwarp();
+  if (lane < 20) {
+    const int h = lane >= 10 ? 1 : 0, q = (lane - 10 * h) >> 1;
+    const int x = x0 + h;
+    const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+    const int yp = y0 + 1 == ny ? 0 : y0 + 1, ym = y0 == 0 ? ny - 1 : y0 - 1;
+    const int cq = q == 0   ? y0 * nx + x
+                   : q == 1 ? y0 * nx + xp
+                   : q == 2 ? y0 * nx + xm
+                   : q == 3 ? yp * nx + x
+                            : ym * nx + x;
+    const size_t d = (size_t)(5 * h + q) * nth;
+    if (lane & 1)
+      bulk_g2s(nb5 + d, nb_in + (size_t)cq * nth, pb, nbar);
+    else
+      bulk_g2s(psi5 + d, psi_in + (size_t)cq * nth, pb, nbar);
+  }
+}
+
+// cell_motor_close for the two cells of a unit, one per half-warp (lane
+// 16 h + k holds orientation k of cell h): the same sums in the same order
+// (a cell's orientations sit in lanes 0-15 of its half, as in lanes 0-15 of a
+// warp of its own), the same scale-down and writes.
+template <typename T>
+__device__ __forceinline__ void pair_motor_close(T acc, T mtot, const T* s_nb, int nth, int ns,
+                                                 int lane, int cell, T* mb_out, T* nb_out, T* c,
+                                                 T* mf_out, T* cpre_out) {
+  T Cpre = acc;
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) Cpre += __shfl_xor_sync(0xffffffffu, Cpre, o);
+  T f = T(1), C = Cpre;
+  if (mtot < Cpre) {
+    f = mtot / Cpre;
+    C = mtot;
+  }
+  const int hl = lane & 15;
+  const size_t cbase = (size_t)cell * nth;
+  if (f != T(1)) {
+    const T ft = f;
+    T* base = mb_out + cbase * ns;
+    for (int e = hl; e < nth * ns; e += 16) base[e] = __ldcg(base + e) * ft;
+    for (int k = hl; k < nth; k += 16) nb_out[cbase + k] = s_nb[k] * ft;
+  } else {
+    for (int k = hl; k < nth; k += 16) nb_out[cbase + k] = s_nb[k];
+  }
+  if (hl == 0) {
+    c[cell] = C;
+    mf_out[cell] = mtot - C;
+    if (cpre_out) cpre_out[cell] = Cpre;
+  }
+}
+
 template <typename T, int V, bool MASSCORR>
 __global__ void __launch_bounds__(128, batch_min_blocks<T>())
     k_substep_batch(const StepArgs<T>* __restrict__ insts, const BatchTile* __restrict__ tiles,
@@ -64,7 +128,7 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
     const uint32_t bytes = (uint32_t)(pt.rc * pns * sizeof(T));
     mbar_expect_tx(&bars[istage], bytes);
     bulk_g2s(stages + (size_t)istage * stage_elems,
-             pmb + ((size_t)(pt.cell0 + pcell) * pnth + (size_t)ppart * pt.rc) * pns, bytes,
+             pmb + ((size_t)(pt.cell0 + pcell * pt.cpu) * pnth + (size_t)ppart * pt.rc) * pns, bytes,
              &bars[istage]);
     ++issued;
     if (++ppart == pt.ch) {
@@ -97,7 +161,7 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
   BatchTile ct{};
   ct.ncell = 0;
   const StepArgs<T>* A = nullptr;
-  int nth = 1, ns = 1, seg = 1, nx = 1, ny = 1, RC = 1, CH = 1;
+  int nth = 1, ns = 1, seg = 1, nx = 1, ny = 1;
   bool nb_tma = false;
   uint32_t wait_limit = 0;
   bool wait_never = false;
@@ -106,7 +170,18 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
   RkConst<T> rk{};
   LaneGeom lg{};
   T mass_hi = T(0), mass_lo = T(0);
-  int cell = 0, ce = 0, cwc = 0, cn = 0, cs = 0, ix = 0, iy = 0;
+  int cell = 0, ix = 0, iy = 0;
+  // the cell at (ix, iy) and its east, west, north and south neighbours
+  // (recomputed where needed rather than kept across the rows)
+  auto nbrs = [&](int (&c)[5]) {
+    const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
+    const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
+    c[0] = iy * nx + ix;
+    c[1] = iy * nx + xp;
+    c[2] = iy * nx + xm;
+    c[3] = yp * nx + ix;
+    c[4] = ym * nx + ix;
+  };
   T mtot = 0;
   CellVel<T> uv{};
   // the next cell's free and total motors, loaded while the current cell is
@@ -150,8 +225,6 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
         seg = A->seg;
         nx = A->nx;
         ny = A->ny;
-        RC = ct.rc;
-        CH = ct.ch;
         nb_tma = A->nb_tma != 0;
         const DevParams* P = A->prm;
         const StepScalars<T> sc = step_scalars<T, MASSCORR>(P, *A, lane);
@@ -163,45 +236,54 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
         pq = PsiConst<T>{dt, sc.g, sc.glide, sc.vsp, sc.inv_dx, sc.inv_dy, sc.inv_dth, sc.dth,
                          A->trig};
         ds = sc.ds;
-        rk = RkConst<T>{hdt * sc.cw, T(1) - hdt * sc.koff, T(0), dt * sc.cw, -dt * sc.koff, T(0)};
+        rk = RkConst<T>{hdt * sc.cw, T(1) - hdt * sc.koff, T(0), dt * sc.cw, -dt * sc.koff, T(0),
+                        T(0), T(0), nth};
         lg = lane_geom(lane, seg, ns, V);
         iy = ct.cell0 / nx;
         ix = ct.cell0 - iy * nx;
-      } else if (++ix == nx) {  // consecutive cells of the tile
-        ix = 0;
+      } else if ((ix += ct.cpu) >= nx) {  // consecutive units of the tile
+        ix -= nx;
         ++iy;
       }
-      cell = ct.cell0 + ccell;
+      // the unit's first cell; Mf of the first cell and the total motors of
+      // the half-warp's cell
+      cell = ct.cell0 + ccell * ct.cpu;
+      const int half = (ct.cpu >> 1) & (lane >> 4);  // the half-warp's cell in a unit of 2
       T mf_n;
       if (have_next && ccell > 0) {
         mf_n = mf_next;
         mtot = mtot_next;
       } else {
         mf_n = A->mf_in[cell];
-        mtot = A->mtot[cell];
+        mtot = A->mtot[cell + half];
       }
       have_next = ccell + 1 < ct.ncell;
-      if (have_next) {  // Mf of the next cell is written only when that cell is done
-        mf_next = A->mf_in[cell + 1];
-        mtot_next = A->mtot[cell + 1];
+      if (have_next) {  // Mf of the next unit is written only when that unit is done
+        mf_next = A->mf_in[cell + ct.cpu];
+        mtot_next = A->mtot[cell + ct.cpu + half];
       }
       if (nb_tma) nb_par ^= 1u;  // members differ in whether they stage by bulk copy
-      const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
-      const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
-      ce = iy * nx + xp;
-      cwc = iy * nx + xm;
-      cn = yp * nx + ix;
-      cs = ym * nx + ix;
       rk.c3 = hdt * kon * mf_n;
       rk.e3 = dt * kon * mf_n;
-      uv = load_cell_vel(A->ucell, cell);
-      if (nb_tma)
-        stage_neighbourhood(nbar, psi5, nb5, A->psi_in, A->nb_in, cell, ce, cwc, cn, cs, nth,
-                            lane);
+      {  // a unit of 2: the second cell's rows (from row nth on) bind to its own Mf
+         // (a unit of 1 has no row nth in a chunk, and its c3b, e3b are c3, e3)
+        const T mf2 = ct.cpu == 2 ? A->mf_in[cell + 1] : mf_n;
+        rk.c3b = hdt * kon * mf2;
+        rk.e3b = dt * kon * mf2;
+      }
+      uv = load_cell_vel(A->ucell, cell + half);
+      if (nb_tma && ct.cpu == 2)
+        stage_pair_neighbourhood(nbar, psi5, nb5, A->psi_in, A->nb_in, ix, iy, nx, ny, nth, lane);
+      else if (nb_tma) {
+        int c[5];
+        nbrs(c);
+        stage_neighbourhood(nbar, psi5, nb5, A->psi_in, A->nb_in, c[0], c[1], c[2], c[3], c[4],
+                            nth, lane);
+      }
     }
 
     // ---- motor rows of this chunk
-    const size_t chunk_off = ((size_t)cell * nth + (size_t)part * RC) * ns;
+    const size_t chunk_off = ((size_t)cell * nth + (size_t)part * ct.rc) * ns;
     {
       const bool ok = __all_sync(0xffffffffu, wait_never ? mbar_wait(never, 0u, wait_limit)
                                                          : mbar_wait(&bars[s], par, wait_limit));
@@ -214,12 +296,12 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
         break;
       }
     }
-    rows_chunk<T, V>(stages + (size_t)s * stage_elems, A->mb_out + chunk_off, RC, ns, seg, lg, rk,
-                     ds, s_nb + part * RC);
+    rows_chunk<T, V, true>(stages + (size_t)s * stage_elems, A->mb_out + chunk_off, ct.rc, ns, seg,
+                           lg, rk, ds, s_nb + part * ct.rc);
     __syncwarp();
     if (lane == 0 && issued < nchunks) issue_next();
     if (++s == S) { s = 0; par ^= 1u; }
-    if (++part != CH) continue;
+    if (++part != ct.ch) continue;
     part = 0;
 
     // ---- end of the cell
@@ -235,7 +317,8 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
         break;
       }
     } else {
-      const int src_cells[5] = {cell, ce, cwc, cn, cs};
+      int src_cells[5];
+      nbrs(src_cells);
       for (int q = 0; q < 5; ++q)
         for (int k = lane; k < nth; k += 32) {
           psi5[q * nth + k] = A->psi_in[(size_t)src_cells[q] * nth + k];
@@ -244,10 +327,18 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
       __syncwarp();
     }
     T acc = T(0), cell_mass = T(0);
-    psi_cell(pq, uv, psi5, nb5, s_nb, nth, lane, A->psi_out + (size_t)cell * nth, cell_mass, acc);
+    // (in a unit of 2, half-warp h takes cell h with lane 16 h + k on orientation k)
+    const int half = (ct.cpu >> 1) & (lane >> 4);
+    const size_t h5 = (size_t)half * 5 * nth;
+    psi_cell(pq, uv, psi5 + h5, nb5 + h5, s_nb + half * nth, nth, ct.cpu == 2 ? lane & 15 : lane,
+             A->psi_out + (size_t)(cell + half) * nth, cell_mass, acc);
     two_sum_acc(mass_hi, mass_lo, cell_mass);
-    cell_motor_close(acc, mtot, s_nb, nth, ns, lane, cell, A->mb_out, A->nb_out, A->c, A->mf_out,
-                     A->cpre_out);
+    if (ct.cpu == 2)
+      pair_motor_close(acc, mtot, s_nb + half * nth, nth, ns, lane, cell + half, A->mb_out,
+                       A->nb_out, A->c, A->mf_out, A->cpre_out);
+    else
+      cell_motor_close(acc, mtot, s_nb, nth, ns, lane, cell, A->mb_out, A->nb_out, A->c,
+                       A->mf_out, A->cpre_out);
     __syncwarp();
     if (++ccell == ct.ncell) close_tile();
   }
@@ -285,7 +376,7 @@ cudaError_t substep_batch_prepare(int block, size_t smem, int* blocks_per_sm) {
   const void* fns[2] = {(const void*)k_substep_batch<T, V, true>,
                         (const void*)k_substep_batch<T, V, false>};
   for (const void* f : fns) {
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = mm::raise_smem_limit(f, (int)smem);
     if (e != cudaSuccess) return e;
   }
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_substep_batch<T, V, true>,

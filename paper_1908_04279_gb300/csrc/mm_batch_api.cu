@@ -67,6 +67,18 @@ void member_chunks(const mm_handle* m, int chunk_bytes, int* rc, int* ch) {
   *rc = nth / c;
 }
 
+// Whether a member's cells go two to a warp: at most 16 orientations (one
+// half-warp per cell for psi and the close), the rows of a cell a whole number
+// of row passes (32 / seg rows each), an even row length (the two cells of a
+// unit share a row) and neighbourhood columns that bulk copies can stage.
+bool member_pairs(const mm_handle* m, int V) {
+  int seg = 1;
+  while (seg < m->g.ns / V) seg <<= 1;
+  const int nth = m->g.ntheta;
+  return nth <= 16 && nth % (32 / seg) == 0 && m->g.nx % 2 == 0 &&
+         ((size_t)nth * m->tsz) % 16 == 0;
+}
+
 template <typename T>
 cudaError_t prepare(int V, int block, size_t smem, int* bps) {
   if constexpr (sizeof(T) == 8) {
@@ -86,25 +98,34 @@ mm_status make_plan(mm_handle* h, int tile_work, int chunk_bytes) {
   int max_chunk_elems = 1, nth_max = 1;
   for (int i = 0; i < n; ++i) {
     const mm_handle* m = B->members[i];
+    // units of 1 cell (rows in ch chunks of rc) or of 2 cells (one chunk of
+    // both cells' rows); tiles of about tile_work motor values, whole units
+    const int cpu = member_pairs(m, B->V) ? 2 : 1;
     int rc, ch;
-    member_chunks(m, chunk_bytes, &rc, &ch);
+    if (cpu == 2) {
+      rc = 2 * m->g.ntheta;
+      ch = 1;
+    } else {
+      member_chunks(m, chunk_bytes, &rc, &ch);
+    }
     max_chunk_elems = std::max(max_chunk_elems, rc * m->g.ns);
-    nth_max = std::max(nth_max, m->g.ntheta);
-    const long long nc = m->ncells;
-    const long long per_cell = (long long)m->g.ntheta * m->g.ns;
-    long long tc = std::max(1LL, (long long)tile_work / per_cell);
-    tc = std::min(tc, nc);
-    const int nt = (int)((nc + tc - 1) / tc);
+    nth_max = std::max(nth_max, cpu * m->g.ntheta);  // a pair stages two neighbourhoods
+    const long long nu = m->ncells / cpu;             // nx even for pairs: ncells is too
+    const long long per_unit = (long long)cpu * m->g.ntheta * m->g.ns;
+    long long tu = std::max(1LL, (long long)tile_work / per_unit);
+    tu = std::min(tu, nu);
+    const int nt = (int)((nu + tu - 1) / tu);
     const int tile0 = (int)tiles.size();
     for (int t = 0; t < nt; ++t) {
       mm::BatchTile bt{};
       bt.inst = i;
-      bt.cell0 = (int)(t * tc);
-      bt.ncell = (int)std::min(tc, nc - t * tc);
+      bt.cell0 = (int)(t * tu * cpu);
+      bt.ncell = (int)std::min(tu, nu - t * tu);
       bt.tile0 = tile0;
       bt.inst_tiles = nt;
       bt.ch = ch;
       bt.rc = rc;
+      bt.cpu = cpu;
       tiles.push_back(bt);
     }
   }

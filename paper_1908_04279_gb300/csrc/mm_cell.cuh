@@ -203,14 +203,18 @@ __device__ __forceinline__ LaneGeom lane_geom(int lane, int seg, int ns, int V) 
 // RK2 constants of one cell: Eq. 4's right-hand side is
 // R = (v/ds) D - k_off M + k_on Mf; the half step is
 // Ms = c1 D(M) + c2 M + c3 and the full step M' = e1 D(Ms) + e2 Ms + M + e3.
+// With SPLIT (rows_chunk), rows from rsplit on take c3b and e3b instead: the
+// rows of a second cell, with its own Mf, in the same chunk.
 template <typename T>
 struct RkConst {
   T c1, c2, c3, e1, e2, e3;
+  T c3b, e3b;
+  int rsplit;
 };
 
 // Float32 rows with V = 4 or 8 nodes per lane as register pairs: the stage
 // updates and the n_b sum as packed two-value instructions (walk_dflux_x2).
-template <int V>
+template <int V, bool SPLIT = false>
 __device__ __forceinline__ void rows_chunk_x2(const float* src_rows, float* dst, int RC, int ns,
                                               int seg, const LaneGeom& lg,
                                               const RkConst<float>& k, float ds,
@@ -218,11 +222,13 @@ __device__ __forceinline__ void rows_chunk_x2(const float* src_rows, float* dst,
   constexpr int H = V / 2;
   const int passes = (RC + lg.rpp - 1) / lg.rpp;
   const float2 c1 = make_float2(k.c1, k.c1), c2 = make_float2(k.c2, k.c2);
-  const float2 c3 = make_float2(k.c3, k.c3), e1 = make_float2(k.e1, k.e1);
-  const float2 e2 = make_float2(k.e2, k.e2), e3 = make_float2(k.e3, k.e3);
+  const float2 e1 = make_float2(k.e1, k.e1), e2 = make_float2(k.e2, k.e2);
 #pragma unroll kStepUnroll
   for (int p = 0; p < passes; ++p) {
     const int r = p * lg.rpp + lg.rslot;  // row within the chunk
+    const bool hi = SPLIT && r >= k.rsplit;
+    const float c3s = hi ? k.c3b : k.c3, e3s = hi ? k.e3b : k.e3;
+    const float2 c3 = make_float2(c3s, c3s), e3 = make_float2(e3s, e3s);
     const bool row_ok = r < RC;
     const bool act = row_ok && lg.lane_ok;
     const int off = (row_ok ? r : 0) * ns + lg.sl * V;
@@ -264,18 +270,20 @@ __device__ __forceinline__ void rows_chunk_x2(const float* src_rows, float* dst,
 // One chunk of RC s-rows (src_rows: the rows at step n, in shared or global
 // memory; dst: global rows at step n+1, in place allowed), with n_b of each
 // new row written to s_nb_chunk[r].
-template <typename T, int V>
+template <typename T, int V, bool SPLIT = false>
 __device__ __forceinline__ void rows_chunk(const T* src_rows, T* dst, int RC, int ns, int seg,
                                            const LaneGeom& lg, const RkConst<T>& k, T ds,
                                            T* s_nb_chunk) {
   if constexpr (sizeof(T) == 4 && (V == 4 || V == 8)) {
-    rows_chunk_x2<V>(src_rows, dst, RC, ns, seg, lg, k, ds, s_nb_chunk);
+    rows_chunk_x2<V, SPLIT>(src_rows, dst, RC, ns, seg, lg, k, ds, s_nb_chunk);
     return;
   }
   const int passes = (RC + lg.rpp - 1) / lg.rpp;
 #pragma unroll kStepUnroll
   for (int p = 0; p < passes; ++p) {
     const int r = p * lg.rpp + lg.rslot;  // row within the chunk
+    const bool hi = SPLIT && r >= k.rsplit;
+    const T c3 = hi ? k.c3b : k.c3, e3 = hi ? k.e3b : k.e3;
     const bool row_ok = r < RC;
     const bool act = row_ok && lg.lane_ok;
     const int off = (row_ok ? r : 0) * ns + lg.sl * V;
@@ -291,12 +299,12 @@ __device__ __forceinline__ void rows_chunk(const T* src_rows, T* dst, int RC, in
     // midpoint RK2 with the constants folded
     walk_dflux<T, V>(M, D, lg.first, lg.last, seg);
 #pragma unroll
-    for (int v = 0; v < V; ++v) Ms[v] = fma_t(k.c1, D[v], fma_t(k.c2, M[v], k.c3));
+    for (int v = 0; v < V; ++v) Ms[v] = fma_t(k.c1, D[v], fma_t(k.c2, M[v], c3));
     walk_dflux<T, V>(Ms, D, lg.first, lg.last, seg);
     T snb = T(0);
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      M[v] = fma_t(k.e1, D[v], fma_t(k.e2, Ms[v], M[v] + k.e3));
+      M[v] = fma_t(k.e1, D[v], fma_t(k.e2, Ms[v], add_rn(M[v], e3)));
       snb += M[v];
     }
     if (!act) snb = T(0);
@@ -397,9 +405,12 @@ __device__ __forceinline__ void psi_cell(const PsiConst<T>& q, const CellVel<T>&
     const T Pc = g * psi5[k], Pe = g * psi5[nth + k], Pw = g * psi5[2 * nth + k];
     const T Pn = g * psi5[3 * nth + k], Ps = g * psi5[4 * nth + k];
     const T ck = cached ? lt->ck : cosk[k], sk = cached ? lt->sk : sink[k];
-    const T Vc = q.vsp + q.glide * nb5[k], Ve = q.vsp + q.glide * nb5[nth + k];
-    const T Vw = q.vsp + q.glide * nb5[2 * nth + k], Vn = q.vsp + q.glide * nb5[3 * nth + k];
-    const T Vs = q.vsp + q.glide * nb5[4 * nth + k];
+    // (every sum of products below is written as explicit fused operations,
+    // so that each kernel inlining this function rounds it the same way)
+    const T Vc = fma_t(q.glide, nb5[k], q.vsp), Ve = fma_t(q.glide, nb5[nth + k], q.vsp);
+    const T Vw = fma_t(q.glide, nb5[2 * nth + k], q.vsp);
+    const T Vn = fma_t(q.glide, nb5[3 * nth + k], q.vsp);
+    const T Vs = fma_t(q.glide, nb5[4 * nth + k], q.vsp);
     const T axc = fma_t(-Vc, ck, u.uxc), axe = fma_t(-Ve, ck, u.uxe), axw = fma_t(-Vw, ck, u.uxw);
     const T ayc = fma_t(-Vc, sk, u.uyc), ayn = fma_t(-Vn, sk, u.uyn), ays = fma_t(-Vs, sk, u.uys);
     const T Ae = T(0.5) * (axc + axe), Aw = T(0.5) * (axw + axc);
@@ -408,13 +419,14 @@ __device__ __forceinline__ void psi_cell(const PsiConst<T>& q, const CellVel<T>&
     const T cp = cached ? lt->cp : cosf[k], sp = cached ? lt->sp : sinf[k];
     const T cm = cached ? lt->cm : cosf[km], sm = cached ? lt->sm : sinf[km];
     // Jeffery rotation p_perp . G . p at the faces k +- 1/2
-    const T wp = -sp * (u.Gxx * cp + u.Gxy * sp) + cp * (u.Gyx * cp + u.Gyy * sp);
-    const T wm = -sm * (u.Gxx * cm + u.Gxy * sm) + cm * (u.Gyx * cm + u.Gyy * sm);
+    const T wp = fma_t(-sp, fma_t(u.Gxx, cp, u.Gxy * sp), cp * fma_t(u.Gyx, cp, u.Gyy * sp));
+    const T wm = fma_t(-sm, fma_t(u.Gxx, cm, u.Gxy * sm), cm * fma_t(u.Gyx, cm, u.Gyy * sm));
     const T Fe = donor(Ae, Pc, Pe), Fw = donor(Aw, Pw, Pc);
     const T Fn = donor(An, Pc, Pn), Fs = donor(As, Ps, Pc);
     const T Fp = donor(wp, Pc, g * psi5[kp]), Fm = donor(wm, g * psi5[km], Pc);
-    const T pnew =
-        Pc - q.dt * ((Fe - Fw) * q.inv_dx + (Fn - Fs) * q.inv_dy + (Fp - Fm) * q.inv_dth);
+    const T div =
+        fma_t(Fp - Fm, q.inv_dth, fma_t(Fn - Fs, q.inv_dy, (Fe - Fw) * q.inv_dx));
+    const T pnew = fma_t(-q.dt, div, Pc);
     psi_out_cell[k] = pnew;
     cell_mass += pnew;
     acc = fma_t(pnew * s_nb[k], q.dth, acc);

@@ -4,9 +4,26 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "mm.h"
 
 namespace mm {
+
+// Raises a kernel's dynamic shared-memory limit to at least `bytes`. The limit
+// belongs to the kernel function, shared by every handle of the process: a
+// handle that needs less must not lower it under another handle's launches.
+inline cudaError_t raise_smem_limit(const void* f, size_t bytes) {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, f);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
+  return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+template <typename F, typename = std::enable_if_t<std::is_function<F>::value>>
+inline cudaError_t raise_smem_limit(F* f, size_t bytes) {
+  return raise_smem_limit(reinterpret_cast<const void*>(f), bytes);
+}
 
 // Device-resident per-handle scalars. Kernels read dt and the rates from here
 // (not from launch arguments) so that captured graphs stay valid when dt or
@@ -112,11 +129,12 @@ struct AdjArgs {
 struct BatchTile {
   int inst;        // instance (index into the StepArgs table)
   int cell0;       // first cell
-  int ncell;       // cells in the tile
+  int ncell;       // units (of cpu cells) in the tile
   int tile0;       // index of the instance's first tile
   int inst_tiles;  // tiles of the instance
-  int ch, rc;      // chunks per cell, s-rows per chunk
-  int pad;
+  int ch, rc;      // chunks per unit, s-rows per chunk
+  int cpu;         // cells per unit: 1, or 2 (two cells of one row: one chunk holds both
+                   // cells' rows; a half-warp each takes psi and the close)
 };
 
 // Kernel launchers (defined in mm_step.cu); V = values per lane.

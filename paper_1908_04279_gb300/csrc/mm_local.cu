@@ -238,8 +238,7 @@ __global__ void __launch_bounds__(256, 2) k_motor_local(const LocalArgs<T> a) {
 
 template <typename T, int V>
 cudaError_t local_prepare(int block, size_t smem, int* bps) {
-  cudaError_t e = cudaFuncSetAttribute(k_motor_local<T, V>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = mm::raise_smem_limit(k_motor_local<T, V>, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_motor_local<T, V>, block, smem);
 }

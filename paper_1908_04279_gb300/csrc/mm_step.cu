@@ -302,7 +302,7 @@ cudaError_t substep_prepare(int block, size_t smem, bool tma, int* blocks_per_sm
                         (const void*)k_substep<T, V, false, true>,
                         (const void*)k_substep<T, V, false, false>};
   for (const void* f : fns) {
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = mm::raise_smem_limit(f, (int)smem);
     if (e != cudaSuccess) return e;
   }
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(

@@ -65,9 +65,10 @@ __device__ __forceinline__ void psi_cell_tl(const PsiConst<T>& q, const CellVel<
     const T dPc = g * dpsi5[k], dPe = g * dpsi5[nth + k], dPw = g * dpsi5[2 * nth + k];
     const T dPn = g * dpsi5[3 * nth + k], dPs = g * dpsi5[4 * nth + k];
     const T ck = cosk[k], sk = sink[k];
-    const T Vc = q.vsp + q.glide * nb5[k], Ve = q.vsp + q.glide * nb5[nth + k];
-    const T Vw = q.vsp + q.glide * nb5[2 * nth + k], Vn = q.vsp + q.glide * nb5[3 * nth + k];
-    const T Vs = q.vsp + q.glide * nb5[4 * nth + k];
+    const T Vc = fma_t(q.glide, nb5[k], q.vsp), Ve = fma_t(q.glide, nb5[nth + k], q.vsp);
+    const T Vw = fma_t(q.glide, nb5[2 * nth + k], q.vsp);
+    const T Vn = fma_t(q.glide, nb5[3 * nth + k], q.vsp);
+    const T Vs = fma_t(q.glide, nb5[4 * nth + k], q.vsp);
     const T axc = fma_t(-Vc, ck, u.uxc), axe = fma_t(-Ve, ck, u.uxe), axw = fma_t(-Vw, ck, u.uxw);
     const T ayc = fma_t(-Vc, sk, u.uyc), ayn = fma_t(-Vn, sk, u.uyn), ays = fma_t(-Vs, sk, u.uys);
     const T Ae = T(0.5) * (axc + axe), Aw = T(0.5) * (axw + axc);
@@ -80,8 +81,9 @@ __device__ __forceinline__ void psi_cell_tl(const PsiConst<T>& q, const CellVel<
     const T dAn = T(0.5) * (dayc + dayn), dAs = T(0.5) * (days + dayc);
     const int kp = k + 1 == nth ? 0 : k + 1, km = k == 0 ? nth - 1 : k - 1;
     const T cp = cosf[k], sp = sinf[k], cm = cosf[km], sm = sinf[km];
-    const T wp = -sp * (u.Gxx * cp + u.Gxy * sp) + cp * (u.Gyx * cp + u.Gyy * sp);
-    const T wm = -sm * (u.Gxx * cm + u.Gxy * sm) + cm * (u.Gyx * cm + u.Gyy * sm);
+    // (the forward substep's fused form: the same upwind sides)
+    const T wp = fma_t(-sp, fma_t(u.Gxx, cp, u.Gxy * sp), cp * fma_t(u.Gyx, cp, u.Gyy * sp));
+    const T wm = fma_t(-sm, fma_t(u.Gxx, cm, u.Gxy * sm), cm * fma_t(u.Gyx, cm, u.Gyy * sm));
     const T dFe = donor_tl(Ae, Pc, Pe, dAe, dPc, dPe), dFw = donor_tl(Aw, Pw, Pc, dAw, dPw, dPc);
     const T dFn = donor_tl(An, Pc, Pn, dAn, dPc, dPn), dFs = donor_tl(As, Ps, Pc, dAs, dPs, dPc);
     const T dFp = donor_tl(wp, Pc, g * psi5[kp], T(0), dPc, g * dpsi5[kp]);
@@ -395,7 +397,7 @@ cudaError_t tan_prepare_t(mm_handle* h, int* per_sm) {
   const void* fns[2] = {(const void*)mm::k_substep_tl<T, V, true>,
                         (const void*)mm::k_substep_tl<T, V, false>};
   for (const void* f : fns) {
-    cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = mm::raise_smem_limit(f, (int)smem);
     if (e != cudaSuccess) return e;
   }
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, mm::k_substep_tl<T, V, true>, 128,

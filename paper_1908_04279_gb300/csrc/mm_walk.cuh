@@ -20,6 +20,10 @@ __device__ __forceinline__ double tmin(double a, double b) { return fmin(a, b); 
 
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return __fmaf_rn(a, b, c); }
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return __fma_rn(a, b, c); }
+// An addition the compiler may not fuse with a product feeding it (the same
+// bits wherever the addend's product is computed).
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
 
 // Donor-cell face flux: upwind state times face velocity, with an explicit fma
 // so that both cells sharing a face compute the same bits (exact telescoping).

@@ -9,6 +9,8 @@ with uneven grids, rates and dt.
   warp);
 * graph and direct launches, members stepped alone in between (their
   parities diverge), odd and even substep counts;
+* members with at most 16 orientations and an even row length go two cells
+  to a warp (8 and 16 orientations), one with an odd row length one;
 * the autotuner leaves the state as it found it;
 * a member recording an adjoint during batched substeps gives the adjoint of
   the same member recorded alone;
@@ -22,9 +24,12 @@ from paper_1908_04279_gb300.inputs import (Grid, Member, Rates, ensemble_members
 
 pytestmark = pytest.mark.gpu
 
-# uneven members: grids, angle and arclength counts, rates
+# uneven members: grids, angle and arclength counts, rates; members 0, 1, 3
+# and 6 go two cells to a warp (at most 16 orientations, even nx), member 5
+# (odd nx) one
 SHAPES = [((8, 8, 16, 16), 0.3, 1.0), ((12, 10, 16, 32), 2.0, 0.6), ((6, 7, 32, 16), 0.07, 1.7),
-          ((16, 16, 16, 16), 0.5, 1.0), ((9, 5, 32, 32), 4.0, 1.2)]
+          ((16, 16, 16, 16), 0.5, 1.0), ((9, 5, 32, 32), 4.0, 1.2), ((7, 6, 16, 16), 1.1, 0.8),
+          ((10, 6, 8, 32), 0.9, 1.4)]
 
 
 @pytest.fixture(scope="module")

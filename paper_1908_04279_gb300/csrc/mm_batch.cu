@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
   CellVel<T> uv{};
   // the next cell's free and total motors, loaded while the current cell is
   // computed (the RK2 constants need them as soon as a cell starts)
-  T mf_next = 0, mtot_next = 0;
+  T mf_next = 0;
   bool have_next = false;
 
   // sum of the finished tile; the last tile of an instance finalises it
@@ -249,19 +249,12 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
       // the half-warp's cell
       cell = ct.cell0 + ccell * ct.cpu;
       const int half = (ct.cpu >> 1) & (lane >> 4);  // the half-warp's cell in a unit of 2
-      T mf_n;
-      if (have_next && ccell > 0) {
-        mf_n = mf_next;
-        mtot = mtot_next;
-      } else {
-        mf_n = A->mf_in[cell];
-        mtot = A->mtot[cell + half];
-      }
+      // (the total motors are needed at the unit's end only)
+      const T mf_n = have_next && ccell > 0 ? mf_next : A->mf_in[cell];
+      mtot = A->mtot[cell + half];
       have_next = ccell + 1 < ct.ncell;
-      if (have_next) {  // Mf of the next unit is written only when that unit is done
-        mf_next = A->mf_in[cell + ct.cpu];
-        mtot_next = A->mtot[cell + ct.cpu + half];
-      }
+      // Mf of the next unit is written only when that unit is done
+      if (have_next) mf_next = A->mf_in[cell + ct.cpu];
       if (nb_tma) nb_par ^= 1u;  // members differ in whether they stage by bulk copy
       rk.c3 = hdt * kon * mf_n;
       rk.e3 = dt * kon * mf_n;

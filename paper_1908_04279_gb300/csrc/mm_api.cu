@@ -918,13 +918,18 @@ size_t vblock_bytes(const mm_handle* h) {
 mm_status rec_save_checkpoint(mm_handle* h, int i) {
   Recording& R = h->rec;
   const size_t t = h->tsz, nc = (size_t)h->ncells;
-  CK(cudaMemcpyAsync(R.ck_mb[i], h->mb, h->mbn * t, cudaMemcpyDeviceToDevice, h->stream));
-  CK(cudaMemcpyAsync(R.ck_psi[i], h->psi[h->parity], h->rows * t, cudaMemcpyDeviceToDevice,
-                     h->stream));
-  CK(cudaMemcpyAsync(R.ck_nb[i], h->nb[h->parity], h->rows * t, cudaMemcpyDeviceToDevice,
-                     h->stream));
-  CK(cudaMemcpyAsync(R.ck_mf[i], h->mf, nc * t, cudaMemcpyDeviceToDevice, h->stream));
-  CK(cudaMemcpyAsync(R.ck_scale + i, &h->prm->psi_scale, 8, cudaMemcpyDeviceToDevice, h->stream));
+  // one launch for the five arrays
+  mm::CopySegs c{};
+  c.n = 5;
+  const void* src[5] = {h->mb, h->psi[h->parity], h->nb[h->parity], h->mf, &h->prm->psi_scale};
+  void* dst[5] = {R.ck_mb[i], R.ck_psi[i], R.ck_nb[i], R.ck_mf[i], R.ck_scale + i};
+  const size_t bytes[5] = {h->mbn * t, h->rows * t, h->rows * t, nc * t, 8};
+  for (int q = 0; q < 5; ++q) {
+    c.src[q] = src[q];
+    c.dst[q] = dst[q];
+    c.bytes[q] = bytes[q];
+  }
+  CK(mm::launch_copy_multi(c, h->stream));
   return MM_OK;
 }
 
@@ -989,12 +994,17 @@ mm_status rec_micro_step(mm_handle* h, int n) {
   if (in_tail) {
     const int j = R.nsub - tail;  // slot of the current state
     const size_t t = h->tsz, nc = (size_t)h->ncells;
-    CK(cudaMemcpyAsync(h->mb, R.sl_mb[j], h->mbn * t, cudaMemcpyDeviceToDevice, h->stream));
-    CK(cudaMemcpyAsync(h->psi[h->parity], R.sl_psi[j], h->rows * t, cudaMemcpyDeviceToDevice,
-                       h->stream));
-    CK(cudaMemcpyAsync(h->nb[h->parity], R.sl_nb[j], h->rows * t, cudaMemcpyDeviceToDevice,
-                       h->stream));
-    CK(cudaMemcpyAsync(h->mf, R.sl_mf[j], nc * t, cudaMemcpyDeviceToDevice, h->stream));
+    mm::CopySegs c{};
+    c.n = 4;
+    const void* src[4] = {R.sl_mb[j], R.sl_psi[j], R.sl_nb[j], R.sl_mf[j]};
+    void* dst[4] = {h->mb, h->psi[h->parity], h->nb[h->parity], h->mf};
+    const size_t bytes[4] = {h->mbn * t, h->rows * t, h->rows * t, nc * t};
+    for (int q = 0; q < 4; ++q) {
+      c.src[q] = src[q];
+      c.dst[q] = dst[q];
+      c.bytes[q] = bytes[q];
+    }
+    CK(mm::launch_copy_multi(c, h->stream));
   }
   return MM_OK;
 }

@@ -23,6 +23,25 @@ __device__ double block_sum(double x, double* red) {
   return t;
 }
 
+// The copies of a CopySegs: 16-byte vectors where both addresses are 16-byte
+// aligned, then the remaining bytes one by one; every thread of the grid takes
+// its share of each segment in turn.
+__global__ void k_copy_multi(const CopySegs c) {
+  const size_t tid = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  for (int q = 0; q < c.n; ++q) {
+    const unsigned char* s = static_cast<const unsigned char*>(c.src[q]);
+    unsigned char* d = static_cast<unsigned char*>(c.dst[q]);
+    const size_t b = c.bytes[q];
+    const bool vec = ((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(d)) & 15) == 0;
+    const size_t nv = vec ? b / 16 : 0;
+    const uint4* s4 = reinterpret_cast<const uint4*>(s);
+    uint4* d4 = reinterpret_cast<uint4*>(d);
+    for (size_t i = tid; i < nv; i += stride) d4[i] = s4[i];
+    for (size_t i = nv * 16 + tid; i < b; i += stride) d[i] = s[i];
+  }
+}
+
 template <typename TO, typename TI>
 __global__ void k_convert(TO* out, const TI* in, size_t n, const double* scale) {
   const double sc = scale ? *scale : 1.0;
@@ -596,6 +615,14 @@ int grid_for(long long n, int block) {
 }
 
 }  // namespace
+
+cudaError_t launch_copy_multi(const CopySegs& c, cudaStream_t s) {
+  size_t most = 0;
+  for (int q = 0; q < c.n; ++q) most = c.bytes[q] > most ? c.bytes[q] : most;
+  if (most == 0) return cudaSuccess;
+  k_copy_multi<<<grid_for((long long)((most + 15) / 16), 256), 256, 0, s>>>(c);
+  return cudaGetLastError();
+}
 
 template <typename TO, typename TI>
 cudaError_t launch_convert(TO* out, const TI* in, size_t n, const double* scale, cudaStream_t s) {

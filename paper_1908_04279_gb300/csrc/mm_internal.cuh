@@ -211,6 +211,16 @@ template <typename T>
 cudaError_t launch_cn_lines(T* psi, int mode, int nx, int ny, int nth, const double* tab, int n,
                             double c, double ha, const double* scale, cudaStream_t s);
 cudaError_t launch_set_scale_one(double* scale, cudaStream_t s);
+// Up to kMaxCopySegs device-to-device copies in one launch (a checkpoint of the
+// state: one launch instead of one copy operation per array).
+constexpr int kMaxCopySegs = 6;
+struct CopySegs {
+  const void* src[kMaxCopySegs];
+  void* dst[kMaxCopySegs];
+  size_t bytes[kMaxCopySegs];
+  int n;
+};
+cudaError_t launch_copy_multi(const CopySegs& c, cudaStream_t s);
 
 // Message returned by mm_last_error(NULL) on this thread.
 void set_thread_error(const char* msg);

@@ -22,6 +22,7 @@
 #include <algorithm>
 #include <utility>
 
+#include "mm_async.cuh"
 #include "mm_cell.cuh"
 #include "mm_host.h"
 
@@ -228,16 +229,43 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
   // barriers); else warp-strided cells
   const int cstart = BW ? (int)blockIdx.x * 4 + wib : gw;
   const int cstep = BW ? (int)gridDim.x * 4 : W;
+  // The psi and n_b columns of a cell and its four neighbours into psi5 / nb5
+  // by asynchronous copies (16 bytes each where a column is a whole number of
+  // 16-byte pieces), one group: a cell's columns are issued as soon as the
+  // previous cell's psi transport has read the buffer, and land while that
+  // cell's rows are computed.
+  auto stage_cols = [&](int c) {
+    const int cy = c / nx, cx = c - cy * nx;
+    const int xp = cx + 1 == nx ? 0 : cx + 1, xm = cx == 0 ? nx - 1 : cx - 1;
+    const int yp = cy + 1 == ny ? 0 : cy + 1, ym = cy == 0 ? ny - 1 : cy - 1;
+    // (a select chain: a dynamically indexed array would live in local memory)
+    auto nbr = [&](int q) {
+      return q == 0 ? c : q == 1 ? cy * nx + xp : q == 2 ? cy * nx + xm : q == 3 ? yp * nx + cx
+                                                                                  : ym * nx + cx;
+    };
+    if ((nth * sizeof(T)) % 16 == 0) {
+      constexpr int P = 16 / sizeof(T);  // values per piece
+      const int per = nth / P;           // pieces per column
+      for (int i = lane; i < 10 * per; i += 32) {
+        const int col = i / per, p = i - col * per, q = col >> 1;
+        const T* src = ((col & 1) ? a.nb_in : a.psi_in) + (size_t)nbr(q) * nth + p * P;
+        T* dst = ((col & 1) ? nb5 : psi5) + (size_t)q * nth + p * P;
+        cp_async16(dst, src);
+      }
+    } else {
+      for (int i = lane; i < 10 * nth; i += 32) {
+        const int col = i / nth, k = i - col * nth, q = col >> 1;
+        if (col & 1)
+          cp_async_t(nb5 + (size_t)q * nth + k, a.nb_in + (size_t)nbr(q) * nth + k);
+        else
+          cp_async_t(psi5 + (size_t)q * nth + k, a.psi_in + (size_t)nbr(q) * nth + k);
+      }
+    }
+    cp_async_commit();
+  };
+  if (cstart < nc) stage_cols(cstart);
   for (int cell = cstart; cell < nc; cell += cstep) {
     const int iy = cell / nx, ix = cell - iy * nx;
-    const int xp = ix + 1 == nx ? 0 : ix + 1, xm = ix == 0 ? nx - 1 : ix - 1;
-    const int yp = iy + 1 == ny ? 0 : iy + 1, ym = iy == 0 ? ny - 1 : iy - 1;
-    const int nbr[5] = {cell, iy * nx + xp, iy * nx + xm, yp * nx + ix, ym * nx + ix};
-    for (int q = 0; q < 5; ++q)
-      for (int k = lane; k < nth; k += 32) {
-        psi5[q * nth + k] = a.psi_in[(size_t)nbr[q] * nth + k];
-        nb5[q * nth + k] = a.nb_in[(size_t)nbr[q] * nth + k];
-      }
     if (BW) {
       // the group's window: the first cell's window widened by 3 columns
       const int c0 = cell - wib, iy0 = c0 / nx, ix0 = c0 - iy0 * nx;
@@ -264,13 +292,15 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
         wacc[w] = T(0);
       }
     }
-    __syncwarp();
     // Eq. 1 first: psi^{n+1} of the cell weights the scatter of its rows
     const CellVel<T> uv = load_cell_vel(a.ucell, cell);
+    cp_async_wait<0>();  // this cell's columns
+    __syncwarp();
     T cell_mass = T(0), unused = T(0);
     psi_cell(pq, uv, psi5, nb5, nb5, nth, lane, pnew, cell_mass, unused, &lt);
     two_sum_acc(mass_hi, mass_lo, cell_mass);
     __syncwarp();
+    if (cell + cstep < nc) stage_cols(cell + cstep);
     for (int k = lane; k < nth; k += 32) a.psi_out[(size_t)cell * nth + k] = pnew[k];
     // Eq. 4 on every row, binding against the anchors' free motors; the next
     // pass's row and anchor indices are loaded while the current one is

@@ -32,6 +32,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "mm_async.cuh"
 #include "mm_cell.cuh"
 #include "mm_host.h"
 
@@ -63,23 +64,7 @@ struct RcArgs {
 constexpr int kRcV = 8;                 // entries per lane of a chunk
 constexpr int kRcChunk = 32 * kRcV;     // entries of a chunk at most
 
-// Asynchronous 4- or 8-byte copies global -> shared (one per thread, any
-// 4/8-byte aligned address), grouped and waited for per thread.
-__device__ __forceinline__ void cp_async_t(float* dst, const float* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(dst)), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_t(double* dst, const double* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(dst)), "l"(src)
-               : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() {
-  asm volatile("cp.async.commit_group;" ::: "memory");
-}
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
-}
+// (asynchronous copies: mm_async.cuh)
 
 // A lane's 8 consecutive entries of a shared-memory stage (16-byte vectors).
 template <typename T>

@@ -61,6 +61,12 @@ __device__ __forceinline__ void walk_adj(const T (&ga)[V], const T (&gb)[V], con
   }
 }
 
+// The reverse kernels are launched with programmatic stream serialization:
+// a launch may be prepared while the kernel before it in the stream still
+// runs, and every block first waits here until that kernel has completed and
+// its memory operations are visible (a no-op when launched without it).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Resident blocks the staged psi reverse kernel is sized for (registers) in
 // float32 (float64 keeps its natural register count).
 #ifndef MM_ADJ_PSI_MIN_BLOCKS
@@ -266,6 +272,7 @@ __device__ __forceinline__ void cell_nbrs(int cell, int nx, int ny, int (&nbr)[5
 // memory: the cell's lam_psi_total (nth values).
 template <typename T>
 __global__ void __launch_bounds__(128) k_adj_psi(const AdjArgs<T> a) {
+  griddep_wait();
   extern __shared__ __align__(16) unsigned char adj_smem[];
   const int nth = a.nth;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -306,6 +313,7 @@ __host__ __device__ inline size_t psi_ring_warp_bytes(int nth, int tsz) {
 // failure, drains its copy and leaves.
 template <typename T>
 __global__ void __launch_bounds__(128, adj_psi_min_blocks<T>()) k_adj_psi_ring(const AdjArgs<T> a) {
+  griddep_wait();
   extern __shared__ __align__(128) unsigned char psr_smem[];
   const int nth = a.nth, nx = a.nx, ny = a.ny;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -669,6 +677,7 @@ __device__ __forceinline__ void flush_params(const AdjArgs<T>& a, const MotorAcc
 // [units][cells] partials; the parameter adjoints accumulate per warp.
 template <typename T, int V>
 __global__ void __launch_bounds__(128, adj_min_blocks<T, V>()) k_adj_motor(const AdjArgs<T> a) {
+  griddep_wait();
   const int nth = a.nth, ns = a.ns, seg = a.seg;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
@@ -765,6 +774,7 @@ __global__ void __launch_bounds__(128, adj_min_blocks<T, V>()) k_adj_motor(const
 template <typename T, int V>
 __global__ void __launch_bounds__(128, adj_min_blocks<T, V>())
     k_adj_motor_ring(const AdjArgs<T> a, int RC, int CH, int S) {
+  griddep_wait();
   extern __shared__ __align__(128) unsigned char ring_smem[];
   const int nth = a.nth, ns = a.ns, seg = a.seg;
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -1103,6 +1113,24 @@ cudaError_t adj_motor_occupancy(int V, int ring_rc, int ns, int S, int* bps) {
   return occ(k_adj_motor<T, 1>, k_adj_motor_ring<T, 1>);
 }
 
+// A launch that may be prepared while the previous kernel of the stream runs
+// (the kernel waits for it in griddep_wait before its first memory access).
+template <typename... P, typename... A>
+cudaError_t launch_overlapped(void (*kernel)(P...), int grid, int block, size_t smem,
+                              cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 template <typename T>
 cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid_psi, int grid_motor,
                            cudaStream_t s) {
@@ -1113,14 +1141,16 @@ cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid_psi, int grid_mo
       cudaError_t e = mm::raise_smem_limit(k_adj_psi_ring<T>, (int)ring_smem);
       if (e != cudaSuccess) return e;
     }
-    k_adj_psi_ring<T><<<grid_psi, block, ring_smem, s>>>(a);
+    cudaError_t e0 = launch_overlapped(k_adj_psi_ring<T>, grid_psi, block, ring_smem, s, a);
+    if (e0 != cudaSuccess) return e0;
   } else {
     const size_t smem = (size_t)4 * a.nth * sizeof(T);
     if (smem > 48 * 1024) {
       cudaError_t e = mm::raise_smem_limit(k_adj_psi<T>, (int)smem);
       if (e != cudaSuccess) return e;
     }
-    k_adj_psi<T><<<grid_psi, block, smem, s>>>(a);
+    cudaError_t e0 = launch_overlapped(k_adj_psi<T>, grid_psi, block, smem, s, a);
+    if (e0 != cudaSuccess) return e0;
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1132,9 +1162,12 @@ cudaError_t launch_adjoint(const AdjArgs<T>& a, int V, int grid_psi, int grid_mo
             mm::raise_smem_limit(ring, (int)rs);
         if (e2 != cudaSuccess) return e2;
       }
-      ring<<<grid_motor, block, rs, s>>>(a, a.ring_rc, a.ring_ch, a.ring_s);
+      cudaError_t e1 =
+          launch_overlapped(ring, grid_motor, block, rs, s, a, a.ring_rc, a.ring_ch, a.ring_s);
+      if (e1 != cudaSuccess) return e1;
     } else {
-      plain<<<grid_motor, block, 0, s>>>(a);
+      cudaError_t e1 = launch_overlapped(plain, grid_motor, block, (size_t)0, s, a);
+      if (e1 != cudaSuccess) return e1;
     }
     return cudaGetLastError();
   };

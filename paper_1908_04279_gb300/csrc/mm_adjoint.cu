@@ -19,6 +19,7 @@
 //     derivative of the branch the forward took, and accumulates the adjoints
 //     of k_off, v_walk and k_on.
 // Limits, order of operations and branch choices follow the oracle's adjoint.
+#include "mm_async.cuh"
 #include "mm_cell.cuh"
 
 namespace mm {
@@ -61,11 +62,8 @@ __device__ __forceinline__ void walk_adj(const T (&ga)[V], const T (&gb)[V], con
   }
 }
 
-// The reverse kernels are launched with programmatic stream serialization:
-// a launch may be prepared while the kernel before it in the stream still
-// runs, and every block first waits here until that kernel has completed and
-// its memory operations are visible (a no-op when launched without it).
-__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// The reverse kernels are launched overlapped (launch_overlapped): every block
+// first waits in griddep_wait for the kernel before it in the stream.
 
 // Resident blocks the staged psi reverse kernel is sized for (registers) in
 // float32 (float64 keeps its natural register count).
@@ -1111,24 +1109,6 @@ cudaError_t adj_motor_occupancy(int V, int ring_rc, int ns, int S, int* bps) {
   if (V == 4) return occ(k_adj_motor<T, 4>, k_adj_motor_ring<T, 4>);
   if (V == 2) return occ(k_adj_motor<T, 2>, k_adj_motor_ring<T, 2>);
   return occ(k_adj_motor<T, 1>, k_adj_motor_ring<T, 1>);
-}
-
-// A launch that may be prepared while the previous kernel of the stream runs
-// (the kernel waits for it in griddep_wait before its first memory access).
-template <typename... P, typename... A>
-cudaError_t launch_overlapped(void (*kernel)(P...), int grid, int block, size_t smem,
-                              cudaStream_t s, A... args) {
-  cudaLaunchConfig_t cfg{};
-  cfg.gridDim = dim3((unsigned)grid);
-  cfg.blockDim = dim3((unsigned)block);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 template <typename T>

@@ -163,16 +163,20 @@ StepArgs<T> step_args_ptrs(mm_handle* h, const StepPtrs& p) {
   a.ucell = (const T*)p.ucell;
   return a;
 }
+// (direct launches of the recording and the reverse sweep: overlapped with
+// the previous kernel of the stream)
 cudaError_t launch_ptrs(mm_handle* h, const StepPtrs& p, cudaStream_t s) {
+  const int g = h->grid_step, b = h->block;
+  const size_t sm = h->smem;
   if (h->prec == MM_FP64) {
     StepArgs<double> a = step_args_ptrs<double>(h, p);
-    return h->V == 2 ? mm::launch_substep<double, 2>(a, h->grid_step, h->block, h->smem, h->tma, s)
-                     : mm::launch_substep<double, 1>(a, h->grid_step, h->block, h->smem, h->tma, s);
+    return h->V == 2 ? mm::launch_substep_overlapped<double, 2>(a, g, b, sm, h->tma, s)
+                     : mm::launch_substep_overlapped<double, 1>(a, g, b, sm, h->tma, s);
   }
   StepArgs<float> a = step_args_ptrs<float>(h, p);
-  if (h->V == 8) return mm::launch_substep<float, 8>(a, h->grid_step, h->block, h->smem, h->tma, s);
-  return h->V == 4 ? mm::launch_substep<float, 4>(a, h->grid_step, h->block, h->smem, h->tma, s)
-                   : mm::launch_substep<float, 1>(a, h->grid_step, h->block, h->smem, h->tma, s);
+  if (h->V == 8) return mm::launch_substep_overlapped<float, 8>(a, g, b, sm, h->tma, s);
+  return h->V == 4 ? mm::launch_substep_overlapped<float, 4>(a, g, b, sm, h->tma, s)
+                   : mm::launch_substep_overlapped<float, 1>(a, g, b, sm, h->tma, s);
 }
 
 mm_status configure(mm_handle* h) {

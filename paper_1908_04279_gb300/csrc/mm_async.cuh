@@ -1,6 +1,9 @@
 // Asynchronous global -> shared copies (cp.async): 4- or 8-byte copies of one
 // value (any 4/8-byte aligned address) and 16-byte copies (both addresses
-// 16-byte aligned), grouped per thread and waited for per thread.
+// 16-byte aligned), grouped per thread and waited for per thread. And
+// overlapped launches: a kernel launched with programmatic stream
+// serialization may be prepared while the kernel before it in the stream still
+// runs; it calls griddep_wait before its first memory access.
 #pragma once
 
 #include "mm_cell.cuh"
@@ -25,6 +28,26 @@ __device__ __forceinline__ void cp_async_commit() {
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Waits until the kernel this one overlaps has completed and its memory
+// operations are visible (a no-op when launched without overlap).
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+cudaError_t launch_overlapped(void (*kernel)(P...), int grid, int block, size_t smem,
+                              cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)grid);
+  cfg.blockDim = dim3((unsigned)block);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 }  // namespace mm

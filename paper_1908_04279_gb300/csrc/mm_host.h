@@ -43,6 +43,14 @@ using mm::StepArgs;
 #define MM_ADJ_FP32_VMAX 8
 #endif
 
+namespace mm {
+// The substep launched overlapped with the previous kernel of its stream
+// (mm_step.cu; direct launches only).
+template <typename T, int V>
+cudaError_t launch_substep_overlapped(const StepArgs<T>& a, int grid, int block, size_t smem,
+                                      bool tma, cudaStream_t s);
+}  // namespace mm
+
 namespace mmh {
 inline thread_local std::string g_create_error;
 constexpr double kPi = 3.14159265358979323846264338327950288;

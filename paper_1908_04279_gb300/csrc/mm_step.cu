@@ -28,6 +28,7 @@
 // Every mbarrier wait is bounded (DevParams::wait_limit polls). A warp whose
 // wait runs out records MM_ERR_TIMEOUT in DevParams::status, waits (bounded)
 // for the copies it still has in flight and leaves.
+#include "mm_async.cuh"
 #include "mm_cell.cuh"
 
 namespace mm {
@@ -38,6 +39,7 @@ size_t step_smem_per_warp(int S, int chunk_elems, int nth, int tsz) {
 
 template <typename T, int V, bool TMA, bool MASSCORR>
 __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepArgs<T> a) {
+  griddep_wait();  // launched overlapped outside graphs (recording, replays)
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int nth = a.nth, ns = a.ns, seg = a.seg;
   const int S = a.stages, RC = a.chunk_rows, CH = a.chunks_per_cell;
@@ -279,20 +281,27 @@ __global__ void __launch_bounds__(128, MM_STEP_MIN_BLOCKS) k_substep(const StepA
 }
 
 template <typename T, int V>
+cudaError_t launch_substep_impl(const StepArgs<T>& a, int grid, int block, size_t smem, bool tma,
+                                cudaStream_t s, bool overlap) {
+  void (*k)(StepArgs<T>) = tma ? (a.mass_correct ? k_substep<T, V, true, true>
+                                                 : k_substep<T, V, true, false>)
+                               : (a.mass_correct ? k_substep<T, V, false, true>
+                                                 : k_substep<T, V, false, false>);
+  if (overlap) return launch_overlapped(k, grid, block, smem, s, a);
+  k<<<grid, block, smem, s>>>(a);
+  return cudaGetLastError();
+}
+template <typename T, int V>
 cudaError_t launch_substep(const StepArgs<T>& a, int grid, int block, size_t smem, bool tma,
                            cudaStream_t s) {
-  if (tma) {
-    if (a.mass_correct)
-      k_substep<T, V, true, true><<<grid, block, smem, s>>>(a);
-    else
-      k_substep<T, V, true, false><<<grid, block, smem, s>>>(a);
-  } else {
-    if (a.mass_correct)
-      k_substep<T, V, false, true><<<grid, block, smem, s>>>(a);
-    else
-      k_substep<T, V, false, false><<<grid, block, smem, s>>>(a);
-  }
-  return cudaGetLastError();
+  return launch_substep_impl<T, V>(a, grid, block, smem, tma, s, false);
+}
+// The same launched overlapped with the previous kernel of the stream (direct
+// launches: the recording's last segment, the replays of the reverse sweep).
+template <typename T, int V>
+cudaError_t launch_substep_overlapped(const StepArgs<T>& a, int grid, int block, size_t smem,
+                                      bool tma, cudaStream_t s) {
+  return launch_substep_impl<T, V>(a, grid, block, smem, tma, s, true);
 }
 
 template <typename T, int V>
@@ -319,10 +328,20 @@ template cudaError_t launch_substep<double, 2>(const StepArgs<double>&, int, int
                                                cudaStream_t);
 template cudaError_t launch_substep<double, 1>(const StepArgs<double>&, int, int, size_t, bool,
                                                cudaStream_t);
+template cudaError_t launch_substep_overlapped<float, 8>(const StepArgs<float>&, int, int, size_t,
+                                                         bool, cudaStream_t);
 template cudaError_t substep_prepare<float, 8>(int, size_t, bool, int*);
+template cudaError_t launch_substep_overlapped<float, 4>(const StepArgs<float>&, int, int, size_t,
+                                                         bool, cudaStream_t);
 template cudaError_t substep_prepare<float, 4>(int, size_t, bool, int*);
+template cudaError_t launch_substep_overlapped<float, 1>(const StepArgs<float>&, int, int, size_t,
+                                                         bool, cudaStream_t);
 template cudaError_t substep_prepare<float, 1>(int, size_t, bool, int*);
+template cudaError_t launch_substep_overlapped<double, 2>(const StepArgs<double>&, int, int, size_t,
+                                                          bool, cudaStream_t);
 template cudaError_t substep_prepare<double, 2>(int, size_t, bool, int*);
+template cudaError_t launch_substep_overlapped<double, 1>(const StepArgs<double>&, int, int, size_t,
+                                                          bool, cudaStream_t);
 template cudaError_t substep_prepare<double, 1>(int, size_t, bool, int*);
 
 }  // namespace mm

@@ -95,6 +95,37 @@ def test_fp64_anchor_long_filaments(mmod, oracle_mod):
     check(*run_both(mmod, oracle_mod, g, r, psi, mb, None, u, 4, "fp64"), TOL["fp64"])
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_anchor_wide_window(mmod, oracle_mod, precision):
+    """A block's window of 25 x 21 anchor cells (48 x 40 cells, l/L = 0.5, 32 x 32):
+    each of the block's threads walks 26 to 28 entries of the sorted (window
+    entry, run) list, in several batches, and the shared window holds every
+    anchor; the row length is a multiple of 4, so 4 cells share one window."""
+    g = Grid(48, 40, 32, 32)
+    r = Rates(ell=0.5, k_on=1.4, glide=0.2)
+    ox, oy = oracle_mod.anchor_offsets(g, r)
+    w = (ox.max() - ox.min() + 1) * (oy.max() - oy.min() + 1)
+    assert 512 < w <= 1024 and g.nx % 4 == 0
+    psi, mb = seeded(g, 231)
+    u = random_divfree_flow(g, 232, 4, 0.1)
+    check(*run_both(mmod, oracle_mod, g, r, psi, mb, None, u, 6, precision), TOL[precision])
+
+
+def test_fp64_anchor_scale_down_shared_window(mmod, oracle_mod):
+    """The forced scale-down on a grid whose row length is a multiple of 4 (the
+    block's 4 cells share one window and sum their runs by the sorted walk)."""
+    g = Grid(8, 6, 12, 16)
+    r = Rates(ell=0.25, k_on=80.0, k_off=0.2)
+    psi, mb = seeded(g, 241, mb_scale=0.05)
+    mtot = 0.03 + 0.1 * np.random.default_rng(242).random((g.ny, g.nx))
+    u = random_divfree_flow(g, 243, 3, 0.05)
+    init, s0, st, gs, F, gf = run_both(mmod, oracle_mod, g, r, psi, mb, mtot, u, 6, "fp64",
+                                       dt_scale=4.0)
+    check(init, s0, st, gs, F, gf, TOL["fp64"])
+    clipped = st.c == mtot
+    assert np.any(clipped) and not np.all(clipped)
+
+
 def test_fp64_anchor_scale_down(mmod, oracle_mod):
     """Few total motors and fast binding with a long step: the binding
     overshoots and the per-anchor scale-down (and the fix-up of the rows and

@@ -689,7 +689,7 @@ def run_ours(args):
                 "motor_cells_per_substep": cells, "algorithmic_bytes_per_launch": algo_e,
                 "achieved_gbs": algo_e / (launch * 1e-3) / 1e9,
                 "plan": {k: info[k] for k in ("grid", "block", "tiles", "V", "tile_work",
-                                              "chunk_bytes")},
+                                              "chunk_bytes", "pair_cells")},
                 "autotune_best_ms_per_substep": best["ms_per_substep"],
                 "autotune_candidates": len(tune)}
 

@@ -457,13 +457,18 @@ mm_status mm_fluid_response(mm_handle* h, double* out, int on_device);
  * choice is cached for the process: a later batch with the same member grids
  * and precision starts with it.
  *
+ * The candidates also try members with at most 16 orientations (and an even
+ * row length) two cells to a warp (cells_per_warp 2: one chunk holds both
+ * cells' rows, half-warps take psi and the close) and one cell to a warp (1).
+ *
  * mm_get_launch_info on a batch: grid, block, shared memory, 1, ring stages,
  * largest chunk (values), tiles, values per lane, tile_work, chunk_bytes,
- * tuned (0/1). */
+ * tuned (0/1), two cells per warp where possible (0/1). */
 typedef struct {
   int tile_work;
   int chunk_bytes;
   double ms_per_substep;
+  int cells_per_warp;
 } mm_batch_tune;
 mm_status mm_create_batch(int n, const mm_grid* grids, const mm_rates* rates, mm_precision prec,
                           void* stream, mm_handle** out);

@@ -26,6 +26,7 @@ struct BatchPlan {
   int V = 1;                  // values per lane, common to all members
   int tile_work = 8192;       // target motor values (rows x ns) per tile
   int chunk_bytes = kChunkBytes;
+  int pairs = 1;              // members that can go two cells to a warp do
   int S = 2, stage_elems = 0, nth_max = 0, block = 128, grid = 1, ntiles = 0;
   size_t smem = 0;
   void* d_args = nullptr;     // [2][n] StepArgs: members at their parities, and flipped
@@ -38,8 +39,12 @@ struct BatchPlan {
 
 namespace {
 
-// Tuned (tile_work, chunk_bytes) per batch shape, for this process.
-std::map<std::string, std::pair<int, int>> g_tune_cache;
+// Tuned (tile_work, chunk_bytes, two cells per warp) per batch shape, for this
+// process.
+struct TuneChoice {
+  int tile_work, chunk_bytes, pairs;
+};
+std::map<std::string, TuneChoice> g_tune_cache;
 
 std::string batch_signature(const mm_handle* h) {
   std::string sig = h->prec == MM_FP64 ? "f64" : "f32";
@@ -100,7 +105,7 @@ mm_status make_plan(mm_handle* h, int tile_work, int chunk_bytes) {
     const mm_handle* m = B->members[i];
     // units of 1 cell (rows in ch chunks of rc) or of 2 cells (one chunk of
     // both cells' rows); tiles of about tile_work motor values, whole units
-    const int cpu = member_pairs(m, B->V) ? 2 : 1;
+    const int cpu = B->pairs && member_pairs(m, B->V) ? 2 : 1;
     int rc, ch;
     if (cpu == 2) {
       rc = 2 * m->g.ntheta;
@@ -335,12 +340,12 @@ mm_status batch_sync(mm_handle* h) {
 const std::vector<mm_handle*>& batch_members(mm_handle* h) { return h->batch->members; }
 
 // grid, block, shared memory, bulk copies (always), ring stages, largest
-// chunk (values), tiles, V, tile_work, chunk_bytes, tuned
+// chunk (values), tiles, V, tile_work, chunk_bytes, tuned, two cells per warp
 mm_status batch_launch_info(mm_handle* h, int* info, int n) {
   const BatchPlan* B = h->batch;
-  const int v[11] = {B->grid, B->block, (int)B->smem, 1, B->S, B->stage_elems, B->ntiles,
-                     B->V, B->tile_work, B->chunk_bytes, B->tuned};
-  for (int i = 0; i < n && i < 11; ++i) info[i] = v[i];
+  const int v[12] = {B->grid,    B->block, (int)B->smem,   1,         B->S,     B->stage_elems,
+                     B->ntiles,  B->V,     B->tile_work,   B->chunk_bytes, B->tuned, B->pairs};
+  for (int i = 0; i < n && i < 12; ++i) info[i] = v[i];
   return MM_OK;
 }
 
@@ -425,8 +430,9 @@ mm_status mm_create_batch(int n, const mm_grid* grids, const mm_rates* rates, mm
   int tw = 8192, cb = kChunkBytes;
   auto c = g_tune_cache.find(batch_signature(h));
   if (c != g_tune_cache.end()) {
-    tw = c->second.first;
-    cb = c->second.second;
+    tw = c->second.tile_work;
+    cb = c->second.chunk_bytes;
+    h->batch->pairs = c->second.pairs;
     h->batch->tuned = 1;
   }
   mm_status st = make_plan(h, tw, cb);
@@ -464,9 +470,11 @@ mm_status mm_batch_autotune(mm_handle* h, int substeps, mm_batch_tune* results, 
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
   float best = 1e30f;
-  int best_w = B->tile_work, best_c = B->chunk_bytes, nres = 0;
-  for (int cb : chunks)
+  int best_w = B->tile_work, best_c = B->chunk_bytes, best_p = B->pairs, nres = 0;
+  for (int pr = 1; pr >= 0 && st == MM_OK; --pr)
+    for (int cb : chunks)
     for (int tw : works) {
+      B->pairs = pr;
       if ((st = make_plan(h, tw, cb)) != MM_OK) break;
       B->args_par.clear();
       if ((st = upload_args(h)) != MM_OK) break;
@@ -483,22 +491,25 @@ mm_status mm_batch_autotune(mm_handle* h, int substeps, mm_batch_tune* results, 
         results[nres].tile_work = tw;
         results[nres].chunk_bytes = cb;
         results[nres].ms_per_substep = ms / substeps;
+        results[nres].cells_per_warp = pr ? 2 : 1;
       }
       ++nres;
       if (ms < best) {
         best = ms;
         best_w = tw;
         best_c = cb;
+        best_p = pr;
       }
     }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   cudaFree(sn.buf);
   if (st != MM_OK) return st;
+  B->pairs = best_p;
   if ((st = make_plan(h, best_w, best_c)) != MM_OK) return st;
   B->args_par.clear();
   B->tuned = 1;
-  g_tune_cache[batch_signature(h)] = {best_w, best_c};
+  g_tune_cache[batch_signature(h)] = {best_w, best_c, best_p};
   if (n_results) *n_results = std::min(nres, max_results);
   return batch_sync(h);
 }

@@ -52,7 +52,8 @@ class mm_moments_out(C.Structure):
 
 
 class mm_batch_tune(C.Structure):
-    _fields_ = [("tile_work", C.c_int), ("chunk_bytes", C.c_int), ("ms_per_substep", C.c_double)]
+    _fields_ = [("tile_work", C.c_int), ("chunk_bytes", C.c_int), ("ms_per_substep", C.c_double),
+                ("cells_per_warp", C.c_int)]
 
 
 class mm_adjoint_seed(C.Structure):
@@ -570,19 +571,20 @@ class Batch:
         self._check(self.lib.mm_debug_set(self.h, int(wait_limit), int(flags)))
 
     def autotune(self, substeps: int = 5):
-        """Time every (tile_work, chunk_bytes) candidate; keep the fastest.
-        Returns the list of timings."""
+        """Time every (tile_work, chunk_bytes, cells per warp) candidate; keep
+        the fastest. Returns the list of timings."""
         res = (mm_batch_tune * 64)()
         n = C.c_int()
         self._check(self.lib.mm_batch_autotune(self.h, int(substeps), res, 64, C.byref(n)))
         return [dict(tile_work=r.tile_work, chunk_bytes=r.chunk_bytes,
-                     ms_per_substep=r.ms_per_substep) for r in res[:n.value]]
+                     cells_per_warp=r.cells_per_warp, ms_per_substep=r.ms_per_substep)
+                for r in res[:n.value]]
 
     def launch_info(self) -> dict:
-        arr = (C.c_int * 11)()
-        self._check(self.lib.mm_get_launch_info(self.h, arr, 11))
+        arr = (C.c_int * 12)()
+        self._check(self.lib.mm_get_launch_info(self.h, arr, 12))
         keys = ("grid", "block", "smem", "tma", "stages", "stage_elems", "tiles", "V",
-                "tile_work", "chunk_bytes", "tuned")
+                "tile_work", "chunk_bytes", "tuned", "pair_cells")
         return dict(zip(keys, list(arr)))
 
     @property

@@ -113,10 +113,13 @@ def test_batch_autotune_restores_state(mmod):
         after = [s.get_state() for s in b.members]
         b.step(2)
         b.sync()
-    assert len(res) == 18 and all(r["ms_per_substep"] > 0 for r in res)
+    # 6 tile sizes x 3 chunk sizes, with two cells per warp where possible and without
+    assert len(res) == 36 and all(r["ms_per_substep"] > 0 for r in res)
+    assert sorted({r["cells_per_warp"] for r in res}) == [1, 2]
     assert info["tuned"] == 1
     best = min(res, key=lambda r: r["ms_per_substep"])
-    assert (info["tile_work"], info["chunk_bytes"]) == (best["tile_work"], best["chunk_bytes"])
+    assert (info["tile_work"], info["chunk_bytes"], info["pair_cells"]) == (
+        best["tile_work"], best["chunk_bytes"], int(best["cells_per_warp"] == 2))
     for x, y in zip(before, after):
         for k in ("psi", "mb", "mf", "c"):
             assert np.array_equal(x[k], y[k]), k

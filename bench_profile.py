@@ -4,12 +4,14 @@
         [--case single|batch|adjoint|moments|local|fluid]
         [--grid NX NY NTHETA NS] [--precision fp32|fp64] [--substeps N]
         [--repeat R] [--K K] [--members M] [--autotune] [--anchors ELL]
-        [--capture ELL RC_CELLS]
+        [--capture ELL RC_CELLS] [--tangent]
 
 single:  the perturbed isotropic state under a seeded 8-mode divergence-free
          flow (amplitude 0.1); R calls of N substeps (with --anchors ELL: motor
          anchors under the motor heads, l/L = ELL; with --capture ELL RC_CELLS:
-         the finite capture radius r_c = RC_CELLS cell widths, l/L = ELL).
+         the finite capture radius r_c = RC_CELLS cell widths, l/L = ELL; with
+         --tangent: the tangent-linear mode along d k_off, every substep
+         advancing the state and its tangent).
 batch:   the first M members of the detachment-rate ensemble (64 by default)
          as one batch; R calls of N batched substeps (after mm_batch_autotune
          with --autotune).
@@ -53,6 +55,7 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--anchors", type=float, default=None)
     ap.add_argument("--capture", type=float, nargs=2, default=None)
+    ap.add_argument("--tangent", action="store_true")
     args = ap.parse_args()
     B.build()
     stream = torch.cuda.current_stream()
@@ -93,6 +96,8 @@ def main():
             sim.set_anchors(True)
         if args.capture is not None:
             sim.set_capture(args.capture[1] / g.nx)
+        if args.tangent:
+            sim.set_tangent((1.0, 0.0, 0.0))
         psi0 = psi_isotropic_perturbed(g, 0)
         u = random_divfree_flow(g, 1, 8, 0.1)
         sim.set_state(psi0)

@@ -96,26 +96,78 @@ __device__ __forceinline__ void psi_cell_tl(const PsiConst<T>& q, const CellVel<
 // The walking term and its tangent on a lane's V nodes: D as walk_dflux, and
 // dD = dF_{j-1} - dF_j with dF = dM + ga da + gb db on the Superbee branch
 // the forward takes (ga, gb from walk_dflux).
+//
+// The branch is chosen with the comparisons of walk_dflux<..., true> and its
+// term taken at once: sigma/2 is one of a, b/2, a/2, b or 0, so its
+// derivative is the same one of da, db/2, da/2, db or 0 (each exact), and
+// dF = dM + that term rounds once, as dM + ga da + gb db does.
 template <typename T, int V>
 __device__ __forceinline__ void walk_tl(const T (&M)[V], const T (&dM)[V], T (&D)[V], T (&dD)[V],
                                         bool first, bool last, int seg) {
-  T ga[V], gb[V];
-  walk_dflux<T, V, true>(M, D, first, last, seg, ga, gb);
+  T ml = __shfl_up_sync(0xffffffffu, M[V - 1], 1, seg);
+  const T mr = __shfl_down_sync(0xffffffffu, M[0], 1, seg);
   T dml = __shfl_up_sync(0xffffffffu, dM[V - 1], 1, seg);
   const T dmr = __shfl_down_sync(0xffffffffu, dM[0], 1, seg);
-  if (first) dml = T(0);
-  T dF[V];
+  if (first) {
+    ml = T(0);
+    dml = T(0);
+  }
+  // d[i] = M_i - M_{i-1} and dd[i] = dM_i - dM_{i-1}, i = 0..V
+  T d[V + 1], hd[V + 1], dd[V + 1];
+  d[0] = M[0] - ml;
+  dd[0] = dM[0] - dml;
+#pragma unroll
+  for (int v = 1; v < V; ++v) {
+    d[v] = M[v] - M[v - 1];
+    dd[v] = dM[v] - dM[v - 1];
+  }
+  d[V] = mr - M[V - 1];
+  dd[V] = dmr - dM[V - 1];
+#pragma unroll
+  for (int i = 0; i <= V; ++i) hd[i] = T(0.5) * d[i];
+  T F[V], dF[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    const T da = dM[v] - (v == 0 ? dml : dM[v - 1]);
-    const T db = (v == V - 1 ? dmr : dM[v + 1]) - dM[v];
-    dF[v] = fma_t(ga[v], da, fma_t(gb[v], db, dM[v]));
+    T sgn = copysign(T(1), d[v + 1]);
+    if (v == V - 1 && last) sgn = T(0);  // plus end: F = M, no slope
+    const T A = d[v] * sgn, hA = hd[v] * sgn;
+    const T hB = fabs(hd[v + 1]), B = fabs(d[v + 1]);
+    const T t1 = tmin(A, hB), t2 = tmin(hA, B);
+    const T r = max3_t(t1, t2, T(0));
+    F[v] = fma_t(r, sgn, M[v]);
+    bool pos, p1, x1a, x2a;
+    if constexpr (sizeof(T) == 8) {
+      // the decisions of walk_dflux<double, V, true>: on the bit patterns
+      const long long iA = __double_as_longlong(A), ihA = __double_as_longlong(hA);
+      const long long ihB = __double_as_longlong(hB), iB = __double_as_longlong(B);
+      pos = __double_as_longlong(r) > 0;
+      p1 = __double_as_longlong(t1) > __double_as_longlong(t2);
+      x1a = iA < ihB;
+      x2a = ihA < iB;
+    } else {
+      pos = r > T(0);
+      p1 = t1 > t2;
+      x1a = A < hB;
+      x2a = hA < B;
+    }
+    const T e1 = x1a ? dd[v] : T(0.5) * dd[v + 1];   // t1 = a (sigma/2 = a) or |b|/2
+    const T e2 = x2a ? T(0.5) * dd[v] : dd[v + 1];   // t2 = a/2 or |b|
+    const T g = pos ? (p1 ? e1 : e2) : T(0);
+    dF[v] = dM[v] + g;
   }
+  T fl = __shfl_up_sync(0xffffffffu, F[V - 1], 1, seg);
   T dfl = __shfl_up_sync(0xffffffffu, dF[V - 1], 1, seg);
-  if (first) dfl = T(0);
+  if (first) {
+    fl = T(0);
+    dfl = T(0);
+  }
+  D[0] = fl - F[0];
   dD[0] = dfl - dF[0];
 #pragma unroll
-  for (int v = 1; v < V; ++v) dD[v] = dF[v - 1] - dF[v];
+  for (int v = 1; v < V; ++v) {
+    D[v] = F[v - 1] - F[v];
+    dD[v] = dF[v - 1] - dF[v];
+  }
 }
 
 // One substep of the state and its tangent (warp per cell, persistent grid).

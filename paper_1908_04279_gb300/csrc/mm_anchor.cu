@@ -10,7 +10,9 @@
 //                     the per-node binding term, n_b of the row, and the row's
 //                     contributions psi ds dtheta Mb added into the anchors'
 //                     float64 accumulators (runs of nodes with the same anchor
-//                     summed in registers first, then one atomic per run);
+//                     summed in registers first; with a block window the run
+//                     sums are summed per window entry by a sorted walk, else
+//                     one atomic per run);
 //   k_anchor_close    thread per anchor: C, the scale-down factor f, Mf = M - C,
 //                     accumulator reset; a flag if any anchor scaled down;
 //   k_anchor_fix      only where the flag is set (the scale-down is rare):
@@ -181,10 +183,11 @@ __host__ __device__ inline size_t anchor_warp_smem(int nth, int tsz, int W = 0) 
 // starts and the rows' contributions to C are summed there (shared-memory
 // atomics), then added to the global accumulators once per window entry.
 // BW (with WIN): the block's 4 warps take 4 consecutive cells of one row and
-// share one window of wx + 3 columns: it is filled and flushed once per group
-// of cells instead of once per cell (the window's set-up and its global
-// atomics dominate when the heads reach far: 27 x 27 cells at 512^2 with
-// l/L = 0.05, against 64 x 64 nodes per cell).
+// share one window of wx + 3 columns, filled once per group of cells; each
+// lane stores one sum per run of its slot, and after the group the block's
+// threads walk the sorted (window entry, run) list, one float64 atomic per
+// entry a thread ends (no shared atomics: those retried under contention at
+// the window centre, where the middle nodes of every orientation land).
 template <typename T, int V, bool MASSCORR, bool WIN, bool BW = false>
 __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(const StepArgs<T> a, const AnchorArgs<T> x) {
   extern __shared__ __align__(16) unsigned char asm_raw[];

@@ -245,3 +245,61 @@ def test_anchor_refusals(mmod):
         with pytest.raises(mmod.MMError) as e:
             b.members[0].set_anchors(True)
         assert e.value.status == 4
+
+
+def test_anchor_precision128_full_size(mmod, oracle_mod):
+    """The bench's anchor workload at full size (128^2 x 32^2, l/L = 0.05, the
+    workload's flow, float32, block window of 4 cells) against the float64
+    oracle, element by element, after 3 substeps."""
+    from paper_1908_04279_gb300.inputs import WORKLOADS, workload_velocity
+    w = WORKLOADS["precision128"]
+    g = w["grid"]
+    r = Rates(ell=0.05)
+    psi = psi_isotropic_perturbed(g, w["seed"])
+    mb = np.zeros((g.ny, g.nx, g.ntheta, g.ns))
+    u = workload_velocity("precision128", 0)
+    check(*run_both(mmod, oracle_mod, g, r, psi, mb, None, u, 3, "fp32"), TOL["fp32"])
+
+
+def test_anchor_large512_conservation_and_sampled_anchors(mmod, oracle_mod):
+    """The bench's large anchor workload (512^2 x 64^2, l/L = 0.05, float32:
+    a 27 x 27 window, each thread of a block walking 72 list entries): after
+    5 substeps the filament number is conserved, bound + free motors equal the
+    total, and the coarse density of 32 sampled anchor cells equals the sum of
+    psi Mb ds dtheta over the configurations whose heads lie in them,
+    recomputed from the exported state (relative 1e-5)."""
+    torch = pytest.importorskip("torch")
+    from paper_1908_04279_gb300.inputs import WORKLOADS, workload_velocity
+    w = WORKLOADS["large512"]
+    g = w["grid"]
+    r = Rates(ell=0.05)
+    dev = torch.device("cuda")
+    with mmod.Simulation(g, r, "fp32") as sim:
+        sim.set_anchors(True)
+        sim.set_state(psi_isotropic_perturbed(g, w["seed"]))
+        sim.set_velocity(torch.tensor(workload_velocity("large512", 0), device=dev))
+        _, s0 = sim.moments(fields=False)
+        sim.step(5)
+        _, s1 = sim.moments(fields=False)
+        psi = torch.empty((g.ny, g.nx, g.ntheta), dtype=torch.float64, device=dev)
+        mb = torch.empty((g.ny, g.nx, g.ntheta, g.ns), dtype=torch.float64, device=dev)
+        mf = torch.empty((g.ny, g.nx), dtype=torch.float64, device=dev)
+        c = torch.empty((g.ny, g.nx), dtype=torch.float64, device=dev)
+        sim.get_state_into(psi, mb, mf, c)
+        torch.cuda.synchronize()
+    assert abs(s1["N_psi"] - s0["N_psi"]) <= 1e-6 * s0["N_psi"]
+    assert abs(s1["motors"] - 1.0) <= 1e-6 and s1["bound"] > 0.0
+    ox, oy = oracle_mod.anchor_offsets(g, r)
+    ox = torch.tensor(ox, dtype=torch.long, device=dev)
+    oy = torch.tensor(oy, dtype=torch.long, device=dev)
+    kk = torch.arange(g.ntheta, device=dev)[:, None].expand(g.ntheta, g.ns)
+    jj = torch.arange(g.ns, device=dev)[None, :].expand(g.ntheta, g.ns)
+    ds, dth = g.L / g.ns, 2.0 * np.pi / g.ntheta
+    rng = np.random.default_rng(251)
+    for ay, ax in zip(rng.integers(0, g.ny, 32), rng.integers(0, g.nx, 32)):
+        cy = (int(ay) - oy) % g.ny
+        cx = (int(ax) - ox) % g.nx
+        want = float((psi[cy, cx, kk] * mb[cy, cx, kk, jj]).sum() * ds * dth)
+        got = float(c[int(ay), int(ax)])
+        assert abs(got - want) <= 1e-5 * abs(want), (int(ay), int(ax), got, want)
+        assert abs(float(mf[int(ay), int(ax)]) + got - 1.0) <= 1e-6

@@ -189,3 +189,29 @@ def test_capture_refusals_and_switching(mmod):
         assert st["mb"].shape == (g.ny, g.nx, g.ntheta, g.ns) and np.all(st["mb"] == 0.0)
         with pytest.raises(mmod.MMError):  # a reach wider than the grid
             sim.set_capture(0.6)
+
+
+def test_capture_precision128_full_size(mmod, oracle_mod):
+    """The bench's capture workload at full size (128^2 x 32^2, l/L = 0.05,
+    r_c = 1.5 cells: 14422 configurations per anchor, float32, the workload's
+    flow) against the float64 oracle, element by element, after one substep
+    from a seeded bound state."""
+    from paper_1908_04279_gb300.inputs import WORKLOADS, workload_velocity
+    O = oracle_mod
+    w = WORKLOADS["precision128"]
+    g = w["grid"]
+    r = Rates(ell=0.05)
+    rc = 1.5 / g.nx
+    tpl = O.rc_template(g, r, rc)
+    assert tpl.nconf == 14422
+    rng = SplitMix64(471)
+    psi = psi_isotropic_perturbed(g, w["seed"])
+    mb = (0.3 / tpl.nconf) * rng.uniforms(g.ny * g.nx * tpl.nconf).reshape(g.ny, g.nx, tpl.nconf)
+    mtot = np.ones((g.ny, g.nx))
+    u = workload_velocity("precision128", 0)
+    st = O.make_state_rc(g, r, rc, psi, mb, mtot)
+    dt = O.dt(g, r, O.make_state(g, psi), u)
+    O.run_rc(g, r, rc, st, u, dt, 1)
+    got, f, sc = _gpu_run(mmod, g, r, rc, "fp32", psi, mb, mtot, u, dt, 1)
+    for k in ("psi", "mb", "mf", "c"):
+        assert rel(got[k], getattr(st, k)) <= 1e-5, (k, rel(got[k], getattr(st, k)))

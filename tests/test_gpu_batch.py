@@ -198,3 +198,34 @@ def test_ensemble64_shapes_step(mmod):
         n1 = [s.moments(fields=False)[1]["N_psi"] for s in b.members]
     for a, c in zip(n0, n1):
         assert abs(c - a) <= 1e-6 * abs(a)
+
+
+def test_ensemble64_members_match_alone(mmod):
+    """The 64-member detachment-rate sweep in one batch (the bench's plan:
+    autotuned, two cells per warp where possible), 10 substeps: four members --
+    two with 16 orientations (two cells per warp) and two with 32 -- equal the
+    same members stepped alone (float32: 1e-6, the mass sums being grouped by
+    tile)."""
+    ms = ensemble_members()
+    picks = [next(i for i, m in enumerate(ms) if (m.grid.ntheta, m.grid.ns) == key)
+             for key in ((16, 16), (16, 32), (32, 16), (32, 32))]
+    with mmod.Batch([m.grid for m in ms], [m.rates for m in ms], "fp32") as b:
+        for sim, m in zip(b.members, ms):
+            psi0, u = member_inputs(m)
+            sim.set_state(psi0)
+            sim.set_velocity(u)
+        b.autotune(substeps=2)
+        assert b.launch_info()["pair_cells"] in (0, 1)
+        b.step(10)
+        b.sync()
+        got = {i: b.members[i].get_state() for i in picks}
+    for i in picks:
+        m = ms[i]
+        psi0, u = member_inputs(m)
+        with mmod.Simulation(m.grid, m.rates, "fp32") as sim:
+            sim.set_state(psi0)
+            sim.set_velocity(u)
+            sim.step(10)
+            ref = sim.get_state()
+        for k in ("psi", "mb", "mf"):
+            assert rel(got[i][k], ref[k]) <= 1e-6, (i, k, rel(got[i][k], ref[k]))

@@ -59,6 +59,9 @@ KERNEL_SRCS = {
     "k_adjoint": ("mm_adjoint.cu", "mm_walk.cuh", "mm_internal.cuh"),
     "k_motor_local": ("mm_local.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
     "k_substep_anchor": ("mm_anchor.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
+    "k_substep_tl": ("mm_tangent.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
+    "k_rc_motor": ("mm_capture.cu", "mm_async.cuh", "mm_cell.cuh", "mm_walk.cuh",
+                   "mm_internal.cuh"),
 }
 
 

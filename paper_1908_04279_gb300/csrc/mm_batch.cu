@@ -248,7 +248,8 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
       // the unit's first cell; Mf of the first cell and the total motors of
       // the half-warp's cell
       cell = ct.cell0 + ccell * ct.cpu;
-      const int half = (ct.cpu >> 1) & (lane >> 4);  // the half-warp's cell in a unit of 2
+      // the half-warp's cell in a unit of 2 with at most 16 orientations
+      const int half = (ct.cpu == 2 && nth <= 16) ? lane >> 4 : 0;
       // (the total motors are needed at the unit's end only)
       const T mf_n = have_next && ccell > 0 ? mf_next : A->mf_in[cell];
       mtot = A->mtot[cell + half];
@@ -319,20 +320,41 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
         }
       __syncwarp();
     }
-    T acc = T(0), cell_mass = T(0);
-    // (in a unit of 2, half-warp h takes cell h with lane 16 h + k on orientation k)
-    const int half = (ct.cpu >> 1) & (lane >> 4);
-    const size_t h5 = (size_t)half * 5 * nth;
-    psi_cell(pq, uv, psi5 + h5, nb5 + h5, s_nb + half * nth, nth, ct.cpu == 2 ? lane & 15 : lane,
-             A->psi_out + (size_t)(cell + half) * nth, cell_mass, acc);
-    two_sum_acc(mass_hi, mass_lo, cell_mass);
-    if (ct.cpu == 2)
-      pair_motor_close(acc, mtot, s_nb + half * nth, nth, ns, lane, cell + half, A->mb_out,
-                       A->nb_out, A->c, A->mf_out, A->cpre_out);
-    else
-      cell_motor_close(acc, mtot, s_nb, nth, ns, lane, cell, A->mb_out, A->nb_out, A->c,
-                       A->mf_out, A->cpre_out);
-    __syncwarp();
+    if (ct.cpu == 2 && nth > 16) {
+      // a unit of 2 with more than 16 orientations: the warp takes the two
+      // cells' psi transport and close one after the other
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        if (h) {  // the second cell's velocity block and total motors
+          uv = load_cell_vel(A->ucell, cell + 1);
+          mtot = A->mtot[cell + 1];
+        }
+        T acc = T(0), cell_mass = T(0);
+        const size_t h5 = (size_t)h * 5 * nth;
+        psi_cell(pq, uv, psi5 + h5, nb5 + h5, s_nb + h * nth, nth, lane,
+                 A->psi_out + (size_t)(cell + h) * nth, cell_mass, acc);
+        two_sum_acc(mass_hi, mass_lo, cell_mass);
+        cell_motor_close(acc, mtot, s_nb + h * nth, nth, ns, lane, cell + h, A->mb_out,
+                         A->nb_out, A->c, A->mf_out, A->cpre_out);
+        __syncwarp();
+      }
+    } else {
+      T acc = T(0), cell_mass = T(0);
+      // (in a unit of 2, half-warp h takes cell h with lane 16 h + k on orientation k)
+      const int half = ct.cpu == 2 ? lane >> 4 : 0;
+      const size_t h5 = (size_t)half * 5 * nth;
+      psi_cell(pq, uv, psi5 + h5, nb5 + h5, s_nb + half * nth, nth,
+               ct.cpu == 2 ? lane & 15 : lane, A->psi_out + (size_t)(cell + half) * nth, cell_mass,
+               acc);
+      two_sum_acc(mass_hi, mass_lo, cell_mass);
+      if (ct.cpu == 2)
+        pair_motor_close(acc, mtot, s_nb + half * nth, nth, ns, lane, cell + half, A->mb_out,
+                         A->nb_out, A->c, A->mf_out, A->cpre_out);
+      else
+        cell_motor_close(acc, mtot, s_nb, nth, ns, lane, cell, A->mb_out, A->nb_out, A->c,
+                         A->mf_out, A->cpre_out);
+      __syncwarp();
+    }
     if (++ccell == ct.ncell) close_tile();
   }
 

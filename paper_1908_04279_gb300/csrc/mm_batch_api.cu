@@ -73,15 +73,17 @@ void member_chunks(const mm_handle* m, int chunk_bytes, int* rc, int* ch) {
 }
 
 // Whether a member's cells go two to a warp: at most 16 orientations (one
-// half-warp per cell for psi and the close), the rows of a cell a whole number
-// of row passes (32 / seg rows each), an even row length (the two cells of a
-// unit share a row) and neighbourhood columns that bulk copies can stage.
+// half-warp per cell for psi and the close), or at most 32 with both cells'
+// rows in 4 KB (the warp takes the two cells' psi and close in turn); the rows
+// of a cell a whole number of row passes (32 / seg rows each), an even row
+// length (the two cells of a unit share a row) and neighbourhood columns that
+// bulk copies can stage.
 bool member_pairs(const mm_handle* m, int V) {
   int seg = 1;
   while (seg < m->g.ns / V) seg <<= 1;
   const int nth = m->g.ntheta;
-  return nth <= 16 && nth % (32 / seg) == 0 && m->g.nx % 2 == 0 &&
-         ((size_t)nth * m->tsz) % 16 == 0;
+  const bool fits = nth <= 16 || (nth <= 32 && (size_t)2 * nth * m->g.ns * m->tsz <= 4096);
+  return fits && nth % (32 / seg) == 0 && m->g.nx % 2 == 0 && ((size_t)nth * m->tsz) % 16 == 0;
 }
 
 template <typename T>

@@ -25,8 +25,9 @@ from paper_1908_04279_gb300.inputs import (Grid, Member, Rates, ensemble_members
 pytestmark = pytest.mark.gpu
 
 # uneven members: grids, angle and arclength counts, rates; members 0, 1, 3
-# and 6 go two cells to a warp (at most 16 orientations, even nx), member 5
-# (odd nx) one
+# and 6 go two cells to a warp (at most 16 orientations, even nx), member 2
+# (32 x 16) in float32 in units of two cells taken in turn, member 5 (odd nx)
+# one cell per warp
 SHAPES = [((8, 8, 16, 16), 0.3, 1.0), ((12, 10, 16, 32), 2.0, 0.6), ((6, 7, 32, 16), 0.07, 1.7),
           ((16, 16, 16, 16), 0.5, 1.0), ((9, 5, 32, 32), 4.0, 1.2), ((7, 6, 16, 16), 1.1, 0.8),
           ((10, 6, 8, 32), 0.9, 1.4)]

@@ -290,6 +290,9 @@ __global__ void __launch_bounds__(128, batch_min_blocks<T>())
         break;
       }
     }
+    // (rows from the unit's row nth on -- the second cell of a unit of 2 --
+    // bind to that cell's Mf; a chunk may hold rows of either or both)
+    rk.rsplit = nth - part * ct.rc;
     rows_chunk<T, V, true>(stages + (size_t)s * stage_elems, A->mb_out + chunk_off, ct.rc, ns, seg,
                            lg, rk, ds, s_nb + part * ct.rc);
     __syncwarp();

@@ -73,16 +73,16 @@ void member_chunks(const mm_handle* m, int chunk_bytes, int* rc, int* ch) {
 }
 
 // Whether a member's cells go two to a warp: at most 16 orientations (one
-// half-warp per cell for psi and the close), or at most 32 with both cells'
-// rows in 4 KB (the warp takes the two cells' psi and close in turn); the rows
-// of a cell a whole number of row passes (32 / seg rows each), an even row
-// length (the two cells of a unit share a row) and neighbourhood columns that
-// bulk copies can stage.
+// half-warp per cell for psi and the close) or at most 32 (the warp takes the
+// two cells' psi and close in turn), with one cell's rows in at most 4 KB (a
+// unit is one chunk or two); the rows of a cell a whole number of row passes
+// (32 / seg rows each), an even row length (the two cells of a unit share a
+// row) and neighbourhood columns that bulk copies can stage.
 bool member_pairs(const mm_handle* m, int V) {
   int seg = 1;
   while (seg < m->g.ns / V) seg <<= 1;
   const int nth = m->g.ntheta;
-  const bool fits = nth <= 16 || (nth <= 32 && (size_t)2 * nth * m->g.ns * m->tsz <= 4096);
+  const bool fits = nth <= 32 && (size_t)nth * m->g.ns * m->tsz <= 4096;
   return fits && nth % (32 / seg) == 0 && m->g.nx % 2 == 0 && ((size_t)nth * m->tsz) % 16 == 0;
 }
 
@@ -110,8 +110,13 @@ mm_status make_plan(mm_handle* h, int tile_work, int chunk_bytes) {
     const int cpu = B->pairs && member_pairs(m, B->V) ? 2 : 1;
     int rc, ch;
     if (cpu == 2) {
-      rc = 2 * m->g.ntheta;
+      // the unit's 2 ntheta rows in chunks of at most 4 KB (a divisor of the
+      // unit's rows: one chunk, or one cell's rows per chunk)
+      const int rows = 2 * m->g.ntheta;
+      const size_t row_bytes = (size_t)m->g.ns * m->tsz;
       ch = 1;
+      while (ch < rows && (rows % ch != 0 || (size_t)(rows / ch) * row_bytes > 4096)) ++ch;
+      rc = rows / ch;
     } else {
       member_chunks(m, chunk_bytes, &rc, &ch);
     }

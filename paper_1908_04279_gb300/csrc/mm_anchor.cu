@@ -49,23 +49,28 @@ struct AnchorArgs {
   // woy..woy+wy-1; widx [nth][ns] is each node's index in it (wx * wy entries).
   const int* widx;
   int wox, woy, wx, wy;
-  // The window shared by a block's 4 consecutive cells of a row (wx + 3
-  // columns): widxb [nth][ns] is each node's index in it for the group's first
-  // cell (+ the cell's place in the group).
-  const int* widxb;
   // [nth][ns / V]: per orientation and lane slot, bits 0-7: bit v set where
   // the slot's node v is the last of a run of nodes with one anchor (the same
-  // in every cell: the anchors' offsets depend on (k, j) only); bits 8-31: the
-  // number of such slot runs before the slot in a cell (k-major, then slot)
+  // in every cell: the anchors' offsets depend on (k, j) only)
   const unsigned* runend;
-  // The block-window form's sum of the slot runs into the window: the 4 cells'
-  // nsr run sums each are listed as (window entry, run) pairs sorted by entry
-  // and cut into 128 equal chunks, one per thread, stored step-major
-  // ([rt_e][128]); an entry packs the run's index in the block's sums (bits
-  // 0-15), its window entry (bits 16-30) and bit 31 set where the entry's
-  // partial sum ends within the chunk. Padding reads a zero kept after the sums.
-  const unsigned* rtab;
-  int rt_e, nsr;
+  // The block-window form: the block's 4 warps take 4 consecutive cells of a
+  // row and share one window of wx + 3 columns; went [nth][ns] is each node's
+  // entry in it for the group's first cell (cell c of the group adds c). A
+  // cell's nsr slot runs (runs of a lane slot's nodes with one anchor) are
+  // ordered by window entry, the same order in every cell: wpos [nth][ns] is
+  // the place of each node's slot run in it. Each warp stores its cell's run
+  // sums in that order (nsrp = 32 ch places, zeros past nsr) and sums them per
+  // entry: lane l takes places l ch .. l ch + ch - 1; sgbits [nw][32] marks
+  // the places that end an entry's sums and sgrank [32] counts such ends
+  // before a lane's first place (nkeys in all). m4 [(wx + 3) wy] gives, per
+  // entry of the block's window, the index of its sum among each of the 4
+  // cells' per-entry sums (0xffff: none).
+  const unsigned short* went;
+  const unsigned short* wpos;
+  const unsigned* sgbits;
+  const unsigned* sgrank;
+  const uint2* m4;
+  int nsr, nsrp, ch, nw, nkeys;
 };
 
 __device__ __forceinline__ int anchor_cell(int ix, int iy, int2 o, int nx, int ny) {
@@ -75,8 +80,31 @@ __device__ __forceinline__ int anchor_cell(int ix, int iy, int2 o, int nx, int n
   return ay * nx + ax;
 }
 
-// List entries a thread of the block-window form loads at once.
-constexpr int kRtBatch = 8;
+// V 16-bit table values of a lane slot, two to a 32-bit word.
+template <int V>
+struct U16Pack {
+  unsigned w[(V + 1) / 2];
+};
+template <int V>
+__device__ __forceinline__ U16Pack<V> ld_u16(const unsigned short* p) {
+  U16Pack<V> r;
+  if constexpr (V == 8) {
+    const uint4 q = __ldg(reinterpret_cast<const uint4*>(p));
+    r.w[0] = q.x, r.w[1] = q.y, r.w[2] = q.z, r.w[3] = q.w;
+  } else if constexpr (V == 4) {
+    const uint2 q = __ldg(reinterpret_cast<const uint2*>(p));
+    r.w[0] = q.x, r.w[1] = q.y;
+  } else if constexpr (V == 2) {
+    r.w[0] = __ldg(reinterpret_cast<const unsigned*>(p));
+  } else {
+    r.w[0] = __ldg(p);
+  }
+  return r;
+}
+template <int V>
+__device__ __forceinline__ unsigned u16_at(const U16Pack<V>& p, int v) {
+  return (v & 1) ? p.w[v >> 1] >> 16 : p.w[v >> 1] & 0xffffu;
+}
 
 // A lane's V values of the motor density, loaded and stored with the streaming
 // (evict-first) cache policy: the density is read and written once per
@@ -183,11 +211,14 @@ __host__ __device__ inline size_t anchor_warp_smem(int nth, int tsz, int W = 0) 
 // starts and the rows' contributions to C are summed there (shared-memory
 // atomics), then added to the global accumulators once per window entry.
 // BW (with WIN): the block's 4 warps take 4 consecutive cells of one row and
-// share one window of wx + 3 columns, filled once per group of cells; each
-// lane stores one sum per run of its slot, and after the group the block's
-// threads walk the sorted (window entry, run) list, one float64 atomic per
-// entry a thread ends (no shared atomics: those retried under contention at
-// the window centre, where the middle nodes of every orientation land).
+// share one window of wx + 3 columns. Each warp stores its cell's slot-run sums
+// ordered by window entry, sums them per entry right after its rows (lanes
+// take equal runs of places; an entry's sum that spans lanes is completed by a
+// segmented scan over the lanes), and after a block barrier the block adds
+// the 4 cells' per-entry sums of each window entry and issues one float64
+// atomic per entry (no shared atomics: those retried under contention at the
+// window centre, where the middle nodes of every orientation land). The next
+// group's window is copied in while that sum runs.
 template <typename T, int V, bool MASSCORR, bool WIN, bool BW = false>
 __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(const StepArgs<T> a, const AnchorArgs<T> x) {
   extern __shared__ __align__(16) unsigned char asm_raw[];
@@ -205,16 +236,19 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
       BW ? asm_raw + 4 * anchor_warp_smem(nth, sizeof(T), 0)
          : wbase + (((size_t)11 * nth * sizeof(T) + 15) & ~(size_t)15);
   T* wmf = reinterpret_cast<T*>(winbase);
-  T* wacc = wmf + Wn;  // the per-warp window's sums
-  // BW: the window's cells after its free motors, then the 4 cells' slot-run
-  // sums [4][nsr] and one zero
-  int* wcell = reinterpret_cast<int*>(BW ? wmf + Wn : wacc + Wn);
-  T* rb = reinterpret_cast<T*>(winbase + (((size_t)Wn * (sizeof(T) + 4) + 15) & ~(size_t)15));
-  if (BW && threadIdx.x == 0) rb[4 * x.nsr] = T(0);
+  T* wacc = wmf + Wn;                                   // WIN: the window's sums
+  int* wcell = reinterpret_cast<int*>(wacc + Wn);       // WIN: the window's cells
+  // BW: after the window's free motors, the 4 warps' ordered run sums [nsrp]
+  // and then their per-entry sums [nkeys]
+  T* rb0 = reinterpret_cast<T*>(winbase + (((size_t)Wn * sizeof(T) + 15) & ~(size_t)15));
+  T* rbw = rb0 + (size_t)wib * x.nsrp;
+  T* sw0 = rb0 + 4 * (size_t)x.nsrp;
+  T* sw = sw0 + (size_t)wib * x.nkeys;
+  if (BW)  // the places past nsr stay zero (no run is stored there)
+    for (int p = x.nsr + lane; p < x.nsrp; p += 32) rbw[p] = T(0);
   const int gw = blockIdx.x * (blockDim.x >> 5) + wib;
   const int W = gridDim.x * (blockDim.x >> 5);
   const int nc = (int)a.ncells;
-  const int* widx_tab = BW ? x.widxb : x.widx;
   // the flag of the other parity was read by the previous substep's fix-up:
   // clear it for the next substep
   if (blockIdx.x == 0 && threadIdx.x == 0) x.flags[x.flag ^ 1] = 0;
@@ -266,24 +300,51 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
     }
     cp_async_commit();
   };
+  // BW: the window of the group whose first cell is c0, copied asynchronously
+  // (the block waits for it with the next cell's columns); entries run over
+  // the window row-major, the block's threads striding by 128 (the window is
+  // no wider than the grid, so one wrap of each coordinate suffices)
+  const int wxb = x.wx + 3;
+  const int wdq = BW ? (int)blockDim.x / wxb : 0, wdr = BW ? (int)blockDim.x - wdq * wxb : 0;
+  auto wrap = [](int g, int n) { return g < 0 ? g + n : g >= n ? g - n : g; };
+  auto fill_window = [&](int c0) {
+    const int iy0 = c0 / nx, ix0 = c0 - iy0 * nx;
+    int wyi = (int)threadIdx.x / wxb, wxi = (int)threadIdx.x - wyi * wxb;
+    for (int w = threadIdx.x; w < Wn; w += blockDim.x) {
+      const int gc = wrap(iy0 + x.woy + wyi, ny) * nx + wrap(ix0 + x.wox + wxi, nx);
+      cp_async_t(wmf + w, a.mf_in + gc);
+      wxi += wdr;
+      wyi += wdq;
+      if (wxi >= wxb) wxi -= wxb, ++wyi;
+    }
+    cp_async_commit();
+  };
+  if (BW && cstart < nc) fill_window(cstart - wib);
   if (cstart < nc) stage_cols(cstart);
+  // the next pass's motor density and table values (loaded while the current
+  // pass is computed; the first pass of a warp's next cell while its last
+  // cell's sums are formed)
+  Pack<T, V> qn;
+  Pack<int, V> wn;          // WIN: window entries
+  U16Pack<V> wen, wps;      // BW: window entries and run places
+  unsigned en = 0;          // the slot's run ends
+  auto load_pass = [&](int cl, int r0) {
+    const int k = r0 + lg.rslot;
+    if (k < nth && lg.lane_ok) {
+      qn = ld_stream<T, V>(a.mb_in + ((size_t)cl * nth + k) * ns + lg.sl * V);
+      if (BW) {
+        wen = ld_u16<V>(x.went + (size_t)k * ns + lg.sl * V);
+        wps = ld_u16<V>(x.wpos + (size_t)k * ns + lg.sl * V);
+      } else if (WIN) {
+        wn = *reinterpret_cast<const Pack<int, V>*>(x.widx + (size_t)k * ns + lg.sl * V);
+      }
+      if (WIN) en = x.runend[(size_t)k * (ns / V) + lg.sl];
+    }
+  };
+  if (cstart < nc) load_pass(cstart, 0);
   for (int cell = cstart; cell < nc; cell += cstep) {
     const int iy = cell / nx, ix = cell - iy * nx;
-    if (BW) {
-      // the group's window: the first cell's window widened by 3 columns
-      const int c0 = cell - wib, iy0 = c0 / nx, ix0 = c0 - iy0 * nx;
-      const int wxb = x.wx + 3;
-      for (int w = threadIdx.x; w < Wn; w += blockDim.x) {
-        const int wyi = w / wxb, wxi = w - wyi * wxb;
-        int gx = (ix0 + x.wox + wxi) % nx, gy = (iy0 + x.woy + wyi) % ny;
-        if (gx < 0) gx += nx;
-        if (gy < 0) gy += ny;
-        const int gc = gy * nx + gx;
-        wcell[w] = gc;
-        wmf[w] = a.mf_in[gc];
-      }
-      __syncthreads();
-    } else if (WIN) {
+    if (WIN && !BW) {
       for (int w = lane; w < Wn; w += 32) {
         const int wyi = w / x.wx, wxi = w - wyi * x.wx;
         int gx = (ix + x.wox + wxi) % nx, gy = (iy + x.woy + wyi) % ny;
@@ -297,52 +358,41 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
     }
     // Eq. 1 first: psi^{n+1} of the cell weights the scatter of its rows
     const CellVel<T> uv = load_cell_vel(a.ucell, cell);
-    cp_async_wait<0>();  // this cell's columns
-    __syncwarp();
+    cp_async_wait<0>();  // this cell's columns (BW: and the group's window)
+    if (BW)
+      __syncthreads();
+    else
+      __syncwarp();
     T cell_mass = T(0), unused = T(0);
     psi_cell(pq, uv, psi5, nb5, nb5, nth, lane, pnew, cell_mass, unused, &lt);
     two_sum_acc(mass_hi, mass_lo, cell_mass);
     __syncwarp();
     if (cell + cstep < nc) stage_cols(cell + cstep);
     for (int k = lane; k < nth; k += 32) a.psi_out[(size_t)cell * nth + k] = pnew[k];
-    // Eq. 4 on every row, binding against the anchors' free motors; the next
-    // pass's row and anchor indices are loaded while the current one is
-    // computed
-    Pack<T, V> qn;
-    Pack<int, V> wn;
-    unsigned en = 0;  // the slot's run ends and first slot run
-    auto load_pass = [&](int r0) {
-      const int k = r0 + lg.rslot;
-      if (k < nth && lg.lane_ok) {
-        qn = ld_stream<T, V>(a.mb_in + ((size_t)cell * nth + k) * ns + lg.sl * V);
-        if (WIN) {
-          wn = *reinterpret_cast<const Pack<int, V>*>(widx_tab + (size_t)k * ns + lg.sl * V);
-          en = x.runend[(size_t)k * (ns / V) + lg.sl];
-        }
-      }
-    };
-    load_pass(0);
+    // Eq. 4 on every row, binding against the anchors' free motors
     for (int r0 = 0; r0 < nth; r0 += lg.rpp) {
       const int k = r0 + lg.rslot;
       const bool row_ok = k < nth, act = row_ok && lg.lane_ok;
       const size_t roff = ((size_t)cell * nth + (row_ok ? k : 0)) * ns + lg.sl * V;
       T M[V], D[V], Ms[V], mfv[V];
       int anc[V];
-      unsigned ends = 0, srun = 0;
+      unsigned ends = 0;
+      U16Pack<V> pos = wps;
       if (act) {
         const Pack<T, V> q = qn;
         if (WIN) {
           // the free motors of each run's anchor, read once at the run's
           // first node
-          const Pack<int, V> wi = wn;
           ends = en & 0xffu;
-          srun = en >> 8;
           const unsigned starts = (ends << 1) | 1u;
           T cur = T(0);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
             M[v] = q.v[v];
-            anc[v] = wi.v[v] + (BW ? wib : 0);
+            if (BW)
+              anc[v] = (int)u16_at<V>(wen, v) + wib;
+            else
+              anc[v] = wn.v[v];
             if ((starts >> v) & 1u) cur = wmf[anc[v]];
             mfv[v] = cur;
           }
@@ -363,7 +413,7 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
           anc[v] = cell;
         }
       }
-      if (r0 + lg.rpp < nth) load_pass(r0 + lg.rpp);
+      if (r0 + lg.rpp < nth) load_pass(cell, r0 + lg.rpp);
       T snb = T(0);
       if constexpr (sizeof(T) == 4 && (V == 4 || V == 8)) {
         // register pairs, packed two-value arithmetic: the same nodal values,
@@ -408,15 +458,14 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
       if (act) {
         st_stream<T, V>(a.mb_out + roff, M);
         if (BW) {
-          // each slot run's sum into its place among the block's run sums
+          // each slot run's sum into its place among the cell's ordered sums
           const T w = pnew[k] * dsdth;
-          T* r = rb + (size_t)wib * x.nsr + srun;
           T s = T(0);
 #pragma unroll
           for (int v = 0; v < V; ++v) {
             s = fma_t(w, M[v], s);
             if ((ends >> v) & 1u) {
-              *r++ = s;
+              rbw[u16_at<V>(pos, v)] = s;
               s = T(0);
             }
           }
@@ -431,31 +480,61 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
       if (lg.first && row_ok) a.nb_out[(size_t)cell * nth + k] = snb * sc.ds;
     }
     __syncwarp();
+    if (cell + cstep < nc) load_pass(cell + cstep, 0);
     if (BW) {
-      // the group's run sums into the global accumulators: each thread sums
-      // its chunk of the (entry, run) list, one atomic per entry it ends
-      __syncthreads();
-      // (rt_e is a multiple of kRtBatch: a batch of list entries is loaded
-      // before any is used, so that their loads overlap)
-      const unsigned* rt = x.rtab + threadIdx.x;
+      // this cell's run sums per window entry: lane l adds its places in
+      // order and stores the sum at each place that ends an entry
+      const int r0 = (int)__ldg(x.sgrank + lane);
+      int r = r0;
       T acc = T(0);
-      for (int i0 = 0; i0 < x.rt_e; i0 += kRtBatch) {
-        unsigned e[kRtBatch];
-#pragma unroll
-        for (int i = 0; i < kRtBatch; ++i) e[i] = __ldg(rt + (size_t)(i0 + i) * 128);
-        T r[kRtBatch];
-#pragma unroll
-        for (int i = 0; i < kRtBatch; ++i) r[i] = rb[e[i] & 0xffffu];
-#pragma unroll
-        for (int i = 0; i < kRtBatch; ++i) {
-          acc += r[i];
-          if (e[i] >> 31) {
-            if (acc != T(0)) atomicAdd(x.cacc + wcell[(e[i] >> 16) & 0x7fffu], (double)acc);
+      for (int w = 0; w < x.nw; ++w) {
+        const unsigned m = __ldg(x.sgbits + 32 * w + lane);
+        const T* src = rbw + lane * x.ch + 32 * w;
+        const int n = min(32, x.ch - 32 * w);
+#pragma unroll 4
+        for (int i = 0; i < n; ++i) {
+          acc += src[i];
+          if ((m >> i) & 1u) {
+            sw[r++] = acc;
             acc = T(0);
           }
         }
       }
+      // the places of an entry in earlier lanes: a segmented scan of the
+      // lanes' open sums (a lane that ended an entry starts the next one)
+      const unsigned had = __ballot_sync(0xffffffffu, r != r0);
+      T v = acc;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const T u = __shfl_up_sync(0xffffffffu, v, d);
+        if (lane >= d) {
+          const unsigned span = ((2u << lane) - 1u) & ~((1u << (lane - d + 1)) - 1u);
+          if (!(had & span)) v += u;
+        }
+      }
+      const T cin = __shfl_up_sync(0xffffffffu, v, 1);
+      if (lane > 0 && r != r0) sw[r0] += cin;
       __syncthreads();
+      // the next group's window; then the 4 cells' sums of each window entry
+      // into its global accumulator, one atomic per entry
+      const int c0 = cell - wib;
+      if (c0 + cstep < nc) fill_window(c0 + cstep);
+      const int iy0 = c0 / nx, ix0 = c0 - iy0 * nx;
+      int wyi = (int)threadIdx.x / wxb, wxi = (int)threadIdx.x - wyi * wxb;
+      for (int w = threadIdx.x; w < Wn; w += blockDim.x) {
+        const uint2 m = __ldg(x.m4 + w);
+        const unsigned rr[4] = {m.x & 0xffffu, m.x >> 16, m.y & 0xffffu, m.y >> 16};
+        T s = T(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (rr[c] != 0xffffu) s += sw0[(size_t)c * x.nkeys + rr[c]];
+        if (s != T(0))
+          atomicAdd(x.cacc + wrap(iy0 + x.woy + wyi, ny) * nx + wrap(ix0 + x.wox + wxi, nx),
+                    (double)s);
+        wxi += wdr;
+        wyi += wdq;
+        if (wxi >= wxb) wxi -= wxb, ++wyi;
+      }
     } else if (WIN) {  // the window's sums into the global accumulators
       for (int w = lane; w < Wn; w += 32) {
         const T v = wacc[w];
@@ -641,15 +720,22 @@ mm::AnchorArgs<T> anchor_args(mm_handle* h, int flag) {
   x.flags = h->anc_flags;
   x.flag = flag;
   x.widx = h->anc_widx;
-  x.widxb = h->anc_widxb;
   x.runend = h->anc_runend;
-  x.rtab = h->anc_rtab;
-  x.rt_e = h->anc_rt_e;
-  x.nsr = h->anc_nsr;
   x.wox = h->anc_win[0];
   x.woy = h->anc_win[1];
   x.wx = h->anc_win[2];
   x.wy = h->anc_win[3];
+  const size_t nn = (size_t)h->g.ntheta * h->g.ns, wnb = (size_t)(x.wx + 3) * x.wy;
+  x.went = h->anc_wtab;
+  x.wpos = h->anc_wtab + nn;
+  x.m4 = reinterpret_cast<const uint2*>(h->anc_rtab);
+  x.sgbits = h->anc_rtab ? h->anc_rtab + 2 * wnb : nullptr;
+  x.sgrank = h->anc_rtab ? x.sgbits + 32 * (size_t)h->anc_sg[2] : nullptr;
+  x.nsr = h->anc_nsr;
+  x.nsrp = h->anc_sg[0];
+  x.ch = h->anc_sg[1];
+  x.nw = h->anc_sg[2];
+  x.nkeys = h->anc_sg[3];
   return x;
 }
 
@@ -660,13 +746,13 @@ int blocks_for(long long work, int per_block, int cap) {
 }
 
 // Shared memory of the block-window form: the 4 warps' columns, then the
-// window of (wx + 3) x wy entries (free motors, cell indices), then the 4
-// cells' slot-run sums and one zero.
+// window's free motors ((wx + 3) x wy entries), then the 4 cells' ordered run
+// sums and their per-entry sums.
 template <typename T>
 size_t anchor_bw_smem(const mm_handle* h) {
   const size_t wn = (size_t)(h->anc_win[2] + 3) * h->anc_win[3];
-  return 4 * mm::anchor_warp_smem(h->g.ntheta, sizeof(T), 0) +
-         ((wn * (sizeof(T) + 4) + 15) & ~(size_t)15) + (4 * (size_t)h->anc_nsr + 1) * sizeof(T);
+  return 4 * mm::anchor_warp_smem(h->g.ntheta, sizeof(T), 0) + ((wn * sizeof(T) + 15) & ~(size_t)15) +
+         4 * ((size_t)h->anc_sg[0] + h->anc_sg[3]) * sizeof(T);
 }
 
 // Warps per block of the anchor substep (shared memory of 11 ntheta values per
@@ -796,7 +882,7 @@ mm_status anchor_alloc(mm_handle* h) {
   if (need + (1 << 20) > freeb) return fail(h, MM_ERR_OOM, "anchor buffers do not fit");
   CK(cudaMalloc((void**)&h->anc_off, (size_t)h->g.ntheta * h->g.ns * sizeof(int2)));
   CK(cudaMalloc((void**)&h->anc_widx, (size_t)h->g.ntheta * h->g.ns * sizeof(int)));
-  CK(cudaMalloc((void**)&h->anc_widxb, (size_t)h->g.ntheta * h->g.ns * sizeof(int)));
+  CK(cudaMalloc((void**)&h->anc_wtab, 2 * (size_t)h->g.ntheta * h->g.ns * sizeof(unsigned short)));
   CK(cudaMalloc((void**)&h->anc_runend, (size_t)h->g.ntheta * h->g.ns * sizeof(unsigned)));
   CK(cudaMalloc((void**)&h->anc_cacc, nc * 8));
   CK(cudaMalloc((void**)&h->anc_fsc, nc * 8));
@@ -839,8 +925,10 @@ mm_status anchor_table(mm_handle* h) {
   std::vector<int> widx((size_t)nth * ns), widxb((size_t)nth * ns);
   h->anc_win[0] = h->anc_win[1] = h->anc_win[2] = h->anc_win[3] = 0;
   // a block's 4 warps share one window when they take 4 consecutive cells of a
-  // row (nx a multiple of 4) and the widened window fits
-  h->anc_bw = nx % 4 == 0 && (wx + 3) * wy <= kAnchorBlockWindowMax && wx * wy <= kAnchorWindowMax;
+  // row (nx a multiple of 4), the widened window fits and the window is no
+  // wider or taller than the grid (a window coordinate then wraps at most once)
+  h->anc_bw = nx % 4 == 0 && (wx + 3) * wy <= kAnchorBlockWindowMax && wx * wy <= kAnchorWindowMax &&
+              wx <= nx && wy <= ny;
   if (wx * wy <= kAnchorWindowMax) {
     for (size_t q = 0; q < widx.size(); ++q) {
       widx[q] = (int)((raw[q].y - ymin) * wx + (raw[q].x - xmin));
@@ -854,62 +942,94 @@ mm_status anchor_table(mm_handle* h) {
   CK(cudaStreamSynchronize(h->stream));
   CK(cudaMemcpy(h->anc_off, off.data(), off.size() * sizeof(int2), cudaMemcpyHostToDevice));
   CK(cudaMemcpy(h->anc_widx, widx.data(), widx.size() * sizeof(int), cudaMemcpyHostToDevice));
-  CK(cudaMemcpy(h->anc_widxb, widxb.data(), widxb.size() * sizeof(int), cudaMemcpyHostToDevice));
   // the run ends of each lane slot of V nodes: a node whose successor in the
   // slot has another anchor, and the slot's last node (the window indices of
-  // two nodes are equal exactly when their offsets are), with the number of
-  // slot runs before the slot; the block window's entry of each slot run
+  // two nodes are equal exactly when their offsets are); the block window's
+  // entry of each slot run and each node's slot run
   const int V = h->V, nsl = ns / V;
+  const size_t nn = (size_t)nth * ns;
   std::vector<unsigned> runend((size_t)nth * nsl, 0);
-  std::vector<int> sr_w;
+  std::vector<int> sr_w, node_run(nn);
   for (int k = 0; k < nth; ++k)
     for (int sl = 0; sl < nsl; ++sl) {
       unsigned m = 0;
-      const unsigned first = (unsigned)sr_w.size();
       for (int v = 0; v < V; ++v) {
         const size_t q = (size_t)k * ns + sl * V + v;
+        node_run[q] = (int)sr_w.size();
         if (v == V - 1 || raw[q].x != raw[q + 1].x || raw[q].y != raw[q + 1].y) {
           m |= 1u << v;
           sr_w.push_back(widxb[q]);
         }
       }
-      runend[(size_t)k * nsl + sl] = m | (first << 8);
+      runend[(size_t)k * nsl + sl] = m;
     }
   CK(cudaMemcpy(h->anc_runend, runend.data(), runend.size() * sizeof(unsigned),
                 cudaMemcpyHostToDevice));
-  // the block window's (entry, run) list: run r of the group's cell c lands in
-  // entry widxb + c; sorted by entry, cut into one chunk per thread of the
-  // block; entries and run indices must fit their bit fields
+  // The block-window form: the slot runs ordered (stably) by window entry, the
+  // same order in every cell; nsrp = 32 ch places (an odd ch: the lanes' reads
+  // of their places fall in distinct banks), the last entry's places running
+  // on over the zeros past nsr. Places, entries and per-entry indices must fit
+  // 16 bits.
   const long long nsr = (long long)sr_w.size();
+  const long long ch = ((nsr + 31) / 32) | 1, nsrp = 32 * ch;
+  const long long wnb = (wx + 3) * wy;
   if (h->anc_rtab) cudaFree(h->anc_rtab);
   h->anc_rtab = nullptr;
   h->anc_nsr = (int)nsr;
-  h->anc_rt_e = 0;
-  if (h->anc_bw && (4 * nsr + 1 > 0xffff || (wx + 3) * wy > 0x7fff)) h->anc_bw = false;
+  h->anc_sg[0] = h->anc_sg[1] = h->anc_sg[2] = h->anc_sg[3] = 0;
+  if (h->anc_bw && (nsrp >= 0xffff || wnb >= 0xffff)) h->anc_bw = false;
   if (h->anc_bw) {
-    std::vector<std::pair<int, int>> lst;  // (entry, index among the block's sums)
-    lst.reserve((size_t)4 * nsr);
-    for (int c = 0; c < 4; ++c)
-      for (long long r = 0; r < nsr; ++r) lst.emplace_back(sr_w[r] + c, (int)(c * nsr + r));
-    std::stable_sort(lst.begin(), lst.end(),
-                     [](const std::pair<int, int>& p, const std::pair<int, int>& q) {
-                       return p.first < q.first;
-                     });
-    const int n = (int)lst.size(), c = (n + 127) / 128;  // a thread's chunk
-    const int E = (c + mm::kRtBatch - 1) / mm::kRtBatch * mm::kRtBatch;
-    const unsigned pad = (unsigned)(4 * nsr);  // the zero after the sums
-    std::vector<unsigned> tab((size_t)E * 128, pad);
-    for (int t = 0; t < 128; ++t)
-      for (int i = 0; i < c; ++i) {
-        const int p = t * c + i;
-        if (p >= n) break;
-        const bool end = i + 1 == c || p + 1 >= n || lst[p + 1].first != lst[p].first;
-        tab[(size_t)i * 128 + t] =
-            (unsigned)lst[p].second | ((unsigned)lst[p].first << 16) | (end ? 1u << 31 : 0u);
-      }
+    std::vector<int> ord((size_t)nsr);
+    for (long long r = 0; r < nsr; ++r) ord[r] = (int)r;
+    std::stable_sort(ord.begin(), ord.end(), [&](int p, int q) { return sr_w[p] < sr_w[q]; });
+    std::vector<int> place((size_t)nsr);
+    for (long long p = 0; p < nsr; ++p) place[ord[p]] = (int)p;
+    // node tables: each node's window entry and its slot run's place
+    std::vector<unsigned short> wt(2 * nn);
+    for (size_t q = 0; q < nn; ++q) {
+      wt[q] = (unsigned short)widxb[q];
+      wt[nn + q] = (unsigned short)place[node_run[q]];
+    }
+    // the places that end an entry's places, and each entry's index among a
+    // cell's per-entry sums (in place order)
+    std::vector<char> end((size_t)nsrp, 0);
+    for (long long p = 0; p + 1 < nsr; ++p) end[p] = sr_w[ord[p]] != sr_w[ord[p + 1]];
+    end[nsrp - 1] = 1;
+    std::vector<int> key_rank((size_t)wnb, 0xffff);
+    int nk = 0;
+    for (long long p = 0; p < nsrp; ++p)
+      if (end[p]) key_rank[sr_w[ord[std::min(p, nsr - 1)]]] = nk++;
+    // lane chunks: end marks per lane ([nw][32] words) and ends before each lane
+    const int nw = (int)((ch + 31) / 32);
+    std::vector<unsigned> tab(2 * (size_t)wnb + 32 * (size_t)nw + 32, 0);
+    unsigned* bits = tab.data() + 2 * wnb;
+    unsigned* rank0 = bits + 32 * nw;
+    int before = 0;
+    for (int l = 0; l < 32; ++l) {
+      rank0[l] = (unsigned)before;
+      for (long long i = 0; i < ch; ++i)
+        if (end[l * ch + i]) {
+          bits[(i / 32) * 32 + l] |= 1u << (i % 32);
+          ++before;
+        }
+    }
+    // per block-window entry, the per-entry sum index of entry e - c in cell c
+    const long long wxb = wx + 3;
+    for (long long e = 0; e < wnb; ++e) {
+      const long long wxi = e % wxb;
+      unsigned r4[4];
+      for (int c = 0; c < 4; ++c)
+        r4[c] = (wxi - c >= 0 && wxi - c < wx) ? (unsigned)key_rank[e - c] : 0xffffu;
+      tab[2 * e] = r4[0] | (r4[1] << 16);
+      tab[2 * e + 1] = r4[2] | (r4[3] << 16);
+    }
+    CK(cudaMemcpy(h->anc_wtab, wt.data(), wt.size() * sizeof(unsigned short), cudaMemcpyHostToDevice));
     CK(cudaMalloc((void**)&h->anc_rtab, tab.size() * sizeof(unsigned)));
     CK(cudaMemcpy(h->anc_rtab, tab.data(), tab.size() * sizeof(unsigned), cudaMemcpyHostToDevice));
-    h->anc_rt_e = E;
+    h->anc_sg[0] = (int)nsrp;
+    h->anc_sg[1] = (int)ch;
+    h->anc_sg[2] = nw;
+    h->anc_sg[3] = nk;
   }
   // captured substep graphs hold the window and block shape as launch arguments
   for (auto& kv : h->graphs) cudaGraphExecDestroy(kv.second);

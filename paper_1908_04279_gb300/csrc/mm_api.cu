@@ -45,7 +45,7 @@ mm_status free_all(mm_handle* h) {
   if (h->diff_tab) cudaFree(h->diff_tab);
   if (h->local_n) cudaFree(h->local_n);
   void* anc[8] = {h->anc_off,  h->anc_cacc,  h->anc_fsc,    h->anc_flags,
-                  h->anc_widx, h->anc_widxb, h->anc_runend, h->anc_rtab};
+                  h->anc_widx, h->anc_wtab,  h->anc_runend, h->anc_rtab};
   for (void* p : anc)
     if (p) cudaFree(p);
   void* ptrs[] = {h->mb,  h->psi[0], h->psi[1], h->nb[0],   h->nb[1],

@@ -144,11 +144,12 @@ struct mm_handle {
   int anc_wpb = 4;              // warps per block of the anchor substep
   void* anc_off = nullptr;      // [nth][ns] int2 anchor cell offsets
   int* anc_widx = nullptr;      // [nth][ns] index of each node's anchor in the window
-  int* anc_widxb = nullptr;     // [nth][ns] the same in a block's window (4 cells of a row)
+  unsigned short* anc_wtab = nullptr;  // [2][nth][ns] block-window entry and run place of each node
   bool anc_bw = false;          // the block's 4 warps share one window
-  unsigned* anc_runend = nullptr;  // [nth][ns / V] run ends and first run of each lane slot
-  unsigned* anc_rtab = nullptr;    // [rt_e][128] the block window's (entry, run) chunks
-  int anc_rt_e = 0, anc_nsr = 0;   // chunk length; slot runs per cell
+  unsigned* anc_runend = nullptr;  // [nth][ns / V] run ends of each lane slot
+  unsigned* anc_rtab = nullptr;    // block window: per-entry sum indices, lane end marks and counts
+  int anc_nsr = 0;                 // slot runs per cell
+  int anc_sg[4] = {0, 0, 0, 0};    // block window: places, lane chunk, mark words, entries
   int anc_win[4] = {0, 0, 0, 0};  // window: first x and y offset, width, height (0: none)
   double* anc_cacc = nullptr;   // [cells] float64 accumulators of C
   double* anc_fsc = nullptr;    // [cells] scale-down factors

@@ -380,7 +380,17 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
       U16Pack<V> pos = wps;
       if (act) {
         const Pack<T, V> q = qn;
-        if (WIN) {
+        if (BW) {
+          // the free motors of each node's anchor (a read per node: cheaper
+          // than selecting the runs' first nodes)
+          ends = en & 0xffu;
+#pragma unroll
+          for (int v = 0; v < V; ++v) {
+            M[v] = q.v[v];
+            anc[v] = (int)u16_at<V>(wen, v) + wib;
+            mfv[v] = wmf[anc[v]];
+          }
+        } else if (WIN) {
           // the free motors of each run's anchor, read once at the run's
           // first node
           ends = en & 0xffu;
@@ -389,10 +399,7 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
 #pragma unroll
           for (int v = 0; v < V; ++v) {
             M[v] = q.v[v];
-            if (BW)
-              anc[v] = (int)u16_at<V>(wen, v) + wib;
-            else
-              anc[v] = wn.v[v];
+            anc[v] = wn.v[v];
             if ((starts >> v) & 1u) cur = wmf[anc[v]];
             mfv[v] = cur;
           }
@@ -490,13 +497,24 @@ __global__ void __launch_bounds__(128, MM_ANCHOR_MIN_BLOCKS) k_substep_anchor(co
       for (int w = 0; w < x.nw; ++w) {
         const unsigned m = __ldg(x.sgbits + 32 * w + lane);
         const T* src = rbw + lane * x.ch + 32 * w;
-        const int n = min(32, x.ch - 32 * w);
+        if (32 * w + 32 <= x.ch) {  // a whole word of places: constant bit masks
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            acc += src[i];
+            if (m & (1u << i)) {
+              sw[r++] = acc;
+              acc = T(0);
+            }
+          }
+        } else {
+          const int n = x.ch - 32 * w;
 #pragma unroll 4
-        for (int i = 0; i < n; ++i) {
-          acc += src[i];
-          if ((m >> i) & 1u) {
-            sw[r++] = acc;
-            acc = T(0);
+          for (int i = 0; i < n; ++i) {
+            acc += src[i];
+            if ((m >> i) & 1u) {
+              sw[r++] = acc;
+              acc = T(0);
+            }
           }
         }
       }

@@ -54,11 +54,13 @@ UNIT = "cell-updates/s"
 CSRC = os.path.join(ROOT, "paper_1908_04279_gb300", "csrc")
 # sources of each kernel a committed profile summary may describe
 KERNEL_SRCS = {
-    "k_substep": ("mm_step.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
+    "k_substep": ("mm_step.cu", "mm_async.cuh", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
     "k_substep_batch": ("mm_batch.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
-    "k_adjoint": ("mm_adjoint.cu", "mm_walk.cuh", "mm_internal.cuh"),
+    "k_adjoint": ("mm_adjoint.cu", "mm_async.cuh", "mm_cell.cuh", "mm_walk.cuh",
+                  "mm_internal.cuh"),
     "k_motor_local": ("mm_local.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
-    "k_substep_anchor": ("mm_anchor.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
+    "k_substep_anchor": ("mm_anchor.cu", "mm_async.cuh", "mm_cell.cuh", "mm_walk.cuh",
+                         "mm_internal.cuh"),
     "k_substep_tl": ("mm_tangent.cu", "mm_cell.cuh", "mm_walk.cuh", "mm_internal.cuh"),
     "k_rc_motor": ("mm_capture.cu", "mm_async.cuh", "mm_cell.cuh", "mm_walk.cuh",
                    "mm_internal.cuh"),

@@ -98,8 +98,9 @@ def test_fp64_anchor_long_filaments(mmod, oracle_mod):
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_anchor_wide_window(mmod, oracle_mod, precision):
     """A block's window of 25 x 21 anchor cells (48 x 40 cells, l/L = 0.5, 32 x 32):
-    each of the block's threads walks 26 to 28 entries of the sorted (window
-    entry, run) list, in several batches, and the shared window holds every
+    a cell's 832 slot runs (888 in float64) lie in 27 (29) places per lane, the
+    sums of the 289 window entries span up to 64 places and so several lanes
+    (joined by the scan over the lanes), and the shared window holds every
     anchor; the row length is a multiple of 4, so 4 cells share one window."""
     g = Grid(48, 40, 32, 32)
     r = Rates(ell=0.5, k_on=1.4, glide=0.2)
@@ -113,7 +114,7 @@ def test_anchor_wide_window(mmod, oracle_mod, precision):
 
 def test_fp64_anchor_scale_down_shared_window(mmod, oracle_mod):
     """The forced scale-down on a grid whose row length is a multiple of 4 (the
-    block's 4 cells share one window and sum their runs by the sorted walk)."""
+    block's 4 cells share one window and sum their runs per window entry)."""
     g = Grid(8, 6, 12, 16)
     r = Rates(ell=0.25, k_on=80.0, k_off=0.2)
     psi, mb = seeded(g, 241, mb_scale=0.05)
@@ -263,7 +264,8 @@ def test_anchor_precision128_full_size(mmod, oracle_mod):
 
 def test_anchor_large512_conservation_and_sampled_anchors(mmod, oracle_mod):
     """The bench's large anchor workload (512^2 x 64^2, l/L = 0.05, float32:
-    a 27 x 27 window, each thread of a block walking 72 list entries): after
+    a 27 x 27 window, each cell's 2072 slot runs summed per window entry in 65
+    places per lane, three words of end marks): after
     5 substeps the filament number is conserved, bound + free motors equal the
     total, and the coarse density of 32 sampled anchor cells equals the sum of
     psi Mb ds dtheta over the configurations whose heads lie in them,

@@ -10,8 +10,9 @@
 //                     the per-node binding term, n_b of the row, and the row's
 //                     contributions psi ds dtheta Mb added into the anchors'
 //                     float64 accumulators (runs of nodes with the same anchor
-//                     summed in registers first; with a block window the run
-//                     sums are summed per window entry by a sorted walk, else
+//                     summed in registers first; with a block window each
+//                     warp sums its cell's run sums per window entry and the
+//                     block adds its 4 cells' sums, one atomic per entry; else
 //                     one atomic per run);
 //   k_anchor_close    thread per anchor: C, the scale-down factor f, Mf = M - C,
 //                     accumulator reset; a flag if any anchor scaled down;

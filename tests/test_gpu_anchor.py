@@ -151,23 +151,28 @@ def test_fp32_anchor_within_tolerance(mmod, oracle_mod):
     check(*run_both(mmod, oracle_mod, g, r, psi, mb, None, u, 20, "fp32"), TOL["fp32"])
 
 
-def test_anchor_zero_length_equals_local_path(mmod):
+@pytest.mark.parametrize("nx,precision,tol", [(10, "fp64", 1e-13), (12, "fp64", 1e-13),
+                                               (12, "fp32", 1e-5)])
+def test_anchor_zero_length_equals_local_path(mmod, nx, precision, tol):
     """With l/L = 0 every anchor is the filament's own cell: the anchor kernels
-    give the local kernel's result (to rounding order)."""
-    g = Grid(10, 8, 16, 16)
+    give the local kernel's result (to rounding order). With 10 cells a row
+    each warp keeps its own window; with 12 the block's 4 cells share one, and
+    a cell's run sums all belong to one window entry: every place of every
+    lane forms one entry, completed by the scan over all 32 lanes."""
+    g = Grid(nx, 8, 16, 16)
     r = Rates(ell=0.0)
     psi, mb = seeded(g, 231)
     u = random_divfree_flow(g, 232, 4, 0.1)
     res = []
     for anchors in (False, True):
-        with mmod.Simulation(g, r, "fp64") as sim:
+        with mmod.Simulation(g, r, precision) as sim:
             sim.set_anchors(anchors)
             sim.set_state(psi, np.ascontiguousarray(mb))
             sim.set_velocity(u)
             sim.step(15)
             res.append(sim.get_state())
     for k in ("psi", "mb", "mf", "c"):
-        assert rel_l2(res[1][k], res[0][k]) <= 1e-13, k
+        assert rel_l2(res[1][k], res[0][k]) <= tol, k
 
 
 def test_anchor_toggle_and_rates(mmod, oracle_mod):

@@ -163,25 +163,6 @@ __device__ __forceinline__ void scatter_runs(double* acc, const int (&anc)[V], c
   atomicAdd(acc + cur, (double)s);
 }
 
-// The same into a shared-memory window accumulator in the state precision.
-template <typename T, int V>
-__device__ __forceinline__ void scatter_runs_smem(T* acc, const int (&widx)[V], const T (&M)[V],
-                                                  T w) {
-  int cur = widx[0];
-  T s = w * M[0];
-#pragma unroll
-  for (int v = 1; v < V; ++v) {
-    if (widx[v] == cur) {
-      s += w * M[v];
-    } else {
-      atomicAdd(acc + cur, s);
-      cur = widx[v];
-      s = w * M[v];
-    }
-  }
-  atomicAdd(acc + cur, s);
-}
-
 // The same driven by the run-end mask of the lane's slot: one shared atomic
 // per run, no comparison of anchors.
 template <typename T, int V>

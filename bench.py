@@ -127,11 +127,15 @@ def read_peaks():
 # from the scheme: per RK2 stage the backward difference, its half, two sign
 # transfers, two minima, the maximum with zero, the flux fma, the flux
 # difference and two fmas of the stage update (11); two stages, plus one add of
-# the n_b sum. The local-step kernel runs them on the float32 pipe, the float64
-# substep on the float64 pipe (its per-(cell, theta) transport work, about 40
-# operations per row, adds under 1 per motor value at 64 nodes and is left out).
+# the n_b sum. The local-step kernel runs them on the float32 pipe. The float64
+# substep runs 13 of them on the float64 pipe (difference, half, flux, flux
+# difference, two stage fmas; the n_b add) and the sign transfers, minima and
+# maximum (10) on the integer pipe, on the values' bit patterns; its per-(cell,
+# theta) transport work, about 40 operations per row, adds under 1 per motor
+# value at 64 nodes and is left out.
 LOCAL_OPS = 23
 SUBSTEP_OPS = 23
+SUBSTEP_FP64_PIPE_OPS = 13
 
 
 def wname_of(leg: dict) -> str:
@@ -813,7 +817,10 @@ def run_ours(args):
                                   "unit": "Tops/s", "frac": fp64_ops / fp64_peak,
                                   "kernel": "k_substep (float64)",
                                   "ops_per_cell_update": SUBSTEP_OPS,
-                                  "peak_source": "measured (mm_alu_peak, float64 fma)"}},
+                                  "peak_source": "measured (mm_alu_peak, float64 fma)",
+                                  "fp64_pipe_ops_per_cell_update": SUBSTEP_FP64_PIPE_OPS,
+                                  "fp64_pipe_frac": fp64_ops * SUBSTEP_FP64_PIPE_OPS
+                                  / SUBSTEP_OPS / fp64_peak}},
             other: o_leg,
             "alu_peaks": {k: {"fma_per_s": v["fma_per_s"], "ms_per_launch": v["ms_per_launch"]}
                           for k, v in alu.items()},

@@ -117,11 +117,7 @@ __device__ __forceinline__ void rc_walk(const T (&M)[kRcV], unsigned mask, T (&D
       if (last) r = 0.0f;
       F[v] = M[v] + copysignf(r, b);
     } else {
-      T sgn = copysign(T(1), b);
-      if (last) sgn = T(0);
-      const T A = a * sgn, hA = ha * sgn, hB = fabs(hb), B = fabs(b);
-      const T r = max3_t(tmin(A, hB), tmin(hA, B), T(0));
-      F[v] = fma_t(r, sgn, M[v]);
+      F[v] = superbee64(a, ha, b, hb, last, M[v]).F;  // the limiter on the bit patterns
     }
   }
   const T fl = __shfl_up_sync(0xffffffffu, F[kRcV - 1], 1);

@@ -128,23 +128,23 @@ __device__ __forceinline__ void walk_tl(const T (&M)[V], const T (&dM)[V], T (&D
   T F[V], dF[V];
 #pragma unroll
   for (int v = 0; v < V; ++v) {
-    T sgn = copysign(T(1), d[v + 1]);
-    if (v == V - 1 && last) sgn = T(0);  // plus end: F = M, no slope
-    const T A = d[v] * sgn, hA = hd[v] * sgn;
-    const T hB = fabs(hd[v + 1]), B = fabs(d[v + 1]);
-    const T t1 = tmin(A, hB), t2 = tmin(hA, B);
-    const T r = max3_t(t1, t2, T(0));
-    F[v] = fma_t(r, sgn, M[v]);
     bool pos, p1, x1a, x2a;
     if constexpr (sizeof(T) == 8) {
-      // the decisions of walk_dflux<double, V, true>: on the bit patterns
-      const long long iA = __double_as_longlong(A), ihA = __double_as_longlong(hA);
-      const long long ihB = __double_as_longlong(hB), iB = __double_as_longlong(B);
-      pos = __double_as_longlong(r) > 0;
-      p1 = __double_as_longlong(t1) > __double_as_longlong(t2);
-      x1a = iA < ihB;
-      x2a = ihA < iB;
+      // the flux and decisions of walk_dflux<double, V, true> (bit patterns)
+      const Lim64 q = superbee64(d[v], hd[v], d[v + 1], hd[v + 1], v == V - 1 && last, M[v]);
+      F[v] = q.F;
+      pos = q.pos;
+      p1 = q.p1;
+      x1a = q.x1a;
+      x2a = q.x2a;
     } else {
+      T sgn = copysign(T(1), d[v + 1]);
+      if (v == V - 1 && last) sgn = T(0);  // plus end: F = M, no slope
+      const T A = d[v] * sgn, hA = hd[v] * sgn;
+      const T hB = fabs(hd[v + 1]), B = fabs(d[v + 1]);
+      const T t1 = tmin(A, hB), t2 = tmin(hA, B);
+      const T r = max3_t(t1, t2, T(0));
+      F[v] = fma_t(r, sgn, M[v]);
       pos = r > T(0);
       p1 = t1 > t2;
       x1a = A < hB;

@@ -41,6 +41,43 @@ __device__ __forceinline__ double max3_t(double a, double b, double c) {
   return fmax(fmax(a, b), c);
 }
 
+// The sign bit of a float64 pattern.
+constexpr long long kSign64 = (long long)0x8000000000000000ull;
+
+// The float64 Superbee flux F = M + sigma/2 of one node (the general form of
+// walk_dflux below) and its branch decisions, with the sign flips, magnitudes,
+// minima and maximum on the bit patterns (integer pipe instead of the float64
+// one, whose rate is a small fraction of float32's), the same values bit for
+// bit: A = a sgn and hA = a/2 sgn take the sign bit of b, |b| and |b|/2 drop
+// it; for hB, B >= 0 the signed 64-bit patterns order as the values do and a
+// negative A (sign bit set, -0 included) orders below them, so min(A, hB) is
+// the smaller pattern; max(t1, t2, 0) is the largest pattern, a negative one
+// giving +0 (fmin and fmax order -0 below +0 alike); F = M + sgn r is one
+// rounded addition, as the fma with sgn = +-1 is (+0 added at the plus end,
+// where sgn = 0 made the product +0). The decisions: r > 0, t1 > t2, A < hB,
+// hA < B (where -0 and +0 would differ, r = 0).
+struct Lim64 {
+  double F;
+  bool pos, p1, x1a, x2a;
+};
+__device__ __forceinline__ Lim64 superbee64(double a, double ha, double b, double hb, bool endp,
+                                            double M) {
+  const long long ib = __double_as_longlong(b);
+  const long long sb = ib & kSign64;
+  const long long iA = __double_as_longlong(a) ^ sb, ihA = __double_as_longlong(ha) ^ sb;
+  const long long iB = ib & ~kSign64, ihB = __double_as_longlong(hb) & ~kSign64;
+  const long long it1 = iA < ihB ? iA : ihB, it2 = ihA < iB ? ihA : iB;
+  long long ir = it1 > it2 ? it1 : it2;
+  if (ir < 0 || endp) ir = 0;
+  Lim64 q;
+  q.F = __dadd_rn(M, __longlong_as_double(endp ? 0ll : ir ^ sb));
+  q.pos = ir > 0;
+  q.p1 = it1 > it2;
+  q.x1a = iA < ihB;
+  q.x2a = ihA < iB;
+  return q;
+}
+
 // min(|a|, |b|) carrying the sign sign(a) xor sign(b): positive where a and b
 // agree in sign, negative where they disagree (one instruction).
 __device__ __forceinline__ float min_xorsign_abs(float a, float b) {
@@ -91,6 +128,18 @@ __device__ __forceinline__ void walk_dflux(const T (&M)[V], T (&D)[V], bool firs
       if (v == V - 1 && last) r = T(0);  // plus end: F = M, no slope
       F[v] = M[v] + copysignf(r, d[v + 1]);
     }
+  } else if constexpr (sizeof(T) == 8) {
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const Lim64 q = superbee64(d[v], hd[v], d[v + 1], hd[v + 1], v == V - 1 && last, M[v]);
+      F[v] = q.F;
+      if constexpr (COEF) {
+        const T a1 = q.x1a ? T(1) : T(0), b1 = q.x1a ? T(0) : T(0.5);
+        const T a2 = q.x2a ? T(0.5) : T(0), b2 = q.x2a ? T(0) : T(1);
+        ga[v] = q.pos ? (q.p1 ? a1 : a2) : T(0);
+        gb[v] = q.pos ? (q.p1 ? b1 : b2) : T(0);
+      }
+    }
   } else {
 #pragma unroll
     for (int v = 0; v < V; ++v) {
@@ -102,24 +151,7 @@ __device__ __forceinline__ void walk_dflux(const T (&M)[V], T (&D)[V], bool firs
       const T r = max3_t(t1, t2, T(0));
       F[v] = fma_t(r, sgn, M[v]);
       if constexpr (COEF) {
-        bool pos, p1, x1a, x2a;
-        if constexpr (sizeof(T) == 8) {
-          // the same four decisions on the bit patterns (integer pipe instead of
-          // the float64 one): hB, B, r >= 0 order as their signed 64-bit
-          // patterns, a negative A or hA (sign bit set) orders below them, and
-          // the cases where -0 and +0 would differ all have r = 0 (pos false)
-          const long long iA = __double_as_longlong(A), ihA = __double_as_longlong(hA);
-          const long long ihB = __double_as_longlong(hB), iB = __double_as_longlong(B);
-          pos = __double_as_longlong(r) > 0;
-          p1 = __double_as_longlong(t1) > __double_as_longlong(t2);
-          x1a = iA < ihB;
-          x2a = ihA < iB;
-        } else {
-          pos = r > T(0);
-          p1 = t1 > t2;
-          x1a = A < hB;
-          x2a = hA < B;
-        }
+        const bool pos = r > T(0), p1 = t1 > t2, x1a = A < hB, x2a = hA < B;
         const T a1 = x1a ? T(1) : T(0), b1 = x1a ? T(0) : T(0.5);
         const T a2 = x2a ? T(0.5) : T(0), b2 = x2a ? T(0) : T(1);
         ga[v] = pos ? (p1 ? a1 : a2) : T(0);

@@ -112,6 +112,25 @@ def test_anchor_wide_window(mmod, oracle_mod, precision):
     check(*run_both(mmod, oracle_mod, g, r, psi, mb, None, u, 6, precision), TOL[precision])
 
 
+@pytest.mark.parametrize("dims,precision,ell", [((8, 6, 12, 20), "fp32", 0.3),
+                                                ((8, 6, 10, 9), "fp32", 0.3),
+                                                ((8, 8, 16, 16), "fp64", 0.9)])
+def test_anchor_block_window_lane_widths(mmod, oracle_mod, dims, precision, ell):
+    """The block-window form with 4 values per lane (ns = 20) and with one
+    (ns = 9) in float32, whose window entries and run places load as 8- and
+    2-byte pieces; and in float64 a 7 x 7 window on an 8 x 8 grid (l/L = 0.9),
+    so that the block's 10 window columns wrap the grid and some cells appear
+    twice in the window."""
+    g = Grid(*dims)
+    r = Rates(ell=ell, k_on=1.5, glide=0.1)
+    ox, oy = oracle_mod.anchor_offsets(g, r)
+    wx, wy = ox.max() - ox.min() + 1, oy.max() - oy.min() + 1
+    assert g.nx % 4 == 0 and wx <= g.nx and wy <= g.ny
+    psi, mb = seeded(g, 251 + sum(dims))
+    u = random_divfree_flow(g, 252, 4, 0.1)
+    check(*run_both(mmod, oracle_mod, g, r, psi, mb, None, u, 8, precision), TOL[precision])
+
+
 def test_fp64_anchor_scale_down_shared_window(mmod, oracle_mod):
     """The forced scale-down on a grid whose row length is a multiple of 4 (the
     block's 4 cells share one window and sum their runs per window entry)."""
